@@ -1,0 +1,108 @@
+"""Label interpolation of Eq. 5 and the partition rule of Sec. 4.1 (test infrastructure only).
+
+Eq. 5: x_j = argmin ||M x - c_j^r||^2 + gamma x^T g(L) x, whose minimiser
+solves (M^T M + gamma g(L)) x = M^T c_j^r, one system per cluster j
+(Alg. 2 step 7).  M^T M is the diagonal 0/1 mask of sampled nodes.
+
+Readings: g(L) = L^p with p = 4 and gamma = 1e-3 for the workloads (the
+paper's preferred high-pass g = 1 - h~ is a separate option); the systems
+are solved by conjugate gradients, one of the solvers Sec. 4.4 names, with
+a diagonal preconditioner mask + gamma, to relative residual 1e-10.  On a
+connected component holding no sample the right-hand side is zero and the
+solution there is zero.  Labels: node i goes to the j maximising
+x_j(i) / ||x_j|| (ties to the lowest j; a zero column scores 0).
+
+Pins (tests/test_oracle_interp.py): agreement with a dense LAPACK solve;
+n = N with gamma -> 0 returns c^r; on disjoint regular cliques with every
+clique sampled the indicators lie in ker L, so x_j is the exact indicator.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+
+def rhs(n_nodes: int, omega: np.ndarray, sample_labels: np.ndarray, k: int) -> np.ndarray:
+    """B = M^T C^r: column j holds 1 at sampled nodes labelled j."""
+    b = np.zeros((n_nodes, k))
+    b[np.asarray(omega, dtype=np.int64), np.asarray(sample_labels, dtype=np.int64)] = 1.0
+    return b
+
+
+def mask(n_nodes: int, omega: np.ndarray) -> np.ndarray:
+    m = np.zeros(n_nodes)
+    m[np.asarray(omega, dtype=np.int64)] = 1.0
+    return m
+
+
+def system_matrix(lap: sp.csr_matrix, msk: np.ndarray, gamma: float, power: int) -> sp.csr_matrix:
+    """M^T M + gamma L^p as an explicit sparse matrix (small graphs)."""
+    g = sp.identity(lap.shape[0], format="csr")
+    for _ in range(power):
+        g = g @ lap
+    return (sp.diags(msk) + gamma * g).tocsr()
+
+
+def apply_system(lap: sp.csr_matrix, msk: np.ndarray, gamma: float, power: int, x: np.ndarray) -> np.ndarray:
+    """(M^T M + gamma L^p) x with p successive products by L."""
+    t = x
+    for _ in range(power):
+        t = lap @ t
+    return msk[:, None] * x + gamma * t if x.ndim == 2 else msk * x + gamma * t
+
+
+def cg(apply, b: np.ndarray, precond: np.ndarray, tol: float = 1e-10, max_iter: int = 20000):
+    """Preconditioned CG on every column of b independently.
+
+    Returns (x, iterations, max relative residual).
+    """
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = r / precond[:, None]
+    p = z.copy()
+    rz = np.sum(r * z, axis=0)
+    bn = np.linalg.norm(b, axis=0)
+    active = bn > 0
+    it = 0
+    for it in range(1, max_iter + 1):
+        rn = np.linalg.norm(r, axis=0)
+        conv = ~active | (rn <= tol * np.where(bn > 0, bn, 1.0))
+        if np.all(conv):
+            it -= 1
+            break
+        ap = apply(p)
+        pap = np.sum(p * ap, axis=0)
+        alpha = np.where(conv | (pap == 0), 0.0, rz / np.where(pap == 0, 1.0, pap))
+        x += alpha * p
+        r -= alpha * ap
+        z = r / precond[:, None]
+        rz_new = np.sum(r * z, axis=0)
+        beta = np.where(conv | (rz == 0), 0.0, rz_new / np.where(rz == 0, 1.0, rz))
+        p = np.where(conv, p, z + beta * p)
+        rz = np.where(conv, rz, rz_new)
+    rel = np.linalg.norm(b - apply(x), axis=0) / np.where(bn > 0, bn, 1.0)
+    return x, it, float(np.max(rel)) if rel.size else 0.0
+
+
+def interpolate(lap: sp.csr_matrix, omega: np.ndarray, sample_labels: np.ndarray, k: int,
+                gamma: float = 1e-3, power: int = 4, tol: float = 1e-10, max_iter: int = 20000):
+    """Solve Eq. 5 for every cluster; returns (X int N x k, iterations, max rel residual)."""
+    n_nodes = lap.shape[0]
+    msk = mask(n_nodes, omega)
+    b = rhs(n_nodes, omega, sample_labels, k)
+    pre = msk + gamma
+    x, it, res = cg(lambda v: apply_system(lap, msk, gamma, power, v), b, pre, tol, max_iter)
+    return x, it, res
+
+
+def interpolate_dense(lap_dense: np.ndarray, omega, sample_labels, k, gamma=1e-3, power=4):
+    n_nodes = lap_dense.shape[0]
+    a = np.diag(mask(n_nodes, omega)) + gamma * np.linalg.matrix_power(lap_dense, power)
+    return np.linalg.solve(a, rhs(n_nodes, omega, sample_labels, k))
+
+
+def labels_from_indicators(x: np.ndarray) -> np.ndarray:
+    """Sec. 4.1: node i -> argmax_j x_j(i) / ||x_j|| (ties to the lowest j)."""
+    nrm = np.linalg.norm(x, axis=0)
+    scaled = np.where(nrm > 0, x / np.where(nrm > 0, nrm, 1.0), 0.0)
+    return np.argmax(scaled, axis=1).astype(np.int32)
