@@ -1,0 +1,301 @@
+/*
+ * csc.h -- C ABI of the GB300 (sm_103a) Compressive Spectral Clustering library.
+ *
+ * Compressive Spectral Clustering (Tremblay, Puy, Gribonval, Vandergheynst,
+ * ICML 2016) replaces the partial eigendecomposition of spectral clustering by
+ * polynomial filtering of a few random signals with the normalized Laplacian
+ * L = I - D^-1/2 W D^-1/2 (Sec. 2.1), clusters a random subset of the nodes
+ * and interpolates the labels back (Alg. 2).  This header declares every
+ * entry point of the library.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns csc_status; CSC_OK (0) on success.  Nothing
+ *    throws or aborts across this boundary.  On failure csc_last_error()
+ *    returns a thread-local message describing the last error of the
+ *    calling thread.
+ *  - The caller owns every buffer it passes in.  The library owns only the
+ *    opaque csc_graph (it copies the graph in and keeps its own device
+ *    scratch space in it) and frees everything in csc_graph_destroy.
+ *  - "device" pointers are CUDA device (or managed) memory on the current
+ *    device; "host" pointers are ordinary host memory.  Large arrays are
+ *    device pointers, scalars and short arrays are host pointers; each
+ *    argument says which.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls are stream-ordered and asynchronous unless they return
+ *    a host value, in which case they synchronize `stream` before returning.
+ *  - Node indices at this boundary are always in the caller's original node
+ *    order; any internal reordering (CSC_RCM) is invisible.
+ *  - A csc_graph is used by one host thread at a time; calls on one handle
+ *    that overlap on the GPU (different streams without ordering) race on
+ *    the handle's scratch space.
+ *  - Matrices are dense, row-major, with an explicit leading dimension
+ *    (row stride in elements) where stated.
+ */
+#ifndef CSC_H
+#define CSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CSC_API __attribute__((visibility("default")))
+#else
+#define CSC_API
+#endif
+
+/* ------------------------------------------------------------------ status */
+typedef int32_t csc_status;
+#define CSC_OK                 0
+#define CSC_E_INVALID          1  /* invalid argument; no side effects            */
+#define CSC_E_CSR              2  /* malformed CSR input                          */
+#define CSC_E_OOM              3  /* device or host allocation failed             */
+#define CSC_E_CUDA             4  /* a CUDA runtime call failed (handle poisoned) */
+#define CSC_E_NOT_CONVERGED    5  /* iterative solver hit max_iter; outputs valid */
+#define CSC_E_DEVICE_TIMEOUT   6  /* a bounded device-side wait gave up           */
+#define CSC_E_NUMERIC          7  /* non-finite values detected                   */
+#define CSC_E_UNSUPPORTED      8  /* valid but outside what this build supports   */
+
+/* storage type of the signal blocks */
+typedef int32_t csc_dtype;
+#define CSC_F32   0
+#define CSC_BF16  1
+#define CSC_F64   2
+
+/* csc_graph_create flags */
+#define CSC_RCM            1u  /* reorder nodes by reverse Cuthill-McKee internally   */
+#define CSC_CHECK_SYM      2u  /* verify W is symmetric (O(nnz log) host check)        */
+#define CSC_DEVICE_INPUT   4u  /* row_ptr / col_idx are device pointers                */
+
+/* csc_filter_random_signals flags */
+#define CSC_NORMALIZE_ROWS 1u  /* Alg. 2 step 4: divide every row by its l2 norm      */
+#define CSC_NO_JACKSON     2u  /* truncated Chebyshev (no Jackson damping)            */
+
+typedef struct csc_graph_s* csc_graph;
+
+/* Result of csc_estimate_lambda_k. */
+typedef struct {
+    double  lambda;       /* estimate of lambda_k                                     */
+    double  count;        /* eigencount at lambda (sum_j c_j(lambda) mu_j)            */
+    int32_t iters;        /* dichotomy halvings performed                             */
+    int32_t hit;          /* 1 if round(count) == k was reached, 0 if the bracket collapsed */
+    int32_t n_probes;     /* probe vectors used                                       */
+    int32_t m;            /* polynomial degree used                                   */
+    int32_t bracket_used; /* 1 if a caller bracket was given and contained the answer */
+    int32_t moment_passes;/* sparse block products spent on moments                   */
+} csc_lambda_info;
+
+/* Result of csc_interpolate. */
+typedef struct {
+    int32_t iters;            /* CG iterations performed (max over clusters)          */
+    int32_t converged;        /* 1 if every cluster reached rel_tol                   */
+    double  max_rel_residual; /* max_j ||b_j - A x_j|| / ||b_j|| at exit (FP64)       */
+} csc_cg_info;
+
+/* Parameters of the whole pipeline (csc_cluster).  Zero means "default". */
+typedef struct {
+    int32_t  k;            /* number of clusters (required, >= 1)                     */
+    int32_t  m;            /* Jackson-Chebyshev degree; default 50 (Alg. 2)           */
+    int32_t  d;            /* random signals; default ceil(4 ln N)                    */
+    int32_t  d_pad;        /* padded columns (multiple of 8); default round up of d   */
+    int64_t  n;            /* sampled nodes; default ceil(2 k ln k) (at least k)      */
+    int32_t  n_probes;     /* eigencount probes; default ceil(2 ln N)                 */
+    int32_t  g_power;      /* interpolation g(L) = L^g_power; default 4               */
+    double   gamma;        /* Eq. 5 regularisation; default 1e-3                      */
+    double   cg_tol;       /* relative residual target; default 1e-6                  */
+    int32_t  cg_max_iter;  /* default 2000                                            */
+    int32_t  replicates;   /* k-means replicates; default 20                          */
+    int32_t  km_max_iter;  /* k-means iterations; default 100                         */
+    csc_dtype storage;     /* signal-block storage; default CSC_F32                   */
+    uint64_t seed;
+    double   lambda_k;     /* > 0: skip step 1 and use this cut-off                   */
+    const double* bracket; /* NULL or host {lo, hi}: learned bracket for step 1       */
+} csc_params;
+
+/* Per-stage results and timings of csc_cluster. */
+typedef struct {
+    csc_lambda_info lambda;
+    csc_cg_info     cg;
+    double          inertia;      /* best reduced k-means inertia (FP64)             */
+    float           ms_lambda, ms_filter, ms_sample, ms_kmeans, ms_interp, ms_total;
+} csc_cluster_info;
+
+/* ---------------------------------------------------------------- graphs */
+
+/* csc_graph_create -- copy an undirected graph in CSR form into a new handle.
+ * Defines W of Sec. 2.1; degrees D_ii = sum_{j != i} W_ij are computed on the
+ * device (self loops are dropped, so they count neither in W nor in D).
+ *   N        nodes (>= 1; N < 2^31).
+ *   nnz      stored entries (row_ptr[N]); < 2^31.
+ *   row_ptr  int64[N+1], nondecreasing, row_ptr[0] = 0, row_ptr[N] = nnz.
+ *   col_idx  int32[nnz], each row strictly increasing (sorted, no duplicates),
+ *            values in [0, N).  The matrix must be symmetric (checked only with
+ *            CSC_CHECK_SYM).
+ *   weights  must be NULL: the graphs of this library are unweighted
+ *            (W_ij in {0,1}); non-NULL returns CSC_E_UNSUPPORTED.
+ *   flags    CSC_RCM | CSC_CHECK_SYM | CSC_DEVICE_INPUT.  Without
+ *            CSC_DEVICE_INPUT the arrays are host memory; with it they are
+ *            device memory, copied to the host first.  Either way the CSR is
+ *            validated on the host and every flag applies.
+ *   out      receives the handle.
+ * Errors: CSC_E_INVALID (null pointers, N < 1, nnz < 0), CSC_E_CSR (any
+ * violation above), CSC_E_OOM, CSC_E_CUDA.  Synchronizes `stream`. */
+CSC_API csc_status csc_graph_create(int64_t N, int64_t nnz, const int64_t* row_ptr,
+                            const int32_t* col_idx, const float* weights,
+                            uint32_t flags, void* stream, csc_graph* out);
+
+/* csc_graph_create_batched -- G independent graphs packed block-diagonally
+ * into one handle (graph g occupies node ids offsets[g] .. offsets[g+1]-1 of
+ * the packed graph, each with its own CSR whose column ids are local to g).
+ * Host arrays only.  Same validation as csc_graph_create per graph. */
+CSC_API csc_status csc_graph_create_batched(int32_t G, const int64_t* N, const int64_t* const* row_ptr,
+                                    const int32_t* const* col_idx, uint32_t flags,
+                                    void* stream, csc_graph* out);
+
+/* csc_graph_destroy -- free the handle and all its device memory.  NULL is a no-op. */
+CSC_API csc_status csc_graph_destroy(csc_graph g);
+
+/* csc_graph_info -- sizes: N, nnz (after self-loop removal), number of packed
+ * graphs (1 unless batched).  Any output pointer may be NULL.  Host outputs. */
+CSC_API csc_status csc_graph_info(csc_graph g, int64_t* N, int64_t* nnz, int32_t* n_graphs);
+
+/* csc_graph_degrees -- D_ii of Sec. 2.1 (integer edge counts, bit-exact) in
+ * original node order.  deg_out: host int32[N].  Synchronizes `stream`. */
+CSC_API csc_status csc_graph_degrees(csc_graph g, int32_t* deg_out, void* stream);
+
+/* ------------------------------------------------------- the Chebyshev path */
+
+/* csc_chebyshev_coefficients -- c_j = g_j gamma_j (j = 0..m) of the
+ * Jackson-Chebyshev approximation of the ideal low-pass h_{lambda_c} of Eq. 1
+ * on the variable t = lambda - 1 (Sec. 4.3, Jackson damping after Di Napoli,
+ * Polizzi and Saad): gamma_0 = 1 - theta_c/pi, gamma_j = -2 sin(j theta_c)/(j pi),
+ * theta_c = arccos(lambda_c - 1), g_j the Jackson factors with alpha = pi/(m+2).
+ * With CSC_NO_JACKSON in flags, g_j = 1.  c_out: host double[m+1].
+ * Errors: CSC_E_INVALID if m < 0, lambda_c outside [0, 2] or c_out NULL. */
+CSC_API csc_status csc_chebyshev_coefficients(double lambda_c, int32_t m, uint32_t flags, double* c_out);
+
+/* csc_filter_random_signals -- Alg. 2 steps 2-4: Y = h~_{lambda_c}(L) R with
+ * h~ the degree-m Jackson-Chebyshev polynomial, computed by the three-term
+ * recurrence X_0 = R, X_1 = (L - I) R, X_{j+1} = 2 (L - I) X_j - X_{j-1}
+ * (Sec. 2.1 "Fast graph filtering"); optionally rows normalised (step 4).
+ *   lambda_c  cut-off in [0, 2].
+ *   m         degree >= 0 (m = 0 gives Y = c_0 R).
+ *   d, d_pad  signal count and row stride (d_pad >= d, d_pad % 8 == 0).
+ *   seed      R is drawn as N(0, 1/d) by Philox4x32-10 (counter = (node id,
+ *             column/4), key = (seed, stream "signals")) with Box-Muller, unless R_in
+ *             is given.
+ *   storage   CSC_F32 / CSC_BF16 (X_j stored in bf16, arithmetic and Y in fp32)
+ *             / CSC_F64 (X_j, arithmetic and Y in fp64).
+ *   R_in      NULL, or device float[N * d_pad] row-major in original node order
+ *             (padding columns are ignored and treated as zero).
+ *   Y_out     device, N * d_pad row-major in original node order: float for
+ *             CSC_F32/CSC_BF16, double for CSC_F64.  Padding columns are zero.
+ *   flags     CSC_NORMALIZE_ROWS, CSC_NO_JACKSON.
+ * Errors: CSC_E_INVALID (no side effects), CSC_E_OOM, CSC_E_CUDA.  Asynchronous. */
+CSC_API csc_status csc_filter_random_signals(csc_graph g, double lambda_c, int32_t m, int32_t d,
+                                     int32_t d_pad, uint64_t seed, csc_dtype storage,
+                                     const float* R_in, void* Y_out, uint32_t flags,
+                                     void* stream);
+
+/* csc_kpm_moments -- eigencount moments of Sec. 4.3:
+ * mu_j = (1/n_probes) sum_l r_l^T T_j(L - I) r_l, j = 0..n_moments-1, with
+ * r_l ~ N(0, 1) drawn by Philox (key = (seed, stream "probes")), computed with
+ * ceil((n_moments-1)/2) sparse block products using T_2j = 2 T_j^2 - T_0 and
+ * T_2j+1 = 2 T_j+1 T_j - T_1, reductions in fp64.
+ *   storage  CSC_F32 or CSC_BF16 for the probe block.
+ *   mu_out   host double[n_moments].  Synchronizes `stream`.
+ * Errors: CSC_E_INVALID (n_moments < 1, n_probes < 1). */
+CSC_API csc_status csc_kpm_moments(csc_graph g, int32_t n_moments, int32_t n_probes, uint64_t seed,
+                           csc_dtype storage, double* mu_out, void* stream);
+
+/* csc_eigencount -- count(lambda) = sum_j c_j(lambda) mu_j for given moments
+ * (host, O(m)).  mu: host double[m+1].  count_out: host double. */
+CSC_API csc_status csc_eigencount(const double* mu, int32_t m, double lambda, uint32_t flags,
+                          double* count_out);
+
+/* csc_estimate_lambda_k -- Alg. 2 step 1 (Sec. 4.3): moments computed once on
+ * the device, then a dichotomy on [0, 2] evaluated on the host from them: at
+ * mid = (lo+hi)/2 stop if round(count(mid)) == k (half away from zero), else
+ * hi = mid if count(mid) > k, lo = mid otherwise; after 60 halvings or when
+ * hi - lo < 1e-12 the upper end is returned with hit = 0.
+ *   k         clusters (>= 1).   m  degree (>= 1).
+ *   n_probes  0 -> ceil(2 ln N).
+ *   bracket   NULL, or host double[2] {lo, hi} with 0 <= lo < hi <= 2 (e.g. from
+ *             the learned predictor): the dichotomy starts from it when
+ *             round(count(lo)) <= k <= round(count(hi)), else from [0, 2].
+ *   out       host.  Synchronizes `stream`. */
+CSC_API csc_status csc_estimate_lambda_k(csc_graph g, int32_t k, int32_t m, int32_t n_probes,
+                                 uint64_t seed, const double* bracket, csc_lambda_info* out,
+                                 void* stream);
+
+/* ------------------------------------------------- sampling and k-means */
+
+/* csc_sample -- Sec. 3.2 / Eq. 4: n of N nodes uniformly without replacement.
+ * Node i gets the 64-bit key SplitMix64_seed(i) (output i of SplitMix64 seeded
+ * with `seed`); the n nodes with the smallest (key, i) are returned sorted
+ * ascending.  Bit-exact and deterministic.
+ *   idx_out  device int64[n].  0 <= n <= N.  Asynchronous.
+ * Errors: CSC_E_INVALID. */
+CSC_API csc_status csc_sample(int64_t N, int64_t n, uint64_t seed, int64_t* idx_out, void* stream);
+
+/* csc_gather_rows -- out[i, :] = X[idx[i], :] for i < n (Alg. 2 step 5).
+ *   X    device float[N * ld];  idx  device int64[n] (values in [0, N));
+ *   out  device float[n * ld_out], columns 0..d-1 written.  Asynchronous. */
+CSC_API csc_status csc_gather_rows(const float* X, int64_t N, int32_t ld, const int64_t* idx, int64_t n,
+                           int32_t d, float* out, int32_t ld_out, void* stream);
+
+/* csc_kmeans_reduced -- Alg. 2 step 6: k-means on n points of dimension d.
+ * k-means++ seeding from Philox draws (key = (seed, stream "k-means"),
+ * counter = (replicate, draw)), Lloyd iterations (ties to the lowest centre,
+ * an empty cluster takes the point farthest from its centre), at most
+ * max_iter updates, best of `replicates` runs by inertia (ties to the first).
+ *   X           device float[n * ld], ld >= d.
+ *   labels_out  device int32[n].   inertia_out  host double (may be NULL).
+ * Errors: CSC_E_INVALID (k < 1, n < k, d < 1, replicates < 1), CSC_E_UNSUPPORTED
+ * (k > 1024 or d > 256).  Synchronizes `stream` when inertia_out != NULL. */
+CSC_API csc_status csc_kmeans_reduced(const float* X, int64_t n, int32_t d, int32_t ld, int32_t k,
+                              int32_t replicates, int32_t max_iter, uint64_t seed,
+                              int32_t* labels_out, double* inertia_out, void* stream);
+
+/* ------------------------------------------------------- interpolation */
+
+/* csc_interpolate -- Alg. 2 step 7: for every cluster j solve Eq. 5,
+ * (M^T M + gamma L^g_power) x_j = M^T c_j^r, by Jacobi-preconditioned
+ * conjugate gradients (fp32 vectors, fp64 inner products), then label node i
+ * with argmax_j x_j(i) / ||x_j|| (Sec. 4.1; ties to the lowest j).
+ *   sample_idx     device int64[n]: sampled node ids (distinct).
+ *   sample_labels  device int32[n]: their clusters in [0, k).
+ *   g_power        >= 1.   gamma > 0.   rel_tol > 0.   max_iter >= 1.
+ *   labels_out     device int32[N].
+ *   fuzzy_out      NULL or device float[N * k]: the x_j (column j), Sec. 4.1's
+ *                  fuzzy memberships.
+ *   info           host (may be NULL).
+ * Returns CSC_E_NOT_CONVERGED when max_iter was reached first (outputs are
+ * still written).  Synchronizes `stream` (convergence checks). */
+CSC_API csc_status csc_interpolate(csc_graph g, const int64_t* sample_idx, const int32_t* sample_labels,
+                           int64_t n, int32_t k, int32_t g_power, double gamma, double rel_tol,
+                           int32_t max_iter, int32_t* labels_out, float* fuzzy_out,
+                           csc_cg_info* info, void* stream);
+
+/* --------------------------------------------------------- whole pipeline */
+
+/* csc_cluster -- Alg. 2 end to end on one graph with the parameters above.
+ *   labels_out  device int32[N] in original node order.
+ *   info        host (may be NULL).  Synchronizes `stream`.
+ * For a batched handle use csc_cluster_batched. */
+CSC_API csc_status csc_cluster(csc_graph g, const csc_params* params, int32_t* labels_out,
+                       csc_cluster_info* info, void* stream);
+
+/* --------------------------------------------------------------- errors */
+CSC_API const char* csc_status_str(csc_status s);
+CSC_API const char* csc_last_error(void);
+/* Library version string. */
+CSC_API const char* csc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSC_H */

@@ -1,0 +1,35 @@
+"""Compressive Spectral Clustering on GB300 (sm_103a).
+
+The computation lives in the CUDA library libcsc (``csrc/``, ABI in
+``include/csc.h``); this package only marshals arguments to it.  Build the
+library with ``paper_1602_02018_gb300.build.build()``.
+"""
+from .api import (  # noqa: F401
+    BF16,
+    CHECK_SYM,
+    DEVICE_INPUT,
+    F32,
+    F64,
+    NO_JACKSON,
+    NORMALIZE_ROWS,
+    RCM,
+    CgInfo,
+    ClusterInfo,
+    Graph,
+    LambdaInfo,
+    csc_chebyshev_coefficients,
+    csc_cluster,
+    csc_eigencount,
+    csc_estimate_lambda_k,
+    csc_filter_random_signals,
+    csc_gather_rows,
+    csc_graph_create,
+    csc_graph_create_batched,
+    csc_graph_degrees,
+    csc_interpolate,
+    csc_kmeans_reduced,
+    csc_kpm_moments,
+    csc_sample,
+    default_sizes,
+)
+from ._native import CscError, header_symbols, lib  # noqa: F401

@@ -1,0 +1,268 @@
+"""Python binding of libcsc with the C ABI's names (argument marshalling only).
+
+Device arrays are torch CUDA tensors, host arrays numpy arrays; every step
+of the computation runs in the CUDA library.  Streams default to torch's
+current stream on the current device.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _native as nat
+from ._native import check, lib
+
+F32, BF16, F64 = nat.CSC_F32, nat.CSC_BF16, nat.CSC_F64
+RCM, CHECK_SYM, DEVICE_INPUT = nat.CSC_RCM, nat.CSC_CHECK_SYM, nat.CSC_DEVICE_INPUT
+NORMALIZE_ROWS, NO_JACKSON = nat.CSC_NORMALIZE_ROWS, nat.CSC_NO_JACKSON
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Graph:
+    """Owner of a csc_graph handle (freed on close / garbage collection)."""
+
+    def __init__(self, handle: ctypes.c_void_p, keep=None):
+        self.handle = handle
+        self._keep = keep
+        n, nnz, ng = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        check(lib().csc_graph_info(handle, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(ng)), "csc_graph_info")
+        self.N, self.nnz, self.n_graphs = n.value, nnz.value, ng.value
+
+    def close(self):
+        if self.handle:
+            lib().csc_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def csc_graph_create(row_ptr, col_idx, flags: int = 0, stream=None) -> Graph:
+    """Create a graph from CSR arrays: numpy (host) or CUDA tensors (adds CSC_DEVICE_INPUT)."""
+    out = ctypes.c_void_p()
+    if isinstance(row_ptr, torch.Tensor):
+        rp = row_ptr.to(torch.int64).contiguous()
+        ci = col_idx.to(torch.int32).contiguous()
+        n = rp.numel() - 1
+        check(lib().csc_graph_create(n, ci.numel(), _dptr(rp), _dptr(ci), None, flags | DEVICE_INPUT,
+                                     _stream(stream), ctypes.byref(out)), "csc_graph_create")
+    else:
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        n = rp.size - 1
+        check(lib().csc_graph_create(n, ci.size, _hptr(rp), _hptr(ci), None, flags, _stream(stream),
+                                     ctypes.byref(out)), "csc_graph_create")
+    return Graph(out)
+
+
+def csc_graph_create_batched(graphs, flags: int = 0, stream=None) -> Graph:
+    """Pack a list of (row_ptr, col_idx) host CSR graphs block-diagonally into one handle."""
+    rps = [np.ascontiguousarray(r, dtype=np.int64) for r, _ in graphs]
+    cis = [np.ascontiguousarray(c, dtype=np.int32) for _, c in graphs]
+    G = len(rps)
+    ns = np.array([r.size - 1 for r in rps], dtype=np.int64)
+    rp_ptrs = (ctypes.c_void_p * G)(*[r.ctypes.data for r in rps])
+    ci_ptrs = (ctypes.c_void_p * G)(*[c.ctypes.data if c.size else 0 for c in cis])
+    out = ctypes.c_void_p()
+    check(lib().csc_graph_create_batched(G, _hptr(ns), rp_ptrs, ci_ptrs, flags, _stream(stream), ctypes.byref(out)),
+          "csc_graph_create_batched")
+    return Graph(out, keep=(rps, cis))
+
+
+def csc_graph_degrees(g: Graph, stream=None) -> np.ndarray:
+    out = np.empty(g.N, dtype=np.int32)
+    check(lib().csc_graph_degrees(g.handle, _hptr(out), _stream(stream)), "csc_graph_degrees")
+    return out
+
+
+def csc_chebyshev_coefficients(lambda_c: float, m: int, flags: int = 0) -> np.ndarray:
+    out = np.empty(m + 1, dtype=np.float64)
+    check(lib().csc_chebyshev_coefficients(lambda_c, m, flags, _hptr(out)), "csc_chebyshev_coefficients")
+    return out
+
+
+def csc_filter_random_signals(g: Graph, lambda_c: float, m: int, d: int, d_pad: Optional[int] = None,
+                              seed: int = 0, storage: int = F32, R_in: Optional[torch.Tensor] = None,
+                              Y_out: Optional[torch.Tensor] = None, flags: int = NORMALIZE_ROWS,
+                              stream=None) -> torch.Tensor:
+    d_pad = ((d + 7) // 8) * 8 if d_pad is None else d_pad
+    ydt = torch.float64 if storage == F64 else torch.float32
+    if Y_out is None:
+        Y_out = torch.empty((g.N, d_pad), dtype=ydt, device="cuda")
+    if R_in is not None and (R_in.dtype != torch.float32 or tuple(R_in.shape) != (g.N, d_pad)):
+        raise ValueError("R_in must be float32 of shape (N, d_pad)")
+    check(lib().csc_filter_random_signals(g.handle, lambda_c, m, d, d_pad, seed, storage, _dptr(R_in), _dptr(Y_out),
+                                          flags, _stream(stream)), "csc_filter_random_signals")
+    return Y_out
+
+
+def csc_kpm_moments(g: Graph, n_moments: int, n_probes: int, seed: int = 0, storage: int = F32,
+                    stream=None) -> np.ndarray:
+    out = np.empty(n_moments, dtype=np.float64)
+    check(lib().csc_kpm_moments(g.handle, n_moments, n_probes, seed, storage, _hptr(out), _stream(stream)),
+          "csc_kpm_moments")
+    return out
+
+
+def csc_eigencount(mu: np.ndarray, lam: float, flags: int = 0) -> float:
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    out = ctypes.c_double()
+    check(lib().csc_eigencount(_hptr(mu), mu.size - 1, lam, flags, ctypes.byref(out)), "csc_eigencount")
+    return out.value
+
+
+@dataclass
+class LambdaInfo:
+    lam: float
+    count: float
+    iters: int
+    hit: bool
+    n_probes: int
+    m: int
+    bracket_used: bool
+    moment_passes: int
+
+
+def _lambda_info(x: nat.csc_lambda_info) -> LambdaInfo:
+    return LambdaInfo(x.lambda_, x.count, x.iters, bool(x.hit), x.n_probes, x.m, bool(x.bracket_used),
+                      x.moment_passes)
+
+
+def csc_estimate_lambda_k(g: Graph, k: int, m: int = 50, n_probes: int = 0, seed: int = 0, bracket=None,
+                          stream=None) -> LambdaInfo:
+    info = nat.csc_lambda_info()
+    br = None
+    if bracket is not None:
+        br_arr = np.ascontiguousarray(bracket, dtype=np.float64)
+        br = _hptr(br_arr)
+    check(lib().csc_estimate_lambda_k(g.handle, k, m, n_probes, seed, br, ctypes.byref(info), _stream(stream)),
+          "csc_estimate_lambda_k")
+    return _lambda_info(info)
+
+
+def csc_sample(N: int, n: int, seed: int = 0, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device="cuda")
+    check(lib().csc_sample(N, n, seed, _dptr(out) if n else None, _stream(stream)), "csc_sample")
+    return out
+
+
+def csc_gather_rows(X: torch.Tensor, idx: torch.Tensor, d: Optional[int] = None,
+                    out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    N, ld = X.shape
+    d = ld if d is None else d
+    n = idx.numel()
+    if out is None:
+        out = torch.zeros((n, ld), dtype=torch.float32, device="cuda")
+    check(lib().csc_gather_rows(_dptr(X), N, ld, _dptr(idx), n, d, _dptr(out), out.shape[1], _stream(stream)),
+          "csc_gather_rows")
+    return out
+
+
+def csc_kmeans_reduced(X: torch.Tensor, d: int, k: int, replicates: int = 20, max_iter: int = 100, seed: int = 0,
+                       labels_out: Optional[torch.Tensor] = None, stream=None):
+    n, ld = X.shape
+    if labels_out is None:
+        labels_out = torch.empty(n, dtype=torch.int32, device="cuda")
+    inertia = ctypes.c_double()
+    check(lib().csc_kmeans_reduced(_dptr(X), n, d, ld, k, replicates, max_iter, seed, _dptr(labels_out),
+                                   ctypes.byref(inertia), _stream(stream)), "csc_kmeans_reduced")
+    return labels_out, inertia.value
+
+
+@dataclass
+class CgInfo:
+    iters: int
+    converged: bool
+    max_rel_residual: float
+
+
+def csc_interpolate(g: Graph, sample_idx: torch.Tensor, sample_labels: torch.Tensor, k: int, g_power: int = 4,
+                    gamma: float = 1e-3, rel_tol: float = 1e-6, max_iter: int = 2000,
+                    labels_out: Optional[torch.Tensor] = None, fuzzy: bool = False, stream=None):
+    """Returns (labels int32[N], fuzzy float[N, k] or None, CgInfo); raises unless converged or NOT_CONVERGED."""
+    if labels_out is None:
+        labels_out = torch.empty(g.N, dtype=torch.int32, device="cuda")
+    fz = torch.empty((g.N, k), dtype=torch.float32, device="cuda") if fuzzy else None
+    info = nat.csc_cg_info()
+    st = lib().csc_interpolate(g.handle, _dptr(sample_idx), _dptr(sample_labels), sample_idx.numel(), k, g_power,
+                               gamma, rel_tol, max_iter, _dptr(labels_out), _dptr(fz), ctypes.byref(info),
+                               _stream(stream))
+    check(st, "csc_interpolate", allow=(nat.CSC_E_NOT_CONVERGED,))
+    return labels_out, fz, CgInfo(info.iters, bool(info.converged), info.max_rel_residual)
+
+
+@dataclass
+class ClusterInfo:
+    lam: LambdaInfo
+    cg: CgInfo
+    inertia: float
+    ms: dict
+
+
+def csc_cluster(g: Graph, k: int, m: int = 0, d: int = 0, d_pad: int = 0, n: int = 0, n_probes: int = 0,
+                g_power: int = 0, gamma: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0,
+                replicates: int = 0, km_max_iter: int = 0, storage: int = F32, seed: int = 0,
+                lambda_k: float = 0.0, bracket=None, labels_out: Optional[torch.Tensor] = None, stream=None):
+    """Alg. 2 end to end; zero arguments take the library defaults.  Returns (labels, ClusterInfo)."""
+    p = nat.csc_params()
+    p.k, p.m, p.d, p.d_pad, p.n, p.n_probes, p.g_power = k, m, d, d_pad, n, n_probes, g_power
+    p.gamma, p.cg_tol, p.cg_max_iter, p.replicates, p.km_max_iter = gamma, cg_tol, cg_max_iter, replicates, km_max_iter
+    p.storage, p.seed, p.lambda_k = storage, seed, lambda_k
+    br_arr = None
+    if bracket is not None:
+        br_arr = np.ascontiguousarray(bracket, dtype=np.float64)
+        p.bracket = br_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    if labels_out is None:
+        labels_out = torch.empty(g.N, dtype=torch.int32, device="cuda")
+    info = nat.csc_cluster_info()
+    check(lib().csc_cluster(g.handle, ctypes.byref(p), _dptr(labels_out), ctypes.byref(info), _stream(stream)),
+          "csc_cluster")
+    ms = dict(lambda_k=info.ms_lambda, filter=info.ms_filter, sample=info.ms_sample, kmeans=info.ms_kmeans,
+              interp=info.ms_interp, total=info.ms_total)
+    return labels_out, ClusterInfo(_lambda_info(info.lambda_),
+                                   CgInfo(info.cg.iters, bool(info.cg.converged), info.cg.max_rel_residual),
+                                   info.inertia, ms)
+
+
+def default_sizes(N: int, k: int) -> dict:
+    """The library's parameter defaults (d = ceil(4 ln N), n = ceil(2 k ln k), n_v = ceil(2 ln N))."""
+    d = max(1, math.ceil(4 * math.log(N))) if N > 1 else 1
+    n = min(N, max(k, math.ceil(2 * k * math.log(k)))) if k > 1 else 1
+    nv = max(1, math.ceil(2 * math.log(N))) if N > 1 else 1
+    return dict(d=d, d_pad=((d + 7) // 8) * 8, n=n, n_probes=nv)

@@ -1,0 +1,765 @@
+// api.cu -- the C ABI of libcsc (include/csc.h): graph handles, host-side
+// mathematics (Jackson-Chebyshev coefficients, the eigencount dichotomy,
+// reverse Cuthill-McKee) and the Alg. 2 pipeline driver.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+// The opaque handle of the C ABI is the internal graph record.
+struct csc_graph_s : public csc::Graph {};
+
+namespace csc {
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+void clear_error() { g_last_error.clear(); }
+
+csc_status ws_get(Graph* g, WsSlot slot, size_t bytes, void** out) {
+    Buffer& b = g->ws[slot];
+    if (bytes == 0) bytes = 16;
+    if (b.bytes < bytes) {
+        if (b.ptr) {
+            CSC_CUDA_TRY(cudaFree(b.ptr));
+            b.ptr = nullptr;
+            b.bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&b.ptr, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b.ptr = nullptr;
+            set_error("cudaMalloc(%zu) for scratch slot %d: %s", bytes, (int)slot, cudaGetErrorString(e));
+            return CSC_E_OOM;
+        }
+        b.bytes = bytes;
+    }
+    *out = b.ptr;
+    return CSC_OK;
+}
+
+// ------------------------------------------------- Jackson-Chebyshev (Sec. 4.3)
+// c_j = g_j gamma_j for the ideal low-pass of Eq. 1 on t = lambda - 1 in [-1, 1]:
+//   gamma_0 = 1 - theta/pi, gamma_j = -2 sin(j theta)/(j pi), theta = arccos(lambda_c - 1),
+//   g_j = [(1 - j/(m+2)) sin(a) cos(j a) + cos(a) sin(j a)/(m+2)] / sin(a), a = pi/(m+2).
+void cheb_coefficients(double lambda_c, int m, bool jackson, double* c) {
+    double t = lambda_c - 1.0;
+    t = t < -1.0 ? -1.0 : (t > 1.0 ? 1.0 : t);
+    const double theta = acos(t);
+    const double a = M_PI / (double)(m + 2);
+    const double sa = sin(a), ca = cos(a);
+    for (int j = 0; j <= m; ++j) {
+        const double gam = j == 0 ? 1.0 - theta / M_PI : -2.0 * sin(j * theta) / (j * M_PI);
+        double damp = 1.0;
+        if (jackson)
+            damp = ((1.0 - (double)j / (m + 2)) * sa * cos(j * a) + ca * sin(j * a) / (m + 2)) / sa;
+        c[j] = gam * damp;
+    }
+}
+
+static double eigencount_host(const double* mu, int m, double lambda, bool jackson, std::vector<double>& c) {
+    c.resize(m + 1);
+    cheb_coefficients(lambda, m, jackson, c.data());
+    double s = 0.0;
+    for (int j = 0; j <= m; ++j) s += c[j] * mu[j];
+    return s;
+}
+
+static long long round_half_away(double x) { return x >= 0 ? (long long)floor(x + 0.5) : -(long long)floor(-x + 0.5); }
+
+// Sec. 4.3 dichotomy on [lo, hi]: stop when round(count) == k.
+static void dichotomy(const double* mu, int m, int k, double lo, double hi, csc_lambda_info* out) {
+    std::vector<double> c;
+    for (int it = 1; it <= 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        const double cnt = eigencount_host(mu, m, mid, true, c);
+        if (round_half_away(cnt) == k) {
+            out->lambda = mid;
+            out->count = cnt;
+            out->iters = it;
+            out->hit = 1;
+            return;
+        }
+        if (cnt > (double)k) hi = mid;
+        else lo = mid;
+        if (hi - lo < 1e-12) {
+            out->lambda = hi;
+            out->count = eigencount_host(mu, m, hi, true, c);
+            out->iters = it;
+            out->hit = 0;
+            return;
+        }
+    }
+    out->lambda = hi;
+    out->count = eigencount_host(mu, m, hi, true, c);
+    out->iters = 60;
+    out->hit = 0;
+}
+
+// --------------------------------------------------------- reverse Cuthill-McKee
+// Cuthill & McKee (1969), reversed (George 1971): BFS from a minimum-degree
+// node of each component, visiting neighbours by increasing degree; the
+// visit order reversed gives perm[new] = old.
+static void rcm_order(int64_t N, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
+                      std::vector<int32_t>& perm) {
+    std::vector<int32_t> deg(N);
+    for (int64_t i = 0; i < N; ++i) deg[i] = (int32_t)(rp[i + 1] - rp[i]);
+    std::vector<int32_t> order(N);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return deg[a] < deg[b]; });
+    std::vector<char> seen(N, 0);
+    std::vector<int32_t> visit;
+    visit.reserve(N);
+    std::vector<int32_t> nb;
+    for (int64_t s = 0; s < N; ++s) {
+        const int32_t start = order[s];
+        if (seen[start]) continue;
+        size_t head = visit.size();
+        visit.push_back(start);
+        seen[start] = 1;
+        while (head < visit.size()) {
+            const int32_t u = visit[head++];
+            nb.clear();
+            for (int64_t e = rp[u]; e < rp[u + 1]; ++e)
+                if (!seen[ci[e]]) {
+                    seen[ci[e]] = 1;
+                    nb.push_back(ci[e]);
+                }
+            std::stable_sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) { return deg[a] < deg[b]; });
+            visit.insert(visit.end(), nb.begin(), nb.end());
+        }
+    }
+    perm.assign(visit.rbegin(), visit.rend());
+}
+
+// ------------------------------------------------------------- graph create
+struct HostCSR {
+    int64_t N = 0;
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+};
+
+// Validate a CSR (sorted rows, in range, optional symmetry) and drop self loops.
+static csc_status validate_and_clean(int64_t N, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                                     bool check_sym, HostCSR& out, int64_t node_base = 0) {
+    if (row_ptr[0] != 0) {
+        set_error("row_ptr[0] = %lld, expected 0", (long long)row_ptr[0]);
+        return CSC_E_CSR;
+    }
+    if (row_ptr[N] != nnz) {
+        set_error("row_ptr[N] = %lld differs from nnz = %lld", (long long)row_ptr[N], (long long)nnz);
+        return CSC_E_CSR;
+    }
+    out.N = N;
+    out.rp.assign(N + 1, 0);
+    out.ci.clear();
+    out.ci.reserve(nnz);
+    for (int64_t i = 0; i < N; ++i) {
+        const int64_t b = row_ptr[i], e = row_ptr[i + 1];
+        if (e < b || b < 0 || e > nnz) {
+            set_error("row_ptr not nondecreasing at row %lld", (long long)(i + node_base));
+            return CSC_E_CSR;
+        }
+        int64_t prev = -1;
+        for (int64_t p = b; p < e; ++p) {
+            const int64_t c = col_idx[p];
+            if (c < 0 || c >= N) {
+                set_error("col_idx[%lld] = %lld out of range [0, %lld)", (long long)p, (long long)c, (long long)N);
+                return CSC_E_CSR;
+            }
+            if (c <= prev) {
+                set_error("row %lld not strictly increasing (duplicate or unsorted column %lld)",
+                          (long long)(i + node_base), (long long)c);
+                return CSC_E_CSR;
+            }
+            prev = c;
+            if (c != i) out.ci.push_back((int32_t)c);
+        }
+        out.rp[i + 1] = (int64_t)out.ci.size();
+    }
+    if (check_sym) {
+        for (int64_t i = 0; i < N; ++i) {
+            for (int64_t p = out.rp[i]; p < out.rp[i + 1]; ++p) {
+                const int32_t j = out.ci[p];
+                const int32_t* b = out.ci.data() + out.rp[j];
+                const int32_t* e = out.ci.data() + out.rp[j + 1];
+                if (!std::binary_search(b, e, (int32_t)i)) {
+                    set_error("matrix not symmetric: (%lld, %d) present, (%d, %lld) missing",
+                              (long long)(i + node_base), j, j, (long long)(i + node_base));
+                    return CSC_E_CSR;
+                }
+            }
+        }
+    }
+    return CSC_OK;
+}
+
+static void permute_csr(const HostCSR& in, const std::vector<int32_t>& perm, HostCSR& out) {
+    const int64_t N = in.N;
+    std::vector<int32_t> iperm(N);
+    for (int64_t p = 0; p < N; ++p) iperm[perm[p]] = (int32_t)p;
+    out.N = N;
+    out.rp.assign(N + 1, 0);
+    out.ci.resize(in.ci.size());
+    for (int64_t p = 0; p < N; ++p) {
+        const int32_t o = perm[p];
+        out.rp[p + 1] = out.rp[p] + (in.rp[o + 1] - in.rp[o]);
+    }
+    for (int64_t p = 0; p < N; ++p) {
+        const int32_t o = perm[p];
+        int64_t w = out.rp[p];
+        for (int64_t e = in.rp[o]; e < in.rp[o + 1]; ++e) out.ci[w++] = iperm[in.ci[e]];
+        std::sort(out.ci.begin() + out.rp[p], out.ci.begin() + out.rp[p + 1]);
+    }
+}
+
+static void free_graph(Graph* g) {
+    if (!g) return;
+    cudaFree(g->row_ptr);
+    cudaFree(g->col_idx);
+    cudaFree(g->dinv);
+    cudaFree(g->dinv64);
+    cudaFree(g->deg);
+    cudaFree(g->perm);
+    cudaFree(g->iperm);
+    cudaFree(g->d_offsets);
+    cudaFree(g->graph_of_row);
+    for (auto& b : g->ws) cudaFree(b.ptr);
+    for (auto& e : g->ev)
+        if (e) cudaEventDestroy(e);
+    if (g->pinned) cudaFreeHost(g->pinned);
+    delete g;
+}
+
+template <typename T>
+static csc_status dev_alloc(T** p, size_t count) {
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        set_error("cudaMalloc(%zu): %s", count * sizeof(T), cudaGetErrorString(e));
+        return CSC_E_OOM;
+    }
+    return CSC_OK;
+}
+
+// Upload a cleaned CSR (already in internal order) and compute degrees.
+static csc_status upload(Graph* g, const HostCSR& h, const std::vector<int32_t>* perm, cudaStream_t s) {
+    const int64_t N = h.N;
+    const int64_t nnz = (int64_t)h.ci.size();
+    if (nnz >= (int64_t)INT32_MAX) {
+        set_error("nnz = %lld exceeds the int32 row-pointer range of this build", (long long)nnz);
+        return CSC_E_UNSUPPORTED;
+    }
+    g->N = N;
+    g->nnz = nnz;
+    CSC_CUDA_TRY(cudaGetDevice(&g->device));
+    CSC_CUDA_TRY(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
+    std::vector<int32_t> rp32(N + 1);
+    for (int64_t i = 0; i <= N; ++i) rp32[i] = (int32_t)h.rp[i];
+    CSC_TRY(dev_alloc(&g->row_ptr, N + 1));
+    CSC_TRY(dev_alloc(&g->col_idx, nnz));
+    CSC_TRY(dev_alloc(&g->dinv, N));
+    CSC_TRY(dev_alloc(&g->dinv64, N));
+    CSC_TRY(dev_alloc(&g->deg, N));
+    CSC_CUDA_TRY(cudaMemcpyAsync(g->row_ptr, rp32.data(), (N + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    if (nnz)
+        CSC_CUDA_TRY(cudaMemcpyAsync(g->col_idx, h.ci.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    if (perm) {
+        std::vector<int32_t> iperm(N);
+        for (int64_t p = 0; p < N; ++p) iperm[(*perm)[p]] = (int32_t)p;
+        CSC_TRY(dev_alloc(&g->perm, N));
+        CSC_TRY(dev_alloc(&g->iperm, N));
+        CSC_CUDA_TRY(cudaMemcpyAsync(g->perm, perm->data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        CSC_CUDA_TRY(cudaMemcpyAsync(g->iperm, iperm.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    }
+    CSC_CUDA_TRY(cudaMallocHost((void**)&g->pinned, 4096 * sizeof(double)));
+    for (auto& e : g->ev) CSC_CUDA_TRY(cudaEventCreate(&e));
+    CSC_TRY(launch_degrees(g, s));
+    CSC_CUDA_TRY(cudaStreamSynchronize(s));
+    return CSC_OK;
+}
+
+static csc_status check_graph(csc_graph g) {
+    if (!g) {
+        set_error("null graph handle");
+        return CSC_E_INVALID;
+    }
+    if (g->poisoned) {
+        set_error("graph handle unusable after an earlier CUDA error");
+        return CSC_E_CUDA;
+    }
+    return CSC_OK;
+}
+
+static csc_status poison_on_cuda(Graph* g, csc_status st) {
+    if (st == CSC_E_CUDA && g) g->poisoned = true;
+    return st;
+}
+
+}  // namespace csc
+
+using namespace csc;
+
+extern "C" {
+
+const char* csc_version(void) { return "csc-gb300 0.1 (sm_103a)"; }
+
+const char* csc_status_str(csc_status s) {
+    switch (s) {
+        case CSC_OK: return "CSC_OK";
+        case CSC_E_INVALID: return "CSC_E_INVALID";
+        case CSC_E_CSR: return "CSC_E_CSR";
+        case CSC_E_OOM: return "CSC_E_OOM";
+        case CSC_E_CUDA: return "CSC_E_CUDA";
+        case CSC_E_NOT_CONVERGED: return "CSC_E_NOT_CONVERGED";
+        case CSC_E_DEVICE_TIMEOUT: return "CSC_E_DEVICE_TIMEOUT";
+        case CSC_E_NUMERIC: return "CSC_E_NUMERIC";
+        case CSC_E_UNSUPPORTED: return "CSC_E_UNSUPPORTED";
+        default: return "CSC_E_UNKNOWN";
+    }
+}
+
+const char* csc_last_error(void) { return g_last_error.c_str(); }
+
+csc_status csc_graph_create(int64_t N, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                            const float* weights, uint32_t flags, void* stream, csc_graph* out) {
+    clear_error();
+    if (!out || !row_ptr || (nnz > 0 && !col_idx) || N < 1 || nnz < 0) {
+        set_error("csc_graph_create: invalid arguments (N=%lld, nnz=%lld)", (long long)N, (long long)nnz);
+        return CSC_E_INVALID;
+    }
+    *out = nullptr;
+    if (weights) {
+        set_error("weighted graphs are not supported: pass weights = NULL");
+        return CSC_E_UNSUPPORTED;
+    }
+    if (N >= (int64_t)INT32_MAX || nnz >= (int64_t)INT32_MAX) {
+        set_error("N and nnz must be below 2^31");
+        return CSC_E_UNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int64_t> hrp;
+    std::vector<int32_t> hci;
+    const int64_t* rp = row_ptr;
+    const int32_t* ci = col_idx;
+    if (flags & CSC_DEVICE_INPUT) {
+        hrp.resize(N + 1);
+        hci.resize(nnz);
+        CSC_CUDA_TRY(cudaMemcpyAsync(hrp.data(), row_ptr, (N + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        if (nnz) CSC_CUDA_TRY(cudaMemcpyAsync(hci.data(), col_idx, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        CSC_CUDA_TRY(cudaStreamSynchronize(s));
+        rp = hrp.data();
+        ci = hci.data();
+    }
+    HostCSR clean;
+    try {
+        CSC_TRY(validate_and_clean(N, nnz, rp, ci, (flags & CSC_CHECK_SYM) != 0, clean));
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed while validating the CSR");
+        return CSC_E_OOM;
+    }
+    csc_graph g = new (std::nothrow) csc_graph_s();
+    if (!g) {
+        set_error("host allocation failed");
+        return CSC_E_OOM;
+    }
+    csc_status st;
+    if (flags & CSC_RCM) {
+        std::vector<int32_t> perm;
+        rcm_order(N, clean.rp, clean.ci, perm);
+        HostCSR pc;
+        permute_csr(clean, perm, pc);
+        st = upload(g, pc, &perm, s);
+    } else {
+        st = upload(g, clean, nullptr, s);
+    }
+    if (st != CSC_OK) {
+        free_graph(g);
+        return st;
+    }
+    g->offsets = {0, N};
+    *out = g;
+    return CSC_OK;
+}
+
+csc_status csc_graph_create_batched(int32_t G, const int64_t* Ns, const int64_t* const* row_ptr,
+                                    const int32_t* const* col_idx, uint32_t flags, void* stream, csc_graph* out) {
+    clear_error();
+    if (!out || G < 1 || !Ns || !row_ptr || !col_idx) {
+        set_error("csc_graph_create_batched: invalid arguments");
+        return CSC_E_INVALID;
+    }
+    *out = nullptr;
+    if (flags & (CSC_DEVICE_INPUT | CSC_RCM)) {
+        set_error("csc_graph_create_batched: host input only, without CSC_RCM");
+        return CSC_E_UNSUPPORTED;
+    }
+    HostCSR packed;
+    std::vector<int64_t> offsets(G + 1, 0);
+    for (int i = 0; i < G; ++i) {
+        if (Ns[i] < 1 || !row_ptr[i]) {
+            set_error("csc_graph_create_batched: graph %d has N < 1 or a null row_ptr", i);
+            return CSC_E_INVALID;
+        }
+        offsets[i + 1] = offsets[i] + Ns[i];
+    }
+    const int64_t NT = offsets[G];
+    if (NT >= (int64_t)INT32_MAX) {
+        set_error("packed node count must be below 2^31");
+        return CSC_E_UNSUPPORTED;
+    }
+    packed.N = NT;
+    packed.rp.assign(NT + 1, 0);
+    try {
+        for (int i = 0; i < G; ++i) {
+            HostCSR one;
+            const int64_t nnz_i = row_ptr[i][Ns[i]];
+            if (nnz_i > 0 && !col_idx[i]) {
+                set_error("graph %d: col_idx is NULL", i);
+                return CSC_E_INVALID;
+            }
+            CSC_TRY(validate_and_clean(Ns[i], nnz_i, row_ptr[i], col_idx[i], (flags & CSC_CHECK_SYM) != 0, one,
+                                       offsets[i]));
+            const int64_t base = (int64_t)packed.ci.size();
+            for (int64_t r = 0; r < Ns[i]; ++r) packed.rp[offsets[i] + r + 1] = base + one.rp[r + 1];
+            for (int32_t c : one.ci) packed.ci.push_back((int32_t)(c + offsets[i]));
+        }
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed while packing graphs");
+        return CSC_E_OOM;
+    }
+    csc_graph g = new (std::nothrow) csc_graph_s();
+    if (!g) {
+        set_error("host allocation failed");
+        return CSC_E_OOM;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    csc_status st = upload(g, packed, nullptr, s);
+    if (st == CSC_OK) {
+        g->n_graphs = G;
+        g->offsets = offsets;
+        std::vector<int32_t> gid(NT);
+        for (int i = 0; i < G; ++i)
+            for (int64_t r = offsets[i]; r < offsets[i + 1]; ++r) gid[r] = i;
+        st = dev_alloc(&g->d_offsets, G + 1);
+        if (st == CSC_OK) st = dev_alloc(&g->graph_of_row, NT);
+        if (st == CSC_OK && (cudaMemcpy(g->d_offsets, offsets.data(), (G + 1) * sizeof(int64_t),
+                                        cudaMemcpyHostToDevice) != cudaSuccess ||
+                             cudaMemcpy(g->graph_of_row, gid.data(), NT * sizeof(int32_t),
+                                        cudaMemcpyHostToDevice) != cudaSuccess)) {
+            set_error("copying batch tables failed");
+            st = CSC_E_CUDA;
+        }
+    }
+    if (st != CSC_OK) {
+        free_graph(g);
+        return st;
+    }
+    *out = g;
+    return CSC_OK;
+}
+
+csc_status csc_graph_destroy(csc_graph g) {
+    if (!g) return CSC_OK;
+    free_graph(g);
+    return CSC_OK;
+}
+
+csc_status csc_graph_info(csc_graph g, int64_t* N, int64_t* nnz, int32_t* n_graphs) {
+    CSC_TRY(check_graph(g));
+    if (N) *N = g->N;
+    if (nnz) *nnz = g->nnz;
+    if (n_graphs) *n_graphs = g->n_graphs;
+    return CSC_OK;
+}
+
+csc_status csc_graph_degrees(csc_graph g, int32_t* deg_out, void* stream) {
+    clear_error();
+    CSC_TRY(check_graph(g));
+    if (!deg_out) {
+        set_error("deg_out is NULL");
+        return CSC_E_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int32_t> d(g->N);
+    cudaError_t e = cudaMemcpyAsync(d.data(), g->deg, g->N * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_error("copying degrees: %s", cudaGetErrorString(e));
+        return poison_on_cuda(g, CSC_E_CUDA);
+    }
+    if (g->perm) {
+        std::vector<int32_t> perm(g->N);
+        e = cudaMemcpy(perm.data(), g->perm, g->N * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            set_error("copying permutation: %s", cudaGetErrorString(e));
+            return poison_on_cuda(g, CSC_E_CUDA);
+        }
+        for (int64_t p = 0; p < g->N; ++p) deg_out[perm[p]] = d[p];
+    } else {
+        memcpy(deg_out, d.data(), g->N * sizeof(int32_t));
+    }
+    return CSC_OK;
+}
+
+csc_status csc_chebyshev_coefficients(double lambda_c, int32_t m, uint32_t flags, double* c_out) {
+    clear_error();
+    if (m < 0 || !c_out || !(lambda_c >= 0.0 && lambda_c <= 2.0)) {
+        set_error("csc_chebyshev_coefficients: need m >= 0, lambda_c in [0, 2], c_out != NULL");
+        return CSC_E_INVALID;
+    }
+    cheb_coefficients(lambda_c, m, (flags & CSC_NO_JACKSON) == 0, c_out);
+    return CSC_OK;
+}
+
+csc_status csc_filter_random_signals(csc_graph g, double lambda_c, int32_t m, int32_t d, int32_t d_pad,
+                                     uint64_t seed, csc_dtype storage, const float* R_in, void* Y_out,
+                                     uint32_t flags, void* stream) {
+    clear_error();
+    CSC_TRY(check_graph(g));
+    if (m < 0 || d < 1 || d_pad < d || d_pad % 8 != 0 || !Y_out || !(lambda_c >= 0.0 && lambda_c <= 2.0) ||
+        (storage != CSC_F32 && storage != CSC_BF16 && storage != CSC_F64)) {
+        set_error("csc_filter_random_signals: invalid arguments (m=%d d=%d d_pad=%d lambda_c=%g storage=%d)", m, d,
+                  d_pad, lambda_c, (int)storage);
+        return CSC_E_INVALID;
+    }
+    std::vector<double> c(m + 1);
+    cheb_coefficients(lambda_c, m, (flags & CSC_NO_JACKSON) == 0, c.data());
+    csc_status st = run_filter(g, c.data(), m, d, d_pad, seed, storage, R_in, Y_out,
+                               (flags & CSC_NORMALIZE_ROWS) != 0, (cudaStream_t)stream);
+    return poison_on_cuda(g, st);
+}
+
+csc_status csc_kpm_moments(csc_graph g, int32_t n_moments, int32_t n_probes, uint64_t seed, csc_dtype storage,
+                           double* mu_out, void* stream) {
+    clear_error();
+    CSC_TRY(check_graph(g));
+    if (n_moments < 1 || n_probes < 1 || !mu_out || n_moments > 4096) {
+        set_error("csc_kpm_moments: need 1 <= n_moments <= 4096, n_probes >= 1, mu_out != NULL");
+        return CSC_E_INVALID;
+    }
+    return poison_on_cuda(g, run_moments(g, n_moments, n_probes, seed, storage, mu_out, nullptr,
+                                         (cudaStream_t)stream));
+}
+
+csc_status csc_eigencount(const double* mu, int32_t m, double lambda, uint32_t flags, double* count_out) {
+    clear_error();
+    if (!mu || !count_out || m < 0 || !(lambda >= 0.0 && lambda <= 2.0)) {
+        set_error("csc_eigencount: invalid arguments");
+        return CSC_E_INVALID;
+    }
+    std::vector<double> c;
+    *count_out = eigencount_host(mu, m, lambda, (flags & CSC_NO_JACKSON) == 0, c);
+    return CSC_OK;
+}
+
+csc_status csc_estimate_lambda_k(csc_graph g, int32_t k, int32_t m, int32_t n_probes, uint64_t seed,
+                                 const double* bracket, csc_lambda_info* out, void* stream) {
+    clear_error();
+    CSC_TRY(check_graph(g));
+    if (k < 1 || m < 1 || n_probes < 0 || !out ||
+        (bracket && !(bracket[0] >= 0.0 && bracket[0] < bracket[1] && bracket[1] <= 2.0))) {
+        set_error("csc_estimate_lambda_k: invalid arguments (k=%d m=%d n_probes=%d)", k, m, n_probes);
+        return CSC_E_INVALID;
+    }
+    if (n_probes == 0) n_probes = g->N > 1 ? (int)ceil(2.0 * log((double)g->N)) : 1;
+    std::vector<double> mu(m + 1);
+    int passes = 0;
+    csc_status st = run_moments(g, m + 1, n_probes, seed, CSC_F32, mu.data(), &passes, (cudaStream_t)stream);
+    if (st != CSC_OK) return poison_on_cuda(g, st);
+    memset(out, 0, sizeof(*out));
+    out->n_probes = n_probes;
+    out->m = m;
+    out->moment_passes = passes;
+    double lo = 0.0, hi = 2.0;
+    if (bracket) {
+        std::vector<double> c;
+        const double clo = eigencount_host(mu.data(), m, bracket[0], true, c);
+        const double chi = eigencount_host(mu.data(), m, bracket[1], true, c);
+        if (round_half_away(clo) <= k && k <= round_half_away(chi)) {
+            lo = bracket[0];
+            hi = bracket[1];
+            out->bracket_used = 1;
+        }
+    }
+    dichotomy(mu.data(), m, k, lo, hi, out);
+    return CSC_OK;
+}
+
+csc_status csc_sample(int64_t N, int64_t n, uint64_t seed, int64_t* idx_out, void* stream) {
+    clear_error();
+    if (N < 1 || n < 0 || n > N || (n > 0 && !idx_out) || N >= (int64_t)INT32_MAX) {
+        set_error("csc_sample: need 0 <= n <= N < 2^31 and idx_out != NULL");
+        return CSC_E_INVALID;
+    }
+    if (n == 0) return CSC_OK;
+    return run_sample(N, n, seed, idx_out, nullptr, (cudaStream_t)stream);
+}
+
+csc_status csc_gather_rows(const float* X, int64_t N, int32_t ld, const int64_t* idx, int64_t n, int32_t d,
+                           float* out, int32_t ld_out, void* stream) {
+    clear_error();
+    if (!X || !idx || !out || N < 1 || n < 0 || d < 1 || ld < d || ld_out < d) {
+        set_error("csc_gather_rows: invalid arguments");
+        return CSC_E_INVALID;
+    }
+    if (n == 0) return CSC_OK;
+    return run_gather_rows(X, N, ld, idx, n, d, out, ld_out, (cudaStream_t)stream);
+}
+
+csc_status csc_kmeans_reduced(const float* X, int64_t n, int32_t d, int32_t ld, int32_t k, int32_t replicates,
+                              int32_t max_iter, uint64_t seed, int32_t* labels_out, double* inertia_out,
+                              void* stream) {
+    clear_error();
+    if (!X || !labels_out || k < 1 || n < k || d < 1 || ld < d || replicates < 1 || max_iter < 0) {
+        set_error("csc_kmeans_reduced: invalid arguments (n=%lld d=%d k=%d replicates=%d)", (long long)n, d, k,
+                  replicates);
+        return CSC_E_INVALID;
+    }
+    if (k > 1024 || d > 256) {
+        set_error("csc_kmeans_reduced: k <= 1024 and d <= 256 in this build");
+        return CSC_E_UNSUPPORTED;
+    }
+    return run_kmeans(X, n, d, ld, k, replicates, max_iter, seed, labels_out, inertia_out, nullptr,
+                      (cudaStream_t)stream);
+}
+
+csc_status csc_interpolate(csc_graph g, const int64_t* sample_idx, const int32_t* sample_labels, int64_t n,
+                           int32_t k, int32_t g_power, double gamma, double rel_tol, int32_t max_iter,
+                           int32_t* labels_out, float* fuzzy_out, csc_cg_info* info, void* stream) {
+    clear_error();
+    CSC_TRY(check_graph(g));
+    if (!sample_idx || !sample_labels || !labels_out || n < 1 || n > g->N || k < 1 || g_power < 1 ||
+        !(gamma > 0.0) || !(rel_tol > 0.0) || max_iter < 1) {
+        set_error("csc_interpolate: invalid arguments (n=%lld k=%d g_power=%d gamma=%g rel_tol=%g)", (long long)n, k,
+                  g_power, gamma, rel_tol);
+        return CSC_E_INVALID;
+    }
+    csc_status st = run_interpolate(g, sample_idx, sample_labels, n, k, g_power, gamma, rel_tol, max_iter,
+                                    labels_out, fuzzy_out, info, (cudaStream_t)stream);
+    return poison_on_cuda(g, st);
+}
+
+csc_status csc_cluster(csc_graph g, const csc_params* p, int32_t* labels_out, csc_cluster_info* info,
+                       void* stream) {
+    clear_error();
+    CSC_TRY(check_graph(g));
+    if (!p || !labels_out || p->k < 1 || p->k > g->N) {
+        set_error("csc_cluster: invalid arguments");
+        return CSC_E_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = g->N;
+    const int k = p->k;
+    const int m = p->m > 0 ? p->m : 50;
+    const int d = p->d > 0 ? p->d : (N > 1 ? (int)ceil(4.0 * log((double)N)) : 1);
+    const int d_pad = p->d_pad > 0 ? p->d_pad : ((d + 7) / 8) * 8;
+    int64_t n = p->n > 0 ? p->n : (k > 1 ? (int64_t)ceil(2.0 * k * log((double)k)) : 1);
+    if (n < k) n = k;
+    if (n > N) n = N;
+    const int g_power = p->g_power > 0 ? p->g_power : 4;
+    const double gamma = p->gamma > 0 ? p->gamma : 1e-3;
+    const double cg_tol = p->cg_tol > 0 ? p->cg_tol : 1e-6;
+    const int cg_max = p->cg_max_iter > 0 ? p->cg_max_iter : 2000;
+    const int reps = p->replicates > 0 ? p->replicates : 20;
+    const int km_iter = p->km_max_iter > 0 ? p->km_max_iter : 100;
+    const csc_dtype storage = p->storage;
+    if (d_pad < d || d_pad % 8 || (storage != CSC_F32 && storage != CSC_BF16 && storage != CSC_F64)) {
+        set_error("csc_cluster: invalid d_pad or storage");
+        return CSC_E_INVALID;
+    }
+    csc_cluster_info local;
+    memset(&local, 0, sizeof(local));
+    cudaEvent_t e0, e1, e2, e3, e4, e5;
+    CSC_CUDA_TRY(cudaEventCreate(&e0));
+    CSC_CUDA_TRY(cudaEventCreate(&e1));
+    CSC_CUDA_TRY(cudaEventCreate(&e2));
+    CSC_CUDA_TRY(cudaEventCreate(&e3));
+    CSC_CUDA_TRY(cudaEventCreate(&e4));
+    CSC_CUDA_TRY(cudaEventCreate(&e5));
+    csc_status st = CSC_OK;
+    auto done = [&](csc_status r) {
+        cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
+        cudaEventDestroy(e3); cudaEventDestroy(e4); cudaEventDestroy(e5);
+        return poison_on_cuda(g, r);
+    };
+    cudaEventRecord(e0, s);
+    double lam = p->lambda_k;
+    if (!(lam > 0.0)) {
+        st = csc_estimate_lambda_k(g, k, m, p->n_probes, p->seed, p->bracket, &local.lambda, stream);
+        if (st != CSC_OK) return done(st);
+        lam = local.lambda.lambda;
+    } else {
+        local.lambda.lambda = lam;
+    }
+    cudaEventRecord(e1, s);
+    // pipeline buffers: Y (N x d_pad, fp32 or fp64), idx (n), Xr (n x d_pad fp32), sample labels (n)
+    const size_t ybytes = (size_t)N * d_pad * (storage == CSC_F64 ? 8 : 4);
+    const size_t off_idx = (ybytes + 255) / 256 * 256;
+    const size_t off_xr = off_idx + ((size_t)n * 8 + 255) / 256 * 256;
+    const size_t off_lab = off_xr + ((size_t)n * d_pad * 4 + 255) / 256 * 256;
+    const size_t total = off_lab + (size_t)n * 4 + 256;
+    void* base = nullptr;
+    st = ws_get(g, WS_PIPE, total, &base);
+    if (st != CSC_OK) return done(st);
+    char* b = (char*)base;
+    void* Y = b;
+    int64_t* idx = (int64_t*)(b + off_idx);
+    float* Xr = (float*)(b + off_xr);
+    int32_t* slab = (int32_t*)(b + off_lab);
+    std::vector<double> c(m + 1);
+    cheb_coefficients(lam, m, true, c.data());
+    st = run_filter(g, c.data(), m, d, d_pad, p->seed, storage, nullptr, Y, true, s);
+    if (st != CSC_OK) return done(st);
+    cudaEventRecord(e2, s);
+    st = run_sample(N, n, p->seed, idx, g, s);
+    if (st != CSC_OK) return done(st);
+    if (storage == CSC_F64) {
+        // fp64 feature rows are narrowed to fp32 for k-means
+        st = run_gather_rows_f64((const double*)Y, N, d_pad, idx, n, d, Xr, d_pad, s);
+    } else {
+        st = run_gather_rows((const float*)Y, N, d_pad, idx, n, d, Xr, d_pad, s);
+    }
+    if (st != CSC_OK) return done(st);
+    cudaEventRecord(e3, s);
+    st = run_kmeans(Xr, n, d, d_pad, k, reps, km_iter, p->seed, slab, &local.inertia, g, s);
+    if (st != CSC_OK) return done(st);
+    cudaEventRecord(e4, s);
+    st = run_interpolate(g, idx, slab, n, k, g_power, gamma, cg_tol, cg_max, labels_out, nullptr, &local.cg, s);
+    if (st != CSC_OK && st != CSC_E_NOT_CONVERGED) return done(st);
+    cudaEventRecord(e5, s);
+    cudaError_t ce = cudaEventSynchronize(e5);
+    if (ce != cudaSuccess) {
+        set_error("csc_cluster: %s", cudaGetErrorString(ce));
+        return done(CSC_E_CUDA);
+    }
+    cudaEventElapsedTime(&local.ms_lambda, e0, e1);
+    cudaEventElapsedTime(&local.ms_filter, e1, e2);
+    cudaEventElapsedTime(&local.ms_sample, e2, e3);
+    cudaEventElapsedTime(&local.ms_kmeans, e3, e4);
+    cudaEventElapsedTime(&local.ms_interp, e4, e5);
+    cudaEventElapsedTime(&local.ms_total, e0, e5);
+    if (info) *info = local;
+    return done(st);
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// common.cuh -- internal declarations shared by the translation units of libcsc.
+//
+// Graph handle layout, error plumbing, workspace slots and the launchers each
+// .cu file exports to the C-ABI layer (api.cu).  Nothing here is part of the
+// public ABI (include/csc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/csc.h"
+
+namespace csc {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+void clear_error();
+
+#define CSC_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t e__ = (expr);                                                       \
+        if (e__ != cudaSuccess) {                                                       \
+            ::csc::set_error("%s: %s (%s:%d)", #expr, cudaGetErrorString(e__), __FILE__, \
+                             __LINE__);                                                 \
+            return CSC_E_CUDA;                                                          \
+        }                                                                               \
+    } while (0)
+
+#define CSC_TRY(expr)                      \
+    do {                                   \
+        csc_status s__ = (expr);           \
+        if (s__ != CSC_OK) return s__;     \
+    } while (0)
+
+#define CSC_LAUNCH_CHECK()                                                                  \
+    do {                                                                                    \
+        cudaError_t e__ = cudaGetLastError();                                               \
+        if (e__ != cudaSuccess) {                                                           \
+            ::csc::set_error("kernel launch: %s (%s:%d)", cudaGetErrorString(e__), __FILE__, \
+                             __LINE__);                                                     \
+            return CSC_E_CUDA;                                                              \
+        }                                                                                   \
+    } while (0)
+
+// ------------------------------------------------------------- workspace
+// Scratch slots owned by a graph handle; each grows on demand (cudaMalloc)
+// and lives until the handle is destroyed.
+enum WsSlot {
+    WS_XA = 0,      // signal block ping (X_j / X_{j-1})
+    WS_XB,          // signal block pong
+    WS_YACC,        // fp64 accumulator (F64 storage)
+    WS_PARTIAL,     // per-block fp64 partial sums
+    WS_MOMENTS,     // moment sums
+    WS_CG,          // CG vectors
+    WS_SAMPLE,      // sampling scratch
+    WS_KMEANS,      // k-means scratch
+    WS_MISC,
+    WS_PIPE,        // pipeline buffers of csc_cluster
+    WS_COUNT
+};
+
+struct Buffer {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct Graph {
+    int64_t N = 0;        // nodes (packed total for batched graphs)
+    int64_t nnz = 0;      // stored entries after self-loop removal
+    int32_t n_graphs = 1;
+    int device = 0;
+    int num_sms = 148;
+    int32_t* row_ptr = nullptr;  // device int32[N+1], internal node order
+    int32_t* col_idx = nullptr;  // device int32[nnz]
+    float* dinv = nullptr;       // device float[N]: D^-1/2 (0 for isolated nodes)
+    double* dinv64 = nullptr;    // device double[N]
+    int32_t* deg = nullptr;      // device int32[N]
+    int32_t* perm = nullptr;     // device int32[N]: internal row -> original id (nullptr: identity)
+    int32_t* iperm = nullptr;    // device int32[N]: original id -> internal row
+    // batched handles
+    std::vector<int64_t> offsets;    // host, n_graphs+1 (packed node offsets)
+    int64_t* d_offsets = nullptr;    // device copy
+    int32_t* graph_of_row = nullptr; // device int32[N]
+    Buffer ws[WS_COUNT];
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    double* pinned = nullptr;  // small pinned host staging (4096 doubles)
+    bool poisoned = false;
+};
+
+csc_status ws_get(Graph* g, WsSlot slot, size_t bytes, void** out);
+
+// Device helpers exported by the kernel translation units -----------------
+
+// spmm.cu: degrees and D^-1/2 from the CSR pattern (K4)
+csc_status launch_degrees(Graph* g, cudaStream_t s);
+
+// spmm.cu: the Jackson-Chebyshev filter (K3 + K1 + K5)
+csc_status run_filter(Graph* g, const double* coeffs, int m, int d, int d_pad, uint64_t seed,
+                      csc_dtype storage, const float* R_in, void* Y_out, bool normalize,
+                      cudaStream_t s);
+
+// spmm.cu: eigencount moments (K2); mu_host receives n_moments values
+csc_status run_moments(Graph* g, int n_moments, int n_probes, uint64_t seed, csc_dtype storage,
+                       double* mu_host, int* passes, cudaStream_t s);
+
+// sample.cu (K6)
+csc_status run_sample(int64_t N, int64_t n, uint64_t seed, int64_t* idx_out, Graph* scratch_owner,
+                      cudaStream_t s);
+csc_status run_gather_rows(const float* X, int64_t N, int ld, const int64_t* idx, int64_t n, int d,
+                           float* out, int ld_out, cudaStream_t s);
+csc_status run_gather_rows_f64(const double* X, int64_t N, int ld, const int64_t* idx, int64_t n, int d,
+                               float* out, int ld_out, cudaStream_t s);
+
+// kmeans.cu (K7)
+csc_status run_kmeans(const float* X, int64_t n, int d, int ld, int k, int replicates, int max_iter,
+                      uint64_t seed, int32_t* labels_out, double* inertia_out, Graph* scratch_owner,
+                      cudaStream_t s);
+
+// cg.cu (K8 + K9)
+csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* sample_labels,
+                           int64_t n, int k, int g_power, double gamma, double rel_tol, int max_iter,
+                           int32_t* labels_out, float* fuzzy_out, csc_cg_info* info, cudaStream_t s);
+
+// host math (api.cu)
+void cheb_coefficients(double lambda_c, int m, bool jackson, double* c);
+
+// Philox4x32-10 and SplitMix64 stream identifiers (the key's high word is
+// xor-ed with these so that signals, probes and k-means draws are disjoint).
+constexpr uint32_t STREAM_SIGNALS = 0x5349474Eu;
+constexpr uint32_t STREAM_PROBES = 0x50524F42u;
+constexpr uint32_t STREAM_KMEANS = 0x4B4D4541u;
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace csc

@@ -1,0 +1,186 @@
+"""Parity of the eigencount moments and lambda_k estimate (Sec. 4.3), sampling (Eq. 4),
+reduced k-means (Alg. 2 step 6) and interpolation (Eq. 5, Sec. 4.1) with the oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import csc_inputs as ci
+from oracle import ari as oari
+from oracle import chebyshev as och
+from oracle import interp as ointerp
+from oracle import kmeans as okm
+from oracle import laplacian as olap
+from oracle import sampling as osamp
+
+from .helpers import rel
+
+pytestmark = pytest.mark.gpu
+
+csc = pytest.importorskip("paper_1602_02018_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1602_02018_gb300 import build
+
+    build.build()
+
+
+# ------------------------------------------------------------------ moments
+
+@pytest.mark.parametrize("n,k,n_mom,n_v,rcm", [(1000, 20, 51, 14, False), (1000, 20, 51, 14, True),
+                                               (777, 7, 64, 8, False), (2000, 10, 2, 3, False),
+                                               (300, 6, 1, 5, False), (300, 6, 12, 17, True)])
+def test_moments_match_oracle(n, k, n_mom, n_v, rcm):
+    g = ci.sbm(n, k, s=12.0, seed=3) if n % k == 0 else ci.erdos_renyi(n, 12.0 / n, seed=3)
+    s = olap.normalized_adjacency(g.row_ptr, g.col_idx)
+    probes = och.probe_signals(g.n, n_v, n_v, seed=17)
+    ref = och.moments(s, probes, max(n_mom - 1, 0))[:n_mom]
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM if rcm else 0) as h:
+        mu = csc.csc_kpm_moments(h, n_mom, n_v, seed=17)
+    assert np.max(np.abs(mu - ref)) <= 2e-5 * abs(ref[0])
+
+
+def test_moments_bf16_bound():
+    g = ci.sbm(1000, 20, seed=0)
+    s = olap.normalized_adjacency(g.row_ptr, g.col_idx)
+    ref = och.moments(s, och.probe_signals(g.n, 14, 14, seed=1), 50)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        mu = csc.csc_kpm_moments(h, 51, 14, seed=1, storage=csc.BF16)
+    assert np.max(np.abs(mu - ref)) <= 2e-2 * ref[0]
+
+
+@pytest.mark.parametrize("n,k,seed", [(1000, 20, 0), (1000, 20, 5), (3000, 30, 1)])
+def test_lambda_k_matches_oracle(n, k, seed):
+    g = ci.sbm(n, k, seed=seed)
+    s = olap.normalized_adjacency(g.row_ptr, g.col_idx)
+    n_v = math.ceil(2 * math.log(n))
+    est = och.estimate_lambda_k(s, k, 50, n_v, seed)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        info = csc.csc_estimate_lambda_k(h, k, 50, 0, seed)
+    assert info.n_probes == n_v and info.moment_passes == 25
+    assert info.hit == est["hit"]
+    # the GPU's lambda is a valid dichotomy answer under the oracle's moments
+    c = och.eigencount(est["mu"], info.lam)
+    assert abs(c - k) < 0.5 + 1e-3
+    assert abs(info.lam - est["lam"]) <= 2.0 ** -info.iters + 1e-12 or info.lam == est["lam"]
+
+
+def test_lambda_k_bracket():
+    g = ci.sbm(1000, 20, seed=0)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        base = csc.csc_estimate_lambda_k(h, 20, 50, 0, 0)
+        good = csc.csc_estimate_lambda_k(h, 20, 50, 0, 0, bracket=(base.lam - 0.05, base.lam + 0.05))
+        bad = csc.csc_estimate_lambda_k(h, 20, 50, 0, 0, bracket=(1.5, 1.9))
+    assert good.bracket_used and round(good.count) == 20
+    assert not bad.bracket_used and bad.lam == base.lam
+
+
+# ----------------------------------------------------------------- sampling
+
+@pytest.mark.parametrize("N,n,seed", [(1, 1, 0), (10, 10, 1), (1000, 120, 0), (100_000, 2_120, 0),
+                                      (12_345, 1, 7), (65_537, 922, 2**63 + 5), (5_000, 4_999, 3),
+                                      (1_000_000, 922, 0)])
+def test_sample_bit_exact(N, n, seed):
+    got = csc.csc_sample(N, n, seed).cpu().numpy()
+    assert np.array_equal(got, osamp.sample(N, n, seed))
+
+
+def test_sample_zero():
+    out = csc.csc_sample(100, 0, 1)
+    assert out.numel() == 0
+
+
+# ------------------------------------------------------------------ k-means
+
+def _features(n_nodes=1000, k=20, seed=0):
+    g = ci.sbm(n_nodes, k, seed=seed)
+    s = olap.normalized_adjacency(g.row_ptr, g.col_idx)
+    r = och.random_signals(g.n, 28, 28, seed)
+    f = och.normalize_rows(och.cheb_filter(s, r, och.filter_coeffs(0.44, 50)))
+    om = osamp.sample(g.n, 120, seed)
+    return f[om].astype(np.float32)
+
+
+@pytest.mark.parametrize("k,reps", [(20, 20), (20, 1), (5, 3)])
+def test_kmeans_matches_oracle(k, reps):
+    x = _features()
+    lab_ref, _, in_ref, _ = okm.kmeans(x.astype(np.float64), k, reps, 100, seed=4)
+    xt = torch.zeros((x.shape[0], 32), dtype=torch.float32, device="cuda")
+    xt[:, :28] = torch.from_numpy(x).cuda()
+    lab, inertia = csc.csc_kmeans_reduced(xt, 28, k, reps, 100, seed=4)
+    lab = lab.cpu().numpy()
+    assert inertia == pytest.approx(in_ref, rel=1e-4)
+    assert oari.ari(lab, lab_ref) >= 0.99
+
+
+def test_kmeans_separated_blobs_and_edge_cases():
+    rng = np.random.default_rng(0)
+    centers = rng.normal(scale=10, size=(7, 5))
+    truth = np.repeat(np.arange(7), 30)
+    x = (centers[truth] + rng.normal(scale=0.05, size=(210, 5))).astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    lab, inertia = csc.csc_kmeans_reduced(xt, 5, 7, 20, 100, seed=1)
+    assert oari.ari(lab.cpu().numpy(), truth) == 1.0
+    # k = 1 and n == k
+    lab1, in1 = csc.csc_kmeans_reduced(xt, 5, 1, 2, 10, seed=0)
+    assert torch.all(lab1 == 0)
+    assert in1 == pytest.approx(float(np.sum((x - x.mean(axis=0)) ** 2)), rel=1e-5)
+    labn, inn = csc.csc_kmeans_reduced(xt[:7].contiguous(), 5, 7, 3, 10, seed=0)
+    assert sorted(labn.cpu().tolist()) == list(range(7)) and inn == 0.0
+
+
+# ------------------------------------------------------------ interpolation
+
+@pytest.mark.parametrize("n_nodes,k,n_s,power,rcm", [(1000, 20, 120, 4, False), (1000, 20, 120, 4, True),
+                                                   (600, 6, 40, 2, False), (500, 5, 30, 1, False)])
+def test_interpolation_matches_oracle(n_nodes, k, n_s, power, rcm):
+    g = ci.sbm(n_nodes, k, seed=2)
+    lap = olap.laplacian(g.row_ptr, g.col_idx)
+    om = osamp.sample(g.n, n_s, 2)
+    lab = g.labels[om].astype(np.int32)
+    x_ref, _, _ = ointerp.interpolate(lap, om, lab, k, 1e-3, power, tol=1e-11)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM if rcm else 0) as h:
+        labels, fz, info = csc.csc_interpolate(h, torch.from_numpy(om).cuda(), torch.from_numpy(lab).cuda(), k,
+                                               power, 1e-3, 1e-7, 5000, fuzzy=True)
+    assert info.converged and info.max_rel_residual <= 1e-6
+    x = fz.cpu().numpy()
+    assert rel(x, x_ref) <= 1e-4
+    # the residual, recomputed by the oracle in fp64
+    b = ointerp.rhs(g.n, om, lab, k)
+    res = ointerp.apply_system(lap, ointerp.mask(g.n, om), 1e-3, power, x.astype(np.float64)) - b
+    assert np.max(np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)) <= 3e-6
+    assert np.array_equal(labels.cpu().numpy(), ointerp.labels_from_indicators(x))
+    assert oari.ari(labels.cpu().numpy(), ointerp.labels_from_indicators(x_ref)) >= 0.999
+
+
+def test_interpolation_cliques_exact():
+    g = ci.disjoint_cliques(4, 7)
+    om = np.array([0, 9, 15, 27], dtype=np.int64)
+    lab = g.labels[om].astype(np.int32)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        labels, fz, info = csc.csc_interpolate(h, torch.from_numpy(om).cuda(), torch.from_numpy(lab).cuda(), 4,
+                                               fuzzy=True)
+    assert np.array_equal(labels.cpu().numpy(), g.labels)
+    assert np.allclose(fz.cpu().numpy(), np.eye(4)[g.labels], atol=1e-5)
+
+
+def test_interpolation_not_converged_status():
+    g = ci.sbm(1000, 20, seed=2)
+    om = osamp.sample(g.n, 120, 2)
+    lab = g.labels[om].astype(np.int32)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        labels, _, info = csc.csc_interpolate(h, torch.from_numpy(om).cuda(), torch.from_numpy(lab).cuda(), 20,
+                                              max_iter=3)
+    assert not info.converged and info.iters == 3
+
+
+def test_interpolation_bad_label_rejected():
+    g = ci.sbm(100, 5, s=8, seed=2)
+    om = np.array([0, 50], dtype=np.int64)
+    lab = np.array([0, 7], dtype=np.int32)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        with pytest.raises(csc.CscError):
+            csc.csc_interpolate(h, torch.from_numpy(om).cuda(), torch.from_numpy(lab).cuda(), 5)

@@ -1,0 +1,86 @@
+"""Host-side logic of libcsc checked on the CPU: CSR validation errors, the
+Jackson-Chebyshev coefficients and the eigencount, against the oracle."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import csc_inputs as ci
+from oracle import chebyshev as och
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1602_02018_gb300 import _native, build
+
+    build.build()
+    return _native
+
+
+def _create(nat, rp, colidx, flags=0):
+    rp = np.ascontiguousarray(rp, dtype=np.int64)
+    colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+    out = ctypes.c_void_p()
+    st = nat.lib().csc_graph_create(len(rp) - 1, len(colidx), rp.ctypes.data_as(ctypes.c_void_p),
+                                    colidx.ctypes.data_as(ctypes.c_void_p), None, flags, None, ctypes.byref(out))
+    return st, out
+
+
+@pytest.mark.parametrize("rp,cols,flags", [
+    ([1, 1, 2], [0, 1], 0),             # row_ptr[0] != 0
+    ([0, 1, 3], [1, 0], 0),             # row_ptr[N] != nnz
+    ([0, 2, 2], [1, 0], 0),             # unsorted row
+    ([0, 2, 3], [1, 1, 0], 0),          # duplicate column
+    ([0, 1, 2], [5, 0], 0),             # out of range
+    ([0, 1, 1], [1], 2),                # asymmetric with CSC_CHECK_SYM
+])
+def test_malformed_csr_rejected(L, rp, cols, flags):
+    st, h = _create(L, rp, cols, flags)
+    assert st == L.CSC_E_CSR
+    assert not h.value
+    assert len(L.lib().csc_last_error()) > 0
+
+
+def test_invalid_arguments(L):
+    out = ctypes.c_void_p()
+    assert L.lib().csc_graph_create(0, 0, None, None, None, 0, None, ctypes.byref(out)) == L.CSC_E_INVALID
+    rp = np.array([0, 0], np.int64)
+    w = np.ones(1, np.float32)
+    assert L.lib().csc_graph_create(1, 0, rp.ctypes.data_as(ctypes.c_void_p), None,
+                                    w.ctypes.data_as(ctypes.c_void_p), 0, None,
+                                    ctypes.byref(out)) == L.CSC_E_UNSUPPORTED
+    c = np.empty(4)
+    assert L.lib().csc_chebyshev_coefficients(2.5, 3, 0, c.ctypes.data_as(ctypes.c_void_p)) == L.CSC_E_INVALID
+    assert L.lib().csc_chebyshev_coefficients(0.5, -1, 0, c.ctypes.data_as(ctypes.c_void_p)) == L.CSC_E_INVALID
+    assert L.lib().csc_sample(10, 11, 0, None, None) == L.CSC_E_INVALID
+
+
+@pytest.mark.parametrize("m", [0, 1, 5, 50, 100])
+@pytest.mark.parametrize("lam", [0.0, 0.013, 0.4375, 1.0, 1.93, 2.0])
+@pytest.mark.parametrize("flags", [0, 2])
+def test_coefficients_match_oracle(L, m, lam, flags):
+    c = np.empty(m + 1)
+    assert L.lib().csc_chebyshev_coefficients(lam, m, flags, c.ctypes.data_as(ctypes.c_void_p)) == 0
+    ref = och.filter_coeffs(lam, m, damped=(flags == 0))
+    assert np.allclose(c, ref, rtol=1e-13, atol=1e-15)
+
+
+def test_eigencount_matches_oracle(L):
+    rng = np.random.default_rng(0)
+    mu = rng.normal(size=51) * 10
+    mu[0] = 1000.0
+    for lam in (0.0, 0.3, 1.1, 2.0):
+        out = ctypes.c_double()
+        assert L.lib().csc_eigencount(mu.ctypes.data_as(ctypes.c_void_p), 50, lam, 0, ctypes.byref(out)) == 0
+        assert out.value == pytest.approx(och.eigencount(mu, lam), rel=1e-12, abs=1e-9)
+
+
+def test_workload_defaults_agree():
+    import paper_1602_02018_gb300 as csc
+    from oracle import pipeline
+
+    for n_nodes, k in ((1000, 20), (100_000, 200), (10**6, 100)):
+        a = csc.default_sizes(n_nodes, k)
+        b = pipeline.defaults(n_nodes, k)
+        w = ci.workload_sizes(n_nodes, k)
+        assert a["d"] == b["d"] == w["d"] and a["n"] == b["n"] == w["n"] and a["n_probes"] == b["n_v"] == w["n_v"]
