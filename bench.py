@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark of Compressive Spectral Clustering on GB300.
+
+One step = one pass of the whole path of Alg. 2 on one synthetic graph:
+eigencount moments and the lambda_k dichotomy, the Jackson-Chebyshev filter
+of d random signals with row normalisation, uniform sampling, reduced
+k-means (20 replicates), CG interpolation of Eq. 5 (g(L) = L^4) and the
+label rule.  The default workload is the SBM with N = 1e5 nodes, k = 200
+equal communities, mean degree 16, eps = eps_c / 4, d = ceil(4 ln N) = 47
+signals padded to 48 columns, m = 50, n = ceil(2 k ln k) = 2120 samples.
+
+value  = Chebyshev-filter throughput m * nnz * d / t_filter (nnz.col/s),
+         t_filter the device time of the filter stage inside each timed step
+         (graph resident in HBM, L2 flushed between steps).
+e2e    = the same work over the end-to-end step through the C ABI with host
+         buffers: host CSR -> csc_graph_create (upload + degrees) ->
+         csc_cluster -> labels copied back to pinned host memory.
+
+`--impl reference` times the FP64 oracle (the CPU restatement of the
+method) on a bounded sample of the same workload: one oracle filter pass.
+Multi-GPU (torchrun): every rank runs its own replica (independent graphs,
+no collective on the data path); value aggregates all ranks' work over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Cheb-filter nnz·col/s and % HBM peak; end-to-end CSC sec vs plain at equal ARI"
+UNIT = "nnz*col/s"
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "sbm_n1e5_k200": dict(kind="sbm", n=100_000, k=200, s=16.0, m=50),
+    "sbm_n1e3_k20": dict(kind="sbm", n=1000, k=20, s=16.0, m=50),
+    "chung_lu_n1e6_k100": dict(kind="chung_lu", n=1_000_000, k=100, exponent=2.1, mean=6.0, m=100),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sbm_n1e5_k200", choices=sorted(WORKLOADS))
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f64"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_graph(w: dict, seed: int):
+    import csc_inputs as ci
+
+    if w["kind"] == "sbm":
+        return ci.sbm(w["n"], w["k"], s=w["s"], seed=seed)
+    return ci.chung_lu(w["n"], exponent=w["exponent"], mean=w["mean"], seed=seed)
+
+
+def sizes(w: dict):
+    import csc_inputs as ci
+
+    return ci.workload_sizes(w["n"], w["k"])
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock, power and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines: list[str] = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(kernel_class: str):
+    """DRAM traffic per launch from the committed ncu summary, if the kernel source is unchanged since."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f).get(kernel_class)
+        if not rec:
+            return None, None
+        src = os.path.join(ROOT, rec["source"])
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if sha != rec["sha256"]:
+            return None, "kernel source changed since the ncu capture"
+        return float(rec["bytes_per_launch_full"]), rec.get("note")
+    except (OSError, KeyError, ValueError):
+        return None, None
+
+
+def adjusted_rand(a, b) -> float:
+    """Adjusted Rand index of two labelings (Hubert & Arabie 1985): scoring of the output only."""
+    import numpy as np
+
+    _, ai = np.unique(a, return_inverse=True)
+    _, bi = np.unique(b, return_inverse=True)
+    t = np.zeros((ai.max() + 1, bi.max() + 1))
+    np.add.at(t, (ai, bi), 1)
+    c2 = lambda x: (x * (x - 1) / 2.0).sum()  # noqa: E731
+    sij, sa, sb, tot = c2(t), c2(t.sum(1)), c2(t.sum(0)), len(a) * (len(a) - 1) / 2.0
+    exp = sa * sb / tot
+    den = 0.5 * (sa + sb) - exp
+    return 1.0 if den == 0 else float((sij - exp) / den)
+
+
+# --------------------------------------------------------- CPU oracle sample
+def oracle_filter_sample(g, lam: float, m: int, d: int, seed: int, min_s: float = 10.0, max_runs: int = 5):
+    """Time the oracle's filter stage (Y = h~(L) R, rows normalised) on the full graph."""
+    from oracle import chebyshev as och
+    from oracle import laplacian as olap
+
+    s = olap.normalized_adjacency(g.row_ptr, g.col_idx)
+    r = och.random_signals(g.n, d, d, seed)
+    c = och.filter_coeffs(lam, m)
+    times = []
+    t_all = time.perf_counter()
+    while len(times) < max_runs:
+        t0 = time.perf_counter()
+        och.normalize_rows(och.cheb_filter(s, r, c))
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all >= min_s:
+            break
+    return times
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return 0
+    sz = sizes(w)
+    g = make_graph(w, args.seed)
+    d, m = sz["d"], w["m"]
+    work = float(m) * g.nnz * d
+    # the cut-off used by the oracle sample: the oracle's own lambda_k would cost its
+    # eigencount stage; the filter's cost does not depend on the cut-off value
+    lam = 0.40625
+    from oracle import chebyshev as och
+    from oracle import laplacian as olap
+
+    s = olap.normalized_adjacency(g.row_ptr, g.col_idx)
+    r = och.random_signals(g.n, d, d, args.seed)
+    c = och.filter_coeffs(lam, m)
+    for _ in range(args.warmup):
+        och.normalize_rows(och.cheb_filter(s, r, c))
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        och.normalize_rows(och.cheb_filter(s, r, c))
+        ts.append(time.perf_counter() - t0)
+    t = statistics.mean(ts)
+    val = work / t
+    sample = (f"oracle Chebyshev filter stage (FP64 scipy, m={m}, d={d}, rows normalised) on the full "
+              f"{args.workload} graph (N={g.n}, nnz={g.nnz}) per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "N": g.n, "nnz": g.nnz, "k": w["k"], "m": m, "d": d,
+                   "d_pad": sz["d_pad"], "n": sz["n"]},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host_cores": os.cpu_count()},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, w, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_1602_02018_gb300 as csc
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    storage = {"f32": csc.F32, "bf16": csc.BF16, "f64": csc.F64}[args.storage]
+    sz = sizes(w)
+    d, d_pad, m, k, n = sz["d"], sz["d_pad"], w["m"], w["k"], sz["n"]
+    g = make_graph(w, args.seed + rank)
+    work = float(m) * g.nnz * d
+    stream = torch.cuda.current_stream()
+    h = csc.csc_graph_create(g.row_ptr, g.col_idx)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def step():
+        return csc.csc_cluster(h, k, m=m, d=d, d_pad=d_pad, n=n, storage=storage, seed=args.seed + rank)
+
+    for _ in range(args.warmup):
+        labels, info = step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    csc.csc_profile_reset()
+    csc.csc_profile_enable(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos = []
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        labels, info = step()
+        ev[i][1].record(stream)
+        infos.append(info)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    csc.csc_profile_enable(False)
+    clocks = sampler.stop()
+    launches = csc.csc_profile_launches()
+    classes = csc.csc_profile_query()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    filt_ms = [x.ms["filter"] for x in infos]
+    ms_step, ms_filter = statistics.mean(step_ms), statistics.mean(filt_ms)
+    if dist:
+        t = torch.tensor([ms_step, ms_filter], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step, ms_filter = t.tolist()
+    value = world * work / (ms_filter / 1e3)
+
+    # roofline of the dominant kernel class (live CUDA-event durations, algorithmic bytes)
+    peak, peak_kind = peaks()
+    dom = max(classes.items(), key=lambda kv: kv[1]["ms"])
+    total_ms = sum(v["ms"] for v in classes.values())
+
+    def roof(name):
+        c = classes[name]
+        per_launch_bytes = c["bytes"] / c["launches"]
+        avg_ms = c["ms"] / c["launches"]
+        achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
+        traffic, note = recorded_traffic(name)
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "traffic": traffic, "traffic_note": note, "algorithmic_bytes_per_launch": per_launch_bytes,
+                "avg_launch_us": avg_ms * 1e3, "launches": c["launches"], "share": c["ms"] / total_ms}
+
+    roofline = roof(dom[0])
+    filter_roofline = roof("cheb_step") if "cheb_step" in classes else None
+
+    lab = labels.cpu().numpy()
+    ari_truth = adjusted_rand(lab, g.labels) if g.labels is not None else None
+    last = infos[-1]
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        rp_pin = torch.from_numpy(g.row_ptr).pin_memory()
+        ci_pin = torch.from_numpy(g.col_idx).pin_memory()
+        lab_host = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        ts = []
+        for i in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h2 = csc.csc_graph_create(rp_pin.numpy(), ci_pin.numpy())
+            labs, _ = csc.csc_cluster(h2, k, m=m, d=d, d_pad=d_pad, n=n, storage=storage, seed=args.seed + rank)
+            lab_host.copy_(labs)
+            torch.cuda.synchronize()
+            h2.close()
+            if i >= args.warmup:
+                ts.append(time.perf_counter() - t0)
+        t_e2e = statistics.mean(ts)
+        if dist:
+            t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = t.item()
+        h2d = (g.n + 1) * 4 + g.nnz * 4
+        d2h = g.n * 4
+        e2e = {"value": world * work / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "csc_seconds": t_e2e,
+               "what": "host CSR -> csc_graph_create (upload, degrees) -> csc_cluster -> labels to pinned host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        times = oracle_filter_sample(g, last.lam.lam, m, d, args.seed)
+        cpu = {"value": work / statistics.mean(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle Chebyshev filter stage (FP64 scipy, m={m}, d={d}, rows normalised) on the full "
+                         f"graph, {len(times)} run(s) of {statistics.mean(times):.2f} s",
+               "host_cores": os.cpu_count()}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": args.workload, "N": g.n, "nnz": g.nnz, "k": k, "m": m, "d": d, "d_pad": d_pad,
+                       "n": n, "n_probes": sz["n_v"], "g_power": 4, "gamma": 1e-3, "cg_tol": 1e-6,
+                       "l2": "flushed between steps (512 MB write)",
+                       "value_basis": "m*nnz*d / device time of the filter stage of each timed step",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "csc_seconds": ms_step / 1e3,
+            "filter_ms": ms_filter,
+            "stages_ms": {kk: statistics.mean(x.ms[kk] for x in infos) for kk in infos[0].ms},
+            "lambda_k": last.lam.lam, "cg_iters": last.cg.iters, "kmeans_inertia": last.inertia,
+            "ari_vs_planted": ari_truth,
+            "roofline": roofline,
+            "filter_roofline": filter_roofline,
+            "kernel_classes": {kk: {"launches": v["launches"], "ms": round(v["ms"], 4)} for kk, v in classes.items()},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    if "WORLD_SIZE" not in os.environ:
+        world = 1
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w, rank, world)
+    return run_ours(args, w, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -289,6 +289,26 @@ CSC_API csc_status csc_interpolate(csc_graph g, const int64_t* sample_idx, const
 CSC_API csc_status csc_cluster(csc_graph g, const csc_params* params, int32_t* labels_out,
                        csc_cluster_info* info, void* stream);
 
+/* ------------------------------------------------------ instrumentation
+ * Launch accounting (not a step of the paper's method): every kernel launch
+ * of the library is counted; while profiling is enabled each launch is also
+ * bracketed by CUDA events recorded on its own stream and tagged with a
+ * kernel-class name and its algorithmic bytes (the minimum bytes the
+ * operation must move).  Process-wide state; not thread-safe against
+ * concurrent enable/reset. */
+
+/* csc_profile_enable -- on != 0 starts event timing of subsequent launches. */
+CSC_API csc_status csc_profile_enable(int32_t on);
+/* csc_profile_reset -- forget all classes and zero the launch counter. */
+CSC_API csc_status csc_profile_reset(void);
+/* csc_profile_launches -- kernel launches since the last reset (host int64 out). */
+CSC_API csc_status csc_profile_launches(int64_t* n);
+/* csc_profile_query -- class i (0-based): its name (NUL-terminated, truncated to
+ * name_len), launches, summed event time in ms and summed algorithmic bytes.
+ * Waits for the recorded events.  CSC_E_INVALID when i is out of range. */
+CSC_API csc_status csc_profile_query(int32_t i, char* name, int32_t name_len, int64_t* launches,
+                                     double* total_ms, double* bytes);
+
 /* --------------------------------------------------------------- errors */
 CSC_API const char* csc_status_str(csc_status s);
 CSC_API const char* csc_last_error(void);

@@ -29,6 +29,10 @@ from .api import (  # noqa: F401
     csc_interpolate,
     csc_kmeans_reduced,
     csc_kpm_moments,
+    csc_profile_enable,
+    csc_profile_launches,
+    csc_profile_query,
+    csc_profile_reset,
     csc_sample,
     default_sizes,
 )

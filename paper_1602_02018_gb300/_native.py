@@ -80,6 +80,10 @@ _SIGNATURES = {
     "csc_interpolate": [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_double, c_double, c_int32,
                         c_void_p, c_void_p, P(csc_cg_info), c_void_p],
     "csc_cluster": [c_void_p, P(csc_params), c_void_p, P(csc_cluster_info), c_void_p],
+    "csc_profile_enable": [c_int32],
+    "csc_profile_reset": [],
+    "csc_profile_launches": [P(c_int64)],
+    "csc_profile_query": [c_int32, ctypes.c_char_p, c_int32, P(c_int64), P(c_double), P(c_double)],
     "csc_status_str": [c_int32],
     "csc_last_error": [],
     "csc_version": [],

@@ -260,6 +260,35 @@ def csc_cluster(g: Graph, k: int, m: int = 0, d: int = 0, d_pad: int = 0, n: int
                                    info.inertia, ms)
 
 
+def csc_profile_enable(on: bool = True) -> None:
+    check(lib().csc_profile_enable(1 if on else 0), "csc_profile_enable")
+
+
+def csc_profile_reset() -> None:
+    check(lib().csc_profile_reset(), "csc_profile_reset")
+
+
+def csc_profile_launches() -> int:
+    n = ctypes.c_int64()
+    check(lib().csc_profile_launches(ctypes.byref(n)), "csc_profile_launches")
+    return n.value
+
+
+def csc_profile_query() -> dict:
+    """{class name: dict(launches, ms, bytes)} for every kernel class seen since the last reset."""
+    out = {}
+    i = 0
+    while True:
+        name = ctypes.create_string_buffer(64)
+        launches, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        st = lib().csc_profile_query(i, name, 64, ctypes.byref(launches), ctypes.byref(ms), ctypes.byref(by))
+        if st != nat.CSC_OK:
+            break
+        out[name.value.decode()] = dict(launches=launches.value, ms=ms.value, bytes=by.value)
+        i += 1
+    return out
+
+
 def default_sizes(N: int, k: int) -> dict:
     """The library's parameter defaults (d = ceil(4 ln N), n = ceil(2 k ln k), n_v = ceil(2 ln N))."""
     d = max(1, math.ceil(4 * math.log(N))) if N > 1 else 1

@@ -368,14 +368,14 @@ static Shape cg_shape(int nv) {
     return {0, 0};
 }
 
-#define CG_DISPATCH(SH, CALL)                                             \
-    do {                                                                  \
-        if (SH.G == 2 && SH.NT == 1) { constexpr int G_ = 2, NT_ = 1; CALL; }   \
-        else if (SH.G == 4) { constexpr int G_ = 4, NT_ = 1; CALL; }      \
-        else if (SH.G == 8) { constexpr int G_ = 8, NT_ = 1; CALL; }      \
-        else if (SH.G == 16) { constexpr int G_ = 16, NT_ = 1; CALL; }    \
-        else if (SH.G == 32 && SH.NT == 1) { constexpr int G_ = 32, NT_ = 1; CALL; } \
-        else { constexpr int G_ = 32, NT_ = 2; CALL; }                    \
+#define CG_DISPATCH(SH, ...)                                                            \
+    do {                                                                                \
+        if (SH.G == 2 && SH.NT == 1) { constexpr int G_ = 2, NT_ = 1; __VA_ARGS__; }          \
+        else if (SH.G == 4) { constexpr int G_ = 4, NT_ = 1; __VA_ARGS__; }                   \
+        else if (SH.G == 8) { constexpr int G_ = 8, NT_ = 1; __VA_ARGS__; }                   \
+        else if (SH.G == 16) { constexpr int G_ = 16, NT_ = 1; __VA_ARGS__; }                 \
+        else if (SH.G == 32 && SH.NT == 1) { constexpr int G_ = 32, NT_ = 1; __VA_ARGS__; }   \
+        else { constexpr int G_ = 32, NT_ = 2; __VA_ARGS__; }                                 \
     } while (0)
 
 csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* sample_labels, int64_t n, int k,
@@ -436,16 +436,21 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     CSC_CUDA_TRY(cudaMemsetAsync(mask, 0, (size_t)N * 4, s));
     CSC_CUDA_TRY(cudaMemsetAsync(slab, 0xff, (size_t)N * 4, s));
     CSC_CUDA_TRY(cudaMemsetAsync(st.n_active, 0, 2 * sizeof(int), s));
-    cg_setup_kernel<<<ceil_div(n, 256), 256, 0, s>>>(sample_idx, sample_labels, n, (int64_t)N, g->iperm, r, mask, slab, ld, k,
-                                                     bad);
-    precond_kernel<<<ceil_div(N, 256), 256, 0, s>>>(mask, (float)gamma, pinv, N);
-    CSC_LAUNCH_CHECK();
+    // algorithmic bytes per launch of each CG kernel (fp32 N x ld blocks)
+    const double blkb = (double)N * ld * 4.0;
+    const double csr_b = 4.0 * g->nnz + 4.0 * (N + 1) + 4.0 * N;
+    const double scal_b = 8.0 * grid * ld;
+    CSC_KLAUNCH("cg_setup", 12.0 * n + 12.0 * n, s,
+                cg_setup_kernel<<<ceil_div(n, 256), 256, 0, s>>>(sample_idx, sample_labels, n, (int64_t)N, g->iperm,
+                                                                 r, mask, slab, ld, k, bad));
+    CSC_KLAUNCH("cg_setup", 8.0 * N, s, precond_kernel<<<ceil_div(N, 256), 256, 0, s>>>(mask, (float)gamma, pinv, N));
     const int kb = ceil_div(k, 128);
-    CG_DISPATCH(sh, (cg_update_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(x, r, p, Ap, nullptr, pinv, N, ld, ld,
-                                                                           part)));
-    cg_beta_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, st, rel_tol * rel_tol, 1);
-    CG_DISPATCH(sh, (cg_pupdate_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(r, p, st.beta, pinv, N, ld, ld)));
-    CSC_LAUNCH_CHECK();
+    CG_DISPATCH(sh, CSC_KLAUNCH("cg_update", blkb + 4.0 * N, s,
+                                cg_update_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(x, r, p, Ap, nullptr, pinv, N, ld,
+                                                                                      ld, part)));
+    CSC_KLAUNCH("cg_scalar", 2 * scal_b, s, cg_beta_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, st, rel_tol * rel_tol, 1));
+    CG_DISPATCH(sh, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
+                                cg_pupdate_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(r, p, st.beta, pinv, N, ld, ld)));
     int* h_active = (int*)g->pinned;
     CSC_CUDA_TRY(cudaMemcpyAsync(h_active, st.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CSC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -459,13 +464,17 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         float* bufs[2] = {t1, t2};
         for (int q = 0; q < g_power - 1; ++q) {
             float* o = bufs[q & 1];
-            CG_DISPATCH(sh, (lap_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(g->row_ptr, g->col_idx, g->dinv, cur, o,
-                                                                             N, ld, ld)));
+            // CSR + D^-1/2, the input block gathered once, the output block written
+            CG_DISPATCH(sh, CSC_KLAUNCH("cg_lap", csr_b + 2 * blkb, s,
+                                        lap_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(g->row_ptr, g->col_idx, g->dinv,
+                                                                                        cur, o, N, ld, ld)));
             cur = o;
         }
-        CG_DISPATCH(sh, (lap_ax_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(g->row_ptr, g->col_idx, g->dinv, cur, in,
-                                                                            mask, (float)gamma, Ap, N, ld, ld, part)));
-        CSC_LAUNCH_CHECK();
+        // CSR + D^-1/2 + mask, t gathered once, p read, Ap written
+        CG_DISPATCH(sh, CSC_KLAUNCH("cg_lap_ax", csr_b + 4.0 * N + 3 * blkb + scal_b, s,
+                                    lap_ax_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(g->row_ptr, g->col_idx, g->dinv,
+                                                                                       cur, in, mask, (float)gamma, Ap,
+                                                                                       N, ld, ld, part)));
         return CSC_OK;
     };
     int it = 0;
@@ -475,13 +484,17 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         const int batch = std::min(check_every, max_iter - it);
         for (int q = 0; q < batch; ++q) {
             CSC_TRY(apply_A(p));
-            cg_alpha_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, st);
-            CG_DISPATCH(sh, (cg_update_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(x, r, p, Ap, st.alpha, pinv, N, ld,
-                                                                                   ld, part)));
+            CSC_KLAUNCH("cg_scalar", scal_b, s, cg_alpha_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, st));
+            // x, r, p, Ap read; x, r written
+            CG_DISPATCH(sh, CSC_KLAUNCH("cg_update", 6 * blkb + 4.0 * N + 2 * scal_b, s,
+                                        cg_update_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(x, r, p, Ap, st.alpha, pinv,
+                                                                                              N, ld, ld, part)));
             CSC_CUDA_TRY(cudaMemsetAsync(st.n_active, 0, sizeof(int), s));
-            cg_beta_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, st, rel_tol * rel_tol, 0);
-            CG_DISPATCH(sh, (cg_pupdate_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(r, p, st.beta, pinv, N, ld, ld)));
-            CSC_LAUNCH_CHECK();
+            CSC_KLAUNCH("cg_scalar", 2 * scal_b, s,
+                        cg_beta_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, st, rel_tol * rel_tol, 0));
+            CG_DISPATCH(sh, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
+                                        cg_pupdate_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(r, p, st.beta, pinv, N, ld,
+                                                                                               ld)));
         }
         it += batch;
         CSC_CUDA_TRY(cudaMemcpyAsync(h_active, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -490,13 +503,16 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     }
     // true residual ||b - A x|| / ||b|| per column
     CSC_TRY(apply_A(x));
-    CG_DISPATCH(sh, (residual_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(Ap, slab, N, ld, ld, part)));
-    column_sum_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, st.rr);
+    CG_DISPATCH(sh, CSC_KLAUNCH("cg_residual", blkb + 4.0 * N, s,
+                                residual_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(Ap, slab, N, ld, ld, part)));
+    CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, st.rr));
     // labels
-    CG_DISPATCH(sh, (colnorm_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(x, N, ld, ld, part)));
-    column_sum_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, norm2);
-    label_argmax_kernel<<<ceil_div(N, 256), 256, 0, s>>>(x, norm2, N, k, ld, g->perm, labels_out, fuzzy_out);
-    CSC_LAUNCH_CHECK();
+    CG_DISPATCH(sh, CSC_KLAUNCH("label_norms", blkb, s,
+                                colnorm_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(x, N, ld, ld, part)));
+    CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, norm2));
+    CSC_KLAUNCH("label_argmax", blkb + 4.0 * N + (fuzzy_out ? (double)N * k * 4 : 0.0), s,
+                label_argmax_kernel<<<ceil_div(N, 256), 256, 0, s>>>(x, norm2, N, k, ld, g->perm, labels_out,
+                                                                     fuzzy_out));
     std::vector<double> rr(k), bn(k);
     CSC_CUDA_TRY(cudaMemcpyAsync(rr.data(), st.rr, k * sizeof(double), cudaMemcpyDeviceToHost, s));
     CSC_CUDA_TRY(cudaMemcpyAsync(bn.data(), st.bn2, k * sizeof(double), cudaMemcpyDeviceToHost, s));

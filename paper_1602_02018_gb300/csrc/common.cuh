@@ -46,6 +46,24 @@ void clear_error();
         }                                                                                   \
     } while (0)
 
+// ------------------------------------------------------- launch accounting
+// Every kernel launch goes through CSC_KLAUNCH(class name, algorithmic bytes,
+// stream, kernel<<<...>>>(...)): it is counted, optionally bracketed by
+// events on its stream (profile.cu), and checked.
+extern bool g_prof_enabled;
+int prof_begin(const char* name, double bytes, cudaStream_t s);
+void prof_end(int slot, cudaStream_t s);
+void count_launch();
+
+#define CSC_KLAUNCH(NAME, BYTES, STREAM, ...)                                                \
+    do {                                                                                    \
+        ::csc::count_launch();                                                              \
+        const int slot__ = ::csc::g_prof_enabled ? ::csc::prof_begin(NAME, (double)(BYTES), STREAM) : -1; \
+        __VA_ARGS__;                                                                        \
+        if (slot__ >= 0) ::csc::prof_end(slot__, STREAM);                                   \
+        CSC_LAUNCH_CHECK();                                                                 \
+    } while (0)
+
 // ------------------------------------------------------------- workspace
 // Scratch slots owned by a graph handle; each grows on demand (cudaMalloc)
 // and lives until the handle is destroyed.

@@ -320,13 +320,14 @@ csc_status run_kmeans(const float* X, int64_t n64, int d, int ld, int k, int rep
         CSC_CUDA_TRY(cudaFuncSetAttribute(kmeans_replicate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
     double* inertia_all = (double*)(b + o_in);
-    kmeans_replicate_kernel<<<reps, kKmThreads, smem, s>>>(X, n, d, ld, k, max_iter, seed, (int32_t*)(b + o_lab),
-                                                           inertia_all, (double*)(b + o_d2),
-                                                           (unsigned long long*)(b + o_sum), (int*)(b + o_cnt),
-                                                           (int32_t*)(b + o_nlab));
+    CSC_KLAUNCH("kmeans", 4.0 * n * d * reps, s,
+                kmeans_replicate_kernel<<<reps, kKmThreads, smem, s>>>(
+                    X, n, d, ld, k, max_iter, seed, (int32_t*)(b + o_lab), inertia_all, (double*)(b + o_d2),
+                    (unsigned long long*)(b + o_sum), (int*)(b + o_cnt), (int32_t*)(b + o_nlab)));
     double* dev_inertia = inertia_all + reps;
-    kmeans_pick_kernel<<<1, 256, 0, s>>>((int32_t*)(b + o_lab), inertia_all, reps, n, labels_out, dev_inertia);
-    CSC_LAUNCH_CHECK();
+    CSC_KLAUNCH("kmeans_pick", 8.0 * n, s,
+                kmeans_pick_kernel<<<1, 256, 0, s>>>((int32_t*)(b + o_lab), inertia_all, reps, n, labels_out,
+                                                     dev_inertia));
     if (inertia_out) {
         CSC_CUDA_TRY(cudaMemcpyAsync(inertia_out, dev_inertia, sizeof(double), cudaMemcpyDeviceToHost, s));
         CSC_CUDA_TRY(cudaStreamSynchronize(s));

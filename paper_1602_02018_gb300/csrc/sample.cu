@@ -213,16 +213,17 @@ csc_status run_sample(int64_t N, int64_t n, uint64_t seed, int64_t* idx_out, Gra
     CSC_CUDA_TRY(cudaMemsetAsync(b, 0, o_ck, s));
     int grid = ceil_div(N, 256);
     if (grid > 4096) grid = 4096;
-    sample_hist1_kernel<<<grid, 256, 0, s>>>(N, seed, h1);
-    sample_find_kernel<<<1, 1024, 0, s>>>(h1, n, sel, 0);
-    sample_hist2_kernel<<<grid, 256, 0, s>>>(N, seed, sel, h2);
-    sample_find_kernel<<<1, 1024, 0, s>>>(h2, n, sel, 1);
-    sample_mark_kernel<<<grid, 256, 0, s>>>(N, seed, sel, fl, ck, cidx, cnt);
-    sample_resolve_kernel<<<1, 1024, 0, s>>>(n, sel, ck, cidx, cnt, fl);
-    compact_count_kernel<<<nblk, 1024, 0, s>>>(fl, N, bc);
-    compact_scan_kernel<<<1, 32, 0, s>>>(bc, nblk);
-    compact_write_kernel<<<nblk, 1024, 0, s>>>(fl, N, bc, idx_out, n);
-    CSC_LAUNCH_CHECK();
+    CSC_KLAUNCH("sample_hist", 4.0 * kBins, s, sample_hist1_kernel<<<grid, 256, 0, s>>>(N, seed, h1));
+    CSC_KLAUNCH("sample_find", 4.0 * kBins, s, sample_find_kernel<<<1, 1024, 0, s>>>(h1, n, sel, 0));
+    CSC_KLAUNCH("sample_hist", 4.0 * kBins, s, sample_hist2_kernel<<<grid, 256, 0, s>>>(N, seed, sel, h2));
+    CSC_KLAUNCH("sample_find", 4.0 * kBins, s, sample_find_kernel<<<1, 1024, 0, s>>>(h2, n, sel, 1));
+    CSC_KLAUNCH("sample_mark", (double)N, s,
+                sample_mark_kernel<<<grid, 256, 0, s>>>(N, seed, sel, fl, ck, cidx, cnt));
+    CSC_KLAUNCH("sample_resolve", 16.0, s, sample_resolve_kernel<<<1, 1024, 0, s>>>(n, sel, ck, cidx, cnt, fl));
+    CSC_KLAUNCH("sample_compact", (double)N, s, compact_count_kernel<<<nblk, 1024, 0, s>>>(fl, N, bc));
+    CSC_KLAUNCH("sample_compact", 8.0 * nblk, s, compact_scan_kernel<<<1, 32, 0, s>>>(bc, nblk));
+    CSC_KLAUNCH("sample_compact", (double)N + 8.0 * n, s,
+                compact_write_kernel<<<nblk, 1024, 0, s>>>(fl, N, bc, idx_out, n));
     if (async_alloc) CSC_CUDA_TRY(cudaFreeAsync(base, s));
     return CSC_OK;
 }
@@ -242,15 +243,15 @@ __global__ void gather_rows_kernel(const S* __restrict__ X, int64_t N, int ld, c
 
 csc_status run_gather_rows(const float* X, int64_t N, int ld, const int64_t* idx, int64_t n, int d, float* out,
                            int ld_out, cudaStream_t s) {
-    gather_rows_kernel<float><<<ceil_div(n * d, 256), 256, 0, s>>>(X, N, ld, idx, n, d, out, ld_out);
-    CSC_LAUNCH_CHECK();
+    CSC_KLAUNCH("gather_rows", 8.0 * n * d + 8.0 * n, s,
+                gather_rows_kernel<float><<<ceil_div(n * d, 256), 256, 0, s>>>(X, N, ld, idx, n, d, out, ld_out));
     return CSC_OK;
 }
 
 csc_status run_gather_rows_f64(const double* X, int64_t N, int ld, const int64_t* idx, int64_t n, int d,
                                float* out, int ld_out, cudaStream_t s) {
-    gather_rows_kernel<double><<<ceil_div(n * d, 256), 256, 0, s>>>(X, N, ld, idx, n, d, out, ld_out);
-    CSC_LAUNCH_CHECK();
+    CSC_KLAUNCH("gather_rows", 12.0 * n * d + 8.0 * n, s,
+                gather_rows_kernel<double><<<ceil_div(n * d, 256), 256, 0, s>>>(X, N, ld, idx, n, d, out, ld_out));
     return CSC_OK;
 }
 

@@ -39,9 +39,9 @@ __global__ void degrees_kernel(const int32_t* __restrict__ rp, int32_t N, int32_
 
 csc_status launch_degrees(Graph* g, cudaStream_t s) {
     if (g->N == 0) return CSC_OK;
-    degrees_kernel<<<ceil_div(g->N, 256), 256, 0, s>>>(g->row_ptr, (int32_t)g->N, g->deg, g->dinv,
-                                                       g->dinv64);
-    CSC_LAUNCH_CHECK();
+    CSC_KLAUNCH("degrees", 4.0 * (g->N + 1) + 16.0 * g->N, s,
+                degrees_kernel<<<ceil_div(g->N, 256), 256, 0, s>>>(g->row_ptr, (int32_t)g->N, g->deg, g->dinv,
+                                                                   g->dinv64));
     return CSC_OK;
 }
 
@@ -300,12 +300,17 @@ static csc_status launch_cheb_step(Graph* g, TileShape sh, const T* xcur, T* xpn
     const A* dv;
     if constexpr (sizeof(A) == 8) dv = g->dinv64; else dv = g->dinv;
     const int grid = grid_for(g, g->N, sh.G);
+    // algorithmic bytes of one order: CSR + D^-1/2, X_j gathered once, X_{j-1} read and
+    // X_{j+1} written (first order: X_0 read, X_1 written), Y written or read+written
+    const double nx = (double)g->N * ncols;
+    const double bytes = 4.0 * g->nnz + 4.0 * (g->N + 1) + (double)sizeof(A) * g->N +
+                         (first ? 2.0 : 3.0) * nx * sizeof(T) + (first ? 1.0 : 2.0) * nx * sizeof(A);
 #define CSC_CHEB_CASE(GG, NN)                                                                    \
     if (sh.G == GG && sh.NT == NN) {                                                             \
-        cheb_step_kernel<T, GG, NN><<<grid, 256, 0, s>>>(g->row_ptr, g->col_idx, dv, xcur, xpn, \
-                                                         Y, g->perm, (int32_t)g->N, ncols, ld,   \
-                                                         (A)c0, (A)cn, first);                   \
-        CSC_LAUNCH_CHECK();                                                                      \
+        CSC_KLAUNCH("cheb_step", bytes, s,                                                       \
+                    cheb_step_kernel<T, GG, NN><<<grid, 256, 0, s>>>(g->row_ptr, g->col_idx, dv, xcur,  \
+                                                                     xpn, Y, g->perm, (int32_t)g->N,    \
+                                                                     ncols, ld, (A)c0, (A)cn, first));   \
         return CSC_OK;                                                                           \
     }
     CSC_CHEB_CASE(2, 1) CSC_CHEB_CASE(2, 2) CSC_CHEB_CASE(2, 3) CSC_CHEB_CASE(4, 1)
@@ -320,12 +325,13 @@ static csc_status launch_cheb_step(Graph* g, TileShape sh, const T* xcur, T* xpn
 template <typename T>
 static csc_status launch_mom_step(Graph* g, TileShape sh, const T* xcur, T* xpn, int ncols, int64_t ld,
                                   int first, double* partials, int grid, cudaStream_t s) {
+    const double bytes = 4.0 * g->nnz + 8.0 * g->N + 4.0 + (first ? 2.0 : 3.0) * (double)g->N * ncols * sizeof(T);
 #define CSC_MOM_CASE(GG, NN)                                                                     \
     if (sh.G == GG && sh.NT == NN) {                                                             \
-        mom_step_kernel<T, GG, NN><<<grid, 256, 0, s>>>(g->row_ptr, g->col_idx, g->dinv, xcur,  \
-                                                        xpn, (int32_t)g->N, ncols, ld, first,    \
-                                                        partials);                               \
-        CSC_LAUNCH_CHECK();                                                                      \
+        CSC_KLAUNCH("mom_step", bytes, s,                                                        \
+                    mom_step_kernel<T, GG, NN><<<grid, 256, 0, s>>>(g->row_ptr, g->col_idx, g->dinv,    \
+                                                                    xcur, xpn, (int32_t)g->N, ncols, ld, \
+                                                                    first, partials));                   \
         return CSC_OK;                                                                           \
     }
     CSC_MOM_CASE(2, 1) CSC_MOM_CASE(2, 2) CSC_MOM_CASE(2, 3) CSC_MOM_CASE(4, 1)
@@ -343,13 +349,15 @@ static csc_status fill_block(Graph* g, T* X, int d, int ld, uint64_t seed, uint3
     const int64_t N = g->N;
     if (R_in) {
         const int64_t tot = N * ld;
-        copy_in_kernel<T><<<ceil_div(tot, 256), 256, 0, s>>>(X, R_in, (int32_t)N, d, ld, ld_in, g->perm);
+        CSC_KLAUNCH("copy_in", (double)tot * (4 + sizeof(T)), s,
+                    copy_in_kernel<T><<<ceil_div(tot, 256), 256, 0, s>>>(X, R_in, (int32_t)N, d, ld, ld_in,
+                                                                         g->perm));
     } else {
         const int64_t tot = N * (ld / 4);
-        gauss_fill_kernel<T><<<ceil_div(tot, 256), 256, 0, s>>>(X, (int32_t)N, d, ld, seed, stream, sigma,
-                                                                g->perm);
+        CSC_KLAUNCH("gauss_fill", (double)N * ld * sizeof(T), s,
+                    gauss_fill_kernel<T><<<ceil_div(tot, 256), 256, 0, s>>>(X, (int32_t)N, d, ld, seed, stream,
+                                                                            sigma, g->perm));
     }
-    CSC_LAUNCH_CHECK();
     return CSC_OK;
 }
 
@@ -369,8 +377,9 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
     CSC_TRY(fill_block<T>(g, X[0], d, d_pad, seed, STREAM_SIGNALS, sigma, R_in, d_pad, s));
     if (m == 0) {
         const int64_t tot = N * d_pad;
-        scale_copy_kernel<T><<<ceil_div(tot, 256), 256, 0, s>>>(X[0], Y, g->perm, (int32_t)N, d_pad, (A)c[0]);
-        CSC_LAUNCH_CHECK();
+        CSC_KLAUNCH("scale_copy", (double)tot * (sizeof(T) + sizeof(A)), s,
+                    scale_copy_kernel<T><<<ceil_div(tot, 256), 256, 0, s>>>(X[0], Y, g->perm, (int32_t)N, d_pad,
+                                                                            (A)c[0]));
     } else {
         const TileShape sh = choose_shape(d_pad / VEC);
         CSC_TRY(launch_cheb_step<T>(g, sh, X[0], X[1], Y, d_pad, d_pad, c[0], c[1], 1, s));
@@ -381,8 +390,8 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
     }
     if (normalize) {
         const int grid = grid_for(g, N, 32);
-        normalize_kernel<A><<<grid, 256, 0, s>>>(Y, (int32_t)N, d, d_pad);
-        CSC_LAUNCH_CHECK();
+        CSC_KLAUNCH("normalize", 2.0 * N * d_pad * sizeof(A), s,
+                    normalize_kernel<A><<<grid, 256, 0, s>>>(Y, (int32_t)N, d, d_pad));
     }
     return CSC_OK;
 }
@@ -425,8 +434,7 @@ static csc_status moments_typed(Graph* g, int n_moments, int n_probes, uint64_t 
     CSC_TRY(fill_block<T>(g, X[0], n_probes, ld, seed, STREAM_PROBES, 1.0f, nullptr, ld, s));
     for (int j = 0; j < J; ++j) {
         CSC_TRY(launch_mom_step<T>(g, sh, X[j & 1], X[(j + 1) & 1], ld, ld, j == 0 ? 1 : 0, P, grid, s));
-        reduce_partials_kernel<<<1, 256, 0, s>>>(P, grid, S + 3 * j);
-        CSC_LAUNCH_CHECK();
+        CSC_KLAUNCH("reduce", 24.0 * grid, s, reduce_partials_kernel<<<1, 256, 0, s>>>(P, grid, S + 3 * j));
     }
     double* host = g->pinned;
     const size_t nsum = (size_t)J * 3;
