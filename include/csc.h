@@ -241,6 +241,26 @@ CSC_API csc_status csc_estimate_lambda_k(csc_graph g, int32_t k, int32_t m, int3
  * Errors: CSC_E_INVALID. */
 CSC_API csc_status csc_sample(int64_t N, int64_t n, uint64_t seed, int64_t* idx_out, void* stream);
 
+/* csc_sample_noalloc -- the same sample as csc_sample (bit for bit), for callers
+ * that cannot allocate device memory: applications whose device memory is all
+ * owned by their own allocator (a framework's caching pool, an arena sized at
+ * start-up), applications with a fixed device-memory budget, and latency-critical
+ * code where cudaMalloc / cudaFree may implicitly synchronize the device.  The
+ * paper has no counterpart; this is a deployment variant of Eq. 4's sampling.
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch is one
+ * fixed array of 327,936 bytes inside the library, present on every device that
+ * loads the library until the process exits.
+ *   N         1 <= N <= 2^26 (67,108,864); larger N returns CSC_E_UNSUPPORTED
+ *             with a message (use csc_sample).
+ *   idx_out   device int64[n], sorted ascending.  Asynchronous on `stream`.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  Every call on a device shares the one scratch array, which
+ * keeps the previous call's contents (each call clears what must start at zero):
+ * calls that overlap on the GPU (different streams, or different host threads
+ * using the same device) race and give wrong results. */
+CSC_API csc_status csc_sample_noalloc(int64_t N, int64_t n, uint64_t seed, int64_t* idx_out, void* stream);
+
 /* csc_gather_rows -- out[i, :] = X[idx[i], :] for i < n (Alg. 2 step 5).
  *   X    device float[N * ld];  idx  device int64[n] (values in [0, N));
  *   out  device float[n * ld_out], columns 0..d-1 written.  Asynchronous. */

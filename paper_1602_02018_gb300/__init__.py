@@ -34,6 +34,7 @@ from .api import (  # noqa: F401
     csc_profile_query,
     csc_profile_reset,
     csc_sample,
+    csc_sample_noalloc,
     default_sizes,
 )
 from ._native import CscError, header_symbols, lib  # noqa: F401

@@ -74,6 +74,7 @@ _SIGNATURES = {
     "csc_estimate_lambda_k": [c_void_p, c_int32, c_int32, c_int32, c_uint64, c_void_p, P(csc_lambda_info),
                               c_void_p],
     "csc_sample": [c_int64, c_int64, c_uint64, c_void_p, c_void_p],
+    "csc_sample_noalloc": [c_int64, c_int64, c_uint64, c_void_p, c_void_p],
     "csc_gather_rows": [c_void_p, c_int64, c_int32, c_void_p, c_int64, c_int32, c_void_p, c_int32, c_void_p],
     "csc_kmeans_reduced": [c_void_p, c_int64, c_int32, c_int32, c_int32, c_int32, c_int32, c_uint64, c_void_p,
                            P(c_double), c_void_p],

@@ -182,6 +182,12 @@ def csc_sample(N: int, n: int, seed: int = 0, out: Optional[torch.Tensor] = None
     return out
 
 
+def csc_sample_noalloc(N: int, n: int, seed: int, out: torch.Tensor, stream=None) -> torch.Tensor:
+    """csc_sample without any device allocation inside the library (the caller gives `out`)."""
+    check(lib().csc_sample_noalloc(N, n, seed, _dptr(out) if n else None, _stream(stream)), "csc_sample_noalloc")
+    return out
+
+
 def csc_gather_rows(X: torch.Tensor, idx: torch.Tensor, d: Optional[int] = None,
                     out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     N, ld = X.shape
