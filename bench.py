@@ -374,6 +374,7 @@ def run_ours(args, w, rank, world, local_rank):
             "roofline": roofline,
             "filter_roofline": filter_roofline,
             "kernel_classes": {kk: {"launches": v["launches"], "ms": round(v["ms"], 4)} for kk, v in classes.items()},
+            "autotuned_shapes": csc.csc_graph_tuned_shapes(h),
             "gpu_launches": launches,
             "clocks": clocks,
             "e2e": e2e,

@@ -162,6 +162,16 @@ CSC_API csc_status csc_graph_destroy(csc_graph g);
  * graphs (1 unless batched).  Any output pointer may be NULL.  Host outputs. */
 CSC_API csc_status csc_graph_info(csc_graph g, int64_t* N, int64_t* nnz, int32_t* n_graphs);
 
+/* csc_graph_tuned_shape -- the launch shapes the autotuner chose on this handle
+ * (not a step of the paper's method).  Shapes are tuned on first use per kernel
+ * kind (1 = Chebyshev step, 2 = moment step, 3 = CG products), storage width and
+ * column count, by timing every compiled shape on the handle's graph.  Entry i
+ * (0-based) is written to kind, dtype_bytes (4 fp32, 2 bf16, 8 fp64), columns and
+ * shape[5] = {lanes per row G, vectors per lane NT, threads per CTA, row ranges P,
+ * column tiles}.  Host outputs (any may be NULL).  CSC_E_INVALID when i is out of range. */
+CSC_API csc_status csc_graph_tuned_shape(csc_graph g, int32_t i, int32_t* kind, int32_t* dtype_bytes,
+                                         int32_t* columns, int32_t* shape);
+
 /* csc_graph_degrees -- D_ii of Sec. 2.1 (integer edge counts, bit-exact) in
  * original node order.  deg_out: host int32[N].  Synchronizes `stream`. */
 CSC_API csc_status csc_graph_degrees(csc_graph g, int32_t* deg_out, void* stream);

@@ -110,6 +110,23 @@ def csc_graph_degrees(g: Graph, stream=None) -> np.ndarray:
     return out
 
 
+def csc_graph_tuned_shapes(g: Graph) -> list:
+    """Launch shapes chosen by the autotuner on this handle (kind, dtype bytes, columns, shape)."""
+    out = []
+    i = 0
+    kinds = {1: "cheb_step", 2: "mom_step", 3: "cg"}
+    while True:
+        kind, db, cols = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        shape = (ctypes.c_int32 * 5)()
+        if lib().csc_graph_tuned_shape(g.handle, i, ctypes.byref(kind), ctypes.byref(db), ctypes.byref(cols),
+                                       shape) != nat.CSC_OK:
+            break
+        out.append(dict(kernel=kinds.get(kind.value, str(kind.value)), dtype_bytes=db.value, columns=cols.value,
+                        G=shape[0], NT=shape[1], threads=shape[2], P=shape[3], tiles=shape[4]))
+        i += 1
+    return out
+
+
 def csc_chebyshev_coefficients(lambda_c: float, m: int, flags: int = 0) -> np.ndarray:
     out = np.empty(m + 1, dtype=np.float64)
     check(lib().csc_chebyshev_coefficients(lambda_c, m, flags, _hptr(out)), "csc_chebyshev_coefficients")

@@ -8,6 +8,9 @@
 
 #include <algorithm>
 #include <chrono>
+#include <iterator>
+#include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <string>
@@ -53,6 +56,73 @@ csc_status ws_get(Graph* g, WsSlot slot, size_t bytes, void** out) {
         b.bytes = bytes;
     }
     *out = b.ptr;
+    return CSC_OK;
+}
+
+namespace {
+struct TuneKey {
+    uint64_t key;
+    int device;
+    int64_t N, nnz;
+    bool operator<(const TuneKey& o) const {
+        if (key != o.key) return key < o.key;
+        if (device != o.device) return device < o.device;
+        if (N != o.N) return N < o.N;
+        return nnz < o.nnz;
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, LaunchCfg> g_tune_cache;
+}  // namespace
+
+bool tune_cache_get(const Graph* g, uint64_t key, LaunchCfg* out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(TuneKey{key, g->device, g->N, g->nnz});
+    if (it == g_tune_cache.end()) return false;
+    *out = it->second;
+    return true;
+}
+
+void tune_cache_put(const Graph* g, uint64_t key, const LaunchCfg& cfg) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[TuneKey{key, g->device, g->N, g->nnz}] = cfg;
+}
+
+csc_status get_partition(Graph* g, int P, const int32_t** out) {
+    auto it = g->parts.find(P);
+    if (it != g->parts.end()) {
+        *out = it->second;
+        return CSC_OK;
+    }
+    const int64_t N = g->N;
+    const std::vector<int32_t>& rp = g->h_row_ptr;
+    // cost(r) = rp[r] + 2r is nondecreasing: boundary b = first row with cost >= b * total / P
+    const double total = (double)rp[N] + 2.0 * (double)N;
+    std::vector<int32_t> bounds(P + 1);
+    bounds[0] = 0;
+    bounds[P] = (int32_t)N;
+    int64_t lo = 0;
+    for (int b = 1; b < P; ++b) {
+        const double target = total * (double)b / (double)P;
+        int64_t a = lo, z = N;
+        while (a < z) {
+            const int64_t mid = (a + z) / 2;
+            if ((double)rp[mid] + 2.0 * (double)mid >= target) z = mid;
+            else a = mid + 1;
+        }
+        lo = a;
+        bounds[b] = (int32_t)a;
+    }
+    int32_t* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, (P + 1) * sizeof(int32_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc for a row partition: %s", cudaGetErrorString(e));
+        return CSC_E_OOM;
+    }
+    CSC_CUDA_TRY(cudaMemcpy(d, bounds.data(), (P + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    g->parts[P] = d;
+    *out = d;
     return CSC_OK;
 }
 
@@ -238,11 +308,16 @@ static void free_graph(Graph* g) {
     cudaFree(g->dinv);
     cudaFree(g->dinv64);
     cudaFree(g->deg);
+    cudaFree(g->invdeg);
+    cudaFree(g->sqdeg);
+    cudaFree(g->invdeg64);
+    cudaFree(g->sqdeg64);
     cudaFree(g->perm);
     cudaFree(g->iperm);
     cudaFree(g->d_offsets);
     cudaFree(g->graph_of_row);
     for (auto& b : g->ws) cudaFree(b.ptr);
+    for (auto& kv : g->parts) cudaFree(kv.second);
     for (auto& e : g->ev)
         if (e) cudaEventDestroy(e);
     if (g->pinned) cudaFreeHost(g->pinned);
@@ -273,13 +348,18 @@ static csc_status upload(Graph* g, const HostCSR& h, const std::vector<int32_t>*
     g->nnz = nnz;
     CSC_CUDA_TRY(cudaGetDevice(&g->device));
     CSC_CUDA_TRY(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
-    std::vector<int32_t> rp32(N + 1);
+    std::vector<int32_t>& rp32 = g->h_row_ptr;
+    rp32.resize(N + 1);
     for (int64_t i = 0; i <= N; ++i) rp32[i] = (int32_t)h.rp[i];
     CSC_TRY(dev_alloc(&g->row_ptr, N + 1));
     CSC_TRY(dev_alloc(&g->col_idx, nnz));
     CSC_TRY(dev_alloc(&g->dinv, N));
     CSC_TRY(dev_alloc(&g->dinv64, N));
     CSC_TRY(dev_alloc(&g->deg, N));
+    CSC_TRY(dev_alloc(&g->invdeg, N));
+    CSC_TRY(dev_alloc(&g->sqdeg, N));
+    CSC_TRY(dev_alloc(&g->invdeg64, N));
+    CSC_TRY(dev_alloc(&g->sqdeg64, N));
     CSC_CUDA_TRY(cudaMemcpyAsync(g->row_ptr, rp32.data(), (N + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     if (nnz)
         CSC_CUDA_TRY(cudaMemcpyAsync(g->col_idx, h.ci.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -489,6 +569,27 @@ csc_status csc_graph_info(csc_graph g, int64_t* N, int64_t* nnz, int32_t* n_grap
     if (N) *N = g->N;
     if (nnz) *nnz = g->nnz;
     if (n_graphs) *n_graphs = g->n_graphs;
+    return CSC_OK;
+}
+
+csc_status csc_graph_tuned_shape(csc_graph g, int32_t i, int32_t* kind, int32_t* dtype_bytes, int32_t* columns,
+                                 int32_t* shape) {
+    clear_error();
+    CSC_TRY(check_graph(g));
+    if (i < 0 || i >= (int32_t)g->tuned.size()) return CSC_E_INVALID;
+    auto it = g->tuned.begin();
+    std::advance(it, i);
+    const uint64_t key = it->first;
+    if (kind) *kind = (int32_t)(key >> 48);
+    if (dtype_bytes) *dtype_bytes = (int32_t)((key >> 40) & 0xff);
+    if (columns) *columns = (int32_t)(key & 0xffffffffu);
+    if (shape) {
+        shape[0] = it->second.G;
+        shape[1] = it->second.NT;
+        shape[2] = it->second.threads;
+        shape[3] = it->second.P;
+        shape[4] = it->second.tiles;
+    }
     return CSC_OK;
 }
 

@@ -3,14 +3,21 @@
 // For every cluster j the minimiser of ||M x - c_j^r||^2 + gamma x^T L^p x solves
 // (M^T M + gamma L^p) x_j = M^T c_j^r.  All k systems are solved together by
 // Jacobi-preconditioned conjugate gradients on an N x k row-major fp32 block
-// (one independent CG per column; per-column inner products in fp64 with
-// fixed-order reductions).  A p = mask * p + gamma L^p p is computed with p
-// sparse passes L t = t - S t (S = D^-1/2 W D^-1/2 rebuilt from the degree
-// vector), the last one fused with the mask term and the <p, A p> partials.
+// (one independent CG per column; per-column inner products summed in
+// compensated fp32 per thread and in fp64 across threads and blocks, in a
+// fixed order).  A p = mask * p + gamma L^p p is computed with p sparse
+// passes, the last one fused with the mask term and the <p, A p> partials.
+// The products by L run in the pre-scaled form v = D^-1/2 t, so only the
+// first of them loads per-edge weights (see lap_kernel).
 // Preconditioner: diag(M^T M) + gamma (diag(L) = 1).
 // Labels: node i -> argmax_j x_j(i) / ||x_j|| (ties to the lowest j).
+//
+// Launch shape (every kernel of one solve): CTA x sweeps the contiguous row
+// range [part[x], part[x+1]) with G lanes per row; CTA y covers the column tile
+// [y*TW, (y+1)*TW), TW = 4*G*NT.  The shape is tuned once per graph and k.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -18,175 +25,190 @@
 
 namespace csc {
 
-constexpr int kCgThreads = 256;
+constexpr int kCgMaxThreads = 512;
 
-// Per-block, per-column fp64 partial sums: every thread holds sums for its
-// NT*4 columns; threads of equal lane across the block's groups are summed
-// in group order, then written to partials[block * ld + col].
+// Compensated (Kahan) fp32 accumulation: per-thread column sums stay in fp32
+// registers (fp64 arithmetic is scarce on this part) with a running error term.
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Per-block, per-column fp64 partial sums of NS quantities: threads of equal lane
+// across the block's row groups are summed in group order and written to
+// partials[(q * gridDim.x + blockIdx.x) * ldp + col0 + c].
 template <int G, int NT, int NS>
-__device__ __forceinline__ void block_column_partials(double (&acc)[NS][NT][4], int lane, int ncols, int64_t ldp,
-                                                      double* __restrict__ partials) {
-    constexpr int GROUPS = kCgThreads / G;
+__device__ __forceinline__ void block_column_partials(KSum (&acc)[NS][NT][4], int lane, int col0, int tcols,
+                                                      int64_t ldp, double* __restrict__ partials) {
+    constexpr int MAXGROUPS = kCgMaxThreads / G;
     constexpr int COLS = G * NT * 4;
-    __shared__ double red[GROUPS * COLS];
+    __shared__ double red[MAXGROUPS * COLS];
+    const int groups = blockDim.x / G;
     const int grp = threadIdx.x / G;
-    for (int s = 0; s < NS; ++s) {
+    for (int q = 0; q < NS; ++q) {
         __syncthreads();
 #pragma unroll
         for (int t = 0; t < NT; ++t)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) red[grp * COLS + (t * G + lane) * 4 + v] = acc[s][t][v];
+            for (int v = 0; v < 4; ++v) red[grp * COLS + (t * G + lane) * 4 + v] = acc[q][t][v].value();
         __syncthreads();
-        for (int c = threadIdx.x; c < COLS && c < ncols; c += kCgThreads) {
+        for (int c = threadIdx.x; c < COLS && c < tcols; c += blockDim.x) {
             double sum = 0.0;
-            for (int q = 0; q < GROUPS; ++q) sum += red[q * COLS + c];
-            partials[((int64_t)s * gridDim.x + blockIdx.x) * ldp + c] = sum;
+            for (int i = 0; i < groups; ++i) sum += red[i * COLS + c];
+            partials[((int64_t)q * gridDim.x + blockIdx.x) * ldp + col0 + c] = sum;
         }
     }
 }
 
-// out = in - S in   (L applied to every column)
-template <int G, int NT>
-__global__ void __launch_bounds__(kCgThreads)
+#define CG_TILE(G, NT)                                   \
+    const int lane = threadIdx.x % (G);                  \
+    const int col0 = blockIdx.y * ((G) * (NT) * 4);      \
+    const int tcols = min((G) * (NT) * 4, ncols - col0); \
+    const int r1 = part[blockIdx.x + 1];
+#define CG_ROWS(G) \
+    for (int row = part[blockIdx.x] + (int)(threadIdx.x / (G)); row < r1; row += (int)(blockDim.x / (G)))
+
+// The L-chain in pre-scaled form v = s t (s = D^-1/2, 1 for isolated nodes):
+//   WIN (first product, unscaled input p):  v = s (p - D^-1/2 W D^-1/2 p)
+//   !WIN (middle products, scaled input v): v' = v - D^-1 W v
+// so only the first product loads per-edge weights.
+template <int G, int NT, bool WIN>
+__global__ void __launch_bounds__(kCgMaxThreads)
 lap_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ dinv,
-           const float* __restrict__ in, float* __restrict__ out, int32_t N, int ncols, int64_t ld) {
-    const int lane = threadIdx.x % G;
-    const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
-    for (int64_t r = group; r < N; r += ngroups) {
-        const int row = (int)r;
+           const float* __restrict__ invdeg, const float* __restrict__ in, float* __restrict__ out,
+           const int32_t* __restrict__ part, int ncols, int64_t ld) {
+    CG_TILE(G, NT)
+    CG_ROWS(G) {
         float acc[NT][4];
-        gather_row<float, G, NT>(rp, ci, dinv, in, ld, row, lane, ncols, acc);
+        gather_row<float, G, NT, WIN, float>(rp, ci, dinv, in + col0, ld, row, lane, tcols, acc);
         const float di = dinv[row];
+        const float sc = di > 0.f ? di : 1.f;
+        const float f = WIN ? di : invdeg[row];
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            const int c = (t * G + lane) * 4;
-            if (c >= ncols) continue;
+            const int cl = (t * G + lane) * 4;
+            if (cl >= tcols) continue;
+            const int64_t o = (int64_t)row * ld + col0 + cl;
             float x[4];
-            StoreTraits<float>::load(in + (int64_t)row * ld + c, x);
+            StoreTraits<float>::load(in + o, x);
 #pragma unroll
-            for (int v = 0; v < 4; ++v) x[v] = x[v] - di * acc[t][v];
-            StoreTraits<float>::store(out + (int64_t)row * ld + c, x);
+            for (int v = 0; v < 4; ++v) x[v] = WIN ? sc * (x[v] - f * acc[t][v]) : x[v] - f * acc[t][v];
+            StoreTraits<float>::store(out + o, x);
         }
     }
 }
 
-// Ap = mask * p + gamma (t - S t), with per-column partials of <p, Ap>.
-template <int G, int NT>
-__global__ void __launch_bounds__(kCgThreads)
+// Ap = mask * p + gamma L t with per-column partials of <p, Ap>; the last product of
+// the chain.  WIN: t = p itself (g(L) = L); else tin = s t from the chain.
+template <int G, int NT, bool WIN>
+__global__ void __launch_bounds__(kCgMaxThreads)
 lap_ax_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ dinv,
-              const float* __restrict__ tin, const float* __restrict__ p, const float* __restrict__ mask, float gamma,
-              float* __restrict__ Ap, int32_t N, int ncols, int64_t ld, double* __restrict__ partials) {
-    const int lane = threadIdx.x % G;
-    const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
-    double dot[1][NT][4];
-#pragma unroll
-    for (int t = 0; t < NT; ++t)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) dot[0][t][v] = 0.0;
-    for (int64_t r = group; r < N; r += ngroups) {
-        const int row = (int)r;
+              const float* __restrict__ sqdeg, const float* __restrict__ tin, const float* __restrict__ p,
+              const float* __restrict__ mask, float gamma, float* __restrict__ Ap, const int32_t* __restrict__ part,
+              int ncols, int64_t ld, double* __restrict__ partials) {
+    CG_TILE(G, NT)
+    KSum dot[1][NT][4];
+    CG_ROWS(G) {
         float acc[NT][4];
-        gather_row<float, G, NT>(rp, ci, dinv, tin, ld, row, lane, ncols, acc);
+        gather_row<float, G, NT, WIN, float>(rp, ci, dinv, tin + col0, ld, row, lane, tcols, acc);
         const float di = dinv[row];
+        const float back = WIN ? 1.f : sqdeg[row];
         const float mk = mask[row];
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            const int c = (t * G + lane) * 4;
-            if (c >= ncols) continue;
+            const int cl = (t * G + lane) * 4;
+            if (cl >= tcols) continue;
+            const int64_t o = (int64_t)row * ld + col0 + cl;
             float tt[4], pp[4], a[4];
-            StoreTraits<float>::load(tin + (int64_t)row * ld + c, tt);
-            StoreTraits<float>::load(p + (int64_t)row * ld + c, pp);
+            StoreTraits<float>::load(tin + o, tt);
+            StoreTraits<float>::load(p + o, pp);
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                a[v] = mk * pp[v] + gamma * (tt[v] - di * acc[t][v]);
-                dot[0][t][v] += (double)pp[v] * (double)a[v];
+                a[v] = mk * pp[v] + gamma * (tt[v] * back - di * acc[t][v]);
+                dot[0][t][v].add(pp[v] * a[v]);
             }
-            StoreTraits<float>::store(Ap + (int64_t)row * ld + c, a);
+            StoreTraits<float>::store(Ap + o, a);
         }
     }
-    block_column_partials<G, NT, 1>(dot, lane, ncols, ld, partials);
+    block_column_partials<G, NT, 1>(dot, lane, col0, tcols, ld, partials);
 }
 
 // x += alpha p; r -= alpha Ap; partials of <r, r/P> and <r, r>.  alpha == nullptr: no update.
 template <int G, int NT>
-__global__ void __launch_bounds__(kCgThreads)
+__global__ void __launch_bounds__(kCgMaxThreads)
 cg_update_kernel(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ p,
                  const float* __restrict__ Ap, const double* __restrict__ alpha, const float* __restrict__ pinv,
-                 int32_t N, int ncols, int64_t ld, double* __restrict__ partials) {
-    const int lane = threadIdx.x % G;
-    const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
-    double dots[2][NT][4];
+                 const int32_t* __restrict__ part, int ncols, int64_t ld, double* __restrict__ partials) {
+    CG_TILE(G, NT)
+    KSum dots[2][NT][4];
     float al[NT][4];
 #pragma unroll
     for (int t = 0; t < NT; ++t)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            dots[0][t][v] = 0.0;
-            dots[1][t][v] = 0.0;
             const int c = (t * G + lane) * 4 + v;
-            al[t][v] = (alpha && c < ncols) ? (float)alpha[c] : 0.f;
+            al[t][v] = (alpha && c < tcols) ? (float)alpha[col0 + c] : 0.f;
         }
-    for (int64_t rr = group; rr < N; rr += ngroups) {
-        const int row = (int)rr;
+    CG_ROWS(G) {
         const float pi = pinv[row];
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            const int c = (t * G + lane) * 4;
-            if (c >= ncols) continue;
-            const int64_t o = (int64_t)row * ld + c;
+            const int cl = (t * G + lane) * 4;
+            if (cl >= tcols) continue;
+            const int64_t o = (int64_t)row * ld + col0 + cl;
             float rv[4];
             StoreTraits<float>::load(r + o, rv);
             if (alpha) {
                 float xv[4], pv[4], av[4];
-                StoreTraits<float>::load(x + o, xv);
+                StoreTraits<float>::load_cs(x + o, xv);
                 StoreTraits<float>::load(p + o, pv);
-                StoreTraits<float>::load(Ap + o, av);
+                StoreTraits<float>::load_cs(Ap + o, av);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
                     xv[v] = fmaf(al[t][v], pv[v], xv[v]);
                     rv[v] = fmaf(-al[t][v], av[v], rv[v]);
                 }
-                StoreTraits<float>::store(x + o, xv);
+                // x is not read again until the next update: evict-first
+                StoreTraits<float>::store_cs(x + o, xv);
                 StoreTraits<float>::store(r + o, rv);
             }
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                const double rd = (double)rv[v];
-                dots[0][t][v] += rd * (double)(rv[v] * pi);
-                dots[1][t][v] += rd * rd;
+                dots[0][t][v].add(rv[v] * (rv[v] * pi));
+                dots[1][t][v].add(rv[v] * rv[v]);
             }
         }
     }
-    block_column_partials<G, NT, 2>(dots, lane, ncols, ld, partials);
+    block_column_partials<G, NT, 2>(dots, lane, col0, tcols, ld, partials);
 }
 
 // p = r/P + beta p
 template <int G, int NT>
-__global__ void __launch_bounds__(kCgThreads)
+__global__ void __launch_bounds__(kCgMaxThreads)
 cg_pupdate_kernel(const float* __restrict__ r, float* __restrict__ p, const double* __restrict__ beta,
-                  const float* __restrict__ pinv, int32_t N, int ncols, int64_t ld) {
-    const int lane = threadIdx.x % G;
-    const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+                  const float* __restrict__ pinv, const int32_t* __restrict__ part, int ncols, int64_t ld) {
+    CG_TILE(G, NT)
     float be[NT][4];
 #pragma unroll
     for (int t = 0; t < NT; ++t)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int c = (t * G + lane) * 4 + v;
-            be[t][v] = c < ncols ? (float)beta[c] : 0.f;
+            be[t][v] = c < tcols ? (float)beta[col0 + c] : 0.f;
         }
-    for (int64_t rr = group; rr < N; rr += ngroups) {
-        const int row = (int)rr;
+    CG_ROWS(G) {
         const float pi = pinv[row];
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            const int c = (t * G + lane) * 4;
-            if (c >= ncols) continue;
-            const int64_t o = (int64_t)row * ld + c;
+            const int cl = (t * G + lane) * 4;
+            if (cl >= tcols) continue;
+            const int64_t o = (int64_t)row * ld + col0 + cl;
             float rv[4], pv[4];
             StoreTraits<float>::load(r + o, rv);
             StoreTraits<float>::load(p + o, pv);
@@ -195,6 +217,53 @@ cg_pupdate_kernel(const float* __restrict__ r, float* __restrict__ p, const doub
             StoreTraits<float>::store(p + o, pv);
         }
     }
+}
+
+// ||b - A x||^2 per column, b rebuilt from the sample labels: partials
+template <int G, int NT>
+__global__ void __launch_bounds__(kCgMaxThreads)
+residual_kernel(const float* __restrict__ Ax, const int32_t* __restrict__ slab, const int32_t* __restrict__ part,
+                int ncols, int64_t ld, double* __restrict__ partials) {
+    CG_TILE(G, NT)
+    KSum acc[1][NT][4];
+    CG_ROWS(G) {
+        const int lab = slab[row];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int cl = (t * G + lane) * 4;
+            if (cl >= tcols) continue;
+            const int c = col0 + cl;
+            float a[4];
+            StoreTraits<float>::load(Ax + (int64_t)row * ld + c, a);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float e = (c + v == lab ? 1.0f : 0.0f) - a[v];
+                acc[0][t][v].add(e * e);
+            }
+        }
+    }
+    block_column_partials<G, NT, 1>(acc, lane, col0, tcols, ld, partials);
+}
+
+// column norms^2 of x (partials)
+template <int G, int NT>
+__global__ void __launch_bounds__(kCgMaxThreads)
+colnorm_kernel(const float* __restrict__ x, const int32_t* __restrict__ part, int ncols, int64_t ld,
+               double* __restrict__ partials) {
+    CG_TILE(G, NT)
+    KSum acc[1][NT][4];
+    CG_ROWS(G) {
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int cl = (t * G + lane) * 4;
+            if (cl >= tcols) continue;
+            float a[4];
+            StoreTraits<float>::load(x + (int64_t)row * ld + col0 + cl, a);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[0][t][v].add(a[v] * a[v]);
+        }
+    }
+    block_column_partials<G, NT, 1>(acc, lane, col0, tcols, ld, partials);
 }
 
 // Column state (fp64, length k each): rz, bnorm2, alpha, beta, active flags.
@@ -208,23 +277,49 @@ struct CgState {
     int* n_active;
 };
 
+// Column sums of block partials in a fixed order: a 32 x 16 thread block covers
+// 32 columns; thread row y sums blocks y, y+16, ... (coalesced across columns),
+// then the 16 row sums are added in order.
+template <int NS>
+__device__ __forceinline__ void reduce_columns(const double* __restrict__ partials, int nblocks, int64_t ldp, int j,
+                                               double (&out)[NS]) {
+    __shared__ double red[NS][16][33];
+    const int x = threadIdx.x, y = threadIdx.y;
+    double s[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) s[q] = 0.0;
+    for (int b = y; b < nblocks; b += 16)
+#pragma unroll
+        for (int q = 0; q < NS; ++q) s[q] += partials[((int64_t)q * nblocks + b) * ldp + j];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) red[q][y][x] = s[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+        double t = 0.0;
+        for (int i = 0; i < 16; ++i) t += red[q][i][x];
+        out[q] = t;
+    }
+}
+
 // pAp_j = sum of partials; alpha_j = rz_j / pAp_j for active columns.
-__global__ void cg_alpha_kernel(const double* __restrict__ partials, int nblocks, int k, int64_t ldp, CgState st) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= k) return;
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * ldp + j];
-    st.alpha[j] = (st.active[j] && s != 0.0) ? st.rz[j] / s : 0.0;
+__global__ void __launch_bounds__(512) cg_alpha_kernel(const double* __restrict__ partials, int nblocks, int k,
+                                                       int64_t ldp, CgState st) {
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    double s[1];
+    reduce_columns<1>(partials, nblocks, ldp, j < k ? j : 0, s);
+    if (threadIdx.y != 0 || j >= k) return;
+    st.alpha[j] = (st.active[j] && s[0] != 0.0) ? st.rz[j] / s[0] : 0.0;
 }
 
 // After an update: rz_new, rr; convergence; beta.  init != 0: first call (sets bn2, active).
-__global__ void cg_beta_kernel(const double* __restrict__ partials, int nblocks, int k, int64_t ldp, CgState st,
-                               double tol2, int init) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= k) return;
-    double rz = 0.0, rr = 0.0;
-    for (int b = 0; b < nblocks; ++b) rz += partials[(int64_t)b * ldp + j];
-    for (int b = 0; b < nblocks; ++b) rr += partials[((int64_t)nblocks + b) * ldp + j];
+__global__ void __launch_bounds__(512) cg_beta_kernel(const double* __restrict__ partials, int nblocks, int k,
+                                                      int64_t ldp, CgState st, double tol2, int init) {
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    double s2[2];
+    reduce_columns<2>(partials, nblocks, ldp, j < k ? j : 0, s2);
+    if (threadIdx.y != 0 || j >= k) return;
+    const double rz = s2[0], rr = s2[1];
     st.rr[j] = rr;
     if (init) {
         st.bn2[j] = rr;
@@ -241,6 +336,14 @@ __global__ void cg_beta_kernel(const double* __restrict__ partials, int nblocks,
     st.rz[j] = rz;
     st.active[j] = act;
     if (act) atomicAdd(st.n_active, 1);
+}
+
+__global__ void __launch_bounds__(512) column_sum_kernel(const double* __restrict__ partials, int nblocks, int k,
+                                                         int64_t ldp, double* __restrict__ out) {
+    const int j = blockIdx.x * 32 + threadIdx.x;
+    double s[1];
+    reduce_columns<1>(partials, nblocks, ldp, j < k ? j : 0, s);
+    if (threadIdx.y == 0 && j < k) out[j] = s[0];
 }
 
 __global__ void cg_setup_kernel(const int64_t* __restrict__ sample_idx, const int32_t* __restrict__ sample_labels,
@@ -264,74 +367,6 @@ __global__ void cg_setup_kernel(const int64_t* __restrict__ sample_idx, const in
 __global__ void precond_kernel(const float* __restrict__ mask, float gamma, float* __restrict__ pinv, int32_t N) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) pinv[i] = 1.0f / (mask[i] + gamma);
-}
-
-// ||b - A x||^2 per column, b rebuilt from the sample labels: partials
-template <int G, int NT>
-__global__ void __launch_bounds__(kCgThreads)
-residual_kernel(const float* __restrict__ Ax, const int32_t* __restrict__ slab, int32_t N, int ncols, int64_t ld,
-                double* __restrict__ partials) {
-    const int lane = threadIdx.x % G;
-    const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
-    double acc[1][NT][4];
-#pragma unroll
-    for (int t = 0; t < NT; ++t)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[0][t][v] = 0.0;
-    for (int64_t rr = group; rr < N; rr += ngroups) {
-        const int row = (int)rr;
-        const int lab = slab[row];
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const int c = (t * G + lane) * 4;
-            if (c >= ncols) continue;
-            float a[4];
-            StoreTraits<float>::load(Ax + (int64_t)row * ld + c, a);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const double e = (c + v == lab ? 1.0 : 0.0) - (double)a[v];
-                acc[0][t][v] += e * e;
-            }
-        }
-    }
-    block_column_partials<G, NT, 1>(acc, lane, ncols, ld, partials);
-}
-
-__global__ void column_sum_kernel(const double* __restrict__ partials, int nblocks, int k, int64_t ldp,
-                                  double* __restrict__ out) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= k) return;
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += partials[(int64_t)b * ldp + j];
-    out[j] = s;
-}
-
-// column norms^2 of x (partials) -- reuse residual-free layout
-template <int G, int NT>
-__global__ void __launch_bounds__(kCgThreads)
-colnorm_kernel(const float* __restrict__ x, int32_t N, int ncols, int64_t ld, double* __restrict__ partials) {
-    const int lane = threadIdx.x % G;
-    const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
-    double acc[1][NT][4];
-#pragma unroll
-    for (int t = 0; t < NT; ++t)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[0][t][v] = 0.0;
-    for (int64_t rr = group; rr < N; rr += ngroups) {
-        const int row = (int)rr;
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const int c = (t * G + lane) * 4;
-            if (c >= ncols) continue;
-            float a[4];
-            StoreTraits<float>::load(x + (int64_t)row * ld + c, a);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[0][t][v] += (double)a[v] * (double)a[v];
-        }
-    }
-    block_column_partials<G, NT, 1>(acc, lane, ncols, ld, partials);
 }
 
 // label(i) = argmax_j x_ij / ||x_j|| (fp64 comparison, ties to the lowest j); one thread per row.
@@ -358,41 +393,88 @@ __global__ void label_argmax_kernel(const float* __restrict__ x, const double* _
 }
 
 // ------------------------------------------------------------- dispatch
-struct Shape {
-    int G, NT;
-};
-static Shape cg_shape(int nv) {
-    static const Shape s[] = {{2, 1}, {4, 1}, {8, 1}, {16, 1}, {32, 1}, {32, 2}};
-    for (const Shape& x : s)
-        if (x.G * x.NT >= nv) return x;
-    return {0, 0};
+static const int kCgShapes[][2] = {{2, 1}, {4, 1}, {8, 1}, {16, 1}, {32, 1}, {32, 2}};
+static const int kCgThreadChoices[] = {256, 512};
+
+#define CG_SWITCH(cfg, ...)                                                                        \
+    do {                                                                                           \
+        switch ((cfg).G * 8 + (cfg).NT) {                                                          \
+            case 2 * 8 + 1: { constexpr int G_ = 2, NT_ = 1; __VA_ARGS__; } break;                 \
+            case 4 * 8 + 1: { constexpr int G_ = 4, NT_ = 1; __VA_ARGS__; } break;                 \
+            case 8 * 8 + 1: { constexpr int G_ = 8, NT_ = 1; __VA_ARGS__; } break;                 \
+            case 16 * 8 + 1: { constexpr int G_ = 16, NT_ = 1; __VA_ARGS__; } break;               \
+            case 32 * 8 + 1: { constexpr int G_ = 32, NT_ = 1; __VA_ARGS__; } break;               \
+            case 32 * 8 + 2: { constexpr int G_ = 32, NT_ = 2; __VA_ARGS__; } break;               \
+            default:                                                                               \
+                set_error("no compiled CG shape G=%d NT=%d", (cfg).G, (cfg).NT);                   \
+                return CSC_E_UNSUPPORTED;                                                          \
+        }                                                                                          \
+    } while (0)
+
+template <int G, int NT>
+static int cg_occupancy_of(int threads) {
+    // the solve's most register-hungry kernel bounds the residency of all of them
+    int a = 1, b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, lap_kernel<G, NT, false>, threads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cg_update_kernel<G, NT>, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    const int n = std::min(a, b);
+    return n < 1 ? 1 : n;
 }
 
-#define CG_DISPATCH(SH, ...)                                                            \
-    do {                                                                                \
-        if (SH.G == 2 && SH.NT == 1) { constexpr int G_ = 2, NT_ = 1; __VA_ARGS__; }          \
-        else if (SH.G == 4) { constexpr int G_ = 4, NT_ = 1; __VA_ARGS__; }                   \
-        else if (SH.G == 8) { constexpr int G_ = 8, NT_ = 1; __VA_ARGS__; }                   \
-        else if (SH.G == 16) { constexpr int G_ = 16, NT_ = 1; __VA_ARGS__; }                 \
-        else if (SH.G == 32 && SH.NT == 1) { constexpr int G_ = 32, NT_ = 1; __VA_ARGS__; }   \
-        else { constexpr int G_ = 32, NT_ = 2; __VA_ARGS__; }                                 \
-    } while (0)
+static csc_status cg_occupancy(const LaunchCfg& c, int* out) {
+    CG_SWITCH(c, *out = cg_occupancy_of<G_, NT_>(c.threads));
+    return CSC_OK;
+}
 
 csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* sample_labels, int64_t n, int k,
                            int g_power, double gamma, double rel_tol, int max_iter, int32_t* labels_out,
                            float* fuzzy_out, csc_cg_info* info, cudaStream_t s) {
     const int32_t N = (int32_t)g->N;
-    // process columns in chunks of at most 256 (the widest compiled shape)
-    if (k > 256) {
-        set_error("csc_interpolate: k <= 256 in this build");
+    const int ld = ((k + 3) / 4) * 4;
+    const int nv = ld / 4;
+    // candidate shapes: column tiles of 4*G*NT floats with at most a third idle
+    std::vector<LaunchCfg> cands;
+    int max_p = 1;
+    int min_waste = 1 << 30;  // narrow blocks (k <= 4) keep the least-waste shapes
+    for (const auto& sh : kCgShapes) {
+        const int cap = sh[0] * sh[1];
+        const int tiles = (nv + cap - 1) / cap;
+        if (tiles <= 64) min_waste = std::min(min_waste, tiles * cap - nv);
+    }
+    for (const auto& sh : kCgShapes) {
+        const int cap = sh[0] * sh[1];
+        const int tiles = (nv + cap - 1) / cap;
+        const int waste = tiles * cap - nv;
+        if (tiles > 64 || (3 * waste > tiles * cap && waste > min_waste)) continue;
+        for (int th : kCgThreadChoices) {
+            LaunchCfg c;
+            c.G = sh[0];
+            c.NT = sh[1];
+            c.threads = th;
+            c.tiles = tiles;
+            int occ = 1;
+            CSC_TRY(cg_occupancy(c, &occ));
+            const int64_t lim = (N + (th / c.G) - 1) / (th / c.G);
+            // one to eight waves of resident CTAs (shorter row ranges balance uneven SMs)
+            for (int waves = 1; waves <= 8; waves *= 2) {
+                int P = (g->num_sms * occ * waves + tiles - 1) / tiles;
+                if (P > lim) P = (int)lim;
+                c.P = P < 1 ? 1 : P;
+                if (!cands.empty() && cands.back().G == c.G && cands.back().NT == c.NT &&
+                    cands.back().threads == th && cands.back().P == c.P)
+                    continue;
+                max_p = std::max(max_p, c.P);
+                cands.push_back(c);
+            }
+        }
+    }
+    if (cands.empty()) {
+        set_error("csc_interpolate: no launch shape for k = %d", k);
         return CSC_E_UNSUPPORTED;
     }
-    const int ld = ((k + 3) / 4) * 4;
-    const Shape sh = cg_shape(ld / 4);
-    const int64_t rows_per_block = kCgThreads / sh.G;
-    int grid = (int)((N + rows_per_block - 1) / rows_per_block);
-    if (grid > g->num_sms * 8) grid = g->num_sms * 8;
-    if (grid < 1) grid = 1;
     const size_t blk = (size_t)N * ld * sizeof(float);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -403,7 +485,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const size_t o_x = take(blk), o_r = take(blk), o_p = take(blk), o_ap = take(blk), o_t1 = take(blk),
                  o_t2 = take(blk);
     const size_t o_mask = take((size_t)N * 4), o_pinv = take((size_t)N * 4), o_slab = take((size_t)N * 4);
-    const size_t o_part = take((size_t)2 * grid * ld * 8);
+    const size_t o_part = take((size_t)2 * max_p * ld * 8);
     const size_t o_state = take((size_t)ld * 8 * 6 + (size_t)ld * 4 + 64);
     void* base = nullptr;
     CSC_TRY(ws_get(g, WS_CG, off, &base));
@@ -436,21 +518,68 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     CSC_CUDA_TRY(cudaMemsetAsync(mask, 0, (size_t)N * 4, s));
     CSC_CUDA_TRY(cudaMemsetAsync(slab, 0xff, (size_t)N * 4, s));
     CSC_CUDA_TRY(cudaMemsetAsync(st.n_active, 0, 2 * sizeof(int), s));
-    // algorithmic bytes per launch of each CG kernel (fp32 N x ld blocks)
-    const double blkb = (double)N * ld * 4.0;
-    const double csr_b = 4.0 * g->nnz + 4.0 * (N + 1) + 4.0 * N;
-    const double scal_b = 8.0 * grid * ld;
-    CSC_KLAUNCH("cg_setup", 12.0 * n + 12.0 * n, s,
+    CSC_KLAUNCH("cg_setup", 24.0 * n, s,
                 cg_setup_kernel<<<ceil_div(n, 256), 256, 0, s>>>(sample_idx, sample_labels, n, (int64_t)N, g->iperm,
                                                                  r, mask, slab, ld, k, bad));
     CSC_KLAUNCH("cg_setup", 8.0 * N, s, precond_kernel<<<ceil_div(N, 256), 256, 0, s>>>(mask, (float)gamma, pinv, N));
-    const int kb = ceil_div(k, 128);
-    CG_DISPATCH(sh, CSC_KLAUNCH("cg_update", blkb + 4.0 * N, s,
-                                cg_update_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(x, r, p, Ap, nullptr, pinv, N, ld,
-                                                                                      ld, part)));
-    CSC_KLAUNCH("cg_scalar", 2 * scal_b, s, cg_beta_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, st, rel_tol * rel_tol, 1));
-    CG_DISPATCH(sh, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
-                                cg_pupdate_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(r, p, st.beta, pinv, N, ld, ld)));
+
+    // launch shape: tuned on the middle product of the chain (the dominant kernel),
+    // reading r and writing scratch; shared by every kernel of the solve
+    LaunchCfg cfg;
+    {
+        const uint64_t key = (3ull << 48) | (uint64_t)(uint32_t)ld;
+        auto it = g->tuned.find(key);
+        if (it != g->tuned.end()) {
+            cfg = it->second;
+        } else if (tune_cache_get(g, key, &cfg)) {
+            g->tuned[key] = cfg;
+        } else {
+            const bool prof = g_prof_enabled;
+            g_prof_enabled = false;  // tuning launches are not part of the measured work
+            float best_ms = 1e30f;
+            cfg = cands[0];
+            for (const LaunchCfg& c : cands) {
+                const int32_t* pr = nullptr;
+                CSC_TRY(get_partition(g, c.P, &pr));
+                const dim3 grid(c.P, c.tiles);
+                float ms = 0.f;
+                for (int rep = 0; rep < 4; ++rep) {
+                    if (rep == 1) cudaEventRecord(g->ev[0], s);
+                    CG_SWITCH(c, lap_kernel<G_, NT_, false><<<grid, c.threads, 0, s>>>(
+                                     g->row_ptr, g->col_idx, g->dinv, g->invdeg, r, t1, pr, ld, ld));
+                }
+                cudaEventRecord(g->ev[1], s);
+                CSC_CUDA_TRY(cudaEventSynchronize(g->ev[1]));
+                CSC_CUDA_TRY(cudaGetLastError());
+                cudaEventElapsedTime(&ms, g->ev[0], g->ev[1]);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    cfg = c;
+                }
+            }
+            g_prof_enabled = prof;
+            g->tuned[key] = cfg;
+            tune_cache_put(g, key, cfg);
+        }
+    }
+    const int32_t* rpart = nullptr;
+    CSC_TRY(get_partition(g, cfg.P, &rpart));
+    const dim3 grid(cfg.P, cfg.tiles);
+    const int th = cfg.threads;
+    const int P = cfg.P;
+
+    // algorithmic bytes per launch of each CG kernel (fp32 N x ld blocks)
+    const double blkb = (double)N * ld * 4.0;
+    const double csr_b = 4.0 * g->nnz + 4.0 * (N + 1) + 4.0 * N;
+    const double scal_b = 8.0 * P * ld;
+    const int kb = ceil_div(k, 32);
+    const dim3 rb(32, 16);
+    CG_SWITCH(cfg, CSC_KLAUNCH("cg_update", blkb + 4.0 * N, s,
+                               cg_update_kernel<G_, NT_><<<grid, th, 0, s>>>(x, r, p, Ap, nullptr, pinv, rpart, ld, ld,
+                                                                             part)));
+    CSC_KLAUNCH("cg_scalar", 2 * scal_b, s, cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, k, ld, st, rel_tol * rel_tol, 1));
+    CG_SWITCH(cfg, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
+                               cg_pupdate_kernel<G_, NT_><<<grid, th, 0, s>>>(r, p, st.beta, pinv, rpart, ld, ld)));
     int* h_active = (int*)g->pinned;
     CSC_CUDA_TRY(cudaMemcpyAsync(h_active, st.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CSC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -464,17 +593,28 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         float* bufs[2] = {t1, t2};
         for (int q = 0; q < g_power - 1; ++q) {
             float* o = bufs[q & 1];
-            // CSR + D^-1/2, the input block gathered once, the output block written
-            CG_DISPATCH(sh, CSC_KLAUNCH("cg_lap", csr_b + 2 * blkb, s,
-                                        lap_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(g->row_ptr, g->col_idx, g->dinv,
-                                                                                        cur, o, N, ld, ld)));
+            // CSR + row factors, the input block gathered once, the output block written
+            if (q == 0)
+                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", csr_b + 2 * blkb, s,
+                                           lap_kernel<G_, NT_, true><<<grid, th, 0, s>>>(
+                                               g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, rpart, ld, ld)));
+            else
+                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", csr_b + 2 * blkb, s,
+                                           lap_kernel<G_, NT_, false><<<grid, th, 0, s>>>(
+                                               g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, rpart, ld, ld)));
             cur = o;
         }
-        // CSR + D^-1/2 + mask, t gathered once, p read, Ap written
-        CG_DISPATCH(sh, CSC_KLAUNCH("cg_lap_ax", csr_b + 4.0 * N + 3 * blkb + scal_b, s,
-                                    lap_ax_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(g->row_ptr, g->col_idx, g->dinv,
-                                                                                       cur, in, mask, (float)gamma, Ap,
-                                                                                       N, ld, ld, part)));
+        // CSR + row factors + mask, t gathered once, p read, Ap written
+        if (g_power == 1)
+            CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", csr_b + 4.0 * N + 3 * blkb + scal_b, s,
+                                       lap_ax_kernel<G_, NT_, true><<<grid, th, 0, s>>>(
+                                           g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
+                                           rpart, ld, ld, part)));
+        else
+            CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", csr_b + 4.0 * N + 3 * blkb + scal_b, s,
+                                       lap_ax_kernel<G_, NT_, false><<<grid, th, 0, s>>>(
+                                           g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
+                                           rpart, ld, ld, part)));
         return CSC_OK;
     };
     int it = 0;
@@ -484,17 +624,17 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         const int batch = std::min(check_every, max_iter - it);
         for (int q = 0; q < batch; ++q) {
             CSC_TRY(apply_A(p));
-            CSC_KLAUNCH("cg_scalar", scal_b, s, cg_alpha_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, st));
+            CSC_KLAUNCH("cg_scalar", scal_b, s, cg_alpha_kernel<<<kb, rb, 0, s>>>(part, P, k, ld, st));
             // x, r, p, Ap read; x, r written
-            CG_DISPATCH(sh, CSC_KLAUNCH("cg_update", 6 * blkb + 4.0 * N + 2 * scal_b, s,
-                                        cg_update_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(x, r, p, Ap, st.alpha, pinv,
-                                                                                              N, ld, ld, part)));
+            CG_SWITCH(cfg, CSC_KLAUNCH("cg_update", 6 * blkb + 4.0 * N + 2 * scal_b, s,
+                                       cg_update_kernel<G_, NT_><<<grid, th, 0, s>>>(x, r, p, Ap, st.alpha, pinv, rpart,
+                                                                                     ld, ld, part)));
             CSC_CUDA_TRY(cudaMemsetAsync(st.n_active, 0, sizeof(int), s));
             CSC_KLAUNCH("cg_scalar", 2 * scal_b, s,
-                        cg_beta_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, st, rel_tol * rel_tol, 0));
-            CG_DISPATCH(sh, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
-                                        cg_pupdate_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(r, p, st.beta, pinv, N, ld,
-                                                                                               ld)));
+                        cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, k, ld, st, rel_tol * rel_tol, 0));
+            CG_SWITCH(cfg, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
+                                       cg_pupdate_kernel<G_, NT_><<<grid, th, 0, s>>>(r, p, st.beta, pinv, rpart, ld,
+                                                                                      ld)));
         }
         it += batch;
         CSC_CUDA_TRY(cudaMemcpyAsync(h_active, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -503,13 +643,13 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     }
     // true residual ||b - A x|| / ||b|| per column
     CSC_TRY(apply_A(x));
-    CG_DISPATCH(sh, CSC_KLAUNCH("cg_residual", blkb + 4.0 * N, s,
-                                residual_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(Ap, slab, N, ld, ld, part)));
-    CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, st.rr));
+    CG_SWITCH(cfg, CSC_KLAUNCH("cg_residual", blkb + 4.0 * N, s,
+                               residual_kernel<G_, NT_><<<grid, th, 0, s>>>(Ap, slab, rpart, ld, ld, part)));
+    CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, rb, 0, s>>>(part, P, k, ld, st.rr));
     // labels
-    CG_DISPATCH(sh, CSC_KLAUNCH("label_norms", blkb, s,
-                                colnorm_kernel<G_, NT_><<<grid, kCgThreads, 0, s>>>(x, N, ld, ld, part)));
-    CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, 128, 0, s>>>(part, grid, k, ld, norm2));
+    CG_SWITCH(cfg, CSC_KLAUNCH("label_norms", blkb, s,
+                               colnorm_kernel<G_, NT_><<<grid, th, 0, s>>>(x, rpart, ld, ld, part)));
+    CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, rb, 0, s>>>(part, P, k, ld, norm2));
     CSC_KLAUNCH("label_argmax", blkb + 4.0 * N + (fuzzy_out ? (double)N * k * 4 : 0.0), s,
                 label_argmax_kernel<<<ceil_div(N, 256), 256, 0, s>>>(x, norm2, N, k, ld, g->perm, labels_out,
                                                                      fuzzy_out));

@@ -9,6 +9,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -86,6 +87,13 @@ struct Buffer {
     size_t bytes = 0;
 };
 
+// Launch shape of a row-sweep SpMM kernel: G lanes per row, NT 16-byte vectors
+// per lane (a column tile of G*NT vectors), `threads` per CTA, P row ranges
+// (one CTA each per tile) and `tiles` column tiles.
+struct LaunchCfg {
+    int G = 0, NT = 0, threads = 0, P = 0, tiles = 1;
+};
+
 struct Graph {
     int64_t N = 0;        // nodes (packed total for batched graphs)
     int64_t nnz = 0;      // stored entries after self-loop removal
@@ -96,6 +104,12 @@ struct Graph {
     int32_t* col_idx = nullptr;  // device int32[nnz]
     float* dinv = nullptr;       // device float[N]: D^-1/2 (0 for isolated nodes)
     double* dinv64 = nullptr;    // device double[N]
+    // Row factors of the pre-scaled form Z = s X with s = D^-1/2 (1 for isolated
+    // nodes): invdeg = 1/deg (0 if isolated), sqdeg = 1/s = sqrt(deg) (1 if isolated)
+    float* invdeg = nullptr;
+    float* sqdeg = nullptr;
+    double* invdeg64 = nullptr;
+    double* sqdeg64 = nullptr;
     int32_t* deg = nullptr;      // device int32[N]
     int32_t* perm = nullptr;     // device int32[N]: internal row -> original id (nullptr: identity)
     int32_t* iperm = nullptr;    // device int32[N]: original id -> internal row
@@ -104,12 +118,23 @@ struct Graph {
     int64_t* d_offsets = nullptr;    // device copy
     int32_t* graph_of_row = nullptr; // device int32[N]
     Buffer ws[WS_COUNT];
+    std::vector<int32_t> h_row_ptr;               // host copy of row_ptr (internal order)
+    std::map<int, int32_t*> parts;                // P -> device int32[P+1] row-range bounds
+    std::map<uint64_t, LaunchCfg> tuned;          // (kernel kind, dtype, columns) -> shape
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     double* pinned = nullptr;  // small pinned host staging (4096 doubles)
     bool poisoned = false;
 };
 
 csc_status ws_get(Graph* g, WsSlot slot, size_t bytes, void** out);
+
+// Tuned launch shapes shared by all handles of the process, keyed by the tuning key,
+// device, N and nnz (graphs of the same size reuse a shape without re-tuning).
+bool tune_cache_get(const Graph* g, uint64_t key, LaunchCfg* out);
+void tune_cache_put(const Graph* g, uint64_t key, const LaunchCfg& cfg);
+
+// P contiguous row ranges of about equal cost (edges + 2 per row); cached per P.
+csc_status get_partition(Graph* g, int P, const int32_t** out);
 
 // Device helpers exported by the kernel translation units -----------------
 

@@ -37,6 +37,10 @@ struct StoreTraits<float> {
     __device__ static inline void store(float* p, const float (&v)[4]) {
         *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
     }
+    // streaming (evict-first) store: data not read again soon
+    __device__ static inline void store_cs(float* p, const float (&v)[4]) {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+    }
     __device__ static inline float round(float v) { return v; }
 };
 
@@ -68,6 +72,13 @@ struct StoreTraits<__nv_bfloat16> {
         for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
         *reinterpret_cast<uint4*>(p) = q;
     }
+    __device__ static inline void store_cs(__nv_bfloat16* p, const float (&v)[8]) {
+        uint4 q;
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&q);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        __stcs(reinterpret_cast<uint4*>(p), q);
+    }
     // the value the recurrence continues with is the stored (rounded) one
     __device__ static inline float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
@@ -86,6 +97,9 @@ struct StoreTraits<double> {
     }
     __device__ static inline void store(double* p, const double (&v)[2]) {
         *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    }
+    __device__ static inline void store_cs(double* p, const double (&v)[2]) {
+        __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
     }
     __device__ static inline double round(double v) { return v; }
 };
@@ -114,12 +128,56 @@ struct AccIO {
             StoreTraits<A>::store(p + q * PER, t);
         }
     }
+    __device__ static inline void store_cs(A* p, const A (&v)[VEC]) {
+#pragma unroll
+        for (int q = 0; q < VEC / PER; ++q) {
+            A t[PER];
+#pragma unroll
+            for (int i = 0; i < PER; ++i) t[i] = v[q * PER + i];
+            StoreTraits<A>::store_cs(p + q * PER, t);
+        }
+    }
 };
 
-// Neighbour sum of one row: acc[t][v] = sum_{e in row} w[col[e]] * X[col[e], c(t, v)]
-// with c(t, v) = (t * G + lane) * VEC + v.  Columns >= ncols are skipped
-// (their accumulators stay 0).  W is float or double.
-template <typename T, int G, int NT, typename W>
+// Packed fp32 pair arithmetic (add.rn.f32x2 / fma.rn.f32x2, one instruction for
+// two lanes' worth of values): halves the floating-point instructions of the gather.
+__device__ __forceinline__ void add_f32x2(float& a0, float& a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 ra, rb;\n\tmov.b64 ra, {%0, %1};\n\tmov.b64 rb, {%2, %3};\n\t"
+        "add.rn.f32x2 ra, ra, rb;\n\tmov.b64 {%0, %1}, ra;\n\t}"
+        : "+f"(a0), "+f"(a1)
+        : "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void fma_f32x2(float& a0, float& a1, float w, float b0, float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rw;\n\tmov.b64 ra, {%0, %1};\n\tmov.b64 rb, {%2, %3};\n\t"
+        "mov.b64 rw, {%4, %4};\n\tfma.rn.f32x2 ra, rw, rb, ra;\n\tmov.b64 {%0, %1}, ra;\n\t}"
+        : "+f"(a0), "+f"(a1)
+        : "f"(b0), "f"(b1), "f"(w));
+}
+
+// acc += w * x over one vector: packed pairs for fp32 accumulators, scalar fma for fp64.
+template <bool WEIGHTED, int VEC>
+__device__ __forceinline__ void acc_vec(float (&acc)[VEC], float w, const float (&x)[VEC]) {
+#pragma unroll
+    for (int v = 0; v < VEC; v += 2) {
+        if (WEIGHTED) fma_f32x2(acc[v], acc[v + 1], w, x[v], x[v + 1]);
+        else add_f32x2(acc[v], acc[v + 1], x[v], x[v + 1]);
+    }
+}
+template <bool WEIGHTED, int VEC>
+__device__ __forceinline__ void acc_vec(double (&acc)[VEC], double w, const double (&x)[VEC]) {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = WEIGHTED ? fma(w, x[v], acc[v]) : acc[v] + x[v];
+}
+
+// Neighbour sum of one row: acc[t][v] = sum_{e in row} w_e * X[col[e], c(t, v)] with
+// c(t, v) = (t * G + lane) * VEC + v, where w_e = wv[col[e]] if WEIGHTED, else 1
+// (the pre-scaled operand form, whose weights are folded into the rows of X).
+// The G lanes of a group load a chunk of the row's column indices (and
+// weights) with one coalesced access each, then broadcast them by shuffles
+// within the group, so the neighbour-row loads of a chunk issue back to back
+// without a dependent index load in front of each.  Columns >= ncols are
+// skipped (their accumulators stay 0).
+template <typename T, int G, int NT, bool WEIGHTED, typename W>
 __device__ __forceinline__ void gather_row(const int32_t* __restrict__ rp,
                                            const int32_t* __restrict__ ci,
                                            const W* __restrict__ wv, const T* __restrict__ X,
@@ -128,6 +186,10 @@ __device__ __forceinline__ void gather_row(const int32_t* __restrict__ rp,
     using Tr = StoreTraits<T>;
     using A = typename Tr::acc_t;
     constexpr int VEC = Tr::VEC;
+    constexpr int J = G >= 16 ? 1 : 16 / G;  // index registers per lane
+    constexpr int CH = G * J;                // edges per chunk
+    const unsigned gmask =
+        G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(unsigned)(G - 1)));
 #pragma unroll
     for (int t = 0; t < NT; ++t)
 #pragma unroll
@@ -137,38 +199,47 @@ __device__ __forceinline__ void gather_row(const int32_t* __restrict__ rp,
     for (int t = 0; t < NT; ++t) valid[t] = ((t * G + lane) * VEC) < ncols;
     int e = __ldg(rp + row);
     const int end = __ldg(rp + row + 1);
-    // 4 edges in flight per lane: indices and weights first, then the row vectors
-    for (; e + 4 <= end; e += 4) {
-        int l[4];
-        A w[4];
+    for (; e < end; e += CH) {
+        int li[J];
+        A wi[J];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) l[u] = __ldg(ci + e + u);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) w[u] = A(__ldg(wv + l[u]));
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            if (!valid[t]) continue;
-            const int64_t c = (int64_t)((t * G + lane) * VEC);
-            A x[4][VEC];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) Tr::load(X + (int64_t)l[u] * ld + c, x[u]);
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) acc[t][v] = fma(w[u], x[u][v], acc[t][v]);
+        for (int j = 0; j < J; ++j) {
+            const int idx = e + j * G + lane;
+            const bool ok = idx < end;
+            li[j] = ok ? __ldg(ci + idx) : 0;
+            if (WEIGHTED) wi[j] = ok ? A(__ldg(wv + li[j])) : A(0);
         }
-    }
-    for (; e < end; ++e) {
-        const int l0 = __ldg(ci + e);
-        const A w0 = A(__ldg(wv + l0));
+        const int cnt = min(CH, end - e);
 #pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            if (!valid[t]) continue;
-            const int64_t c = (int64_t)((t * G + lane) * VEC);
-            A x[VEC];
-            Tr::load(X + (int64_t)l0 * ld + c, x);
+        for (int q0 = 0; q0 < CH; q0 += 4) {
+            if (q0 >= cnt) break;
+            int l[4];
+            A w[4];
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[t][v] = fma(w0, x[v], acc[t][v]);
+            for (int u = 0; u < 4; ++u) {
+                const int q = q0 + u;
+                l[u] = __shfl_sync(gmask, li[q / G], q % G, G);
+                if (WEIGHTED) w[u] = __shfl_sync(gmask, wi[q / G], q % G, G);
+                else w[u] = A(1);
+            }
+            // one address per neighbour row; the tiles of a lane are fixed offsets from it
+            const T* rowp[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) rowp[u] = X + (int64_t)l[u] * ld + lane * VEC;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                if (!valid[t]) continue;
+                A x[4][VEC];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (q0 + u < cnt) Tr::load(rowp[u] + t * G * VEC, x[u]);
+                    else
+#pragma unroll
+                        for (int v = 0; v < VEC; ++v) x[u][v] = A(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc_vec<WEIGHTED, VEC>(acc[t], w[u], x[u]);
+            }
         }
     }
 }

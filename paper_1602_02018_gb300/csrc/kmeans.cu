@@ -1,23 +1,33 @@
 // kmeans.cu -- k-means on the reduced feature set (Alg. 2 step 6).
 //
-// One CTA per replicate (the paper runs 20 replicates, Sec. 5).  Seeding is
-// k-means++ with uniforms from Philox4x32-10 (key = (seed, "k-means"),
+// One thread-block cluster per replicate (the paper runs 20 replicates, Sec. 5):
+// the C CTAs of a cluster split the n points into contiguous slices; every CTA
+// keeps the whole k x d centre table in its shared memory, and CTA r owns the
+// clusters j with j % C == r.  Centre sums are exact 64-bit fixed-point
+// integers added with distributed-shared-memory atomics into the owner's
+// shared memory, so they do not depend on the order of the additions; owners
+// then write the new centres into every CTA of the cluster.
+//
+// Seeding is k-means++ with uniforms from Philox4x32-10 (key = (seed, "k-means"),
 // counter = (replicate, draw)): the first centre is point floor(u n), centre
 // t >= 1 the first point whose running sum of squared distances to the chosen
 // centres reaches u * total.  Lloyd iterations assign each point to its
-// nearest centre (ties to the lower index) and move each centre to the mean
-// of its points; an empty cluster (in increasing index) takes the point
-// farthest from its own centre, which moves to it.  Centre sums are exact
-// 64-bit fixed-point integers, so they do not depend on the order in which
-// threads add them.  The best replicate by inertia (ties to the first) wins.
+// nearest centre (ties to the lower index) and move each centre to the mean of
+// its points; an empty cluster (in increasing index) takes the point farthest
+// from its own centre, which moves to it.  The best replicate by inertia (ties
+// to the first) wins.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "common.cuh"
 #include "device.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace csc {
 
-constexpr int kKmThreads = 512;
+constexpr int kKmThreads = 256;
+constexpr int kKmLanesPerPoint = 8;  // lanes sharing one point in the assignment
 
 __device__ __forceinline__ float sqdist(const float* __restrict__ x, const float* __restrict__ c, int d) {
     float s = 0.f;
@@ -28,247 +38,333 @@ __device__ __forceinline__ float sqdist(const float* __restrict__ x, const float
     return s;
 }
 
-// block-wide reductions over kKmThreads threads
-__device__ double block_sum_d(double v, double* sh) {
-    v = warp_sum(v);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < kKmThreads / 32; ++i) t += sh[i];
-        sh[32] = t;
-    }
-    __syncthreads();
-    return sh[32];
-}
-
-// argmax of (value, -index): largest value, ties to the lowest index
-__device__ void block_argmax(float v, int idx, float* shv, int* shi, float* out_v, int* out_i) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ov = __shfl_xor_sync(0xffffffffu, v, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
-        if (ov > v || (ov == v && oi < idx)) {
-            v = ov;
-            idx = oi;
-        }
-    }
-    __syncthreads();
-    if (lane == 0) {
-        shv[w] = v;
-        shi[w] = idx;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float bv = shv[0];
-        int bi = shi[0];
-        for (int i = 1; i < kKmThreads / 32; ++i)
-            if (shv[i] > bv || (shv[i] == bv && shi[i] < bi)) {
-                bv = shv[i];
-                bi = shi[i];
-            }
-        *out_v = bv;
-        *out_i = bi;
-    }
-    __syncthreads();
-}
-
 __device__ __forceinline__ double km_uniform(uint64_t seed, uint32_t rep, uint32_t t) {
     const Philox4 r = philox4x32_10(rep, 0u, t, 0u, (uint32_t)seed, (uint32_t)(seed >> 32) ^ STREAM_KMEANS);
     return (double)philox_uniform(r.x[0]);
 }
 
-__global__ void __launch_bounds__(kKmThreads)
-kmeans_replicate_kernel(const float* __restrict__ X, int n, int d, int ld, int k, int max_iter, uint64_t seed,
-                        int32_t* __restrict__ labels_all, double* __restrict__ inertia_all,
-                        double* __restrict__ d2_all, unsigned long long* __restrict__ sums_all,
-                        int* __restrict__ counts_all, int32_t* __restrict__ newlab_all) {
-    extern __shared__ float C[];  // k x d centres
-    __shared__ double shd[40];
-    __shared__ float shv[32];
-    __shared__ int shi[32];
-    __shared__ int sh_pick;
-    __shared__ float sh_best;
-    __shared__ int sh_changed;
-    __shared__ double sh_scale;
-    const int rep = blockIdx.x;
-    double* d2 = d2_all + (int64_t)rep * n;
-    int32_t* lab = labels_all + (int64_t)rep * n;
-    int32_t* nlab = newlab_all + (int64_t)rep * n;
-    unsigned long long* sums = sums_all + (int64_t)rep * k * d;
-    int* counts = counts_all + (int64_t)rep * k;
-    const int T = threadIdx.x;
+// Per-CTA scalars; the other CTAs of the cluster read them through DSMEM.
+struct KmShared {
+    double part;                          // this CTA's share of a cluster-wide sum
+    double scan_w[kKmThreads / 32];
+    int pick;                             // chosen point (seeding / empty-cluster refill)
+    int changed;
+    float best_v;                         // this CTA's farthest point / local maximum
+    int best_i;
+    double scale;
+    float shv[kKmThreads / 32];
+    int shi[kKmThreads / 32];
+};
 
-    // fixed-point scale for exact centre sums: n * max|x| * scale < 2^62
+// Dynamic shared memory of one CTA.
+struct KmLayout {
+    size_t cen, sums, counts, empty, d2, lab, nlab, total;
+    static __host__ __device__ size_t al(size_t x) { return (x + 15) / 16 * 16; }
+    __host__ __device__ KmLayout(int k, int d, int own_k, int n_loc) {
+        cen = 0;
+        sums = al(cen + (size_t)k * d * 4);
+        counts = al(sums + (size_t)own_k * d * 8);
+        empty = al(counts + (size_t)own_k * 4);
+        d2 = al(empty + (size_t)k * 4);
+        lab = al(d2 + (size_t)n_loc * 8);
+        nlab = al(lab + (size_t)n_loc * 4);
+        total = al(nlab + (size_t)n_loc * 4);
+    }
+};
+
+// Block-wide exclusive scan of one double per thread (fixed order); the block
+// total goes to *tot.
+__device__ double km_block_scan(double v, double* warp_tot, double* tot) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        for (int i = 0; i < kKmThreads / 32; ++i) {
+            const double t = warp_tot[i];
+            warp_tot[i] = acc;
+            acc += t;
+        }
+        *tot = acc;
+    }
+    __syncthreads();
+    return warp_tot[w] + x - v;
+}
+
+__global__ void __launch_bounds__(kKmThreads)
+kmeans_cluster_kernel(const float* __restrict__ X, int n, int d, int ld, int k, int max_iter, uint64_t seed,
+                      int32_t* __restrict__ labels_all, double* __restrict__ inertia_all) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ KmShared S;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int rep = blockIdx.x / C;
+    const int T = threadIdx.x;
+    const int own_k = (k + C - 1) / C;
+    const int n_loc = (n + C - 1) / C;
+    const KmLayout L(k, d, own_k, n_loc);
+    float* Cen = (float*)(smem + L.cen);
+    unsigned long long* sums = (unsigned long long*)(smem + L.sums);
+    int* counts = (int*)(smem + L.counts);
+    int* empty = (int*)(smem + L.empty);
+    double* d2 = (double*)(smem + L.d2);
+    int* lab = (int*)(smem + L.lab);
+    int* nlab = (int*)(smem + L.nlab);
+    const int i0 = rank * n_loc;
+    const int cnt = max(0, min(n, i0 + n_loc) - i0);  // this CTA's points: i0 .. i0+cnt-1
+
+    // fixed-point scale for exact centre sums: n * max|x| * scale < 2^62 (cluster-wide max)
     {
         float mx = 0.f;
-        for (int64_t t = T; t < (int64_t)n * d; t += kKmThreads) mx = fmaxf(mx, fabsf(X[(t / d) * ld + t % d]));
+        for (int64_t t = T; t < (int64_t)cnt * d; t += kKmThreads)
+            mx = fmaxf(mx, fabsf(X[(int64_t)(i0 + t / d) * ld + t % d]));
         for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if ((T & 31) == 0) shv[T >> 5] = mx;
+        if ((T & 31) == 0) S.shv[T >> 5] = mx;
         __syncthreads();
         if (T == 0) {
             float m = 0.f;
-            for (int i = 0; i < kKmThreads / 32; ++i) m = fmaxf(m, shv[i]);
-            int e = 61 - (int)ceil(log2((double)n + 1.0)) - (m > 0.f ? (int)ceil(log2((double)m)) : 0);
-            sh_scale = ldexp(1.0, e > 1000 ? 1000 : e);
+            for (int i = 0; i < kKmThreads / 32; ++i) m = fmaxf(m, S.shv[i]);
+            S.best_v = m;
         }
-        __syncthreads();
-    }
-    const double scale = sh_scale;
-
-    // ---- k-means++ seeding
-    if (T == 0) {
-        const double u = km_uniform(seed, (uint32_t)rep, 0u);
-        int p = (int)(u * (double)n);
-        sh_pick = p < n - 1 ? p : n - 1;
-    }
-    __syncthreads();
-    for (int q = T; q < d; q += kKmThreads) C[q] = X[(int64_t)sh_pick * ld + q];
-    __syncthreads();
-    for (int i = T; i < n; i += kKmThreads) d2[i] = (double)sqdist(X + (int64_t)i * ld, C, d);
-    __syncthreads();
-    const int chunk = (n + kKmThreads - 1) / kKmThreads;
-    for (int t = 1; t < k; ++t) {
-        // per-thread contiguous chunk sums, exclusive scan across threads
-        const int i0 = T * chunk, i1 = min(n, i0 + chunk);
-        double part = 0.0;
-        for (int i = i0; i < i1; ++i) part += d2[i];
-        // exclusive scan of `part` over the block (fp64, fixed order)
-        __shared__ double scan_w[kKmThreads / 32];
-        double incl = part;
-        const int lane = T & 31, w = T >> 5;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const double y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) scan_w[w] = incl;
-        __syncthreads();
+        cluster.sync();
         if (T == 0) {
-            double acc = 0.0;
-            for (int i = 0; i < kKmThreads / 32; ++i) {
-                const double v = scan_w[i];
-                scan_w[i] = acc;
-                acc += v;
-            }
-            shd[33] = acc;  // total
-            sh_pick = n;    // "not found yet"
+            float m = 0.f;
+            for (int r = 0; r < C; ++r) m = fmaxf(m, cluster.map_shared_rank(&S, r)->best_v);
+            const int e = 61 - (int)ceil(log2((double)n + 1.0)) - (m > 0.f ? (int)ceil(log2((double)m)) : 0);
+            S.scale = ldexp(1.0, e > 1000 ? 1000 : e);
         }
+        cluster.sync();  // the maxima are read before best_v is reused
+    }
+    const double scale = S.scale;
+
+    // ------------------------------------------------------- k-means++ seeding
+    {
+        const double u0 = km_uniform(seed, (uint32_t)rep, 0u);
+        const int p0 = min((int)(u0 * (double)n), n - 1);
+        for (int q = T; q < d; q += kKmThreads) Cen[q] = X[(int64_t)p0 * ld + q];
         __syncthreads();
-        const double excl = scan_w[w] + incl - part;
-        const double total = shd[33];
+        for (int i = T; i < cnt; i += kKmThreads) d2[i] = (double)sqdist(X + (int64_t)(i0 + i) * ld, Cen, d);
+        __syncthreads();
+    }
+    const int chunk = (cnt + kKmThreads - 1) / kKmThreads;
+    for (int t = 1; t < k; ++t) {
+        // per-thread contiguous chunks of this CTA's points; fixed-order scan of the chunk sums
+        const int a0 = min(cnt, T * chunk), a1 = min(cnt, a0 + chunk);
+        double mine = 0.0;
+        for (int i = a0; i < a1; ++i) mine += d2[i];
+        const double excl_t = km_block_scan(mine, S.scan_w, &S.part);
+        if (T == 0) S.pick = n - 1;  // stays if rounding leaves the target past the end
+        cluster.sync();
+        // cluster-wide total and this CTA's offset, in rank order (identical in every CTA)
+        double total = 0.0, my_off = 0.0;
+        for (int r = 0; r < C; ++r) {
+            const double pr = cluster.map_shared_rank(&S, r)->part;
+            if (r == rank) my_off = total;
+            total += pr;
+        }
         const double u = km_uniform(seed, (uint32_t)rep, (uint32_t)t);
         if (total <= 0.0) {
-            if (T == 0) {
-                int p = (int)(u * (double)n);
-                sh_pick = p < n - 1 ? p : n - 1;
+            if (rank == 0 && T == 0) {
+                const int p = min((int)(u * (double)n), n - 1);
+                for (int r = 0; r < C; ++r) cluster.map_shared_rank(&S, r)->pick = p;
             }
         } else {
             const double target = u * total;
-            // first i with cumulative >= target lies in the chunk where excl < target <= excl + part
-            if (i0 < i1 && excl < target && target <= excl + part) {
-                double acc = excl;
-                int p = i1 - 1;
-                for (int i = i0; i < i1; ++i) {
+            const double lo = my_off + excl_t, hi = my_off + excl_t + mine;
+            if (a0 < a1 && lo < target && target <= hi) {
+                double acc = lo;
+                int p = a1 - 1;
+                for (int i = a0; i < a1; ++i) {
                     acc += d2[i];
                     if (acc >= target) {
                         p = i;
                         break;
                     }
                 }
-                atomicMin(&sh_pick, p);
+                for (int r = 0; r < C; ++r) cluster.map_shared_rank(&S, r)->pick = i0 + p;
             }
         }
+        cluster.sync();
+        const int p = S.pick;
+        for (int q = T; q < d; q += kKmThreads) Cen[t * d + q] = X[(int64_t)p * ld + q];
         __syncthreads();
-        if (T == 0 && sh_pick >= n) sh_pick = n - 1;  // rounding left the target past the end
-        __syncthreads();
-        const int p = sh_pick;
-        for (int q = T; q < d; q += kKmThreads) C[t * d + q] = X[(int64_t)p * ld + q];
-        __syncthreads();
-        for (int i = T; i < n; i += kKmThreads) {
-            const double dd = (double)sqdist(X + (int64_t)i * ld, C + t * d, d);
+        for (int i = T; i < cnt; i += kKmThreads) {
+            const double dd = (double)sqdist(X + (int64_t)(i0 + i) * ld, Cen + t * d, d);
             if (dd < d2[i]) d2[i] = dd;
         }
         __syncthreads();
     }
 
-    // ---- Lloyd iterations
-    auto assign = [&](int32_t* out) {
+    // ----------------------------------------------------------- Lloyd iterations
+    // Assignment: kKmLanesPerPoint lanes per point split the centres, then a
+    // min-reduction within the lane group (ties to the lower centre index).  The
+    // loop count is uniform across the block so every shuffle has all lanes.
+    constexpr int kGroups = kKmThreads / kKmLanesPerPoint;
+    auto assign = [&](int* out, bool count_changes) {
         int changed = 0;
-        for (int i = T; i < n; i += kKmThreads) {
-            const float* x = X + (int64_t)i * ld;
-            float best = sqdist(x, C, d);
-            int bj = 0;
-            for (int j = 1; j < k; ++j) {
-                const float dj = sqdist(x, C + j * d, d);
-                if (dj < best) {
-                    best = dj;
-                    bj = j;
+        const int sub = T % kKmLanesPerPoint;
+        const int rounds = (cnt + kGroups - 1) / kGroups;
+        for (int it = 0; it < rounds; ++it) {
+            const int pt = it * kGroups + T / kKmLanesPerPoint;
+            const bool valid = pt < cnt;
+            float best = INFINITY;
+            int bj = 0x7fffffff;
+            if (valid) {
+                const float* x = X + (int64_t)(i0 + pt) * ld;
+                for (int j = sub; j < k; j += kKmLanesPerPoint) {
+                    const float dj = sqdist(x, Cen + j * d, d);
+                    if (dj < best) {
+                        best = dj;
+                        bj = j;
+                    }
                 }
             }
-            if (out == nlab && bj != lab[i]) changed = 1;
-            out[i] = bj;
+#pragma unroll
+            for (int o = kKmLanesPerPoint / 2; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, best, o, kKmLanesPerPoint);
+                const int oj = __shfl_xor_sync(0xffffffffu, bj, o, kKmLanesPerPoint);
+                if (ov < best || (ov == best && oj < bj)) {
+                    best = ov;
+                    bj = oj;
+                }
+            }
+            if (valid && sub == 0) {
+                if (count_changes && bj != lab[pt]) changed = 1;
+                out[pt] = bj;
+            }
         }
         return changed;
     };
-    assign(lab);
+    assign(lab, false);
     __syncthreads();
     for (int it = 1; it <= max_iter; ++it) {
-        for (int q = T; q < k * d; q += kKmThreads) sums[q] = 0ull;
-        for (int j = T; j < k; j += kKmThreads) counts[j] = 0;
-        __syncthreads();
-        for (int i = T; i < n; i += kKmThreads) {
+        for (int q = T; q < own_k * d; q += kKmThreads) sums[q] = 0ull;
+        for (int j = T; j < own_k; j += kKmThreads) counts[j] = 0;
+        cluster.sync();  // every owner has zeroed before anyone adds
+        for (int i = T; i < cnt; i += kKmThreads) {
             const int j = lab[i];
-            atomicAdd(counts + j, 1);
+            const int owner = j % C, slot = j / C;
+            unsigned long long* rs = cluster.map_shared_rank(sums, owner) + (size_t)slot * d;
+            atomicAdd(cluster.map_shared_rank(counts, owner) + slot, 1);
+            const float* x = X + (int64_t)(i0 + i) * ld;
             for (int q = 0; q < d; ++q) {
-                const long long v = llrint((double)X[(int64_t)i * ld + q] * scale);
-                atomicAdd(sums + (int64_t)j * d + q, (unsigned long long)v);
+                const long long v = llrint((double)x[q] * scale);
+                atomicAdd(rs + q, (unsigned long long)v);
             }
         }
-        __syncthreads();
-        for (int q = T; q < k * d; q += kKmThreads) {
-            const int j = q / d;
-            if (counts[j] > 0) C[q] = (float)((double)(long long)sums[q] / scale / (double)counts[j]);
+        cluster.sync();
+        // owners: new centres of their clusters into every CTA; empty flags likewise
+        for (int q = T; q < own_k * d; q += kKmThreads) {
+            const int slot = q / d, j = slot * C + rank;
+            if (j >= k) continue;
+            const int c = counts[slot];
+            if (c > 0) {
+                const float v = (float)((double)(long long)sums[q] / scale / (double)c);
+                for (int r = 0; r < C; ++r) cluster.map_shared_rank(Cen, r)[j * d + q % d] = v;
+            }
         }
-        __syncthreads();
+        for (int slot = T; slot < own_k; slot += kKmThreads) {
+            const int j = slot * C + rank;
+            if (j < k) {
+                const int e = counts[slot] == 0 ? 1 : 0;
+                for (int r = 0; r < C; ++r) cluster.map_shared_rank(empty, r)[j] = e;
+            }
+        }
+        cluster.sync();
+        // empty clusters in increasing index: the point farthest from its own centre moves there
         for (int j = 0; j < k; ++j) {
-            if (counts[j] > 0) continue;  // uniform across the block
+            if (!empty[j]) continue;  // the same list in every CTA
             float bv = -1.f;
             int bi = 0x7fffffff;
-            for (int i = T; i < n; i += kKmThreads) {
-                const float v = sqdist(X + (int64_t)i * ld, C + lab[i] * d, d);
+            for (int i = T; i < cnt; i += kKmThreads) {
+                const float v = sqdist(X + (int64_t)(i0 + i) * ld, Cen + lab[i] * d, d);
                 if (v > bv) {
                     bv = v;
-                    bi = i;
+                    bi = i0 + i;
                 }
             }
-            block_argmax(bv, bi, shv, shi, &sh_best, &sh_pick);
-            const int p = sh_pick;
-            for (int q = T; q < d; q += kKmThreads) C[j * d + q] = X[(int64_t)p * ld + q];
-            __syncthreads();
-            if (T == 0) {
-                // the donor cluster keeps its centre and is not revisited this update
-                counts[j] = 1;
-                lab[p] = j;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            if ((T & 31) == 0) {
+                S.shv[T >> 5] = bv;
+                S.shi[T >> 5] = bi;
             }
             __syncthreads();
+            if (T == 0) {
+                float v = S.shv[0];
+                int ix = S.shi[0];
+                for (int w = 1; w < kKmThreads / 32; ++w)
+                    if (S.shv[w] > v || (S.shv[w] == v && S.shi[w] < ix)) {
+                        v = S.shv[w];
+                        ix = S.shi[w];
+                    }
+                S.best_v = v;
+                S.best_i = ix;
+            }
+            cluster.sync();
+            if (T == 0) {
+                float v = -2.f;
+                int ix = 0x7fffffff;
+                for (int r = 0; r < C; ++r) {
+                    const KmShared* o = cluster.map_shared_rank(&S, r);
+                    if (o->best_v > v || (o->best_v == v && o->best_i < ix)) {
+                        v = o->best_v;
+                        ix = o->best_i;
+                    }
+                }
+                S.pick = ix;
+            }
+            __syncthreads();
+            const int p = S.pick;
+            for (int q = T; q < d; q += kKmThreads) Cen[j * d + q] = X[(int64_t)p * ld + q];
+            if (T == 0 && p >= i0 && p < i0 + cnt) lab[p - i0] = j;  // the donor keeps its centre
+            cluster.sync();  // candidates read everywhere before the next empty cluster
         }
-        if (T == 0) sh_changed = 0;
+        if (T == 0) S.changed = 0;
         __syncthreads();
-        const int ch = assign(nlab);
-        if (ch) atomicOr(&sh_changed, 1);
+        if (assign(nlab, true)) S.changed = 1;
         __syncthreads();
-        for (int i = T; i < n; i += kKmThreads) lab[i] = nlab[i];
-        __syncthreads();
-        if (!sh_changed) break;
+        for (int i = T; i < cnt; i += kKmThreads) lab[i] = nlab[i];
+        cluster.sync();
+        int any = 0;
+        for (int r = 0; r < C; ++r) any |= cluster.map_shared_rank(&S, r)->changed;
+        cluster.sync();  // flags read before the next iteration resets them
+        if (!any) break;
     }
+    // inertia: fp32 distances, fp64 sums in a fixed order; labels
     double in = 0.0;
-    for (int i = T; i < n; i += kKmThreads) in += (double)sqdist(X + (int64_t)i * ld, C + lab[i] * d, d);
-    in = block_sum_d(in, shd);
-    if (T == 0) inertia_all[rep] = in;
+    for (int i = T; i < cnt; i += kKmThreads) in += (double)sqdist(X + (int64_t)(i0 + i) * ld, Cen + lab[i] * d, d);
+    in = warp_sum(in);
+    if ((T & 31) == 0) S.scan_w[T >> 5] = in;
+    __syncthreads();
+    if (T == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kKmThreads / 32; ++w) t += S.scan_w[w];
+        S.part = t;
+    }
+    for (int i = T; i < cnt; i += kKmThreads) labels_all[(int64_t)rep * n + i0 + i] = lab[i];
+    cluster.sync();
+    if (rank == 0 && T == 0) {
+        double t = 0.0;
+        for (int r = 0; r < C; ++r) t += cluster.map_shared_rank(&S, r)->part;
+        inertia_all[rep] = t;
+    }
+    cluster.sync();  // every CTA's shared memory stays alive until rank 0 has read it
 }
 
 __global__ void kmeans_pick_kernel(const int32_t* __restrict__ labels_all, const double* __restrict__ inertia_all,
@@ -288,9 +384,22 @@ __global__ void kmeans_pick_kernel(const int32_t* __restrict__ labels_all, const
 csc_status run_kmeans(const float* X, int64_t n64, int d, int ld, int k, int reps, int max_iter, uint64_t seed,
                       int32_t* labels_out, double* inertia_out, Graph* owner, cudaStream_t s) {
     const int n = (int)n64;
-    const size_t smem = (size_t)k * d * sizeof(float);
+    int dev = 0, sms = 148;
+    CSC_CUDA_TRY(cudaGetDevice(&dev));
+    CSC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // cluster size: spread the replicates over the SMs, at most 8 CTAs (the portable
+    // cluster size), and slices of at least 16 points
+    int C = sms / reps;
+    C = C < 1 ? 1 : (C > 8 ? 8 : C);
+    while (C > 1 && (n + C - 1) / C < 16) --C;
+    size_t smem = 0;
+    for (;; --C) {
+        const KmLayout L(k, d, (k + C - 1) / C, (n + C - 1) / C);
+        smem = L.total;
+        if (smem <= 200 * 1024 || C == 1) break;
+    }
     if (smem > 200 * 1024) {
-        set_error("k-means: k*d = %d exceeds the shared-memory centre table", k * d);
+        set_error("k-means: k*d = %d with n = %d needs %zu bytes of shared memory per CTA", k * d, n, smem);
         return CSC_E_UNSUPPORTED;
     }
     size_t off = 0;
@@ -299,9 +408,7 @@ csc_status run_kmeans(const float* X, int64_t n64, int d, int ld, int k, int rep
         off += (bytes + 255) / 256 * 256;
         return o;
     };
-    const size_t o_lab = take((size_t)reps * n * 4), o_nlab = take((size_t)reps * n * 4);
-    const size_t o_in = take((size_t)reps * 8 + 8), o_d2 = take((size_t)reps * n * 8);
-    const size_t o_sum = take((size_t)reps * k * d * 8), o_cnt = take((size_t)reps * k * 4);
+    const size_t o_lab = take((size_t)reps * n * 4), o_in = take((size_t)reps * 8 + 8);
     void* base = nullptr;
     bool async_alloc = false;
     if (owner) {
@@ -316,18 +423,27 @@ csc_status run_kmeans(const float* X, int64_t n64, int d, int ld, int k, int rep
         async_alloc = true;
     }
     char* b = (char*)base;
-    if (smem > 48 * 1024)
-        CSC_CUDA_TRY(cudaFuncSetAttribute(kmeans_replicate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
+    CSC_CUDA_TRY(cudaFuncSetAttribute(kmeans_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     double* inertia_all = (double*)(b + o_in);
+    int32_t* labels_all = (int32_t*)(b + o_lab);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(reps * C, 1, 1);
+    cfg.blockDim = dim3(kKmThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     CSC_KLAUNCH("kmeans", 4.0 * n * d * reps, s,
-                kmeans_replicate_kernel<<<reps, kKmThreads, smem, s>>>(
-                    X, n, d, ld, k, max_iter, seed, (int32_t*)(b + o_lab), inertia_all, (double*)(b + o_d2),
-                    (unsigned long long*)(b + o_sum), (int*)(b + o_cnt), (int32_t*)(b + o_nlab)));
+                CSC_CUDA_TRY(cudaLaunchKernelEx(&cfg, kmeans_cluster_kernel, X, n, d, ld, k, max_iter, seed,
+                                                labels_all, inertia_all)));
     double* dev_inertia = inertia_all + reps;
     CSC_KLAUNCH("kmeans_pick", 8.0 * n, s,
-                kmeans_pick_kernel<<<1, 256, 0, s>>>((int32_t*)(b + o_lab), inertia_all, reps, n, labels_out,
-                                                     dev_inertia));
+                kmeans_pick_kernel<<<1, 256, 0, s>>>(labels_all, inertia_all, reps, n, labels_out, dev_inertia));
     if (inertia_out) {
         CSC_CUDA_TRY(cudaMemcpyAsync(inertia_out, dev_inertia, sizeof(double), cudaMemcpyDeviceToHost, s));
         CSC_CUDA_TRY(cudaStreamSynchronize(s));

@@ -12,13 +12,24 @@
 //                       the eigencount moments of Sec. 4.3 follow by
 //                       T_2j = 2 T_j^2 - T_0 and T_2j+1 = 2 T_j+1 T_j - T_1.
 //
+// Pre-scaled form: the kernels carry Z_j = s X_j with s = D^-1/2 (s_i = 1 for
+// an isolated node), for which the recurrence reads
+//   Z_{j+1} = -2 D^-1 W Z_j - Z_{j-1},   Z_1 = -D^-1 W Z_0,   Z_0 = s R,
+// so the neighbour sum is unweighted: the edge weight 1/sqrt(d_i d_l) is
+// carried by the rows of Z and by the row factor 1/d_i, both from the degree
+// vector, and no per-edge weight is loaded.  Y = D^1/2 sum_j c_j Z_j: the
+// accumulator holds sum_j c_j Z_j until the last order multiplies by sqrt(d_i).
+//
 // Layout: signal blocks are N x ld row-major (ld = padded column count, a
 // multiple of the 16-byte vector width), ping-ponged between two scratch
-// buffers; X_{j+1} overwrites X_{j-1} in place (each element is read and
+// buffers; Z_{j+1} overwrites Z_{j-1} in place (each element is read and
 // written by the same thread).  The accumulator Y is the caller's output
 // buffer, addressed in original node order through `perm`.
 #include <math.h>
 #include <stdio.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "device.cuh"
@@ -27,7 +38,9 @@ namespace csc {
 
 // ------------------------------------------------------------------- K4
 __global__ void degrees_kernel(const int32_t* __restrict__ rp, int32_t N, int32_t* __restrict__ deg,
-                               float* __restrict__ dinv, double* __restrict__ dinv64) {
+                               float* __restrict__ dinv, double* __restrict__ dinv64, float* __restrict__ invdeg,
+                               float* __restrict__ sqdeg, double* __restrict__ invdeg64,
+                               double* __restrict__ sqdeg64) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const int dg = rp[i + 1] - rp[i];
@@ -35,21 +48,36 @@ __global__ void degrees_kernel(const int32_t* __restrict__ rp, int32_t N, int32_
     const double r = dg > 0 ? 1.0 / sqrt((double)dg) : 0.0;
     dinv64[i] = r;
     dinv[i] = (float)r;
+    const double id = dg > 0 ? 1.0 / (double)dg : 0.0;
+    const double sq = dg > 0 ? sqrt((double)dg) : 1.0;
+    invdeg64[i] = id;
+    sqdeg64[i] = sq;
+    invdeg[i] = (float)id;
+    sqdeg[i] = (float)sq;
 }
 
 csc_status launch_degrees(Graph* g, cudaStream_t s) {
     if (g->N == 0) return CSC_OK;
-    CSC_KLAUNCH("degrees", 4.0 * (g->N + 1) + 16.0 * g->N, s,
+    CSC_KLAUNCH("degrees", 4.0 * (g->N + 1) + 40.0 * g->N, s,
                 degrees_kernel<<<ceil_div(g->N, 256), 256, 0, s>>>(g->row_ptr, (int32_t)g->N, g->deg, g->dinv,
-                                                                   g->dinv64));
+                                                                   g->dinv64, g->invdeg, g->sqdeg, g->invdeg64,
+                                                                   g->sqdeg64));
     return CSC_OK;
+}
+
+// s_i of the pre-scaled form: D^-1/2, or 1 for an isolated node
+template <typename A>
+__device__ __forceinline__ A row_scale(A dinv_i) {
+    return dinv_i > A(0) ? dinv_i : A(1);
 }
 
 // ------------------------------------------------------------------- K3
 // One thread per (row, column quad): four normals from one Philox call.
+// Writes Z_0 = s R (row scale s of the pre-scaled form; `scale` = D^-1/2, NULL for none).
 template <typename T>
 __global__ void gauss_fill_kernel(T* __restrict__ X, int32_t N, int d, int ld, uint64_t seed,
-                                  uint32_t stream, float sigma, const int32_t* __restrict__ perm) {
+                                  uint32_t stream, float sigma, const int32_t* __restrict__ perm,
+                                  const typename StoreTraits<T>::acc_t* __restrict__ scale) {
     using Tr = StoreTraits<T>;
     const int quads = ld / 4;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,70 +100,89 @@ __global__ void gauss_fill_kernel(T* __restrict__ X, int32_t N, int d, int ld, u
 #pragma unroll
         for (int v = 0; v < 4; ++v) z[v] = (4 * q + v < d) ? z[v] * sigma : 0.f;
     }
+    using A = typename Tr::acc_t;
+    const A sc = scale ? row_scale<A>(scale[row]) : A(1);
     T* dst = X + (int64_t)row * ld + 4 * q;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) dst[v] = (T)z[v];
+    for (int v = 0; v < 4; ++v) dst[v] = (T)((A)z[v] * sc);
 }
 
 // Copy a caller block R_in (original order, row stride ld_in, fp32) into X (internal order).
 template <typename T>
 __global__ void copy_in_kernel(T* __restrict__ X, const float* __restrict__ R, int32_t N, int d, int ld,
-                               int ld_in, const int32_t* __restrict__ perm) {
+                               int ld_in, const int32_t* __restrict__ perm,
+                               const typename StoreTraits<T>::acc_t* __restrict__ scale) {
+    using A = typename StoreTraits<T>::acc_t;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)N * ld) return;
     const int row = (int)(t / ld);
     const int c = (int)(t % ld);
     const int64_t orig = perm ? perm[row] : row;
-    X[t] = (T)(c < d ? R[orig * ld_in + c] : 0.0f);
+    const A sc = scale ? row_scale<A>(scale[row]) : A(1);
+    X[t] = (T)(c < d ? (A)R[orig * ld_in + c] * sc : A(0));
 }
 
 // ------------------------------------------------------------------- K1
+// mode bit 1: first order (Z_1 = -D^-1 W Z_0, Y = c_0 Z_0 + c_1 Z_1)
+// mode bit 2: last order (Y is brought back to X space: Y *= sqrt(d_i))
+//
+// Launch shape (all SpMM kernels): CTA x sweeps the contiguous row range
+// [part[x], part[x+1]) in order, G lanes per row, so that rows close in the
+// node order -- the neighbours in a community, or in a bandwidth-reduced (RCM)
+// order -- are gathered by the same CTA while they are in its L1; CTA y covers
+// the column tile [y*TW, (y+1)*TW) with TW = G*NT*VEC.
 template <typename T, int G, int NT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 cheb_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                 const typename StoreTraits<T>::acc_t* __restrict__ dinv, const T* __restrict__ xcur,
-                 T* __restrict__ xprev_next, typename StoreTraits<T>::acc_t* __restrict__ Y,
-                 const int32_t* __restrict__ perm, int32_t N, int ncols, int64_t ld,
-                 typename StoreTraits<T>::acc_t c0, typename StoreTraits<T>::acc_t c_next, int first) {
+                 const typename StoreTraits<T>::acc_t* __restrict__ invdeg,
+                 const typename StoreTraits<T>::acc_t* __restrict__ sqdeg, const T* __restrict__ zcur,
+                 T* __restrict__ zprev_next, typename StoreTraits<T>::acc_t* __restrict__ Y,
+                 const int32_t* __restrict__ perm, const int32_t* __restrict__ part, int ncols, int64_t ld,
+                 typename StoreTraits<T>::acc_t c0, typename StoreTraits<T>::acc_t c_next, int mode) {
     using Tr = StoreTraits<T>;
     using A = typename Tr::acc_t;
     constexpr int VEC = Tr::VEC;
+    constexpr int TW = G * NT * VEC;
+    const bool first = (mode & 1) != 0, last = (mode & 2) != 0;
     const int lane = threadIdx.x % G;
-    const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
-    for (int64_t r = group; r < N; r += ngroups) {
-        const int row = (int)r;
+    const int col0 = blockIdx.y * TW;
+    const int tcols = min(TW, ncols - col0);
+    const int r1 = part[blockIdx.x + 1];
+    for (int row = part[blockIdx.x] + (int)(threadIdx.x / G); row < r1; row += (int)(blockDim.x / G)) {
         A acc[NT][VEC];
-        gather_row<T, G, NT>(rp, ci, dinv, xcur, ld, row, lane, ncols, acc);
-        const A di = dinv[row];
+        gather_row<T, G, NT, false, A>(rp, ci, nullptr, zcur + col0, ld, row, lane, tcols, acc);
+        const A f = (first ? A(-1) : A(-2)) * invdeg[row];
+        const A back = last ? sqdeg[row] : A(1);
         const int64_t yrow = perm ? (int64_t)perm[row] : (int64_t)row;
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            const int c = (t * G + lane) * VEC;
-            if (c >= ncols) continue;
-            A xn[VEC], y[VEC];
-            T* xp_ptr = xprev_next + (int64_t)row * ld + c;
+            const int cl = (t * G + lane) * VEC;
+            if (cl >= tcols) continue;
+            const int c = col0 + cl;
+            A zn[VEC], y[VEC];
+            T* zp_ptr = zprev_next + (int64_t)row * ld + c;
             A* y_ptr = Y + yrow * ld + c;
             if (first) {
-                A x0[VEC];
-                Tr::load(xcur + (int64_t)row * ld + c, x0);
+                A z0[VEC];
+                Tr::load(zcur + (int64_t)row * ld + c, z0);
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) xn[v] = Tr::round(-di * acc[t][v]);
-                Tr::store(xp_ptr, xn);
+                for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v]);
+                Tr::store(zp_ptr, zn);
                 // Y accumulates the stored (for bf16: rounded) values the recurrence continues with
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) y[v] = c0 * x0[v] + c_next * xn[v];
+                for (int v = 0; v < VEC; ++v) y[v] = (c0 * z0[v] + c_next * zn[v]) * back;
             } else {
-                A xp[VEC];
-                Tr::load_cs(xp_ptr, xp);
+                A zp[VEC];
+                Tr::load_cs(zp_ptr, zp);
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) xn[v] = Tr::round(A(-2) * di * acc[t][v] - xp[v]);
-                Tr::store(xp_ptr, xn);
+                for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v] - zp[v]);
+                Tr::store(zp_ptr, zn);
                 AccIO<A, VEC>::load_cs(y_ptr, y);
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) y[v] = fma(c_next, xn[v], y[v]);
+                for (int v = 0; v < VEC; ++v) y[v] = fma(c_next, zn[v], y[v]) * back;
             }
-            AccIO<A, VEC>::store(y_ptr, y);
+            // Y is read again only by the next order: evict-first keeps Z_j resident in L2
+            AccIO<A, VEC>::store_cs(y_ptr, y);
         }
     }
 }
@@ -144,13 +191,14 @@ cheb_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
 template <typename T>
 __global__ void scale_copy_kernel(const T* __restrict__ X, typename StoreTraits<T>::acc_t* __restrict__ Y,
                                   const int32_t* __restrict__ perm, int32_t N, int ld,
-                                  typename StoreTraits<T>::acc_t c0) {
+                                  typename StoreTraits<T>::acc_t c0,
+                                  const typename StoreTraits<T>::acc_t* __restrict__ sqdeg) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)N * ld) return;
     const int row = (int)(t / ld);
     const int c = (int)(t % ld);
     const int64_t yrow = perm ? perm[row] : row;
-    Y[yrow * ld + c] = c0 * (typename StoreTraits<T>::acc_t)X[t];
+    Y[yrow * ld + c] = c0 * (typename StoreTraits<T>::acc_t)X[t] * sqdeg[row];
 }
 
 // ------------------------------------------------------------------- K5
@@ -176,51 +224,61 @@ __global__ void normalize_kernel(A* __restrict__ Y, int32_t N, int d, int ld) {
 }
 
 // ------------------------------------------------------------------- K2
-// Moment step: like cheb_step without Y; block partials of three fp64 sums:
+// Moment step on the pre-scaled probes Z = s X: like cheb_step without Y; block
+// partials of three fp64 sums of X-space inner products, <X_a, X_b> =
+// sum_i d_i <Z_a, Z_b>_i (d_i -> 1 for an isolated node):
 //   first: s0 = <X0,X0>, s1 = <X1,X0>, s2 = <X1,X1>
 //   later: s1 = <X_{j+1},X_j>, s2 = <X_{j+1},X_{j+1}>
 template <typename T, int G, int NT>
-__global__ void __launch_bounds__(256)
-mom_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                const float* __restrict__ dinv, const T* __restrict__ xcur, T* __restrict__ xprev_next,
-                int32_t N, int ncols, int64_t ld, int first, double* __restrict__ partials) {
+__global__ void __launch_bounds__(512)
+mom_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ invdeg,
+                const int32_t* __restrict__ deg, const T* __restrict__ zcur, T* __restrict__ zprev_next,
+                const int32_t* __restrict__ part, int ncols, int64_t ld, int first, double* __restrict__ partials) {
     using Tr = StoreTraits<T>;
     constexpr int VEC = Tr::VEC;
+    constexpr int TW = G * NT * VEC;
     const int lane = threadIdx.x % G;
-    const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+    const int col0 = blockIdx.y * TW;
+    const int tcols = min(TW, ncols - col0);
+    const int r1 = part[blockIdx.x + 1];
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int64_t r = group; r < N; r += ngroups) {
-        const int row = (int)r;
+    for (int row = part[blockIdx.x] + (int)(threadIdx.x / G); row < r1; row += (int)(blockDim.x / G)) {
         float acc[NT][VEC];
-        gather_row<T, G, NT>(rp, ci, dinv, xcur, ld, row, lane, ncols, acc);
-        const float di = dinv[row];
+        gather_row<T, G, NT, false, float>(rp, ci, nullptr, zcur + col0, ld, row, lane, tcols, acc);
+        const float f = (first ? -1.0f : -2.0f) * invdeg[row];
+        const int dg = deg[row];
+        const double wr = dg > 0 ? (double)dg : 1.0;
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f;  // this row's products, fp32, then one fp64 add each
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-            const int c = (t * G + lane) * VEC;
-            if (c >= ncols) continue;
-            float xc[VEC], xn[VEC];
-            Tr::load(xcur + (int64_t)row * ld + c, xc);
-            T* xp_ptr = xprev_next + (int64_t)row * ld + c;
+            const int cl = (t * G + lane) * VEC;
+            if (cl >= tcols) continue;
+            const int c = col0 + cl;
+            float zc[VEC], zn[VEC];
+            Tr::load(zcur + (int64_t)row * ld + c, zc);
+            T* zp_ptr = zprev_next + (int64_t)row * ld + c;
             if (first) {
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) xn[v] = Tr::round(-di * acc[t][v]);
+                for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v]);
             } else {
-                float xp[VEC];
-                Tr::load_cs(xp_ptr, xp);
+                float zp[VEC];
+                Tr::load_cs(zp_ptr, zp);
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) xn[v] = Tr::round(-2.0f * di * acc[t][v] - xp[v]);
+                for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v] - zp[v]);
             }
-            Tr::store(xp_ptr, xn);
+            Tr::store(zp_ptr, zn);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
-                s0 += (double)xc[v] * (double)xc[v];
-                s1 += (double)xn[v] * (double)xc[v];
-                s2 += (double)xn[v] * (double)xn[v];
+                p0 = fmaf(zc[v], zc[v], p0);
+                p1 = fmaf(zn[v], zc[v], p1);
+                p2 = fmaf(zn[v], zn[v], p2);
             }
         }
+        s0 += wr * (double)p0;
+        s1 += wr * (double)p1;
+        s2 += wr * (double)p2;
     }
-    __shared__ double red[3][8];
+    __shared__ double red[3][32];
     s0 = warp_sum(s0);
     s1 = warp_sum(s1);
     s2 = warp_sum(s2);
@@ -232,7 +290,7 @@ mom_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
     if (threadIdx.x < 3) {
         double t = 0.0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[threadIdx.x][i];
-        partials[(int64_t)blockIdx.x * 3 + threadIdx.x] = t;
+        partials[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = t;
     }
 }
 
@@ -256,107 +314,221 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partials, int 
 }
 
 // ------------------------------------------------------------- dispatch
+// (G, NT) pairs compiled for the SpMM kernels.
 struct TileShape {
     int G, NT;
 };
-
-// (G, NT) pairs compiled for the SpMM kernels.
 static const TileShape kShapes[] = {{2, 1}, {2, 2}, {2, 3}, {4, 1}, {4, 2}, {4, 3}, {8, 1},
                                     {8, 2}, {8, 3}, {16, 1}, {16, 2}, {32, 1}, {32, 2}};
+static const int kThreadChoices[] = {256, 512};
 
-// Pick the compiled shape covering nv 16-byte vectors per row with the least
-// idle lanes; ties go to the group width closest to 8 lanes.
-static TileShape choose_shape(int nv) {
-    TileShape best{32, 2};
-    int best_waste = 1 << 30, best_pref = 1 << 30;
-    for (const TileShape& s : kShapes) {
-        const int cap = s.G * s.NT;
-        if (cap < nv) continue;
-        const int waste = cap - nv;
-        const int pref = s.G >= 8 ? s.G / 8 : 8 / s.G;
-        if (waste < best_waste || (waste == best_waste && pref < best_pref)) {
-            best = s;
-            best_waste = waste;
-            best_pref = pref;
+enum KernelKind { KK_CHEB = 1, KK_MOM = 2 };
+
+// Expands BODY for the compiled (G, NT) equal to (cfg.G, cfg.NT), with GG / NN bound.
+#define CSC_SHAPE_SWITCH(cfg, BODY)                                                       \
+    switch ((cfg).G * 8 + (cfg).NT) {                                                     \
+        case 2 * 8 + 1: { constexpr int GG = 2, NN = 1; BODY; } break;                    \
+        case 2 * 8 + 2: { constexpr int GG = 2, NN = 2; BODY; } break;                    \
+        case 2 * 8 + 3: { constexpr int GG = 2, NN = 3; BODY; } break;                    \
+        case 4 * 8 + 1: { constexpr int GG = 4, NN = 1; BODY; } break;                    \
+        case 4 * 8 + 2: { constexpr int GG = 4, NN = 2; BODY; } break;                    \
+        case 4 * 8 + 3: { constexpr int GG = 4, NN = 3; BODY; } break;                    \
+        case 8 * 8 + 1: { constexpr int GG = 8, NN = 1; BODY; } break;                    \
+        case 8 * 8 + 2: { constexpr int GG = 8, NN = 2; BODY; } break;                    \
+        case 8 * 8 + 3: { constexpr int GG = 8, NN = 3; BODY; } break;                    \
+        case 16 * 8 + 1: { constexpr int GG = 16, NN = 1; BODY; } break;                  \
+        case 16 * 8 + 2: { constexpr int GG = 16, NN = 2; BODY; } break;                  \
+        case 32 * 8 + 1: { constexpr int GG = 32, NN = 1; BODY; } break;                  \
+        case 32 * 8 + 2: { constexpr int GG = 32, NN = 2; BODY; } break;                  \
+        default:                                                                          \
+            set_error("no compiled tile shape G=%d NT=%d", (cfg).G, (cfg).NT);            \
+            return CSC_E_UNSUPPORTED;                                                     \
+    }
+
+template <typename T>
+static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur, T* xpn,
+                                   typename StoreTraits<T>::acc_t* Y, int ncols, int64_t ld,
+                                   double c0, double cn, int mode, cudaStream_t s) {
+    using A = typename StoreTraits<T>::acc_t;
+    const A *idg, *sqd;
+    if constexpr (sizeof(A) == 8) {
+        idg = g->invdeg64;
+        sqd = g->sqdeg64;
+    } else {
+        idg = g->invdeg;
+        sqd = g->sqdeg;
+    }
+    const int first = mode & 1;
+    const int32_t* part = nullptr;
+    CSC_TRY(get_partition(g, cfg.P, &part));
+    const dim3 grid(cfg.P, cfg.tiles);
+    // algorithmic bytes of one order: CSR + row factors, Z_j gathered once, Z_{j-1} read and
+    // Z_{j+1} written (first order: Z_0 read, Z_1 written), Y written or read+written
+    const double nx = (double)g->N * ncols;
+    const double bytes = 4.0 * g->nnz + 4.0 * (g->N + 1) + (double)sizeof(A) * g->N * (mode & 2 ? 2 : 1) +
+                         (first ? 2.0 : 3.0) * nx * sizeof(T) + (first ? 1.0 : 2.0) * nx * sizeof(A);
+    CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", bytes, s,
+                                      cheb_step_kernel<T, GG, NN><<<grid, cfg.threads, 0, s>>>(
+                                          g->row_ptr, g->col_idx, idg, sqd, xcur, xpn, Y, g->perm, part, ncols, ld,
+                                          (A)c0, (A)cn, mode)));
+    return CSC_OK;
+}
+
+template <typename T>
+static csc_status launch_mom_step(Graph* g, const LaunchCfg& cfg, const T* xcur, T* xpn, int ncols, int64_t ld,
+                                  int first, double* partials, cudaStream_t s) {
+    const double bytes = 4.0 * g->nnz + 8.0 * g->N + 4.0 + (first ? 2.0 : 3.0) * (double)g->N * ncols * sizeof(T);
+    const int32_t* part = nullptr;
+    CSC_TRY(get_partition(g, cfg.P, &part));
+    const dim3 grid(cfg.P, cfg.tiles);
+    CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("mom_step", bytes, s,
+                                      mom_step_kernel<T, GG, NN><<<grid, cfg.threads, 0, s>>>(
+                                          g->row_ptr, g->col_idx, g->invdeg, g->deg, xcur, xpn, part, ncols, ld,
+                                          first, partials)));
+    return CSC_OK;
+}
+
+// Resident CTAs per SM for a kernel at a block size.
+template <typename K>
+static int occupancy(K kernel, int threads) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n < 1 ? 1 : n;
+}
+
+template <typename T>
+static int kernel_occupancy(int kind, const TileShape& sh, int threads) {
+    int occ = 1;
+    auto f = [&](auto kptr) { occ = occupancy(kptr, threads); };
+#define CSC_OCC_CASE(GG, NN)                                                             \
+    if (sh.G == GG && sh.NT == NN) {                                                     \
+        if (kind == KK_CHEB) f(cheb_step_kernel<T, GG, NN>);                             \
+        else if constexpr (sizeof(T) <= 4) f(mom_step_kernel<T, GG, NN>);               \
+    }
+    CSC_OCC_CASE(2, 1) CSC_OCC_CASE(2, 2) CSC_OCC_CASE(2, 3) CSC_OCC_CASE(4, 1) CSC_OCC_CASE(4, 2)
+    CSC_OCC_CASE(4, 3) CSC_OCC_CASE(8, 1) CSC_OCC_CASE(8, 2) CSC_OCC_CASE(8, 3) CSC_OCC_CASE(16, 1)
+    CSC_OCC_CASE(16, 2) CSC_OCC_CASE(32, 1) CSC_OCC_CASE(32, 2)
+#undef CSC_OCC_CASE
+    return occ;
+}
+
+// Candidate launch shapes for nv 16-byte vectors per row: every compiled (G, NT)
+// whose column tiles leave at most a third of their lanes idle, at each block size,
+// with one CTA per row range and tile for every resident CTA slot of the GPU.
+template <typename T>
+static std::vector<LaunchCfg> candidates(Graph* g, int kind, int nv) {
+    std::vector<LaunchCfg> out;
+    // narrow rows (a few vectors) cannot fill any group: then the least-waste shapes are kept
+    int min_waste = 1 << 30;
+    for (const TileShape& sh : kShapes) {
+        const int cap = sh.G * sh.NT;
+        const int tiles = (nv + cap - 1) / cap;
+        if (tiles <= 16) min_waste = std::min(min_waste, tiles * cap - nv);
+    }
+    for (const TileShape& sh : kShapes) {
+        const int cap = sh.G * sh.NT;
+        const int tiles = (nv + cap - 1) / cap;
+        if (tiles > 16) continue;
+        const int waste = tiles * cap - nv;
+        if (3 * waste > tiles * cap && waste > min_waste) continue;
+        for (int th : kThreadChoices) {
+            LaunchCfg c;
+            c.G = sh.G;
+            c.NT = sh.NT;
+            c.threads = th;
+            c.tiles = tiles;
+            const int occ = kernel_occupancy<T>(kind, sh, th);
+            const int64_t max_p = (g->N + (th / sh.G) - 1) / (th / sh.G);  // at least one row per group
+            // one to eight waves of resident CTAs: more, shorter row ranges balance SMs that
+            // run at different speeds (distance to the memory holding their rows)
+            for (int waves = 1; waves <= 8; waves *= 2) {
+                int P = (g->num_sms * occ * waves + tiles - 1) / tiles;
+                if (P > max_p) P = (int)max_p;
+                c.P = P < 1 ? 1 : P;
+                if (!out.empty() && out.back().G == c.G && out.back().NT == c.NT && out.back().threads == th &&
+                    out.back().P == c.P)
+                    continue;
+                out.push_back(c);
+            }
         }
     }
-    return best;
+    return out;
 }
 
-static int grid_for(Graph* g, int64_t rows, int G) {
-    const int64_t groups_per_block = 256 / G;
-    int64_t blocks = (rows + groups_per_block - 1) / groups_per_block;
-    const int64_t cap = (int64_t)g->num_sms * 8;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    return (int)blocks;
-}
-
-template <typename T>
-static csc_status launch_cheb_step(Graph* g, TileShape sh, const T* xcur, T* xpn,
-                                   typename StoreTraits<T>::acc_t* Y, int ncols, int64_t ld,
-                                   double c0, double cn, int first, cudaStream_t s) {
-    using A = typename StoreTraits<T>::acc_t;
-    const A* dv;
-    if constexpr (sizeof(A) == 8) dv = g->dinv64; else dv = g->dinv;
-    const int grid = grid_for(g, g->N, sh.G);
-    // algorithmic bytes of one order: CSR + D^-1/2, X_j gathered once, X_{j-1} read and
-    // X_{j+1} written (first order: X_0 read, X_1 written), Y written or read+written
-    const double nx = (double)g->N * ncols;
-    const double bytes = 4.0 * g->nnz + 4.0 * (g->N + 1) + (double)sizeof(A) * g->N +
-                         (first ? 2.0 : 3.0) * nx * sizeof(T) + (first ? 1.0 : 2.0) * nx * sizeof(A);
-#define CSC_CHEB_CASE(GG, NN)                                                                    \
-    if (sh.G == GG && sh.NT == NN) {                                                             \
-        CSC_KLAUNCH("cheb_step", bytes, s,                                                       \
-                    cheb_step_kernel<T, GG, NN><<<grid, 256, 0, s>>>(g->row_ptr, g->col_idx, dv, xcur,  \
-                                                                     xpn, Y, g->perm, (int32_t)g->N,    \
-                                                                     ncols, ld, (A)c0, (A)cn, first));   \
-        return CSC_OK;                                                                           \
+// Time each candidate (3 launches after one warm-up) and keep the fastest.  `run`
+// launches one candidate on scratch data of the real problem.
+template <typename RunFn>
+static csc_status autotune(Graph* g, uint64_t key, const std::vector<LaunchCfg>& cands, cudaStream_t s,
+                           RunFn run, LaunchCfg* out) {
+    auto it = g->tuned.find(key);
+    if (it != g->tuned.end()) {
+        *out = it->second;
+        return CSC_OK;
     }
-    CSC_CHEB_CASE(2, 1) CSC_CHEB_CASE(2, 2) CSC_CHEB_CASE(2, 3) CSC_CHEB_CASE(4, 1)
-    CSC_CHEB_CASE(4, 2) CSC_CHEB_CASE(4, 3) CSC_CHEB_CASE(8, 1) CSC_CHEB_CASE(8, 2)
-    CSC_CHEB_CASE(8, 3) CSC_CHEB_CASE(16, 1) CSC_CHEB_CASE(16, 2) CSC_CHEB_CASE(32, 1)
-    CSC_CHEB_CASE(32, 2)
-#undef CSC_CHEB_CASE
-    set_error("no compiled tile shape G=%d NT=%d", sh.G, sh.NT);
-    return CSC_E_UNSUPPORTED;
+    if (tune_cache_get(g, key, out)) {
+        g->tuned[key] = *out;
+        return CSC_OK;
+    }
+    if (cands.empty()) {
+        set_error("autotune: no launch shape fits");
+        return CSC_E_UNSUPPORTED;
+    }
+    const bool prof = g_prof_enabled;
+    g_prof_enabled = false;  // tuning launches are not part of the measured work
+    cudaEvent_t a = g->ev[0], b = g->ev[1];
+    float best_ms = 1e30f;
+    LaunchCfg best = cands[0];
+    csc_status st = CSC_OK;
+    for (const LaunchCfg& c : cands) {
+        st = run(c);
+        if (st != CSC_OK) break;
+        cudaEventRecord(a, s);
+        for (int r = 0; r < 3 && st == CSC_OK; ++r) st = run(c);
+        cudaEventRecord(b, s);
+        if (st != CSC_OK) break;
+        if (cudaEventSynchronize(b) != cudaSuccess) {
+            st = CSC_E_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    g_prof_enabled = prof;
+    if (st != CSC_OK) return st;
+    g->tuned[key] = best;
+    tune_cache_put(g, key, best);
+    *out = best;
+    return CSC_OK;
 }
 
-template <typename T>
-static csc_status launch_mom_step(Graph* g, TileShape sh, const T* xcur, T* xpn, int ncols, int64_t ld,
-                                  int first, double* partials, int grid, cudaStream_t s) {
-    const double bytes = 4.0 * g->nnz + 8.0 * g->N + 4.0 + (first ? 2.0 : 3.0) * (double)g->N * ncols * sizeof(T);
-#define CSC_MOM_CASE(GG, NN)                                                                     \
-    if (sh.G == GG && sh.NT == NN) {                                                             \
-        CSC_KLAUNCH("mom_step", bytes, s,                                                        \
-                    mom_step_kernel<T, GG, NN><<<grid, 256, 0, s>>>(g->row_ptr, g->col_idx, g->dinv,    \
-                                                                    xcur, xpn, (int32_t)g->N, ncols, ld, \
-                                                                    first, partials));                   \
-        return CSC_OK;                                                                           \
-    }
-    CSC_MOM_CASE(2, 1) CSC_MOM_CASE(2, 2) CSC_MOM_CASE(2, 3) CSC_MOM_CASE(4, 1)
-    CSC_MOM_CASE(4, 2) CSC_MOM_CASE(4, 3) CSC_MOM_CASE(8, 1) CSC_MOM_CASE(8, 2)
-    CSC_MOM_CASE(8, 3) CSC_MOM_CASE(16, 1) CSC_MOM_CASE(16, 2) CSC_MOM_CASE(32, 1)
-    CSC_MOM_CASE(32, 2)
-#undef CSC_MOM_CASE
-    set_error("no compiled tile shape G=%d NT=%d", sh.G, sh.NT);
-    return CSC_E_UNSUPPORTED;
+static uint64_t tune_key(int kind, int dtype, int ncols) {
+    return ((uint64_t)kind << 48) | ((uint64_t)(dtype & 0xff) << 40) | (uint64_t)(uint32_t)ncols;
 }
 
 template <typename T>
 static csc_status fill_block(Graph* g, T* X, int d, int ld, uint64_t seed, uint32_t stream, float sigma,
                              const float* R_in, int ld_in, cudaStream_t s) {
+    using A = typename StoreTraits<T>::acc_t;
     const int64_t N = g->N;
+    const A* scale;  // Z_0 = D^-1/2 R (row factor 1 for isolated nodes)
+    if constexpr (sizeof(A) == 8) scale = g->dinv64; else scale = g->dinv;
     if (R_in) {
         const int64_t tot = N * ld;
         CSC_KLAUNCH("copy_in", (double)tot * (4 + sizeof(T)), s,
                     copy_in_kernel<T><<<ceil_div(tot, 256), 256, 0, s>>>(X, R_in, (int32_t)N, d, ld, ld_in,
-                                                                         g->perm));
+                                                                         g->perm, scale));
     } else {
         const int64_t tot = N * (ld / 4);
         CSC_KLAUNCH("gauss_fill", (double)N * ld * sizeof(T), s,
                     gauss_fill_kernel<T><<<ceil_div(tot, 256), 256, 0, s>>>(X, (int32_t)N, d, ld, seed, stream,
-                                                                            sigma, g->perm));
+                                                                            sigma, g->perm, scale));
     }
     return CSC_OK;
 }
@@ -377,19 +549,30 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
     CSC_TRY(fill_block<T>(g, X[0], d, d_pad, seed, STREAM_SIGNALS, sigma, R_in, d_pad, s));
     if (m == 0) {
         const int64_t tot = N * d_pad;
+        const A* sqd;
+        if constexpr (sizeof(A) == 8) sqd = g->sqdeg64; else sqd = g->sqdeg;
         CSC_KLAUNCH("scale_copy", (double)tot * (sizeof(T) + sizeof(A)), s,
                     scale_copy_kernel<T><<<ceil_div(tot, 256), 256, 0, s>>>(X[0], Y, g->perm, (int32_t)N, d_pad,
-                                                                            (A)c[0]));
+                                                                            (A)c[0], sqd));
     } else {
-        const TileShape sh = choose_shape(d_pad / VEC);
-        CSC_TRY(launch_cheb_step<T>(g, sh, X[0], X[1], Y, d_pad, d_pad, c[0], c[1], 1, s));
+        // launch shape tuned once per handle on this graph: trial orders read Z_0 and write
+        // scratch (the Z_1 buffer and Y are overwritten by the first real order)
+        LaunchCfg cfg;
+        CSC_TRY(autotune(g, tune_key(KK_CHEB, (int)sizeof(T), d_pad), candidates<T>(g, KK_CHEB, d_pad / VEC), s,
+                         [&](const LaunchCfg& c) {
+                             return launch_cheb_step<T>(g, c, X[0], X[1], Y, d_pad, d_pad, 0.0, 0.0, 0, s);
+                         },
+                         &cfg));
+        CSC_TRY(launch_cheb_step<T>(g, cfg, X[0], X[1], Y, d_pad, d_pad, c[0], c[1], 1 | (m == 1 ? 2 : 0), s));
         for (int j = 1; j < m; ++j) {
-            // X_j lives in X[j & 1]; X_{j-1} (overwritten by X_{j+1}) in the other buffer
-            CSC_TRY(launch_cheb_step<T>(g, sh, X[j & 1], X[(j + 1) & 1], Y, d_pad, d_pad, 0.0, c[j + 1], 0, s));
+            // Z_j lives in X[j & 1]; Z_{j-1} (overwritten by Z_{j+1}) in the other buffer
+            CSC_TRY(launch_cheb_step<T>(g, cfg, X[j & 1], X[(j + 1) & 1], Y, d_pad, d_pad, 0.0, c[j + 1],
+                                        j == m - 1 ? 2 : 0, s));
         }
     }
     if (normalize) {
-        const int grid = grid_for(g, N, 32);
+        int grid = ceil_div(N, 8);
+        if (grid > g->num_sms * 8) grid = g->num_sms * 8;
         CSC_KLAUNCH("normalize", 2.0 * N * d_pad * sizeof(A), s,
                     normalize_kernel<A><<<grid, 256, 0, s>>>(Y, (int32_t)N, d, d_pad));
     }
@@ -423,17 +606,23 @@ static csc_status moments_typed(Graph* g, int n_moments, int n_probes, uint64_t 
     CSC_TRY(ws_get(g, WS_XA, bytes, &xa));
     CSC_TRY(ws_get(g, WS_XB, bytes, &xb));
     T* X[2] = {(T*)xa, (T*)xb};
-    const TileShape sh = choose_shape(ld / VEC);
-    const int grid = grid_for(g, N, sh.G);
     // moments 0..M-1 need X_0..X_J with 2J >= M-1
     const int J = n_moments <= 2 ? 1 : n_moments / 2;
-    CSC_TRY(ws_get(g, WS_PARTIAL, (size_t)grid * 3 * sizeof(double), &part));
+    const std::vector<LaunchCfg> cands = candidates<T>(g, KK_MOM, ld / VEC);
+    int max_blocks = 1;
+    for (const LaunchCfg& c : cands) max_blocks = std::max(max_blocks, c.P * c.tiles);
+    CSC_TRY(ws_get(g, WS_PARTIAL, (size_t)max_blocks * 3 * sizeof(double), &part));
     CSC_TRY(ws_get(g, WS_MOMENTS, (size_t)J * 3 * sizeof(double), &sums));
     double* P = (double*)part;
     double* S = (double*)sums;
     CSC_TRY(fill_block<T>(g, X[0], n_probes, ld, seed, STREAM_PROBES, 1.0f, nullptr, ld, s));
+    LaunchCfg cfg;
+    CSC_TRY(autotune(g, tune_key(KK_MOM, (int)sizeof(T), ld), cands, s,
+                     [&](const LaunchCfg& c) { return launch_mom_step<T>(g, c, X[0], X[1], ld, ld, 0, P, s); },
+                     &cfg));
+    const int grid = cfg.P * cfg.tiles;
     for (int j = 0; j < J; ++j) {
-        CSC_TRY(launch_mom_step<T>(g, sh, X[j & 1], X[(j + 1) & 1], ld, ld, j == 0 ? 1 : 0, P, grid, s));
+        CSC_TRY(launch_mom_step<T>(g, cfg, X[j & 1], X[(j + 1) & 1], ld, ld, j == 0 ? 1 : 0, P, s));
         CSC_KLAUNCH("reduce", 24.0 * grid, s, reduce_partials_kernel<<<1, 256, 0, s>>>(P, grid, S + 3 * j));
     }
     double* host = g->pinned;
