@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", action="store_true",
+                    help="filter in FP64 / FP32 / BF16 storage on the workload: time, error vs FP64, label ARI")
     return ap.parse_args()
 
 
@@ -256,7 +258,8 @@ def run_ours(args, w, rank, world, local_rank):
     g = make_graph(w, args.seed + rank)
     work = float(m) * g.nnz * d
     stream = torch.cuda.current_stream()
-    h = csc.csc_graph_create(g.row_ptr, g.col_idx)
+    flags = csc.RCM if w["kind"] == "chung_lu" else 0  # power-law workload: RCM-reordered CSR
+    h = csc.csc_graph_create(g.row_ptr, g.col_idx, flags)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
     def step():
@@ -330,7 +333,7 @@ def run_ours(args, w, rank, world, local_rank):
         for i in range(args.warmup + args.steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            h2 = csc.csc_graph_create(rp_pin.numpy(), ci_pin.numpy())
+            h2 = csc.csc_graph_create(rp_pin.numpy(), ci_pin.numpy(), flags)
             labs, _ = csc.csc_cluster(h2, k, m=m, d=d, d_pad=d_pad, n=n, storage=storage, seed=args.seed + rank)
             lab_host.copy_(labs)
             torch.cuda.synchronize()
@@ -387,6 +390,65 @@ def run_ours(args, w, rank, world, local_rank):
     return 0
 
 
+def run_precision(args, w):
+    """Precision table: the filter (rows normalised) in each storage type on the same
+    generated signal block; relative Frobenius error against the FP64 storage path
+    (pinned to the FP64 oracle in the tests), filter time, and the ARI of full CSC
+    labels against the FP32 labels."""
+    import torch
+
+    import paper_1602_02018_gb300 as csc
+
+    sz = sizes(w)
+    d, d_pad, m, k = sz["d"], sz["d_pad"], w["m"], w["k"]
+    g = make_graph(w, args.seed)
+    flags = csc.RCM if w["kind"] == "chung_lu" else 0
+    h = csc.csc_graph_create(g.row_ptr, g.col_idx, flags)
+    lam = csc.csc_estimate_lambda_k(h, k, m, 0, args.seed).lam
+    out = {"workload": args.workload, "N": g.n, "nnz": g.nnz, "k": k, "m": m, "d": d, "d_pad": d_pad,
+           "lambda_k": lam, "rcm": bool(flags), "storage": {}}
+    ys = {}
+    for name, st in (("f64", csc.F64), ("f32", csc.F32), ("bf16", csc.BF16)):
+        for _ in range(2):
+            y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, seed=args.seed, storage=st)
+        torch.cuda.synchronize()
+        csc.csc_profile_reset()
+        csc.csc_profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        reps = 3
+        for _ in range(reps):
+            y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, seed=args.seed, storage=st)
+        e1.record()
+        torch.cuda.synchronize()
+        csc.csc_profile_enable(False)
+        ms = e0.elapsed_time(e1) / reps
+        c = csc.csc_profile_query()["cheb_step"]
+        peak, _ = peaks()
+        per_launch = c["bytes"] / c["launches"]
+        avg_s = c["ms"] / c["launches"] / 1e3
+        ys[name] = y.double()
+        out["storage"][name] = {"filter_ms": ms, "nnz_col_per_s": m * g.nnz * d / (ms / 1e3),
+                                "cheb_step_us": avg_s * 1e6, "cheb_step_GBs": per_launch / avg_s / 1e9,
+                                "cheb_step_frac_hbm": per_launch / avg_s / 1e9 / peak}
+    for name in ("f32", "bf16"):
+        out["storage"][name]["rel_err_vs_f64"] = float(torch.linalg.norm(ys[name] - ys["f64"]) /
+                                                       torch.linalg.norm(ys["f64"]))
+    labs = {}
+    for name, st in (("f32", csc.F32), ("bf16", csc.BF16)):
+        t0 = time.perf_counter()
+        lab, info = csc.csc_cluster(h, k, m=m, d=d, d_pad=d_pad, storage=st, seed=args.seed)
+        torch.cuda.synchronize()
+        out["storage"][name]["csc_seconds"] = time.perf_counter() - t0
+        out["storage"][name]["cg_iters"] = info.cg.iters
+        labs[name] = lab.cpu().numpy()
+    out["ari_bf16_vs_f32_labels"] = adjusted_rand(labs["bf16"], labs["f32"])
+    out["autotuned_shapes"] = csc.csc_graph_tuned_shapes(h)
+    print(json.dumps(out), flush=True)
+    h.close()
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -395,6 +457,11 @@ def main():
         world = 1
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     w = WORKLOADS[args.workload]
+    if args.precision:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        return run_precision(args, w)
     if args.impl == "reference":
         return run_reference(args, w, rank, world)
     return run_ours(args, w, rank, world, local_rank)

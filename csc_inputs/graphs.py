@@ -207,8 +207,17 @@ def chung_lu_weights(n: int, exponent: float = 2.1, mean: float = 6.0, w_min: fl
     return w, w_max * w_min
 
 
+def _components(n: int, src: np.ndarray, dst: np.ndarray) -> np.ndarray:
+    """Connected-component label of every node (union-find over the edge list)."""
+    import scipy.sparse as sp
+    import scipy.sparse.csgraph as csg
+
+    a = sp.coo_matrix((np.ones(src.size), (src, dst)), shape=(n, n))
+    return csg.connected_components(a, directed=False)[1]
+
+
 def chung_lu(n: int, exponent: float = 2.1, mean: float = 6.0, seed: int = 0,
-             min_degree_one: bool = True) -> CSRGraph:
+             min_degree_one: bool = True, connect: bool = True) -> CSRGraph:
     """Chung-Lu graph with p_ij = min(1, w_i w_j / sum(w)), drawn exactly.
 
     Miller-Hagberg: with weights sorted descending, each source u walks the
@@ -216,7 +225,10 @@ def chung_lu(n: int, exponent: float = 2.1, mean: float = 6.0, seed: int = 0,
     accepts with probability q/p.  All sources advance together, so the cost
     is O(n + #edges) numpy work.  With ``min_degree_one`` every node left
     isolated gets one edge to a node drawn with probability proportional to
-    its weight, so the minimum degree is 1.
+    its weight, so the minimum degree is 1.  With ``connect`` every connected
+    component other than the largest gets one more edge, from a node drawn
+    uniformly in it to a node of the largest component drawn with probability
+    proportional to its weight, so the graph is connected.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     w_asc, w_max = chung_lu_weights(n, exponent, mean)
@@ -265,6 +277,23 @@ def chung_lu(n: int, exponent: float = 2.1, mean: float = 6.0, seed: int = 0,
             tgt[same] = (tgt[same] + 1) % n
             src = np.concatenate([src, iso])
             dst = np.concatenate([dst, tgt])
+    if connect and n > 1:
+        comp = _components(n, src, dst)
+        sizes = np.bincount(comp)
+        giant = int(np.argmax(sizes))
+        others = np.nonzero(np.arange(sizes.size) != giant)[0]
+        if others.size:
+            # one node per small component, uniformly within it
+            order = np.argsort(comp, kind="stable")
+            starts = np.concatenate([[0], np.cumsum(sizes)])
+            pick = starts[others] + (rng.random(others.size) * sizes[others]).astype(np.int64)
+            a_nodes = order[pick]
+            gnodes = np.nonzero(comp == giant)[0]
+            cdf = np.cumsum(w_asc[gnodes]) / np.sum(w_asc[gnodes])
+            b_nodes = gnodes[np.minimum(np.searchsorted(cdf, rng.random(others.size), side="right"),
+                                        gnodes.size - 1)]
+            src = np.concatenate([src, a_nodes])
+            dst = np.concatenate([dst, b_nodes])
     return from_edges(n, src, dst, None,
                       dict(kind="chung_lu", n=n, exponent=exponent, mean=mean,
                            w_max=float(w_max), seed=seed))

@@ -167,10 +167,21 @@ CSC_API csc_status csc_graph_info(csc_graph g, int64_t* N, int64_t* nnz, int32_t
  * kind (1 = Chebyshev step, 2 = moment step, 3 = CG products), storage width and
  * column count, by timing every compiled shape on the handle's graph.  Entry i
  * (0-based) is written to kind, dtype_bytes (4 fp32, 2 bf16, 8 fp64), columns and
- * shape[5] = {lanes per row G, vectors per lane NT, threads per CTA, row ranges P,
- * column tiles}.  Host outputs (any may be NULL).  CSC_E_INVALID when i is out of range. */
+ * shape[6] = {lanes per row G, vectors per lane NT, threads per CTA, row ranges P,
+ * column tiles, shared-memory window rows (0: none)}.  Host outputs (any may be
+ * NULL).  CSC_E_INVALID when i is out of range. */
 CSC_API csc_status csc_graph_tuned_shape(csc_graph g, int32_t i, int32_t* kind, int32_t* dtype_bytes,
                                          int32_t* columns, int32_t* shape);
+
+/* csc_graph_pin_shape -- fix the launch shape of one kernel kind on this handle
+ * instead of tuning it (reproducible timings; tests of every compiled shape).
+ * kind, dtype_bytes, columns and shape[6] as in csc_graph_tuned_shape (host).
+ * (G, NT) must be a compiled pair, threads 256 or 512, tiles = ceil(vectors per
+ * row / (G NT)); a window (kind 1 only) needs tiles = 1 and fits shared memory.
+ * Errors: CSC_E_INVALID (no side effects); an uncompiled (G, NT) surfaces as
+ * CSC_E_UNSUPPORTED at the next launch. */
+CSC_API csc_status csc_graph_pin_shape(csc_graph g, int32_t kind, int32_t dtype_bytes, int32_t columns,
+                                       const int32_t* shape);
 
 /* csc_graph_degrees -- D_ii of Sec. 2.1 (integer edge counts, bit-exact) in
  * original node order.  deg_out: host int32[N].  Synchronizes `stream`. */

@@ -26,6 +26,7 @@ from .api import (  # noqa: F401
     csc_graph_create,
     csc_graph_create_batched,
     csc_graph_degrees,
+    csc_graph_pin_shape,
     csc_graph_tuned_shapes,
     csc_interpolate,
     csc_kmeans_reduced,

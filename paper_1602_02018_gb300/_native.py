@@ -67,6 +67,7 @@ _SIGNATURES = {
     "csc_graph_info": [c_void_p, P(c_int64), P(c_int64), P(c_int32)],
     "csc_graph_degrees": [c_void_p, c_void_p, c_void_p],
     "csc_graph_tuned_shape": [c_void_p, c_int32, P(c_int32), P(c_int32), P(c_int32), c_void_p],
+    "csc_graph_pin_shape": [c_void_p, c_int32, c_int32, c_int32, c_void_p],
     "csc_chebyshev_coefficients": [c_double, c_int32, c_uint32, c_void_p],
     "csc_filter_random_signals": [c_void_p, c_double, c_int32, c_int32, c_int32, c_uint64, c_int32, c_void_p,
                                   c_void_p, c_uint32, c_void_p],

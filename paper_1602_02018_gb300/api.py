@@ -117,14 +117,22 @@ def csc_graph_tuned_shapes(g: Graph) -> list:
     kinds = {1: "cheb_step", 2: "mom_step", 3: "cg"}
     while True:
         kind, db, cols = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-        shape = (ctypes.c_int32 * 5)()
+        shape = (ctypes.c_int32 * 6)()
         if lib().csc_graph_tuned_shape(g.handle, i, ctypes.byref(kind), ctypes.byref(db), ctypes.byref(cols),
                                        shape) != nat.CSC_OK:
             break
         out.append(dict(kernel=kinds.get(kind.value, str(kind.value)), dtype_bytes=db.value, columns=cols.value,
-                        G=shape[0], NT=shape[1], threads=shape[2], P=shape[3], tiles=shape[4]))
+                        G=shape[0], NT=shape[1], threads=shape[2], P=shape[3], tiles=shape[4], win=shape[5]))
         i += 1
     return out
+
+
+def csc_graph_pin_shape(g: Graph, kernel: str, dtype_bytes: int, columns: int, G: int, NT: int, threads: int,
+                        P: int, tiles: int, win: int = 0) -> None:
+    """Fix a launch shape on this handle instead of tuning it."""
+    kind = {"cheb_step": 1, "mom_step": 2, "cg": 3}[kernel]
+    shape = (ctypes.c_int32 * 6)(G, NT, threads, P, tiles, win)
+    check(lib().csc_graph_pin_shape(g.handle, kind, dtype_bytes, columns, shape), "csc_graph_pin_shape")
 
 
 def csc_chebyshev_coefficients(lambda_c: float, m: int, flags: int = 0) -> np.ndarray:

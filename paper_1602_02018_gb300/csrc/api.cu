@@ -95,8 +95,9 @@ csc_status get_partition(Graph* g, int P, const int32_t** out) {
         return CSC_OK;
     }
     const int64_t N = g->N;
-    const std::vector<int32_t>& rp = g->h_row_ptr;
-    // cost(r) = rp[r] + 2r is nondecreasing: boundary b = first row with cost >= b * total / P
+    const std::vector<int64_t>& rp = g->h_light;  // heavy rows' edges are swept elsewhere
+    // cost(r) = light edges before r + 2r is nondecreasing: boundary b = first row with
+    // cost >= b * total / P
     const double total = (double)rp[N] + 2.0 * (double)N;
     std::vector<int32_t> bounds(P + 1);
     bounds[0] = 0;
@@ -122,6 +123,57 @@ csc_status get_partition(Graph* g, int P, const int32_t** out) {
     }
     CSC_CUDA_TRY(cudaMemcpy(d, bounds.data(), (P + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     g->parts[P] = d;
+    g->h_parts[P] = bounds;
+    *out = d;
+    return CSC_OK;
+}
+
+csc_status get_windows(Graph* g, int P, int W, const int32_t** out) {
+    auto it = g->wins.find({P, W});
+    if (it != g->wins.end()) {
+        *out = it->second;
+        return CSC_OK;
+    }
+    const int32_t* dp = nullptr;
+    CSC_TRY(get_partition(g, P, &dp));
+    const std::vector<int32_t>& b = g->h_parts[P];
+    const std::vector<int32_t>& rp = g->h_row_ptr;
+    const int64_t N = g->N;
+    std::vector<int32_t> cols_host;
+    CSC_TRY([&]() -> csc_status {
+        cols_host.resize(g->nnz);
+        if (g->nnz)
+            CSC_CUDA_TRY(cudaMemcpy(cols_host.data(), g->col_idx, g->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        return CSC_OK;
+    }());
+    std::vector<int32_t> starts(P), buf;
+    for (int x = 0; x < P; ++x) {
+        buf.assign(cols_host.begin() + rp[b[x]], cols_host.begin() + rp[b[x + 1]]);
+        std::sort(buf.begin(), buf.end());
+        // the window [c, c + W) starting at a neighbour column that holds the most neighbours
+        int64_t best = -1, best_start = b[x];
+        size_t j = 0;
+        for (size_t i = 0; i < buf.size(); ++i) {
+            while (j < buf.size() && buf[j] < (int64_t)buf[i] + W) ++j;
+            if ((int64_t)(j - i) > best) {
+                best = (int64_t)(j - i);
+                best_start = buf[i];
+            }
+        }
+        int64_t w0 = best_start;
+        if (w0 + W > N) w0 = N - W;
+        if (w0 < 0) w0 = 0;
+        starts[x] = (int32_t)w0;
+    }
+    int32_t* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, P * sizeof(int32_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc for window starts: %s", cudaGetErrorString(e));
+        return CSC_E_OOM;
+    }
+    CSC_CUDA_TRY(cudaMemcpy(d, starts.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice));
+    g->wins[{P, W}] = d;
     *out = d;
     return CSC_OK;
 }
@@ -318,6 +370,9 @@ static void free_graph(Graph* g) {
     cudaFree(g->graph_of_row);
     for (auto& b : g->ws) cudaFree(b.ptr);
     for (auto& kv : g->parts) cudaFree(kv.second);
+    for (auto& kv : g->wins) cudaFree(kv.second);
+    cudaFree(g->dev_err);
+    cudaFree(g->heavy);
     for (auto& e : g->ev)
         if (e) cudaEventDestroy(e);
     if (g->pinned) cudaFreeHost(g->pinned);
@@ -351,6 +406,18 @@ static csc_status upload(Graph* g, const HostCSR& h, const std::vector<int32_t>*
     std::vector<int32_t>& rp32 = g->h_row_ptr;
     rp32.resize(N + 1);
     for (int64_t i = 0; i <= N; ++i) rp32[i] = (int32_t)h.rp[i];
+    std::vector<int32_t> heavy;
+    g->h_light.assign(N + 1, 0);
+    for (int64_t i = 0; i < N; ++i) {
+        const int64_t dg = h.rp[i + 1] - h.rp[i];
+        if (dg > kHeavyRow) heavy.push_back((int32_t)i);
+        g->h_light[i + 1] = g->h_light[i] + (dg > kHeavyRow ? 0 : dg);
+    }
+    g->n_heavy = (int)heavy.size();
+    if (!heavy.empty()) {
+        CSC_TRY(dev_alloc(&g->heavy, heavy.size()));
+        CSC_CUDA_TRY(cudaMemcpy(g->heavy, heavy.data(), heavy.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     CSC_TRY(dev_alloc(&g->row_ptr, N + 1));
     CSC_TRY(dev_alloc(&g->col_idx, nnz));
     CSC_TRY(dev_alloc(&g->dinv, N));
@@ -372,6 +439,8 @@ static csc_status upload(Graph* g, const HostCSR& h, const std::vector<int32_t>*
         CSC_CUDA_TRY(cudaMemcpyAsync(g->iperm, iperm.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     }
     CSC_CUDA_TRY(cudaMallocHost((void**)&g->pinned, 4096 * sizeof(double)));
+    CSC_TRY(dev_alloc(&g->dev_err, 1));
+    CSC_CUDA_TRY(cudaMemsetAsync(g->dev_err, 0, sizeof(int), s));
     for (auto& e : g->ev) CSC_CUDA_TRY(cudaEventCreate(&e));
     CSC_TRY(launch_degrees(g, s));
     CSC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -589,7 +658,48 @@ csc_status csc_graph_tuned_shape(csc_graph g, int32_t i, int32_t* kind, int32_t*
         shape[2] = it->second.threads;
         shape[3] = it->second.P;
         shape[4] = it->second.tiles;
+        shape[5] = it->second.win;
     }
+    return CSC_OK;
+}
+
+csc_status csc_graph_pin_shape(csc_graph g, int32_t kind, int32_t dtype_bytes, int32_t columns,
+                               const int32_t* shape) {
+    clear_error();
+    CSC_TRY(check_graph(g));
+    if (!shape || kind < 1 || kind > 3 || columns < 1 || shape[0] < 1 || shape[1] < 1 ||
+        (shape[2] != 256 && shape[2] != 512) || shape[3] < 1 || shape[4] < 1 || shape[5] < 0 ||
+        (kind != 1 && shape[5] != 0) || (shape[5] > 0 && shape[4] != 1) || shape[5] > g->N) {
+        set_error("csc_graph_pin_shape: invalid shape");
+        return CSC_E_INVALID;
+    }
+    const int vec_bytes = 16;
+    const int elem = kind == 3 ? 4 : dtype_bytes;
+    if (elem != 2 && elem != 4 && elem != 8) {
+        set_error("csc_graph_pin_shape: dtype_bytes must be 2, 4 or 8");
+        return CSC_E_INVALID;
+    }
+    const int nv = (columns * elem + vec_bytes - 1) / vec_bytes;
+    const int cap = shape[0] * shape[1];
+    if ((nv + cap - 1) / cap != shape[4]) {
+        set_error("csc_graph_pin_shape: %d column tiles do not match %d columns at G*NT = %d", shape[4], columns, cap);
+        return CSC_E_INVALID;
+    }
+    if (shape[5] > 0 && 128 + (size_t)shape[5] * columns * elem > 227 * 1024) {
+        set_error("csc_graph_pin_shape: window of %d rows exceeds shared memory", shape[5]);
+        return CSC_E_INVALID;
+    }
+    LaunchCfg c;
+    c.G = shape[0];
+    c.NT = shape[1];
+    c.threads = shape[2];
+    c.P = shape[3];
+    c.tiles = shape[4];
+    c.win = shape[5];
+    const uint64_t key = kind == 3 ? ((3ull << 48) | (uint64_t)(uint32_t)columns)
+                                   : (((uint64_t)kind << 48) | ((uint64_t)(dtype_bytes & 0xff) << 40) |
+                                      (uint64_t)(uint32_t)columns);
+    g->tuned[key] = c;
     return CSC_OK;
 }
 
@@ -852,6 +962,14 @@ csc_status csc_cluster(csc_graph g, const csc_params* p, int32_t* labels_out, cs
     if (ce != cudaSuccess) {
         set_error("csc_cluster: %s", cudaGetErrorString(ce));
         return done(CSC_E_CUDA);
+    }
+    {
+        int derr = 0;
+        if (cudaMemcpy(&derr, g->dev_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && derr) {
+            cudaMemset(g->dev_err, 0, sizeof(int));
+            set_error("csc_cluster: a bounded device wait gave up (the results were computed without it)");
+            st = CSC_E_DEVICE_TIMEOUT;
+        }
     }
     cudaEventElapsedTime(&local.ms_lambda, e0, e1);
     cudaEventElapsedTime(&local.ms_filter, e1, e2);

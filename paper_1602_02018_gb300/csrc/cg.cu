@@ -42,10 +42,11 @@ struct KSum {
 
 // Per-block, per-column fp64 partial sums of NS quantities: threads of equal lane
 // across the block's row groups are summed in group order and written to
-// partials[(q * gridDim.x + blockIdx.x) * ldp + col0 + c].
+// partials[(q * nslots + slot) * ldp + col0 + c].
 template <int G, int NT, int NS>
 __device__ __forceinline__ void block_column_partials(KSum (&acc)[NS][NT][4], int lane, int col0, int tcols,
-                                                      int64_t ldp, double* __restrict__ partials) {
+                                                      int64_t ldp, double* __restrict__ partials, int64_t slot,
+                                                      int64_t nslots) {
     constexpr int MAXGROUPS = kCgMaxThreads / G;
     constexpr int COLS = G * NT * 4;
     __shared__ double red[MAXGROUPS * COLS];
@@ -61,7 +62,7 @@ __device__ __forceinline__ void block_column_partials(KSum (&acc)[NS][NT][4], in
         for (int c = threadIdx.x; c < COLS && c < tcols; c += blockDim.x) {
             double sum = 0.0;
             for (int i = 0; i < groups; ++i) sum += red[i * COLS + c];
-            partials[((int64_t)q * gridDim.x + blockIdx.x) * ldp + col0 + c] = sum;
+            partials[((int64_t)q * nslots + slot) * ldp + col0 + c] = sum;
         }
     }
 }
@@ -79,64 +80,123 @@ __device__ __forceinline__ void block_column_partials(KSum (&acc)[NS][NT][4], in
 //   !WIN (middle products, scaled input v): v' = v - D^-1 W v
 // so only the first product loads per-edge weights.
 template <int G, int NT, bool WIN>
+__device__ __forceinline__ void lap_epilogue(int row, int lane, int col0, int tcols, float (&acc)[NT][4],
+                                             const float* __restrict__ dinv, const float* __restrict__ invdeg,
+                                             const float* __restrict__ in, float* __restrict__ out, int64_t ld) {
+    const float di = dinv[row];
+    const float sc = di > 0.f ? di : 1.f;
+    const float f = WIN ? di : invdeg[row];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const int cl = (t * G + lane) * 4;
+        if (cl >= tcols) continue;
+        const int64_t o = (int64_t)row * ld + col0 + cl;
+        float x[4];
+        StoreTraits<float>::load(in + o, x);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) x[v] = WIN ? sc * (x[v] - f * acc[t][v]) : x[v] - f * acc[t][v];
+        StoreTraits<float>::store(out + o, x);
+    }
+}
+
+// Rows of degree > kHeavyRow are left to lap_heavy_kernel.
+template <int G, int NT, bool WIN>
 __global__ void __launch_bounds__(kCgMaxThreads)
 lap_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ dinv,
            const float* __restrict__ invdeg, const float* __restrict__ in, float* __restrict__ out,
            const int32_t* __restrict__ part, int ncols, int64_t ld) {
     CG_TILE(G, NT)
     CG_ROWS(G) {
+        const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
+        if (e1 - e0 > kHeavyRow) continue;
         float acc[NT][4];
-        gather_row<float, G, NT, WIN, float>(rp, ci, dinv, in + col0, ld, row, lane, tcols, acc);
-        const float di = dinv[row];
-        const float sc = di > 0.f ? di : 1.f;
-        const float f = WIN ? di : invdeg[row];
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const int cl = (t * G + lane) * 4;
-            if (cl >= tcols) continue;
-            const int64_t o = (int64_t)row * ld + col0 + cl;
-            float x[4];
-            StoreTraits<float>::load(in + o, x);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) x[v] = WIN ? sc * (x[v] - f * acc[t][v]) : x[v] - f * acc[t][v];
-            StoreTraits<float>::store(out + o, x);
-        }
+        gather_range<float, G, NT, WIN, float>(e0, e1, ci, dinv, in + col0, ld, lane, tcols, acc);
+        lap_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, invdeg, in, out, ld);
     }
+}
+
+// Heavy rows: one CTA of kHeavyThreads per row (CTA x = heavy row, CTA y = column tile).
+template <int G, int NT, bool WIN>
+__global__ void __launch_bounds__(kHeavyThreads)
+lap_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ dinv,
+                 const float* __restrict__ invdeg, const float* __restrict__ in, float* __restrict__ out,
+                 const int32_t* __restrict__ heavy, int ncols, int64_t ld) {
+    const int lane = threadIdx.x % G;
+    const int col0 = blockIdx.y * (G * NT * 4);
+    const int tcols = min(G * NT * 4, ncols - col0);
+    const int row = heavy[blockIdx.x];
+    float acc[NT][4];
+    gather_heavy<float, G, NT, WIN, float>(__ldg(rp + row), __ldg(rp + row + 1), ci, dinv, in + col0, ld, lane, tcols,
+                                           acc);
+    if (threadIdx.x < G) lap_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, invdeg, in, out, ld);
 }
 
 // Ap = mask * p + gamma L t with per-column partials of <p, Ap>; the last product of
 // the chain.  WIN: t = p itself (g(L) = L); else tin = s t from the chain.
 template <int G, int NT, bool WIN>
+__device__ __forceinline__ void lap_ax_epilogue(int row, int lane, int col0, int tcols, float (&acc)[NT][4],
+                                                const float* __restrict__ dinv, const float* __restrict__ sqdeg,
+                                                const float* __restrict__ tin, const float* __restrict__ p,
+                                                const float* __restrict__ mask, float gamma, float* __restrict__ Ap,
+                                                int64_t ld, KSum (&dot)[1][NT][4]) {
+    const float di = dinv[row];
+    const float back = WIN ? 1.f : sqdeg[row];
+    const float mk = mask[row];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const int cl = (t * G + lane) * 4;
+        if (cl >= tcols) continue;
+        const int64_t o = (int64_t)row * ld + col0 + cl;
+        float tt[4], pp[4], a[4];
+        StoreTraits<float>::load(tin + o, tt);
+        StoreTraits<float>::load(p + o, pp);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            a[v] = mk * pp[v] + gamma * (tt[v] * back - di * acc[t][v]);
+            dot[0][t][v].add(pp[v] * a[v]);
+        }
+        StoreTraits<float>::store(Ap + o, a);
+    }
+}
+
+// <p, A p> partial slots: [0, gridDim.x) for the row ranges, then one per heavy
+// row (lap_ax_heavy_kernel); nslots counts both.
+template <int G, int NT, bool WIN>
 __global__ void __launch_bounds__(kCgMaxThreads)
 lap_ax_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ dinv,
               const float* __restrict__ sqdeg, const float* __restrict__ tin, const float* __restrict__ p,
               const float* __restrict__ mask, float gamma, float* __restrict__ Ap, const int32_t* __restrict__ part,
-              int ncols, int64_t ld, double* __restrict__ partials) {
+              int ncols, int64_t ld, double* __restrict__ partials, int nslots) {
     CG_TILE(G, NT)
     KSum dot[1][NT][4];
     CG_ROWS(G) {
+        const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
+        if (e1 - e0 > kHeavyRow) continue;
         float acc[NT][4];
-        gather_row<float, G, NT, WIN, float>(rp, ci, dinv, tin + col0, ld, row, lane, tcols, acc);
-        const float di = dinv[row];
-        const float back = WIN ? 1.f : sqdeg[row];
-        const float mk = mask[row];
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const int cl = (t * G + lane) * 4;
-            if (cl >= tcols) continue;
-            const int64_t o = (int64_t)row * ld + col0 + cl;
-            float tt[4], pp[4], a[4];
-            StoreTraits<float>::load(tin + o, tt);
-            StoreTraits<float>::load(p + o, pp);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                a[v] = mk * pp[v] + gamma * (tt[v] * back - di * acc[t][v]);
-                dot[0][t][v].add(pp[v] * a[v]);
-            }
-            StoreTraits<float>::store(Ap + o, a);
-        }
+        gather_range<float, G, NT, WIN, float>(e0, e1, ci, dinv, tin + col0, ld, lane, tcols, acc);
+        lap_ax_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, sqdeg, tin, p, mask, gamma, Ap, ld, dot);
     }
-    block_column_partials<G, NT, 1>(dot, lane, col0, tcols, ld, partials);
+    block_column_partials<G, NT, 1>(dot, lane, col0, tcols, ld, partials, blockIdx.x, nslots);
+}
+
+template <int G, int NT, bool WIN>
+__global__ void __launch_bounds__(kHeavyThreads)
+lap_ax_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ dinv,
+                    const float* __restrict__ sqdeg, const float* __restrict__ tin, const float* __restrict__ p,
+                    const float* __restrict__ mask, float gamma, float* __restrict__ Ap,
+                    const int32_t* __restrict__ heavy, int ncols, int64_t ld, double* __restrict__ partials,
+                    int slot_base, int nslots) {
+    const int lane = threadIdx.x % G;
+    const int col0 = blockIdx.y * (G * NT * 4);
+    const int tcols = min(G * NT * 4, ncols - col0);
+    const int row = heavy[blockIdx.x];
+    float acc[NT][4];
+    gather_heavy<float, G, NT, WIN, float>(__ldg(rp + row), __ldg(rp + row + 1), ci, dinv, tin + col0, ld, lane,
+                                           tcols, acc);
+    KSum dot[1][NT][4];
+    if (threadIdx.x < G)
+        lap_ax_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, sqdeg, tin, p, mask, gamma, Ap, ld, dot);
+    block_column_partials<G, NT, 1>(dot, lane, col0, tcols, ld, partials, slot_base + blockIdx.x, nslots);
 }
 
 // x += alpha p; r -= alpha Ap; partials of <r, r/P> and <r, r>.  alpha == nullptr: no update.
@@ -185,7 +245,7 @@ cg_update_kernel(float* __restrict__ x, float* __restrict__ r, const float* __re
             }
         }
     }
-    block_column_partials<G, NT, 2>(dots, lane, col0, tcols, ld, partials);
+    block_column_partials<G, NT, 2>(dots, lane, col0, tcols, ld, partials, blockIdx.x, gridDim.x);
 }
 
 // p = r/P + beta p
@@ -242,7 +302,7 @@ residual_kernel(const float* __restrict__ Ax, const int32_t* __restrict__ slab, 
             }
         }
     }
-    block_column_partials<G, NT, 1>(acc, lane, col0, tcols, ld, partials);
+    block_column_partials<G, NT, 1>(acc, lane, col0, tcols, ld, partials, blockIdx.x, gridDim.x);
 }
 
 // column norms^2 of x (partials)
@@ -263,7 +323,7 @@ colnorm_kernel(const float* __restrict__ x, const int32_t* __restrict__ part, in
             for (int v = 0; v < 4; ++v) acc[0][t][v].add(a[v] * a[v]);
         }
     }
-    block_column_partials<G, NT, 1>(acc, lane, col0, tcols, ld, partials);
+    block_column_partials<G, NT, 1>(acc, lane, col0, tcols, ld, partials, blockIdx.x, gridDim.x);
 }
 
 // Column state (fp64, length k each): rz, bnorm2, alpha, beta, active flags.
@@ -475,6 +535,22 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         set_error("csc_interpolate: no launch shape for k = %d", k);
         return CSC_E_UNSUPPORTED;
     }
+    // a shape pinned on the handle or tuned earlier is used as is: its row-range count
+    // sizes the per-block partials too
+    const uint64_t tkey = (3ull << 48) | (uint64_t)(uint32_t)ld;
+    LaunchCfg known;
+    bool have_known = false;
+    {
+        auto it = g->tuned.find(tkey);
+        if (it != g->tuned.end()) {
+            known = it->second;
+            have_known = true;
+        } else if (tune_cache_get(g, tkey, &known)) {
+            g->tuned[tkey] = known;
+            have_known = true;
+        }
+        if (have_known) max_p = std::max(max_p, known.P);
+    }
     const size_t blk = (size_t)N * ld * sizeof(float);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -485,7 +561,8 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const size_t o_x = take(blk), o_r = take(blk), o_p = take(blk), o_ap = take(blk), o_t1 = take(blk),
                  o_t2 = take(blk);
     const size_t o_mask = take((size_t)N * 4), o_pinv = take((size_t)N * 4), o_slab = take((size_t)N * 4);
-    const size_t o_part = take((size_t)2 * max_p * ld * 8);
+    // two quantities per row-range block; <p, A p> also has one slot per heavy row
+    const size_t o_part = take((size_t)2 * (max_p + g->n_heavy) * ld * 8);
     const size_t o_state = take((size_t)ld * 8 * 6 + (size_t)ld * 4 + 64);
     void* base = nullptr;
     CSC_TRY(ws_get(g, WS_CG, off, &base));
@@ -527,12 +604,9 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     // reading r and writing scratch; shared by every kernel of the solve
     LaunchCfg cfg;
     {
-        const uint64_t key = (3ull << 48) | (uint64_t)(uint32_t)ld;
-        auto it = g->tuned.find(key);
-        if (it != g->tuned.end()) {
-            cfg = it->second;
-        } else if (tune_cache_get(g, key, &cfg)) {
-            g->tuned[key] = cfg;
+        const uint64_t key = tkey;
+        if (have_known) {
+            cfg = known;
         } else {
             const bool prof = g_prof_enabled;
             g_prof_enabled = false;  // tuning launches are not part of the measured work
@@ -567,11 +641,17 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const dim3 grid(cfg.P, cfg.tiles);
     const int th = cfg.threads;
     const int P = cfg.P;
+    const int H = (int)g->n_heavy;
+    const int PH = P + H;  // <p, A p> partial slots
+    const dim3 hgrid(H > 0 ? H : 1, cfg.tiles);
 
     // algorithmic bytes per launch of each CG kernel (fp32 N x ld blocks)
     const double blkb = (double)N * ld * 4.0;
     const double csr_b = 4.0 * g->nnz + 4.0 * (N + 1) + 4.0 * N;
     const double scal_b = 8.0 * P * ld;
+    const double scal_ax = 8.0 * PH * ld;
+    // share of the sparse bytes that falls on heavy rows (launched separately)
+    const double heavy_frac = g->nnz > 0 ? (double)(g->nnz - g->h_light.back()) / (double)g->nnz : 0.0;
     const int kb = ceil_div(k, 32);
     const dim3 rb(32, 16);
     CG_SWITCH(cfg, CSC_KLAUNCH("cg_update", blkb + 4.0 * N, s,
@@ -593,28 +673,53 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         float* bufs[2] = {t1, t2};
         for (int q = 0; q < g_power - 1; ++q) {
             float* o = bufs[q & 1];
-            // CSR + row factors, the input block gathered once, the output block written
-            if (q == 0)
-                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", csr_b + 2 * blkb, s,
+            // CSR + row factors, the input block gathered once, the output block written;
+            // heavy rows (if any) in their own launch, bytes split by their edge share
+            const double lb = csr_b + 2 * blkb;
+            if (q == 0) {
+                if (H > 0)
+                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * heavy_frac, s,
+                                               lap_heavy_kernel<G_, NT_, true><<<hgrid, kHeavyThreads, 0, s>>>(
+                                                   g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, g->heavy, ld,
+                                                   ld)));
+                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * (1.0 - heavy_frac), s,
                                            lap_kernel<G_, NT_, true><<<grid, th, 0, s>>>(
                                                g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, rpart, ld, ld)));
-            else
-                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", csr_b + 2 * blkb, s,
+            } else {
+                if (H > 0)
+                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * heavy_frac, s,
+                                               lap_heavy_kernel<G_, NT_, false><<<hgrid, kHeavyThreads, 0, s>>>(
+                                                   g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, g->heavy, ld,
+                                                   ld)));
+                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * (1.0 - heavy_frac), s,
                                            lap_kernel<G_, NT_, false><<<grid, th, 0, s>>>(
                                                g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, rpart, ld, ld)));
+            }
             cur = o;
         }
         // CSR + row factors + mask, t gathered once, p read, Ap written
-        if (g_power == 1)
-            CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", csr_b + 4.0 * N + 3 * blkb + scal_b, s,
+        const double ab = csr_b + 4.0 * N + 3 * blkb + scal_ax;
+        if (g_power == 1) {
+            if (H > 0)
+                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * heavy_frac, s,
+                                           lap_ax_heavy_kernel<G_, NT_, true><<<hgrid, kHeavyThreads, 0, s>>>(
+                                               g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma,
+                                               Ap, g->heavy, ld, ld, part, P, PH)));
+            CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * (1.0 - heavy_frac), s,
                                        lap_ax_kernel<G_, NT_, true><<<grid, th, 0, s>>>(
                                            g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
-                                           rpart, ld, ld, part)));
-        else
-            CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", csr_b + 4.0 * N + 3 * blkb + scal_b, s,
+                                           rpart, ld, ld, part, PH)));
+        } else {
+            if (H > 0)
+                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * heavy_frac, s,
+                                           lap_ax_heavy_kernel<G_, NT_, false><<<hgrid, kHeavyThreads, 0, s>>>(
+                                               g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma,
+                                               Ap, g->heavy, ld, ld, part, P, PH)));
+            CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * (1.0 - heavy_frac), s,
                                        lap_ax_kernel<G_, NT_, false><<<grid, th, 0, s>>>(
                                            g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
-                                           rpart, ld, ld, part)));
+                                           rpart, ld, ld, part, PH)));
+        }
         return CSC_OK;
     };
     int it = 0;
@@ -624,7 +729,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         const int batch = std::min(check_every, max_iter - it);
         for (int q = 0; q < batch; ++q) {
             CSC_TRY(apply_A(p));
-            CSC_KLAUNCH("cg_scalar", scal_b, s, cg_alpha_kernel<<<kb, rb, 0, s>>>(part, P, k, ld, st));
+            CSC_KLAUNCH("cg_scalar", scal_ax, s, cg_alpha_kernel<<<kb, rb, 0, s>>>(part, PH, k, ld, st));
             // x, r, p, Ap read; x, r written
             CG_SWITCH(cfg, CSC_KLAUNCH("cg_update", 6 * blkb + 4.0 * N + 2 * scal_b, s,
                                        cg_update_kernel<G_, NT_><<<grid, th, 0, s>>>(x, r, p, Ap, st.alpha, pinv, rpart,

@@ -65,6 +65,11 @@ void count_launch();
         CSC_LAUNCH_CHECK();                                                                 \
     } while (0)
 
+// Rows with more edges than this ("heavy" rows: the hubs of power-law graphs) are
+// not swept by one lane group of the row-range kernels; a second kernel gives each
+// of them a CTA whose groups split its edge list.
+constexpr int kHeavyRow = 256;
+
 // ------------------------------------------------------------- workspace
 // Scratch slots owned by a graph handle; each grows on demand (cudaMalloc)
 // and lives until the handle is destroyed.
@@ -92,6 +97,7 @@ struct Buffer {
 // (one CTA each per tile) and `tiles` column tiles.
 struct LaunchCfg {
     int G = 0, NT = 0, threads = 0, P = 0, tiles = 1;
+    int win = 0;  // rows of the shared-memory neighbour window (0: none)
 };
 
 struct Graph {
@@ -119,7 +125,13 @@ struct Graph {
     int32_t* graph_of_row = nullptr; // device int32[N]
     Buffer ws[WS_COUNT];
     std::vector<int32_t> h_row_ptr;               // host copy of row_ptr (internal order)
+    std::vector<int64_t> h_light;                 // prefix sums of the edges of non-heavy rows
+    int32_t* heavy = nullptr;                     // device int32[n_heavy]: heavy rows
+    int n_heavy = 0;
     std::map<int, int32_t*> parts;                // P -> device int32[P+1] row-range bounds
+    std::map<int, std::vector<int32_t>> h_parts;  // host copies of the bounds
+    std::map<std::pair<int, int>, int32_t*> wins; // (P, W) -> device int32[P] window starts
+    int* dev_err = nullptr;                       // device error word (bounded waits that gave up)
     std::map<uint64_t, LaunchCfg> tuned;          // (kernel kind, dtype, columns) -> shape
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     double* pinned = nullptr;  // small pinned host staging (4096 doubles)
@@ -135,6 +147,10 @@ void tune_cache_put(const Graph* g, uint64_t key, const LaunchCfg& cfg);
 
 // P contiguous row ranges of about equal cost (edges + 2 per row); cached per P.
 csc_status get_partition(Graph* g, int P, const int32_t** out);
+
+// Start rows of the W-row windows (one per row range of partition P) that cover
+// the most neighbour indices of each range; cached per (P, W).
+csc_status get_windows(Graph* g, int P, int W, const int32_t** out);
 
 // Device helpers exported by the kernel translation units -----------------
 

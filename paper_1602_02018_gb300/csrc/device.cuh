@@ -29,6 +29,11 @@ struct StoreTraits<float> {
         float4 q = __ldg(reinterpret_cast<const float4*>(p));
         v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
     }
+    // generic-address load (global or shared memory)
+    __device__ static inline void load_generic(const float* p, float (&v)[4]) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
     // streaming load (data read once: X_{j-1}, Y)
     __device__ static inline void load_cs(const float* p, float (&v)[4]) {
         float4 q = __ldcs(reinterpret_cast<const float4*>(p));
@@ -61,6 +66,10 @@ struct StoreTraits<__nv_bfloat16> {
         uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
         unpack(q, v);
     }
+    __device__ static inline void load_generic(const __nv_bfloat16* p, float (&v)[8]) {
+        const uint4 q = *reinterpret_cast<const uint4*>(p);
+        unpack(q, v);
+    }
     __device__ static inline void load_cs(const __nv_bfloat16* p, float (&v)[8]) {
         uint4 q = __ldcs(reinterpret_cast<const uint4*>(p));
         unpack(q, v);
@@ -89,6 +98,10 @@ struct StoreTraits<double> {
     static constexpr int VEC = 2;
     __device__ static inline void load(const double* p, double (&v)[2]) {
         double2 q = __ldg(reinterpret_cast<const double2*>(p));
+        v[0] = q.x; v[1] = q.y;
+    }
+    __device__ static inline void load_generic(const double* p, double (&v)[2]) {
+        const double2 q = *reinterpret_cast<const double2*>(p);
         v[0] = q.x; v[1] = q.y;
     }
     __device__ static inline void load_cs(const double* p, double (&v)[2]) {
@@ -177,12 +190,15 @@ __device__ __forceinline__ void acc_vec(double (&acc)[VEC], double w, const doub
 // within the group, so the neighbour-row loads of a chunk issue back to back
 // without a dependent index load in front of each.  Columns >= ncols are
 // skipped (their accumulators stay 0).
-template <typename T, int G, int NT, bool WEIGHTED, typename W>
-__device__ __forceinline__ void gather_row(const int32_t* __restrict__ rp,
-                                           const int32_t* __restrict__ ci,
-                                           const W* __restrict__ wv, const T* __restrict__ X,
-                                           int64_t ld, int row, int lane, int ncols,
-                                           typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC]) {
+//
+// With SWIN, rows w0 .. w0+wn-1 of X (full rows, row stride ld) are also held
+// in shared memory at swin, and neighbours inside that window are read there.
+template <typename T, int G, int NT, bool WEIGHTED, typename W, bool SWIN = false>
+__device__ __forceinline__ void gather_range(int e, const int end, const int32_t* __restrict__ ci,
+                                             const W* __restrict__ wv, const T* __restrict__ X, int64_t ld,
+                                             int lane, int ncols,
+                                             typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC],
+                                             const T* swin = nullptr, int w0 = 0, int wn = 0) {
     using Tr = StoreTraits<T>;
     using A = typename Tr::acc_t;
     constexpr int VEC = Tr::VEC;
@@ -197,8 +213,6 @@ __device__ __forceinline__ void gather_row(const int32_t* __restrict__ rp,
     bool valid[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) valid[t] = ((t * G + lane) * VEC) < ncols;
-    int e = __ldg(rp + row);
-    const int end = __ldg(rp + row + 1);
     for (; e < end; e += CH) {
         int li[J];
         A wi[J];
@@ -210,38 +224,142 @@ __device__ __forceinline__ void gather_row(const int32_t* __restrict__ rp,
             if (WEIGHTED) wi[j] = ok ? A(__ldg(wv + li[j])) : A(0);
         }
         const int cnt = min(CH, end - e);
+        // edges in flight per lane: 8 one-vector rows, or 4 rows of NT >= 2 vectors
+        constexpr int B = NT == 1 ? 8 : 4;
 #pragma unroll
-        for (int q0 = 0; q0 < CH; q0 += 4) {
+        for (int q0 = 0; q0 < CH; q0 += B) {
             if (q0 >= cnt) break;
-            int l[4];
-            A w[4];
+            int l[B];
+            A w[B];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < B; ++u) {
                 const int q = q0 + u;
                 l[u] = __shfl_sync(gmask, li[q / G], q % G, G);
                 if (WEIGHTED) w[u] = __shfl_sync(gmask, wi[q / G], q % G, G);
                 else w[u] = A(1);
             }
             // one address per neighbour row; the tiles of a lane are fixed offsets from it
-            const T* rowp[4];
+            const T* rowp[B];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) rowp[u] = X + (int64_t)l[u] * ld + lane * VEC;
+            for (int u = 0; u < B; ++u) {
+                if (SWIN && (unsigned)(l[u] - w0) < (unsigned)wn)
+                    rowp[u] = swin + (int64_t)(l[u] - w0) * ld + lane * VEC;  // shared-memory copy
+                else
+                    rowp[u] = X + (int64_t)l[u] * ld + lane * VEC;
+            }
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
                 if (!valid[t]) continue;
-                A x[4][VEC];
+                A x[B][VEC];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (q0 + u < cnt) Tr::load(rowp[u] + t * G * VEC, x[u]);
+                for (int u = 0; u < B; ++u) {
+                    if (q0 + u < cnt) {
+                        if (SWIN) Tr::load_generic(rowp[u] + t * G * VEC, x[u]);
+                        else Tr::load(rowp[u] + t * G * VEC, x[u]);
+                    }
                     else
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) x[u][v] = A(0);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) acc_vec<WEIGHTED, VEC>(acc[t], w[u], x[u]);
+                for (int u = 0; u < B; ++u) acc_vec<WEIGHTED, VEC>(acc[t], w[u], x[u]);
             }
         }
     }
+}
+
+// The neighbour sum of a whole row (see gather_range).
+template <typename T, int G, int NT, bool WEIGHTED, typename W, bool SWIN = false>
+__device__ __forceinline__ void gather_row(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                           const W* __restrict__ wv, const T* __restrict__ X, int64_t ld, int row,
+                                           int lane, int ncols,
+                                           typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC],
+                                           const T* swin = nullptr, int w0 = 0, int wn = 0) {
+    gather_range<T, G, NT, WEIGHTED, W, SWIN>(__ldg(rp + row), __ldg(rp + row + 1), ci, wv, X, ld, lane, ncols, acc,
+                                              swin, w0, wn);
+}
+
+// Neighbour sum of a heavy row (see kHeavyRow) by a whole CTA of kHeavyThreads
+// threads: group q takes the q-th contiguous slice of the row's edges; the
+// slices' sums are added in a fixed order (a shuffle tree across the groups of a
+// warp, then the warps in order through shared memory), and group 0 returns the
+// total for its lanes' columns in acc (other groups' acc is unspecified).
+constexpr int kHeavyThreads = 256;
+
+template <typename T, int G, int NT, bool WEIGHTED, typename W>
+__device__ __forceinline__ void gather_heavy(int e0, int e1, const int32_t* __restrict__ ci, const W* __restrict__ wv,
+                                             const T* __restrict__ X, int64_t ld, int lane, int ncols,
+                                             typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC]) {
+    using A = typename StoreTraits<T>::acc_t;
+    constexpr int VEC = StoreTraits<T>::VEC;
+    constexpr int TW = G * NT * VEC;
+    constexpr int WARPS = kHeavyThreads / 32;
+    __shared__ A red[WARPS * TW];
+    const int groups = kHeavyThreads / G;
+    const int q = threadIdx.x / G;
+    const int len = (e1 - e0 + groups - 1) / groups;
+    const int a = min(e1, e0 + q * len), b = min(e1, a + len);
+    gather_range<T, G, NT, WEIGHTED, W>(a, b, ci, wv, X, ld, lane, ncols, acc);
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v)
+#pragma unroll
+            for (int o = G; o < 32; o <<= 1) acc[t][v] += __shfl_xor_sync(0xffffffffu, acc[t][v], o);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) < G)
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) red[w * TW + (t * G + lane) * VEC + v] = acc[t][v];
+    __syncthreads();
+    if (q == 0)
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                A s = A(0);
+                for (int i = 0; i < WARPS; ++i) s += red[i * TW + (t * G + lane) * VEC + v];
+                acc[t][v] = s;
+            }
+}
+
+// ------------------------------------------------------ bulk copies (TMA)
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared bulk copy completing on the mbarrier (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bounded wait for phase `parity` of the mbarrier; false if the limit was reached.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int max_tries) {
+    const uint32_t a = smem_addr(bar);
+    for (int i = 0; i < max_tries; ++i) {
+        uint32_t done = 0;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
 }
 
 // ------------------------------------------------------------ generators

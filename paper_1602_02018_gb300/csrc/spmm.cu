@@ -130,7 +130,59 @@ __global__ void copy_in_kernel(T* __restrict__ X, const float* __restrict__ R, i
 // [part[x], part[x+1]) in order, G lanes per row, so that rows close in the
 // node order -- the neighbours in a community, or in a bandwidth-reduced (RCM)
 // order -- are gathered by the same CTA while they are in its L1; CTA y covers
-// the column tile [y*TW, (y+1)*TW) with TW = G*NT*VEC.
+// the column tile [y*TW, (y+1)*TW) with TW = G*NT*VEC.  Rows with more than
+// kHeavyRow edges are skipped here and done by the *_heavy kernels.
+
+// The per-row update of one order given the row's neighbour sum acc (column tile col0).
+template <typename T, int G, int NT>
+__device__ __forceinline__ void cheb_epilogue(int row, int lane, int col0, int tcols,
+                                              typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC],
+                                              const typename StoreTraits<T>::acc_t* __restrict__ invdeg,
+                                              const typename StoreTraits<T>::acc_t* __restrict__ sqdeg,
+                                              const T* __restrict__ zcur, T* __restrict__ zprev_next,
+                                              typename StoreTraits<T>::acc_t* __restrict__ Y,
+                                              const int32_t* __restrict__ perm, int64_t ld,
+                                              typename StoreTraits<T>::acc_t c0, typename StoreTraits<T>::acc_t c_next,
+                                              int mode) {
+    using Tr = StoreTraits<T>;
+    using A = typename Tr::acc_t;
+    constexpr int VEC = Tr::VEC;
+    const bool first = (mode & 1) != 0, last = (mode & 2) != 0;
+    const A f = (first ? A(-1) : A(-2)) * invdeg[row];
+    const A back = last ? sqdeg[row] : A(1);
+    const int64_t yrow = perm ? (int64_t)perm[row] : (int64_t)row;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const int cl = (t * G + lane) * VEC;
+        if (cl >= tcols) continue;
+        const int c = col0 + cl;
+        A zn[VEC], y[VEC];
+        T* zp_ptr = zprev_next + (int64_t)row * ld + c;
+        A* y_ptr = Y + yrow * ld + c;
+        if (first) {
+            A z0[VEC];
+            Tr::load(zcur + (int64_t)row * ld + c, z0);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v]);
+            Tr::store(zp_ptr, zn);
+            // Y accumulates the stored (for bf16: rounded) values the recurrence continues with
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) y[v] = (c0 * z0[v] + c_next * zn[v]) * back;
+        } else {
+            A zp[VEC];
+            Tr::load_cs(zp_ptr, zp);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v] - zp[v]);
+            Tr::store(zp_ptr, zn);
+            AccIO<A, VEC>::load_cs(y_ptr, y);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) y[v] = fma(c_next, zn[v], y[v]) * back;
+        }
+        // Y is read again only by the next order: evict-first keeps Z_j resident in L2
+        AccIO<A, VEC>::store_cs(y_ptr, y);
+    }
+}
+
 template <typename T, int G, int NT>
 __global__ void __launch_bounds__(512)
 cheb_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -139,55 +191,91 @@ cheb_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                  T* __restrict__ zprev_next, typename StoreTraits<T>::acc_t* __restrict__ Y,
                  const int32_t* __restrict__ perm, const int32_t* __restrict__ part, int ncols, int64_t ld,
                  typename StoreTraits<T>::acc_t c0, typename StoreTraits<T>::acc_t c_next, int mode) {
-    using Tr = StoreTraits<T>;
-    using A = typename Tr::acc_t;
-    constexpr int VEC = Tr::VEC;
+    using A = typename StoreTraits<T>::acc_t;
+    constexpr int VEC = StoreTraits<T>::VEC;
     constexpr int TW = G * NT * VEC;
-    const bool first = (mode & 1) != 0, last = (mode & 2) != 0;
     const int lane = threadIdx.x % G;
     const int col0 = blockIdx.y * TW;
     const int tcols = min(TW, ncols - col0);
     const int r1 = part[blockIdx.x + 1];
     for (int row = part[blockIdx.x] + (int)(threadIdx.x / G); row < r1; row += (int)(blockDim.x / G)) {
+        const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
+        if (e1 - e0 > kHeavyRow) continue;
         A acc[NT][VEC];
-        gather_row<T, G, NT, false, A>(rp, ci, nullptr, zcur + col0, ld, row, lane, tcols, acc);
-        const A f = (first ? A(-1) : A(-2)) * invdeg[row];
-        const A back = last ? sqdeg[row] : A(1);
-        const int64_t yrow = perm ? (int64_t)perm[row] : (int64_t)row;
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const int cl = (t * G + lane) * VEC;
-            if (cl >= tcols) continue;
-            const int c = col0 + cl;
-            A zn[VEC], y[VEC];
-            T* zp_ptr = zprev_next + (int64_t)row * ld + c;
-            A* y_ptr = Y + yrow * ld + c;
-            if (first) {
-                A z0[VEC];
-                Tr::load(zcur + (int64_t)row * ld + c, z0);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v]);
-                Tr::store(zp_ptr, zn);
-                // Y accumulates the stored (for bf16: rounded) values the recurrence continues with
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) y[v] = (c0 * z0[v] + c_next * zn[v]) * back;
-            } else {
-                A zp[VEC];
-                Tr::load_cs(zp_ptr, zp);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v] - zp[v]);
-                Tr::store(zp_ptr, zn);
-                AccIO<A, VEC>::load_cs(y_ptr, y);
-#pragma unroll
-                for (int v = 0; v < VEC; ++v) y[v] = fma(c_next, zn[v], y[v]) * back;
-            }
-            // Y is read again only by the next order: evict-first keeps Z_j resident in L2
-            AccIO<A, VEC>::store_cs(y_ptr, y);
-        }
+        gather_range<T, G, NT, false, A>(e0, e1, ci, nullptr, zcur + col0, ld, lane, tcols, acc);
+        cheb_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, sqdeg, zcur, zprev_next, Y, perm, ld, c0, c_next,
+                                mode);
     }
 }
 
-// Y = c0 * X0 (degree 0)
+// Heavy rows: one CTA (kHeavyThreads threads) per row, its groups splitting the edges.
+template <typename T, int G, int NT>
+__global__ void __launch_bounds__(kHeavyThreads)
+cheb_step_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                       const typename StoreTraits<T>::acc_t* __restrict__ invdeg,
+                       const typename StoreTraits<T>::acc_t* __restrict__ sqdeg, const T* __restrict__ zcur,
+                       T* __restrict__ zprev_next, typename StoreTraits<T>::acc_t* __restrict__ Y,
+                       const int32_t* __restrict__ perm, const int32_t* __restrict__ heavy, int ncols, int64_t ld,
+                       typename StoreTraits<T>::acc_t c0, typename StoreTraits<T>::acc_t c_next, int mode) {
+    using A = typename StoreTraits<T>::acc_t;
+    constexpr int VEC = StoreTraits<T>::VEC;
+    constexpr int TW = G * NT * VEC;
+    const int lane = threadIdx.x % G;
+    const int col0 = blockIdx.y * TW;
+    const int tcols = min(TW, ncols - col0);
+    const int row = heavy[blockIdx.x];
+    A acc[NT][VEC];
+    gather_heavy<T, G, NT, false, A>(__ldg(rp + row), __ldg(rp + row + 1), ci, nullptr, zcur + col0, ld, lane, tcols,
+                                     acc);
+    if (threadIdx.x < G)
+        cheb_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, sqdeg, zcur, zprev_next, Y, perm, ld, c0, c_next,
+                                mode);
+}
+
+// The same order with a shared-memory neighbour window: the CTA first copies rows
+// win[x] .. win[x]+wn-1 of Z_j (full rows, contiguous in memory) into shared memory
+// with bulk asynchronous copies, then reads the neighbours inside that window
+// there.  The wait on the copies is bounded; a CTA that gives up sets *err and
+// reads every neighbour from global memory instead.
+template <typename T, int G, int NT>
+__global__ void __launch_bounds__(512)
+cheb_step_win_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                     const typename StoreTraits<T>::acc_t* __restrict__ invdeg,
+                     const typename StoreTraits<T>::acc_t* __restrict__ sqdeg, const T* __restrict__ zcur,
+                     T* __restrict__ zprev_next, typename StoreTraits<T>::acc_t* __restrict__ Y,
+                     const int32_t* __restrict__ perm, const int32_t* __restrict__ part, int ncols, int64_t ld,
+                     typename StoreTraits<T>::acc_t c0, typename StoreTraits<T>::acc_t c_next, int mode,
+                     const int32_t* __restrict__ win, int wn, int* __restrict__ err) {
+    using A = typename StoreTraits<T>::acc_t;
+    constexpr int VEC = StoreTraits<T>::VEC;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    T* swin = reinterpret_cast<T*>(smem + 128);
+    const int w0 = win[blockIdx.x];
+    const uint32_t total = (uint32_t)((size_t)wn * ld * sizeof(T));
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_expect_tx(bar, total);
+        const char* src = reinterpret_cast<const char*>(zcur + (int64_t)w0 * ld);
+        for (uint32_t off = 0; off < total; off += 65536u)
+            bulk_g2s(reinterpret_cast<char*>(swin) + off, src + off, min(65536u, total - off), bar);
+    }
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    const bool ok = mbar_wait(bar, 0, 1 << 20);
+    if (!ok) atomicOr(err, 1);
+    const int wuse = ok ? wn : 0;
+    const int lane = threadIdx.x % G;
+    const int r1 = part[blockIdx.x + 1];
+    for (int row = part[blockIdx.x] + (int)(threadIdx.x / G); row < r1; row += (int)(blockDim.x / G)) {
+        const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
+        if (e1 - e0 > kHeavyRow) continue;
+        A acc[NT][VEC];
+        gather_range<T, G, NT, false, A, true>(e0, e1, ci, nullptr, zcur, ld, lane, ncols, acc, swin, w0, wuse);
+        cheb_epilogue<T, G, NT>(row, lane, 0, ncols, acc, invdeg, sqdeg, zcur, zprev_next, Y, perm, ld, c0, c_next,
+                                mode);
+    }
+}
+
 template <typename T>
 __global__ void scale_copy_kernel(const T* __restrict__ X, typename StoreTraits<T>::acc_t* __restrict__ Y,
                                   const int32_t* __restrict__ perm, int32_t N, int ld,
@@ -229,55 +317,47 @@ __global__ void normalize_kernel(A* __restrict__ Y, int32_t N, int d, int ld) {
 // sum_i d_i <Z_a, Z_b>_i (d_i -> 1 for an isolated node):
 //   first: s0 = <X0,X0>, s1 = <X1,X0>, s2 = <X1,X1>
 //   later: s1 = <X_{j+1},X_j>, s2 = <X_{j+1},X_{j+1}>
+// One row of the moment step: Z_{j+1} of the row's columns of this tile, and the
+// row's fp32 products <z_c, z_c>, <z_n, z_c>, <z_n, z_n> summed over them.
 template <typename T, int G, int NT>
-__global__ void __launch_bounds__(512)
-mom_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ invdeg,
-                const int32_t* __restrict__ deg, const T* __restrict__ zcur, T* __restrict__ zprev_next,
-                const int32_t* __restrict__ part, int ncols, int64_t ld, int first, double* __restrict__ partials) {
+__device__ __forceinline__ void mom_epilogue(int row, int lane, int col0, int tcols, float (&acc)[NT][StoreTraits<T>::VEC],
+                                             const float* __restrict__ invdeg, const T* __restrict__ zcur,
+                                             T* __restrict__ zprev_next, int64_t ld, int first, float& p0, float& p1,
+                                             float& p2) {
     using Tr = StoreTraits<T>;
     constexpr int VEC = Tr::VEC;
-    constexpr int TW = G * NT * VEC;
-    const int lane = threadIdx.x % G;
-    const int col0 = blockIdx.y * TW;
-    const int tcols = min(TW, ncols - col0);
-    const int r1 = part[blockIdx.x + 1];
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int row = part[blockIdx.x] + (int)(threadIdx.x / G); row < r1; row += (int)(blockDim.x / G)) {
-        float acc[NT][VEC];
-        gather_row<T, G, NT, false, float>(rp, ci, nullptr, zcur + col0, ld, row, lane, tcols, acc);
-        const float f = (first ? -1.0f : -2.0f) * invdeg[row];
-        const int dg = deg[row];
-        const double wr = dg > 0 ? (double)dg : 1.0;
-        float p0 = 0.f, p1 = 0.f, p2 = 0.f;  // this row's products, fp32, then one fp64 add each
+    const float f = (first ? -1.0f : -2.0f) * invdeg[row];
+    p0 = p1 = p2 = 0.f;
 #pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            const int cl = (t * G + lane) * VEC;
-            if (cl >= tcols) continue;
-            const int c = col0 + cl;
-            float zc[VEC], zn[VEC];
-            Tr::load(zcur + (int64_t)row * ld + c, zc);
-            T* zp_ptr = zprev_next + (int64_t)row * ld + c;
-            if (first) {
+    for (int t = 0; t < NT; ++t) {
+        const int cl = (t * G + lane) * VEC;
+        if (cl >= tcols) continue;
+        const int c = col0 + cl;
+        float zc[VEC], zn[VEC];
+        Tr::load(zcur + (int64_t)row * ld + c, zc);
+        T* zp_ptr = zprev_next + (int64_t)row * ld + c;
+        if (first) {
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v]);
-            } else {
-                float zp[VEC];
-                Tr::load_cs(zp_ptr, zp);
+            for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v]);
+        } else {
+            float zp[VEC];
+            Tr::load_cs(zp_ptr, zp);
 #pragma unroll
-                for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v] - zp[v]);
-            }
-            Tr::store(zp_ptr, zn);
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-                p0 = fmaf(zc[v], zc[v], p0);
-                p1 = fmaf(zn[v], zc[v], p1);
-                p2 = fmaf(zn[v], zn[v], p2);
-            }
+            for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v] - zp[v]);
         }
-        s0 += wr * (double)p0;
-        s1 += wr * (double)p1;
-        s2 += wr * (double)p2;
+        Tr::store(zp_ptr, zn);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+            p0 = fmaf(zc[v], zc[v], p0);
+            p1 = fmaf(zn[v], zc[v], p1);
+            p2 = fmaf(zn[v], zn[v], p2);
+        }
     }
+}
+
+// Block partials of three fp64 sums -> partials[slot * 3 + q].
+__device__ __forceinline__ void mom_block_partials(double s0, double s1, double s2, int64_t slot,
+                                                   double* __restrict__ partials) {
     __shared__ double red[3][32];
     s0 = warp_sum(s0);
     s1 = warp_sum(s1);
@@ -290,8 +370,64 @@ mom_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, 
     if (threadIdx.x < 3) {
         double t = 0.0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[threadIdx.x][i];
-        partials[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = t;
+        partials[slot * 3 + threadIdx.x] = t;
     }
+}
+
+template <typename T, int G, int NT>
+__global__ void __launch_bounds__(512)
+mom_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ invdeg,
+                const int32_t* __restrict__ deg, const T* __restrict__ zcur, T* __restrict__ zprev_next,
+                const int32_t* __restrict__ part, int ncols, int64_t ld, int first, double* __restrict__ partials) {
+    constexpr int VEC = StoreTraits<T>::VEC;
+    constexpr int TW = G * NT * VEC;
+    const int lane = threadIdx.x % G;
+    const int col0 = blockIdx.y * TW;
+    const int tcols = min(TW, ncols - col0);
+    const int r1 = part[blockIdx.x + 1];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int row = part[blockIdx.x] + (int)(threadIdx.x / G); row < r1; row += (int)(blockDim.x / G)) {
+        const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
+        if (e1 - e0 > kHeavyRow) continue;
+        float acc[NT][VEC];
+        gather_range<T, G, NT, false, float>(e0, e1, ci, nullptr, zcur + col0, ld, lane, tcols, acc);
+        float p0, p1, p2;
+        mom_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, zcur, zprev_next, ld, first, p0, p1, p2);
+        const int dg = deg[row];
+        const double wr = dg > 0 ? (double)dg : 1.0;
+        s0 += wr * (double)p0;
+        s1 += wr * (double)p1;
+        s2 += wr * (double)p2;
+    }
+    mom_block_partials(s0, s1, s2, (int64_t)blockIdx.y * gridDim.x + blockIdx.x, partials);
+}
+
+// Heavy rows: one CTA per row; partial slots after the regular blocks' (slot_base).
+template <typename T, int G, int NT>
+__global__ void __launch_bounds__(kHeavyThreads)
+mom_step_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                      const float* __restrict__ invdeg, const int32_t* __restrict__ deg, const T* __restrict__ zcur,
+                      T* __restrict__ zprev_next, const int32_t* __restrict__ heavy, int ncols, int64_t ld, int first,
+                      double* __restrict__ partials, int64_t slot_base) {
+    constexpr int VEC = StoreTraits<T>::VEC;
+    constexpr int TW = G * NT * VEC;
+    const int lane = threadIdx.x % G;
+    const int col0 = blockIdx.y * TW;
+    const int tcols = min(TW, ncols - col0);
+    const int row = heavy[blockIdx.x];
+    float acc[NT][VEC];
+    gather_heavy<T, G, NT, false, float>(__ldg(rp + row), __ldg(rp + row + 1), ci, nullptr, zcur + col0, ld, lane,
+                                         tcols, acc);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    if (threadIdx.x < G) {
+        float p0, p1, p2;
+        mom_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, zcur, zprev_next, ld, first, p0, p1, p2);
+        const double wr = (double)deg[row];
+        s0 = wr * (double)p0;
+        s1 = wr * (double)p1;
+        s2 = wr * (double)p2;
+    }
+    mom_block_partials(s0, s1, s2, slot_base + (int64_t)blockIdx.y * gridDim.x + blockIdx.x, partials);
 }
 
 // Sum block partials in a fixed order: out[q] = sum_b partials[b*3+q].
@@ -363,10 +499,35 @@ static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur
     CSC_TRY(get_partition(g, cfg.P, &part));
     const dim3 grid(cfg.P, cfg.tiles);
     // algorithmic bytes of one order: CSR + row factors, Z_j gathered once, Z_{j-1} read and
-    // Z_{j+1} written (first order: Z_0 read, Z_1 written), Y written or read+written
+    // Z_{j+1} written (first order: Z_0 read, Z_1 written), Y written or read+written;
+    // split between the row-range launch and the heavy-row launch by their edges and rows
     const double nx = (double)g->N * ncols;
-    const double bytes = 4.0 * g->nnz + 4.0 * (g->N + 1) + (double)sizeof(A) * g->N * (mode & 2 ? 2 : 1) +
-                         (first ? 2.0 : 3.0) * nx * sizeof(T) + (first ? 1.0 : 2.0) * nx * sizeof(A);
+    const double all_bytes = 4.0 * g->nnz + 4.0 * (g->N + 1) + (double)sizeof(A) * g->N * (mode & 2 ? 2 : 1) +
+                             (first ? 2.0 : 3.0) * nx * sizeof(T) + (first ? 1.0 : 2.0) * nx * sizeof(A);
+    const double heavy_edges = (double)g->nnz - (double)g->h_light[g->N];
+    const double heavy_frac = g->n_heavy ? (heavy_edges + g->n_heavy) / ((double)g->nnz + g->N) : 0.0;
+    const double bytes = all_bytes * (1.0 - heavy_frac);
+    if (g->n_heavy > 0) {
+        const dim3 hgrid(g->n_heavy, cfg.win > 0 ? 1 : cfg.tiles);
+        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * heavy_frac, s,
+                                          cheb_step_heavy_kernel<T, GG, NN><<<hgrid, kHeavyThreads, 0, s>>>(
+                                              g->row_ptr, g->col_idx, idg, sqd, xcur, xpn, Y, g->perm, g->heavy,
+                                              ncols, ld, (A)c0, (A)cn, mode)));
+    }
+    if (cfg.win > 0) {
+        const int32_t* win = nullptr;
+        CSC_TRY(get_windows(g, cfg.P, cfg.win, &win));
+        const size_t smem = 128 + (size_t)cfg.win * ld * sizeof(T);
+        CSC_SHAPE_SWITCH(cfg, {
+            CSC_CUDA_TRY(cudaFuncSetAttribute(cheb_step_win_kernel<T, GG, NN>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            CSC_KLAUNCH("cheb_step", bytes, s,
+                        cheb_step_win_kernel<T, GG, NN><<<grid, cfg.threads, smem, s>>>(
+                            g->row_ptr, g->col_idx, idg, sqd, xcur, xpn, Y, g->perm, part, ncols, ld, (A)c0, (A)cn,
+                            mode, win, cfg.win, g->dev_err));
+        });
+        return CSC_OK;
+    }
     CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", bytes, s,
                                       cheb_step_kernel<T, GG, NN><<<grid, cfg.threads, 0, s>>>(
                                           g->row_ptr, g->col_idx, idg, sqd, xcur, xpn, Y, g->perm, part, ncols, ld,
@@ -381,6 +542,14 @@ static csc_status launch_mom_step(Graph* g, const LaunchCfg& cfg, const T* xcur,
     const int32_t* part = nullptr;
     CSC_TRY(get_partition(g, cfg.P, &part));
     const dim3 grid(cfg.P, cfg.tiles);
+    if (g->n_heavy > 0) {
+        // heavy rows' partial sums go to the slots after the row-range blocks'
+        const dim3 hgrid(g->n_heavy, cfg.tiles);
+        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("mom_step", 0.0, s,
+                                          mom_step_heavy_kernel<T, GG, NN><<<hgrid, kHeavyThreads, 0, s>>>(
+                                              g->row_ptr, g->col_idx, g->invdeg, g->deg, xcur, xpn, g->heavy, ncols,
+                                              ld, first, partials, (int64_t)cfg.P * cfg.tiles)));
+    }
     CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("mom_step", bytes, s,
                                       mom_step_kernel<T, GG, NN><<<grid, cfg.threads, 0, s>>>(
                                           g->row_ptr, g->col_idx, g->invdeg, g->deg, xcur, xpn, part, ncols, ld,
@@ -400,12 +569,22 @@ static int occupancy(K kernel, int threads) {
 }
 
 template <typename T>
-static int kernel_occupancy(int kind, const TileShape& sh, int threads) {
+static int kernel_occupancy(int kind, const TileShape& sh, int threads, size_t win_smem = 0) {
     int occ = 1;
     auto f = [&](auto kptr) { occ = occupancy(kptr, threads); };
+    auto fw = [&](auto kptr) {
+        cudaFuncSetAttribute(kptr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem);
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kptr, threads, win_smem) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        occ = n;
+    };
 #define CSC_OCC_CASE(GG, NN)                                                             \
     if (sh.G == GG && sh.NT == NN) {                                                     \
-        if (kind == KK_CHEB) f(cheb_step_kernel<T, GG, NN>);                             \
+        if (kind == KK_CHEB && win_smem) fw(cheb_step_win_kernel<T, GG, NN>);           \
+        else if (kind == KK_CHEB) f(cheb_step_kernel<T, GG, NN>);                        \
         else if constexpr (sizeof(T) <= 4) f(mom_step_kernel<T, GG, NN>);               \
     }
     CSC_OCC_CASE(2, 1) CSC_OCC_CASE(2, 2) CSC_OCC_CASE(2, 3) CSC_OCC_CASE(4, 1) CSC_OCC_CASE(4, 2)
@@ -452,6 +631,27 @@ static std::vector<LaunchCfg> candidates(Graph* g, int kind, int nv) {
                     out.back().P == c.P)
                     continue;
                 out.push_back(c);
+            }
+            // shared-memory neighbour windows (single column tile): up to ~64 / 100 / 200 KB
+            if (kind == KK_CHEB && tiles == 1) {
+                const size_t row_bytes = (size_t)nv * 16;
+                for (size_t budget : {64 * 1024, 100 * 1024, 200 * 1024}) {
+                    int64_t W = (int64_t)((budget - 128) / row_bytes);
+                    if (W > g->N) W = g->N;
+                    if (W < 64) continue;
+                    const size_t smem = 128 + (size_t)W * row_bytes;
+                    const int wocc = kernel_occupancy<T>(kind, sh, th, smem);
+                    if (wocc < 1) continue;
+                    LaunchCfg cw = c;
+                    cw.win = (int)W;
+                    for (int waves = 1; waves <= 2; waves *= 2) {
+                        int P = g->num_sms * wocc * waves;
+                        if (P > max_p) P = (int)max_p;
+                        cw.P = P < 1 ? 1 : P;
+                        out.push_back(cw);
+                    }
+                    if (W == g->N) break;
+                }
             }
         }
     }
@@ -610,7 +810,16 @@ static csc_status moments_typed(Graph* g, int n_moments, int n_probes, uint64_t 
     const int J = n_moments <= 2 ? 1 : n_moments / 2;
     const std::vector<LaunchCfg> cands = candidates<T>(g, KK_MOM, ld / VEC);
     int max_blocks = 1;
-    for (const LaunchCfg& c : cands) max_blocks = std::max(max_blocks, c.P * c.tiles);
+    for (const LaunchCfg& c : cands) max_blocks = std::max(max_blocks, (c.P + g->n_heavy) * c.tiles);
+    {
+        // a shape pinned on the handle or tuned earlier sizes the block partials too
+        const uint64_t key = tune_key(KK_MOM, (int)sizeof(T), ld);
+        LaunchCfg known;
+        auto it = g->tuned.find(key);
+        if (it != g->tuned.end()) max_blocks = std::max(max_blocks, (it->second.P + g->n_heavy) * it->second.tiles);
+        else if (tune_cache_get(g, key, &known))
+            max_blocks = std::max(max_blocks, (known.P + g->n_heavy) * known.tiles);
+    }
     CSC_TRY(ws_get(g, WS_PARTIAL, (size_t)max_blocks * 3 * sizeof(double), &part));
     CSC_TRY(ws_get(g, WS_MOMENTS, (size_t)J * 3 * sizeof(double), &sums));
     double* P = (double*)part;
@@ -620,7 +829,7 @@ static csc_status moments_typed(Graph* g, int n_moments, int n_probes, uint64_t 
     CSC_TRY(autotune(g, tune_key(KK_MOM, (int)sizeof(T), ld), cands, s,
                      [&](const LaunchCfg& c) { return launch_mom_step<T>(g, c, X[0], X[1], ld, ld, 0, P, s); },
                      &cfg));
-    const int grid = cfg.P * cfg.tiles;
+    const int grid = (cfg.P + g->n_heavy) * cfg.tiles;  // block partial slots per step
     for (int j = 0; j < J; ++j) {
         CSC_TRY(launch_mom_step<T>(g, cfg, X[j & 1], X[(j + 1) & 1], ld, ld, j == 0 ? 1 : 0, P, s));
         CSC_KLAUNCH("reduce", 24.0 * grid, s, reduce_partials_kernel<<<1, 256, 0, s>>>(P, grid, S + 3 * j));
