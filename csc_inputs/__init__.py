@@ -24,3 +24,4 @@ from .graphs import (  # noqa: F401
     block_diagonal,
 )
 from .signals import gaussian_block, workload_sizes  # noqa: F401
+from .datasets import bracket_graph, batched_sbm_set  # noqa: F401

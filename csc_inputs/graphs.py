@@ -181,30 +181,51 @@ def sbm(n: int, k: int, s: float = 16.0, eps: Optional[float] = None, seed: int 
 # ---------------------------------------------------------------------------
 
 def _pareto_mean(alpha: float, w_max: float) -> float:
+    """Mean of a Pareto(1, alpha) law truncated to [1, w_max]."""
+    if abs(alpha - 1.0) < 1e-9:
+        return np.log(w_max) / (1.0 - 1.0 / w_max)
     return alpha * (1 - w_max ** (1 - alpha)) / ((alpha - 1) * (1 - w_max ** (-alpha)))
 
 
-def chung_lu_weights(n: int, exponent: float = 2.1, mean: float = 6.0, w_min: float = 1.0):
-    """Deterministic quantiles of a Pareto(w_min, exponent) truncated so its mean is ``mean``.
+def chung_lu_weights(n: int, exponent: float = 2.1, mean: float = 6.0, w_min: float = 1.0,
+                     cutoff: Optional[float] = None):
+    """Deterministic quantiles of a truncated Pareto law with mean ``mean``.
 
-    Degree exponent gamma gives tail index alpha = gamma - 1; the truncation
-    point w_max solves E[w] = mean by bisection.  Node i gets the quantile at
-    u = (i + 0.5) / n, so weights are sorted ascending.
+    Degree exponent gamma gives tail index alpha = gamma - 1.  Without
+    ``cutoff`` the lower end is ``w_min`` and the truncation point w_max solves
+    E[w] = mean by bisection.  With ``cutoff`` the upper end is w_max = cutoff
+    and the lower end w_min solves E[w] = mean instead (for exponents whose
+    untruncated mean with w_min = 1 is below ``mean``).  Node i gets the
+    quantile at u = (i + 0.5) / n, so weights are sorted ascending.
     """
     alpha = exponent - 1.0
-    lo, hi = 1.0 + 1e-9, 1e12
-    if _pareto_mean(alpha, hi) * w_min < mean:
-        raise ValueError("mean degree unreachable for this exponent")
-    for _ in range(200):
-        mid = np.sqrt(lo * hi)
-        if _pareto_mean(alpha, mid) * w_min < mean:
-            lo = mid
-        else:
-            hi = mid
-    w_max = hi
+    if cutoff is None:
+        lo, hi = 1.0 + 1e-9, 1e12
+        if _pareto_mean(alpha, hi) * w_min < mean:
+            raise ValueError("mean degree unreachable for this exponent")
+        for _ in range(200):
+            mid = np.sqrt(lo * hi)
+            if _pareto_mean(alpha, mid) * w_min < mean:
+                lo = mid
+            else:
+                hi = mid
+        ratio = hi
+    else:
+        if not cutoff > mean:
+            raise ValueError("cutoff must exceed the mean")
+        # E[w] = w_min * mean(ratio = cutoff / w_min) is increasing in w_min
+        lo, hi = 1e-12, float(mean)
+        for _ in range(200):
+            mid = np.sqrt(lo * hi)
+            if mid * _pareto_mean(alpha, cutoff / mid) < mean:
+                lo = mid
+            else:
+                hi = mid
+        w_min = hi
+        ratio = cutoff / w_min
     u = (np.arange(n, dtype=np.float64) + 0.5) / n
-    w = w_min * (1.0 - u * (1.0 - w_max ** (-alpha))) ** (-1.0 / alpha)
-    return w, w_max * w_min
+    w = w_min * (1.0 - u * (1.0 - ratio ** (-alpha))) ** (-1.0 / alpha)
+    return w, ratio * w_min
 
 
 def _components(n: int, src: np.ndarray, dst: np.ndarray) -> np.ndarray:
@@ -217,7 +238,7 @@ def _components(n: int, src: np.ndarray, dst: np.ndarray) -> np.ndarray:
 
 
 def chung_lu(n: int, exponent: float = 2.1, mean: float = 6.0, seed: int = 0,
-             min_degree_one: bool = True, connect: bool = True) -> CSRGraph:
+             min_degree_one: bool = True, connect: bool = True, cutoff: Optional[float] = None) -> CSRGraph:
     """Chung-Lu graph with p_ij = min(1, w_i w_j / sum(w)), drawn exactly.
 
     Miller-Hagberg: with weights sorted descending, each source u walks the
@@ -228,10 +249,11 @@ def chung_lu(n: int, exponent: float = 2.1, mean: float = 6.0, seed: int = 0,
     its weight, so the minimum degree is 1.  With ``connect`` every connected
     component other than the largest gets one more edge, from a node drawn
     uniformly in it to a node of the largest component drawn with probability
-    proportional to its weight, so the graph is connected.
+    proportional to its weight, so the graph is connected.  ``cutoff`` fixes
+    the largest weight instead of the smallest (see ``chung_lu_weights``).
     """
     rng = np.random.Generator(np.random.PCG64(seed))
-    w_asc, w_max = chung_lu_weights(n, exponent, mean)
+    w_asc, w_max = chung_lu_weights(n, exponent, mean, cutoff=cutoff)
     order = np.argsort(-w_asc, kind="stable")  # descending
     w = w_asc[order]
     total = w.sum()
