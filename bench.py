@@ -61,6 +61,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--learned", action="store_true",
+                    help="learned lambda_k bracket: train on the bracket graph set, report held-out gains")
+    ap.add_argument("--n-train", type=int, default=2000)
+    ap.add_argument("--n-test", type=int, default=200)
+    ap.add_argument("--save-data", default="", help="write the bracket features and targets (npz) here")
     ap.add_argument("--precision", action="store_true",
                     help="filter in FP64 / FP32 / BF16 storage on the workload: time, error vs FP64, label ARI")
     return ap.parse_args()
@@ -449,6 +454,100 @@ def run_precision(args, w):
     return 0
 
 
+def run_learned(args):
+    """Learned lambda_k bracket on the bracket graph set (N log-uniform 1e4-2e5, k 10-500,
+    SBM / Chung-Lu mix): features and targets from the library, device training, then
+    on the held-out graphs the bracket coverage and, for both eigencount estimators
+    (moments-once and paper-literal re-filtering), the lambda_k stage's wall time and
+    sparse products with and without the network, plus CSC's ARI on the SBM graphs."""
+    import multiprocessing as mp
+
+    import numpy as np
+    import torch
+
+    import paper_1602_02018_gb300 as csc
+    from csc_inputs.datasets import bracket_graph_arrays
+    from paper_1602_02018_gb300 import learned
+
+    torch.cuda.set_device(0)
+    n_tr, n_te, m = args.n_train, args.n_test, 50
+    tasks = [(i, (1e4, 2e5), (10, 500)) for i in range(n_tr + n_te)]
+    t0 = time.perf_counter()
+    feats, brs, held = [None] * len(tasks), [None] * len(tasks), {}
+    ctx = mp.get_context("spawn")
+    t_gen = 0.0
+    with ctx.Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
+        for i, rp, col, lab, k in pool.imap_unordered(bracket_graph_arrays, tasks, chunksize=2):
+            with csc.csc_graph_create(rp, col) as h:
+                f, b = learned.bracket_sample(h, k, m, 0, 0)
+            feats[i], brs[i] = f, b
+            if i >= n_tr:
+                held[i] = (rp, col, lab, k)
+    t_gen = time.perf_counter() - t0
+    feats = np.stack(feats)
+    brs = np.array(brs, dtype=np.float64)
+    t1 = time.perf_counter()
+    if args.save_data:
+        np.savez(args.save_data, feats=feats, brs=brs)
+    model = learned.BracketModel.fit(feats[:n_tr], brs[:n_tr], epochs=300, batch=64, lr=1e-3, seed=0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    pred = model.predict_brackets(feats[n_tr:])
+    cov = learned.covered(pred, brs[n_tr:])
+    rows = []
+    for i in range(n_tr, n_tr + n_te):
+        rp, col, lab, k = held[i]
+        r = dict(i=i, N=len(rp) - 1, k=k, sbm=lab is not None)
+        with csc.csc_graph_create(rp, col) as h:
+            # warm the launch-shape tuning of this graph for every estimator first
+            csc.csc_estimate_lambda_k(h, k, m, 0, 0)
+            csc.csc_estimate_lambda_k_refilter(h, k, m, 0, 0)
+            model.estimate(h, k, m, 0, 0)
+            for name, fn in (("plain", lambda: csc.csc_estimate_lambda_k(h, k, m, 0, 0)),
+                             ("learned", lambda: model.estimate(h, k, m, 0, 0)[0]),
+                             ("plain_refilter", lambda: csc.csc_estimate_lambda_k_refilter(h, k, m, 0, 0)),
+                             ("learned_refilter", lambda: model.estimate(h, k, m, 0, 0, refilter=True)[0])):
+                torch.cuda.synchronize()
+                ta = time.perf_counter()
+                info = fn()
+                r[name] = dict(ms=(time.perf_counter() - ta) * 1e3, products=info.moment_passes, lam=info.lam,
+                               hit=info.hit, used=info.bracket_used, iters=info.iters)
+            if lab is not None:
+                la, _ = csc.csc_cluster(h, k, lambda_k=r["plain"]["lam"], seed=0)
+                lb, _ = csc.csc_cluster(h, k, lambda_k=r["learned"]["lam"], seed=0)
+                r["ari_plain"] = adjusted_rand(la.cpu().numpy(), lab)
+                r["ari_learned"] = adjusted_rand(lb.cpu().numpy(), lab)
+        rows.append(r)
+
+    def tot(key, f):
+        return float(sum(r[key][f] for r in rows))
+
+    sb = [r for r in rows if r["sbm"]]
+    out = {"mode": "learned_bracket", "n_train": n_tr, "n_test": n_te, "m": m,
+           "data_seconds": t_gen, "train_seconds": t_train, "epochs": 300, "batch": 64,
+           "fit_samples": model.n_fit, "calibration_samples": model.n_val,
+           "final_train_loss": float(model.loss_history[-1]), "first_train_loss": float(model.loss_history[0]),
+           "widen": model.widen, "held_out_coverage": float(cov.mean()),
+           "median_bracket_width": float(np.median(pred[:, 1] - pred[:, 0])),
+           "moments_once": {"plain_ms": tot("plain", "ms"), "learned_ms": tot("learned", "ms"),
+                            "plain_products": tot("plain", "products"),
+                            "learned_products": tot("learned", "products"),
+                            "bracket_used": sum(r["learned"]["used"] for r in rows)},
+           "refilter": {"plain_ms": tot("plain_refilter", "ms"), "learned_ms": tot("learned_refilter", "ms"),
+                        "plain_products": tot("plain_refilter", "products"),
+                        "learned_products": tot("learned_refilter", "products"),
+                        "bracket_used": sum(r["learned_refilter"]["used"] for r in rows),
+                        "hits_plain": sum(r["plain_refilter"]["hit"] for r in rows),
+                        "hits_learned": sum(r["learned_refilter"]["hit"] for r in rows)},
+           "sbm_graphs": len(sb),
+           "ari_plain_mean": float(np.mean([r["ari_plain"] for r in sb])) if sb else None,
+           "ari_learned_mean": float(np.mean([r["ari_learned"] for r in sb])) if sb else None,
+           "ari_abs_diff_mean": float(np.mean([abs(r["ari_learned"] - r["ari_plain"]) for r in sb])) if sb else None,
+           "graphs": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -457,6 +556,8 @@ def main():
         world = 1
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     w = WORKLOADS[args.workload]
+    if args.learned:
+        return run_learned(args)
     if args.precision:
         import torch
 

@@ -66,3 +66,10 @@ def batched_sbm_set(seed: int = 0, count: int = 256, n_range: Tuple[float, float
 
 def sizes_of(graphs: Sequence[Tuple[CSRGraph, int]]) -> np.ndarray:
     return np.array([g.n for g, _ in graphs], dtype=np.int64)
+
+
+def bracket_graph_arrays(args):
+    """Process-pool task: (i, n_range, k_range) -> (i, row_ptr, col_idx, labels, k)."""
+    i, n_range, k_range = args
+    g, k = bracket_graph(i, n_range, k_range)
+    return i, g.row_ptr, g.col_idx, g.labels, k

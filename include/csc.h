@@ -85,7 +85,7 @@ typedef struct {
     int32_t n_probes;     /* probe vectors used                                       */
     int32_t m;            /* polynomial degree used                                   */
     int32_t bracket_used; /* 1 if a caller bracket was given and contained the answer */
-    int32_t moment_passes;/* sparse block products spent on moments                   */
+    int32_t moment_passes;/* sparse block products spent on eigencounts                */
 } csc_lambda_info;
 
 /* Result of csc_interpolate. */
@@ -251,6 +251,109 @@ CSC_API csc_status csc_eigencount(const double* mu, int32_t m, double lambda, ui
 CSC_API csc_status csc_estimate_lambda_k(csc_graph g, int32_t k, int32_t m, int32_t n_probes,
                                  uint64_t seed, const double* bracket, csc_lambda_info* out,
                                  void* stream);
+
+/* csc_estimate_lambda_k_refilter -- the Sec. 4.3 estimator read literally: every
+ * dichotomy threshold lambda filters the n_probes N(0, 1) probes (the probes of
+ * csc_kpm_moments) with the degree-m Jackson-Chebyshev step at lambda (m sparse
+ * block products) and takes count = (1/n_probes) sum_l r_l^T h~_lambda(L) r_l,
+ * reduced on the device in fp64.  The dichotomy rule is that of
+ * csc_estimate_lambda_k.  In exact arithmetic the counts equal the
+ * moments-once counts; this entry point exists to measure what the paper's
+ * form costs.  bracket: NULL or host {lo, hi}, checked by the counts at both
+ * ends (two passes) and used when round(count(lo)) <= k <= round(count(hi)).
+ * out->moment_passes counts the sparse products.  Synchronizes `stream`. */
+CSC_API csc_status csc_estimate_lambda_k_refilter(csc_graph g, int32_t k, int32_t m, int32_t n_probes,
+                                          uint64_t seed, const double* bracket, csc_lambda_info* out,
+                                          void* stream);
+
+/* ------------------------------------------- learned lambda_k bracket
+ * The paper is silent on learning lambda_k; these calls add a predictor of a
+ * bracket for the Sec. 4.3 dichotomy, and the eigencount remains the judge:
+ * a bracket is used only when the eigencount confirms it, otherwise the
+ * plain dichotomy runs.  The predictor is a 72 -> 256 -> 256 -> 2 ReLU
+ * perceptron (smooth-L1 loss, Adam) trained on the device by the calls below.
+ * Parameters are one device float[CSC_MLP_PARAMS] in the order W1 [72 x 256]
+ * (row = input, row-major), b1 [256], W2 [256 x 256], b2, W3 [256 x 2], b3 [2].
+ * All device buffers are owned by the caller. */
+#define CSC_MLP_IN 72
+#define CSC_MLP_HIDDEN 256
+#define CSC_MLP_OUT 2
+#define CSC_MLP_PARAMS 84994
+#define CSC_BRACKET_PROBES 8
+#define CSC_BRACKET_MOMENTS 64
+/* flags of csc_estimate_lambda_k_learned */
+#define CSC_EIGENCOUNT_REFILTER 1u /* judge the bracket with the paper-literal estimator */
+
+/* csc_bracket_features -- the 72 predictor inputs of one graph (host float[72]):
+ * [0, 64) eigencount moments mu_j / N of CSC_BRACKET_PROBES N(0, 1) probes
+ * (the Sec. 4.3 estimator, j = 0..63, one device moment pass); 64: ln N;
+ * 65: k; 66..71: ln(1 + q) for the degree quantiles q at 0, 0.1, 0.25, 0.5,
+ * 0.75, 1 (sorted degree at index floor(p (N - 1))).  mu_out: NULL or host
+ * double[64], the raw moments.  Synchronizes `stream`. */
+CSC_API csc_status csc_bracket_features(csc_graph g, int32_t k, uint64_t seed, float* feat_out,
+                                        double* mu_out, void* stream);
+
+/* csc_bracket_target -- host: the cut-offs where count(lambda) = sum_j c_j(lambda)
+ * mu_j (Sec. 4.3, degree m, mu: host double[m+1]) crosses k - 1/2 and k + 1/2,
+ * each by 60 bisection halvings on [0, 2]; every lambda between them rounds to
+ * count k.  lo_hi_out: host double[2]. */
+CSC_API csc_status csc_bracket_target(const double* mu, int32_t m, int32_t k, double* lo_hi_out);
+
+/* csc_mlp_init -- He-uniform weights U(-a, a), a = sqrt(6 / fan_in), from Philox
+ * (counter = parameter index, key = seed), zero biases.  params: device. */
+CSC_API csc_status csc_mlp_init(float* params, uint64_t seed, void* stream);
+
+/* csc_mlp_forward -- Y = relu(relu(X W1 + b1) W2 + b2) W3 + b3 for B rows.
+ * X: device float[B x 72]; Y: device float[B x 2]; 1 <= B <= 65536. */
+CSC_API csc_status csc_mlp_forward(const float* params, const float* X, int32_t B, float* Y, void* stream);
+
+/* csc_mlp_loss_grad -- smooth-L1 (beta = 1) loss averaged over the B x 2 outputs
+ * against targets T (device float[B x 2]) and its gradient (device
+ * float[CSC_MLP_PARAMS], overwritten).  loss: NULL or host double (then the
+ * call synchronizes `stream`). */
+CSC_API csc_status csc_mlp_loss_grad(const float* params, const float* X, const float* T, int32_t B,
+                                     float* grad, double* loss, void* stream);
+
+/* csc_mlp_adam_step -- one Adam update (beta1 0.9, beta2 0.999, eps 1e-8, bias
+ * corrected at step t >= 1).  m, v: device float[CSC_MLP_PARAMS] moment
+ * estimates (zero before the first step). */
+CSC_API csc_status csc_mlp_adam_step(float* params, const float* grad, float* m, float* v, int32_t t,
+                                     float lr, void* stream);
+
+/* csc_mlp_train -- `epochs` passes of minibatch Adam over n samples (X: device
+ * float[n x 72], T: device float[n x 2]), batches of `batch` rows in an order
+ * shuffled per epoch by SplitMix64(seed).  Adam state starts at zero.
+ * epoch_loss: NULL or host double[epochs], the mean batch loss of each
+ * epoch.  Synchronizes `stream`. */
+CSC_API csc_status csc_mlp_train(float* params, const float* X, const float* T, int32_t n, int32_t epochs,
+                                 int32_t batch, float lr, uint64_t seed, double* epoch_loss, void* stream);
+
+/* csc_estimate_lambda_k_learned -- Alg. 2 step 1 with a predicted bracket:
+ *   1. csc_bracket_features (one moment pass over 8 probes, 64 moments);
+ *   2. z = (features - mean) / std, y = network(z), (centre, ln half-width) =
+ *      y * target_std + target_mean, bracket = centre -+ widen * exp(ln half-width)
+ *      clipped to [0, 2];
+ *   3. the Sec. 4.3 halving started from the prediction: the count at the
+ *      centre c decides the side, the predicted end on that side (c -+ hw) is
+ *      evaluated next, and the halving continues inside [c - hw, c + hw] when
+ *      that end lies across k, else on the rest of [0, 2]; it stops as soon
+ *      as round(count) == k, like csc_estimate_lambda_k;
+ *   4. moments-once (flags = 0): step 3 runs on the 8-probe moments (m <= 63);
+ *      an answer found inside the prediction is returned (bracket_used = 1,
+ *      n_probes = 8); otherwise the plain path runs: n_probes probes
+ *      (0 -> ceil(2 ln N)) and the dichotomy on [0, 2] (bracket_used = 0).
+ *      With flags & CSC_EIGENCOUNT_REFILTER, step 3 evaluates every count
+ *      with the paper-literal estimator of csc_estimate_lambda_k_refilter
+ *      (n_probes probes); bracket_used tells whether the answer lay inside
+ *      the prediction.
+ * params: device float[CSC_MLP_PARAMS].  norm: host float[148] = feature mean
+ * [72], feature std [72], target mean [2], target std [2].  widen > 0.
+ * bracket_out: NULL or host double[2], the predicted bracket.  moment_passes
+ * counts the sparse products of both moment passes.  Synchronizes `stream`. */
+CSC_API csc_status csc_estimate_lambda_k_learned(csc_graph g, int32_t k, int32_t m, int32_t n_probes,
+                                                 uint64_t seed, const float* params, const float* norm,
+                                                 double widen, uint32_t flags, csc_lambda_info* out,
+                                                 double* bracket_out, void* stream);
 
 /* ------------------------------------------------- sampling and k-means */
 

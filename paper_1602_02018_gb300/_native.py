@@ -36,6 +36,9 @@ CSC_E_UNSUPPORTED = 8
 CSC_F32, CSC_BF16, CSC_F64 = 0, 1, 2
 CSC_RCM, CSC_CHECK_SYM, CSC_DEVICE_INPUT = 1, 2, 4
 CSC_NORMALIZE_ROWS, CSC_NO_JACKSON = 1, 2
+CSC_MLP_IN, CSC_MLP_HIDDEN, CSC_MLP_OUT, CSC_MLP_PARAMS = 72, 256, 2, 84994
+CSC_BRACKET_PROBES, CSC_BRACKET_MOMENTS = 8, 64
+CSC_EIGENCOUNT_REFILTER = 1
 
 
 class csc_lambda_info(ctypes.Structure):
@@ -75,6 +78,18 @@ _SIGNATURES = {
     "csc_eigencount": [c_void_p, c_int32, c_double, c_uint32, P(c_double)],
     "csc_estimate_lambda_k": [c_void_p, c_int32, c_int32, c_int32, c_uint64, c_void_p, P(csc_lambda_info),
                               c_void_p],
+    "csc_bracket_features": [c_void_p, c_int32, c_uint64, c_void_p, c_void_p, c_void_p],
+    "csc_bracket_target": [c_void_p, c_int32, c_int32, c_void_p],
+    "csc_mlp_init": [c_void_p, c_uint64, c_void_p],
+    "csc_mlp_forward": [c_void_p, c_void_p, c_int32, c_void_p, c_void_p],
+    "csc_mlp_loss_grad": [c_void_p, c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p],
+    "csc_mlp_adam_step": [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_float, c_void_p],
+    "csc_mlp_train": [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_uint64, c_void_p,
+                      c_void_p],
+    "csc_estimate_lambda_k_learned": [c_void_p, c_int32, c_int32, c_int32, c_uint64, c_void_p, c_void_p, c_double,
+                                      c_uint32, P(csc_lambda_info), c_void_p, c_void_p],
+    "csc_estimate_lambda_k_refilter": [c_void_p, c_int32, c_int32, c_int32, c_uint64, c_void_p,
+                                       P(csc_lambda_info), c_void_p],
     "csc_sample": [c_int64, c_int64, c_uint64, c_void_p, c_void_p],
     "csc_sample_noalloc": [c_int64, c_int64, c_uint64, c_void_p, c_void_p],
     "csc_gather_rows": [c_void_p, c_int64, c_int32, c_void_p, c_int64, c_int32, c_void_p, c_int32, c_void_p],

@@ -200,6 +200,116 @@ def csc_estimate_lambda_k(g: Graph, k: int, m: int = 50, n_probes: int = 0, seed
     return _lambda_info(info)
 
 
+# ------------------------------------------------------- learned lambda_k bracket
+
+MLP_PARAMS = nat.CSC_MLP_PARAMS
+
+
+def _f32_dev(t: torch.Tensor, shape, name: str) -> torch.Tensor:
+    if t.dtype != torch.float32 or tuple(t.shape) != tuple(shape) or not t.is_cuda:
+        raise ValueError(f"{name} must be a float32 CUDA tensor of shape {tuple(shape)}")
+    return t
+
+
+def csc_bracket_features(g: Graph, k: int, seed: int = 0, stream=None):
+    """(features float32[72], raw 8-probe moments float64[64])."""
+    feat = np.empty(nat.CSC_MLP_IN, dtype=np.float32)
+    mu = np.empty(nat.CSC_BRACKET_MOMENTS, dtype=np.float64)
+    check(lib().csc_bracket_features(g.handle, k, seed, _hptr(feat), _hptr(mu), _stream(stream)),
+          "csc_bracket_features")
+    return feat, mu
+
+
+def csc_bracket_target(mu: np.ndarray, k: int) -> tuple:
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    out = np.empty(2, dtype=np.float64)
+    check(lib().csc_bracket_target(_hptr(mu), mu.size - 1, k, _hptr(out)), "csc_bracket_target")
+    return float(out[0]), float(out[1])
+
+
+def csc_mlp_init(seed: int = 0, params: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    if params is None:
+        params = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+    _f32_dev(params, (MLP_PARAMS,), "params")
+    check(lib().csc_mlp_init(_dptr(params), seed, _stream(stream)), "csc_mlp_init")
+    return params
+
+
+def csc_mlp_forward(params: torch.Tensor, X: torch.Tensor, Y: Optional[torch.Tensor] = None,
+                    stream=None) -> torch.Tensor:
+    B = X.shape[0]
+    _f32_dev(params, (MLP_PARAMS,), "params")
+    _f32_dev(X, (B, nat.CSC_MLP_IN), "X")
+    if Y is None:
+        Y = torch.empty((B, nat.CSC_MLP_OUT), dtype=torch.float32, device="cuda")
+    check(lib().csc_mlp_forward(_dptr(params), _dptr(X), B, _dptr(Y), _stream(stream)), "csc_mlp_forward")
+    return Y
+
+
+def csc_mlp_loss_grad(params: torch.Tensor, X: torch.Tensor, T: torch.Tensor, stream=None):
+    """(loss, gradient float32[MLP_PARAMS])."""
+    B = X.shape[0]
+    _f32_dev(params, (MLP_PARAMS,), "params")
+    _f32_dev(X, (B, nat.CSC_MLP_IN), "X")
+    _f32_dev(T, (B, nat.CSC_MLP_OUT), "T")
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+    loss = ctypes.c_double()
+    check(lib().csc_mlp_loss_grad(_dptr(params), _dptr(X), _dptr(T), B, _dptr(grad), ctypes.byref(loss),
+                                  _stream(stream)), "csc_mlp_loss_grad")
+    return loss.value, grad
+
+
+def csc_mlp_adam_step(params: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, t: int,
+                      lr: float, stream=None) -> None:
+    for name, a in (("params", params), ("grad", grad), ("m", m), ("v", v)):
+        _f32_dev(a, (MLP_PARAMS,), name)
+    check(lib().csc_mlp_adam_step(_dptr(params), _dptr(grad), _dptr(m), _dptr(v), t, lr, _stream(stream)),
+          "csc_mlp_adam_step")
+
+
+def csc_mlp_train(params: torch.Tensor, X: torch.Tensor, T: torch.Tensor, epochs: int, batch: int, lr: float,
+                  seed: int = 0, stream=None) -> np.ndarray:
+    """Minibatch Adam in place on `params`; returns the mean loss of each epoch."""
+    n = X.shape[0]
+    _f32_dev(params, (MLP_PARAMS,), "params")
+    _f32_dev(X, (n, nat.CSC_MLP_IN), "X")
+    _f32_dev(T, (n, nat.CSC_MLP_OUT), "T")
+    hist = np.zeros(max(epochs, 1), dtype=np.float64)
+    check(lib().csc_mlp_train(_dptr(params), _dptr(X), _dptr(T), n, epochs, batch, lr, seed, _hptr(hist),
+                              _stream(stream)), "csc_mlp_train")
+    return hist[:epochs]
+
+
+def csc_estimate_lambda_k_learned(g: Graph, k: int, params: torch.Tensor, norm: np.ndarray, m: int = 50,
+                                  n_probes: int = 0, seed: int = 0, widen: float = 1.0, refilter: bool = False,
+                                  stream=None):
+    """(LambdaInfo, predicted bracket (lo, hi))."""
+    _f32_dev(params, (MLP_PARAMS,), "params")
+    norm = np.ascontiguousarray(norm, dtype=np.float32)
+    if norm.shape != (2 * nat.CSC_MLP_IN + 2 * nat.CSC_MLP_OUT,):
+        raise ValueError("norm must hold feature mean, feature std, target mean, target std (148 floats)")
+    info = nat.csc_lambda_info()
+    br = np.zeros(2, dtype=np.float64)
+    flags = nat.CSC_EIGENCOUNT_REFILTER if refilter else 0
+    check(lib().csc_estimate_lambda_k_learned(g.handle, k, m, n_probes, seed, _dptr(params), _hptr(norm), widen,
+                                              flags, ctypes.byref(info), _hptr(br), _stream(stream)),
+          "csc_estimate_lambda_k_learned")
+    return _lambda_info(info), (float(br[0]), float(br[1]))
+
+
+def csc_estimate_lambda_k_refilter(g: Graph, k: int, m: int = 50, n_probes: int = 0, seed: int = 0, bracket=None,
+                                   stream=None) -> LambdaInfo:
+    """The paper-literal estimator: one filter pass over the probes per threshold."""
+    info = nat.csc_lambda_info()
+    br = None
+    if bracket is not None:
+        br_arr = np.ascontiguousarray(bracket, dtype=np.float64)
+        br = _hptr(br_arr)
+    check(lib().csc_estimate_lambda_k_refilter(g.handle, k, m, n_probes, seed, br, ctypes.byref(info),
+                                               _stream(stream)), "csc_estimate_lambda_k_refilter")
+    return _lambda_info(info)
+
+
 def csc_sample(N: int, n: int, seed: int = 0, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     if out is None:
         out = torch.empty(n, dtype=torch.int64, device="cuda")

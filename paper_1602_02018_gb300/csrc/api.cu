@@ -207,33 +207,86 @@ static double eigencount_host(const double* mu, int m, double lambda, bool jacks
 
 static long long round_half_away(double x) { return x >= 0 ? (long long)floor(x + 0.5) : -(long long)floor(-x + 0.5); }
 
-// Sec. 4.3 dichotomy on [lo, hi]: stop when round(count) == k.
-static void dichotomy(const double* mu, int m, int k, double lo, double hi, csc_lambda_info* out) {
-    std::vector<double> c;
+// Sec. 4.3 dichotomy on [lo, hi]: stop when round(count) == k.  `count(lambda,
+// &value)` evaluates the eigencount (host arithmetic on moments, or a filter
+// pass for the paper-literal estimator) and returns a status.
+template <typename CountFn>
+static csc_status dichotomy_fn(CountFn&& count, int k, double lo, double hi, csc_lambda_info* out) {
     for (int it = 1; it <= 60; ++it) {
         const double mid = 0.5 * (lo + hi);
-        const double cnt = eigencount_host(mu, m, mid, true, c);
+        double cnt = 0.0;
+        CSC_TRY(count(mid, &cnt));
         if (round_half_away(cnt) == k) {
             out->lambda = mid;
             out->count = cnt;
             out->iters = it;
             out->hit = 1;
-            return;
+            return CSC_OK;
         }
         if (cnt > (double)k) hi = mid;
         else lo = mid;
-        if (hi - lo < 1e-12) {
+        if (hi - lo < 1e-12 || it == 60) {
             out->lambda = hi;
-            out->count = eigencount_host(mu, m, hi, true, c);
+            CSC_TRY(count(hi, &out->count));
             out->iters = it;
             out->hit = 0;
-            return;
+            return CSC_OK;
         }
     }
-    out->lambda = hi;
-    out->count = eigencount_host(mu, m, hi, true, c);
-    out->iters = 60;
-    out->hit = 0;
+    return CSC_OK;
+}
+
+// The Sec. 4.3 halving started from a predicted cut-off c with half-width hw:
+// the count at c decides the side, the predicted end on that side (c - hw or
+// c + hw, clipped to [0, 2]) is evaluated next; when it lies across k the
+// halving continues inside the prediction, else on the remaining part of
+// [0, 2].  *inside tells whether the answer came from within [c - hw, c + hw].
+template <typename CountFn>
+static csc_status guarded_dichotomy(CountFn&& count, int k, double c, double hw, csc_lambda_info* out,
+                                    bool* inside) {
+    c = std::min(2.0, std::max(0.0, c));
+    double v = 0.0;
+    CSC_TRY(count(c, &v));
+    *inside = true;
+    if (round_half_away(v) == k) {
+        out->lambda = c;
+        out->count = v;
+        out->iters = 1;
+        out->hit = 1;
+        return CSC_OK;
+    }
+    const bool above = v > (double)k;  // answer below c
+    const double e = above ? std::max(0.0, c - hw) : std::min(2.0, c + hw);
+    double ve = 0.0;
+    CSC_TRY(count(e, &ve));
+    if (round_half_away(ve) == k) {
+        out->lambda = e;
+        out->count = ve;
+        out->iters = 2;
+        out->hit = 1;
+        return CSC_OK;
+    }
+    double lo, hi;
+    if (above) {
+        if (ve < (double)k) lo = e, hi = c;
+        else lo = 0.0, hi = e, *inside = false;
+    } else {
+        if (ve > (double)k) lo = c, hi = e;
+        else lo = e, hi = 2.0, *inside = false;
+    }
+    CSC_TRY(dichotomy_fn(count, k, lo, hi, out));
+    out->iters += 2;
+    return CSC_OK;
+}
+
+static void dichotomy(const double* mu, int m, int k, double lo, double hi, csc_lambda_info* out) {
+    std::vector<double> c;
+    dichotomy_fn(
+        [&](double lam, double* v) {
+            *v = eigencount_host(mu, m, lam, true, c);
+            return CSC_OK;
+        },
+        k, lo, hi, out);
 }
 
 // --------------------------------------------------------- reverse Cuthill-McKee
@@ -414,6 +467,20 @@ static csc_status upload(Graph* g, const HostCSR& h, const std::vector<int32_t>*
         g->h_light[i + 1] = g->h_light[i] + (dg > kHeavyRow ? 0 : dg);
     }
     g->n_heavy = (int)heavy.size();
+    {
+        // degree quantiles by counting sort (the sorted degree at index floor(p (N - 1)))
+        int64_t max_deg = 0;
+        for (int64_t i = 0; i < N; ++i) max_deg = std::max(max_deg, h.rp[i + 1] - h.rp[i]);
+        std::vector<int64_t> cnt(max_deg + 2, 0);
+        for (int64_t i = 0; i < N; ++i) ++cnt[h.rp[i + 1] - h.rp[i]];
+        static const double kQ[6] = {0.0, 0.1, 0.25, 0.5, 0.75, 1.0};
+        int64_t below = 0, dv = 0;
+        for (int q = 0; q < 6; ++q) {
+            const int64_t at = (int64_t)floor(kQ[q] * (double)(N - 1));
+            while (below + cnt[dv] <= at) below += cnt[dv++];
+            g->deg_quant[q] = (int32_t)dv;
+        }
+    }
     if (!heavy.empty()) {
         CSC_TRY(dev_alloc(&g->heavy, heavy.size()));
         CSC_CUDA_TRY(cudaMemcpy(g->heavy, heavy.data(), heavy.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -813,6 +880,190 @@ csc_status csc_estimate_lambda_k(csc_graph g, int32_t k, int32_t m, int32_t n_pr
         }
     }
     dichotomy(mu.data(), m, k, lo, hi, out);
+    return CSC_OK;
+}
+
+// ------------------------------------------------ learned lambda_k bracket
+
+// Smallest lambda in [0, 2] (60 halvings) where count(lambda) reaches `level`;
+// count is nondecreasing in lambda.
+static double count_crossing(const double* mu, int m, double level) {
+    std::vector<double> c;
+    double lo = 0.0, hi = 2.0;
+    for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (eigencount_host(mu, m, mid, true, c) < level) lo = mid;
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+static csc_status bracket_features(Graph* g, int k, uint64_t seed, float* feat, double* mu, int* passes,
+                                   cudaStream_t s) {
+    CSC_TRY(run_moments(g, CSC_BRACKET_MOMENTS, CSC_BRACKET_PROBES, seed, CSC_F32, mu, passes, s));
+    const int64_t N = g->N;
+    for (int j = 0; j < CSC_BRACKET_MOMENTS; ++j) feat[j] = (float)(mu[j] / (double)N);
+    feat[CSC_BRACKET_MOMENTS] = (float)log((double)N);
+    feat[CSC_BRACKET_MOMENTS + 1] = (float)k;
+    // degree quantiles (computed when the graph was created)
+    for (int q = 0; q < 6; ++q) feat[CSC_BRACKET_MOMENTS + 2 + q] = (float)log1p((double)g->deg_quant[q]);
+    return CSC_OK;
+}
+
+csc_status csc_bracket_features(csc_graph g, int32_t k, uint64_t seed, float* feat_out, double* mu_out,
+                                void* stream) {
+    clear_error();
+    CSC_TRY(check_graph(g));
+    if (k < 1 || !feat_out) {
+        set_error("csc_bracket_features: need k >= 1 and feat_out");
+        return CSC_E_INVALID;
+    }
+    double mu[CSC_BRACKET_MOMENTS];
+    int passes = 0;
+    csc_status st = bracket_features(g, k, seed, feat_out, mu, &passes, (cudaStream_t)stream);
+    if (st != CSC_OK) return poison_on_cuda(g, st);
+    if (mu_out) memcpy(mu_out, mu, sizeof(mu));
+    return CSC_OK;
+}
+
+csc_status csc_bracket_target(const double* mu, int32_t m, int32_t k, double* lo_hi_out) {
+    clear_error();
+    if (!mu || !lo_hi_out || m < 0 || k < 1) {
+        set_error("csc_bracket_target: invalid arguments");
+        return CSC_E_INVALID;
+    }
+    lo_hi_out[0] = count_crossing(mu, m, (double)k - 0.5);
+    lo_hi_out[1] = count_crossing(mu, m, (double)k + 0.5);
+    return CSC_OK;
+}
+
+// Paper-literal dichotomy: every threshold costs one filter pass over the probes.
+// A caller bracket is checked by the counts at its two ends first.
+static csc_status refilter_dichotomy(Graph* g, int k, int m, int n_probes, uint64_t seed, const double* bracket,
+                                     csc_lambda_info* out, int* products, cudaStream_t s) {
+    auto count = [&](double lam, double* v) -> csc_status {
+        *products += m;
+        return run_refilter_count(g, lam, m, n_probes, seed, v, s);
+    };
+    double lo = 0.0, hi = 2.0;
+    if (bracket && bracket[0] < bracket[1]) {
+        double clo = 0.0, chi = 0.0;
+        CSC_TRY(count(bracket[0], &clo));
+        CSC_TRY(count(bracket[1], &chi));
+        if (round_half_away(clo) <= k && k <= round_half_away(chi)) {
+            lo = bracket[0];
+            hi = bracket[1];
+            out->bracket_used = 1;
+        }
+    }
+    return dichotomy_fn(count, k, lo, hi, out);
+}
+
+csc_status csc_estimate_lambda_k_refilter(csc_graph g, int32_t k, int32_t m, int32_t n_probes, uint64_t seed,
+                                          const double* bracket, csc_lambda_info* out, void* stream) {
+    clear_error();
+    CSC_TRY(check_graph(g));
+    if (k < 1 || m < 1 || n_probes < 0 || !out ||
+        (bracket && !(bracket[0] >= 0.0 && bracket[0] < bracket[1] && bracket[1] <= 2.0))) {
+        set_error("csc_estimate_lambda_k_refilter: invalid arguments (k=%d m=%d n_probes=%d)", k, m, n_probes);
+        return CSC_E_INVALID;
+    }
+    if (n_probes == 0) n_probes = g->N > 1 ? (int)ceil(2.0 * log((double)g->N)) : 1;
+    memset(out, 0, sizeof(*out));
+    out->n_probes = n_probes;
+    out->m = m;
+    int products = 0;
+    csc_status st = refilter_dichotomy(g, k, m, n_probes, seed, bracket, out, &products, (cudaStream_t)stream);
+    out->moment_passes = products;
+    return poison_on_cuda(g, st);
+}
+
+csc_status csc_estimate_lambda_k_learned(csc_graph g, int32_t k, int32_t m, int32_t n_probes, uint64_t seed,
+                                         const float* params, const float* norm, double widen, uint32_t flags,
+                                         csc_lambda_info* out, double* bracket_out, void* stream) {
+    clear_error();
+    CSC_TRY(check_graph(g));
+    if (k < 1 || m < 1 || n_probes < 0 || !out || !params || !norm || !(widen > 0.0)) {
+        set_error("csc_estimate_lambda_k_learned: invalid arguments (k=%d m=%d n_probes=%d)", k, m, n_probes);
+        return CSC_E_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    float feat[CSC_MLP_IN];
+    double mu8[CSC_BRACKET_MOMENTS];
+    int passes8 = 0;
+    csc_status st = bracket_features(g, k, seed, feat, mu8, &passes8, s);
+    if (st != CSC_OK) return poison_on_cuda(g, st);
+    // standardise, run the network on the device, undo the target scaling
+    float* io = (float*)g->pinned + 64;  // pinned host staging (past the CG flags)
+    for (int i = 0; i < CSC_MLP_IN; ++i) {
+        const float sd = norm[CSC_MLP_IN + i];
+        io[i] = sd > 0.f ? (feat[i] - norm[i]) / sd : 0.f;
+    }
+    void* dbuf = nullptr;
+    CSC_TRY(ws_get(g, WS_MLP, 512, &dbuf));
+    float* dx = (float*)dbuf;
+    float* dy = dx + 96;
+    CSC_CUDA_TRY(cudaMemcpyAsync(dx, io, CSC_MLP_IN * sizeof(float), cudaMemcpyHostToDevice, s));
+    st = mlp_forward_device(params, dx, 1, dy, s);
+    if (st != CSC_OK) return poison_on_cuda(g, st);
+    CSC_CUDA_TRY(cudaMemcpyAsync(io + 96, dy, 2 * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CSC_CUDA_TRY(cudaStreamSynchronize(s));
+    const float* tm = norm + 2 * CSC_MLP_IN;
+    const double centre = (double)io[96] * tm[2] + tm[0];
+    const double lnhw = (double)io[97] * tm[3] + tm[1];
+    const double hw = widen * exp(std::min(lnhw, 10.0));
+    if (bracket_out) {
+        bracket_out[0] = std::max(0.0, centre - hw);
+        bracket_out[1] = std::min(2.0, centre + hw);
+    }
+    memset(out, 0, sizeof(*out));
+    out->m = m;
+    bool inside = false;
+    if (flags & CSC_EIGENCOUNT_REFILTER) {
+        // paper-literal estimator throughout, started from the prediction
+        if (n_probes == 0) n_probes = g->N > 1 ? (int)ceil(2.0 * log((double)g->N)) : 1;
+        out->n_probes = n_probes;
+        int products = passes8;
+        st = guarded_dichotomy(
+            [&](double lam, double* v) -> csc_status {
+                products += m;
+                return run_refilter_count(g, lam, m, n_probes, seed, v, s);
+            },
+            k, centre, hw, out, &inside);
+        out->moment_passes = products;
+        out->bracket_used = inside ? 1 : 0;
+        return poison_on_cuda(g, st);
+    }
+    if (m < CSC_BRACKET_MOMENTS) {
+        // moments-once on the 8-probe moments; accepted when found inside the prediction
+        std::vector<double> c;
+        csc_lambda_info trial;
+        memset(&trial, 0, sizeof(trial));
+        guarded_dichotomy(
+            [&](double lam, double* v) -> csc_status {
+                *v = eigencount_host(mu8, m, lam, true, c);
+                return CSC_OK;
+            },
+            k, centre, hw, &trial, &inside);
+        if (inside && trial.hit) {
+            *out = trial;
+            out->m = m;
+            out->n_probes = CSC_BRACKET_PROBES;
+            out->moment_passes = passes8;
+            out->bracket_used = 1;
+            return CSC_OK;
+        }
+    }
+    // the eigencount rejected the bracket: plain moments-once dichotomy
+    if (n_probes == 0) n_probes = g->N > 1 ? (int)ceil(2.0 * log((double)g->N)) : 1;
+    std::vector<double> mu(m + 1);
+    int passes = 0;
+    st = run_moments(g, m + 1, n_probes, seed, CSC_F32, mu.data(), &passes, s);
+    if (st != CSC_OK) return poison_on_cuda(g, st);
+    out->n_probes = n_probes;
+    out->moment_passes = passes8 + passes;
+    out->bracket_used = 0;
+    dichotomy(mu.data(), m, k, 0.0, 2.0, out);
     return CSC_OK;
 }
 

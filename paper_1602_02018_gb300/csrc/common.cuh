@@ -84,6 +84,8 @@ enum WsSlot {
     WS_KMEANS,      // k-means scratch
     WS_MISC,
     WS_PIPE,        // pipeline buffers of csc_cluster
+    WS_MLP,         // predictor input / output of the learned bracket
+    WS_REFILTER,    // filtered probes and partials of the paper-literal eigencount
     WS_COUNT
 };
 
@@ -126,6 +128,7 @@ struct Graph {
     Buffer ws[WS_COUNT];
     std::vector<int32_t> h_row_ptr;               // host copy of row_ptr (internal order)
     std::vector<int64_t> h_light;                 // prefix sums of the edges of non-heavy rows
+    int32_t deg_quant[6] = {0, 0, 0, 0, 0, 0};    // degrees at p = 0, .1, .25, .5, .75, 1 (floor(p (N-1)))
     int32_t* heavy = nullptr;                     // device int32[n_heavy]: heavy rows
     int n_heavy = 0;
     std::map<int, int32_t*> parts;                // P -> device int32[P+1] row-range bounds
@@ -165,6 +168,13 @@ csc_status run_filter(Graph* g, const double* coeffs, int m, int d, int d_pad, u
 // spmm.cu: eigencount moments (K2); mu_host receives n_moments values
 csc_status run_moments(Graph* g, int n_moments, int n_probes, uint64_t seed, csc_dtype storage,
                        double* mu_host, int* passes, cudaStream_t s);
+
+// spmm.cu: paper-literal eigencount at one cut-off (m sparse products)
+csc_status run_refilter_count(Graph* g, double lambda, int m, int n_probes, uint64_t seed, double* count,
+                              cudaStream_t s);
+
+// mlp.cu: Y = network(X) for B rows (device pointers)
+csc_status mlp_forward_device(const float* params, const float* X, int B, float* Y, cudaStream_t s);
 
 // sample.cu (K6)
 csc_status run_sample(int64_t N, int64_t n, uint64_t seed, int64_t* idx_out, Graph* scratch_owner,

@@ -74,6 +74,55 @@ __device__ __forceinline__ A row_scale(A dinv_i) {
 // ------------------------------------------------------------------- K3
 // One thread per (row, column quad): four normals from one Philox call.
 // Writes Z_0 = s R (row scale s of the pre-scaled form; `scale` = D^-1/2, NULL for none).
+// Entries 4q..4q+3 of row `orig` (original order) of the signal block: Philox4x32-10
+// with counter (orig, 0, q, 0) and key (seed_lo, seed_hi ^ stream), Box-Muller on
+// the two uniform pairs, times sigma; columns >= d are 0.
+__device__ __forceinline__ void gauss_quad(uint32_t orig, int q, int d, uint64_t seed, uint32_t stream, float sigma,
+                                           float (&z)[4]) {
+    z[0] = z[1] = z[2] = z[3] = 0.f;
+    if (4 * q >= d) return;
+    const Philox4 r = philox4x32_10(orig, 0u, (uint32_t)q, 0u, (uint32_t)seed, (uint32_t)(seed >> 32) ^ stream);
+    const float u0 = philox_uniform(r.x[0]), u1 = philox_uniform(r.x[1]);
+    const float u2 = philox_uniform(r.x[2]), u3 = philox_uniform(r.x[3]);
+    const float r01 = sqrtf(-2.0f * logf(u0));
+    const float r23 = sqrtf(-2.0f * logf(u2));
+    float s1, c1, s3, c3;
+    sincospif(2.0f * u1, &s1, &c1);
+    sincospif(2.0f * u3, &s3, &c3);
+    z[0] = r01 * c1; z[1] = r01 * s1; z[2] = r23 * c3; z[3] = r23 * s3;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) z[v] = (4 * q + v < d) ? z[v] * sigma : 0.f;
+}
+
+// Block partials of sum_i sum_c R[i, c] Y[i, c] with R regenerated from Philox
+// (probe stream, sigma 1) -- the trace estimate of Sec. 4.3 read literally:
+// count = (1/n_v) sum_l r_l^T h~(L) r_l.  Y is in original node order.
+// partials[3 b] = block sum, partials[3 b + 1 .. 2] = 0 (reduce_partials format).
+__global__ void __launch_bounds__(256) probe_trace_kernel(const float* __restrict__ Y, int32_t N, int d, int ld,
+                                                          uint64_t seed, double* __restrict__ partials) {
+    __shared__ double red[8];
+    const int quads = ld / 4;
+    double acc = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)N * quads;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int o = (int)(t / quads), q = (int)(t % quads);
+        float z[4];
+        gauss_quad((uint32_t)o, q, d, seed, STREAM_PROBES, 1.0f, z);
+        const float4 y = *reinterpret_cast<const float4*>(Y + (int64_t)o * ld + 4 * q);
+        acc += (double)z[0] * y.x + (double)z[1] * y.y + (double)z[2] * y.z + (double)z[3] * y.w;
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        partials[3 * (int64_t)blockIdx.x] = t;
+        partials[3 * (int64_t)blockIdx.x + 1] = 0.0;
+        partials[3 * (int64_t)blockIdx.x + 2] = 0.0;
+    }
+}
+
 template <typename T>
 __global__ void gauss_fill_kernel(T* __restrict__ X, int32_t N, int d, int ld, uint64_t seed,
                                   uint32_t stream, float sigma, const int32_t* __restrict__ perm,
@@ -85,21 +134,8 @@ __global__ void gauss_fill_kernel(T* __restrict__ X, int32_t N, int d, int ld, u
     const int row = (int)(t / quads);
     const int q = (int)(t % quads);
     const uint32_t orig = perm ? (uint32_t)perm[row] : (uint32_t)row;
-    float z[4] = {0.f, 0.f, 0.f, 0.f};
-    if (4 * q < d) {
-        const Philox4 r = philox4x32_10(orig, 0u, (uint32_t)q, 0u, (uint32_t)seed,
-                                        (uint32_t)(seed >> 32) ^ stream);
-        const float u0 = philox_uniform(r.x[0]), u1 = philox_uniform(r.x[1]);
-        const float u2 = philox_uniform(r.x[2]), u3 = philox_uniform(r.x[3]);
-        const float r01 = sqrtf(-2.0f * logf(u0));
-        const float r23 = sqrtf(-2.0f * logf(u2));
-        float s1, c1, s3, c3;
-        sincospif(2.0f * u1, &s1, &c1);
-        sincospif(2.0f * u3, &s3, &c3);
-        z[0] = r01 * c1; z[1] = r01 * s1; z[2] = r23 * c3; z[3] = r23 * s3;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) z[v] = (4 * q + v < d) ? z[v] * sigma : 0.f;
-    }
+    float z[4];
+    gauss_quad(orig, q, d, seed, stream, sigma, z);
     using A = typename Tr::acc_t;
     const A sc = scale ? row_scale<A>(scale[row]) : A(1);
     T* dst = X + (int64_t)row * ld + 4 * q;
@@ -735,7 +771,8 @@ static csc_status fill_block(Graph* g, T* X, int d, int ld, uint64_t seed, uint3
 
 template <typename T>
 static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pad, uint64_t seed,
-                               const float* R_in, void* Y_out, bool normalize, cudaStream_t s) {
+                               const float* R_in, void* Y_out, bool normalize, cudaStream_t s,
+                               uint32_t rng_stream = STREAM_SIGNALS, float sigma_override = 0.f) {
     using A = typename StoreTraits<T>::acc_t;
     constexpr int VEC = StoreTraits<T>::VEC;
     const int64_t N = g->N;
@@ -745,8 +782,8 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
     CSC_TRY(ws_get(g, WS_XB, bytes, &xb));
     T* X[2] = {(T*)xa, (T*)xb};
     A* Y = (A*)Y_out;
-    const float sigma = d > 0 ? (float)(1.0 / sqrt((double)d)) : 1.0f;
-    CSC_TRY(fill_block<T>(g, X[0], d, d_pad, seed, STREAM_SIGNALS, sigma, R_in, d_pad, s));
+    const float sigma = sigma_override > 0.f ? sigma_override : d > 0 ? (float)(1.0 / sqrt((double)d)) : 1.0f;
+    CSC_TRY(fill_block<T>(g, X[0], d, d_pad, seed, rng_stream, sigma, R_in, d_pad, s));
     if (m == 0) {
         const int64_t tot = N * d_pad;
         const A* sqd;
@@ -793,6 +830,33 @@ csc_status run_filter(Graph* g, const double* coeffs, int m, int d, int d_pad, u
             set_error("unknown storage type %d", (int)storage);
             return CSC_E_INVALID;
     }
+}
+
+// Paper-literal eigencount at one cut-off: filter n_probes N(0, 1) probes (the
+// probe stream of csc_kpm_moments) with the degree-m Jackson-Chebyshev step at
+// lambda, then count = (1/n_probes) sum_l r_l^T Y_l.  m sparse products.
+csc_status run_refilter_count(Graph* g, double lambda, int m, int n_probes, uint64_t seed, double* count,
+                              cudaStream_t s) {
+    const int64_t N = g->N;
+    const int ld = ((n_probes + 7) / 8) * 8;
+    std::vector<double> c(m + 1);
+    cheb_coefficients(lambda, m, true, c.data());
+    const int nblk = std::min(ceil_div(N * (ld / 4), 256), g->num_sms * 8);
+    void *yb = nullptr, *pb = nullptr;
+    CSC_TRY(ws_get(g, WS_REFILTER, (size_t)N * ld * sizeof(float) + 256 + ((size_t)nblk * 3 + 3) * 8, &yb));
+    float* Y = (float*)yb;
+    pb = (char*)yb + (((size_t)N * ld * sizeof(float) + 255) / 256) * 256;
+    double* part = (double*)pb;
+    double* sum = part + (size_t)nblk * 3;
+    CSC_TRY(filter_typed<float>(g, c.data(), m, n_probes, ld, seed, nullptr, Y, false, s, STREAM_PROBES, 1.0f));
+    CSC_KLAUNCH("probe_trace", 4.0 * N * ld, s,
+                probe_trace_kernel<<<nblk, 256, 0, s>>>(Y, (int32_t)N, n_probes, ld, seed, part));
+    CSC_KLAUNCH("reduce", 24.0 * nblk, s, reduce_partials_kernel<<<1, 256, 0, s>>>(part, nblk, sum));
+    double* host = g->pinned;
+    CSC_CUDA_TRY(cudaMemcpyAsync(host, sum, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CSC_CUDA_TRY(cudaStreamSynchronize(s));
+    *count = host[0] / (double)n_probes;
+    return CSC_OK;
 }
 
 template <typename T>
