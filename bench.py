@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--n-train", type=int, default=2000)
     ap.add_argument("--n-test", type=int, default=200)
     ap.add_argument("--save-data", default="", help="write the bracket features and targets (npz) here")
+    ap.add_argument("--batched", action="store_true",
+                    help="256 SBM graphs packed block-diagonally: graphs/s against one call per graph")
+    ap.add_argument("--n-graphs", type=int, default=256)
     ap.add_argument("--precision", action="store_true",
                     help="filter in FP64 / FP32 / BF16 storage on the workload: time, error vs FP64, label ARI")
     return ap.parse_args()
@@ -548,6 +551,72 @@ def run_learned(args):
     return 0
 
 
+def run_batched(args):
+    """Block-diagonal batch of SBM graphs (N log-uniform 2e3-5e4, k 5-50, mean degree 16,
+    eps = eps_c / 4, d = 32, m = 50): graphs/s of csc_cluster_batched on the packed handle
+    against one csc_cluster call per graph, and the per-graph ARI of both against the
+    planted communities.  Inputs are resident (handles built before timing)."""
+    import multiprocessing as mp
+
+    import numpy as np
+    import torch
+
+    import paper_1602_02018_gb300 as csc
+    from csc_inputs.datasets import batched_sbm_arrays
+
+    torch.cuda.set_device(0)
+    G = args.n_graphs
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
+        res = sorted(pool.map(batched_sbm_arrays, [(args.seed, b) for b in range(G)], chunksize=4),
+                     key=lambda r: r[0])
+    t_gen = time.perf_counter() - t0
+    ks = np.array([r[4] for r in res], dtype=np.int32)
+    sizes = np.array([len(r[1]) - 1 for r in res])
+    nnz = int(sum(len(r[2]) for r in res))
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    kw = dict(d=32, d_pad=32, m=50)
+    hb = csc.csc_graph_create_batched([(r[1], r[2]) for r in res])
+    singles = [csc.csc_graph_create(r[1], r[2]) for r in res]
+    # warm-up: launch-shape tuning of every handle
+    for _ in range(max(1, args.warmup)):
+        csc.csc_cluster_batched(hb, ks, seed=args.seed, **kw)
+    for h, k in zip(singles, ks):
+        csc.csc_cluster(h, int(k), seed=args.seed, **kw)
+    torch.cuda.synchronize()
+    steps = max(1, args.steps)
+    t_b, t_s = [], []
+    ari_b, ari_s = np.zeros(G), np.zeros(G)
+    for step in range(steps):
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        labels, lam, info = csc.csc_cluster_batched(hb, ks, seed=args.seed, **kw)
+        torch.cuda.synchronize()
+        t_b.append(time.perf_counter() - ta)
+        ta = time.perf_counter()
+        sep = [csc.csc_cluster(h, int(k), seed=args.seed, **kw)[0] for h, k in zip(singles, ks)]
+        torch.cuda.synchronize()
+        t_s.append(time.perf_counter() - ta)
+    lb = labels.cpu().numpy()
+    for i, r in enumerate(res):
+        ari_b[i] = adjusted_rand(lb[offs[i]:offs[i + 1]], r[3])
+        ari_s[i] = adjusted_rand(sep[i].cpu().numpy(), r[3])
+    tb, ts = statistics.median(t_b), statistics.median(t_s)
+    out = {"mode": "batched", "graphs": G, "nodes": int(offs[-1]), "nnz": nnz, "k_mean": float(ks.mean()),
+           "data_seconds": t_gen, "steps": steps, "warmup": args.warmup,
+           "batched_seconds": tb, "separate_seconds": ts,
+           "batched_graphs_per_s": G / tb, "separate_graphs_per_s": G / ts, "speedup": ts / tb,
+           "batched_stage_ms": info.ms, "cg_iters": info.cg.iters, "lambda_hits": info.lambda_hits,
+           "ari_batched_mean": float(ari_b.mean()), "ari_separate_mean": float(ari_s.mean()),
+           "ari_abs_diff_mean": float(np.abs(ari_b - ari_s).mean()),
+           "note": "inputs resident on the device; per-step wall time with a device synchronize"}
+    print(json.dumps(out), flush=True)
+    for h in singles:
+        h.close()
+    hb.close()
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -558,6 +627,8 @@ def main():
     w = WORKLOADS[args.workload]
     if args.learned:
         return run_learned(args)
+    if args.batched:
+        return run_batched(args)
     if args.precision:
         import torch
 

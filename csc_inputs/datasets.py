@@ -11,7 +11,8 @@ k uniform in ``k_range``.
     capped at N / 20 since these graphs have no planted communities.
 ``batched_sbm_set(seed)`` draws the block-diagonal batch: ``count`` SBMs with
 N log-uniform in ``n_range``, k uniform in ``k_range``, N rounded to a
-multiple of k, mean degree 16 and eps = eps_c / 4.
+multiple of k (at least 10 k), mean degree 16 and eps = eps_c / 4; graph b
+draws its size from its own generator, so graphs can be made in parallel.
 
 Only input generation lives here (no arithmetic of the clustering method).
 """
@@ -51,17 +52,27 @@ def bracket_graph(i: int, n_range: Tuple[float, float] = (1e4, 2e5),
     return g, k
 
 
+def batched_sbm_graph(seed: int, b: int, n_range: Tuple[float, float] = (2e3, 5e4),
+                      k_range: Tuple[int, int] = (5, 50)) -> Tuple[CSRGraph, int]:
+    """Graph b of the block-diagonal batch drawn with ``seed``, and its k."""
+    rng = np.random.Generator(np.random.PCG64(0x42415443 + 1000003 * seed + b))
+    n = int(round(_loguniform(rng, *n_range)))
+    k = int(rng.integers(k_range[0], k_range[1] + 1))
+    n = max(k * 10, (n // k) * k)
+    return sbm(n, k, s=16.0, seed=seed * 100003 + b), k
+
+
 def batched_sbm_set(seed: int = 0, count: int = 256, n_range: Tuple[float, float] = (2e3, 5e4),
                     k_range: Tuple[int, int] = (5, 50)) -> List[Tuple[CSRGraph, int]]:
     """``count`` SBM graphs of uneven size with their k (the block-diagonal batch)."""
-    rng = np.random.Generator(np.random.PCG64(0x42415443 + seed))
-    out = []
-    for b in range(count):
-        n = int(round(_loguniform(rng, *n_range)))
-        k = int(rng.integers(k_range[0], k_range[1] + 1))
-        n = max(k * 10, (n // k) * k)
-        out.append((sbm(n, k, s=16.0, seed=seed * 100003 + b), k))
-    return out
+    return [batched_sbm_graph(seed, b, n_range, k_range) for b in range(count)]
+
+
+def batched_sbm_arrays(args):
+    """Process-pool task: (seed, b) -> (b, row_ptr, col_idx, labels, k)."""
+    seed, b = args
+    g, k = batched_sbm_graph(seed, b)
+    return b, g.row_ptr, g.col_idx, g.labels, k
 
 
 def sizes_of(graphs: Sequence[Tuple[CSRGraph, int]]) -> np.ndarray:

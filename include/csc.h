@@ -123,6 +123,13 @@ typedef struct {
     float           ms_lambda, ms_filter, ms_sample, ms_kmeans, ms_interp, ms_total;
 } csc_cluster_info;
 
+/* Results and stage timings of csc_cluster_batched. */
+typedef struct {
+    csc_cg_info cg;               /* CG over all graphs' systems (max iterations / residual) */
+    int32_t     lambda_hits;      /* graphs whose dichotomy reached round(count) == k        */
+    float       ms_lambda, ms_filter, ms_sample, ms_kmeans, ms_interp, ms_total;
+} csc_batch_info;
+
 /* ---------------------------------------------------------------- graphs */
 
 /* csc_graph_create -- copy an undirected graph in CSR form into a new handle.
@@ -432,6 +439,71 @@ CSC_API csc_status csc_interpolate(csc_graph g, const int64_t* sample_idx, const
  * For a batched handle use csc_cluster_batched. */
 CSC_API csc_status csc_cluster(csc_graph g, const csc_params* params, int32_t* labels_out,
                        csc_cluster_info* info, void* stream);
+
+/* ------------------------------------------------------------ batches
+ * Alg. 2 on the G graphs of a handle made by csc_graph_create_batched: graph i
+ * owns the packed rows offsets[i] .. offsets[i+1]-1 (block-diagonal W), and
+ * every sparse product serves all graphs at once.  Graph i's results are those
+ * of the single-graph calls on graph i alone, except that the signal and probe
+ * blocks are drawn for the packed rows, and graph i samples and seeds k-means
+ * with seed + i.  Host arrays of per-graph values have G entries.  Node
+ * indices and labels are packed (graph i's node j is offsets[i] + j); labels
+ * are per-graph cluster numbers in [0, k_i). */
+
+/* csc_kpm_moments_batched -- the moments of csc_kpm_moments for each graph (the
+ * trace runs over the graph's own rows).  mu_out: host double[G x n_moments]. */
+CSC_API csc_status csc_kpm_moments_batched(csc_graph g, int32_t n_moments, int32_t n_probes, uint64_t seed,
+                                           csc_dtype storage, double* mu_out, void* stream);
+
+/* csc_estimate_lambda_k_batched -- csc_estimate_lambda_k per graph from one
+ * moment pass over the packed graph.  k: host int32[G] (1 <= k_i <= N_i).
+ * n_probes: 0 -> ceil(2 ln max_i N_i) for every graph.  lambda_out: host
+ * double[G]; info_out: NULL or host csc_lambda_info[G].  Synchronizes. */
+CSC_API csc_status csc_estimate_lambda_k_batched(csc_graph g, const int32_t* k, int32_t m, int32_t n_probes,
+                                                 uint64_t seed, double* lambda_out, csc_lambda_info* info_out,
+                                                 void* stream);
+
+/* csc_filter_batched -- csc_filter_random_signals with graph i's rows filtered at
+ * cut-off lambda[i] (host double[G], each in [0, 2]); m >= 1.  Y_out: device
+ * N x d_pad (packed rows), as for the single-graph call. */
+CSC_API csc_status csc_filter_batched(csc_graph g, const double* lambda, int32_t m, int32_t d, int32_t d_pad,
+                                      uint64_t seed, csc_dtype storage, const float* R_in, void* Y_out,
+                                      uint32_t flags, void* stream);
+
+/* csc_sample_batched -- csc_sample(N_i, n[i], seed + i) for every graph in one
+ * launch (one CTA per graph): idx_out (device int64[sum n]) holds graph 0's
+ * packed indices in increasing order, then graph 1's, ...  n: host int64[G],
+ * 0 <= n[i] <= N_i.  Synchronizes. */
+CSC_API csc_status csc_sample_batched(csc_graph g, const int64_t* n, uint64_t seed, int64_t* idx_out, void* stream);
+
+/* csc_kmeans_batched -- csc_kmeans_reduced on n_problems point sets in one launch:
+ * problem i has n[i] rows of X (device, stride ld) after those of problems < i,
+ * k[i] clusters and seed + i; labels_out: device int32[sum n], same row order.
+ * inertia_out: NULL or host double[n_problems].  Synchronizes. */
+CSC_API csc_status csc_kmeans_batched(const float* X, int32_t n_problems, const int64_t* n, const int32_t* k,
+                                      int32_t d, int32_t ld, int32_t replicates, int32_t max_iter, uint64_t seed,
+                                      int32_t* labels_out, double* inertia_out, void* stream);
+
+/* csc_interpolate_batched -- csc_interpolate per graph (Eq. 5): graph i solves
+ * its k[i] systems on its own rows; all systems share every sparse product and
+ * CG step, each with its own scalars and stopping test.  sample_idx: device
+ * int64[n_total] packed node indices; sample_labels: device int32[n_total],
+ * each below its graph's k.  labels_out: device int32[N]; fuzzy_out: NULL or
+ * device float[N x max_i k_i] (columns >= k_i untouched). */
+CSC_API csc_status csc_interpolate_batched(csc_graph g, const int64_t* sample_idx, const int32_t* sample_labels,
+                                           int64_t n_total, const int32_t* k, int32_t g_power, double gamma,
+                                           double rel_tol, int32_t max_iter, int32_t* labels_out, float* fuzzy_out,
+                                           csc_cg_info* info, void* stream);
+
+/* csc_cluster_batched -- Alg. 2 for every graph: csc_estimate_lambda_k_batched,
+ * csc_filter_batched (rows normalised), csc_sample_batched with n_i =
+ * ceil(2 k_i ln k_i), row gather, csc_kmeans_batched, csc_interpolate_batched.
+ * p: the shared parameters of csc_cluster (p->k, p->n, p->lambda_k and
+ * p->bracket are ignored; d defaults to ceil(4 ln max_i N_i)).  k: host
+ * int32[G].  labels_out: device int32[N].  lambda_out: NULL or host
+ * double[G].  info: NULL or host.  Synchronizes. */
+CSC_API csc_status csc_cluster_batched(csc_graph g, const int32_t* k, const csc_params* p, int32_t* labels_out,
+                                       double* lambda_out, csc_batch_info* info, void* stream);
 
 /* ------------------------------------------------------ instrumentation
  * Launch accounting (not a step of the paper's method): every kernel launch

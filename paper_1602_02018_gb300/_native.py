@@ -57,6 +57,11 @@ class csc_params(ctypes.Structure):
                 ("storage", c_int32), ("seed", c_uint64), ("lambda_k", c_double), ("bracket", P(c_double))]
 
 
+class csc_batch_info(ctypes.Structure):
+    _fields_ = [("cg", csc_cg_info), ("lambda_hits", c_int32), ("ms_lambda", c_float), ("ms_filter", c_float),
+                ("ms_sample", c_float), ("ms_kmeans", c_float), ("ms_interp", c_float), ("ms_total", c_float)]
+
+
 class csc_cluster_info(ctypes.Structure):
     _fields_ = [("lambda_", csc_lambda_info), ("cg", csc_cg_info), ("inertia", c_double),
                 ("ms_lambda", c_float), ("ms_filter", c_float), ("ms_sample", c_float),
@@ -90,6 +95,17 @@ _SIGNATURES = {
                                       c_uint32, P(csc_lambda_info), c_void_p, c_void_p],
     "csc_estimate_lambda_k_refilter": [c_void_p, c_int32, c_int32, c_int32, c_uint64, c_void_p,
                                        P(csc_lambda_info), c_void_p],
+    "csc_kpm_moments_batched": [c_void_p, c_int32, c_int32, c_uint64, c_int32, c_void_p, c_void_p],
+    "csc_estimate_lambda_k_batched": [c_void_p, c_void_p, c_int32, c_int32, c_uint64, c_void_p, c_void_p,
+                                      c_void_p],
+    "csc_filter_batched": [c_void_p, c_void_p, c_int32, c_int32, c_int32, c_uint64, c_int32, c_void_p, c_void_p,
+                           c_uint32, c_void_p],
+    "csc_sample_batched": [c_void_p, c_void_p, c_uint64, c_void_p, c_void_p],
+    "csc_kmeans_batched": [c_void_p, c_int32, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_uint64,
+                           c_void_p, c_void_p, c_void_p],
+    "csc_interpolate_batched": [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int32, c_double, c_double,
+                                c_int32, c_void_p, c_void_p, P(csc_cg_info), c_void_p],
+    "csc_cluster_batched": [c_void_p, c_void_p, P(csc_params), c_void_p, c_void_p, P(csc_batch_info), c_void_p],
     "csc_sample": [c_int64, c_int64, c_uint64, c_void_p, c_void_p],
     "csc_sample_noalloc": [c_int64, c_int64, c_uint64, c_void_p, c_void_p],
     "csc_gather_rows": [c_void_p, c_int64, c_int32, c_void_p, c_int64, c_int32, c_void_p, c_int32, c_void_p],

@@ -401,6 +401,110 @@ def csc_cluster(g: Graph, k: int, m: int = 0, d: int = 0, d_pad: int = 0, n: int
                                    info.inertia, ms)
 
 
+# ----------------------------------------------------------------- batches
+
+def graph_offsets(g: Graph, sizes) -> np.ndarray:
+    """Packed row offsets of a batch from its graphs' node counts."""
+    return np.concatenate([[0], np.cumsum(np.asarray(sizes, dtype=np.int64))])
+
+
+def csc_kpm_moments_batched(g: Graph, n_moments: int, n_probes: int, seed: int = 0, storage: int = F32,
+                            stream=None) -> np.ndarray:
+    out = np.empty((g.n_graphs, n_moments), dtype=np.float64)
+    check(lib().csc_kpm_moments_batched(g.handle, n_moments, n_probes, seed, storage, _hptr(out), _stream(stream)),
+          "csc_kpm_moments_batched")
+    return out
+
+
+def csc_estimate_lambda_k_batched(g: Graph, k, m: int = 50, n_probes: int = 0, seed: int = 0, stream=None):
+    """(lambda float64[G], [LambdaInfo] per graph)."""
+    kk = np.ascontiguousarray(k, dtype=np.int32)
+    lam = np.empty(g.n_graphs, dtype=np.float64)
+    infos = (nat.csc_lambda_info * g.n_graphs)()
+    check(lib().csc_estimate_lambda_k_batched(g.handle, _hptr(kk), m, n_probes, seed, _hptr(lam), infos,
+                                              _stream(stream)), "csc_estimate_lambda_k_batched")
+    return lam, [_lambda_info(x) for x in infos]
+
+
+def csc_filter_batched(g: Graph, lam, m: int, d: int, d_pad: Optional[int] = None, seed: int = 0,
+                       storage: int = F32, R_in: Optional[torch.Tensor] = None, Y_out: Optional[torch.Tensor] = None,
+                       flags: int = NORMALIZE_ROWS, stream=None) -> torch.Tensor:
+    d_pad = ((d + 7) // 8) * 8 if d_pad is None else d_pad
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    ydt = torch.float64 if storage == F64 else torch.float32
+    if Y_out is None:
+        Y_out = torch.empty((g.N, d_pad), dtype=ydt, device="cuda")
+    if R_in is not None and (R_in.dtype != torch.float32 or tuple(R_in.shape) != (g.N, d_pad)):
+        raise ValueError("R_in must be float32 of shape (N, d_pad)")
+    check(lib().csc_filter_batched(g.handle, _hptr(lam), m, d, d_pad, seed, storage, _dptr(R_in), _dptr(Y_out),
+                                   flags, _stream(stream)), "csc_filter_batched")
+    return Y_out
+
+
+def csc_sample_batched(g: Graph, n, seed: int = 0, stream=None) -> torch.Tensor:
+    nn = np.ascontiguousarray(n, dtype=np.int64)
+    out = torch.empty(int(nn.sum()), dtype=torch.int64, device="cuda")
+    check(lib().csc_sample_batched(g.handle, _hptr(nn), seed, _dptr(out), _stream(stream)), "csc_sample_batched")
+    return out
+
+
+def csc_kmeans_batched(X: torch.Tensor, n, k, d: Optional[int] = None, replicates: int = 20, max_iter: int = 100,
+                       seed: int = 0, stream=None):
+    """(labels int32[sum n] on the device, inertia float64[problems])."""
+    nn = np.ascontiguousarray(n, dtype=np.int64)
+    kk = np.ascontiguousarray(k, dtype=np.int32)
+    ld = X.shape[1]
+    d = ld if d is None else d
+    labels = torch.empty(int(nn.sum()), dtype=torch.int32, device="cuda")
+    inertia = np.empty(nn.size, dtype=np.float64)
+    check(lib().csc_kmeans_batched(_dptr(X), nn.size, _hptr(nn), _hptr(kk), d, ld, replicates, max_iter, seed,
+                                   _dptr(labels), _hptr(inertia), _stream(stream)), "csc_kmeans_batched")
+    return labels, inertia
+
+
+def csc_interpolate_batched(g: Graph, sample_idx: torch.Tensor, sample_labels: torch.Tensor, k, g_power: int = 4,
+                            gamma: float = 1e-3, rel_tol: float = 1e-6, max_iter: int = 2000, fuzzy: bool = False,
+                            stream=None):
+    kk = np.ascontiguousarray(k, dtype=np.int32)
+    labels = torch.empty(g.N, dtype=torch.int32, device="cuda")
+    fz = torch.zeros((g.N, int(kk.max())), dtype=torch.float32, device="cuda") if fuzzy else None
+    info = nat.csc_cg_info()
+    check(lib().csc_interpolate_batched(g.handle, _dptr(sample_idx), _dptr(sample_labels), sample_idx.numel(),
+                                        _hptr(kk), g_power, gamma, rel_tol, max_iter, _dptr(labels), _dptr(fz),
+                                        ctypes.byref(info), _stream(stream)),
+          "csc_interpolate_batched", allow=(nat.CSC_E_NOT_CONVERGED,))
+    return labels, fz, CgInfo(info.iters, bool(info.converged), info.max_rel_residual)
+
+
+@dataclass
+class BatchInfo:
+    cg: CgInfo
+    lambda_hits: int
+    ms: dict
+
+
+def csc_cluster_batched(g: Graph, k, m: int = 0, d: int = 0, d_pad: int = 0, n_probes: int = 0, g_power: int = 0,
+                        gamma: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0, replicates: int = 0,
+                        km_max_iter: int = 0, storage: int = F32, seed: int = 0,
+                        labels_out: Optional[torch.Tensor] = None, stream=None):
+    """Alg. 2 for every graph of a batched handle.  Returns (labels, lambda float64[G], BatchInfo)."""
+    kk = np.ascontiguousarray(k, dtype=np.int32)
+    p = nat.csc_params()
+    p.k, p.m, p.d, p.d_pad, p.n, p.n_probes, p.g_power = 0, m, d, d_pad, 0, n_probes, g_power
+    p.gamma, p.cg_tol, p.cg_max_iter, p.replicates, p.km_max_iter = gamma, cg_tol, cg_max_iter, replicates, km_max_iter
+    p.storage, p.seed, p.lambda_k = storage, seed, 0.0
+    if labels_out is None:
+        labels_out = torch.empty(g.N, dtype=torch.int32, device="cuda")
+    lam = np.empty(g.n_graphs, dtype=np.float64)
+    info = nat.csc_batch_info()
+    check(lib().csc_cluster_batched(g.handle, _hptr(kk), ctypes.byref(p), _dptr(labels_out), _hptr(lam),
+                                    ctypes.byref(info), _stream(stream)), "csc_cluster_batched")
+    ms = dict(lambda_k=info.ms_lambda, filter=info.ms_filter, sample=info.ms_sample, kmeans=info.ms_kmeans,
+              interp=info.ms_interp, total=info.ms_total)
+    return labels_out, lam, BatchInfo(CgInfo(info.cg.iters, bool(info.cg.converged), info.cg.max_rel_residual),
+                                      info.lambda_hits, ms)
+
+
 def csc_profile_enable(on: bool = True) -> None:
     check(lib().csc_profile_enable(1 if on else 0), "csc_profile_enable")
 

@@ -18,9 +18,6 @@
 
 #include "common.cuh"
 
-// The opaque handle of the C ABI is the internal graph record.
-struct csc_graph_s : public csc::Graph {};
-
 namespace csc {
 
 // ---------------------------------------------------------------- errors
@@ -88,6 +85,25 @@ void tune_cache_put(const Graph* g, uint64_t key, const LaunchCfg& cfg) {
     g_tune_cache[TuneKey{key, g->device, g->N, g->nnz}] = cfg;
 }
 
+// Row ranges [bounds[b], bounds[b+1]) of rows lo..hi-1 split q ways with equal cost,
+// cost(r) = light edges before r + 2r (nondecreasing).
+static void split_rows(const std::vector<int64_t>& rp, int64_t lo, int64_t hi, int q, int32_t* bounds) {
+    const double c0 = (double)rp[lo] + 2.0 * (double)lo;
+    const double total = (double)rp[hi] + 2.0 * (double)hi - c0;
+    int64_t a0 = lo;
+    for (int b = 1; b < q; ++b) {
+        const double target = c0 + total * (double)b / (double)q;
+        int64_t a = a0, z = hi;
+        while (a < z) {
+            const int64_t mid = (a + z) / 2;
+            if ((double)rp[mid] + 2.0 * (double)mid >= target) z = mid;
+            else a = mid + 1;
+        }
+        a0 = a;
+        bounds[b] = (int32_t)a;
+    }
+}
+
 csc_status get_partition(Graph* g, int P, const int32_t** out) {
     auto it = g->parts.find(P);
     if (it != g->parts.end()) {
@@ -96,23 +112,49 @@ csc_status get_partition(Graph* g, int P, const int32_t** out) {
     }
     const int64_t N = g->N;
     const std::vector<int64_t>& rp = g->h_light;  // heavy rows' edges are swept elsewhere
-    // cost(r) = light edges before r + 2r is nondecreasing: boundary b = first row with
-    // cost >= b * total / P
-    const double total = (double)rp[N] + 2.0 * (double)N;
     std::vector<int32_t> bounds(P + 1);
     bounds[0] = 0;
     bounds[P] = (int32_t)N;
-    int64_t lo = 0;
-    for (int b = 1; b < P; ++b) {
-        const double target = total * (double)b / (double)P;
-        int64_t a = lo, z = N;
-        while (a < z) {
-            const int64_t mid = (a + z) / 2;
-            if ((double)rp[mid] + 2.0 * (double)mid >= target) z = mid;
-            else a = mid + 1;
+    std::vector<int32_t> gblk;
+    const int G = g->n_graphs;
+    if (G <= 1) {
+        split_rows(rp, 0, N, P, bounds.data());
+        gblk = {0, P};
+    } else {
+        // batched handle: every range inside one graph (per-graph sums then need no
+        // segmentation inside a CTA); graph i gets 1 + its cost share of the other P - G
+        if (P < G) {
+            set_error("a row partition of a batch of %d graphs needs at least %d ranges (got %d)", G, G, P);
+            return CSC_E_INVALID;
         }
-        lo = a;
-        bounds[b] = (int32_t)a;
+        std::vector<double> cost(G);
+        double total = 0.0;
+        for (int i = 0; i < G; ++i) {
+            const int64_t a = g->offsets[i], b = g->offsets[i + 1];
+            cost[i] = (double)(rp[b] - rp[a]) + 2.0 * (double)(b - a);
+            total += cost[i];
+        }
+        std::vector<int> q(G);
+        std::vector<std::pair<double, int>> frac(G);
+        int used = 0;
+        for (int i = 0; i < G; ++i) {
+            const double share = total > 0 ? (double)(P - G) * cost[i] / total : 0.0;
+            q[i] = 1 + (int)floor(share);
+            frac[i] = {-(share - floor(share)), i};
+            used += q[i];
+        }
+        std::sort(frac.begin(), frac.end());  // largest remainder first, ties to the lower graph
+        for (int r = 0; used < P; ++r, ++used) ++q[frac[r % G].second];
+        gblk.assign(G + 1, 0);
+        int b = 0;
+        for (int i = 0; i < G; ++i) {
+            gblk[i] = b;
+            bounds[b] = (int32_t)g->offsets[i];
+            split_rows(rp, g->offsets[i], g->offsets[i + 1], q[i], bounds.data() + b);
+            bounds[b] = (int32_t)g->offsets[i];
+            b += q[i];
+        }
+        gblk[G] = P;
     }
     int32_t* d = nullptr;
     cudaError_t e = cudaMalloc(&d, (P + 1) * sizeof(int32_t));
@@ -124,7 +166,46 @@ csc_status get_partition(Graph* g, int P, const int32_t** out) {
     CSC_CUDA_TRY(cudaMemcpy(d, bounds.data(), (P + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     g->parts[P] = d;
     g->h_parts[P] = bounds;
+    int32_t* dg = nullptr;
+    e = cudaMalloc(&dg, gblk.size() * sizeof(int32_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc for partition segments: %s", cudaGetErrorString(e));
+        return CSC_E_OOM;
+    }
+    CSC_CUDA_TRY(cudaMemcpy(dg, gblk.data(), gblk.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    g->part_gblk[P] = dg;
     *out = d;
+    return CSC_OK;
+}
+
+csc_status get_segments(Graph* g, int P, const int32_t** gblk, const int32_t** ghvy) {
+    const int32_t* part = nullptr;
+    CSC_TRY(get_partition(g, P, &part));
+    *gblk = g->part_gblk[P];
+    if (!g->d_hvy_start) {
+        // first heavy row of each graph (the heavy list is in increasing row order)
+        const int G = g->n_graphs < 1 ? 1 : g->n_graphs;
+        std::vector<int32_t> hs(G + 1, 0);
+        std::vector<int32_t> heavy(g->n_heavy);
+        if (g->n_heavy)
+            CSC_CUDA_TRY(cudaMemcpy(heavy.data(), g->heavy, g->n_heavy * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        for (int i = 0; i <= G; ++i) {
+            const int64_t off = G == 1 ? (i == 0 ? 0 : g->N) : g->offsets[i];
+            hs[i] = (int32_t)(std::lower_bound(heavy.begin(), heavy.end(), (int32_t)std::min<int64_t>(off, INT32_MAX)) -
+                              heavy.begin());
+        }
+        hs[G] = g->n_heavy;
+        cudaError_t e = cudaMalloc(&g->d_hvy_start, (G + 1) * sizeof(int32_t));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            g->d_hvy_start = nullptr;
+            set_error("cudaMalloc for heavy-row segments: %s", cudaGetErrorString(e));
+            return CSC_E_OOM;
+        }
+        CSC_CUDA_TRY(cudaMemcpy(g->d_hvy_start, hs.data(), (G + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    *ghvy = g->d_hvy_start;
     return CSC_OK;
 }
 
@@ -289,6 +370,8 @@ static void dichotomy(const double* mu, int m, int k, double lo, double hi, csc_
         k, lo, hi, out);
 }
 
+void estimate_from_moments(const double* mu, int m, int k, csc_lambda_info* out) { dichotomy(mu, m, k, 0.0, 2.0, out); }
+
 // --------------------------------------------------------- reverse Cuthill-McKee
 // Cuthill & McKee (1969), reversed (George 1971): BFS from a minimum-degree
 // node of each component, visiting neighbours by increasing degree; the
@@ -423,6 +506,8 @@ static void free_graph(Graph* g) {
     cudaFree(g->graph_of_row);
     for (auto& b : g->ws) cudaFree(b.ptr);
     for (auto& kv : g->parts) cudaFree(kv.second);
+    for (auto& kv : g->part_gblk) cudaFree(kv.second);
+    cudaFree(g->d_hvy_start);
     for (auto& kv : g->wins) cudaFree(kv.second);
     cudaFree(g->dev_err);
     cudaFree(g->heavy);

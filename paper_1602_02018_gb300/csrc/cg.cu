@@ -67,11 +67,31 @@ __device__ __forceinline__ void block_column_partials(KSum (&acc)[NS][NT][4], in
     }
 }
 
-#define CG_TILE(G, NT)                                   \
-    const int lane = threadIdx.x % (G);                  \
-    const int col0 = blockIdx.y * ((G) * (NT) * 4);      \
-    const int tcols = min((G) * (NT) * 4, ncols - col0); \
-    const int r1 = part[blockIdx.x + 1];
+// Batch view of the CG kernels (all members NULL for one graph): gid = graph of
+// each row, gk4 = each graph's k rounded up to a multiple of 4 (the columns its
+// rows carry; the rest stay zero), gact = each graph's columns still iterating
+// (a graph with none left is skipped: its x, r and p no longer change).
+struct CgBatch {
+    const int32_t* gid = nullptr;
+    const int32_t* gk4 = nullptr;
+    const int* gact = nullptr;
+    __device__ __forceinline__ int cols(int row, int ncols) const {
+        if (!gid) return ncols;
+        const int gr = gid[row];
+        if (gact && gact[gr] == 0) return 0;
+        return min(ncols, gk4[gr]);
+    }
+};
+
+// Column tile of this CTA; a CTA whose graph needs no column of the tile (or has
+// converged) leaves at once -- uniformly, before any barrier.
+#define CG_TILE(G, NT)                                                          \
+    const int lane = threadIdx.x % (G);                                         \
+    const int col0 = blockIdx.y * ((G) * (NT) * 4);                             \
+    const int r1 = part[blockIdx.x + 1];                                        \
+    const int ncols_b = part[blockIdx.x] < r1 ? bt.cols(part[blockIdx.x], ncols) : ncols; \
+    const int tcols = min((G) * (NT) * 4, ncols_b - col0);                      \
+    if (tcols <= 0) return;
 #define CG_ROWS(G) \
     for (int row = part[blockIdx.x] + (int)(threadIdx.x / (G)); row < r1; row += (int)(blockDim.x / (G)))
 
@@ -104,7 +124,7 @@ template <int G, int NT, bool WIN>
 __global__ void __launch_bounds__(kCgMaxThreads)
 lap_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ dinv,
            const float* __restrict__ invdeg, const float* __restrict__ in, float* __restrict__ out,
-           const int32_t* __restrict__ part, int ncols, int64_t ld) {
+           const int32_t* __restrict__ part, int ncols, int64_t ld, CgBatch bt) {
     CG_TILE(G, NT)
     CG_ROWS(G) {
         const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
@@ -120,11 +140,12 @@ template <int G, int NT, bool WIN>
 __global__ void __launch_bounds__(kHeavyThreads)
 lap_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ dinv,
                  const float* __restrict__ invdeg, const float* __restrict__ in, float* __restrict__ out,
-                 const int32_t* __restrict__ heavy, int ncols, int64_t ld) {
+                 const int32_t* __restrict__ heavy, int ncols, int64_t ld, CgBatch bt) {
     const int lane = threadIdx.x % G;
     const int col0 = blockIdx.y * (G * NT * 4);
-    const int tcols = min(G * NT * 4, ncols - col0);
     const int row = heavy[blockIdx.x];
+    const int tcols = min(G * NT * 4, bt.cols(row, ncols) - col0);
+    if (tcols <= 0) return;
     float acc[NT][4];
     gather_heavy<float, G, NT, WIN, float>(__ldg(rp + row), __ldg(rp + row + 1), ci, dinv, in + col0, ld, lane, tcols,
                                            acc);
@@ -166,7 +187,7 @@ __global__ void __launch_bounds__(kCgMaxThreads)
 lap_ax_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ dinv,
               const float* __restrict__ sqdeg, const float* __restrict__ tin, const float* __restrict__ p,
               const float* __restrict__ mask, float gamma, float* __restrict__ Ap, const int32_t* __restrict__ part,
-              int ncols, int64_t ld, double* __restrict__ partials, int nslots) {
+              int ncols, int64_t ld, double* __restrict__ partials, int nslots, CgBatch bt) {
     CG_TILE(G, NT)
     KSum dot[1][NT][4];
     CG_ROWS(G) {
@@ -185,11 +206,12 @@ lap_ax_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ 
                     const float* __restrict__ sqdeg, const float* __restrict__ tin, const float* __restrict__ p,
                     const float* __restrict__ mask, float gamma, float* __restrict__ Ap,
                     const int32_t* __restrict__ heavy, int ncols, int64_t ld, double* __restrict__ partials,
-                    int slot_base, int nslots) {
+                    int slot_base, int nslots, CgBatch bt) {
     const int lane = threadIdx.x % G;
     const int col0 = blockIdx.y * (G * NT * 4);
-    const int tcols = min(G * NT * 4, ncols - col0);
     const int row = heavy[blockIdx.x];
+    const int tcols = min(G * NT * 4, bt.cols(row, ncols) - col0);
+    if (tcols <= 0) return;
     float acc[NT][4];
     gather_heavy<float, G, NT, WIN, float>(__ldg(rp + row), __ldg(rp + row + 1), ci, dinv, tin + col0, ld, lane,
                                            tcols, acc);
@@ -203,17 +225,20 @@ lap_ax_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ 
 template <int G, int NT>
 __global__ void __launch_bounds__(kCgMaxThreads)
 cg_update_kernel(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ p,
-                 const float* __restrict__ Ap, const double* __restrict__ alpha, const float* __restrict__ pinv,
-                 const int32_t* __restrict__ part, int ncols, int64_t ld, double* __restrict__ partials) {
+                 const float* __restrict__ Ap, const double* __restrict__ alpha, const int32_t* __restrict__ gid,
+                 const float* __restrict__ pinv, const int32_t* __restrict__ part, int ncols, int64_t ld,
+                 double* __restrict__ partials, CgBatch bt) {
     CG_TILE(G, NT)
     KSum dots[2][NT][4];
     float al[NT][4];
+    // the columns' scalars of this range's graph (a batch's ranges lie inside one graph)
+    const int64_t sg = (gid && part[blockIdx.x] < r1) ? (int64_t)gid[part[blockIdx.x]] * ld : 0;
 #pragma unroll
     for (int t = 0; t < NT; ++t)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int c = (t * G + lane) * 4 + v;
-            al[t][v] = (alpha && c < tcols) ? (float)alpha[col0 + c] : 0.f;
+            al[t][v] = (alpha && c < tcols) ? (float)alpha[sg + col0 + c] : 0.f;
         }
     CG_ROWS(G) {
         const float pi = pinv[row];
@@ -252,15 +277,17 @@ cg_update_kernel(float* __restrict__ x, float* __restrict__ r, const float* __re
 template <int G, int NT>
 __global__ void __launch_bounds__(kCgMaxThreads)
 cg_pupdate_kernel(const float* __restrict__ r, float* __restrict__ p, const double* __restrict__ beta,
-                  const float* __restrict__ pinv, const int32_t* __restrict__ part, int ncols, int64_t ld) {
+                  const int32_t* __restrict__ gid, const float* __restrict__ pinv, const int32_t* __restrict__ part,
+                  int ncols, int64_t ld, CgBatch bt) {
     CG_TILE(G, NT)
     float be[NT][4];
+    const int64_t sg = (gid && part[blockIdx.x] < r1) ? (int64_t)gid[part[blockIdx.x]] * ld : 0;
 #pragma unroll
     for (int t = 0; t < NT; ++t)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int c = (t * G + lane) * 4 + v;
-            be[t][v] = c < tcols ? (float)beta[col0 + c] : 0.f;
+            be[t][v] = c < tcols ? (float)beta[sg + col0 + c] : 0.f;
         }
     CG_ROWS(G) {
         const float pi = pinv[row];
@@ -283,7 +310,7 @@ cg_pupdate_kernel(const float* __restrict__ r, float* __restrict__ p, const doub
 template <int G, int NT>
 __global__ void __launch_bounds__(kCgMaxThreads)
 residual_kernel(const float* __restrict__ Ax, const int32_t* __restrict__ slab, const int32_t* __restrict__ part,
-                int ncols, int64_t ld, double* __restrict__ partials) {
+                int ncols, int64_t ld, double* __restrict__ partials, CgBatch bt) {
     CG_TILE(G, NT)
     KSum acc[1][NT][4];
     CG_ROWS(G) {
@@ -309,7 +336,7 @@ residual_kernel(const float* __restrict__ Ax, const int32_t* __restrict__ slab, 
 template <int G, int NT>
 __global__ void __launch_bounds__(kCgMaxThreads)
 colnorm_kernel(const float* __restrict__ x, const int32_t* __restrict__ part, int ncols, int64_t ld,
-               double* __restrict__ partials) {
+               double* __restrict__ partials, CgBatch bt) {
     CG_TILE(G, NT)
     KSum acc[1][NT][4];
     CG_ROWS(G) {
@@ -337,20 +364,46 @@ struct CgState {
     int* n_active;
 };
 
-// Column sums of block partials in a fixed order: a 32 x 16 thread block covers
-// 32 columns; thread row y sums blocks y, y+16, ... (coalesced across columns),
-// then the 16 row sums are added in order.
+// Which partial slots belong to graph blockIdx.y of a batch: row ranges
+// [gblk[y], gblk[y+1]) and heavy rows [ghvy[y], ghvy[y+1]) (slots P + h); with
+// gblk == nullptr there is one graph: ranges [0, P), heavy rows [0, H).
+struct Segs {
+    const int32_t* gblk = nullptr;
+    const int32_t* ghvy = nullptr;
+    const int32_t* gk = nullptr;  // each graph's k (columns at or past it are not iterated)
+    int* gact = nullptr;          // each graph's count of columns still iterating
+    int P = 0, H = 0;
+    __device__ __forceinline__ int kg(int g, int k) const { return gk ? gk[g] : k; }
+    __device__ __forceinline__ void get(int g, int& b0, int& b1, int& h0, int& h1) const {
+        b0 = gblk ? gblk[g] : 0;
+        b1 = gblk ? gblk[g + 1] : P;
+        h0 = ghvy ? ghvy[g] : 0;
+        h1 = ghvy ? ghvy[g + 1] : H;
+    }
+};
+
+// Column sums of block partials of one graph in a fixed order: a 32 x 16 thread
+// block covers 32 columns; thread row y sums slots y, y+16, ... of the graph's
+// row ranges, then (heavy = true) of its heavy rows, coalesced across columns;
+// then the 16 row sums are added in order.  nslots: the stride between the NS
+// quantities' slot arrays.
 template <int NS>
-__device__ __forceinline__ void reduce_columns(const double* __restrict__ partials, int nblocks, int64_t ldp, int j,
-                                               double (&out)[NS]) {
+__device__ __forceinline__ void reduce_columns(const double* __restrict__ partials, int nslots, const Segs& sg,
+                                               bool heavy, int64_t ldp, int j, double (&out)[NS]) {
     __shared__ double red[NS][16][33];
     const int x = threadIdx.x, y = threadIdx.y;
+    int b0, b1, h0, h1;
+    sg.get(blockIdx.y, b0, b1, h0, h1);
     double s[NS];
 #pragma unroll
     for (int q = 0; q < NS; ++q) s[q] = 0.0;
-    for (int b = y; b < nblocks; b += 16)
+    for (int b = b0 + y; b < b1; b += 16)
 #pragma unroll
-        for (int q = 0; q < NS; ++q) s[q] += partials[((int64_t)q * nblocks + b) * ldp + j];
+        for (int q = 0; q < NS; ++q) s[q] += partials[((int64_t)q * nslots + b) * ldp + j];
+    if (heavy)
+        for (int h = h0 + y; h < h1; h += 16)
+#pragma unroll
+            for (int q = 0; q < NS; ++q) s[q] += partials[((int64_t)q * nslots + sg.P + h) * ldp + j];
 #pragma unroll
     for (int q = 0; q < NS; ++q) red[q][y][x] = s[q];
     __syncthreads();
@@ -362,63 +415,75 @@ __device__ __forceinline__ void reduce_columns(const double* __restrict__ partia
     }
 }
 
-// pAp_j = sum of partials; alpha_j = rz_j / pAp_j for active columns.
-__global__ void __launch_bounds__(512) cg_alpha_kernel(const double* __restrict__ partials, int nblocks, int k,
-                                                       int64_t ldp, CgState st) {
-    const int j = blockIdx.x * 32 + threadIdx.x;
+// pAp_j = sum of partials (row ranges and heavy rows); alpha_j = rz_j / pAp_j for
+// active columns.  Graph blockIdx.y's column j lives at state index y * ldp + j.
+__global__ void __launch_bounds__(512) cg_alpha_kernel(const double* __restrict__ partials, int nslots, Segs sg,
+                                                       int k, int64_t ldp, CgState st) {
+    const int jc = blockIdx.x * 32 + threadIdx.x;
     double s[1];
-    reduce_columns<1>(partials, nblocks, ldp, j < k ? j : 0, s);
-    if (threadIdx.y != 0 || j >= k) return;
+    reduce_columns<1>(partials, nslots, sg, true, ldp, jc < k ? jc : 0, s);
+    if (threadIdx.y != 0 || jc >= sg.kg(blockIdx.y, k)) return;
+    const int64_t j = (int64_t)blockIdx.y * ldp + jc;
     st.alpha[j] = (st.active[j] && s[0] != 0.0) ? st.rz[j] / s[0] : 0.0;
 }
 
 // After an update: rz_new, rr; convergence; beta.  init != 0: first call (sets bn2, active).
-__global__ void __launch_bounds__(512) cg_beta_kernel(const double* __restrict__ partials, int nblocks, int k,
-                                                      int64_t ldp, CgState st, double tol2, int init) {
-    const int j = blockIdx.x * 32 + threadIdx.x;
+__global__ void __launch_bounds__(512) cg_beta_kernel(const double* __restrict__ partials, int nslots, Segs sg,
+                                                      int k, int64_t ldp, CgState st, double tol2, int init) {
+    const int jc = blockIdx.x * 32 + threadIdx.x;
     double s2[2];
-    reduce_columns<2>(partials, nblocks, ldp, j < k ? j : 0, s2);
-    if (threadIdx.y != 0 || j >= k) return;
+    reduce_columns<2>(partials, nslots, sg, false, ldp, jc < k ? jc : 0, s2);
+    if (threadIdx.y != 0 || jc >= sg.kg(blockIdx.y, k)) return;
+    const int64_t j = (int64_t)blockIdx.y * ldp + jc;
+    int act = st.active[j];
+    if (!init && !act) return;  // a finished column keeps its state (its graph may be skipped)
     const double rz = s2[0], rr = s2[1];
     st.rr[j] = rr;
     if (init) {
         st.bn2[j] = rr;
         st.rz[j] = rz;
         st.beta[j] = 0.0;
-        const int act = rr > 0.0 ? 1 : 0;
-        st.active[j] = act;
-        if (act) atomicAdd(st.n_active, 1);
-        return;
+        act = rr > 0.0 ? 1 : 0;
+    } else {
+        if (rr <= tol2 * st.bn2[j]) act = 0;
+        st.beta[j] = (act && st.rz[j] != 0.0) ? rz / st.rz[j] : 0.0;
+        st.rz[j] = rz;
     }
-    int act = st.active[j];
-    if (act && rr <= tol2 * st.bn2[j]) act = 0;
-    st.beta[j] = (act && st.rz[j] != 0.0) ? rz / st.rz[j] : 0.0;
-    st.rz[j] = rz;
     st.active[j] = act;
-    if (act) atomicAdd(st.n_active, 1);
+    if (act) {
+        atomicAdd(st.n_active, 1);
+        if (sg.gact) atomicAdd(sg.gact + blockIdx.y, 1);
+    }
 }
 
-__global__ void __launch_bounds__(512) column_sum_kernel(const double* __restrict__ partials, int nblocks, int k,
-                                                         int64_t ldp, double* __restrict__ out) {
+__global__ void __launch_bounds__(512) column_sum_kernel(const double* __restrict__ partials, int nslots, Segs sg,
+                                                         int k, int64_t ldp, double* __restrict__ out) {
     const int j = blockIdx.x * 32 + threadIdx.x;
     double s[1];
-    reduce_columns<1>(partials, nblocks, ldp, j < k ? j : 0, s);
-    if (threadIdx.y == 0 && j < k) out[j] = s[0];
+    reduce_columns<1>(partials, nslots, sg, false, ldp, j < k ? j : 0, s);
+    if (threadIdx.y == 0 && j < sg.kg(blockIdx.y, k)) out[(int64_t)blockIdx.y * ldp + j] = s[0];
 }
 
+// gk / gid (batched handle): a sample's label must be below its graph's k.
 __global__ void cg_setup_kernel(const int64_t* __restrict__ sample_idx, const int32_t* __restrict__ sample_labels,
                                 int64_t n, int64_t N, const int32_t* __restrict__ iperm, float* __restrict__ r,
                                 float* __restrict__ mask, int32_t* __restrict__ slab, int64_t ld, int k,
+                                const int32_t* __restrict__ gk, const int32_t* __restrict__ gid,
                                 int* __restrict__ bad) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t node = sample_idx[i];
     const int lab = sample_labels[i];
-    if (lab < 0 || lab >= k || node < 0 || node >= N) {
+    if (node < 0 || node >= N) {
         atomicOr(bad, 1);
         return;
     }
     const int64_t row = iperm ? iperm[node] : node;
+    const int kk = gk ? gk[gid[row]] : k;
+    if (lab < 0 || lab >= kk) {
+        atomicOr(bad, 1);
+        return;
+    }
     r[row * ld + lab] = 1.0f;
     mask[row] = 1.0f;
     slab[row] = lab;
@@ -430,11 +495,15 @@ __global__ void precond_kernel(const float* __restrict__ mask, float gamma, floa
 }
 
 // label(i) = argmax_j x_ij / ||x_j|| (fp64 comparison, ties to the lowest j); one thread per row.
-__global__ void label_argmax_kernel(const float* __restrict__ x, const double* __restrict__ norm2, int32_t N, int k,
-                                    int64_t ld, const int32_t* __restrict__ perm, int32_t* __restrict__ labels,
-                                    float* __restrict__ fuzzy) {
+__global__ void label_argmax_kernel(const float* __restrict__ x, const double* __restrict__ norm2_all, int32_t N,
+                                    int k_all, int64_t ld, const int32_t* __restrict__ gk,
+                                    const int32_t* __restrict__ gid, const int32_t* __restrict__ perm,
+                                    int32_t* __restrict__ labels, float* __restrict__ fuzzy) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= N) return;
+    const int gr = gid ? gid[row] : 0;
+    const int k = gk ? gk[gr] : k_all;
+    const double* norm2 = norm2_all + (int64_t)gr * ld;
     const float* xr = x + (int64_t)row * ld;
     int best = 0;
     double bv = -INFINITY;
@@ -449,7 +518,7 @@ __global__ void label_argmax_kernel(const float* __restrict__ x, const double* _
     const int64_t orig = perm ? perm[row] : row;
     labels[orig] = best;
     if (fuzzy)
-        for (int j = 0; j < k; ++j) fuzzy[orig * k + j] = xr[j];
+        for (int j = 0; j < k; ++j) fuzzy[orig * k_all + j] = xr[j];
 }
 
 // ------------------------------------------------------------- dispatch
@@ -491,8 +560,10 @@ static csc_status cg_occupancy(const LaunchCfg& c, int* out) {
 
 csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* sample_labels, int64_t n, int k,
                            int g_power, double gamma, double rel_tol, int max_iter, int32_t* labels_out,
-                           float* fuzzy_out, csc_cg_info* info, cudaStream_t s) {
+                           float* fuzzy_out, csc_cg_info* info, cudaStream_t s, const int32_t* k_graphs) {
     const int32_t N = (int32_t)g->N;
+    // one independent set of k systems per graph of a batch (k_graphs: each graph's k)
+    const int nseg = (k_graphs && g->n_graphs > 1) ? g->n_graphs : 1;
     const int ld = ((k + 3) / 4) * 4;
     const int nv = ld / 4;
     // candidate shapes: column tiles of 4*G*NT floats with at most a third idle
@@ -522,6 +593,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
             for (int waves = 1; waves <= 8; waves *= 2) {
                 int P = (g->num_sms * occ * waves + tiles - 1) / tiles;
                 if (P > lim) P = (int)lim;
+                if (P < g->n_graphs) P = g->n_graphs;  // a batch needs a range per graph
                 c.P = P < 1 ? 1 : P;
                 if (!cands.empty() && cands.back().G == c.G && cands.back().NT == c.NT &&
                     cands.back().threads == th && cands.back().P == c.P)
@@ -563,7 +635,9 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const size_t o_mask = take((size_t)N * 4), o_pinv = take((size_t)N * 4), o_slab = take((size_t)N * 4);
     // two quantities per row-range block; <p, A p> also has one slot per heavy row
     const size_t o_part = take((size_t)2 * (max_p + g->n_heavy) * ld * 8);
-    const size_t o_state = take((size_t)ld * 8 * 6 + (size_t)ld * 4 + 64);
+    const size_t sl = (size_t)nseg * ld;  // per-(graph, column) state length
+    const size_t o_state = take(sl * 8 * 6 + sl * 4 + 64);
+    const size_t o_gk = take((size_t)nseg * 4 * 3);
     void* base = nullptr;
     CSC_TRY(ws_get(g, WS_CG, off, &base));
     char* b = (char*)base;
@@ -580,14 +654,35 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     double* sd = (double*)(b + o_state);
     CgState st;
     st.rz = sd;
-    st.bn2 = sd + ld;
-    st.alpha = sd + 2 * ld;
-    st.beta = sd + 3 * ld;
-    st.rr = sd + 4 * ld;
-    double* norm2 = sd + 5 * ld;
-    st.active = (int*)(sd + 6 * ld);
-    st.n_active = st.active + ld;
+    st.bn2 = sd + sl;
+    st.alpha = sd + 2 * sl;
+    st.beta = sd + 3 * sl;
+    st.rr = sd + 4 * sl;
+    double* norm2 = sd + 5 * sl;
+    st.active = (int*)(sd + 6 * sl);
+    st.n_active = st.active + sl;
     int* bad = st.n_active + 1;
+    int32_t* d_gk = nullptr;
+    const int32_t* gid = nullptr;
+    CgBatch bt, bt_all;  // bt also skips finished graphs; bt_all only narrows the columns
+    std::vector<int32_t> hk;
+    if (nseg > 1) {
+        d_gk = (int32_t*)(b + o_gk);
+        int32_t* d_gk4 = d_gk + nseg;
+        int* d_gact = (int*)(d_gk4 + nseg);
+        hk.assign(k_graphs, k_graphs + nseg);
+        for (int q = 0; q < nseg; ++q) hk.push_back((k_graphs[q] + 3) / 4 * 4);
+        CSC_CUDA_TRY(cudaMemcpyAsync(d_gk, hk.data(), (size_t)2 * nseg * 4, cudaMemcpyHostToDevice, s));
+        CSC_CUDA_TRY(cudaMemsetAsync(d_gact, 0, (size_t)nseg * 4, s));
+        gid = g->graph_of_row;
+        bt.gid = bt_all.gid = gid;
+        bt.gk4 = bt_all.gk4 = d_gk4;
+        bt.gact = d_gact;
+        // columns past a graph's k are never written: keep them zero
+        CSC_CUDA_TRY(cudaMemsetAsync(p, 0, blk, s));
+        CSC_CUDA_TRY(cudaMemsetAsync(Ap, 0, blk, s));
+    }
+    CSC_CUDA_TRY(cudaMemsetAsync(sd, 0, sl * 8 * 6 + sl * 4, s));
 
     // zero x, r, mask; slab = -1
     CSC_CUDA_TRY(cudaMemsetAsync(x, 0, blk, s));
@@ -597,7 +692,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     CSC_CUDA_TRY(cudaMemsetAsync(st.n_active, 0, 2 * sizeof(int), s));
     CSC_KLAUNCH("cg_setup", 24.0 * n, s,
                 cg_setup_kernel<<<ceil_div(n, 256), 256, 0, s>>>(sample_idx, sample_labels, n, (int64_t)N, g->iperm,
-                                                                 r, mask, slab, ld, k, bad));
+                                                                 r, mask, slab, ld, k, d_gk, gid, bad));
     CSC_KLAUNCH("cg_setup", 8.0 * N, s, precond_kernel<<<ceil_div(N, 256), 256, 0, s>>>(mask, (float)gamma, pinv, N));
 
     // launch shape: tuned on the middle product of the chain (the dominant kernel),
@@ -620,7 +715,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                 for (int rep = 0; rep < 4; ++rep) {
                     if (rep == 1) cudaEventRecord(g->ev[0], s);
                     CG_SWITCH(c, lap_kernel<G_, NT_, false><<<grid, c.threads, 0, s>>>(
-                                     g->row_ptr, g->col_idx, g->dinv, g->invdeg, r, t1, pr, ld, ld));
+                                     g->row_ptr, g->col_idx, g->dinv, g->invdeg, r, t1, pr, ld, ld, CgBatch()));
                 }
                 cudaEventRecord(g->ev[1], s);
                 CSC_CUDA_TRY(cudaEventSynchronize(g->ev[1]));
@@ -644,6 +739,19 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const int H = (int)g->n_heavy;
     const int PH = P + H;  // <p, A p> partial slots
     const dim3 hgrid(H > 0 ? H : 1, cfg.tiles);
+    Segs sg;
+    sg.P = P;
+    sg.H = H;
+    if (nseg > 1) {
+        CSC_TRY(get_segments(g, P, &sg.gblk, &sg.ghvy));
+        sg.gk = d_gk;
+        sg.gact = (int*)bt.gact;
+    }
+    auto reset_active = [&]() -> csc_status {
+        CSC_CUDA_TRY(cudaMemsetAsync(st.n_active, 0, sizeof(int), s));
+        if (sg.gact) CSC_CUDA_TRY(cudaMemsetAsync(sg.gact, 0, (size_t)nseg * sizeof(int), s));
+        return CSC_OK;
+    };
 
     // algorithmic bytes per launch of each CG kernel (fp32 N x ld blocks)
     const double blkb = (double)N * ld * 4.0;
@@ -652,14 +760,16 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const double scal_ax = 8.0 * PH * ld;
     // share of the sparse bytes that falls on heavy rows (launched separately)
     const double heavy_frac = g->nnz > 0 ? (double)(g->nnz - g->h_light.back()) / (double)g->nnz : 0.0;
-    const int kb = ceil_div(k, 32);
+    const dim3 kb(ceil_div(k, 32), nseg);
     const dim3 rb(32, 16);
     CG_SWITCH(cfg, CSC_KLAUNCH("cg_update", blkb + 4.0 * N, s,
-                               cg_update_kernel<G_, NT_><<<grid, th, 0, s>>>(x, r, p, Ap, nullptr, pinv, rpart, ld, ld,
-                                                                             part)));
-    CSC_KLAUNCH("cg_scalar", 2 * scal_b, s, cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, k, ld, st, rel_tol * rel_tol, 1));
+                               cg_update_kernel<G_, NT_><<<grid, th, 0, s>>>(x, r, p, Ap, nullptr, gid, pinv, rpart, ld,
+                                                                             ld, part, bt_all)));
+    CSC_KLAUNCH("cg_scalar", 2 * scal_b, s,
+                cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, st, rel_tol * rel_tol, 1));
     CG_SWITCH(cfg, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
-                               cg_pupdate_kernel<G_, NT_><<<grid, th, 0, s>>>(r, p, st.beta, pinv, rpart, ld, ld)));
+                               cg_pupdate_kernel<G_, NT_><<<grid, th, 0, s>>>(r, p, st.beta, gid, pinv, rpart, ld,
+                                                                              ld, bt)));
     int* h_active = (int*)g->pinned;
     CSC_CUDA_TRY(cudaMemcpyAsync(h_active, st.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CSC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -667,7 +777,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         set_error("csc_interpolate: a sample label is outside [0, k) or a sample index outside [0, N)");
         return CSC_E_INVALID;
     }
-    auto apply_A = [&](const float* in) -> csc_status {
+    auto apply_A = [&](const float* in, const CgBatch& bb) -> csc_status {
         // t = L^(p-1) in, then Ap = mask*in + gamma * L t with <in, Ap> partials
         const float* cur = in;
         float* bufs[2] = {t1, t2};
@@ -681,19 +791,21 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                     CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * heavy_frac, s,
                                                lap_heavy_kernel<G_, NT_, true><<<hgrid, kHeavyThreads, 0, s>>>(
                                                    g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, g->heavy, ld,
-                                                   ld)));
+                                                   ld, bb)));
                 CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * (1.0 - heavy_frac), s,
                                            lap_kernel<G_, NT_, true><<<grid, th, 0, s>>>(
-                                               g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, rpart, ld, ld)));
+                                               g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, rpart, ld, ld,
+                                               bb)));
             } else {
                 if (H > 0)
                     CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * heavy_frac, s,
                                                lap_heavy_kernel<G_, NT_, false><<<hgrid, kHeavyThreads, 0, s>>>(
                                                    g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, g->heavy, ld,
-                                                   ld)));
+                                                   ld, bb)));
                 CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * (1.0 - heavy_frac), s,
                                            lap_kernel<G_, NT_, false><<<grid, th, 0, s>>>(
-                                               g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, rpart, ld, ld)));
+                                               g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, rpart, ld, ld,
+                                               bb)));
             }
             cur = o;
         }
@@ -704,21 +816,21 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                 CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * heavy_frac, s,
                                            lap_ax_heavy_kernel<G_, NT_, true><<<hgrid, kHeavyThreads, 0, s>>>(
                                                g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma,
-                                               Ap, g->heavy, ld, ld, part, P, PH)));
+                                               Ap, g->heavy, ld, ld, part, P, PH, bb)));
             CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * (1.0 - heavy_frac), s,
                                        lap_ax_kernel<G_, NT_, true><<<grid, th, 0, s>>>(
                                            g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
-                                           rpart, ld, ld, part, PH)));
+                                           rpart, ld, ld, part, PH, bb)));
         } else {
             if (H > 0)
                 CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * heavy_frac, s,
                                            lap_ax_heavy_kernel<G_, NT_, false><<<hgrid, kHeavyThreads, 0, s>>>(
                                                g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma,
-                                               Ap, g->heavy, ld, ld, part, P, PH)));
+                                               Ap, g->heavy, ld, ld, part, P, PH, bb)));
             CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * (1.0 - heavy_frac), s,
                                        lap_ax_kernel<G_, NT_, false><<<grid, th, 0, s>>>(
                                            g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
-                                           rpart, ld, ld, part, PH)));
+                                           rpart, ld, ld, part, PH, bb)));
         }
         return CSC_OK;
     };
@@ -728,18 +840,18 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     while (!converged && it < max_iter) {
         const int batch = std::min(check_every, max_iter - it);
         for (int q = 0; q < batch; ++q) {
-            CSC_TRY(apply_A(p));
-            CSC_KLAUNCH("cg_scalar", scal_ax, s, cg_alpha_kernel<<<kb, rb, 0, s>>>(part, PH, k, ld, st));
+            CSC_TRY(apply_A(p, bt));
+            CSC_KLAUNCH("cg_scalar", scal_ax, s, cg_alpha_kernel<<<kb, rb, 0, s>>>(part, PH, sg, k, ld, st));
             // x, r, p, Ap read; x, r written
             CG_SWITCH(cfg, CSC_KLAUNCH("cg_update", 6 * blkb + 4.0 * N + 2 * scal_b, s,
-                                       cg_update_kernel<G_, NT_><<<grid, th, 0, s>>>(x, r, p, Ap, st.alpha, pinv, rpart,
-                                                                                     ld, ld, part)));
-            CSC_CUDA_TRY(cudaMemsetAsync(st.n_active, 0, sizeof(int), s));
+                                       cg_update_kernel<G_, NT_><<<grid, th, 0, s>>>(x, r, p, Ap, st.alpha, gid, pinv,
+                                                                                     rpart, ld, ld, part, bt)));
+            CSC_TRY(reset_active());
             CSC_KLAUNCH("cg_scalar", 2 * scal_b, s,
-                        cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, k, ld, st, rel_tol * rel_tol, 0));
+                        cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, st, rel_tol * rel_tol, 0));
             CG_SWITCH(cfg, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
-                                       cg_pupdate_kernel<G_, NT_><<<grid, th, 0, s>>>(r, p, st.beta, pinv, rpart, ld,
-                                                                                      ld)));
+                                       cg_pupdate_kernel<G_, NT_><<<grid, th, 0, s>>>(r, p, st.beta, gid, pinv, rpart,
+                                                                                      ld, ld, bt)));
         }
         it += batch;
         CSC_CUDA_TRY(cudaMemcpyAsync(h_active, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -747,24 +859,27 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         converged = h_active[0] == 0;
     }
     // true residual ||b - A x|| / ||b|| per column
-    CSC_TRY(apply_A(x));
+    CSC_TRY(apply_A(x, bt_all));
     CG_SWITCH(cfg, CSC_KLAUNCH("cg_residual", blkb + 4.0 * N, s,
-                               residual_kernel<G_, NT_><<<grid, th, 0, s>>>(Ap, slab, rpart, ld, ld, part)));
-    CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, rb, 0, s>>>(part, P, k, ld, st.rr));
+                               residual_kernel<G_, NT_><<<grid, th, 0, s>>>(Ap, slab, rpart, ld, ld, part, bt_all)));
+    CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, st.rr));
     // labels
     CG_SWITCH(cfg, CSC_KLAUNCH("label_norms", blkb, s,
-                               colnorm_kernel<G_, NT_><<<grid, th, 0, s>>>(x, rpart, ld, ld, part)));
-    CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, rb, 0, s>>>(part, P, k, ld, norm2));
+                               colnorm_kernel<G_, NT_><<<grid, th, 0, s>>>(x, rpart, ld, ld, part, bt_all)));
+    CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, norm2));
     CSC_KLAUNCH("label_argmax", blkb + 4.0 * N + (fuzzy_out ? (double)N * k * 4 : 0.0), s,
-                label_argmax_kernel<<<ceil_div(N, 256), 256, 0, s>>>(x, norm2, N, k, ld, g->perm, labels_out,
-                                                                     fuzzy_out));
-    std::vector<double> rr(k), bn(k);
-    CSC_CUDA_TRY(cudaMemcpyAsync(rr.data(), st.rr, k * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CSC_CUDA_TRY(cudaMemcpyAsync(bn.data(), st.bn2, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+                label_argmax_kernel<<<ceil_div(N, 256), 256, 0, s>>>(x, norm2, N, k, ld, d_gk, gid, g->perm,
+                                                                     labels_out, fuzzy_out));
+    std::vector<double> rr(sl), bn(sl);
+    CSC_CUDA_TRY(cudaMemcpyAsync(rr.data(), st.rr, sl * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CSC_CUDA_TRY(cudaMemcpyAsync(bn.data(), st.bn2, sl * sizeof(double), cudaMemcpyDeviceToHost, s));
     CSC_CUDA_TRY(cudaStreamSynchronize(s));
     double worst = 0.0;
-    for (int j = 0; j < k; ++j)
-        if (bn[j] > 0) worst = std::max(worst, sqrt(rr[j] / bn[j]));
+    for (int q = 0; q < nseg; ++q)
+        for (int j = 0; j < k; ++j) {
+            const size_t i = (size_t)q * ld + j;
+            if (bn[i] > 0) worst = std::max(worst, sqrt(rr[i] / bn[i]));
+        }
     if (info) {
         info->iters = it;
         info->converged = converged ? 1 : 0;

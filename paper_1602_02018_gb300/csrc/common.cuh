@@ -86,6 +86,7 @@ enum WsSlot {
     WS_PIPE,        // pipeline buffers of csc_cluster
     WS_MLP,         // predictor input / output of the learned bracket
     WS_REFILTER,    // filtered probes and partials of the paper-literal eigencount
+    WS_COEF,        // per-graph filter coefficients of a batch
     WS_COUNT
 };
 
@@ -133,6 +134,8 @@ struct Graph {
     int n_heavy = 0;
     std::map<int, int32_t*> parts;                // P -> device int32[P+1] row-range bounds
     std::map<int, std::vector<int32_t>> h_parts;  // host copies of the bounds
+    std::map<int, int32_t*> part_gblk;            // P -> device int32[G+1]: first range of each graph
+    int32_t* d_hvy_start = nullptr;               // device int32[G+1]: first heavy row of each graph
     std::map<std::pair<int, int>, int32_t*> wins; // (P, W) -> device int32[P] window starts
     int* dev_err = nullptr;                       // device error word (bounded waits that gave up)
     std::map<uint64_t, LaunchCfg> tuned;          // (kernel kind, dtype, columns) -> shape
@@ -150,6 +153,9 @@ void tune_cache_put(const Graph* g, uint64_t key, const LaunchCfg& cfg);
 
 // P contiguous row ranges of about equal cost (edges + 2 per row); cached per P.
 csc_status get_partition(Graph* g, int P, const int32_t** out);
+// Per-graph segments of partition P: first range of each graph (device int32[G+1]; a
+// batched handle's ranges never straddle graphs) and first heavy row of each graph.
+csc_status get_segments(Graph* g, int P, const int32_t** gblk, const int32_t** ghvy);
 
 // Start rows of the W-row windows (one per row range of partition P) that cover
 // the most neighbour indices of each range; cached per (P, W).
@@ -161,13 +167,17 @@ csc_status get_windows(Graph* g, int P, int W, const int32_t** out);
 csc_status launch_degrees(Graph* g, cudaStream_t s);
 
 // spmm.cu: the Jackson-Chebyshev filter (K3 + K1 + K5)
+// Batched handle: c_graphs is host double[n_graphs x (m + 1)], graph i's coefficients.
+csc_status run_filter_batched(Graph* g, const double* c_graphs, int m, int d, int d_pad, uint64_t seed,
+                              csc_dtype storage, const float* R_in, void* Y_out, bool normalize, cudaStream_t s);
 csc_status run_filter(Graph* g, const double* coeffs, int m, int d, int d_pad, uint64_t seed,
                       csc_dtype storage, const float* R_in, void* Y_out, bool normalize,
                       cudaStream_t s);
 
 // spmm.cu: eigencount moments (K2); mu_host receives n_moments values
+// per_graph: one moment vector per graph of a batched handle (mu_host: n_graphs x n_moments)
 csc_status run_moments(Graph* g, int n_moments, int n_probes, uint64_t seed, csc_dtype storage,
-                       double* mu_host, int* passes, cudaStream_t s);
+                       double* mu_host, int* passes, cudaStream_t s, bool per_graph = false);
 
 // spmm.cu: paper-literal eigencount at one cut-off (m sparse products)
 csc_status run_refilter_count(Graph* g, double lambda, int m, int n_probes, uint64_t seed, double* count,
@@ -185,17 +195,33 @@ csc_status run_gather_rows_f64(const double* X, int64_t N, int ld, const int64_t
                                float* out, int ld_out, cudaStream_t s);
 
 // kmeans.cu (K7)
+// One k-means problem of run_kmeans_multi: n points at X (rows of stride ld), k
+// clusters, the replicate seed, and the device output labels[n].
+struct KmTask {
+    const float* X = nullptr;
+    int n = 0, k = 0;
+    uint64_t seed = 0;
+    int32_t* labels_out = nullptr;
+};
+// Several k-means problems in one launch (grid y = problem); inertia_out: NULL or
+// host double[tasks.size()].  Synchronizes s.
+csc_status run_kmeans_multi(const std::vector<KmTask>& tasks, int d, int ld, int reps, int max_iter,
+                            double* inertia_out, Graph* owner, cudaStream_t s);
 csc_status run_kmeans(const float* X, int64_t n, int d, int ld, int k, int replicates, int max_iter,
                       uint64_t seed, int32_t* labels_out, double* inertia_out, Graph* scratch_owner,
                       cudaStream_t s);
 
-// cg.cu (K8 + K9)
+// cg.cu (K8 + K9).  k_graphs: NULL, or (batched handle) host int32[n_graphs], each
+// graph's k (k = their maximum): one set of systems per graph.
 csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* sample_labels,
                            int64_t n, int k, int g_power, double gamma, double rel_tol, int max_iter,
-                           int32_t* labels_out, float* fuzzy_out, csc_cg_info* info, cudaStream_t s);
+                           int32_t* labels_out, float* fuzzy_out, csc_cg_info* info, cudaStream_t s,
+                           const int32_t* k_graphs = nullptr);
 
 // host math (api.cu)
 void cheb_coefficients(double lambda_c, int m, bool jackson, double* c);
+// The Sec. 4.3 dichotomy on [0, 2] from degree-m moments (fills lambda, count, iters, hit).
+void estimate_from_moments(const double* mu, int m, int k, csc_lambda_info* out);
 
 // Philox4x32-10 and SplitMix64 stream identifiers (the key's high word is
 // xor-ed with these so that signals, probes and k-means draws are disjoint).
@@ -206,3 +232,7 @@ constexpr uint32_t STREAM_KMEANS = 0x4B4D4541u;
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 }  // namespace csc
+
+// The opaque handle of the C ABI is the internal graph record.
+struct csc_graph_s : public csc::Graph {};
+

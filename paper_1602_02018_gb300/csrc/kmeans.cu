@@ -18,6 +18,10 @@
 // to the first) wins.
 #include <cooperative_groups.h>
 #include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "device.cuh"
@@ -98,9 +102,24 @@ __device__ double km_block_scan(double v, double* warp_tot, double* tot) {
     return warp_tot[w] + x - v;
 }
 
+// One k-means problem of a launch (blockIdx.y): points X[0..n) (rows of stride ld),
+// k clusters, its seed, and where its replicates' labels (reps x n) and inertias go.
+struct KmProblem {
+    const float* X;
+    int n, k;
+    uint64_t seed;
+    int32_t* labels_all;
+    double* inertia_all;
+};
+
 __global__ void __launch_bounds__(kKmThreads)
-kmeans_cluster_kernel(const float* __restrict__ X, int n, int d, int ld, int k, int max_iter, uint64_t seed,
-                      int32_t* __restrict__ labels_all, double* __restrict__ inertia_all) {
+kmeans_cluster_kernel(const KmProblem* __restrict__ probs, int d, int ld, int max_iter) {
+    const KmProblem pr = probs[blockIdx.y];
+    const float* __restrict__ X = pr.X;
+    const int n = pr.n, k = pr.k;
+    const uint64_t seed = pr.seed;
+    int32_t* __restrict__ labels_all = pr.labels_all;
+    double* __restrict__ inertia_all = pr.inertia_all;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ KmShared S;
     cg::cluster_group cluster = cg::this_cluster();
@@ -367,8 +386,15 @@ kmeans_cluster_kernel(const float* __restrict__ X, int n, int d, int ld, int k, 
     cluster.sync();  // every CTA's shared memory stays alive until rank 0 has read it
 }
 
-__global__ void kmeans_pick_kernel(const int32_t* __restrict__ labels_all, const double* __restrict__ inertia_all,
-                                   int reps, int n, int32_t* __restrict__ labels_out, double* __restrict__ inertia_out) {
+// Best replicate of problem blockIdx.y (ties to the first): labels to out[y], inertia to inertia_out[y].
+__global__ void kmeans_pick_kernel(const KmProblem* __restrict__ probs, int reps, int32_t* const* __restrict__ out,
+                                   double* __restrict__ inertia_out_all) {
+    const KmProblem pr = probs[blockIdx.y];
+    const int32_t* __restrict__ labels_all = pr.labels_all;
+    const double* __restrict__ inertia_all = pr.inertia_all;
+    const int n = pr.n;
+    int32_t* __restrict__ labels_out = out[blockIdx.y];
+    double* __restrict__ inertia_out = inertia_out_all + blockIdx.y;
     __shared__ int best;
     if (threadIdx.x == 0) {
         int b = 0;
@@ -381,25 +407,34 @@ __global__ void kmeans_pick_kernel(const int32_t* __restrict__ labels_all, const
     for (int i = threadIdx.x; i < n; i += blockDim.x) labels_out[i] = labels_all[(int64_t)best * n + i];
 }
 
-csc_status run_kmeans(const float* X, int64_t n64, int d, int ld, int k, int reps, int max_iter, uint64_t seed,
-                      int32_t* labels_out, double* inertia_out, Graph* owner, cudaStream_t s) {
-    const int n = (int)n64;
+csc_status run_kmeans_multi(const std::vector<KmTask>& tasks, int d, int ld, int reps, int max_iter,
+                            double* inertia_out, Graph* owner, cudaStream_t s) {
+    const int NP = (int)tasks.size();
+    if (NP == 0) return CSC_OK;
     int dev = 0, sms = 148;
     CSC_CUDA_TRY(cudaGetDevice(&dev));
     CSC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // cluster size: spread the replicates over the SMs, at most 8 CTAs (the portable
-    // cluster size), and slices of at least 16 points
-    int C = sms / reps;
+    int n_max = 0, n_min = 1 << 30, k_max = 0;
+    int64_t lab_total = 0;
+    for (const KmTask& t : tasks) {
+        n_max = std::max(n_max, t.n);
+        n_min = std::min(n_min, t.n);
+        k_max = std::max(k_max, t.k);
+        lab_total += (int64_t)reps * t.n;
+    }
+    // cluster size: spread the replicates of all problems over the SMs, at most 8 CTAs
+    // (the portable cluster size), and slices of at least 16 points
+    int C = sms / (reps * NP);
     C = C < 1 ? 1 : (C > 8 ? 8 : C);
-    while (C > 1 && (n + C - 1) / C < 16) --C;
+    while (C > 1 && (n_min + C - 1) / C < 16) --C;
     size_t smem = 0;
     for (;; --C) {
-        const KmLayout L(k, d, (k + C - 1) / C, (n + C - 1) / C);
+        const KmLayout L(k_max, d, (k_max + C - 1) / C, (n_max + C - 1) / C);
         smem = L.total;
         if (smem <= 200 * 1024 || C == 1) break;
     }
     if (smem > 200 * 1024) {
-        set_error("k-means: k*d = %d with n = %d needs %zu bytes of shared memory per CTA", k * d, n, smem);
+        set_error("k-means: k*d = %d with n = %d needs %zu bytes of shared memory per CTA", k_max * d, n_max, smem);
         return CSC_E_UNSUPPORTED;
     }
     size_t off = 0;
@@ -408,7 +443,9 @@ csc_status run_kmeans(const float* X, int64_t n64, int d, int ld, int k, int rep
         off += (bytes + 255) / 256 * 256;
         return o;
     };
-    const size_t o_lab = take((size_t)reps * n * 4), o_in = take((size_t)reps * 8 + 8);
+    const size_t o_lab = take((size_t)lab_total * 4), o_in = take((size_t)reps * NP * 8),
+                 o_best = take((size_t)NP * 8), o_prob = take((size_t)NP * sizeof(KmProblem)),
+                 o_out = take((size_t)NP * sizeof(int32_t*));
     void* base = nullptr;
     bool async_alloc = false;
     if (owner) {
@@ -423,11 +460,27 @@ csc_status run_kmeans(const float* X, int64_t n64, int d, int ld, int k, int rep
         async_alloc = true;
     }
     char* b = (char*)base;
+    std::vector<KmProblem> probs(NP);
+    std::vector<int32_t*> outs(NP);
+    int64_t lab_off = 0;
+    for (int p = 0; p < NP; ++p) {
+        probs[p].X = tasks[p].X;
+        probs[p].n = tasks[p].n;
+        probs[p].k = tasks[p].k;
+        probs[p].seed = tasks[p].seed;
+        probs[p].labels_all = (int32_t*)(b + o_lab) + lab_off;
+        probs[p].inertia_all = (double*)(b + o_in) + (size_t)p * reps;
+        lab_off += (int64_t)reps * tasks[p].n;
+        outs[p] = tasks[p].labels_out;
+    }
+    KmProblem* d_probs = (KmProblem*)(b + o_prob);
+    int32_t** d_outs = (int32_t**)(b + o_out);
+    double* d_best = (double*)(b + o_best);
+    CSC_CUDA_TRY(cudaMemcpyAsync(d_probs, probs.data(), NP * sizeof(KmProblem), cudaMemcpyHostToDevice, s));
+    CSC_CUDA_TRY(cudaMemcpyAsync(d_outs, outs.data(), NP * sizeof(int32_t*), cudaMemcpyHostToDevice, s));
     CSC_CUDA_TRY(cudaFuncSetAttribute(kmeans_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    double* inertia_all = (double*)(b + o_in);
-    int32_t* labels_all = (int32_t*)(b + o_lab);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(reps * C, 1, 1);
+    cfg.gridDim = dim3(reps * C, NP, 1);
     cfg.blockDim = dim3(kKmThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
@@ -438,18 +491,34 @@ csc_status run_kmeans(const float* X, int64_t n64, int d, int ld, int k, int rep
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    CSC_KLAUNCH("kmeans", 4.0 * n * d * reps, s,
-                CSC_CUDA_TRY(cudaLaunchKernelEx(&cfg, kmeans_cluster_kernel, X, n, d, ld, k, max_iter, seed,
-                                                labels_all, inertia_all)));
-    double* dev_inertia = inertia_all + reps;
-    CSC_KLAUNCH("kmeans_pick", 8.0 * n, s,
-                kmeans_pick_kernel<<<1, 256, 0, s>>>(labels_all, inertia_all, reps, n, labels_out, dev_inertia));
+    double pts = 0.0;
+    for (const KmTask& t : tasks) pts += (double)t.n;
+    CSC_KLAUNCH("kmeans", 4.0 * pts * d * reps, s,
+                CSC_CUDA_TRY(cudaLaunchKernelEx(&cfg, kmeans_cluster_kernel, (const KmProblem*)d_probs, d, ld,
+                                                max_iter)));
+    CSC_KLAUNCH("kmeans_pick", 8.0 * pts, s,
+                kmeans_pick_kernel<<<dim3(1, NP), 256, 0, s>>>(d_probs, reps, d_outs, d_best));
+    std::vector<double> hb;
     if (inertia_out) {
-        CSC_CUDA_TRY(cudaMemcpyAsync(inertia_out, dev_inertia, sizeof(double), cudaMemcpyDeviceToHost, s));
-        CSC_CUDA_TRY(cudaStreamSynchronize(s));
+        hb.resize(NP);
+        CSC_CUDA_TRY(cudaMemcpyAsync(hb.data(), d_best, NP * sizeof(double), cudaMemcpyDeviceToHost, s));
     }
+    // the host descriptor arrays die with this frame
+    CSC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (inertia_out) memcpy(inertia_out, hb.data(), NP * sizeof(double));
     if (async_alloc) CSC_CUDA_TRY(cudaFreeAsync(base, s));
     return CSC_OK;
+}
+
+csc_status run_kmeans(const float* X, int64_t n64, int d, int ld, int k, int reps, int max_iter, uint64_t seed,
+                      int32_t* labels_out, double* inertia_out, Graph* owner, cudaStream_t s) {
+    std::vector<KmTask> t(1);
+    t[0].X = X;
+    t[0].n = (int)n64;
+    t[0].k = k;
+    t[0].seed = seed;
+    t[0].labels_out = labels_out;
+    return run_kmeans_multi(t, d, ld, reps, max_iter, inertia_out, owner, s);
 }
 
 }  // namespace csc

@@ -170,6 +170,16 @@ __global__ void copy_in_kernel(T* __restrict__ X, const float* __restrict__ R, i
 // kHeavyRow edges are skipped here and done by the *_heavy kernels.
 
 // The per-row update of one order given the row's neighbour sum acc (column tile col0).
+// Per-graph filter coefficients of a batched handle: c[gid[row] * stride + j] is
+// c_j of the row's graph (c == nullptr: the scalar coefficients apply).
+template <typename A>
+struct CoefTab {
+    const A* c = nullptr;
+    const int32_t* gid = nullptr;
+    int stride = 0;
+    int j = 0;  // index of c_next; c_0 at 0
+};
+
 template <typename T, int G, int NT>
 __device__ __forceinline__ void cheb_epilogue(int row, int lane, int col0, int tcols,
                                               typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC],
@@ -226,15 +236,21 @@ cheb_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                  const typename StoreTraits<T>::acc_t* __restrict__ sqdeg, const T* __restrict__ zcur,
                  T* __restrict__ zprev_next, typename StoreTraits<T>::acc_t* __restrict__ Y,
                  const int32_t* __restrict__ perm, const int32_t* __restrict__ part, int ncols, int64_t ld,
-                 typename StoreTraits<T>::acc_t c0, typename StoreTraits<T>::acc_t c_next, int mode) {
+                 typename StoreTraits<T>::acc_t c0, typename StoreTraits<T>::acc_t c_next, int mode,
+                 CoefTab<typename StoreTraits<T>::acc_t> tab) {
     using A = typename StoreTraits<T>::acc_t;
     constexpr int VEC = StoreTraits<T>::VEC;
     constexpr int TW = G * NT * VEC;
     const int lane = threadIdx.x % G;
     const int col0 = blockIdx.y * TW;
     const int tcols = min(TW, ncols - col0);
-    const int r1 = part[blockIdx.x + 1];
-    for (int row = part[blockIdx.x] + (int)(threadIdx.x / G); row < r1; row += (int)(blockDim.x / G)) {
+    const int r0 = part[blockIdx.x], r1 = part[blockIdx.x + 1];
+    if (tab.c && r0 < r1) {  // a batch's row range lies inside one graph
+        const A* cg = tab.c + (int64_t)tab.gid[r0] * tab.stride;
+        c0 = cg[0];
+        c_next = cg[tab.j];
+    }
+    for (int row = r0 + (int)(threadIdx.x / G); row < r1; row += (int)(blockDim.x / G)) {
         const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
         if (e1 - e0 > kHeavyRow) continue;
         A acc[NT][VEC];
@@ -252,7 +268,8 @@ cheb_step_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict
                        const typename StoreTraits<T>::acc_t* __restrict__ sqdeg, const T* __restrict__ zcur,
                        T* __restrict__ zprev_next, typename StoreTraits<T>::acc_t* __restrict__ Y,
                        const int32_t* __restrict__ perm, const int32_t* __restrict__ heavy, int ncols, int64_t ld,
-                       typename StoreTraits<T>::acc_t c0, typename StoreTraits<T>::acc_t c_next, int mode) {
+                       typename StoreTraits<T>::acc_t c0, typename StoreTraits<T>::acc_t c_next, int mode,
+                       CoefTab<typename StoreTraits<T>::acc_t> tab) {
     using A = typename StoreTraits<T>::acc_t;
     constexpr int VEC = StoreTraits<T>::VEC;
     constexpr int TW = G * NT * VEC;
@@ -260,6 +277,11 @@ cheb_step_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict
     const int col0 = blockIdx.y * TW;
     const int tcols = min(TW, ncols - col0);
     const int row = heavy[blockIdx.x];
+    if (tab.c) {
+        const A* cg = tab.c + (int64_t)tab.gid[row] * tab.stride;
+        c0 = cg[0];
+        c_next = cg[tab.j];
+    }
     A acc[NT][VEC];
     gather_heavy<T, G, NT, false, A>(__ldg(rp + row), __ldg(rp + row + 1), ci, nullptr, zcur + col0, ld, lane, tcols,
                                      acc);
@@ -485,6 +507,38 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partials, int 
     }
 }
 
+// Per-graph sums of the block partials of one step, in a fixed order: block g adds,
+// for each column tile, the slots of its graph's row ranges [gblk[g], gblk[g+1]) and
+// then those of its heavy rows [ghvy[g], ghvy[g+1]) (slot layout of mom_step_kernel /
+// mom_step_heavy_kernel).  nseg = 1 sums everything (gblk, ghvy unused).
+// out[(g * J + j) * 3 + q].
+__global__ void __launch_bounds__(256) segment_partials_kernel(const double* __restrict__ partials, int P, int tiles,
+                                                               int H, const int32_t* __restrict__ gblk,
+                                                               const int32_t* __restrict__ ghvy, int nseg, int j,
+                                                               int J, double* __restrict__ out) {
+    __shared__ double red[3][8];
+    const int gi = blockIdx.x;
+    const int b0 = nseg == 1 ? 0 : gblk[gi], b1 = nseg == 1 ? P : gblk[gi + 1];
+    const int h0 = nseg == 1 ? 0 : ghvy[gi], h1 = nseg == 1 ? H : ghvy[gi + 1];
+    const int nb = b1 - b0, nh = h1 - h0;
+    const int per_tile = nb + nh;
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int t = threadIdx.x; t < per_tile * tiles; t += blockDim.x) {
+        const int y = t / per_tile, i = t % per_tile;
+        const int64_t slot = i < nb ? (int64_t)y * P + b0 + i : (int64_t)P * tiles + (int64_t)y * H + h0 + (i - nb);
+        for (int q = 0; q < 3; ++q) a[q] += partials[slot * 3 + q];
+    }
+    for (int q = 0; q < 3; ++q) a[q] = warp_sum(a[q]);
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < 3; ++q) red[q][threadIdx.x >> 5] = a[q];
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+        out[((int64_t)gi * J + j) * 3 + threadIdx.x] = t;
+    }
+}
+
 // ------------------------------------------------------------- dispatch
 // (G, NT) pairs compiled for the SpMM kernels.
 struct TileShape {
@@ -520,7 +574,8 @@ enum KernelKind { KK_CHEB = 1, KK_MOM = 2 };
 template <typename T>
 static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur, T* xpn,
                                    typename StoreTraits<T>::acc_t* Y, int ncols, int64_t ld,
-                                   double c0, double cn, int mode, cudaStream_t s) {
+                                   double c0, double cn, int mode, cudaStream_t s,
+                                   CoefTab<typename StoreTraits<T>::acc_t> tab = {}) {
     using A = typename StoreTraits<T>::acc_t;
     const A *idg, *sqd;
     if constexpr (sizeof(A) == 8) {
@@ -548,9 +603,13 @@ static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur
         CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * heavy_frac, s,
                                           cheb_step_heavy_kernel<T, GG, NN><<<hgrid, kHeavyThreads, 0, s>>>(
                                               g->row_ptr, g->col_idx, idg, sqd, xcur, xpn, Y, g->perm, g->heavy,
-                                              ncols, ld, (A)c0, (A)cn, mode)));
+                                              ncols, ld, (A)c0, (A)cn, mode, tab)));
     }
     if (cfg.win > 0) {
+        if (tab.c) {
+            set_error("per-graph coefficients need a launch shape without a neighbour window");
+            return CSC_E_UNSUPPORTED;
+        }
         const int32_t* win = nullptr;
         CSC_TRY(get_windows(g, cfg.P, cfg.win, &win));
         const size_t smem = 128 + (size_t)cfg.win * ld * sizeof(T);
@@ -567,7 +626,7 @@ static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur
     CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", bytes, s,
                                       cheb_step_kernel<T, GG, NN><<<grid, cfg.threads, 0, s>>>(
                                           g->row_ptr, g->col_idx, idg, sqd, xcur, xpn, Y, g->perm, part, ncols, ld,
-                                          (A)c0, (A)cn, mode)));
+                                          (A)c0, (A)cn, mode, tab)));
     return CSC_OK;
 }
 
@@ -662,6 +721,7 @@ static std::vector<LaunchCfg> candidates(Graph* g, int kind, int nv) {
             for (int waves = 1; waves <= 8; waves *= 2) {
                 int P = (g->num_sms * occ * waves + tiles - 1) / tiles;
                 if (P > max_p) P = (int)max_p;
+                if (P < g->n_graphs) P = g->n_graphs;  // a batch needs a range per graph
                 c.P = P < 1 ? 1 : P;
                 if (!out.empty() && out.back().G == c.G && out.back().NT == c.NT && out.back().threads == th &&
                     out.back().P == c.P)
@@ -669,7 +729,7 @@ static std::vector<LaunchCfg> candidates(Graph* g, int kind, int nv) {
                 out.push_back(c);
             }
             // shared-memory neighbour windows (single column tile): up to ~64 / 100 / 200 KB
-            if (kind == KK_CHEB && tiles == 1) {
+            if (kind == KK_CHEB && tiles == 1 && g->n_graphs <= 1) {
                 const size_t row_bytes = (size_t)nv * 16;
                 for (size_t budget : {64 * 1024, 100 * 1024, 200 * 1024}) {
                     int64_t W = (int64_t)((budget - 128) / row_bytes);
@@ -772,7 +832,8 @@ static csc_status fill_block(Graph* g, T* X, int d, int ld, uint64_t seed, uint3
 template <typename T>
 static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pad, uint64_t seed,
                                const float* R_in, void* Y_out, bool normalize, cudaStream_t s,
-                               uint32_t rng_stream = STREAM_SIGNALS, float sigma_override = 0.f) {
+                               uint32_t rng_stream = STREAM_SIGNALS, float sigma_override = 0.f,
+                               const double* c_graphs = nullptr) {
     using A = typename StoreTraits<T>::acc_t;
     constexpr int VEC = StoreTraits<T>::VEC;
     const int64_t N = g->N;
@@ -784,6 +845,25 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
     A* Y = (A*)Y_out;
     const float sigma = sigma_override > 0.f ? sigma_override : d > 0 ? (float)(1.0 / sqrt((double)d)) : 1.0f;
     CSC_TRY(fill_block<T>(g, X[0], d, d_pad, seed, rng_stream, sigma, R_in, d_pad, s));
+    CoefTab<A> tab;
+    if (c_graphs) {
+        // per-graph coefficients, G x (m + 1), in the accumulator type
+        const int G = g->n_graphs;
+        if (m == 0 || !g->graph_of_row) {
+            set_error("per-graph filter coefficients need m >= 1 and a batched handle");
+            return CSC_E_UNSUPPORTED;
+        }
+        std::vector<A> h((size_t)G * (m + 1));
+        for (size_t i = 0; i < h.size(); ++i) h[i] = (A)c_graphs[i];
+        void* dc = nullptr;
+        CSC_TRY(ws_get(g, WS_COEF, h.size() * sizeof(A), &dc));
+        CSC_CUDA_TRY(cudaMemcpyAsync(dc, h.data(), h.size() * sizeof(A), cudaMemcpyHostToDevice, s));
+        // the host copy dies with this frame: wait for the copy
+        CSC_CUDA_TRY(cudaStreamSynchronize(s));
+        tab.c = (const A*)dc;
+        tab.gid = g->graph_of_row;
+        tab.stride = m + 1;
+    }
     if (m == 0) {
         const int64_t tot = N * d_pad;
         const A* sqd;
@@ -800,11 +880,14 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
                              return launch_cheb_step<T>(g, c, X[0], X[1], Y, d_pad, d_pad, 0.0, 0.0, 0, s);
                          },
                          &cfg));
-        CSC_TRY(launch_cheb_step<T>(g, cfg, X[0], X[1], Y, d_pad, d_pad, c[0], c[1], 1 | (m == 1 ? 2 : 0), s));
+        tab.j = 1;
+        CSC_TRY(launch_cheb_step<T>(g, cfg, X[0], X[1], Y, d_pad, d_pad, c ? c[0] : 0.0, c ? c[1] : 0.0,
+                                    1 | (m == 1 ? 2 : 0), s, tab));
         for (int j = 1; j < m; ++j) {
             // Z_j lives in X[j & 1]; Z_{j-1} (overwritten by Z_{j+1}) in the other buffer
-            CSC_TRY(launch_cheb_step<T>(g, cfg, X[j & 1], X[(j + 1) & 1], Y, d_pad, d_pad, 0.0, c[j + 1],
-                                        j == m - 1 ? 2 : 0, s));
+            tab.j = j + 1;
+            CSC_TRY(launch_cheb_step<T>(g, cfg, X[j & 1], X[(j + 1) & 1], Y, d_pad, d_pad, 0.0, c ? c[j + 1] : 0.0,
+                                        j == m - 1 ? 2 : 0, s, tab));
         }
     }
     if (normalize) {
@@ -814,6 +897,24 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
                     normalize_kernel<A><<<grid, 256, 0, s>>>(Y, (int32_t)N, d, d_pad));
     }
     return CSC_OK;
+}
+
+csc_status run_filter_batched(Graph* g, const double* c_graphs, int m, int d, int d_pad, uint64_t seed,
+                              csc_dtype storage, const float* R_in, void* Y_out, bool normalize, cudaStream_t s) {
+    switch (storage) {
+        case CSC_F32:
+            return filter_typed<float>(g, nullptr, m, d, d_pad, seed, R_in, Y_out, normalize, s, STREAM_SIGNALS, 0.f,
+                                       c_graphs);
+        case CSC_BF16:
+            return filter_typed<__nv_bfloat16>(g, nullptr, m, d, d_pad, seed, R_in, Y_out, normalize, s,
+                                               STREAM_SIGNALS, 0.f, c_graphs);
+        case CSC_F64:
+            return filter_typed<double>(g, nullptr, m, d, d_pad, seed, R_in, Y_out, normalize, s, STREAM_SIGNALS,
+                                        0.f, c_graphs);
+        default:
+            set_error("unknown storage type %d", (int)storage);
+            return CSC_E_INVALID;
+    }
 }
 
 csc_status run_filter(Graph* g, const double* coeffs, int m, int d, int d_pad, uint64_t seed,
@@ -861,7 +962,7 @@ csc_status run_refilter_count(Graph* g, double lambda, int m, int n_probes, uint
 
 template <typename T>
 static csc_status moments_typed(Graph* g, int n_moments, int n_probes, uint64_t seed, double* mu,
-                                int* passes, cudaStream_t s) {
+                                int* passes, cudaStream_t s, bool per_graph) {
     constexpr int VEC = StoreTraits<T>::VEC;
     const int64_t N = g->N;
     const int ld = ((n_probes + 7) / 8) * 8;
@@ -884,8 +985,9 @@ static csc_status moments_typed(Graph* g, int n_moments, int n_probes, uint64_t 
         else if (tune_cache_get(g, key, &known))
             max_blocks = std::max(max_blocks, (known.P + g->n_heavy) * known.tiles);
     }
+    const int nseg = per_graph ? std::max(1, (int)g->n_graphs) : 1;
     CSC_TRY(ws_get(g, WS_PARTIAL, (size_t)max_blocks * 3 * sizeof(double), &part));
-    CSC_TRY(ws_get(g, WS_MOMENTS, (size_t)J * 3 * sizeof(double), &sums));
+    CSC_TRY(ws_get(g, WS_MOMENTS, (size_t)nseg * J * 3 * sizeof(double), &sums));
     double* P = (double*)part;
     double* S = (double*)sums;
     CSC_TRY(fill_block<T>(g, X[0], n_probes, ld, seed, STREAM_PROBES, 1.0f, nullptr, ld, s));
@@ -894,41 +996,50 @@ static csc_status moments_typed(Graph* g, int n_moments, int n_probes, uint64_t 
                      [&](const LaunchCfg& c) { return launch_mom_step<T>(g, c, X[0], X[1], ld, ld, 0, P, s); },
                      &cfg));
     const int grid = (cfg.P + g->n_heavy) * cfg.tiles;  // block partial slots per step
+    const int32_t *gblk = nullptr, *ghvy = nullptr;
+    if (nseg > 1) CSC_TRY(get_segments(g, cfg.P, &gblk, &ghvy));
     for (int j = 0; j < J; ++j) {
         CSC_TRY(launch_mom_step<T>(g, cfg, X[j & 1], X[(j + 1) & 1], ld, ld, j == 0 ? 1 : 0, P, s));
-        CSC_KLAUNCH("reduce", 24.0 * grid, s, reduce_partials_kernel<<<1, 256, 0, s>>>(P, grid, S + 3 * j));
+        CSC_KLAUNCH("reduce", 24.0 * grid, s,
+                    segment_partials_kernel<<<nseg, 256, 0, s>>>(P, cfg.P, cfg.tiles, g->n_heavy, gblk, ghvy, nseg, j,
+                                                                J, S));
     }
+    const size_t nsum = (size_t)nseg * J * 3;
+    std::vector<double> hbuf;
     double* host = g->pinned;
-    const size_t nsum = (size_t)J * 3;
     if (nsum > 4096) {
-        set_error("too many moments requested (%d)", n_moments);
-        return CSC_E_UNSUPPORTED;
+        hbuf.resize(nsum);
+        host = hbuf.data();
     }
     CSC_CUDA_TRY(cudaMemcpyAsync(host, S, nsum * sizeof(double), cudaMemcpyDeviceToHost, s));
     CSC_CUDA_TRY(cudaStreamSynchronize(s));
     const double nv = (double)n_probes;
-    // step 0: s0 = <X0,X0>, s1 = <X1,X0>, s2 = <X1,X1>
-    const double mu0 = host[0] / nv;
-    const double mu1 = host[1] / nv;
-    mu[0] = mu0;
-    if (n_moments > 1) mu[1] = mu1;
-    if (n_moments > 2) mu[2] = 2.0 * host[2] / nv - mu0;
-    for (int j = 1; j < J; ++j) {
-        const int odd = 2 * j + 1, even = 2 * j + 2;
-        if (odd < n_moments) mu[odd] = 2.0 * host[3 * j + 1] / nv - mu1;
-        if (even < n_moments) mu[even] = 2.0 * host[3 * j + 2] / nv - mu0;
+    for (int gi = 0; gi < nseg; ++gi) {
+        const double* h = host + (size_t)gi * J * 3;
+        double* m = mu + (size_t)gi * n_moments;
+        // step 0: s0 = <X0,X0>, s1 = <X1,X0>, s2 = <X1,X1>
+        const double mu0 = h[0] / nv;
+        const double mu1 = h[1] / nv;
+        m[0] = mu0;
+        if (n_moments > 1) m[1] = mu1;
+        if (n_moments > 2) m[2] = 2.0 * h[2] / nv - mu0;
+        for (int j = 1; j < J; ++j) {
+            const int odd = 2 * j + 1, even = 2 * j + 2;
+            if (odd < n_moments) m[odd] = 2.0 * h[3 * j + 1] / nv - mu1;
+            if (even < n_moments) m[even] = 2.0 * h[3 * j + 2] / nv - mu0;
+        }
     }
     if (passes) *passes = J;
     return CSC_OK;
 }
 
 csc_status run_moments(Graph* g, int n_moments, int n_probes, uint64_t seed, csc_dtype storage,
-                       double* mu_host, int* passes, cudaStream_t s) {
+                       double* mu_host, int* passes, cudaStream_t s, bool per_graph) {
     switch (storage) {
         case CSC_F32:
-            return moments_typed<float>(g, n_moments, n_probes, seed, mu_host, passes, s);
+            return moments_typed<float>(g, n_moments, n_probes, seed, mu_host, passes, s, per_graph);
         case CSC_BF16:
-            return moments_typed<__nv_bfloat16>(g, n_moments, n_probes, seed, mu_host, passes, s);
+            return moments_typed<__nv_bfloat16>(g, n_moments, n_probes, seed, mu_host, passes, s, per_graph);
         default:
             set_error("moments support CSC_F32 and CSC_BF16 storage");
             return CSC_E_UNSUPPORTED;
