@@ -280,8 +280,8 @@ def run_ours(args, w, rank, world, local_rank):
         dist.barrier()
     sampler = ClockSampler(local_rank)
     sampler.start()
+    # timed region: no per-launch events (the filter replays its captured CUDA graph)
     csc.csc_profile_reset()
-    csc.csc_profile_enable(True)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     infos = []
     torch.cuda.synchronize()
@@ -294,9 +294,18 @@ def run_ours(args, w, rank, world, local_rank):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    csc.csc_profile_enable(False)
     clocks = sampler.stop()
     launches = csc.csc_profile_launches()
+    # per-kernel CUDA-event durations for the roofline: a second pass of the same steps with
+    # every launch bracketed by events on its stream (eager launches, so each kernel is seen)
+    prof_steps = max(3, args.steps // 2)
+    csc.csc_profile_reset()
+    csc.csc_profile_enable(True)
+    for i in range(prof_steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    csc.csc_profile_enable(False)
     classes = csc.csc_profile_query()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     filt_ms = [x.ms["filter"] for x in infos]
@@ -387,6 +396,7 @@ def run_ours(args, w, rank, world, local_rank):
             "kernel_classes": {kk: {"launches": v["launches"], "ms": round(v["ms"], 4)} for kk, v in classes.items()},
             "autotuned_shapes": csc.csc_graph_tuned_shapes(h),
             "gpu_launches": launches,
+            "roofline_pass": f"{prof_steps} extra steps with per-launch CUDA events (eager launches)",
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,

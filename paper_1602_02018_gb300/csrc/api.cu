@@ -505,6 +505,8 @@ static void free_graph(Graph* g) {
     cudaFree(g->d_offsets);
     cudaFree(g->graph_of_row);
     for (auto& b : g->ws) cudaFree(b.ptr);
+    for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second.first);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     for (auto& kv : g->parts) cudaFree(kv.second);
     for (auto& kv : g->part_gblk) cudaFree(kv.second);
     cudaFree(g->d_hvy_start);
@@ -541,6 +543,11 @@ static csc_status upload(Graph* g, const HostCSR& h, const std::vector<int32_t>*
     g->nnz = nnz;
     CSC_CUDA_TRY(cudaGetDevice(&g->device));
     CSC_CUDA_TRY(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
+    {
+        int l2 = 0;
+        CSC_CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, g->device));
+        g->l2_bytes = l2;
+    }
     std::vector<int32_t>& rp32 = g->h_row_ptr;
     rp32.resize(N + 1);
     for (int64_t i = 0; i <= N; ++i) rp32[i] = (int32_t)h.rp[i];

@@ -55,6 +55,7 @@ extern bool g_prof_enabled;
 int prof_begin(const char* name, double bytes, cudaStream_t s);
 void prof_end(int slot, cudaStream_t s);
 void count_launch();
+void count_launches(int64_t n);
 
 #define CSC_KLAUNCH(NAME, BYTES, STREAM, ...)                                                \
     do {                                                                                    \
@@ -87,6 +88,7 @@ enum WsSlot {
     WS_MLP,         // predictor input / output of the learned bracket
     WS_REFILTER,    // filtered probes and partials of the paper-literal eigencount
     WS_COEF,        // per-graph filter coefficients of a batch
+    WS_COEF1,       // filter coefficients read by a captured CUDA graph
     WS_COUNT
 };
 
@@ -109,6 +111,7 @@ struct Graph {
     int32_t n_graphs = 1;
     int device = 0;
     int num_sms = 148;
+    int64_t l2_bytes = 0;
     int32_t* row_ptr = nullptr;  // device int32[N+1], internal node order
     int32_t* col_idx = nullptr;  // device int32[nnz]
     float* dinv = nullptr;       // device float[N]: D^-1/2 (0 for isolated nodes)
@@ -136,6 +139,10 @@ struct Graph {
     std::map<int, std::vector<int32_t>> h_parts;  // host copies of the bounds
     std::map<int, int32_t*> part_gblk;            // P -> device int32[G+1]: first range of each graph
     int32_t* d_hvy_start = nullptr;               // device int32[G+1]: first heavy row of each graph
+    // captured CUDA graphs of fixed launch sequences (key -> executable, kernel launches)
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;
+    std::map<std::string, std::pair<cudaGraphExec_t, int64_t>> graphs;
     std::map<std::pair<int, int>, int32_t*> wins; // (P, W) -> device int32[P] window starts
     int* dev_err = nullptr;                       // device error word (bounded waits that gave up)
     std::map<uint64_t, LaunchCfg> tuned;          // (kernel kind, dtype, columns) -> shape
@@ -150,6 +157,49 @@ csc_status ws_get(Graph* g, WsSlot slot, size_t bytes, void** out);
 // device, N and nnz (graphs of the same size reuse a shape without re-tuning).
 bool tune_cache_get(const Graph* g, uint64_t key, LaunchCfg* out);
 void tune_cache_put(const Graph* g, uint64_t key, const LaunchCfg& cfg);
+
+// Launch the sequence `record(stream)` issues, as a CUDA graph captured once per
+// key on the handle's capture stream and replayed on s.  The recorded launches
+// must not depend on anything but the key.  *launches: kernel launches per replay.
+int64_t launch_count();
+template <typename Rec>
+csc_status replay_graph(Graph* g, const std::string& key, cudaStream_t s, int64_t* launches, Rec&& record) {
+    auto it = g->graphs.find(key);
+    if (it == g->graphs.end()) {
+        if (!g->cap_stream) CSC_CUDA_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+        if (g->graphs.size() >= 32) {  // bound the cache
+            for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second.first);
+            g->graphs.clear();
+        }
+        const int64_t before = launch_count();
+        // relaxed: one-time host set-up inside `record` (a partition upload) runs eagerly
+        CSC_CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed));
+        const csc_status st = record(g->cap_stream);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+        const int64_t n = launch_count() - before;
+        count_launches(-n);  // captured, not run
+        if (st != CSC_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            if (st == CSC_OK) set_error("CUDA graph capture: %s", cudaGetErrorString(e));
+            return st != CSC_OK ? st : CSC_E_CUDA;
+        }
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            cudaGetLastError();
+            set_error("CUDA graph instantiation: %s", cudaGetErrorString(ei));
+            return CSC_E_CUDA;
+        }
+        it = g->graphs.emplace(key, std::make_pair(exec, n)).first;
+    }
+    CSC_CUDA_TRY(cudaGraphLaunch(it->second.first, s));
+    count_launches(it->second.second);
+    *launches = it->second.second;
+    return CSC_OK;
+}
 
 // P contiguous row ranges of about equal cost (edges + 2 per row); cached per P.
 csc_status get_partition(Graph* g, int P, const int32_t** out);

@@ -132,6 +132,15 @@ struct AccIO {
             for (int i = 0; i < PER; ++i) v[q * PER + i] = t[i];
         }
     }
+    __device__ static inline void load(const A* p, A (&v)[VEC]) {
+#pragma unroll
+        for (int q = 0; q < VEC / PER; ++q) {
+            A t[PER];
+            StoreTraits<A>::load(p + q * PER, t);
+#pragma unroll
+            for (int i = 0; i < PER; ++i) v[q * PER + i] = t[i];
+        }
+    }
     __device__ static inline void store(A* p, const A (&v)[VEC]) {
 #pragma unroll
         for (int q = 0; q < VEC / PER; ++q) {

@@ -71,6 +71,8 @@ void resolve_locked() {
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 int prof_begin(const char* name, double bytes, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_mu);

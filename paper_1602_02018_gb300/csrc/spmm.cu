@@ -170,8 +170,9 @@ __global__ void copy_in_kernel(T* __restrict__ X, const float* __restrict__ R, i
 // kHeavyRow edges are skipped here and done by the *_heavy kernels.
 
 // The per-row update of one order given the row's neighbour sum acc (column tile col0).
-// Per-graph filter coefficients of a batched handle: c[gid[row] * stride + j] is
-// c_j of the row's graph (c == nullptr: the scalar coefficients apply).
+// Filter coefficients read from device memory: c[gid[row] * stride + j] is c_j of
+// the row's graph in a batch; with gid == nullptr, c[j] for every row (the form
+// replayed by a captured CUDA graph); c == nullptr: the scalar coefficients apply.
 template <typename A>
 struct CoefTab {
     const A* c = nullptr;
@@ -194,6 +195,7 @@ __device__ __forceinline__ void cheb_epilogue(int row, int lane, int col0, int t
     using A = typename Tr::acc_t;
     constexpr int VEC = Tr::VEC;
     const bool first = (mode & 1) != 0, last = (mode & 2) != 0;
+    const bool keep = (mode & 4) != 0;  // working set fits L2: no evict-first hints
     const A f = (first ? A(-1) : A(-2)) * invdeg[row];
     const A back = last ? sqdeg[row] : A(1);
     const int64_t yrow = perm ? (int64_t)perm[row] : (int64_t)row;
@@ -216,16 +218,20 @@ __device__ __forceinline__ void cheb_epilogue(int row, int lane, int col0, int t
             for (int v = 0; v < VEC; ++v) y[v] = (c0 * z0[v] + c_next * zn[v]) * back;
         } else {
             A zp[VEC];
-            Tr::load_cs(zp_ptr, zp);
+            if (keep) Tr::load(zp_ptr, zp);
+            else Tr::load_cs(zp_ptr, zp);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v] - zp[v]);
             Tr::store(zp_ptr, zn);
-            AccIO<A, VEC>::load_cs(y_ptr, y);
+            if (keep) AccIO<A, VEC>::load(y_ptr, y);
+            else AccIO<A, VEC>::load_cs(y_ptr, y);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) y[v] = fma(c_next, zn[v], y[v]) * back;
         }
         // Y is read again only by the next order: evict-first keeps Z_j resident in L2
-        AccIO<A, VEC>::store_cs(y_ptr, y);
+        // (unless everything fits there)
+        if (keep) AccIO<A, VEC>::store(y_ptr, y);
+        else AccIO<A, VEC>::store_cs(y_ptr, y);
     }
 }
 
@@ -246,7 +252,7 @@ cheb_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
     const int tcols = min(TW, ncols - col0);
     const int r0 = part[blockIdx.x], r1 = part[blockIdx.x + 1];
     if (tab.c && r0 < r1) {  // a batch's row range lies inside one graph
-        const A* cg = tab.c + (int64_t)tab.gid[r0] * tab.stride;
+        const A* cg = tab.gid ? tab.c + (int64_t)tab.gid[r0] * tab.stride : tab.c;
         c0 = cg[0];
         c_next = cg[tab.j];
     }
@@ -278,7 +284,7 @@ cheb_step_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict
     const int tcols = min(TW, ncols - col0);
     const int row = heavy[blockIdx.x];
     if (tab.c) {
-        const A* cg = tab.c + (int64_t)tab.gid[row] * tab.stride;
+        const A* cg = tab.gid ? tab.c + (int64_t)tab.gid[row] * tab.stride : tab.c;
         c0 = cg[0];
         c_next = cg[tab.j];
     }
@@ -540,6 +546,9 @@ __global__ void __launch_bounds__(256) segment_partials_kernel(const double* __r
 }
 
 // ------------------------------------------------------------- dispatch
+// Working sets up to this share of L2 are loaded and stored without evict-first hints.
+static const double kKeepL2Fraction = 0.75;
+
 // (G, NT) pairs compiled for the SpMM kernels.
 struct TileShape {
     int G, NT;
@@ -586,6 +595,9 @@ static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur
         sqd = g->sqdeg;
     }
     const int first = mode & 1;
+    // Z_j, Z_{j-1}, Y and the CSR within three quarters of L2: plain caching
+    const double ws = (double)g->N * ld * (2.0 * sizeof(T) + sizeof(A)) + 4.0 * g->nnz + 8.0 * g->N;
+    if (ws <= kKeepL2Fraction * (double)g->l2_bytes) mode |= 4;
     const int32_t* part = nullptr;
     CSC_TRY(get_partition(g, cfg.P, &part));
     const dim3 grid(cfg.P, cfg.tiles);
@@ -880,14 +892,39 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
                              return launch_cheb_step<T>(g, c, X[0], X[1], Y, d_pad, d_pad, 0.0, 0.0, 0, s);
                          },
                          &cfg));
-        tab.j = 1;
-        CSC_TRY(launch_cheb_step<T>(g, cfg, X[0], X[1], Y, d_pad, d_pad, c ? c[0] : 0.0, c ? c[1] : 0.0,
-                                    1 | (m == 1 ? 2 : 0), s, tab));
-        for (int j = 1; j < m; ++j) {
-            // Z_j lives in X[j & 1]; Z_{j-1} (overwritten by Z_{j+1}) in the other buffer
-            tab.j = j + 1;
-            CSC_TRY(launch_cheb_step<T>(g, cfg, X[j & 1], X[(j + 1) & 1], Y, d_pad, d_pad, 0.0, c ? c[j + 1] : 0.0,
-                                        j == m - 1 ? 2 : 0, s, tab));
+        // the m orders; replayed from a captured CUDA graph when no per-launch timing is
+        // asked for (one launch instead of m, no launch gaps between orders)
+        auto orders = [&](cudaStream_t st, CoefTab<A> tb) -> csc_status {
+            tb.j = 1;
+            CSC_TRY(launch_cheb_step<T>(g, cfg, X[0], X[1], Y, d_pad, d_pad, c ? c[0] : 0.0, c ? c[1] : 0.0,
+                                        1 | (m == 1 ? 2 : 0), st, tb));
+            for (int j = 1; j < m; ++j) {
+                // Z_j lives in X[j & 1]; Z_{j-1} (overwritten by Z_{j+1}) in the other buffer
+                tb.j = j + 1;
+                CSC_TRY(launch_cheb_step<T>(g, cfg, X[j & 1], X[(j + 1) & 1], Y, d_pad, d_pad, 0.0,
+                                            c ? c[j + 1] : 0.0, j == m - 1 ? 2 : 0, st, tb));
+            }
+            return CSC_OK;
+        };
+        if (!tab.c && !g_prof_enabled && m >= 2 && cfg.win == 0 && g->use_graphs) {
+            // coefficients to a device array the graph reads (stream-ordered before the replay)
+            std::vector<A> hc(m + 1);
+            for (int j = 0; j <= m; ++j) hc[j] = (A)c[j];
+            void* dc = nullptr;
+            CSC_TRY(ws_get(g, WS_COEF1, (m + 1) * sizeof(A), &dc));
+            CSC_CUDA_TRY(cudaMemcpyAsync(dc, hc.data(), (m + 1) * sizeof(A), cudaMemcpyHostToDevice, s));
+            CoefTab<A> gt;
+            gt.c = (const A*)dc;
+            char key[256];
+            snprintf(key, sizeof(key), "cheb:%zu:%d:%d:%d:%d:%d:%d:%d:%p:%p:%p:%p", sizeof(T), d_pad, m, cfg.G,
+                     cfg.NT, cfg.threads, cfg.P, cfg.tiles, (void*)X[0], (void*)X[1], (void*)Y, dc);
+            int64_t launches = 0;
+            const int32_t* pr = nullptr;
+            CSC_TRY(get_partition(g, cfg.P, &pr));  // before the capture
+            CSC_TRY(replay_graph(g, key, s, &launches, [&](cudaStream_t cap) { return orders(cap, gt); }));
+            (void)launches;
+        } else {
+            CSC_TRY(orders(s, tab));
         }
     }
     if (normalize) {

@@ -215,3 +215,26 @@ def test_pin_shape_rejects_bad_shapes():
             csc.csc_graph_pin_shape(h, "cheb_step", 4, 48, 4, 1, 256, 10, 1, 0)   # tiles
         with pytest.raises(csc.CscError):
             csc.csc_graph_pin_shape(h, "cg", 4, 200, 32, 2, 256, 10, 1, 50)       # window on CG
+
+
+def test_graph_replay_matches_eager_launches():
+    """Without per-launch timing the m orders replay a captured CUDA graph; the result
+    is bit-identical to the eager launches, and every replayed kernel is counted."""
+    g = GRAPHS[6][1]
+    d, d_pad, m, lam = 47, 48, 30, 0.43
+    r = torch.from_numpy(ci.gaussian_block(g.n, d, d_pad, seed=3)).cuda()
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        csc.csc_profile_enable(True)
+        eager = csc.csc_filter_random_signals(h, lam, m, d, d_pad, R_in=r, flags=0).clone()
+        csc.csc_profile_enable(False)
+        csc.csc_profile_reset()
+        first = csc.csc_filter_random_signals(h, lam, m, d, d_pad, R_in=r, flags=0).clone()
+        n1 = csc.csc_profile_launches()
+        second = csc.csc_filter_random_signals(h, lam, m, d, d_pad, R_in=r, flags=0).clone()
+        n2 = csc.csc_profile_launches() - n1
+        other = csc.csc_filter_random_signals(h, 0.9, m, d, d_pad, R_in=r, flags=0).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(eager, first) and torch.equal(first, second)
+    assert n1 == n2 >= m + 1  # copy-in + m orders (+ heavy-row launches, if any)
+    ref = _oracle_filter(g, r.cpu().numpy().astype(np.float64), 0.9, m)
+    assert rel(other.cpu().numpy(), ref) <= 1e-5  # new coefficients reach the replay
