@@ -16,6 +16,7 @@
 // range [part[x], part[x+1]) with G lanes per row; CTA y covers the column tile
 // [y*TW, (y+1)*TW), TW = 4*G*NT.  The shape is tuned once per graph and k.
 #include <math.h>
+#include <stdio.h>
 
 #include <algorithm>
 #include <vector>
@@ -747,7 +748,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         sg.gk = d_gk;
         sg.gact = (int*)bt.gact;
     }
-    auto reset_active = [&]() -> csc_status {
+    auto reset_active = [&](cudaStream_t s) -> csc_status {
         CSC_CUDA_TRY(cudaMemsetAsync(st.n_active, 0, sizeof(int), s));
         if (sg.gact) CSC_CUDA_TRY(cudaMemsetAsync(sg.gact, 0, (size_t)nseg * sizeof(int), s));
         return CSC_OK;
@@ -777,7 +778,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         set_error("csc_interpolate: a sample label is outside [0, k) or a sample index outside [0, N)");
         return CSC_E_INVALID;
     }
-    auto apply_A = [&](const float* in, const CgBatch& bb) -> csc_status {
+    auto apply_A = [&](const float* in, const CgBatch& bb, cudaStream_t s) -> csc_status {
         // t = L^(p-1) in, then Ap = mask*in + gamma * L t with <in, Ap> partials
         const float* cur = in;
         float* bufs[2] = {t1, t2};
@@ -834,24 +835,39 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         }
         return CSC_OK;
     };
-    int it = 0;
-    const int check_every = 8;
-    bool converged = h_active[0] == 0;
-    while (!converged && it < max_iter) {
-        const int batch = std::min(check_every, max_iter - it);
-        for (int q = 0; q < batch; ++q) {
-            CSC_TRY(apply_A(p, bt));
+    // `count` CG iterations; between convergence checks they replay as one CUDA graph
+    // when no per-launch timing is asked for
+    auto iterations = [&](cudaStream_t s, int count) -> csc_status {
+        for (int q = 0; q < count; ++q) {
+            CSC_TRY(apply_A(p, bt, s));
             CSC_KLAUNCH("cg_scalar", scal_ax, s, cg_alpha_kernel<<<kb, rb, 0, s>>>(part, PH, sg, k, ld, st));
             // x, r, p, Ap read; x, r written
             CG_SWITCH(cfg, CSC_KLAUNCH("cg_update", 6 * blkb + 4.0 * N + 2 * scal_b, s,
                                        cg_update_kernel<G_, NT_><<<grid, th, 0, s>>>(x, r, p, Ap, st.alpha, gid, pinv,
                                                                                      rpart, ld, ld, part, bt)));
-            CSC_TRY(reset_active());
+            CSC_TRY(reset_active(s));
             CSC_KLAUNCH("cg_scalar", 2 * scal_b, s,
                         cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, st, rel_tol * rel_tol, 0));
             CG_SWITCH(cfg, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
                                        cg_pupdate_kernel<G_, NT_><<<grid, th, 0, s>>>(r, p, st.beta, gid, pinv, rpart,
                                                                                       ld, ld, bt)));
+        }
+        return CSC_OK;
+    };
+    int it = 0;
+    const int check_every = 8;
+    bool converged = h_active[0] == 0;
+    while (!converged && it < max_iter) {
+        const int batch = std::min(check_every, max_iter - it);
+        if (!g_prof_enabled && g->use_graphs) {
+            char key[320];
+            snprintf(key, sizeof(key), "cg:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%.17g:%.17g:%p:%p:%p:%p:%p", batch, ld, k,
+                     nseg, g_power, cfg.G, cfg.NT, cfg.threads, cfg.P, cfg.tiles, gamma, rel_tol, (void*)x, (void*)sd,
+                     (void*)part, (void*)d_gk, (const void*)sg.gblk);
+            int64_t launches = 0;
+            CSC_TRY(replay_graph(g, key, s, &launches, [&](cudaStream_t cap) { return iterations(cap, batch); }));
+        } else {
+            CSC_TRY(iterations(s, batch));
         }
         it += batch;
         CSC_CUDA_TRY(cudaMemcpyAsync(h_active, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -859,7 +875,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         converged = h_active[0] == 0;
     }
     // true residual ||b - A x|| / ||b|| per column
-    CSC_TRY(apply_A(x, bt_all));
+    CSC_TRY(apply_A(x, bt_all, s));
     CG_SWITCH(cfg, CSC_KLAUNCH("cg_residual", blkb + 4.0 * N, s,
                                residual_kernel<G_, NT_><<<grid, th, 0, s>>>(Ap, slab, rpart, ld, ld, part, bt_all)));
     CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, st.rr));

@@ -1035,11 +1035,26 @@ static csc_status moments_typed(Graph* g, int n_moments, int n_probes, uint64_t 
     const int grid = (cfg.P + g->n_heavy) * cfg.tiles;  // block partial slots per step
     const int32_t *gblk = nullptr, *ghvy = nullptr;
     if (nseg > 1) CSC_TRY(get_segments(g, cfg.P, &gblk, &ghvy));
-    for (int j = 0; j < J; ++j) {
-        CSC_TRY(launch_mom_step<T>(g, cfg, X[j & 1], X[(j + 1) & 1], ld, ld, j == 0 ? 1 : 0, P, s));
-        CSC_KLAUNCH("reduce", 24.0 * grid, s,
-                    segment_partials_kernel<<<nseg, 256, 0, s>>>(P, cfg.P, cfg.tiles, g->n_heavy, gblk, ghvy, nseg, j,
-                                                                J, S));
+    auto steps = [&](cudaStream_t st) -> csc_status {
+        for (int j = 0; j < J; ++j) {
+            CSC_TRY(launch_mom_step<T>(g, cfg, X[j & 1], X[(j + 1) & 1], ld, ld, j == 0 ? 1 : 0, P, st));
+            CSC_KLAUNCH("reduce", 24.0 * grid, st,
+                        segment_partials_kernel<<<nseg, 256, 0, st>>>(P, cfg.P, cfg.tiles, g->n_heavy, gblk, ghvy,
+                                                                     nseg, j, J, S));
+        }
+        return CSC_OK;
+    };
+    if (!g_prof_enabled && g->use_graphs && J >= 2) {
+        // the J steps replay as one captured CUDA graph
+        const int32_t* pr = nullptr;
+        CSC_TRY(get_partition(g, cfg.P, &pr));
+        char key[256];
+        snprintf(key, sizeof(key), "mom:%zu:%d:%d:%d:%d:%d:%d:%d:%d:%p:%p:%p:%p", sizeof(T), ld, J, nseg, cfg.G,
+                 cfg.NT, cfg.threads, cfg.P, cfg.tiles, (void*)X[0], (void*)X[1], (void*)P, (void*)S);
+        int64_t launches = 0;
+        CSC_TRY(replay_graph(g, key, s, &launches, steps));
+    } else {
+        CSC_TRY(steps(s));
     }
     const size_t nsum = (size_t)nseg * J * 3;
     std::vector<double> hbuf;

@@ -11,8 +11,9 @@ graph is (centre, ln half-width) of the interval where its eigencount, from
 degree-m moments of the full probe count, lies in [k - 1/2, k + 1/2]; features
 and targets are standardised by their training mean and standard deviation (a
 feature of zero spread maps to 0); the predicted half-width is multiplied by
-a factor ``widen`` calibrated on samples held back from the fit so that a
-chosen share of their brackets is reached.
+a factor ``widen`` calibrated on samples held back from the fit, to the value
+with the fewest eigencount evaluations of the halving started from the
+prediction (or to reach a chosen share of their brackets).
 """
 from __future__ import annotations
 
@@ -60,6 +61,49 @@ def needed_widen(pred_t: np.ndarray, brackets: np.ndarray) -> np.ndarray:
     return dist / hw
 
 
+def search_evaluations(c: float, hw: float, lo: float, hi: float) -> int:
+    """Eigencount evaluations the halving started from the prediction (centre c,
+    half-width hw) spends when the accepted cut-offs are exactly [lo, hi]: count
+    rounds to k inside, exceeds k above, falls short below (a monotone count)."""
+    def side(x):  # 0: accepted, +1: count above k, -1: below
+        return 0 if lo <= x <= hi else (1 if x > hi else -1)
+
+    def halve(a, b, n):
+        for it in range(1, 61):
+            mid = 0.5 * (a + b)
+            sd = side(mid)
+            if sd == 0:
+                return n + it
+            if sd > 0:
+                b = mid
+            else:
+                a = mid
+            if b - a < 1e-12 or it == 60:
+                return n + it + 1
+        return n + 60
+
+    c = min(2.0, max(0.0, c))
+    sc = side(c)
+    if sc == 0:
+        return 1
+    e = max(0.0, c - hw) if sc > 0 else min(2.0, c + hw)
+    se = side(e)
+    if se == 0:
+        return 2
+    if sc > 0:
+        return halve(e, c, 2) if se < 0 else halve(0.0, e, 2)
+    return halve(c, e, 2) if se > 0 else halve(e, 2.0, 2)
+
+
+def best_widen(pred_t: np.ndarray, brackets: np.ndarray, grid=None) -> float:
+    """The half-width factor with the fewest mean evaluations of the started halving."""
+    grid = np.geomspace(0.25, 4096.0, 57) if grid is None else grid
+    hw = np.exp(np.minimum(pred_t[:, 1], 10.0))
+    cost = [np.mean([search_evaluations(pred_t[i, 0], w * hw[i], brackets[i, 0], brackets[i, 1])
+                     for i in range(len(hw))]) for w in grid]
+    return float(grid[int(np.argmin(cost))])
+
+
 @dataclass
 class BracketModel:
     params: torch.Tensor  # device float32[CSC_MLP_PARAMS]
@@ -71,9 +115,12 @@ class BracketModel:
 
     @classmethod
     def fit(cls, feats: np.ndarray, brackets: np.ndarray, epochs: int = 300, batch: int = 32, lr: float = 1e-3,
-            seed: int = 0, coverage: float = 0.9, val_frac: float = 0.15) -> "BracketModel":
-        """Train on all but the last ``val_frac`` of the samples; ``widen`` is set so that
-        a ``coverage`` share of those held-back samples is reached."""
+            seed: int = 0, coverage: float = 0.9, val_frac: float = 0.15,
+            widen_rule: str = "evaluations") -> "BracketModel":
+        """Train on all but the last ``val_frac`` of the samples.  ``widen`` is calibrated
+        on those held-back samples: by default to the fewest mean eigencount
+        evaluations of the started halving (``search_evaluations``), or with
+        ``widen_rule="coverage"`` so that a ``coverage`` share of their brackets is met."""
         feats = np.asarray(feats, dtype=np.float64)
         brackets = np.asarray(brackets, dtype=np.float64)
         n_val = int(round(val_frac * len(feats))) if len(feats) >= 10 else 0
@@ -92,8 +139,11 @@ class BracketModel:
         hist = csc.csc_mlp_train(params, x, y, epochs, batch, lr, seed)
         model = cls(params, norm, 1.0, hist)
         cal = slice(n_fit, None) if n_val else slice(0, n_fit)
-        need = needed_widen(model.predict_targets(feats[cal]), brackets[cal])
-        model.widen = float(max(1.0, np.quantile(need, coverage)))
+        pred = model.predict_targets(feats[cal])
+        if widen_rule == "coverage":
+            model.widen = float(max(1.0, np.quantile(needed_widen(pred, brackets[cal]), coverage)))
+        else:
+            model.widen = best_widen(pred, brackets[cal])
         model.n_fit, model.n_val = n_fit, n_val
         return model
 

@@ -209,3 +209,19 @@ def test_interpolation_every_cg_shape(G, NT, threads):
                                                4, 1e-3, 1e-7, 5000, fuzzy=True)
     assert info.converged
     assert rel(fz.cpu().numpy(), x_ref) <= 1e-3
+
+
+def test_interpolation_graph_replay_matches_eager():
+    """CG iterations replayed from captured CUDA graphs give the eager launches' bits."""
+    g = ci.sbm(1000, 20, seed=2)
+    om = osamp.sample(g.n, 120, 2)
+    lab = torch.from_numpy(g.labels[om].astype(np.int32)).cuda()
+    omd = torch.from_numpy(om).cuda()
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        csc.csc_profile_enable(True)
+        l0, f0, i0 = csc.csc_interpolate(h, omd, lab, 20, fuzzy=True)
+        csc.csc_profile_enable(False)
+        l1, f1, i1 = csc.csc_interpolate(h, omd, lab, 20, fuzzy=True)
+        l2, f2, i2 = csc.csc_interpolate(h, omd, lab, 20, fuzzy=True)
+    assert i0.iters == i1.iters == i2.iters
+    assert torch.equal(f0, f1) and torch.equal(f1, f2) and torch.equal(l0, l2)
