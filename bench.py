@@ -463,6 +463,8 @@ def run_precision(args, w):
         out["storage"][name]["cg_iters"] = info.cg.iters
         labs[name] = lab.cpu().numpy()
     out["ari_bf16_vs_f32_labels"] = adjusted_rand(labs["bf16"], labs["f32"])
+    if g.labels is not None:
+        out["ari_vs_planted"] = {name: adjusted_rand(lab, g.labels) for name, lab in labs.items()}
     out["autotuned_shapes"] = csc.csc_graph_tuned_shapes(h)
     print(json.dumps(out), flush=True)
     h.close()
