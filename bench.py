@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sbm_n1e5_k200", choices=sorted(WORKLOADS))
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f64"])
+    ap.add_argument("--filter", default="clenshaw", choices=["forward", "clenshaw"],
+                    help="evaluate the Chebyshev filter by Clenshaw's backward recurrence (default, same Y "
+                         "with fewer bytes per order) or by the forward three-term recurrence")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -270,8 +273,11 @@ def run_ours(args, w, rank, world, local_rank):
     h = csc.csc_graph_create(g.row_ptr, g.col_idx, flags)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
+    fflags = csc.CLENSHAW if args.filter == "clenshaw" else 0
+
     def step():
-        return csc.csc_cluster(h, k, m=m, d=d, d_pad=d_pad, n=n, storage=storage, seed=args.seed + rank)
+        return csc.csc_cluster(h, k, m=m, d=d, d_pad=d_pad, n=n, storage=storage, seed=args.seed + rank,
+                               flags=fflags)
 
     for _ in range(args.warmup):
         labels, info = step()
@@ -353,7 +359,8 @@ def run_ours(args, w, rank, world, local_rank):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h2 = csc.csc_graph_create(rp_pin.numpy(), ci_pin.numpy(), flags)
-            labs, _ = csc.csc_cluster(h2, k, m=m, d=d, d_pad=d_pad, n=n, storage=storage, seed=args.seed + rank)
+            labs, _ = csc.csc_cluster(h2, k, m=m, d=d, d_pad=d_pad, n=n, storage=storage, seed=args.seed + rank,
+                                      flags=fflags)
             lab_host.copy_(labs)
             torch.cuda.synchronize()
             h2.close()
@@ -387,7 +394,8 @@ def run_ours(args, w, rank, world, local_rank):
                        "n": n, "n_probes": sz["n_v"], "g_power": 4, "gamma": 1e-3, "cg_tol": 1e-6,
                        "l2": "flushed between steps (512 MB write)",
                        "value_basis": "m*nnz*d / device time of the filter stage of each timed step",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "filter": args.filter},
             "csc_seconds": ms_step / 1e3,
             "filter_ms": ms_filter,
             "stages_ms": {kk: statistics.mean(x.ms[kk] for x in infos) for kk in infos[0].ms},

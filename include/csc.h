@@ -73,6 +73,8 @@ typedef int32_t csc_dtype;
 /* csc_filter_random_signals flags */
 #define CSC_NORMALIZE_ROWS 1u  /* Alg. 2 step 4: divide every row by its l2 norm      */
 #define CSC_NO_JACKSON     2u  /* truncated Chebyshev (no Jackson damping)            */
+#define CSC_CLENSHAW       4u  /* evaluate the same polynomial by Clenshaw's backward
+                                  recurrence, R regenerated or re-read per order     */
 
 typedef struct csc_graph_s* csc_graph;
 
@@ -113,6 +115,7 @@ typedef struct {
     uint64_t seed;
     double   lambda_k;     /* > 0: skip step 1 and use this cut-off                   */
     const double* bracket; /* NULL or host {lo, hi}: learned bracket for step 1       */
+    uint32_t flags;        /* CSC_CLENSHAW: filter by Clenshaw's recurrence             */
 } csc_params;
 
 /* Per-stage results and timings of csc_cluster. */
@@ -221,7 +224,12 @@ CSC_API csc_status csc_chebyshev_coefficients(double lambda_c, int32_t m, uint32
  *             (padding columns are ignored and treated as zero).
  *   Y_out     device, N * d_pad row-major in original node order: float for
  *             CSC_F32/CSC_BF16, double for CSC_F64.  Padding columns are zero.
- *   flags     CSC_NORMALIZE_ROWS, CSC_NO_JACKSON.
+ *   flags     CSC_NORMALIZE_ROWS, CSC_NO_JACKSON, CSC_CLENSHAW.  Without
+ *             CSC_CLENSHAW the orders run the three-term forward recurrence
+ *             X_{j+1} = 2 (L - I) X_j - X_{j-1} accumulating Y (Sec. 2.1); with it
+ *             Clenshaw's recurrence b_j = c_j R + 2 (L - I) b_{j+1} - b_{j+2},
+ *             Y = c_0 R + (L - I) b_1 - b_2 (Clenshaw 1955), which needs no Y
+ *             traffic until the last order; both give Y up to rounding.
  * Errors: CSC_E_INVALID (no side effects), CSC_E_OOM, CSC_E_CUDA.  Asynchronous. */
 CSC_API csc_status csc_filter_random_signals(csc_graph g, double lambda_c, int32_t m, int32_t d,
                                      int32_t d_pad, uint64_t seed, csc_dtype storage,

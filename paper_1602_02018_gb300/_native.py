@@ -35,7 +35,7 @@ CSC_E_UNSUPPORTED = 8
 
 CSC_F32, CSC_BF16, CSC_F64 = 0, 1, 2
 CSC_RCM, CSC_CHECK_SYM, CSC_DEVICE_INPUT = 1, 2, 4
-CSC_NORMALIZE_ROWS, CSC_NO_JACKSON = 1, 2
+CSC_NORMALIZE_ROWS, CSC_NO_JACKSON, CSC_CLENSHAW = 1, 2, 4
 CSC_MLP_IN, CSC_MLP_HIDDEN, CSC_MLP_OUT, CSC_MLP_PARAMS = 72, 256, 2, 84994
 CSC_BRACKET_PROBES, CSC_BRACKET_MOMENTS = 8, 64
 CSC_EIGENCOUNT_REFILTER = 1
@@ -54,7 +54,8 @@ class csc_params(ctypes.Structure):
     _fields_ = [("k", c_int32), ("m", c_int32), ("d", c_int32), ("d_pad", c_int32), ("n", c_int64),
                 ("n_probes", c_int32), ("g_power", c_int32), ("gamma", c_double), ("cg_tol", c_double),
                 ("cg_max_iter", c_int32), ("replicates", c_int32), ("km_max_iter", c_int32),
-                ("storage", c_int32), ("seed", c_uint64), ("lambda_k", c_double), ("bracket", P(c_double))]
+                ("storage", c_int32), ("seed", c_uint64), ("lambda_k", c_double), ("bracket", P(c_double)),
+                ("flags", c_uint32)]
 
 
 class csc_batch_info(ctypes.Structure):

@@ -19,7 +19,7 @@ from ._native import check, lib
 
 F32, BF16, F64 = nat.CSC_F32, nat.CSC_BF16, nat.CSC_F64
 RCM, CHECK_SYM, DEVICE_INPUT = nat.CSC_RCM, nat.CSC_CHECK_SYM, nat.CSC_DEVICE_INPUT
-NORMALIZE_ROWS, NO_JACKSON = nat.CSC_NORMALIZE_ROWS, nat.CSC_NO_JACKSON
+NORMALIZE_ROWS, NO_JACKSON, CLENSHAW = nat.CSC_NORMALIZE_ROWS, nat.CSC_NO_JACKSON, nat.CSC_CLENSHAW
 
 
 def _stream(stream) -> ctypes.c_void_p:
@@ -114,7 +114,7 @@ def csc_graph_tuned_shapes(g: Graph) -> list:
     """Launch shapes chosen by the autotuner on this handle (kind, dtype bytes, columns, shape)."""
     out = []
     i = 0
-    kinds = {1: "cheb_step", 2: "mom_step", 3: "cg"}
+    kinds = {1: "cheb_step", 2: "mom_step", 3: "cg", 4: "clenshaw"}
     while True:
         kind, db, cols = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         shape = (ctypes.c_int32 * 6)()
@@ -130,7 +130,7 @@ def csc_graph_tuned_shapes(g: Graph) -> list:
 def csc_graph_pin_shape(g: Graph, kernel: str, dtype_bytes: int, columns: int, G: int, NT: int, threads: int,
                         P: int, tiles: int, win: int = 0) -> None:
     """Fix a launch shape on this handle instead of tuning it."""
-    kind = {"cheb_step": 1, "mom_step": 2, "cg": 3}[kernel]
+    kind = {"cheb_step": 1, "mom_step": 2, "cg": 3, "clenshaw": 4}[kernel]
     shape = (ctypes.c_int32 * 6)(G, NT, threads, P, tiles, win)
     check(lib().csc_graph_pin_shape(g.handle, kind, dtype_bytes, columns, shape), "csc_graph_pin_shape")
 
@@ -379,12 +379,13 @@ class ClusterInfo:
 def csc_cluster(g: Graph, k: int, m: int = 0, d: int = 0, d_pad: int = 0, n: int = 0, n_probes: int = 0,
                 g_power: int = 0, gamma: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0,
                 replicates: int = 0, km_max_iter: int = 0, storage: int = F32, seed: int = 0,
-                lambda_k: float = 0.0, bracket=None, labels_out: Optional[torch.Tensor] = None, stream=None):
+                lambda_k: float = 0.0, bracket=None, labels_out: Optional[torch.Tensor] = None, flags: int = 0,
+                stream=None):
     """Alg. 2 end to end; zero arguments take the library defaults.  Returns (labels, ClusterInfo)."""
     p = nat.csc_params()
     p.k, p.m, p.d, p.d_pad, p.n, p.n_probes, p.g_power = k, m, d, d_pad, n, n_probes, g_power
     p.gamma, p.cg_tol, p.cg_max_iter, p.replicates, p.km_max_iter = gamma, cg_tol, cg_max_iter, replicates, km_max_iter
-    p.storage, p.seed, p.lambda_k = storage, seed, lambda_k
+    p.storage, p.seed, p.lambda_k, p.flags = storage, seed, lambda_k, flags
     br_arr = None
     if bracket is not None:
         br_arr = np.ascontiguousarray(bracket, dtype=np.float64)
@@ -486,13 +487,13 @@ class BatchInfo:
 def csc_cluster_batched(g: Graph, k, m: int = 0, d: int = 0, d_pad: int = 0, n_probes: int = 0, g_power: int = 0,
                         gamma: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0, replicates: int = 0,
                         km_max_iter: int = 0, storage: int = F32, seed: int = 0,
-                        labels_out: Optional[torch.Tensor] = None, stream=None):
+                        labels_out: Optional[torch.Tensor] = None, flags: int = 0, stream=None):
     """Alg. 2 for every graph of a batched handle.  Returns (labels, lambda float64[G], BatchInfo)."""
     kk = np.ascontiguousarray(k, dtype=np.int32)
     p = nat.csc_params()
     p.k, p.m, p.d, p.d_pad, p.n, p.n_probes, p.g_power = 0, m, d, d_pad, 0, n_probes, g_power
     p.gamma, p.cg_tol, p.cg_max_iter, p.replicates, p.km_max_iter = gamma, cg_tol, cg_max_iter, replicates, km_max_iter
-    p.storage, p.seed, p.lambda_k = storage, seed, 0.0
+    p.storage, p.seed, p.lambda_k, p.flags = storage, seed, 0.0, flags
     if labels_out is None:
         labels_out = torch.empty(g.N, dtype=torch.int32, device="cuda")
     lam = np.empty(g.n_graphs, dtype=np.float64)

@@ -826,7 +826,7 @@ csc_status csc_graph_pin_shape(csc_graph g, int32_t kind, int32_t dtype_bytes, i
                                const int32_t* shape) {
     clear_error();
     CSC_TRY(check_graph(g));
-    if (!shape || kind < 1 || kind > 3 || columns < 1 || shape[0] < 1 || shape[1] < 1 ||
+    if (!shape || kind < 1 || kind > 4 || columns < 1 || shape[0] < 1 || shape[1] < 1 ||
         (shape[2] != 256 && shape[2] != 512) || shape[3] < 1 || shape[4] < 1 || shape[5] < 0 ||
         (kind != 1 && shape[5] != 0) || (shape[5] > 0 && shape[4] != 1) || shape[5] > g->N) {
         set_error("csc_graph_pin_shape: invalid shape");
@@ -915,7 +915,7 @@ csc_status csc_filter_random_signals(csc_graph g, double lambda_c, int32_t m, in
     std::vector<double> c(m + 1);
     cheb_coefficients(lambda_c, m, (flags & CSC_NO_JACKSON) == 0, c.data());
     csc_status st = run_filter(g, c.data(), m, d, d_pad, seed, storage, R_in, Y_out,
-                               (flags & CSC_NORMALIZE_ROWS) != 0, (cudaStream_t)stream);
+                               (flags & CSC_NORMALIZE_ROWS) != 0, (cudaStream_t)stream, (flags & CSC_CLENSHAW) != 0);
     return poison_on_cuda(g, st);
 }
 
@@ -1282,7 +1282,7 @@ csc_status csc_cluster(csc_graph g, const csc_params* p, int32_t* labels_out, cs
     int32_t* slab = (int32_t*)(b + off_lab);
     std::vector<double> c(m + 1);
     cheb_coefficients(lam, m, true, c.data());
-    st = run_filter(g, c.data(), m, d, d_pad, p->seed, storage, nullptr, Y, true, s);
+    st = run_filter(g, c.data(), m, d, d_pad, p->seed, storage, nullptr, Y, true, s, (p->flags & CSC_CLENSHAW) != 0);
     if (st != CSC_OK) return done(st);
     cudaEventRecord(e2, s);
     st = run_sample(N, n, p->seed, idx, g, s);

@@ -226,12 +226,14 @@ csc_status csc_filter_batched(csc_graph g, const double* lambda, int32_t m, int3
     }
     if (G == 1) {
         csc_status st = run_filter(g, c.data(), m, d, d_pad, seed, storage, R_in, Y_out,
-                                   (flags & CSC_NORMALIZE_ROWS) != 0, (cudaStream_t)stream);
+                                   (flags & CSC_NORMALIZE_ROWS) != 0, (cudaStream_t)stream,
+                                   (flags & CSC_CLENSHAW) != 0);
         if (st == CSC_E_CUDA) g->poisoned = true;
         return st;
     }
     csc_status st = run_filter_batched(g, c.data(), m, d, d_pad, seed, storage, R_in, Y_out,
-                                       (flags & CSC_NORMALIZE_ROWS) != 0, (cudaStream_t)stream);
+                                       (flags & CSC_NORMALIZE_ROWS) != 0, (cudaStream_t)stream,
+                                       (flags & CSC_CLENSHAW) != 0);
     if (st == CSC_E_CUDA) g->poisoned = true;
     return st;
 }
@@ -372,8 +374,9 @@ csc_status csc_cluster_batched(csc_graph g, const int32_t* k, const csc_params* 
     int32_t* slab = (int32_t*)(b + off_lab);
     std::vector<double> c((size_t)G * (m + 1));
     for (int i = 0; i < G; ++i) cheb_coefficients(lam[i], m, true, c.data() + (size_t)i * (m + 1));
-    st = G > 1 ? run_filter_batched(g, c.data(), m, d, d_pad, p->seed, storage, nullptr, Y, true, s)
-               : run_filter(g, c.data(), m, d, d_pad, p->seed, storage, nullptr, Y, true, s);
+    const bool clen = (p->flags & CSC_CLENSHAW) != 0;
+    st = G > 1 ? run_filter_batched(g, c.data(), m, d, d_pad, p->seed, storage, nullptr, Y, true, s, clen)
+               : run_filter(g, c.data(), m, d, d_pad, p->seed, storage, nullptr, Y, true, s, clen);
     if (st != CSC_OK) return done(st);
     cudaEventRecord(ev[2], s);
     st = run_sample_batched(g, n_per.data(), p->seed, idx, s);

@@ -89,6 +89,7 @@ enum WsSlot {
     WS_REFILTER,    // filtered probes and partials of the paper-literal eigencount
     WS_COEF,        // per-graph filter coefficients of a batch
     WS_COEF1,       // filter coefficients read by a captured CUDA graph
+    WS_XR,          // s R, read by every order of the Clenshaw form
     WS_COUNT
 };
 
@@ -219,10 +220,11 @@ csc_status launch_degrees(Graph* g, cudaStream_t s);
 // spmm.cu: the Jackson-Chebyshev filter (K3 + K1 + K5)
 // Batched handle: c_graphs is host double[n_graphs x (m + 1)], graph i's coefficients.
 csc_status run_filter_batched(Graph* g, const double* c_graphs, int m, int d, int d_pad, uint64_t seed,
-                              csc_dtype storage, const float* R_in, void* Y_out, bool normalize, cudaStream_t s);
+                              csc_dtype storage, const float* R_in, void* Y_out, bool normalize, cudaStream_t s,
+                              bool clenshaw = false);
 csc_status run_filter(Graph* g, const double* coeffs, int m, int d, int d_pad, uint64_t seed,
                       csc_dtype storage, const float* R_in, void* Y_out, bool normalize,
-                      cudaStream_t s);
+                      cudaStream_t s, bool clenshaw = false);
 
 // spmm.cu: eigencount moments (K2); mu_host receives n_moments values
 // per_graph: one moment vector per graph of a batched handle (mu_host: n_graphs x n_moments)

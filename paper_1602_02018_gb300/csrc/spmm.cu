@@ -71,6 +71,17 @@ __device__ __forceinline__ A row_scale(A dinv_i) {
     return dinv_i > A(0) ? dinv_i : A(1);
 }
 
+// Filter coefficients read from device memory: c[gid[row] * stride + j] is c_j of
+// the row's graph in a batch; with gid == nullptr, c[j] for every row (the form
+// replayed by a captured CUDA graph); c == nullptr: the scalar coefficients apply.
+template <typename A>
+struct CoefTab {
+    const A* c = nullptr;
+    const int32_t* gid = nullptr;
+    int stride = 0;
+    int j = 0;  // index of c_next; c_0 at 0
+};
+
 // ------------------------------------------------------------------- K3
 // One thread per (row, column quad): four normals from one Philox call.
 // Writes Z_0 = s R (row scale s of the pre-scaled form; `scale` = D^-1/2, NULL for none).
@@ -126,7 +137,8 @@ __global__ void __launch_bounds__(256) probe_trace_kernel(const float* __restric
 template <typename T>
 __global__ void gauss_fill_kernel(T* __restrict__ X, int32_t N, int d, int ld, uint64_t seed,
                                   uint32_t stream, float sigma, const int32_t* __restrict__ perm,
-                                  const typename StoreTraits<T>::acc_t* __restrict__ scale) {
+                                  const typename StoreTraits<T>::acc_t* __restrict__ scale,
+                                  CoefTab<typename StoreTraits<T>::acc_t> ftab) {
     using Tr = StoreTraits<T>;
     const int quads = ld / 4;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -137,7 +149,8 @@ __global__ void gauss_fill_kernel(T* __restrict__ X, int32_t N, int d, int ld, u
     float z[4];
     gauss_quad(orig, q, d, seed, stream, sigma, z);
     using A = typename Tr::acc_t;
-    const A sc = scale ? row_scale<A>(scale[row]) : A(1);
+    A sc = scale ? row_scale<A>(scale[row]) : A(1);
+    if (ftab.c) sc *= (ftab.gid ? ftab.c + (int64_t)ftab.gid[row] * ftab.stride : ftab.c)[ftab.j];
     T* dst = X + (int64_t)row * ld + 4 * q;
 #pragma unroll
     for (int v = 0; v < 4; ++v) dst[v] = (T)((A)z[v] * sc);
@@ -147,14 +160,16 @@ __global__ void gauss_fill_kernel(T* __restrict__ X, int32_t N, int d, int ld, u
 template <typename T>
 __global__ void copy_in_kernel(T* __restrict__ X, const float* __restrict__ R, int32_t N, int d, int ld,
                                int ld_in, const int32_t* __restrict__ perm,
-                               const typename StoreTraits<T>::acc_t* __restrict__ scale) {
+                               const typename StoreTraits<T>::acc_t* __restrict__ scale,
+                               CoefTab<typename StoreTraits<T>::acc_t> ftab) {
     using A = typename StoreTraits<T>::acc_t;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)N * ld) return;
     const int row = (int)(t / ld);
     const int c = (int)(t % ld);
     const int64_t orig = perm ? perm[row] : row;
-    const A sc = scale ? row_scale<A>(scale[row]) : A(1);
+    A sc = scale ? row_scale<A>(scale[row]) : A(1);
+    if (ftab.c) sc *= (ftab.gid ? ftab.c + (int64_t)ftab.gid[row] * ftab.stride : ftab.c)[ftab.j];
     X[t] = (T)(c < d ? (A)R[orig * ld_in + c] * sc : A(0));
 }
 
@@ -170,16 +185,6 @@ __global__ void copy_in_kernel(T* __restrict__ X, const float* __restrict__ R, i
 // kHeavyRow edges are skipped here and done by the *_heavy kernels.
 
 // The per-row update of one order given the row's neighbour sum acc (column tile col0).
-// Filter coefficients read from device memory: c[gid[row] * stride + j] is c_j of
-// the row's graph in a batch; with gid == nullptr, c[j] for every row (the form
-// replayed by a captured CUDA graph); c == nullptr: the scalar coefficients apply.
-template <typename A>
-struct CoefTab {
-    const A* c = nullptr;
-    const int32_t* gid = nullptr;
-    int stride = 0;
-    int j = 0;  // index of c_next; c_0 at 0
-};
 
 template <typename T, int G, int NT>
 __device__ __forceinline__ void cheb_epilogue(int row, int lane, int col0, int tcols,
@@ -351,6 +356,165 @@ __global__ void scale_copy_kernel(const T* __restrict__ X, typename StoreTraits<
     const int c = (int)(t % ld);
     const int64_t yrow = perm ? perm[row] : row;
     Y[yrow * ld + c] = c0 * (typename StoreTraits<T>::acc_t)X[t] * sqdeg[row];
+}
+
+// ------------------------------------------------------- K4 (Clenshaw form)
+// The same Y = sum_j c_j T_j(L - I) R evaluated by Clenshaw's backward recurrence
+// (Clenshaw 1955): b_j = c_j R + 2 (L - I) b_{j+1} - b_{j+2} for j = m-1 .. 1 from
+// b_m = c_m R, b_{m+1} = 0, and Y = c_0 R + (L - I) b_1 - b_2.  In the pre-scaled form
+// B_j = s b_j:  B_j = c_j s R - 2 D^-1 W B_{j+1} - B_{j+2},  Y = D^1/2 (c_0 s R -
+// D^-1 W B_1 - B_2).  Each order gathers B_{j+1}, reads B_{j+2} and overwrites it
+// with B_j; the block s R is stored once in the storage type and read back every
+// order instead of accumulating Y in memory, so an order moves 4 N d stored values
+// plus the CSR instead of 3 N d stored plus 2 N d accumulator values.  The last
+// order writes Y (optionally normalised per row when one column tile holds the
+// whole row).
+
+// Row epilogue of one Clenshaw order.  mode: 1 = no B_{j+2} (j = m-1), 2 = last
+// order (write Y), 4 = plain caching (working set fits L2), 8 = normalise Y rows
+// (the group's lanes hold the whole row; gmask = the group's lanes).
+// rs: the block s R stored in T (internal row order, stride ld).  LAST: the order
+// j = 0 (writes Y); a separate instantiation so the other orders carry no Y state.
+template <typename T, int G, int NT, bool LAST>
+__device__ __forceinline__ void clenshaw_epilogue(int row, int lane, int col0, int tcols,
+                                                  typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC],
+                                                  const typename StoreTraits<T>::acc_t* __restrict__ invdeg,
+                                                  const typename StoreTraits<T>::acc_t* __restrict__ sqdeg,
+                                                  T* __restrict__ bpp, typename StoreTraits<T>::acc_t* __restrict__ Y,
+                                                  const int32_t* __restrict__ perm, int64_t ld,
+                                                  typename StoreTraits<T>::acc_t cj, int mode,
+                                                  const T* __restrict__ rs, unsigned gmask) {
+    using Tr = StoreTraits<T>;
+    using A = typename Tr::acc_t;
+    constexpr int VEC = Tr::VEC;
+    const bool first = (mode & 1) != 0, keep = (mode & 4) != 0;
+    constexpr bool last = LAST;
+    const A f = (last ? A(-1) : A(-2)) * invdeg[row];
+    A out[LAST ? NT : 1][VEC];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const int cl = (t * G + lane) * VEC;
+        if (cl >= tcols) continue;
+        const int c = col0 + cl;
+        const int to = LAST ? t : 0;
+        A r[VEC], b2[VEC];
+        // s R and B_{j+2} are dead after this order: evict-first unless all fits L2, so
+        // the gathered B_{j+1} and the B_j written here (gathered next) stay resident
+        if (keep) Tr::load(rs + (int64_t)row * ld + c, r);
+        else Tr::load_cs(rs + (int64_t)row * ld + c, r);
+        if (first) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) b2[v] = A(0);
+        } else if (keep) {
+            Tr::load(bpp + (int64_t)row * ld + c, b2);
+        } else {
+            Tr::load_cs(bpp + (int64_t)row * ld + c, b2);
+        }
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) out[to][v] = cj * r[v] + f * acc[t][v] - b2[v];
+        if constexpr (!LAST) {
+            A bn[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) bn[v] = Tr::round(out[0][v]);
+            Tr::store(bpp + (int64_t)row * ld + c, bn);
+        }
+    }
+    if constexpr (!LAST) return;
+    else {
+    const A back = sqdeg[row];
+    double inv = 1.0;
+    if (mode & 8) {
+        double ss = 0.0;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int cl = (t * G + lane) * VEC;
+            if (cl >= tcols) continue;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+                const double y = (double)(out[t][v] * back);
+                ss += y * y;
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) ss += __shfl_xor_sync(gmask, ss, o, G);
+        if (ss > 0.0) inv = 1.0 / sqrt(ss);
+    }
+    const int64_t yrow = perm ? (int64_t)perm[row] : (int64_t)row;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const int cl = (t * G + lane) * VEC;
+        if (cl >= tcols) continue;
+        A y[VEC];
+        if (mode & 8) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) y[v] = (A)((double)(out[t][v] * back) * inv);
+        } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) y[v] = out[t][v] * back;
+        }
+        AccIO<A, VEC>::store(Y + yrow * ld + col0 + cl, y);
+    }
+    }
+}
+
+template <typename T, int G, int NT, bool LAST>
+__global__ void __launch_bounds__(512)
+clenshaw_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                     const typename StoreTraits<T>::acc_t* __restrict__ invdeg,
+                     const typename StoreTraits<T>::acc_t* __restrict__ sqdeg,
+                     const T* __restrict__ bnext, T* __restrict__ bpp, typename StoreTraits<T>::acc_t* __restrict__ Y,
+                     const int32_t* __restrict__ perm, const int32_t* __restrict__ part, int ncols, int64_t ld,
+                     typename StoreTraits<T>::acc_t cj, int mode, CoefTab<typename StoreTraits<T>::acc_t> tab,
+                     const T* __restrict__ rs) {
+    using A = typename StoreTraits<T>::acc_t;
+    constexpr int VEC = StoreTraits<T>::VEC;
+    constexpr int TW = G * NT * VEC;
+    const int lane = threadIdx.x % G;
+    const int col0 = blockIdx.y * TW;
+    const int tcols = min(TW, ncols - col0);
+    const int r0 = part[blockIdx.x], r1 = part[blockIdx.x + 1];
+    if (tab.c && r0 < r1) cj = (tab.gid ? tab.c + (int64_t)tab.gid[r0] * tab.stride : tab.c)[tab.j];
+    const unsigned gmask =
+        G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(unsigned)(G - 1)));
+    for (int row = r0 + (int)(threadIdx.x / G); row < r1; row += (int)(blockDim.x / G)) {
+        const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
+        if (e1 - e0 > kHeavyRow) continue;
+        A acc[NT][VEC];
+        gather_range<T, G, NT, false, A>(e0, e1, ci, nullptr, bnext + col0, ld, lane, tcols, acc);
+        clenshaw_epilogue<T, G, NT, LAST>(row, lane, col0, tcols, acc, invdeg, sqdeg, bpp, Y, perm, ld, cj, mode, rs,
+                                          gmask);
+    }
+}
+
+template <typename T, int G, int NT>
+__global__ void __launch_bounds__(kHeavyThreads)
+clenshaw_step_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const typename StoreTraits<T>::acc_t* __restrict__ invdeg,
+                           const typename StoreTraits<T>::acc_t* __restrict__ sqdeg,
+                           const T* __restrict__ bnext, T* __restrict__ bpp,
+                           typename StoreTraits<T>::acc_t* __restrict__ Y, const int32_t* __restrict__ perm,
+                           const int32_t* __restrict__ heavy, int ncols, int64_t ld, typename StoreTraits<T>::acc_t cj,
+                           int mode, CoefTab<typename StoreTraits<T>::acc_t> tab, const T* __restrict__ rs) {
+    using A = typename StoreTraits<T>::acc_t;
+    constexpr int VEC = StoreTraits<T>::VEC;
+    constexpr int TW = G * NT * VEC;
+    const int lane = threadIdx.x % G;
+    const int col0 = blockIdx.y * TW;
+    const int tcols = min(TW, ncols - col0);
+    const int row = heavy[blockIdx.x];
+    if (tab.c) cj = (tab.gid ? tab.c + (int64_t)tab.gid[row] * tab.stride : tab.c)[tab.j];
+    A acc[NT][VEC];
+    gather_heavy<T, G, NT, false, A>(__ldg(rp + row), __ldg(rp + row + 1), ci, nullptr, bnext + col0, ld, lane, tcols,
+                                     acc);
+    const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+    if (threadIdx.x < G) {
+        if (mode & 2)
+            clenshaw_epilogue<T, G, NT, true>(row, lane, col0, tcols, acc, invdeg, sqdeg, bpp, Y, perm, ld, cj, mode,
+                                              rs, gmask);
+        else
+            clenshaw_epilogue<T, G, NT, false>(row, lane, col0, tcols, acc, invdeg, sqdeg, bpp, Y, perm, ld, cj, mode,
+                                               rs, gmask);
+    }
 }
 
 // ------------------------------------------------------------------- K5
@@ -557,7 +721,7 @@ static const TileShape kShapes[] = {{2, 1}, {2, 2}, {2, 3}, {4, 1}, {4, 2}, {4, 
                                     {8, 2}, {8, 3}, {16, 1}, {16, 2}, {32, 1}, {32, 2}};
 static const int kThreadChoices[] = {256, 512};
 
-enum KernelKind { KK_CHEB = 1, KK_MOM = 2 };
+enum KernelKind { KK_CHEB = 1, KK_MOM = 2, KK_CLEN = 4 };
 
 // Expands BODY for the compiled (G, NT) equal to (cfg.G, cfg.NT), with GG / NN bound.
 #define CSC_SHAPE_SWITCH(cfg, BODY)                                                       \
@@ -642,6 +806,55 @@ static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur
     return CSC_OK;
 }
 
+// One Clenshaw order (see clenshaw_step_kernel): heavy rows first, then the row ranges.
+template <typename T>
+static csc_status launch_clenshaw_step(Graph* g, const LaunchCfg& cfg, const T* bnext, T* bpp,
+                                       typename StoreTraits<T>::acc_t* Y, int ncols, int64_t ld, double cj, int mode,
+                                       const T* rs, cudaStream_t s, CoefTab<typename StoreTraits<T>::acc_t> tab = {}) {
+    using A = typename StoreTraits<T>::acc_t;
+    const A *idg, *sqd;
+    if constexpr (sizeof(A) == 8) {
+        idg = g->invdeg64;
+        sqd = g->sqdeg64;
+    } else {
+        idg = g->invdeg;
+        sqd = g->sqdeg;
+    }
+    const double ws = (double)g->N * ld * 3.0 * sizeof(T) + 4.0 * g->nnz + 8.0 * g->N;
+    if (ws <= kKeepL2Fraction * (double)g->l2_bytes) mode |= 4;
+    const int32_t* part = nullptr;
+    CSC_TRY(get_partition(g, cfg.P, &part));
+    const dim3 grid(cfg.P, cfg.tiles);
+    // algorithmic bytes of one order: CSR + row factors, B_{j+1} gathered once, B_{j+2} read
+    // (not on the first order), B_j written (not on the last), Y written (last), s R read
+    const double nx = (double)g->N * ncols;
+    const bool first = mode & 1, last = mode & 2;
+    const double all_bytes = 4.0 * g->nnz + 4.0 * (g->N + 1) + (double)sizeof(A) * g->N * (last ? 2 : 1) +
+                             nx * sizeof(T) * (2.0 + (first ? 0.0 : 1.0) + (last ? 0.0 : 1.0)) +
+                             (last ? nx * sizeof(A) : 0.0);
+    const double heavy_edges = (double)g->nnz - (double)g->h_light[g->N];
+    const double heavy_frac = g->n_heavy ? (heavy_edges + g->n_heavy) / ((double)g->nnz + g->N) : 0.0;
+    if (g->n_heavy > 0) {
+        const dim3 hgrid(g->n_heavy, cfg.tiles);
+        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * heavy_frac, s,
+                                          clenshaw_step_heavy_kernel<T, GG, NN><<<hgrid, kHeavyThreads, 0, s>>>(
+                                              g->row_ptr, g->col_idx, idg, sqd, bnext, bpp, Y, g->perm, g->heavy,
+                                              ncols, ld, (A)cj, mode, tab, rs)));
+    }
+    if (last) {
+        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * (1.0 - heavy_frac), s,
+                                          clenshaw_step_kernel<T, GG, NN, true><<<grid, cfg.threads, 0, s>>>(
+                                              g->row_ptr, g->col_idx, idg, sqd, bnext, bpp, Y, g->perm, part, ncols,
+                                              ld, (A)cj, mode, tab, rs)));
+    } else {
+        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * (1.0 - heavy_frac), s,
+                                          clenshaw_step_kernel<T, GG, NN, false><<<grid, cfg.threads, 0, s>>>(
+                                              g->row_ptr, g->col_idx, idg, sqd, bnext, bpp, Y, g->perm, part, ncols,
+                                              ld, (A)cj, mode, tab, rs)));
+    }
+    return CSC_OK;
+}
+
 template <typename T>
 static csc_status launch_mom_step(Graph* g, const LaunchCfg& cfg, const T* xcur, T* xpn, int ncols, int64_t ld,
                                   int first, double* partials, cudaStream_t s) {
@@ -692,6 +905,7 @@ static int kernel_occupancy(int kind, const TileShape& sh, int threads, size_t w
     if (sh.G == GG && sh.NT == NN) {                                                     \
         if (kind == KK_CHEB && win_smem) fw(cheb_step_win_kernel<T, GG, NN>);           \
         else if (kind == KK_CHEB) f(cheb_step_kernel<T, GG, NN>);                        \
+        else if (kind == KK_CLEN) f(clenshaw_step_kernel<T, GG, NN, false>);             \
         else if constexpr (sizeof(T) <= 4) f(mom_step_kernel<T, GG, NN>);               \
     }
     CSC_OCC_CASE(2, 1) CSC_OCC_CASE(2, 2) CSC_OCC_CASE(2, 3) CSC_OCC_CASE(4, 1) CSC_OCC_CASE(4, 2)
@@ -822,7 +1036,8 @@ static uint64_t tune_key(int kind, int dtype, int ncols) {
 
 template <typename T>
 static csc_status fill_block(Graph* g, T* X, int d, int ld, uint64_t seed, uint32_t stream, float sigma,
-                             const float* R_in, int ld_in, cudaStream_t s) {
+                             const float* R_in, int ld_in, cudaStream_t s,
+                             CoefTab<typename StoreTraits<T>::acc_t> ftab = {}) {
     using A = typename StoreTraits<T>::acc_t;
     const int64_t N = g->N;
     const A* scale;  // Z_0 = D^-1/2 R (row factor 1 for isolated nodes)
@@ -831,12 +1046,12 @@ static csc_status fill_block(Graph* g, T* X, int d, int ld, uint64_t seed, uint3
         const int64_t tot = N * ld;
         CSC_KLAUNCH("copy_in", (double)tot * (4 + sizeof(T)), s,
                     copy_in_kernel<T><<<ceil_div(tot, 256), 256, 0, s>>>(X, R_in, (int32_t)N, d, ld, ld_in,
-                                                                         g->perm, scale));
+                                                                         g->perm, scale, ftab));
     } else {
         const int64_t tot = N * (ld / 4);
         CSC_KLAUNCH("gauss_fill", (double)N * ld * sizeof(T), s,
                     gauss_fill_kernel<T><<<ceil_div(tot, 256), 256, 0, s>>>(X, (int32_t)N, d, ld, seed, stream,
-                                                                            sigma, g->perm, scale));
+                                                                            sigma, g->perm, scale, ftab));
     }
     return CSC_OK;
 }
@@ -845,7 +1060,7 @@ template <typename T>
 static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pad, uint64_t seed,
                                const float* R_in, void* Y_out, bool normalize, cudaStream_t s,
                                uint32_t rng_stream = STREAM_SIGNALS, float sigma_override = 0.f,
-                               const double* c_graphs = nullptr) {
+                               const double* c_graphs = nullptr, bool clenshaw = false) {
     using A = typename StoreTraits<T>::acc_t;
     constexpr int VEC = StoreTraits<T>::VEC;
     const int64_t N = g->N;
@@ -856,7 +1071,6 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
     T* X[2] = {(T*)xa, (T*)xb};
     A* Y = (A*)Y_out;
     const float sigma = sigma_override > 0.f ? sigma_override : d > 0 ? (float)(1.0 / sqrt((double)d)) : 1.0f;
-    CSC_TRY(fill_block<T>(g, X[0], d, d_pad, seed, rng_stream, sigma, R_in, d_pad, s));
     CoefTab<A> tab;
     if (c_graphs) {
         // per-graph coefficients, G x (m + 1), in the accumulator type
@@ -876,14 +1090,17 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
         tab.gid = g->graph_of_row;
         tab.stride = m + 1;
     }
+    const bool graphs = !g_prof_enabled && m >= 2 && g->use_graphs;
     if (m == 0) {
+        CSC_TRY(fill_block<T>(g, X[0], d, d_pad, seed, rng_stream, sigma, R_in, d_pad, s));
         const int64_t tot = N * d_pad;
         const A* sqd;
         if constexpr (sizeof(A) == 8) sqd = g->sqdeg64; else sqd = g->sqdeg;
         CSC_KLAUNCH("scale_copy", (double)tot * (sizeof(T) + sizeof(A)), s,
                     scale_copy_kernel<T><<<ceil_div(tot, 256), 256, 0, s>>>(X[0], Y, g->perm, (int32_t)N, d_pad,
                                                                             (A)c[0], sqd));
-    } else {
+    } else if (!clenshaw) {
+        CSC_TRY(fill_block<T>(g, X[0], d, d_pad, seed, rng_stream, sigma, R_in, d_pad, s));
         // launch shape tuned once per handle on this graph: trial orders read Z_0 and write
         // scratch (the Z_1 buffer and Y are overwritten by the first real order)
         LaunchCfg cfg;
@@ -906,7 +1123,7 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
             }
             return CSC_OK;
         };
-        if (!tab.c && !g_prof_enabled && m >= 2 && cfg.win == 0 && g->use_graphs) {
+        if (!tab.c && graphs && cfg.win == 0) {
             // coefficients to a device array the graph reads (stream-ordered before the replay)
             std::vector<A> hc(m + 1);
             for (int j = 0; j <= m; ++j) hc[j] = (A)c[j];
@@ -926,6 +1143,56 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
         } else {
             CSC_TRY(orders(s, tab));
         }
+    } else {
+        // Clenshaw form: coefficients always from device memory (per graph in a batch)
+        if (!tab.c) {
+            std::vector<A> hc(m + 1);
+            for (int j = 0; j <= m; ++j) hc[j] = (A)c[j];
+            void* dc = nullptr;
+            CSC_TRY(ws_get(g, WS_COEF1, (m + 1) * sizeof(A), &dc));
+            CSC_CUDA_TRY(cudaMemcpyAsync(dc, hc.data(), (m + 1) * sizeof(A), cudaMemcpyHostToDevice, s));
+            tab.c = (const A*)dc;
+        }
+        // B_m = c_m s R, and s R itself in a third buffer that every order reads
+        CoefTab<A> ft = tab;
+        ft.j = m;
+        CSC_TRY(fill_block<T>(g, X[0], d, d_pad, seed, rng_stream, sigma, R_in, d_pad, s, ft));
+        void* xr = nullptr;
+        CSC_TRY(ws_get(g, WS_XR, bytes, &xr));
+        T* RS = (T*)xr;
+        CSC_TRY(fill_block<T>(g, RS, d, d_pad, seed, rng_stream, sigma, R_in, d_pad, s));
+        LaunchCfg cfg;
+        CSC_TRY(autotune(g, tune_key(KK_CLEN, (int)sizeof(T), d_pad), candidates<T>(g, KK_CLEN, d_pad / VEC), s,
+                         [&](const LaunchCfg& c) {
+                             return launch_clenshaw_step<T>(g, c, X[0], X[1], Y, d_pad, d_pad, 0.0, 1, RS, s);
+                         },
+                         &cfg));
+        const bool fused_norm = normalize && cfg.tiles == 1;
+        auto orders = [&](cudaStream_t st) -> csc_status {
+            CoefTab<A> tb = tab;
+            // B_j lives in X[(m - j) & 1]; B_{j+2} (overwritten by B_j) in the same buffer
+            for (int j = m - 1; j >= 1; --j) {
+                tb.j = j;
+                CSC_TRY(launch_clenshaw_step<T>(g, cfg, X[(m - j - 1) & 1], X[(m - j) & 1], Y, d_pad, d_pad, 0.0,
+                                                j == m - 1 ? 1 : 0, RS, st, tb));
+            }
+            tb.j = 0;
+            return launch_clenshaw_step<T>(g, cfg, X[(m - 1) & 1], X[m & 1], Y, d_pad, d_pad, 0.0,
+                                           2 | (m == 1 ? 1 : 0) | (fused_norm ? 8 : 0), RS, st, tb);
+        };
+        if (graphs) {
+            char key[320];
+            snprintf(key, sizeof(key), "clen:%zu:%d:%d:%d:%d:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p", sizeof(T), d_pad, m, d,
+                     (int)fused_norm, cfg.G, cfg.NT, cfg.threads, cfg.P, cfg.tiles, (const void*)RS, (void*)X[0],
+                     (void*)X[1], (void*)Y, (const void*)tab.c);
+            int64_t launches = 0;
+            const int32_t* pr = nullptr;
+            CSC_TRY(get_partition(g, cfg.P, &pr));  // before the capture
+            CSC_TRY(replay_graph(g, key, s, &launches, orders));
+        } else {
+            CSC_TRY(orders(s));
+        }
+        if (fused_norm) return CSC_OK;
     }
     if (normalize) {
         int grid = ceil_div(N, 8);
@@ -937,17 +1204,18 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
 }
 
 csc_status run_filter_batched(Graph* g, const double* c_graphs, int m, int d, int d_pad, uint64_t seed,
-                              csc_dtype storage, const float* R_in, void* Y_out, bool normalize, cudaStream_t s) {
+                              csc_dtype storage, const float* R_in, void* Y_out, bool normalize, cudaStream_t s,
+                              bool clenshaw) {
     switch (storage) {
         case CSC_F32:
             return filter_typed<float>(g, nullptr, m, d, d_pad, seed, R_in, Y_out, normalize, s, STREAM_SIGNALS, 0.f,
-                                       c_graphs);
+                                       c_graphs, clenshaw);
         case CSC_BF16:
             return filter_typed<__nv_bfloat16>(g, nullptr, m, d, d_pad, seed, R_in, Y_out, normalize, s,
-                                               STREAM_SIGNALS, 0.f, c_graphs);
+                                               STREAM_SIGNALS, 0.f, c_graphs, clenshaw);
         case CSC_F64:
             return filter_typed<double>(g, nullptr, m, d, d_pad, seed, R_in, Y_out, normalize, s, STREAM_SIGNALS,
-                                        0.f, c_graphs);
+                                        0.f, c_graphs, clenshaw);
         default:
             set_error("unknown storage type %d", (int)storage);
             return CSC_E_INVALID;
@@ -956,14 +1224,17 @@ csc_status run_filter_batched(Graph* g, const double* c_graphs, int m, int d, in
 
 csc_status run_filter(Graph* g, const double* coeffs, int m, int d, int d_pad, uint64_t seed,
                       csc_dtype storage, const float* R_in, void* Y_out, bool normalize,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool clenshaw) {
     switch (storage) {
         case CSC_F32:
-            return filter_typed<float>(g, coeffs, m, d, d_pad, seed, R_in, Y_out, normalize, s);
+            return filter_typed<float>(g, coeffs, m, d, d_pad, seed, R_in, Y_out, normalize, s, STREAM_SIGNALS, 0.f,
+                                       nullptr, clenshaw);
         case CSC_BF16:
-            return filter_typed<__nv_bfloat16>(g, coeffs, m, d, d_pad, seed, R_in, Y_out, normalize, s);
+            return filter_typed<__nv_bfloat16>(g, coeffs, m, d, d_pad, seed, R_in, Y_out, normalize, s,
+                                               STREAM_SIGNALS, 0.f, nullptr, clenshaw);
         case CSC_F64:
-            return filter_typed<double>(g, coeffs, m, d, d_pad, seed, R_in, Y_out, normalize, s);
+            return filter_typed<double>(g, coeffs, m, d, d_pad, seed, R_in, Y_out, normalize, s, STREAM_SIGNALS, 0.f,
+                                        nullptr, clenshaw);
         default:
             set_error("unknown storage type %d", (int)storage);
             return CSC_E_INVALID;

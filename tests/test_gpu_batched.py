@@ -208,3 +208,19 @@ def test_cluster_batched_matches_separate_runs():
         a_s.append(oari.ari(l1.cpu().numpy(), g.labels))
     assert abs(np.mean(a_b) - np.mean(a_s)) <= 0.03
     assert np.mean(a_b) >= 0.8
+
+
+@pytest.mark.parametrize("storage,tol", [(0, 1e-5), (2, 1e-12)])
+def test_clenshaw_per_graph_cutoffs_match_oracle(storage, tol):
+    d, d_pad, m = 21, 24, 30
+    lam = np.linspace(0.2, 1.1, len(BATCH))
+    r = ci.gaussian_block(int(OFFS[-1]), d, d_pad, seed=7)
+    with _handle() as h:
+        y = csc.csc_filter_batched(h, lam, m, d, d_pad, storage=storage, R_in=torch.from_numpy(r).cuda(),
+                                   flags=csc.CLENSHAW).cpu().numpy()
+    for i, (g, _) in enumerate(BATCH):
+        s = olap.normalized_adjacency(g.row_ptr, g.col_idx)
+        ri = r[OFFS[i]:OFFS[i + 1]].astype(np.float64)
+        ref = och.cheb_filter(s, ri, och.filter_coeffs(lam[i], m))
+        err = np.linalg.norm(y[OFFS[i]:OFFS[i + 1]] - ref)
+        assert err <= tol * np.linalg.norm(ref) + FLOOR[storage] * np.linalg.norm(ri), i

@@ -238,3 +238,83 @@ def test_graph_replay_matches_eager_launches():
     assert n1 == n2 >= m + 1  # copy-in + m orders (+ heavy-row launches, if any)
     ref = _oracle_filter(g, r.cpu().numpy().astype(np.float64), 0.9, m)
     assert rel(other.cpu().numpy(), ref) <= 1e-5  # new coefficients reach the replay
+
+
+# ----------------------------------------------------- Clenshaw evaluation
+
+@pytest.mark.parametrize("gi,d,d_pad,m,lam", CASES)
+@pytest.mark.parametrize("rcm", [False, True])
+@pytest.mark.parametrize("normalize", [False, True])
+def test_clenshaw_f32_matches_oracle(gi, d, d_pad, m, lam, rcm, normalize):
+    """Clenshaw's backward recurrence gives the oracle's forward-recurrence features."""
+    g = GRAPHS[gi][1]
+    r = ci.gaussian_block(g.n, d, d_pad, seed=11)
+    ref = _oracle_filter(g, r.astype(np.float64), lam, m, normalize=normalize)
+    flags = csc.CLENSHAW | (csc.NORMALIZE_ROWS if normalize else 0)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM if rcm else 0) as h:
+        y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, R_in=torch.from_numpy(r).cuda(),
+                                          flags=flags).cpu().numpy()
+    assert np.all(y[:, d:] == 0)
+    assert rel(y, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("n,d,d_pad,seed", [(1000, 28, 32, 0), (777, 47, 48, 123456789012), (5, 1, 8, 3)])
+@pytest.mark.parametrize("m", [1, 2, 30])
+def test_clenshaw_regenerated_signals_match_oracle(n, d, d_pad, seed, m):
+    """R regenerated from Philox in every order equals the oracle's draw of the block."""
+    g = ci.erdos_renyi(n, min(1.0, 8.0 / n), seed=1) if n > 5 else ci.path(n)
+    r_ref = och.random_signals(n, d, d_pad, seed)
+    ref = _oracle_filter(g, r_ref, 0.7, m, normalize=True)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM) as h:
+        y = csc.csc_filter_random_signals(h, 0.7, m, d, d_pad, seed=seed,
+                                          flags=csc.CLENSHAW | csc.NORMALIZE_ROWS).cpu().numpy()
+    assert rel(y, ref) <= 2e-5
+
+
+@pytest.mark.parametrize("G,NT", SHAPES)
+@pytest.mark.parametrize("threads", [256, 512])
+def test_clenshaw_every_compiled_shape(G, NT, threads):
+    """Each (lanes, vectors) pair and CTA size; rows normalised in the last order when one
+    tile holds a row, by the separate pass otherwise."""
+    g = GRAPHS[6][1]
+    d, d_pad, m, lam = 47, 48, 20, 0.43
+    tiles = -(-(d_pad // 4) // (G * NT))
+    r = ci.gaussian_block(g.n, d, d_pad, seed=3)
+    ref = _oracle_filter(g, r.astype(np.float64), lam, m, normalize=True)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM) as h:
+        csc.csc_graph_pin_shape(h, "clenshaw", 4, d_pad, G, NT, threads, 37, tiles, 0)
+        y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, R_in=torch.from_numpy(r).cuda(),
+                                          flags=csc.CLENSHAW | csc.NORMALIZE_ROWS).cpu().numpy()
+    assert rel(y, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("storage,tol", [(1, 5e-2), (2, 1e-12)])
+@pytest.mark.parametrize("G,NT", [(2, 3), (8, 1), (4, 2)])
+def test_clenshaw_bf16_f64(storage, tol, G, NT):
+    g = GRAPHS[6][1]
+    d, d_pad, m, lam = 28, 32, 15, 0.5
+    vec = 8 if storage == 1 else 2
+    tiles = -(-(d_pad // vec) // (G * NT))
+    r = ci.gaussian_block(g.n, d, d_pad, seed=4)
+    ref = _oracle_filter(g, r.astype(np.float64), lam, m)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        csc.csc_graph_pin_shape(h, "clenshaw", 2 if storage == 1 else 8, d_pad, G, NT, 256, 29, tiles, 0)
+        y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, storage=storage, R_in=torch.from_numpy(r).cuda(),
+                                          flags=csc.CLENSHAW).cpu().numpy()
+    assert rel(y, ref) <= tol
+
+
+def test_clenshaw_graph_replay_matches_eager():
+    g = GRAPHS[6][1]
+    d, d_pad, m, lam = 47, 48, 30, 0.43
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        csc.csc_profile_enable(True)
+        eager = csc.csc_filter_random_signals(h, lam, m, d, d_pad, seed=5,
+                                              flags=csc.CLENSHAW | csc.NORMALIZE_ROWS).clone()
+        csc.csc_profile_enable(False)
+        a = csc.csc_filter_random_signals(h, lam, m, d, d_pad, seed=5, flags=csc.CLENSHAW | csc.NORMALIZE_ROWS).clone()
+        b = csc.csc_filter_random_signals(h, lam, m, d, d_pad, seed=5, flags=csc.CLENSHAW | csc.NORMALIZE_ROWS).clone()
+        fwd = csc.csc_filter_random_signals(h, lam, m, d, d_pad, seed=5, flags=csc.NORMALIZE_ROWS).clone()
+    torch.cuda.synchronize()
+    assert torch.equal(eager, a) and torch.equal(a, b)
+    assert rel(a.cpu().numpy(), fwd.cpu().numpy()) <= 1e-5

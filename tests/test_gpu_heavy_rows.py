@@ -130,3 +130,18 @@ def test_interpolation_heavy(power, G, NT, threads):
     assert np.max(np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)) <= 3e-6
     assert rel(x, x_ref) <= 1e-3
     assert np.array_equal(labels.cpu().numpy(), ointerp.labels_from_indicators(x))
+
+
+@pytest.mark.parametrize("gname", ["hub", "power_law"])
+@pytest.mark.parametrize("normalize", [False, True])
+def test_clenshaw_heavy(gname, normalize):
+    g = HUB if gname == "hub" else POWER_LAW
+    d, d_pad, m, lam = 21, 24, 40, 0.3
+    r = ci.gaussian_block(g.n, d, d_pad, seed=9)
+    ref = _oracle_filter(g, r.astype(np.float64), lam, m)
+    if normalize:
+        ref = och.normalize_rows(ref)
+    flags = csc.CLENSHAW | (csc.NORMALIZE_ROWS if normalize else 0)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM) as h:
+        y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, R_in=torch.from_numpy(r).cuda(), flags=flags)
+    assert rel(y.cpu().numpy(), ref) <= 1e-5
