@@ -12,9 +12,13 @@ connected component holding no sample the right-hand side is zero and the
 solution there is zero.  Labels: node i goes to the j maximising
 x_j(i) / ||x_j|| (ties to the lowest j; a zero column scores 0).
 
-Pins (tests/test_oracle_interp.py): agreement with a dense LAPACK solve;
+Pins (tests/test_oracle_misc.py): agreement with a dense LAPACK solve;
 n = N with gamma -> 0 returns c^r; on disjoint regular cliques with every
 clique sampled the indicators lie in ker L, so x_j is the exact indicator.
+High-pass variant: agreement with the system built from LAPACK eigh
+(g~(L) = U (1 - h~(Lambda)) U^T); on disjoint cliques the indicators lie in the
+pass band (h~ = 1 up to the Jackson error at lambda = 0), so x_j is within that
+error of the indicator.
 """
 from __future__ import annotations
 
@@ -93,6 +97,42 @@ def interpolate(lap: sp.csr_matrix, omega: np.ndarray, sample_labels: np.ndarray
     pre = msk + gamma
     x, it, res = cg(lambda v: apply_system(lap, msk, gamma, power, v), b, pre, tol, max_iter)
     return x, it, res
+
+
+# --- the paper's high-pass choice: g = 1 - h~_{lambda_k} (Sec. 4.4 after Eq. 5) ---
+# g~(L) = I - h~(L), h~ the Jackson-Chebyshev low-pass of degree m at the cut-off
+# lambda_k (the filter of Alg. 2 step 4), applied with the forward recurrence.
+
+def apply_highpass(s_mat: sp.csr_matrix, msk: np.ndarray, gamma: float, lam: float, m: int,
+                   x: np.ndarray) -> np.ndarray:
+    """(M^T M + gamma (I - h~(L))) x, with h~(L) x by the oracle's Chebyshev filter."""
+    from . import chebyshev as och
+
+    xx = x if x.ndim == 2 else x[:, None]
+    hx = och.cheb_filter(s_mat, xx, och.filter_coeffs(lam, m))
+    out = msk[:, None] * xx + gamma * (xx - hx)
+    return out if x.ndim == 2 else out[:, 0]
+
+
+def interpolate_highpass(s_mat: sp.csr_matrix, omega: np.ndarray, sample_labels: np.ndarray, k: int,
+                         lam: float, m: int, gamma: float = 1e-3, tol: float = 1e-10, max_iter: int = 20000):
+    """Eq. 5 with g = 1 - h~_{lambda}: (X, iterations, max rel residual); s_mat = D^-1/2 W D^-1/2."""
+    n_nodes = s_mat.shape[0]
+    msk = mask(n_nodes, omega)
+    b = rhs(n_nodes, omega, sample_labels, k)
+    pre = msk + gamma
+    return cg(lambda v: apply_highpass(s_mat, msk, gamma, lam, m, v), b, pre, tol, max_iter)
+
+
+def interpolate_highpass_dense(lap_dense: np.ndarray, omega, sample_labels, k, lam, m, gamma=1e-3):
+    """The same system built from the eigendecomposition: g~(L) = U (1 - h~(Lambda)) U^T."""
+    from . import chebyshev as och
+
+    n_nodes = lap_dense.shape[0]
+    w, u = np.linalg.eigh(lap_dense)
+    g = u @ np.diag(1.0 - och.h_tilde(w, lam, m)) @ u.T
+    a = np.diag(mask(n_nodes, omega)) + gamma * g
+    return np.linalg.solve(a, rhs(n_nodes, omega, sample_labels, k))
 
 
 def interpolate_dense(lap_dense: np.ndarray, omega, sample_labels, k, gamma=1e-3, power=4):

@@ -109,6 +109,32 @@ def test_interp_disjoint_regular_cliques_exact():
     assert np.array_equal(interp.labels_from_indicators(x), g.labels)
 
 
+def test_interp_highpass_matches_eigendecomposition():
+    """g = 1 - h~ applied by the Chebyshev recurrence equals U (1 - h~(Lambda)) U^T."""
+    g = ci.sbm(200, 4, s=8, seed=1)
+    s_mat = laplacian.normalized_adjacency(g.row_ptr, g.col_idx)
+    lap = laplacian.laplacian(g.row_ptr, g.col_idx)
+    om = sampling.sample(200, 30, seed=2)
+    lab = g.labels[om]
+    x, it, res = interp.interpolate_highpass(s_mat, om, lab, 4, lam=0.3, m=30, gamma=1e-2, tol=1e-12)
+    ref = interp.interpolate_highpass_dense(lap.toarray(), om, lab, 4, 0.3, 30, 1e-2)
+    assert res < 1e-11
+    assert np.linalg.norm(x - ref) / np.linalg.norm(ref) < 1e-8
+
+
+def test_interp_highpass_cliques_near_exact():
+    """Indicators of disjoint cliques span the eigenvalue 0 where h~ = 1 up to the
+    Jackson error, so every clique sampled recovers them within gamma times that error."""
+    g = ci.disjoint_cliques(4, 7)
+    s_mat = laplacian.normalized_adjacency(g.row_ptr, g.col_idx)
+    om = np.array([0, 9, 15, 27])
+    lab = g.labels[om]
+    x, _, _ = interp.interpolate_highpass(s_mat, om, lab, 4, lam=0.5, m=50, gamma=1e-3, tol=1e-13)
+    truth = np.eye(4)[g.labels]
+    assert np.max(np.abs(x - truth)) < 1e-3
+    assert np.array_equal(interp.labels_from_indicators(x), g.labels)
+
+
 def test_label_rule_normalises_and_breaks_ties_low():
     x = np.array([[1.0, 2.0], [1.0, 0.0], [0.0, 0.0]])
     # column norms sqrt(2) and 2: row 0 -> 0.707 vs 1.0 -> 1; row 2 tie -> 0
