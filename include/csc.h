@@ -74,7 +74,8 @@ typedef int32_t csc_dtype;
 #define CSC_NORMALIZE_ROWS 1u  /* Alg. 2 step 4: divide every row by its l2 norm      */
 #define CSC_NO_JACKSON     2u  /* truncated Chebyshev (no Jackson damping)            */
 #define CSC_CLENSHAW       4u  /* evaluate the same polynomial by Clenshaw's backward
-                                  recurrence, R regenerated or re-read per order     */
+                                  recurrence, s R stored and re-read per order       */
+#define CSC_HIGHPASS       8u  /* csc_cluster: interpolate with g = 1 - h~ (Sec. 4.4)  */
 
 typedef struct csc_graph_s* csc_graph;
 
@@ -115,7 +116,8 @@ typedef struct {
     uint64_t seed;
     double   lambda_k;     /* > 0: skip step 1 and use this cut-off                   */
     const double* bracket; /* NULL or host {lo, hi}: learned bracket for step 1       */
-    uint32_t flags;        /* CSC_CLENSHAW: filter by Clenshaw's recurrence             */
+    uint32_t flags;        /* CSC_CLENSHAW: filter by Clenshaw's recurrence; CSC_HIGHPASS:
+                              interpolate with g = 1 - h~ at lambda_k, degree m          */
 } csc_params;
 
 /* Per-stage results and timings of csc_cluster. */
@@ -438,6 +440,18 @@ CSC_API csc_status csc_interpolate(csc_graph g, const int64_t* sample_idx, const
                            int64_t n, int32_t k, int32_t g_power, double gamma, double rel_tol,
                            int32_t max_iter, int32_t* labels_out, float* fuzzy_out,
                            csc_cg_info* info, void* stream);
+
+/* csc_interpolate_highpass -- Eq. 5 with the paper's preferred high-pass
+ * regulariser g = 1 - h~_{lambda_c} (the discussion after Eq. 5, Sec. 4.4): h~ the
+ * Jackson-Chebyshev low-pass of degree m at lambda_c (the filter of Alg. 2 step 4),
+ * so every CG iteration applies h~(L) to the k columns (m sparse products, Clenshaw
+ * form) and A p = mask p + gamma (p - h~(L) p).  Arguments as csc_interpolate,
+ * with lambda_c in [0, 2] and m >= 1 instead of g_power.  One graph per handle
+ * (a batched handle is rejected with CSC_E_UNSUPPORTED). */
+CSC_API csc_status csc_interpolate_highpass(csc_graph g, const int64_t* sample_idx, const int32_t* sample_labels,
+                                            int64_t n, int32_t k, double lambda_c, int32_t m, double gamma,
+                                            double rel_tol, int32_t max_iter, int32_t* labels_out,
+                                            float* fuzzy_out, csc_cg_info* info, void* stream);
 
 /* --------------------------------------------------------- whole pipeline */
 

@@ -19,7 +19,8 @@ from ._native import check, lib
 
 F32, BF16, F64 = nat.CSC_F32, nat.CSC_BF16, nat.CSC_F64
 RCM, CHECK_SYM, DEVICE_INPUT = nat.CSC_RCM, nat.CSC_CHECK_SYM, nat.CSC_DEVICE_INPUT
-NORMALIZE_ROWS, NO_JACKSON, CLENSHAW = nat.CSC_NORMALIZE_ROWS, nat.CSC_NO_JACKSON, nat.CSC_CLENSHAW
+NORMALIZE_ROWS, NO_JACKSON, CLENSHAW, HIGHPASS = (nat.CSC_NORMALIZE_ROWS, nat.CSC_NO_JACKSON, nat.CSC_CLENSHAW,
+                                                  nat.CSC_HIGHPASS)
 
 
 def _stream(stream) -> ctypes.c_void_p:
@@ -365,6 +366,22 @@ def csc_interpolate(g: Graph, sample_idx: torch.Tensor, sample_labels: torch.Ten
                                gamma, rel_tol, max_iter, _dptr(labels_out), _dptr(fz), ctypes.byref(info),
                                _stream(stream))
     check(st, "csc_interpolate", allow=(nat.CSC_E_NOT_CONVERGED,))
+    return labels_out, fz, CgInfo(info.iters, bool(info.converged), info.max_rel_residual)
+
+
+def csc_interpolate_highpass(g: Graph, sample_idx: torch.Tensor, sample_labels: torch.Tensor, k: int,
+                             lambda_c: float, m: int = 50, gamma: float = 1e-3, rel_tol: float = 1e-6,
+                             max_iter: int = 2000, labels_out: Optional[torch.Tensor] = None, fuzzy: bool = False,
+                             stream=None):
+    """Eq. 5 with g = 1 - h~_{lambda_c}: (labels, fuzzy or None, CgInfo)."""
+    if labels_out is None:
+        labels_out = torch.empty(g.N, dtype=torch.int32, device="cuda")
+    fz = torch.empty((g.N, k), dtype=torch.float32, device="cuda") if fuzzy else None
+    info = nat.csc_cg_info()
+    st = lib().csc_interpolate_highpass(g.handle, _dptr(sample_idx), _dptr(sample_labels), sample_idx.numel(), k,
+                                        lambda_c, m, gamma, rel_tol, max_iter, _dptr(labels_out), _dptr(fz),
+                                        ctypes.byref(info), _stream(stream))
+    check(st, "csc_interpolate_highpass", allow=(nat.CSC_E_NOT_CONVERGED,))
     return labels_out, fz, CgInfo(info.iters, bool(info.converged), info.max_rel_residual)
 
 

@@ -1213,6 +1213,25 @@ csc_status csc_interpolate(csc_graph g, const int64_t* sample_idx, const int32_t
     return poison_on_cuda(g, st);
 }
 
+csc_status csc_interpolate_highpass(csc_graph g, const int64_t* sample_idx, const int32_t* sample_labels, int64_t n,
+                                    int32_t k, double lambda_c, int32_t m, double gamma, double rel_tol,
+                                    int32_t max_iter, int32_t* labels_out, float* fuzzy_out, csc_cg_info* info,
+                                    void* stream) {
+    clear_error();
+    CSC_TRY(check_graph(g));
+    if (!sample_idx || !sample_labels || !labels_out || n < 1 || n > g->N || k < 1 || m < 1 ||
+        !(lambda_c >= 0.0 && lambda_c <= 2.0) || !(gamma > 0.0) || !(rel_tol > 0.0) || max_iter < 1) {
+        set_error("csc_interpolate_highpass: invalid arguments (n=%lld k=%d m=%d lambda_c=%g gamma=%g)", (long long)n,
+                  k, m, lambda_c, gamma);
+        return CSC_E_INVALID;
+    }
+    std::vector<double> c(m + 1);
+    cheb_coefficients(lambda_c, m, true, c.data());
+    csc_status st = run_interpolate(g, sample_idx, sample_labels, n, k, 1, gamma, rel_tol, max_iter, labels_out,
+                                    fuzzy_out, info, (cudaStream_t)stream, nullptr, c.data(), m);
+    return poison_on_cuda(g, st);
+}
+
 csc_status csc_cluster(csc_graph g, const csc_params* p, int32_t* labels_out, csc_cluster_info* info,
                        void* stream) {
     clear_error();
@@ -1298,7 +1317,13 @@ csc_status csc_cluster(csc_graph g, const csc_params* p, int32_t* labels_out, cs
     st = run_kmeans(Xr, n, d, d_pad, k, reps, km_iter, p->seed, slab, &local.inertia, g, s);
     if (st != CSC_OK) return done(st);
     cudaEventRecord(e4, s);
-    st = run_interpolate(g, idx, slab, n, k, g_power, gamma, cg_tol, cg_max, labels_out, nullptr, &local.cg, s);
+    std::vector<double> hpc;
+    if (p->flags & CSC_HIGHPASS) {
+        hpc.resize(m + 1);
+        cheb_coefficients(lam, m, true, hpc.data());
+    }
+    st = run_interpolate(g, idx, slab, n, k, g_power, gamma, cg_tol, cg_max, labels_out, nullptr, &local.cg, s,
+                         nullptr, hpc.empty() ? nullptr : hpc.data(), m);
     if (st != CSC_OK && st != CSC_E_NOT_CONVERGED) return done(st);
     cudaEventRecord(e5, s);
     cudaError_t ce = cudaEventSynchronize(e5);

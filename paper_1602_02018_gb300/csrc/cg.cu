@@ -222,6 +222,37 @@ lap_ax_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ 
     block_column_partials<G, NT, 1>(dot, lane, col0, tcols, ld, partials, slot_base + blockIdx.x, nslots);
 }
 
+// High-pass form of A p (g = 1 - h~): Ap = mask p + gamma (p - h~(L) p), with
+// hp = h~(L) p computed by the Clenshaw operator; partials of <p, Ap> in slots
+// [0, gridDim.x).
+template <int G, int NT>
+__global__ void __launch_bounds__(kCgMaxThreads)
+hp_ax_kernel(const float* __restrict__ p, const float* __restrict__ hp, const float* __restrict__ mask, float gamma,
+             float* __restrict__ Ap, const int32_t* __restrict__ part, int ncols, int64_t ld,
+             double* __restrict__ partials, CgBatch bt) {
+    CG_TILE(G, NT)
+    KSum dot[1][NT][4];
+    CG_ROWS(G) {
+        const float mk = mask[row];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int cl = (t * G + lane) * 4;
+            if (cl >= tcols) continue;
+            const int64_t o = (int64_t)row * ld + col0 + cl;
+            float x[4], h[4], a[4];
+            StoreTraits<float>::load(p + o, x);
+            StoreTraits<float>::load(hp + o, h);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                a[v] = mk * x[v] + gamma * (x[v] - h[v]);
+                dot[0][t][v].add(x[v] * a[v]);
+            }
+            StoreTraits<float>::store(Ap + o, a);
+        }
+    }
+    block_column_partials<G, NT, 1>(dot, lane, col0, tcols, ld, partials, blockIdx.x, gridDim.x);
+}
+
 // x += alpha p; r -= alpha Ap; partials of <r, r/P> and <r, r>.  alpha == nullptr: no update.
 template <int G, int NT>
 __global__ void __launch_bounds__(kCgMaxThreads)
@@ -561,10 +592,16 @@ static csc_status cg_occupancy(const LaunchCfg& c, int* out) {
 
 csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* sample_labels, int64_t n, int k,
                            int g_power, double gamma, double rel_tol, int max_iter, int32_t* labels_out,
-                           float* fuzzy_out, csc_cg_info* info, cudaStream_t s, const int32_t* k_graphs) {
+                           float* fuzzy_out, csc_cg_info* info, cudaStream_t s, const int32_t* k_graphs,
+                           const double* hp_coef, int hp_m) {
     const int32_t N = (int32_t)g->N;
     // one independent set of k systems per graph of a batch (k_graphs: each graph's k)
     const int nseg = (k_graphs && g->n_graphs > 1) ? g->n_graphs : 1;
+    const bool hp = hp_coef != nullptr;  // g = 1 - h~ instead of L^p
+    if (hp && nseg > 1) {
+        set_error("the high-pass interpolation runs on one graph at a time");
+        return CSC_E_UNSUPPORTED;
+    }
     const int ld = ((k + 3) / 4) * 4;
     const int nv = ld / 4;
     // candidate shapes: column tiles of 4*G*NT floats with at most a third idle
@@ -737,8 +774,10 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const dim3 grid(cfg.P, cfg.tiles);
     const int th = cfg.threads;
     const int P = cfg.P;
-    const int H = (int)g->n_heavy;
+    const int H = hp ? 0 : (int)g->n_heavy;  // the high-pass A p has no heavy-row slots
     const int PH = P + H;  // <p, A p> partial slots
+    PolyOp op;
+    if (hp) CSC_TRY(poly_prepare(g, hp_coef, hp_m, ld, &op, s));
     const dim3 hgrid(H > 0 ? H : 1, cfg.tiles);
     Segs sg;
     sg.P = P;
@@ -779,6 +818,13 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         return CSC_E_INVALID;
     }
     auto apply_A = [&](const float* in, const CgBatch& bb, cudaStream_t s) -> csc_status {
+        if (hp) {
+            CSC_TRY(poly_apply(g, op, in, t1, s));
+            CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", 4.0 * N + 3 * blkb + scal_b, s,
+                                       hp_ax_kernel<G_, NT_><<<grid, th, 0, s>>>(in, t1, mask, (float)gamma, Ap, rpart,
+                                                                                 ld, ld, part, bb)));
+            return CSC_OK;
+        }
         // t = L^(p-1) in, then Ap = mask*in + gamma * L t with <in, Ap> partials
         const float* cur = in;
         float* bufs[2] = {t1, t2};
@@ -861,9 +907,9 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         const int batch = std::min(check_every, max_iter - it);
         if (!g_prof_enabled && g->use_graphs) {
             char key[320];
-            snprintf(key, sizeof(key), "cg:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%.17g:%.17g:%p:%p:%p:%p:%p", batch, ld, k,
-                     nseg, g_power, cfg.G, cfg.NT, cfg.threads, cfg.P, cfg.tiles, gamma, rel_tol, (void*)x, (void*)sd,
-                     (void*)part, (void*)d_gk, (const void*)sg.gblk);
+            snprintf(key, sizeof(key), "cg:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%.17g:%.17g:%p:%p:%p:%p:%p:%p", batch, ld,
+                     k, nseg, g_power, hp ? hp_m : -1, cfg.G, cfg.NT, cfg.threads, cfg.P, cfg.tiles, gamma, rel_tol,
+                     (void*)x, (void*)sd, (void*)part, (void*)d_gk, (const void*)sg.gblk, (const void*)op.coef);
             int64_t launches = 0;
             CSC_TRY(replay_graph(g, key, s, &launches, [&](cudaStream_t cap) { return iterations(cap, batch); }));
         } else {

@@ -218,6 +218,16 @@ csc_status get_windows(Graph* g, int P, int W, const int32_t** out);
 csc_status launch_degrees(Graph* g, cudaStream_t s);
 
 // spmm.cu: the Jackson-Chebyshev filter (K3 + K1 + K5)
+// h~(L) = sum_j c_j T_j(L - I) on an fp32 block in internal row order (Clenshaw form).
+struct PolyOp {
+    LaunchCfg cfg;
+    const float* coef = nullptr;
+    int m = 0, ld = 0;
+    float *b0 = nullptr, *b1 = nullptr, *rs = nullptr;
+};
+csc_status poly_prepare(Graph* g, const double* c, int m, int ld, PolyOp* op, cudaStream_t s);
+csc_status poly_apply(Graph* g, const PolyOp& op, const float* X, float* Y, cudaStream_t s);
+
 // Batched handle: c_graphs is host double[n_graphs x (m + 1)], graph i's coefficients.
 csc_status run_filter_batched(Graph* g, const double* c_graphs, int m, int d, int d_pad, uint64_t seed,
                               csc_dtype storage, const float* R_in, void* Y_out, bool normalize, cudaStream_t s,
@@ -264,11 +274,12 @@ csc_status run_kmeans(const float* X, int64_t n, int d, int ld, int k, int repli
                       cudaStream_t s);
 
 // cg.cu (K8 + K9).  k_graphs: NULL, or (batched handle) host int32[n_graphs], each
-// graph's k (k = their maximum): one set of systems per graph.
+// graph's k (k = their maximum): one set of systems per graph.  hp_coef: NULL for
+// g(L) = L^g_power, or host double[hp_m + 1], the coefficients of h~ for g = 1 - h~.
 csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* sample_labels,
                            int64_t n, int k, int g_power, double gamma, double rel_tol, int max_iter,
                            int32_t* labels_out, float* fuzzy_out, csc_cg_info* info, cudaStream_t s,
-                           const int32_t* k_graphs = nullptr);
+                           const int32_t* k_graphs = nullptr, const double* hp_coef = nullptr, int hp_m = 0);
 
 // host math (api.cu)
 void cheb_coefficients(double lambda_c, int m, bool jackson, double* c);

@@ -810,7 +810,9 @@ static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur
 template <typename T>
 static csc_status launch_clenshaw_step(Graph* g, const LaunchCfg& cfg, const T* bnext, T* bpp,
                                        typename StoreTraits<T>::acc_t* Y, int ncols, int64_t ld, double cj, int mode,
-                                       const T* rs, cudaStream_t s, CoefTab<typename StoreTraits<T>::acc_t> tab = {}) {
+                                       const T* rs, cudaStream_t s, CoefTab<typename StoreTraits<T>::acc_t> tab = {},
+                                       bool internal = false) {
+    const int32_t* perm = internal ? nullptr : g->perm;  // internal: Y rows in internal order
     using A = typename StoreTraits<T>::acc_t;
     const A *idg, *sqd;
     if constexpr (sizeof(A) == 8) {
@@ -838,18 +840,18 @@ static csc_status launch_clenshaw_step(Graph* g, const LaunchCfg& cfg, const T* 
         const dim3 hgrid(g->n_heavy, cfg.tiles);
         CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * heavy_frac, s,
                                           clenshaw_step_heavy_kernel<T, GG, NN><<<hgrid, kHeavyThreads, 0, s>>>(
-                                              g->row_ptr, g->col_idx, idg, sqd, bnext, bpp, Y, g->perm, g->heavy,
+                                              g->row_ptr, g->col_idx, idg, sqd, bnext, bpp, Y, perm, g->heavy,
                                               ncols, ld, (A)cj, mode, tab, rs)));
     }
     if (last) {
         CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * (1.0 - heavy_frac), s,
                                           clenshaw_step_kernel<T, GG, NN, true><<<grid, cfg.threads, 0, s>>>(
-                                              g->row_ptr, g->col_idx, idg, sqd, bnext, bpp, Y, g->perm, part, ncols,
+                                              g->row_ptr, g->col_idx, idg, sqd, bnext, bpp, Y, perm, part, ncols,
                                               ld, (A)cj, mode, tab, rs)));
     } else {
         CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * (1.0 - heavy_frac), s,
                                           clenshaw_step_kernel<T, GG, NN, false><<<grid, cfg.threads, 0, s>>>(
-                                              g->row_ptr, g->col_idx, idg, sqd, bnext, bpp, Y, g->perm, part, ncols,
+                                              g->row_ptr, g->col_idx, idg, sqd, bnext, bpp, Y, perm, part, ncols,
                                               ld, (A)cj, mode, tab, rs)));
     }
     return CSC_OK;
@@ -1220,6 +1222,69 @@ csc_status run_filter_batched(Graph* g, const double* c_graphs, int m, int d, in
             set_error("unknown storage type %d", (int)storage);
             return CSC_E_INVALID;
     }
+}
+
+// ---------------------------------------------- h~(L) on a block in internal order
+// Used by the interpolation with g = 1 - h~: Y = sum_j c_j T_j(L - I) X for an fp32
+// block X already in internal row order (stride ld, all ld columns), Y likewise, by
+// the Clenshaw form.  poly_prepare uploads the coefficients and settles the launch
+// shape (it may synchronize); poly_apply only launches, so it can be captured.
+csc_status poly_prepare(Graph* g, const double* c, int m, int ld, PolyOp* op, cudaStream_t s) {
+    if (m < 1 || ld % 4) {
+        set_error("polynomial operator: need m >= 1 and ld a multiple of 4");
+        return CSC_E_INVALID;
+    }
+    const size_t bytes = (size_t)g->N * ld * sizeof(float);
+    void *a = nullptr, *b = nullptr, *r = nullptr, *dc = nullptr;
+    CSC_TRY(ws_get(g, WS_XA, bytes, &a));
+    CSC_TRY(ws_get(g, WS_XB, bytes, &b));
+    CSC_TRY(ws_get(g, WS_XR, bytes, &r));
+    CSC_TRY(ws_get(g, WS_COEF1, (m + 1) * sizeof(float), &dc));
+    std::vector<float> hc(m + 1);
+    for (int j = 0; j <= m; ++j) hc[j] = (float)c[j];
+    CSC_CUDA_TRY(cudaMemcpyAsync(dc, hc.data(), (m + 1) * sizeof(float), cudaMemcpyHostToDevice, s));
+    CSC_CUDA_TRY(cudaStreamSynchronize(s));
+    op->b0 = (float*)a;
+    op->b1 = (float*)b;
+    op->rs = (float*)r;
+    op->coef = (const float*)dc;
+    op->m = m;
+    op->ld = ld;
+    // launch shape: the Clenshaw order's tuned shape for this column count
+    CSC_TRY(autotune(g, tune_key(KK_CLEN, (int)sizeof(float), ld), candidates<float>(g, KK_CLEN, ld / 4), s,
+                     [&](const LaunchCfg& cf) {
+                         return launch_clenshaw_step<float>(g, cf, op->b0, op->b1, nullptr, ld, ld, 0.0, 1, op->rs, s,
+                                                            {}, true);
+                     },
+                     &op->cfg));
+    const int32_t* pr = nullptr;
+    return get_partition(g, op->cfg.P, &pr);
+}
+
+csc_status poly_apply(Graph* g, const PolyOp& op, const float* X, float* Y, cudaStream_t s) {
+    const int64_t N = g->N;
+    const int ld = op.ld, m = op.m;
+    const int64_t tot = N * ld;
+    CoefTab<float> tab;
+    tab.c = op.coef;
+    CoefTab<float> ft = tab;
+    ft.j = m;
+    // s X and B_m = c_m s X (internal order: no permutation)
+    CSC_KLAUNCH("copy_in", (double)tot * 8, s,
+                copy_in_kernel<float><<<ceil_div(tot, 256), 256, 0, s>>>(op.rs, X, (int32_t)N, ld, ld, ld, nullptr,
+                                                                        g->dinv, CoefTab<float>()));
+    CSC_KLAUNCH("copy_in", (double)tot * 8, s,
+                copy_in_kernel<float><<<ceil_div(tot, 256), 256, 0, s>>>(op.b0, X, (int32_t)N, ld, ld, ld, nullptr,
+                                                                        g->dinv, ft));
+    float* B[2] = {op.b0, op.b1};
+    for (int j = m - 1; j >= 1; --j) {
+        tab.j = j;
+        CSC_TRY(launch_clenshaw_step<float>(g, op.cfg, B[(m - j - 1) & 1], B[(m - j) & 1], Y, ld, ld, 0.0,
+                                            j == m - 1 ? 1 : 0, op.rs, s, tab, true));
+    }
+    tab.j = 0;
+    return launch_clenshaw_step<float>(g, op.cfg, B[(m - 1) & 1], B[m & 1], Y, ld, ld, 0.0, 2 | (m == 1 ? 1 : 0),
+                                       op.rs, s, tab, true);
 }
 
 csc_status run_filter(Graph* g, const double* coeffs, int m, int d, int d_pad, uint64_t seed,

@@ -145,3 +145,20 @@ def test_clenshaw_heavy(gname, normalize):
     with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM) as h:
         y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, R_in=torch.from_numpy(r).cuda(), flags=flags)
     assert rel(y.cpu().numpy(), ref) <= 1e-5
+
+
+def test_interpolation_highpass_heavy():
+    g = HUB
+    k = 10
+    om = osamp.sample(g.n, 300, 7)
+    lab = g.labels[om].astype(np.int32)
+    s = olap.normalized_adjacency(g.row_ptr, g.col_idx)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        labels, fz, info = csc.csc_interpolate_highpass(h, torch.from_numpy(om).cuda(), torch.from_numpy(lab).cuda(),
+                                                        k, 0.35, 40, 1e-3, 1e-7, 5000, fuzzy=True)
+    assert info.converged
+    x = fz.cpu().numpy().astype(np.float64)
+    b = ointerp.rhs(g.n, om, lab, k)
+    res = ointerp.apply_highpass(s, ointerp.mask(g.n, om), 1e-3, 0.35, 40, x) - b
+    assert np.max(np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)) <= 3e-6
+    assert np.array_equal(labels.cpu().numpy(), ointerp.labels_from_indicators(x))

@@ -225,3 +225,74 @@ def test_interpolation_graph_replay_matches_eager():
         l2, f2, i2 = csc.csc_interpolate(h, omd, lab, 20, fuzzy=True)
     assert i0.iters == i1.iters == i2.iters
     assert torch.equal(f0, f1) and torch.equal(f1, f2) and torch.equal(l0, l2)
+
+
+# ------------------------------------------- interpolation with g = 1 - h~
+
+def _check_highpass(g, om, lab, k, lam, m, gamma, fz, dense=True):
+    s = olap.normalized_adjacency(g.row_ptr, g.col_idx)
+    msk = ointerp.mask(g.n, om)
+    b = ointerp.rhs(g.n, om, lab, k)
+    x = fz.astype(np.float64)
+    res = ointerp.apply_highpass(s, msk, gamma, lam, m, x) - b
+    rres = np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)
+    assert np.max(rres) <= 3e-6
+    x_ref, _, _ = ointerp.interpolate_highpass(s, om, lab, k, lam, m, gamma, tol=1e-11)
+    if dense:
+        lap = olap.laplacian(g.row_ptr, g.col_idx).toarray()
+        w, u = np.linalg.eigh(lap)
+        a = np.diag(msk) + gamma * (u @ np.diag(1.0 - och.h_tilde(w, lam, m)) @ u.T)
+        kappa = np.linalg.cond(a)
+        err = np.linalg.norm(x - x_ref, axis=0) / np.linalg.norm(x_ref, axis=0)
+        assert np.all(err <= kappa * rres * (1 + 1e-6) + 1e-9)
+    return x_ref
+
+
+@pytest.mark.parametrize("n_nodes,k,n_s,lam,m,rcm", [(1000, 20, 120, 0.44, 50, False), (1000, 20, 120, 0.44, 50, True),
+                                                     (600, 6, 40, 0.3, 20, False)])
+def test_interpolation_highpass_matches_oracle(n_nodes, k, n_s, lam, m, rcm):
+    g = ci.sbm(n_nodes, k, seed=2)
+    om = osamp.sample(g.n, n_s, 2)
+    lab = g.labels[om].astype(np.int32)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM if rcm else 0) as h:
+        labels, fz, info = csc.csc_interpolate_highpass(h, torch.from_numpy(om).cuda(), torch.from_numpy(lab).cuda(),
+                                                        k, lam, m, 1e-3, 1e-7, 5000, fuzzy=True)
+    assert info.converged and info.max_rel_residual <= 1e-6
+    x = fz.cpu().numpy()
+    x_ref = _check_highpass(g, om, lab, k, lam, m, 1e-3, x)
+    assert np.array_equal(labels.cpu().numpy(), ointerp.labels_from_indicators(x))
+    assert oari.ari(labels.cpu().numpy(), ointerp.labels_from_indicators(x_ref)) >= 0.999
+
+
+def test_interpolation_highpass_cliques():
+    g = ci.disjoint_cliques(4, 7)
+    om = np.array([0, 9, 15, 27], dtype=np.int64)
+    lab = g.labels[om].astype(np.int32)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        labels, fz, info = csc.csc_interpolate_highpass(h, torch.from_numpy(om).cuda(), torch.from_numpy(lab).cuda(),
+                                                        4, 0.5, 50, fuzzy=True)
+    assert np.array_equal(labels.cpu().numpy(), g.labels)
+    assert np.max(np.abs(fz.cpu().numpy() - np.eye(4)[g.labels])) < 2e-3
+
+
+def test_interpolation_highpass_graph_replay_matches_eager():
+    g = ci.sbm(1000, 20, seed=2)
+    om = torch.from_numpy(osamp.sample(g.n, 120, 2)).cuda()
+    lab = torch.from_numpy(g.labels[om.cpu().numpy()].astype(np.int32)).cuda()
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        csc.csc_profile_enable(True)
+        l0, f0, i0 = csc.csc_interpolate_highpass(h, om, lab, 20, 0.44, 50, fuzzy=True)
+        csc.csc_profile_enable(False)
+        l1, f1, i1 = csc.csc_interpolate_highpass(h, om, lab, 20, 0.44, 50, fuzzy=True)
+    assert i0.iters == i1.iters and torch.equal(f0, f1) and torch.equal(l0, l1)
+
+
+def test_cluster_highpass_recovers_communities():
+    """Alg. 2 end to end with g = 1 - h~: ARI against the planted partition, beside L^4."""
+    g = ci.sbm(2000, 20, seed=4)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        l4, i4 = csc.csc_cluster(h, 20, seed=1)
+        lh, ih = csc.csc_cluster(h, 20, seed=1, flags=csc.HIGHPASS)
+    a4 = oari.ari(l4.cpu().numpy(), g.labels)
+    ah = oari.ari(lh.cpu().numpy(), g.labels)
+    assert ih.cg.converged and ah >= 0.8 and ah >= a4 - 0.05
