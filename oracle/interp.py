@@ -15,6 +15,11 @@ x_j(i) / ||x_j|| (ties to the lowest j; a zero column scores 0).
 Pins (tests/test_oracle_misc.py): agreement with a dense LAPACK solve;
 n = N with gamma -> 0 returns c^r; on disjoint regular cliques with every
 clique sampled the indicators lie in ker L, so x_j is the exact indicator.
+Weighted decoder (variable-density draws, see the comment above
+interpolate_weighted; tests/test_oracle_sampling.py): unit weights on distinct
+draws reproduce Eq. 5; a node drawn twice equals one draw of twice the
+weight; the solution is a stationary point of the objective written term by
+term over the draws (finite differences) and beats random perturbations.
 High-pass variant: agreement with the system built from LAPACK eigh
 (g~(L) = U (1 - h~(Lambda)) U^T); on disjoint cliques the indicators lie in the
 pass band (h~ = 1 up to the Jackson error at lambda = 0), so x_j is within that
@@ -139,6 +144,51 @@ def interpolate_dense(lap_dense: np.ndarray, omega, sample_labels, k, gamma=1e-3
     n_nodes = lap_dense.shape[0]
     a = np.diag(mask(n_nodes, omega)) + gamma * np.linalg.matrix_power(lap_dense, power)
     return np.linalg.solve(a, rhs(n_nodes, omega, sample_labels, k))
+
+
+# --- weighted decoder for variable-density samples -----------------------------
+# The sampling theory the paper cites for variable density (Sec. 3.2.3 after
+# Theorem 3.4) decodes with the fidelity term weighted by P^{-1/2}:
+#   x_j = argmin_x sum_t w_t (x(omega_t) - c_j(t))^2 + gamma x^T g(L) x,
+# the sum over draws t (a node drawn twice counts twice), w_t = 1 / (N p_t).
+# Normal equations: (M^T W M + gamma g(L)) x = M^T W c_j; M^T W M is diagonal
+# with the summed weights of each node's draws.  Unit weights and distinct
+# draws give Eq. 5 exactly.
+
+def weighted_mask(n_nodes: int, omega: np.ndarray, w: np.ndarray) -> np.ndarray:
+    m = np.zeros(n_nodes)
+    np.add.at(m, np.asarray(omega, dtype=np.int64), np.asarray(w, dtype=np.float64))
+    return m
+
+
+def weighted_rhs(n_nodes: int, omega: np.ndarray, sample_labels: np.ndarray, w: np.ndarray, k: int) -> np.ndarray:
+    b = np.zeros((n_nodes, k))
+    np.add.at(b, (np.asarray(omega, dtype=np.int64), np.asarray(sample_labels, dtype=np.int64)),
+              np.asarray(w, dtype=np.float64))
+    return b
+
+
+def interpolate_weighted(lap: sp.csr_matrix, omega: np.ndarray, sample_labels: np.ndarray, w: np.ndarray, k: int,
+                         gamma: float = 1e-3, power: int = 4, tol: float = 1e-10, max_iter: int = 20000):
+    """Weighted Eq. 5 for every cluster; returns (X, iterations, max rel residual)."""
+    n_nodes = lap.shape[0]
+    msk = weighted_mask(n_nodes, omega, w)
+    b = weighted_rhs(n_nodes, omega, sample_labels, w, k)
+    return cg(lambda v: apply_system(lap, msk, gamma, power, v), b, msk + gamma, tol, max_iter)
+
+
+def weighted_objective(lap_dense: np.ndarray, omega, sample_labels, w, gamma: float, power: int,
+                       x: np.ndarray) -> np.ndarray:
+    """The weighted objective of every column of x, term by term over the draws (small cases)."""
+    k = x.shape[1]
+    g = np.linalg.matrix_power(lap_dense, power)
+    out = np.zeros(k)
+    for j in range(k):
+        for t in range(len(omega)):
+            target = 1.0 if sample_labels[t] == j else 0.0
+            out[j] += float(w[t]) * (x[omega[t], j] - target) ** 2
+        out[j] += gamma * x[:, j] @ g @ x[:, j]
+    return out
 
 
 def labels_from_indicators(x: np.ndarray) -> np.ndarray:

@@ -5,9 +5,12 @@ Steps, in the paper's order, each delegated to the module that follows it:
 2. Jackson-Chebyshev coefficients of h_{lambda_k} (chebyshev, Sec. 4.3);
 3. R: d signals N(0, 1/d) (rng, shared Philox convention);
 4. Y = h~(L) R, rows normalised (chebyshev, Alg. 2 step 4);
-5. Omega: n nodes uniformly without replacement (sampling, Eq. 4);
+5. Omega: n nodes uniformly without replacement (sampling, Eq. 4), or n
+   variable-density draws with scores ||Y_i||^2 of the unnormalised block
+   (sampling, Sec. 3.2.3 and the remark closing Sec. 4.2);
 6. k-means on the n sampled feature rows (kmeans);
-7. interpolation by Eq. 5 and the argmax rule (interp, Sec. 4.1).
+7. interpolation by Eq. 5 (weighted by the draws' 1 / (N p) under variable
+   density) and the argmax rule (interp, Sec. 4.1).
 
 Parity unpinned as a whole: the paper prints no recovery value (its
 figures are absent), so end-to-end results are checked against the SBM
@@ -34,7 +37,8 @@ def defaults(n_nodes: int, k: int) -> dict:
 def csc(row_ptr, col_idx, k: int, seed: int = 0, m: int = 50, d: int | None = None,
         n: int | None = None, n_v: int | None = None, gamma: float = 1e-3, g_power: int = 4,
         replicates: int = 20, max_iter_km: int = 100, cg_tol: float = 1e-10,
-        lambda_k: float | None = None, r_in: np.ndarray | None = None, timings: dict | None = None):
+        lambda_k: float | None = None, r_in: np.ndarray | None = None, timings: dict | None = None,
+        variable_density: bool = False):
     """Run Alg. 2 and return a dict with every intermediate result."""
     t0 = time.perf_counter()
     n_nodes = len(row_ptr) - 1
@@ -59,17 +63,23 @@ def csc(row_ptr, col_idx, k: int, seed: int = 0, m: int = 50, d: int | None = No
     feats = chebyshev.normalize_rows(y)
     tt["filter"] = time.perf_counter() - t
     t = time.perf_counter()
-    omega = sampling.sample(n_nodes, n, seed)
+    if variable_density:
+        omega, w = sampling.sample_variable_density(sampling.coherence_scores(y), n, seed)
+    else:
+        omega, w = sampling.sample(n_nodes, n, seed), None
     lab_r, _, inertia, _ = kmeans.kmeans(feats[omega], k, replicates, max_iter_km, seed)
     tt["kmeans"] = time.perf_counter() - t
     t = time.perf_counter()
-    x, cg_it, cg_res = interp.interpolate(lap, omega, lab_r, k, gamma, g_power, cg_tol)
+    if w is None:
+        x, cg_it, cg_res = interp.interpolate(lap, omega, lab_r, k, gamma, g_power, cg_tol)
+    else:
+        x, cg_it, cg_res = interp.interpolate_weighted(lap, omega, lab_r, w, k, gamma, g_power, cg_tol)
     labels = interp.labels_from_indicators(x)
     tt["interp"] = time.perf_counter() - t
     tt["total"] = time.perf_counter() - t0
     if timings is not None:
         timings.update(tt)
-    return dict(lam=lam, est=est, coeffs=coeffs, r=r, y=y, features=feats, omega=omega,
+    return dict(lam=lam, est=est, coeffs=coeffs, r=r, y=y, features=feats, omega=omega, weights=w,
                 sample_labels=lab_r, inertia=inertia, x=x, cg_iters=cg_it, cg_res=cg_res,
                 labels=labels, params=dict(k=k, m=m, d=d, n=n, n_v=n_v, gamma=gamma,
                                            g_power=g_power, seed=seed))
