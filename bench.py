@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f64"])
     ap.add_argument("--interp", default="l4", choices=["l4", "highpass"],
                     help="interpolation regulariser: g(L) = L^4 (default) or the paper's g = 1 - h~ at lambda_k")
+    ap.add_argument("--sampling", default="uniform", choices=["uniform", "variable"],
+                    help="uniform sampling of Eq. 4 (default) or variable-density draws with the weighted decoder")
     ap.add_argument("--filter", default="clenshaw", choices=["forward", "clenshaw"],
                     help="evaluate the Chebyshev filter by Clenshaw's backward recurrence (default, same Y "
                          "with fewer bytes per order) or by the forward three-term recurrence")
@@ -275,7 +277,8 @@ def run_ours(args, w, rank, world, local_rank):
     h = csc.csc_graph_create(g.row_ptr, g.col_idx, flags)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
-    fflags = (csc.CLENSHAW if args.filter == "clenshaw" else 0) | (csc.HIGHPASS if args.interp == "highpass" else 0)
+    fflags = ((csc.CLENSHAW if args.filter == "clenshaw" else 0) | (csc.HIGHPASS if args.interp == "highpass" else 0)
+              | (csc.VARDENSITY if args.sampling == "variable" else 0))
 
     def step():
         return csc.csc_cluster(h, k, m=m, d=d, d_pad=d_pad, n=n, storage=storage, seed=args.seed + rank,
@@ -397,7 +400,7 @@ def run_ours(args, w, rank, world, local_rank):
                        "l2": "flushed between steps (512 MB write)",
                        "value_basis": "m*nnz*d / device time of the filter stage of each timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "filter": args.filter, "interp": args.interp},
+                       "filter": args.filter, "interp": args.interp, "sampling": args.sampling},
             "csc_seconds": ms_step / 1e3,
             "filter_ms": ms_filter,
             "stages_ms": {kk: statistics.mean(x.ms[kk] for x in infos) for kk in infos[0].ms},

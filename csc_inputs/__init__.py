@@ -23,5 +23,5 @@ from .graphs import (  # noqa: F401
     erdos_renyi,
     block_diagonal,
 )
-from .signals import gaussian_block, workload_sizes  # noqa: F401
+from .signals import gaussian_block, score_profile, workload_sizes  # noqa: F401
 from .datasets import bracket_graph, batched_sbm_set  # noqa: F401

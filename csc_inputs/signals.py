@@ -6,6 +6,10 @@ step 3 uses sigma^2 = 1/d) with numpy's PCG64, laid out row-major with
 to the CUDA path and to the oracle, so a filter comparison isolates filter
 error from generator error.
 
+``score_profile`` draws a seeded vector of non-negative sampling scores (the
+input of variable-density sampling) with one of a few shapes: heavy-tailed,
+with runs of zeros, flat, a single positive entry, per-community constants.
+
 ``workload_sizes`` lists the parameter values of the five workloads (the
 defaults of Alg. 2 with natural logarithms and ceilings).
 """
@@ -28,6 +32,34 @@ def gaussian_block(n: int, d: int, d_pad: int | None = None, seed: int = 0,
     if d:
         out[:, :d] = rng.standard_normal((n, d)) * sigma
     return out.astype(dtype)
+
+
+def score_profile(n: int, kind: str = "heavy", seed: int = 0) -> np.ndarray:
+    """float64[n] of scores >= 0 with at least one positive entry."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if kind == "heavy":      # lognormal spread over ~8 decades
+        out = np.exp(rng.normal(0.0, 4.0, n))
+    elif kind == "zeros":    # about half exactly zero, the rest exponential
+        out = rng.exponential(1.0, n) * (rng.random(n) < 0.5)
+        out[rng.integers(0, n)] = 1.0
+    elif kind == "flat":
+        out = np.full(n, 0.37)
+    elif kind == "single":
+        out = np.zeros(n)
+        out[rng.integers(0, n)] = 2.5
+    elif kind == "blocks":   # constant within contiguous blocks of random sizes, 1 / size
+        out = np.empty(n)
+        i = 0
+        while i < n:
+            b = int(rng.integers(1, max(2, n // 8) + 1))
+            out[i:i + b] = 1.0 / b
+            i += b
+    elif kind == "tiny":     # subnormal and normal values side by side
+        out = rng.random(n) * 1e-300
+        out[rng.integers(0, n)] = 5e-324
+    else:
+        raise ValueError(f"unknown score profile {kind!r}")
+    return out.astype(np.float64)
 
 
 def pad8(x: int) -> int:

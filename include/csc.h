@@ -76,6 +76,8 @@ typedef int32_t csc_dtype;
 #define CSC_CLENSHAW       4u  /* evaluate the same polynomial by Clenshaw's backward
                                   recurrence, s R stored and re-read per order       */
 #define CSC_HIGHPASS       8u  /* csc_cluster: interpolate with g = 1 - h~ (Sec. 4.4)  */
+#define CSC_VARDENSITY    16u  /* csc_cluster: variable-density draws (scores ||Y_i||^2)
+                                  and the weighted decoder (Sec. 3.2.3, Theorem 3.4)  */
 
 typedef struct csc_graph_s* csc_graph;
 
@@ -117,7 +119,9 @@ typedef struct {
     double   lambda_k;     /* > 0: skip step 1 and use this cut-off                   */
     const double* bracket; /* NULL or host {lo, hi}: learned bracket for step 1       */
     uint32_t flags;        /* CSC_CLENSHAW: filter by Clenshaw's recurrence; CSC_HIGHPASS:
-                              interpolate with g = 1 - h~ at lambda_k, degree m          */
+                              interpolate with g = 1 - h~ at lambda_k, degree m;
+                              CSC_VARDENSITY: csc_coherence_scores, csc_sample_weighted
+                              and the weighted decoder in place of uniform sampling     */
 } csc_params;
 
 /* Per-stage results and timings of csc_cluster. */
@@ -402,6 +406,38 @@ CSC_API csc_status csc_sample(int64_t N, int64_t n, uint64_t seed, int64_t* idx_
  * using the same device) race and give wrong results. */
 CSC_API csc_status csc_sample_noalloc(int64_t N, int64_t n, uint64_t seed, int64_t* idx_out, void* stream);
 
+/* csc_coherence_scores -- s_i = ||Y_i||^2 over the first d columns (FP64 sum) of
+ * an UNnormalised filtered block Y = h~(L) R.  With R's N(0, 1/d) entries its
+ * expectation is ||h~(L) delta_i||^2, the estimate of the squared local cumulative
+ * coherence v_k(i)^2 given in the remark closing Sec. 4.2.  With normalize != 0
+ * the rows are then divided by their norms in place (Alg. 2 step 4; zero rows are
+ * left as they are).
+ *   Y          device, N x ld row-major (ld >= d): float when y_type is CSC_F32 or
+ *              CSC_BF16 (the filter's output for those storages), double for CSC_F64.
+ *   score_out  device double[N].  Asynchronous.
+ * Errors: CSC_E_INVALID. */
+CSC_API csc_status csc_coherence_scores(void* Y, csc_dtype y_type, int64_t N, int32_t d, int32_t ld,
+                                        int32_t normalize, double* score_out, void* stream);
+
+/* csc_sample_weighted -- variable-density sampling (Sec. 3.2.3 after Theorem 3.4):
+ * n draws i.i.d. WITH replacement, node i with probability q_i / Q, where
+ * q_i = floor(2^32 * (s_i / max_j s_j)) (one correctly rounded FP64 division) and
+ * Q = sum_i q_i.  Draw t takes the word r_t = SplitMix64_seed(t), the point
+ * u_t = floor(r_t * Q / 2^64) and the node with the smallest inclusive prefix
+ * sum of q above u_t (exact integer inverse CDF: bit-exact and deterministic).
+ *   score    device double[N]: finite, >= 0, at least one > 0 (for example
+ *            csc_coherence_scores, the distribution p_i ~ v_k(i)^2 of the cited
+ *            sampling theory).
+ *   idx_out  device int64[n], sorted ascending, repeated draws adjacent.
+ *   w_out    NULL or device float[n]: each draw's decoder weight Q / (N q_i)
+ *            (FP64, rounded to float): 1 for a flat profile.
+ *   1 <= N < 2^31, 0 <= n < 2^31.  Synchronizes `stream` (the scores are checked
+ *   on the device and the verdict read back).
+ * Errors: CSC_E_INVALID (arguments; a negative, NaN or infinite score; every score
+ * zero), CSC_E_OOM. */
+CSC_API csc_status csc_sample_weighted(const double* score, int64_t N, int64_t n, uint64_t seed, int64_t* idx_out,
+                                       float* w_out, void* stream);
+
 /* csc_gather_rows -- out[i, :] = X[idx[i], :] for i < n (Alg. 2 step 5).
  *   X    device float[N * ld];  idx  device int64[n] (values in [0, N));
  *   out  device float[n * ld_out], columns 0..d-1 written.  Asynchronous. */
@@ -451,6 +487,26 @@ CSC_API csc_status csc_interpolate(csc_graph g, const int64_t* sample_idx, const
 CSC_API csc_status csc_interpolate_highpass(csc_graph g, const int64_t* sample_idx, const int32_t* sample_labels,
                                             int64_t n, int32_t k, double lambda_c, int32_t m, double gamma,
                                             double rel_tol, int32_t max_iter, int32_t* labels_out,
+                                            float* fuzzy_out, csc_cg_info* info, void* stream);
+
+/* csc_interpolate_weighted -- the decoder of variable-density draws: Eq. 5 with
+ * the fidelity term weighted per draw (the P^{-1/2} weighting of the sampling
+ * theory cited after Theorem 3.4),
+ *   x_j = argmin_x sum_t w_t (x(omega_t) - [label_t == j])^2 + gamma x^T L^g_power x,
+ * the sum over draws t, so a node drawn twice counts twice.  The normal equations
+ * (M^T W M + gamma L^p) x = M^T W c_j are solved by the CG of csc_interpolate
+ * (preconditioner 1 / (sum of the node's weights + gamma)); the residual is
+ * measured against the weighted right-hand side, kept in an extra N x k block.
+ * Arguments as csc_interpolate plus
+ *   sample_w  device float[n], finite and > 0 (csc_sample_weighted's w_out).
+ *   n         >= 1 draws; repeats allowed (n may exceed N).
+ * Weights of repeated draws are summed in an unspecified order (bit-reproducible
+ * when a node's draws carry equal weights, as csc_sample_weighted's do).
+ * Unit weights on distinct draws give csc_interpolate's systems.
+ * Errors: as csc_interpolate; a weight not finite and positive is CSC_E_INVALID. */
+CSC_API csc_status csc_interpolate_weighted(csc_graph g, const int64_t* sample_idx, const int32_t* sample_labels,
+                                            const float* sample_w, int64_t n, int32_t k, int32_t g_power,
+                                            double gamma, double rel_tol, int32_t max_iter, int32_t* labels_out,
                                             float* fuzzy_out, csc_cg_info* info, void* stream);
 
 /* --------------------------------------------------------- whole pipeline */
@@ -521,9 +577,10 @@ CSC_API csc_status csc_interpolate_batched(csc_graph g, const int64_t* sample_id
  * csc_filter_batched (rows normalised), csc_sample_batched with n_i =
  * ceil(2 k_i ln k_i), row gather, csc_kmeans_batched, csc_interpolate_batched.
  * p: the shared parameters of csc_cluster (p->k, p->n, p->lambda_k and
- * p->bracket are ignored; d defaults to ceil(4 ln max_i N_i)).  k: host
- * int32[G].  labels_out: device int32[N].  lambda_out: NULL or host
- * double[G].  info: NULL or host.  Synchronizes. */
+ * p->bracket are ignored; d defaults to ceil(4 ln max_i N_i); p->flags may
+ * hold CSC_CLENSHAW, while CSC_HIGHPASS or CSC_VARDENSITY give
+ * CSC_E_UNSUPPORTED).  k: host int32[G].  labels_out: device int32[N].
+ * lambda_out: NULL or host double[G].  info: NULL or host.  Synchronizes. */
 CSC_API csc_status csc_cluster_batched(csc_graph g, const int32_t* k, const csc_params* p, int32_t* labels_out,
                                        double* lambda_out, csc_batch_info* info, void* stream);
 

@@ -35,7 +35,7 @@ CSC_E_UNSUPPORTED = 8
 
 CSC_F32, CSC_BF16, CSC_F64 = 0, 1, 2
 CSC_RCM, CSC_CHECK_SYM, CSC_DEVICE_INPUT = 1, 2, 4
-CSC_NORMALIZE_ROWS, CSC_NO_JACKSON, CSC_CLENSHAW, CSC_HIGHPASS = 1, 2, 4, 8
+CSC_NORMALIZE_ROWS, CSC_NO_JACKSON, CSC_CLENSHAW, CSC_HIGHPASS, CSC_VARDENSITY = 1, 2, 4, 8, 16
 CSC_MLP_IN, CSC_MLP_HIDDEN, CSC_MLP_OUT, CSC_MLP_PARAMS = 72, 256, 2, 84994
 CSC_BRACKET_PROBES, CSC_BRACKET_MOMENTS = 8, 64
 CSC_EIGENCOUNT_REFILTER = 1
@@ -110,6 +110,10 @@ _SIGNATURES = {
     "csc_interpolate_highpass": [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_double, c_int32, c_double,
                                  c_double, c_int32, c_void_p, c_void_p, P(csc_cg_info), c_void_p],
     "csc_sample": [c_int64, c_int64, c_uint64, c_void_p, c_void_p],
+    "csc_coherence_scores": [c_void_p, c_int32, c_int64, c_int32, c_int32, c_int32, c_void_p, c_void_p],
+    "csc_sample_weighted": [c_void_p, c_int64, c_int64, c_uint64, c_void_p, c_void_p, c_void_p],
+    "csc_interpolate_weighted": [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_int32, c_double,
+                                 c_double, c_int32, c_void_p, c_void_p, P(csc_cg_info), c_void_p],
     "csc_sample_noalloc": [c_int64, c_int64, c_uint64, c_void_p, c_void_p],
     "csc_gather_rows": [c_void_p, c_int64, c_int32, c_void_p, c_int64, c_int32, c_void_p, c_int32, c_void_p],
     "csc_kmeans_reduced": [c_void_p, c_int64, c_int32, c_int32, c_int32, c_int32, c_int32, c_uint64, c_void_p,

@@ -19,8 +19,9 @@ from ._native import check, lib
 
 F32, BF16, F64 = nat.CSC_F32, nat.CSC_BF16, nat.CSC_F64
 RCM, CHECK_SYM, DEVICE_INPUT = nat.CSC_RCM, nat.CSC_CHECK_SYM, nat.CSC_DEVICE_INPUT
-NORMALIZE_ROWS, NO_JACKSON, CLENSHAW, HIGHPASS = (nat.CSC_NORMALIZE_ROWS, nat.CSC_NO_JACKSON, nat.CSC_CLENSHAW,
-                                                  nat.CSC_HIGHPASS)
+NORMALIZE_ROWS, NO_JACKSON, CLENSHAW, HIGHPASS, VARDENSITY = (nat.CSC_NORMALIZE_ROWS, nat.CSC_NO_JACKSON,
+                                                              nat.CSC_CLENSHAW, nat.CSC_HIGHPASS,
+                                                              nat.CSC_VARDENSITY)
 
 
 def _stream(stream) -> ctypes.c_void_p:
@@ -318,6 +319,36 @@ def csc_sample(N: int, n: int, seed: int = 0, out: Optional[torch.Tensor] = None
     return out
 
 
+def csc_coherence_scores(Y: torch.Tensor, d: int, normalize: bool = False, out: Optional[torch.Tensor] = None,
+                         stream=None) -> torch.Tensor:
+    """s_i = ||Y_i||^2 (fp64) over the first d columns; optionally normalise Y's rows in place."""
+    if Y.dtype not in (torch.float32, torch.float64):
+        raise ValueError("Y must be float32 or float64")
+    N, ld = Y.shape
+    y_type = F64 if Y.dtype == torch.float64 else F32
+    if out is None:
+        out = torch.empty(N, dtype=torch.float64, device="cuda")
+    check(lib().csc_coherence_scores(_dptr(Y), y_type, N, d, ld, 1 if normalize else 0, _dptr(out),
+                                     _stream(stream)), "csc_coherence_scores")
+    return out
+
+
+def csc_sample_weighted(score: torch.Tensor, n: int, seed: int = 0, idx_out: Optional[torch.Tensor] = None,
+                        w_out: Optional[torch.Tensor] = None, weights: bool = True, stream=None):
+    """(idx int64[n] sorted with repeats, decoder weights float32[n] or None) of n variable-density draws."""
+    if score.dtype != torch.float64:
+        raise ValueError("score must be float64")
+    N = score.numel()
+    if idx_out is None:
+        idx_out = torch.empty(n, dtype=torch.int64, device="cuda")
+    if weights and w_out is None:
+        w_out = torch.empty(n, dtype=torch.float32, device="cuda")
+    check(lib().csc_sample_weighted(_dptr(score), N, n, seed, _dptr(idx_out) if n else None,
+                                    _dptr(w_out) if (weights and n) else None, _stream(stream)),
+          "csc_sample_weighted")
+    return idx_out, (w_out if weights else None)
+
+
 def csc_sample_noalloc(N: int, n: int, seed: int, out: torch.Tensor, stream=None) -> torch.Tensor:
     """csc_sample without any device allocation inside the library (the caller gives `out`)."""
     check(lib().csc_sample_noalloc(N, n, seed, _dptr(out) if n else None, _stream(stream)), "csc_sample_noalloc")
@@ -366,6 +397,24 @@ def csc_interpolate(g: Graph, sample_idx: torch.Tensor, sample_labels: torch.Ten
                                gamma, rel_tol, max_iter, _dptr(labels_out), _dptr(fz), ctypes.byref(info),
                                _stream(stream))
     check(st, "csc_interpolate", allow=(nat.CSC_E_NOT_CONVERGED,))
+    return labels_out, fz, CgInfo(info.iters, bool(info.converged), info.max_rel_residual)
+
+
+def csc_interpolate_weighted(g: Graph, sample_idx: torch.Tensor, sample_labels: torch.Tensor,
+                             sample_w: torch.Tensor, k: int, g_power: int = 4, gamma: float = 1e-3,
+                             rel_tol: float = 1e-6, max_iter: int = 2000, labels_out: Optional[torch.Tensor] = None,
+                             fuzzy: bool = False, stream=None):
+    """Weighted decoder of variable-density draws: (labels, fuzzy or None, CgInfo)."""
+    if sample_w.dtype != torch.float32 or sample_w.numel() != sample_idx.numel():
+        raise ValueError("sample_w must be float32 with one weight per draw")
+    if labels_out is None:
+        labels_out = torch.empty(g.N, dtype=torch.int32, device="cuda")
+    fz = torch.empty((g.N, k), dtype=torch.float32, device="cuda") if fuzzy else None
+    info = nat.csc_cg_info()
+    st = lib().csc_interpolate_weighted(g.handle, _dptr(sample_idx), _dptr(sample_labels), _dptr(sample_w),
+                                        sample_idx.numel(), k, g_power, gamma, rel_tol, max_iter, _dptr(labels_out),
+                                        _dptr(fz), ctypes.byref(info), _stream(stream))
+    check(st, "csc_interpolate_weighted", allow=(nat.CSC_E_NOT_CONVERGED,))
     return labels_out, fz, CgInfo(info.iters, bool(info.converged), info.max_rel_residual)
 
 

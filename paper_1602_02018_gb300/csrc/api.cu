@@ -1169,6 +1169,32 @@ csc_status csc_sample(int64_t N, int64_t n, uint64_t seed, int64_t* idx_out, voi
     return run_sample(N, n, seed, idx_out, nullptr, (cudaStream_t)stream);
 }
 
+csc_status csc_coherence_scores(void* Y, csc_dtype y_type, int64_t N, int32_t d, int32_t ld, int32_t normalize,
+                                double* score_out, void* stream) {
+    clear_error();
+    if (!Y || !score_out || N < 1 || N >= (int64_t)INT32_MAX || d < 1 || ld < d ||
+        (y_type != CSC_F32 && y_type != CSC_BF16 && y_type != CSC_F64)) {
+        set_error("csc_coherence_scores: invalid arguments (N=%lld d=%d ld=%d y_type=%d)", (long long)N, d, ld,
+                  (int)y_type);
+        return CSC_E_INVALID;
+    }
+    int dev = 0, sms = 0;
+    CSC_CUDA_TRY(cudaGetDevice(&dev));
+    CSC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return run_row_scores(Y, y_type == CSC_F64, N, d, ld, score_out, normalize != 0, sms, (cudaStream_t)stream);
+}
+
+csc_status csc_sample_weighted(const double* score, int64_t N, int64_t n, uint64_t seed, int64_t* idx_out,
+                               float* w_out, void* stream) {
+    clear_error();
+    if (!score || N < 1 || N >= (int64_t)INT32_MAX || n < 0 || n >= (int64_t)INT32_MAX || (n > 0 && !idx_out)) {
+        set_error("csc_sample_weighted: need 1 <= N < 2^31, 0 <= n < 2^31, score and idx_out != NULL");
+        return CSC_E_INVALID;
+    }
+    if (n == 0) return CSC_OK;
+    return run_sample_weighted(score, N, n, seed, idx_out, w_out, nullptr, (cudaStream_t)stream);
+}
+
 csc_status csc_gather_rows(const float* X, int64_t N, int32_t ld, const int64_t* idx, int64_t n, int32_t d,
                            float* out, int32_t ld_out, void* stream) {
     clear_error();
@@ -1232,6 +1258,23 @@ csc_status csc_interpolate_highpass(csc_graph g, const int64_t* sample_idx, cons
     return poison_on_cuda(g, st);
 }
 
+csc_status csc_interpolate_weighted(csc_graph g, const int64_t* sample_idx, const int32_t* sample_labels,
+                                    const float* sample_w, int64_t n, int32_t k, int32_t g_power, double gamma,
+                                    double rel_tol, int32_t max_iter, int32_t* labels_out, float* fuzzy_out,
+                                    csc_cg_info* info, void* stream) {
+    clear_error();
+    CSC_TRY(check_graph(g));
+    if (!sample_idx || !sample_labels || !sample_w || !labels_out || n < 1 || n >= (int64_t)INT32_MAX || k < 1 ||
+        g_power < 1 || !(gamma > 0.0) || !(rel_tol > 0.0) || max_iter < 1) {
+        set_error("csc_interpolate_weighted: invalid arguments (n=%lld k=%d g_power=%d gamma=%g rel_tol=%g)",
+                  (long long)n, k, g_power, gamma, rel_tol);
+        return CSC_E_INVALID;
+    }
+    csc_status st = run_interpolate(g, sample_idx, sample_labels, n, k, g_power, gamma, rel_tol, max_iter,
+                                    labels_out, fuzzy_out, info, (cudaStream_t)stream, nullptr, nullptr, 0, sample_w);
+    return poison_on_cuda(g, st);
+}
+
 csc_status csc_cluster(csc_graph g, const csc_params* p, int32_t* labels_out, csc_cluster_info* info,
                        void* stream) {
     clear_error();
@@ -1285,12 +1328,16 @@ csc_status csc_cluster(csc_graph g, const csc_params* p, int32_t* labels_out, cs
         local.lambda.lambda = lam;
     }
     cudaEventRecord(e1, s);
-    // pipeline buffers: Y (N x d_pad, fp32 or fp64), idx (n), Xr (n x d_pad fp32), sample labels (n)
+    // pipeline buffers: Y (N x d_pad, fp32 or fp64), idx (n), Xr (n x d_pad fp32), sample labels (n);
+    // variable density adds the scores (N doubles) and the draw weights (n floats)
+    const bool vd = (p->flags & CSC_VARDENSITY) != 0;
     const size_t ybytes = (size_t)N * d_pad * (storage == CSC_F64 ? 8 : 4);
     const size_t off_idx = (ybytes + 255) / 256 * 256;
     const size_t off_xr = off_idx + ((size_t)n * 8 + 255) / 256 * 256;
     const size_t off_lab = off_xr + ((size_t)n * d_pad * 4 + 255) / 256 * 256;
-    const size_t total = off_lab + (size_t)n * 4 + 256;
+    const size_t off_w = off_lab + ((size_t)n * 4 + 255) / 256 * 256;
+    const size_t off_sc = off_w + (vd ? ((size_t)n * 4 + 255) / 256 * 256 : 0);
+    const size_t total = off_sc + (vd ? (size_t)N * 8 : 0) + 256;
     void* base = nullptr;
     st = ws_get(g, WS_PIPE, total, &base);
     if (st != CSC_OK) return done(st);
@@ -1299,12 +1346,17 @@ csc_status csc_cluster(csc_graph g, const csc_params* p, int32_t* labels_out, cs
     int64_t* idx = (int64_t*)(b + off_idx);
     float* Xr = (float*)(b + off_xr);
     int32_t* slab = (int32_t*)(b + off_lab);
+    float* wdraw = vd ? (float*)(b + off_w) : nullptr;
+    double* score = vd ? (double*)(b + off_sc) : nullptr;
     std::vector<double> c(m + 1);
     cheb_coefficients(lam, m, true, c.data());
-    st = run_filter(g, c.data(), m, d, d_pad, p->seed, storage, nullptr, Y, true, s, (p->flags & CSC_CLENSHAW) != 0);
+    st = run_filter(g, c.data(), m, d, d_pad, p->seed, storage, nullptr, Y, !vd, s, (p->flags & CSC_CLENSHAW) != 0);
+    if (st != CSC_OK) return done(st);
+    // variable density: scores ||Y_i||^2 of the unnormalised rows, then step 4's normalisation
+    if (vd) st = run_row_scores(Y, storage == CSC_F64, N, d, d_pad, score, true, g->num_sms, s);
     if (st != CSC_OK) return done(st);
     cudaEventRecord(e2, s);
-    st = run_sample(N, n, p->seed, idx, g, s);
+    st = vd ? run_sample_weighted(score, N, n, p->seed, idx, wdraw, g, s) : run_sample(N, n, p->seed, idx, g, s);
     if (st != CSC_OK) return done(st);
     if (storage == CSC_F64) {
         // fp64 feature rows are narrowed to fp32 for k-means
@@ -1323,7 +1375,7 @@ csc_status csc_cluster(csc_graph g, const csc_params* p, int32_t* labels_out, cs
         cheb_coefficients(lam, m, true, hpc.data());
     }
     st = run_interpolate(g, idx, slab, n, k, g_power, gamma, cg_tol, cg_max, labels_out, nullptr, &local.cg, s,
-                         nullptr, hpc.empty() ? nullptr : hpc.data(), m);
+                         nullptr, hpc.empty() ? nullptr : hpc.data(), m, wdraw);
     if (st != CSC_OK && st != CSC_E_NOT_CONVERGED) return done(st);
     cudaEventRecord(e5, s);
     cudaError_t ce = cudaEventSynchronize(e5);

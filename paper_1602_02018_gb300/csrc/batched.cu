@@ -312,6 +312,10 @@ csc_status csc_cluster_batched(csc_graph g, const int32_t* k, const csc_params* 
         set_error("csc_cluster_batched: invalid arguments");
         return CSC_E_INVALID;
     }
+    if (p->flags & (CSC_HIGHPASS | CSC_VARDENSITY)) {
+        set_error("csc_cluster_batched: CSC_HIGHPASS and CSC_VARDENSITY are single-graph options (csc_cluster)");
+        return CSC_E_UNSUPPORTED;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     int64_t nmax = 1;
     std::vector<int64_t> n_per(G), soff(G + 1, 0);

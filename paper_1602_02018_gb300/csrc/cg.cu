@@ -338,11 +338,12 @@ cg_pupdate_kernel(const float* __restrict__ r, float* __restrict__ p, const doub
     }
 }
 
-// ||b - A x||^2 per column, b rebuilt from the sample labels: partials
+// ||b - A x||^2 per column: partials.  b is rebuilt from the sample labels, or
+// read from bfull (weighted decoder) when that is not NULL.
 template <int G, int NT>
 __global__ void __launch_bounds__(kCgMaxThreads)
-residual_kernel(const float* __restrict__ Ax, const int32_t* __restrict__ slab, const int32_t* __restrict__ part,
-                int ncols, int64_t ld, double* __restrict__ partials, CgBatch bt) {
+residual_kernel(const float* __restrict__ Ax, const int32_t* __restrict__ slab, const float* __restrict__ bfull,
+                const int32_t* __restrict__ part, int ncols, int64_t ld, double* __restrict__ partials, CgBatch bt) {
     CG_TILE(G, NT)
     KSum acc[1][NT][4];
     CG_ROWS(G) {
@@ -352,11 +353,17 @@ residual_kernel(const float* __restrict__ Ax, const int32_t* __restrict__ slab, 
             const int cl = (t * G + lane) * 4;
             if (cl >= tcols) continue;
             const int c = col0 + cl;
-            float a[4];
+            float a[4], bv[4];
             StoreTraits<float>::load(Ax + (int64_t)row * ld + c, a);
+            if (bfull) {
+                StoreTraits<float>::load(bfull + (int64_t)row * ld + c, bv);
+            } else {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) bv[v] = c + v == lab ? 1.0f : 0.0f;
+            }
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                const float e = (c + v == lab ? 1.0f : 0.0f) - a[v];
+                const float e = bv[v] - a[v];
                 acc[0][t][v].add(e * e);
             }
         }
@@ -497,10 +504,13 @@ __global__ void __launch_bounds__(512) column_sum_kernel(const double* __restric
 }
 
 // gk / gid (batched handle): a sample's label must be below its graph's k.
+// w (weighted decoder of variable-density draws): NULL for the 0/1 mask of Eq. 5,
+// else each draw adds its weight to the mask and to the right-hand side (a node
+// drawn twice counts twice); weights must be finite and positive.
 __global__ void cg_setup_kernel(const int64_t* __restrict__ sample_idx, const int32_t* __restrict__ sample_labels,
-                                int64_t n, int64_t N, const int32_t* __restrict__ iperm, float* __restrict__ r,
-                                float* __restrict__ mask, int32_t* __restrict__ slab, int64_t ld, int k,
-                                const int32_t* __restrict__ gk, const int32_t* __restrict__ gid,
+                                const float* __restrict__ w, int64_t n, int64_t N, const int32_t* __restrict__ iperm,
+                                float* __restrict__ r, float* __restrict__ mask, int32_t* __restrict__ slab,
+                                int64_t ld, int k, const int32_t* __restrict__ gk, const int32_t* __restrict__ gid,
                                 int* __restrict__ bad) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -516,8 +526,18 @@ __global__ void cg_setup_kernel(const int64_t* __restrict__ sample_idx, const in
         atomicOr(bad, 1);
         return;
     }
-    r[row * ld + lab] = 1.0f;
-    mask[row] = 1.0f;
+    if (w) {
+        const float wt = w[i];
+        if (!(wt > 0.0f) || isinf(wt)) {
+            atomicOr(bad, 1);
+            return;
+        }
+        atomicAdd(r + row * ld + lab, wt);
+        atomicAdd(mask + row, wt);
+    } else {
+        r[row * ld + lab] = 1.0f;
+        mask[row] = 1.0f;
+    }
     slab[row] = lab;
 }
 
@@ -593,7 +613,7 @@ static csc_status cg_occupancy(const LaunchCfg& c, int* out) {
 csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* sample_labels, int64_t n, int k,
                            int g_power, double gamma, double rel_tol, int max_iter, int32_t* labels_out,
                            float* fuzzy_out, csc_cg_info* info, cudaStream_t s, const int32_t* k_graphs,
-                           const double* hp_coef, int hp_m) {
+                           const double* hp_coef, int hp_m, const float* sample_w) {
     const int32_t N = (int32_t)g->N;
     // one independent set of k systems per graph of a batch (k_graphs: each graph's k)
     const int nseg = (k_graphs && g->n_graphs > 1) ? g->n_graphs : 1;
@@ -671,6 +691,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const size_t o_x = take(blk), o_r = take(blk), o_p = take(blk), o_ap = take(blk), o_t1 = take(blk),
                  o_t2 = take(blk);
     const size_t o_mask = take((size_t)N * 4), o_pinv = take((size_t)N * 4), o_slab = take((size_t)N * 4);
+    const size_t o_b = take(sample_w ? blk : 0);  // weighted right-hand side, kept for the residual
     // two quantities per row-range block; <p, A p> also has one slot per heavy row
     const size_t o_part = take((size_t)2 * (max_p + g->n_heavy) * ld * 8);
     const size_t sl = (size_t)nseg * ld;  // per-(graph, column) state length
@@ -688,6 +709,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     float* mask = (float*)(b + o_mask);
     float* pinv = (float*)(b + o_pinv);
     int32_t* slab = (int32_t*)(b + o_slab);
+    float* bfull = sample_w ? (float*)(b + o_b) : nullptr;
     double* part = (double*)(b + o_part);
     double* sd = (double*)(b + o_state);
     CgState st;
@@ -729,8 +751,10 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     CSC_CUDA_TRY(cudaMemsetAsync(slab, 0xff, (size_t)N * 4, s));
     CSC_CUDA_TRY(cudaMemsetAsync(st.n_active, 0, 2 * sizeof(int), s));
     CSC_KLAUNCH("cg_setup", 24.0 * n, s,
-                cg_setup_kernel<<<ceil_div(n, 256), 256, 0, s>>>(sample_idx, sample_labels, n, (int64_t)N, g->iperm,
-                                                                 r, mask, slab, ld, k, d_gk, gid, bad));
+                cg_setup_kernel<<<ceil_div(n, 256), 256, 0, s>>>(sample_idx, sample_labels, sample_w, n,
+                                                                 (int64_t)N, g->iperm, r, mask, slab, ld, k, d_gk,
+                                                                 gid, bad));
+    if (bfull) CSC_CUDA_TRY(cudaMemcpyAsync(bfull, r, blk, cudaMemcpyDeviceToDevice, s));
     CSC_KLAUNCH("cg_setup", 8.0 * N, s, precond_kernel<<<ceil_div(N, 256), 256, 0, s>>>(mask, (float)gamma, pinv, N));
 
     // launch shape: tuned on the middle product of the chain (the dominant kernel),
@@ -814,7 +838,8 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     CSC_CUDA_TRY(cudaMemcpyAsync(h_active, st.n_active, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CSC_CUDA_TRY(cudaStreamSynchronize(s));
     if (h_active[1]) {
-        set_error("csc_interpolate: a sample label is outside [0, k) or a sample index outside [0, N)");
+        set_error("csc_interpolate: a sample label is outside [0, k), a sample index outside [0, N) or a sample "
+                  "weight not finite and positive");
         return CSC_E_INVALID;
     }
     auto apply_A = [&](const float* in, const CgBatch& bb, cudaStream_t s) -> csc_status {
@@ -923,7 +948,8 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     // true residual ||b - A x|| / ||b|| per column
     CSC_TRY(apply_A(x, bt_all, s));
     CG_SWITCH(cfg, CSC_KLAUNCH("cg_residual", blkb + 4.0 * N, s,
-                               residual_kernel<G_, NT_><<<grid, th, 0, s>>>(Ap, slab, rpart, ld, ld, part, bt_all)));
+                               residual_kernel<G_, NT_><<<grid, th, 0, s>>>(Ap, slab, bfull, rpart, ld, ld, part,
+                                                                            bt_all)));
     CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, st.rr));
     // labels
     CG_SWITCH(cfg, CSC_KLAUNCH("label_norms", blkb, s,

@@ -249,6 +249,10 @@ csc_status run_refilter_count(Graph* g, double lambda, int m, int n_probes, uint
 csc_status mlp_forward_device(const float* params, const float* X, int B, float* Y, cudaStream_t s);
 
 // sample.cu (K6)
+csc_status run_sample_weighted(const double* score, int64_t N, int64_t n, uint64_t seed, int64_t* idx_out,
+                               float* w_out, Graph* scratch_owner, cudaStream_t s);
+csc_status run_row_scores(void* Y, bool y_f64, int64_t N, int d, int ld, double* score, bool normalize,
+                          int num_sms, cudaStream_t s);
 csc_status run_sample(int64_t N, int64_t n, uint64_t seed, int64_t* idx_out, Graph* scratch_owner,
                       cudaStream_t s);
 csc_status run_gather_rows(const float* X, int64_t N, int ld, const int64_t* idx, int64_t n, int d,
@@ -276,10 +280,12 @@ csc_status run_kmeans(const float* X, int64_t n, int d, int ld, int k, int repli
 // cg.cu (K8 + K9).  k_graphs: NULL, or (batched handle) host int32[n_graphs], each
 // graph's k (k = their maximum): one set of systems per graph.  hp_coef: NULL for
 // g(L) = L^g_power, or host double[hp_m + 1], the coefficients of h~ for g = 1 - h~.
+// sample_w: NULL for Eq. 5's 0/1 mask, or device float[n] draw weights (weighted decoder).
 csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* sample_labels,
                            int64_t n, int k, int g_power, double gamma, double rel_tol, int max_iter,
                            int32_t* labels_out, float* fuzzy_out, csc_cg_info* info, cudaStream_t s,
-                           const int32_t* k_graphs = nullptr, const double* hp_coef = nullptr, int hp_m = 0);
+                           const int32_t* k_graphs = nullptr, const double* hp_coef = nullptr, int hp_m = 0,
+                           const float* sample_w = nullptr);
 
 // host math (api.cu)
 void cheb_coefficients(double lambda_c, int m, bool jackson, double* c);

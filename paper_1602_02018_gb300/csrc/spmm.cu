@@ -519,8 +519,10 @@ clenshaw_step_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __rest
 
 // ------------------------------------------------------------------- K5
 // One warp per row: fp64 sum of squares of the first d columns, then scale.
+// score (optional) receives the sum of squares ||Y_i||^2, the coherence estimate
+// of the remark closing Sec. 4.2; scale = 0 leaves Y as it is.
 template <typename A>
-__global__ void normalize_kernel(A* __restrict__ Y, int32_t N, int d, int ld) {
+__global__ void normalize_kernel(A* __restrict__ Y, int32_t N, int d, int ld, double* __restrict__ score, int scale) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -532,7 +534,8 @@ __global__ void normalize_kernel(A* __restrict__ Y, int32_t N, int d, int ld) {
             s += v * v;
         }
         s = warp_sum(s);
-        if (s > 0.0) {
+        if (score && lane == 0) score[row] = s;
+        if (scale && s > 0.0) {
             const double inv = 1.0 / sqrt(s);
             for (int c = lane; c < d; c += 32) y[c] = (A)((double)y[c] * inv);
         }
@@ -1200,7 +1203,7 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
         int grid = ceil_div(N, 8);
         if (grid > g->num_sms * 8) grid = g->num_sms * 8;
         CSC_KLAUNCH("normalize", 2.0 * N * d_pad * sizeof(A), s,
-                    normalize_kernel<A><<<grid, 256, 0, s>>>(Y, (int32_t)N, d, d_pad));
+                    normalize_kernel<A><<<grid, 256, 0, s>>>(Y, (int32_t)N, d, d_pad, nullptr, 1));
     }
     return CSC_OK;
 }
@@ -1304,6 +1307,25 @@ csc_status run_filter(Graph* g, const double* coeffs, int m, int d, int d_pad, u
             set_error("unknown storage type %d", (int)storage);
             return CSC_E_INVALID;
     }
+}
+
+// s_i = ||Y_i||^2 over the first d columns (fp64), then optionally Y_i / ||Y_i||.
+// Y is the filter's output: float for fp32 and bf16 storage, double for fp64.
+csc_status run_row_scores(void* Y, bool y_f64, int64_t N, int d, int ld, double* score, bool normalize,
+                          int num_sms, cudaStream_t s) {
+    int grid = ceil_div(N, 8);
+    if (grid > num_sms * 8) grid = num_sms * 8;
+    const double bytes = (normalize ? 2.0 : 1.0) * N * d * (y_f64 ? 8.0 : 4.0) + 8.0 * N;
+    if (y_f64) {
+        CSC_KLAUNCH("normalize", bytes, s,
+                    normalize_kernel<double><<<grid, 256, 0, s>>>((double*)Y, (int32_t)N, d, ld, score,
+                                                                  normalize ? 1 : 0));
+    } else {
+        CSC_KLAUNCH("normalize", bytes, s,
+                    normalize_kernel<float><<<grid, 256, 0, s>>>((float*)Y, (int32_t)N, d, ld, score,
+                                                                 normalize ? 1 : 0));
+    }
+    return CSC_OK;
 }
 
 // Paper-literal eigencount at one cut-off: filter n_probes N(0, 1) probes (the
