@@ -180,8 +180,9 @@ CSC_API csc_status csc_graph_info(csc_graph g, int64_t* N, int64_t* nnz, int32_t
 
 /* csc_graph_tuned_shape -- the launch shapes the autotuner chose on this handle
  * (not a step of the paper's method).  Shapes are tuned on first use per kernel
- * kind (1 = Chebyshev step, 2 = moment step, 3 = CG products), storage width and
- * column count, by timing every compiled shape on the handle's graph.  Entry i
+ * kind (1 = Chebyshev step, 2 = moment step, 3 = CG products, 4 = Clenshaw step),
+ * storage width and column count, by timing every compiled shape on the handle's
+ * graph.  Entry i
  * (0-based) is written to kind, dtype_bytes (4 fp32, 2 bf16, 8 fp64), columns and
  * shape[6] = {lanes per row G, vectors per lane NT, threads per CTA, row ranges P,
  * column tiles, shared-memory window rows (0: none)}.  Host outputs (any may be
