@@ -546,31 +546,78 @@ __global__ void precond_kernel(const float* __restrict__ mask, float gamma, floa
     if (i < N) pinv[i] = 1.0f / (mask[i] + gamma);
 }
 
-// label(i) = argmax_j x_ij / ||x_j|| (fp64 comparison, ties to the lowest j); one thread per row.
-__global__ void label_argmax_kernel(const float* __restrict__ x, const double* __restrict__ norm2_all, int32_t N,
-                                    int k_all, int64_t ld, const int32_t* __restrict__ gk,
-                                    const int32_t* __restrict__ gid, const int32_t* __restrict__ perm,
-                                    int32_t* __restrict__ labels, float* __restrict__ fuzzy) {
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= N) return;
-    const int gr = gid ? gid[row] : 0;
-    const int k = gk ? gk[gr] : k_all;
-    const double* norm2 = norm2_all + (int64_t)gr * ld;
-    const float* xr = x + (int64_t)row * ld;
-    int best = 0;
-    double bv = -INFINITY;
-    for (int j = 0; j < k; ++j) {
-        const double nj = norm2[j];
-        const double v = nj > 0.0 ? (double)xr[j] / sqrt(nj) : 0.0;
-        if (v > bv) {
-            bv = v;
-            best = j;
+// ||x_j|| (fp64) and 1/||x_j|| rounded to fp32 of every (graph, column); 0 and 0
+// for a zero column.
+__global__ void label_scale_kernel(const double* __restrict__ norm2, int64_t n, double* __restrict__ nrm,
+                                   float* __restrict__ rnrm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double q = norm2[i];
+    const double r = q > 0.0 ? sqrt(q) : 0.0;
+    nrm[i] = r;
+    rnrm[i] = q > 0.0 ? (float)(1.0 / r) : 0.f;
+}
+
+// label(i) = argmax_j x_ij / ||x_j|| with the quotient rounded in fp64 (ties to the
+// lowest j; a zero column scores 0), one warp per row.  FP64 is slow on this part,
+// so the quotients are first approximated in fp32, x times the fp32 reciprocal
+// (within 2^-22 relative of the fp64 quotient); only columns within 2^-20 relative
+// of the largest approximation, which always include the winner, get the fp64
+// division.  The decision therefore equals dividing every entry in fp64.  A row
+// whose approximations are not all finite, or whose largest one lies below 2^-100,
+// takes the fp64 division everywhere.
+__global__ void label_argmax_kernel(const float* __restrict__ x, const double* __restrict__ nrm_all,
+                                    const float* __restrict__ rnrm_all, int32_t N, int k_all, int64_t ld,
+                                    const int32_t* __restrict__ gk, const int32_t* __restrict__ gid,
+                                    const int32_t* __restrict__ perm, int32_t* __restrict__ labels,
+                                    float* __restrict__ fuzzy) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < N; row += nw) {
+        const int gr = gid ? gid[row] : 0;
+        const int k = gk ? gk[gr] : k_all;
+        const double* nrm = nrm_all + (int64_t)gr * ld;
+        const float* rnrm = rnrm_all + (int64_t)gr * ld;
+        const float* xr = x + row * ld;
+        float am = -INFINITY;
+        int finite = 1;
+        for (int j = lane; j < k; j += 32) {
+            const float a = xr[j] * rnrm[j];
+            finite &= isfinite(a) ? 1 : 0;
+            am = fmaxf(am, a);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, o));
+        // non-finite approximations, or a maximum so small that fp32 loses relative
+        // precision (subnormal range): fp64 division everywhere
+        const bool all = __all_sync(0xffffffffu, finite) == 0 || fabsf(am) < 0x1p-100f;
+        const float thr = am - fabsf(am) * 0x1p-20f;
+        double bv = -INFINITY;
+        int best = 0x7fffffff;
+        for (int j = lane; j < k; j += 32) {
+            if (all || xr[j] * rnrm[j] >= thr) {
+                const double nj = nrm[j];
+                const double v = nj > 0.0 ? (double)xr[j] / nj : 0.0;
+                if (v > bv || (v == bv && j < best)) {
+                    bv = v;
+                    best = j;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+            if (ov > bv || (ov == bv && ob < best)) {
+                bv = ov;
+                best = ob;
+            }
+        }
+        const int64_t orig = perm ? perm[row] : row;
+        if (lane == 0) labels[orig] = best < k ? best : 0;
+        if (fuzzy)
+            for (int j = lane; j < k; j += 32) fuzzy[orig * k_all + j] = xr[j];
     }
-    const int64_t orig = perm ? perm[row] : row;
-    labels[orig] = best;
-    if (fuzzy)
-        for (int j = 0; j < k; ++j) fuzzy[orig * k_all + j] = xr[j];
 }
 
 // ------------------------------------------------------------- dispatch
@@ -695,7 +742,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     // two quantities per row-range block; <p, A p> also has one slot per heavy row
     const size_t o_part = take((size_t)2 * (max_p + g->n_heavy) * ld * 8);
     const size_t sl = (size_t)nseg * ld;  // per-(graph, column) state length
-    const size_t o_state = take(sl * 8 * 6 + sl * 4 + 64);
+    const size_t o_state = take(sl * 8 * 8 + sl * 4 + 64);
     const size_t o_gk = take((size_t)nseg * 4 * 3);
     void* base = nullptr;
     CSC_TRY(ws_get(g, WS_CG, off, &base));
@@ -719,7 +766,9 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     st.beta = sd + 3 * sl;
     st.rr = sd + 4 * sl;
     double* norm2 = sd + 5 * sl;
-    st.active = (int*)(sd + 6 * sl);
+    double* nrm = sd + 6 * sl;   // column norms ||x_j|| (label rule)
+    float* rnrm = (float*)(sd + 7 * sl);  // their reciprocals (fp32)
+    st.active = (int*)(sd + 8 * sl);
     st.n_active = st.active + sl;
     int* bad = st.n_active + 1;
     int32_t* d_gk = nullptr;
@@ -742,7 +791,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         CSC_CUDA_TRY(cudaMemsetAsync(p, 0, blk, s));
         CSC_CUDA_TRY(cudaMemsetAsync(Ap, 0, blk, s));
     }
-    CSC_CUDA_TRY(cudaMemsetAsync(sd, 0, sl * 8 * 6 + sl * 4, s));
+    CSC_CUDA_TRY(cudaMemsetAsync(sd, 0, sl * 8 * 8 + sl * 4, s));
 
     // zero x, r, mask; slab = -1
     CSC_CUDA_TRY(cudaMemsetAsync(x, 0, blk, s));
@@ -955,9 +1004,15 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     CG_SWITCH(cfg, CSC_KLAUNCH("label_norms", blkb, s,
                                colnorm_kernel<G_, NT_><<<grid, th, 0, s>>>(x, rpart, ld, ld, part, bt_all)));
     CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, norm2));
-    CSC_KLAUNCH("label_argmax", blkb + 4.0 * N + (fuzzy_out ? (double)N * k * 4 : 0.0), s,
-                label_argmax_kernel<<<ceil_div(N, 256), 256, 0, s>>>(x, norm2, N, k, ld, d_gk, gid, g->perm,
-                                                                     labels_out, fuzzy_out));
+    CSC_KLAUNCH("label_argmax", 24.0 * sl, s,
+                label_scale_kernel<<<ceil_div((int64_t)sl, 256), 256, 0, s>>>(norm2, (int64_t)sl, nrm, rnrm));
+    {
+        int lgrid = ceil_div(N, 8);  // a warp per row, 8 per CTA
+        if (lgrid > g->num_sms * 16) lgrid = g->num_sms * 16;
+        CSC_KLAUNCH("label_argmax", blkb + 4.0 * N + (fuzzy_out ? (double)N * k * 4 : 0.0), s,
+                    label_argmax_kernel<<<lgrid, 256, 0, s>>>(x, nrm, rnrm, N, k, ld, d_gk, gid, g->perm,
+                                                              labels_out, fuzzy_out));
+    }
     std::vector<double> rr(sl), bn(sl);
     CSC_CUDA_TRY(cudaMemcpyAsync(rr.data(), st.rr, sl * sizeof(double), cudaMemcpyDeviceToHost, s));
     CSC_CUDA_TRY(cudaMemcpyAsync(bn.data(), st.bn2, sl * sizeof(double), cudaMemcpyDeviceToHost, s));
