@@ -122,6 +122,11 @@ typedef struct {
                               interpolate with g = 1 - h~ at lambda_k, degree m;
                               CSC_VARDENSITY: csc_coherence_scores, csc_sample_weighted
                               and the weighted decoder in place of uniform sampling     */
+    int32_t  m_count;      /* degree of the eigencount filter of step 1 (Sec. 4.3 does
+                              not fix it); default m.  The damped step leaks a little of
+                              every eigenvalue above the cut-off into the count, which on
+                              graphs of ~1e6 nodes can alone reach k: a higher degree
+                              (e.g. 4 m) sharpens it for a few extra moment passes      */
 } csc_params;
 
 /* Per-stage results and timings of csc_cluster. */

@@ -1,7 +1,8 @@
 """Alg. 2 (Compressive Spectral Clustering) end to end in FP64, test infrastructure only.
 
 Steps, in the paper's order, each delegated to the module that follows it:
-1. estimate lambda_k by eigencount and dichotomy (chebyshev, Sec. 4.3);
+1. estimate lambda_k by eigencount and dichotomy (chebyshev, Sec. 4.3), with the
+   eigencount filter of degree m_count (default m; the paper does not fix it);
 2. Jackson-Chebyshev coefficients of h_{lambda_k} (chebyshev, Sec. 4.3);
 3. R: d signals N(0, 1/d) (rng, shared Philox convention);
 4. Y = h~(L) R, rows normalised (chebyshev, Alg. 2 step 4);
@@ -38,7 +39,7 @@ def csc(row_ptr, col_idx, k: int, seed: int = 0, m: int = 50, d: int | None = No
         n: int | None = None, n_v: int | None = None, gamma: float = 1e-3, g_power: int = 4,
         replicates: int = 20, max_iter_km: int = 100, cg_tol: float = 1e-10,
         lambda_k: float | None = None, r_in: np.ndarray | None = None, timings: dict | None = None,
-        variable_density: bool = False):
+        variable_density: bool = False, m_count: int | None = None):
     """Run Alg. 2 and return a dict with every intermediate result."""
     t0 = time.perf_counter()
     n_nodes = len(row_ptr) - 1
@@ -51,7 +52,7 @@ def csc(row_ptr, col_idx, k: int, seed: int = 0, m: int = 50, d: int | None = No
     tt = {}
     t = time.perf_counter()
     if lambda_k is None:
-        est = chebyshev.estimate_lambda_k(s, k, m, n_v, seed)
+        est = chebyshev.estimate_lambda_k(s, k, m if m_count is None else m_count, n_v, seed)
         lam = est["lam"]
     else:
         est, lam = None, lambda_k
@@ -81,5 +82,6 @@ def csc(row_ptr, col_idx, k: int, seed: int = 0, m: int = 50, d: int | None = No
         timings.update(tt)
     return dict(lam=lam, est=est, coeffs=coeffs, r=r, y=y, features=feats, omega=omega, weights=w,
                 sample_labels=lab_r, inertia=inertia, x=x, cg_iters=cg_it, cg_res=cg_res,
-                labels=labels, params=dict(k=k, m=m, d=d, n=n, n_v=n_v, gamma=gamma,
+                labels=labels, params=dict(k=k, m=m, m_count=m if m_count is None else m_count, d=d, n=n, n_v=n_v,
+                                           gamma=gamma,
                                            g_power=g_power, seed=seed))

@@ -1321,7 +1321,8 @@ csc_status csc_cluster(csc_graph g, const csc_params* p, int32_t* labels_out, cs
     cudaEventRecord(e0, s);
     double lam = p->lambda_k;
     if (!(lam > 0.0)) {
-        st = csc_estimate_lambda_k(g, k, m, p->n_probes, p->seed, p->bracket, &local.lambda, stream);
+        st = csc_estimate_lambda_k(g, k, p->m_count > 0 ? p->m_count : m, p->n_probes, p->seed, p->bracket,
+                                   &local.lambda, stream);
         if (st != CSC_OK) return done(st);
         lam = local.lambda.lambda;
     } else {

@@ -358,7 +358,8 @@ csc_status csc_cluster_batched(csc_graph g, const int32_t* k, const csc_params* 
     cudaEventRecord(ev[0], s);
     std::vector<double> lam(G);
     std::vector<csc_lambda_info> linfo(G);
-    csc_status st = lambda_batched(g, k, m, p->n_probes, p->seed, lam.data(), linfo.data(), s);
+    csc_status st = lambda_batched(g, k, p->m_count > 0 ? p->m_count : m, p->n_probes, p->seed, lam.data(),
+                                   linfo.data(), s);
     if (st != CSC_OK) return done(st);
     for (int i = 0; i < G; ++i) local.lambda_hits += linfo[i].hit;
     cudaEventRecord(ev[1], s);

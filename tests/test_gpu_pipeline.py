@@ -100,3 +100,25 @@ def test_csc_full_size_sbm_1e5():
     assert np.array_equal(lab, lab2.cpu().numpy())
     # recovery of the planted partition (the oracle pipeline scores ~0.86 on this graph)
     assert oari.ari(lab, g.labels) >= 0.8
+
+
+def test_eigencount_degree_parameter():
+    """m_count sets the degree of step 1's eigencount filter only: csc_cluster's lambda_k is
+    csc_estimate_lambda_k's at that degree, a valid dichotomy answer for the oracle's moments."""
+    g = ci.sbm(1000, 20, seed=1)
+    ref = opipe.csc(g.row_ptr, g.col_idx, 20, seed=1, m_count=150)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        est = csc.csc_estimate_lambda_k(h, 20, 150, seed=1)
+        labels, info = csc.csc_cluster(h, 20, seed=1, m_count=150)
+        _, info50 = csc.csc_cluster(h, 20, seed=1)
+    assert info.lam.lam == est.lam and info.lam.m == 150 and info50.lam.m == 50
+    assert info.lam.hit and abs(info.lam.lam - ref["lam"]) < 1e-9 + 2.0 ** -info.lam.iters
+    assert oari.ari(labels.cpu().numpy(), g.labels) >= 0.9
+
+
+def test_eigencount_degree_parameter_batched():
+    gs = [ci.sbm(600, 6, seed=i) for i in range(3)]
+    with csc.csc_graph_create_batched([(g.row_ptr, g.col_idx) for g in gs]) as h:
+        lam_ref, _ = csc.csc_estimate_lambda_k_batched(h, [6, 6, 6], 120)
+        _, lam, info = csc.csc_cluster_batched(h, [6, 6, 6], m_count=120)
+    assert np.array_equal(lam, lam_ref)
