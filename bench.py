@@ -602,7 +602,8 @@ def run_batched(args):
     sizes = np.array([len(r[1]) - 1 for r in res])
     nnz = int(sum(len(r[2]) for r in res))
     offs = np.concatenate([[0], np.cumsum(sizes)])
-    kw = dict(d=32, d_pad=32, m=50)
+    flags = (csc.CLENSHAW if args.filter == "clenshaw" else 0) | (csc.HIGHPASS if args.interp == "highpass" else 0)
+    kw = dict(d=32, d_pad=32, m=50, flags=flags)
     hb = csc.csc_graph_create_batched([(r[1], r[2]) for r in res])
     singles = [csc.csc_graph_create(r[1], r[2]) for r in res]
     # warm-up: launch-shape tuning of every handle
@@ -636,6 +637,7 @@ def run_batched(args):
            "batched_stage_ms": info.ms, "cg_iters": info.cg.iters, "lambda_hits": info.lambda_hits,
            "ari_batched_mean": float(ari_b.mean()), "ari_separate_mean": float(ari_s.mean()),
            "ari_abs_diff_mean": float(np.abs(ari_b - ari_s).mean()),
+           "filter": args.filter, "interp": args.interp,
            "note": "inputs resident on the device; per-step wall time with a device synchronize"}
     print(json.dumps(out), flush=True)
     for h in singles:

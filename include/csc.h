@@ -579,13 +579,25 @@ CSC_API csc_status csc_interpolate_batched(csc_graph g, const int64_t* sample_id
                                            double rel_tol, int32_t max_iter, int32_t* labels_out, float* fuzzy_out,
                                            csc_cg_info* info, void* stream);
 
+/* csc_interpolate_batched_highpass -- csc_interpolate_highpass per graph: graph i's
+ * systems use g = 1 - h~ with its own cut-off lambda[i] (host double[G], each in
+ * [0, 2]) and the common degree m >= 1; the Clenshaw products of every CG iteration
+ * serve all graphs at once (each row range takes its graph's coefficients).  Other
+ * arguments as csc_interpolate_batched. */
+CSC_API csc_status csc_interpolate_batched_highpass(csc_graph g, const int64_t* sample_idx,
+                                                    const int32_t* sample_labels, int64_t n_total, const int32_t* k,
+                                                    const double* lambda, int32_t m, double gamma, double rel_tol,
+                                                    int32_t max_iter, int32_t* labels_out, float* fuzzy_out,
+                                                    csc_cg_info* info, void* stream);
+
 /* csc_cluster_batched -- Alg. 2 for every graph: csc_estimate_lambda_k_batched,
  * csc_filter_batched (rows normalised), csc_sample_batched with n_i =
  * ceil(2 k_i ln k_i), row gather, csc_kmeans_batched, csc_interpolate_batched.
  * p: the shared parameters of csc_cluster (p->k, p->n, p->lambda_k and
  * p->bracket are ignored; d defaults to ceil(4 ln max_i N_i); p->flags may
- * hold CSC_CLENSHAW, while CSC_HIGHPASS or CSC_VARDENSITY give
- * CSC_E_UNSUPPORTED).  k: host int32[G].  labels_out: device int32[N].
+ * hold CSC_CLENSHAW and CSC_HIGHPASS (each graph interpolated with g = 1 - h~ at
+ * its own lambda_k, as csc_interpolate_batched_highpass), while CSC_VARDENSITY
+ * gives CSC_E_UNSUPPORTED).  k: host int32[G].  labels_out: device int32[N].
  * lambda_out: NULL or host double[G].  info: NULL or host.  Synchronizes. */
 CSC_API csc_status csc_cluster_batched(csc_graph g, const int32_t* k, const csc_params* p, int32_t* labels_out,
                                        double* lambda_out, csc_batch_info* info, void* stream);

@@ -107,6 +107,8 @@ _SIGNATURES = {
     "csc_interpolate_batched": [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int32, c_double, c_double,
                                 c_int32, c_void_p, c_void_p, P(csc_cg_info), c_void_p],
     "csc_cluster_batched": [c_void_p, c_void_p, P(csc_params), c_void_p, c_void_p, P(csc_batch_info), c_void_p],
+    "csc_interpolate_batched_highpass": [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_int32, c_double,
+                                         c_double, c_int32, c_void_p, c_void_p, P(csc_cg_info), c_void_p],
     "csc_interpolate_highpass": [c_void_p, c_void_p, c_void_p, c_int64, c_int32, c_double, c_int32, c_double,
                                  c_double, c_int32, c_void_p, c_void_p, P(csc_cg_info), c_void_p],
     "csc_sample": [c_int64, c_int64, c_uint64, c_void_p, c_void_p],

@@ -543,6 +543,23 @@ def csc_interpolate_batched(g: Graph, sample_idx: torch.Tensor, sample_labels: t
     return labels, fz, CgInfo(info.iters, bool(info.converged), info.max_rel_residual)
 
 
+def csc_interpolate_batched_highpass(g: Graph, sample_idx: torch.Tensor, sample_labels: torch.Tensor, k, lam,
+                                     m: int = 50, gamma: float = 1e-3, rel_tol: float = 1e-6, max_iter: int = 2000,
+                                     fuzzy: bool = False, stream=None):
+    """Per-graph Eq. 5 with g = 1 - h~ at each graph's cut-off lam[i]: (labels, fuzzy or None, CgInfo)."""
+    kk = np.ascontiguousarray(k, dtype=np.int32)
+    ll = np.ascontiguousarray(lam, dtype=np.float64)
+    labels = torch.empty(g.N, dtype=torch.int32, device="cuda")
+    fz = torch.zeros((g.N, int(kk.max())), dtype=torch.float32, device="cuda") if fuzzy else None
+    info = nat.csc_cg_info()
+    check(lib().csc_interpolate_batched_highpass(g.handle, _dptr(sample_idx), _dptr(sample_labels),
+                                                 sample_idx.numel(), _hptr(kk), _hptr(ll), m, gamma, rel_tol,
+                                                 max_iter, _dptr(labels), _dptr(fz), ctypes.byref(info),
+                                                 _stream(stream)),
+          "csc_interpolate_batched_highpass", allow=(nat.CSC_E_NOT_CONVERGED,))
+    return labels, fz, CgInfo(info.iters, bool(info.converged), info.max_rel_residual)
+
+
 @dataclass
 class BatchInfo:
     cg: CgInfo

@@ -303,6 +303,35 @@ csc_status csc_interpolate_batched(csc_graph g, const int64_t* sample_idx, const
     return st;
 }
 
+csc_status csc_interpolate_batched_highpass(csc_graph g, const int64_t* sample_idx, const int32_t* sample_labels,
+                                            int64_t n_total, const int32_t* k, const double* lambda, int32_t m,
+                                            double gamma, double rel_tol, int32_t max_iter, int32_t* labels_out,
+                                            float* fuzzy_out, csc_cg_info* info, void* stream) {
+    clear_error();
+    CSC_TRY(check_batch(g, "csc_interpolate_batched_highpass"));
+    const int G = std::max(1, (int)g->n_graphs);
+    if (!sample_idx || !sample_labels || n_total < 1 || !k || !lambda || m < 1 || !(gamma > 0.0) ||
+        !(rel_tol > 0.0) || max_iter < 1 || !labels_out) {
+        set_error("csc_interpolate_batched_highpass: invalid arguments");
+        return CSC_E_INVALID;
+    }
+    int kmax = 1;
+    std::vector<double> c((size_t)G * (m + 1));
+    for (int i = 0; i < G; ++i) {
+        if (k[i] < 1 || !(lambda[i] >= 0.0 && lambda[i] <= 2.0)) {
+            set_error("csc_interpolate_batched_highpass: graph %d has k < 1 or a cut-off outside [0, 2]", i);
+            return CSC_E_INVALID;
+        }
+        kmax = std::max(kmax, k[i]);
+        cheb_coefficients(lambda[i], m, true, c.data() + (size_t)i * (m + 1));
+    }
+    csc_status st = run_interpolate(g, sample_idx, sample_labels, n_total, kmax, 1, gamma, rel_tol, max_iter,
+                                    labels_out, fuzzy_out, info, (cudaStream_t)stream, G > 1 ? k : nullptr, c.data(),
+                                    m);
+    if (st == CSC_E_CUDA) g->poisoned = true;
+    return st;
+}
+
 csc_status csc_cluster_batched(csc_graph g, const int32_t* k, const csc_params* p, int32_t* labels_out,
                                double* lambda_out, csc_batch_info* info, void* stream) {
     clear_error();
@@ -312,8 +341,8 @@ csc_status csc_cluster_batched(csc_graph g, const int32_t* k, const csc_params* 
         set_error("csc_cluster_batched: invalid arguments");
         return CSC_E_INVALID;
     }
-    if (p->flags & (CSC_HIGHPASS | CSC_VARDENSITY)) {
-        set_error("csc_cluster_batched: CSC_HIGHPASS and CSC_VARDENSITY are single-graph options (csc_cluster)");
+    if (p->flags & CSC_VARDENSITY) {
+        set_error("csc_cluster_batched: CSC_VARDENSITY is a single-graph option (csc_cluster)");
         return CSC_E_UNSUPPORTED;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -403,8 +432,10 @@ csc_status csc_cluster_batched(csc_graph g, const int32_t* k, const csc_params* 
         if (st != CSC_OK) return done(st);
     }
     cudaEventRecord(ev[4], s);
-    st = run_interpolate(g, idx, slab, n_total, kmax, g_power, gamma, cg_tol, cg_max, labels_out, nullptr, &local.cg,
-                         s, G > 1 ? k : nullptr);
+    // CSC_HIGHPASS: g = 1 - h~ with each graph's own cut-off (the filter's coefficients c)
+    const bool hp = (p->flags & CSC_HIGHPASS) != 0;
+    st = run_interpolate(g, idx, slab, n_total, kmax, hp ? 1 : g_power, gamma, cg_tol, cg_max, labels_out, nullptr,
+                         &local.cg, s, G > 1 ? k : nullptr, hp ? c.data() : nullptr, m);
     if (st != CSC_OK && st != CSC_E_NOT_CONVERGED) return done(st);
     cudaEventRecord(ev[5], s);
     cudaError_t ce = cudaEventSynchronize(ev[5]);

@@ -664,11 +664,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const int32_t N = (int32_t)g->N;
     // one independent set of k systems per graph of a batch (k_graphs: each graph's k)
     const int nseg = (k_graphs && g->n_graphs > 1) ? g->n_graphs : 1;
-    const bool hp = hp_coef != nullptr;  // g = 1 - h~ instead of L^p
-    if (hp && nseg > 1) {
-        set_error("the high-pass interpolation runs on one graph at a time");
-        return CSC_E_UNSUPPORTED;
-    }
+    const bool hp = hp_coef != nullptr;  // g = 1 - h~ instead of L^p (per graph for a batch)
     const int ld = ((k + 3) / 4) * 4;
     const int nv = ld / 4;
     // candidate shapes: column tiles of 4*G*NT floats with at most a third idle
@@ -850,7 +846,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const int H = hp ? 0 : (int)g->n_heavy;  // the high-pass A p has no heavy-row slots
     const int PH = P + H;  // <p, A p> partial slots
     PolyOp op;
-    if (hp) CSC_TRY(poly_prepare(g, hp_coef, hp_m, ld, &op, s));
+    if (hp) CSC_TRY(poly_prepare(g, hp_coef, hp_m, ld, &op, s, nseg));
     const dim3 hgrid(H > 0 ? H : 1, cfg.tiles);
     Segs sg;
     sg.P = P;

@@ -222,10 +222,13 @@ csc_status launch_degrees(Graph* g, cudaStream_t s);
 struct PolyOp {
     LaunchCfg cfg;
     const float* coef = nullptr;
+    const int32_t* gid = nullptr;  // batched handle: graph of each row (coef holds one row of m + 1 per graph)
     int m = 0, ld = 0;
     float *b0 = nullptr, *b1 = nullptr, *rs = nullptr;
 };
-csc_status poly_prepare(Graph* g, const double* c, int m, int ld, PolyOp* op, cudaStream_t s);
+// c: host double[n_coef x (m + 1)]; n_coef = 1, or the handle's graph count (graph i's
+// polynomial is applied to graph i's rows).
+csc_status poly_prepare(Graph* g, const double* c, int m, int ld, PolyOp* op, cudaStream_t s, int n_coef = 1);
 csc_status poly_apply(Graph* g, const PolyOp& op, const float* X, float* Y, cudaStream_t s);
 
 // Batched handle: c_graphs is host double[n_graphs x (m + 1)], graph i's coefficients.
@@ -280,6 +283,7 @@ csc_status run_kmeans(const float* X, int64_t n, int d, int ld, int k, int repli
 // cg.cu (K8 + K9).  k_graphs: NULL, or (batched handle) host int32[n_graphs], each
 // graph's k (k = their maximum): one set of systems per graph.  hp_coef: NULL for
 // g(L) = L^g_power, or host double[hp_m + 1], the coefficients of h~ for g = 1 - h~.
+// With k_graphs, hp_coef holds one row of hp_m + 1 coefficients per graph.
 // sample_w: NULL for Eq. 5's 0/1 mask, or device float[n] draw weights (weighted decoder).
 csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* sample_labels,
                            int64_t n, int k, int g_power, double gamma, double rel_tol, int max_iter,

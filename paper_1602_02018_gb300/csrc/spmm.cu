@@ -1232,9 +1232,9 @@ csc_status run_filter_batched(Graph* g, const double* c_graphs, int m, int d, in
 // block X already in internal row order (stride ld, all ld columns), Y likewise, by
 // the Clenshaw form.  poly_prepare uploads the coefficients and settles the launch
 // shape (it may synchronize); poly_apply only launches, so it can be captured.
-csc_status poly_prepare(Graph* g, const double* c, int m, int ld, PolyOp* op, cudaStream_t s) {
-    if (m < 1 || ld % 4) {
-        set_error("polynomial operator: need m >= 1 and ld a multiple of 4");
+csc_status poly_prepare(Graph* g, const double* c, int m, int ld, PolyOp* op, cudaStream_t s, int n_coef) {
+    if (m < 1 || ld % 4 || n_coef < 1 || (n_coef > 1 && n_coef != g->n_graphs)) {
+        set_error("polynomial operator: need m >= 1, ld a multiple of 4 and one coefficient row or one per graph");
         return CSC_E_INVALID;
     }
     const size_t bytes = (size_t)g->N * ld * sizeof(float);
@@ -1242,15 +1242,17 @@ csc_status poly_prepare(Graph* g, const double* c, int m, int ld, PolyOp* op, cu
     CSC_TRY(ws_get(g, WS_XA, bytes, &a));
     CSC_TRY(ws_get(g, WS_XB, bytes, &b));
     CSC_TRY(ws_get(g, WS_XR, bytes, &r));
-    CSC_TRY(ws_get(g, WS_COEF1, (m + 1) * sizeof(float), &dc));
-    std::vector<float> hc(m + 1);
-    for (int j = 0; j <= m; ++j) hc[j] = (float)c[j];
-    CSC_CUDA_TRY(cudaMemcpyAsync(dc, hc.data(), (m + 1) * sizeof(float), cudaMemcpyHostToDevice, s));
+    const size_t nc = (size_t)n_coef * (m + 1);
+    CSC_TRY(ws_get(g, WS_COEF1, nc * sizeof(float), &dc));
+    std::vector<float> hc(nc);
+    for (size_t j = 0; j < nc; ++j) hc[j] = (float)c[j];
+    CSC_CUDA_TRY(cudaMemcpyAsync(dc, hc.data(), nc * sizeof(float), cudaMemcpyHostToDevice, s));
     CSC_CUDA_TRY(cudaStreamSynchronize(s));
     op->b0 = (float*)a;
     op->b1 = (float*)b;
     op->rs = (float*)r;
     op->coef = (const float*)dc;
+    op->gid = n_coef > 1 ? g->graph_of_row : nullptr;
     op->m = m;
     op->ld = ld;
     // launch shape: the Clenshaw order's tuned shape for this column count
@@ -1270,6 +1272,8 @@ csc_status poly_apply(Graph* g, const PolyOp& op, const float* X, float* Y, cuda
     const int64_t tot = N * ld;
     CoefTab<float> tab;
     tab.c = op.coef;
+    tab.gid = op.gid;
+    tab.stride = m + 1;
     CoefTab<float> ft = tab;
     ft.j = m;
     // s X and B_m = c_m s X (internal order: no permutation)

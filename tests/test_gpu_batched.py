@@ -224,3 +224,49 @@ def test_clenshaw_per_graph_cutoffs_match_oracle(storage, tol):
         ref = och.cheb_filter(s, ri, och.filter_coeffs(lam[i], m))
         err = np.linalg.norm(y[OFFS[i]:OFFS[i + 1]] - ref)
         assert err <= tol * np.linalg.norm(ref) + FLOOR[storage] * np.linalg.norm(ri), i
+
+
+def test_interpolation_highpass_per_graph_matches_oracle():
+    """Each graph's systems use g = 1 - h~ at its own cut-off; the residual recomputed
+    by the oracle's high-pass operator on that graph alone."""
+    gamma, m = 1e-3, 30
+    lam = np.linspace(0.25, 0.9, len(BATCH))
+    n = [min(g.n, max(k, math.ceil(2 * k * math.log(k))) if k > 1 else 1) for g, k in BATCH]
+    oms = [osamp.sample(g.n, n[i], 5 + i) for i, (g, _) in enumerate(BATCH)]
+    labs = [(g.labels[om] if g.labels is not None else om % k).astype(np.int32) for (g, k), om in zip(BATCH, oms)]
+    idx = np.concatenate([om + OFFS[i] for i, om in enumerate(oms)])
+    with _handle() as h:
+        labels, fz, info = csc.csc_interpolate_batched_highpass(h, torch.from_numpy(idx).cuda(),
+                                                                torch.from_numpy(np.concatenate(labs)).cuda(), KS,
+                                                                lam, m, gamma, 1e-7, 5000, fuzzy=True)
+    assert info.converged
+    labels, fz = labels.cpu().numpy(), fz.cpu().numpy()
+    for i, (g, k) in enumerate(BATCH):
+        s = olap.normalized_adjacency(g.row_ptr, g.col_idx)
+        x = fz[OFFS[i]:OFFS[i + 1], :k].astype(np.float64)
+        b = ointerp.rhs(g.n, oms[i], labs[i], k)
+        res = ointerp.apply_highpass(s, ointerp.mask(g.n, oms[i]), gamma, lam[i], m, x) - b
+        bn = np.linalg.norm(b, axis=0)
+        # a cluster with no sample has b = 0 and the solution 0: its residual is checked absolutely
+        rres = np.linalg.norm(res, axis=0) / np.where(bn > 0, bn, 1.0)
+        assert np.max(rres) <= 3e-6, i
+        assert np.all(x[:, bn == 0] == 0), i
+        assert np.array_equal(labels[OFFS[i]:OFFS[i + 1]], ointerp.labels_from_indicators(x)), i
+
+
+def test_cluster_batched_highpass_matches_separate_runs():
+    gs = [ci.sbm(n, k, seed=10 + i) for i, (n, k) in enumerate([(1200, 12), (2000, 20), (900, 9), (3000, 15)])]
+    ks = [12, 20, 9, 15]
+    with csc.csc_graph_create_batched([(g.row_ptr, g.col_idx) for g in gs]) as h:
+        lb, lam, info = csc.csc_cluster_batched(h, ks, seed=3, flags=csc.HIGHPASS)
+    assert info.cg.converged
+    lb = lb.cpu().numpy()
+    offs = np.concatenate([[0], np.cumsum([g.n for g in gs])])
+    a_b, a_s = [], []
+    for i, (g, k) in enumerate(zip(gs, ks)):
+        a_b.append(oari.ari(lb[offs[i]:offs[i + 1]], g.labels))
+        with csc.csc_graph_create(g.row_ptr, g.col_idx) as h1:
+            l1, i1 = csc.csc_cluster(h1, k, seed=3 + i, flags=csc.HIGHPASS)
+        a_s.append(oari.ari(l1.cpu().numpy(), g.labels))
+    assert abs(np.mean(a_b) - np.mean(a_s)) <= 0.03
+    assert np.mean(a_b) >= 0.85
