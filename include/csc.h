@@ -488,8 +488,9 @@ CSC_API csc_status csc_interpolate(csc_graph g, const int64_t* sample_idx, const
  * Jackson-Chebyshev low-pass of degree m at lambda_c (the filter of Alg. 2 step 4),
  * so every CG iteration applies h~(L) to the k columns (m sparse products, Clenshaw
  * form) and A p = mask p + gamma (p - h~(L) p).  Arguments as csc_interpolate,
- * with lambda_c in [0, 2] and m >= 1 instead of g_power.  One graph per handle
- * (a batched handle is rejected with CSC_E_UNSUPPORTED). */
+ * with lambda_c in [0, 2] and m >= 1 instead of g_power.  On a batched handle
+ * the packed graph is one graph here (one cut-off, one set of k systems); per-graph
+ * systems are csc_interpolate_batched_highpass. */
 CSC_API csc_status csc_interpolate_highpass(csc_graph g, const int64_t* sample_idx, const int32_t* sample_labels,
                                             int64_t n, int32_t k, double lambda_c, int32_t m, double gamma,
                                             double rel_tol, int32_t max_iter, int32_t* labels_out,
