@@ -846,7 +846,11 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const int H = hp ? 0 : (int)g->n_heavy;  // the high-pass A p has no heavy-row slots
     const int PH = P + H;  // <p, A p> partial slots
     PolyOp op;
-    if (hp) CSC_TRY(poly_prepare(g, hp_coef, hp_m, ld, &op, s, nseg));
+    if (hp) {
+        CSC_TRY(poly_prepare(g, hp_coef, hp_m, ld, &op, s, nseg));
+        // a batch's graphs carry only their own k columns (rounded up to 4) through h~
+        if (nseg > 1) op.gcols = d_gk + nseg;
+    }
     const dim3 hgrid(H > 0 ? H : 1, cfg.tiles);
     Segs sg;
     sg.P = P;

@@ -223,6 +223,7 @@ struct PolyOp {
     LaunchCfg cfg;
     const float* coef = nullptr;
     const int32_t* gid = nullptr;  // batched handle: graph of each row (coef holds one row of m + 1 per graph)
+    const int32_t* gcols = nullptr;  // with gid: columns each graph carries (multiple of 4); NULL: all
     int m = 0, ld = 0;
     float *b0 = nullptr, *b1 = nullptr, *rs = nullptr;
 };

@@ -79,7 +79,8 @@ struct CoefTab {
     const A* c = nullptr;
     const int32_t* gid = nullptr;
     int stride = 0;
-    int j = 0;  // index of c_next; c_0 at 0
+    int j = 0;                        // index of c_next; c_0 at 0
+    const int32_t* gcols = nullptr;   // with gid: columns each graph carries (the rest are not touched)
 };
 
 // ------------------------------------------------------------------- K3
@@ -471,8 +472,11 @@ clenshaw_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__
     constexpr int TW = G * NT * VEC;
     const int lane = threadIdx.x % G;
     const int col0 = blockIdx.y * TW;
-    const int tcols = min(TW, ncols - col0);
     const int r0 = part[blockIdx.x], r1 = part[blockIdx.x + 1];
+    // a batch whose graphs carry fewer columns than the block: only the range's graph's
+    const int ncols_b = (tab.gcols && r0 < r1) ? min(ncols, tab.gcols[tab.gid[r0]]) : ncols;
+    const int tcols = min(TW, ncols_b - col0);
+    if (tcols <= 0) return;
     if (tab.c && r0 < r1) cj = (tab.gid ? tab.c + (int64_t)tab.gid[r0] * tab.stride : tab.c)[tab.j];
     const unsigned gmask =
         G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(unsigned)(G - 1)));
@@ -500,8 +504,9 @@ clenshaw_step_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __rest
     constexpr int TW = G * NT * VEC;
     const int lane = threadIdx.x % G;
     const int col0 = blockIdx.y * TW;
-    const int tcols = min(TW, ncols - col0);
     const int row = heavy[blockIdx.x];
+    const int tcols = min(TW, (tab.gcols ? min(ncols, tab.gcols[tab.gid[row]]) : ncols) - col0);
+    if (tcols <= 0) return;
     if (tab.c) cj = (tab.gid ? tab.c + (int64_t)tab.gid[row] * tab.stride : tab.c)[tab.j];
     A acc[NT][VEC];
     gather_heavy<T, G, NT, false, A>(__ldg(rp + row), __ldg(rp + row + 1), ci, nullptr, bnext + col0, ld, lane, tcols,
@@ -1274,6 +1279,7 @@ csc_status poly_apply(Graph* g, const PolyOp& op, const float* X, float* Y, cuda
     tab.c = op.coef;
     tab.gid = op.gid;
     tab.stride = m + 1;
+    tab.gcols = op.gid ? op.gcols : nullptr;
     CoefTab<float> ft = tab;
     ft.j = m;
     // s X and B_m = c_m s X (internal order: no permutation)
