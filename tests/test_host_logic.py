@@ -84,3 +84,20 @@ def test_workload_defaults_agree():
         b = pipeline.defaults(n_nodes, k)
         w = ci.workload_sizes(n_nodes, k)
         assert a["d"] == b["d"] == w["d"] and a["n"] == b["n"] == w["n"] and a["n_probes"] == b["n_v"] == w["n_v"]
+
+
+def test_sweep_tables_format():
+    """The recovery-sweep report renders every table from a result dictionary."""
+    from tests import fig1_sweep as fs
+
+    var = fs.variants()
+    row = dict(csc={("def", None): 0.9, ("hp", None): 0.95}, sc=1.0, lam_est=0.4, lk=0.3, lk1=0.5, est_in_gap=1.0)
+    for f, (_, vals) in var.items():
+        for v in vals:
+            row["csc"][(f, v)] = 0.8
+    res = {"hom": {0.02: row}, "het": {0.0: row},
+           "fg": {(1000, 20): {t: dict(ari=0.9, ms=4.0, wall_s=0.004) for t in ("l4", "hp", "hp200")}},
+           "fg_sc": dict(ari=0.99, sec=0.3)}
+    text = fs.format_tables(res, 3)
+    for needle in ("Fig. 1 a", "Fig. 1 d", "Fig. 1 e", "Heterogeneous SBM", "Fig. 1 f-g", "SC (Alg. 1"):
+        assert needle in text

@@ -209,3 +209,17 @@ def test_common_scale_of_weights_and_gamma_cancels():
     x1, _, _ = interp.interpolate_weighted(lap, om, lab, w, 3, 1e-3, 4, tol=1e-13)
     x2, _, _ = interp.interpolate_weighted(lap, om, lab, w * np.float32(8), 3, 8e-3, 4, tol=1e-13)
     assert np.linalg.norm(x1 - x2) / np.linalg.norm(x1) < 1e-8
+
+
+def test_pipeline_with_variable_density_recovers_planted_communities():
+    """Alg. 2 with variable-density draws and the weighted decoder, end to end in the
+    oracle: the planted communities of a small SBM are recovered and the draws carry
+    weights Q / (N q) (a sanity check of the wiring; no printed value to pin to)."""
+    from oracle import ari, pipeline
+
+    g = ci.sbm(400, 4, s=12.0, seed=7)
+    out = pipeline.csc(g.row_ptr, g.col_idx, 4, seed=1, variable_density=True, replicates=5, n=40)
+    assert ari.ari(out["labels"], g.labels) >= 0.9
+    q = sampling.quantize_scores(sampling.coherence_scores(out["y"]))
+    assert np.array_equal(out["weights"], sampling.decoder_weights(q, out["omega"]))
+    assert len(out["omega"]) == out["params"]["n"]
