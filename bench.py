@@ -440,10 +440,12 @@ def run_precision(args, w):
     lam = csc.csc_estimate_lambda_k(h, k, m, 0, args.seed).lam
     out = {"workload": args.workload, "N": g.n, "nnz": g.nnz, "k": k, "m": m, "d": d, "d_pad": d_pad,
            "lambda_k": lam, "rcm": bool(flags), "storage": {}}
+    out["filter"] = args.filter
+    fflags = csc.NORMALIZE_ROWS | (csc.CLENSHAW if args.filter == "clenshaw" else 0)
     ys = {}
     for name, st in (("f64", csc.F64), ("f32", csc.F32), ("bf16", csc.BF16)):
         for _ in range(2):
-            y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, seed=args.seed, storage=st)
+            y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, seed=args.seed, storage=st, flags=fflags)
         torch.cuda.synchronize()
         csc.csc_profile_reset()
         csc.csc_profile_enable(True)
@@ -451,7 +453,7 @@ def run_precision(args, w):
         e0.record()
         reps = 3
         for _ in range(reps):
-            y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, seed=args.seed, storage=st)
+            y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, seed=args.seed, storage=st, flags=fflags)
         e1.record()
         torch.cuda.synchronize()
         csc.csc_profile_enable(False)
@@ -470,7 +472,8 @@ def run_precision(args, w):
     labs = {}
     for name, st in (("f32", csc.F32), ("bf16", csc.BF16)):
         t0 = time.perf_counter()
-        lab, info = csc.csc_cluster(h, k, m=m, d=d, d_pad=d_pad, storage=st, seed=args.seed)
+        lab, info = csc.csc_cluster(h, k, m=m, d=d, d_pad=d_pad, storage=st, seed=args.seed,
+                                    flags=csc.CLENSHAW if args.filter == "clenshaw" else 0)
         torch.cuda.synchronize()
         out["storage"][name]["csc_seconds"] = time.perf_counter() - t0
         out["storage"][name]["cg_iters"] = info.cg.iters
