@@ -62,9 +62,10 @@ struct KmShared {
 
 // Dynamic shared memory of one CTA.
 struct KmLayout {
-    size_t cen, sums, counts, empty, d2, lab, nlab, total;
+    size_t cen, sums, counts, empty, d2, lab, nlab, xs, total;
     static __host__ __device__ size_t al(size_t x) { return (x + 15) / 16 * 16; }
-    __host__ __device__ KmLayout(int k, int d, int own_k, int n_loc) {
+    // stage_x: the CTA's points are copied into shared memory (rows of d floats)
+    __host__ __device__ KmLayout(int k, int d, int own_k, int n_loc, bool stage_x) {
         cen = 0;
         sums = al(cen + (size_t)k * d * 4);
         counts = al(sums + (size_t)own_k * d * 8);
@@ -72,7 +73,8 @@ struct KmLayout {
         d2 = al(empty + (size_t)k * 4);
         lab = al(d2 + (size_t)n_loc * 8);
         nlab = al(lab + (size_t)n_loc * 4);
-        total = al(nlab + (size_t)n_loc * 4);
+        xs = al(nlab + (size_t)n_loc * 4);
+        total = al(xs + (stage_x ? (size_t)n_loc * d * 4 : 0));
     }
 };
 
@@ -113,7 +115,7 @@ struct KmProblem {
 };
 
 __global__ void __launch_bounds__(kKmThreads)
-kmeans_cluster_kernel(const KmProblem* __restrict__ probs, int d, int ld, int max_iter) {
+kmeans_cluster_kernel(const KmProblem* __restrict__ probs, int d, int ld, int max_iter, int stage_x) {
     const KmProblem pr = probs[blockIdx.y];
     const float* __restrict__ X = pr.X;
     const int n = pr.n, k = pr.k;
@@ -129,7 +131,7 @@ kmeans_cluster_kernel(const KmProblem* __restrict__ probs, int d, int ld, int ma
     const int T = threadIdx.x;
     const int own_k = (k + C - 1) / C;
     const int n_loc = (n + C - 1) / C;
-    const KmLayout L(k, d, own_k, n_loc);
+    const KmLayout L(k, d, own_k, n_loc, stage_x != 0);
     float* Cen = (float*)(smem + L.cen);
     unsigned long long* sums = (unsigned long long*)(smem + L.sums);
     int* counts = (int*)(smem + L.counts);
@@ -139,6 +141,17 @@ kmeans_cluster_kernel(const KmProblem* __restrict__ probs, int d, int ld, int ma
     int* nlab = (int*)(smem + L.nlab);
     const int i0 = rank * n_loc;
     const int cnt = max(0, min(n, i0 + n_loc) - i0);  // this CTA's points: i0 .. i0+cnt-1
+    // the CTA's points, read by every seeding draw and Lloyd step: staged into shared
+    // memory (rows of d floats) when they fit, else read in place (rows of ld)
+    const float* Xl = X + (int64_t)i0 * ld;
+    int ldl = ld;
+    if (stage_x) {
+        float* xs = (float*)(smem + L.xs);
+        for (int64_t t = T; t < (int64_t)cnt * d; t += kKmThreads) xs[t] = Xl[(t / d) * ld + t % d];
+        Xl = xs;
+        ldl = d;
+        __syncthreads();
+    }
 
     // fixed-point scale for exact centre sums: n * max|x| * scale < 2^62 (cluster-wide max)
     {
@@ -170,7 +183,7 @@ kmeans_cluster_kernel(const KmProblem* __restrict__ probs, int d, int ld, int ma
         const int p0 = min((int)(u0 * (double)n), n - 1);
         for (int q = T; q < d; q += kKmThreads) Cen[q] = X[(int64_t)p0 * ld + q];
         __syncthreads();
-        for (int i = T; i < cnt; i += kKmThreads) d2[i] = (double)sqdist(X + (int64_t)(i0 + i) * ld, Cen, d);
+        for (int i = T; i < cnt; i += kKmThreads) d2[i] = (double)sqdist(Xl + (int64_t)i * ldl, Cen, d);
         __syncthreads();
     }
     const int chunk = (cnt + kKmThreads - 1) / kKmThreads;
@@ -216,7 +229,7 @@ kmeans_cluster_kernel(const KmProblem* __restrict__ probs, int d, int ld, int ma
         for (int q = T; q < d; q += kKmThreads) Cen[t * d + q] = X[(int64_t)p * ld + q];
         __syncthreads();
         for (int i = T; i < cnt; i += kKmThreads) {
-            const double dd = (double)sqdist(X + (int64_t)(i0 + i) * ld, Cen + t * d, d);
+            const double dd = (double)sqdist(Xl + (int64_t)i * ldl, Cen + t * d, d);
             if (dd < d2[i]) d2[i] = dd;
         }
         __syncthreads();
@@ -237,7 +250,7 @@ kmeans_cluster_kernel(const KmProblem* __restrict__ probs, int d, int ld, int ma
             float best = INFINITY;
             int bj = 0x7fffffff;
             if (valid) {
-                const float* x = X + (int64_t)(i0 + pt) * ld;
+                const float* x = Xl + (int64_t)pt * ldl;
                 for (int j = sub; j < k; j += kKmLanesPerPoint) {
                     const float dj = sqdist(x, Cen + j * d, d);
                     if (dj < best) {
@@ -273,7 +286,7 @@ kmeans_cluster_kernel(const KmProblem* __restrict__ probs, int d, int ld, int ma
             const int owner = j % C, slot = j / C;
             unsigned long long* rs = cluster.map_shared_rank(sums, owner) + (size_t)slot * d;
             atomicAdd(cluster.map_shared_rank(counts, owner) + slot, 1);
-            const float* x = X + (int64_t)(i0 + i) * ld;
+            const float* x = Xl + (int64_t)i * ldl;
             for (int q = 0; q < d; ++q) {
                 const long long v = llrint((double)x[q] * scale);
                 atomicAdd(rs + q, (unsigned long long)v);
@@ -304,7 +317,7 @@ kmeans_cluster_kernel(const KmProblem* __restrict__ probs, int d, int ld, int ma
             float bv = -1.f;
             int bi = 0x7fffffff;
             for (int i = T; i < cnt; i += kKmThreads) {
-                const float v = sqdist(X + (int64_t)(i0 + i) * ld, Cen + lab[i] * d, d);
+                const float v = sqdist(Xl + (int64_t)i * ldl, Cen + lab[i] * d, d);
                 if (v > bv) {
                     bv = v;
                     bi = i0 + i;
@@ -367,7 +380,7 @@ kmeans_cluster_kernel(const KmProblem* __restrict__ probs, int d, int ld, int ma
     }
     // inertia: fp32 distances, fp64 sums in a fixed order; labels
     double in = 0.0;
-    for (int i = T; i < cnt; i += kKmThreads) in += (double)sqdist(X + (int64_t)(i0 + i) * ld, Cen + lab[i] * d, d);
+    for (int i = T; i < cnt; i += kKmThreads) in += (double)sqdist(Xl + (int64_t)i * ldl, Cen + lab[i] * d, d);
     in = warp_sum(in);
     if ((T & 31) == 0) S.scan_w[T >> 5] = in;
     __syncthreads();
@@ -429,10 +442,14 @@ csc_status run_kmeans_multi(const std::vector<KmTask>& tasks, int d, int ld, int
     while (C > 1 && (n_min + C - 1) / C < 16) --C;
     size_t smem = 0;
     for (;; --C) {
-        const KmLayout L(k_max, d, (k_max + C - 1) / C, (n_max + C - 1) / C);
+        const KmLayout L(k_max, d, (k_max + C - 1) / C, (n_max + C - 1) / C, false);
         smem = L.total;
         if (smem <= 200 * 1024 || C == 1) break;
     }
+    // stage each CTA's points in shared memory when they fit beside the rest
+    const KmLayout Ls(k_max, d, (k_max + C - 1) / C, (n_max + C - 1) / C, true);
+    const int stage_x = Ls.total <= 200 * 1024 ? 1 : 0;
+    if (stage_x) smem = Ls.total;
     if (smem > 200 * 1024) {
         set_error("k-means: k*d = %d with n = %d needs %zu bytes of shared memory per CTA", k_max * d, n_max, smem);
         return CSC_E_UNSUPPORTED;
@@ -495,7 +512,7 @@ csc_status run_kmeans_multi(const std::vector<KmTask>& tasks, int d, int ld, int
     for (const KmTask& t : tasks) pts += (double)t.n;
     CSC_KLAUNCH("kmeans", 4.0 * pts * d * reps, s,
                 CSC_CUDA_TRY(cudaLaunchKernelEx(&cfg, kmeans_cluster_kernel, (const KmProblem*)d_probs, d, ld,
-                                                max_iter)));
+                                                max_iter, stage_x)));
     CSC_KLAUNCH("kmeans_pick", 8.0 * pts, s,
                 kmeans_pick_kernel<<<dim3(1, NP), 256, 0, s>>>(d_probs, reps, d_outs, d_best));
     std::vector<double> hb;
