@@ -156,3 +156,17 @@ def test_ari_pins():
     perm = np.array([3, 1, 4, 0, 2])
     assert ari.ari(u, v) == pytest.approx(ari.ari(perm[u], v), abs=1e-15)
     assert abs(ari.ari(u, v)) < 0.05
+
+
+@pytest.mark.parametrize("k,size,n", [(6, 12, 36), (4, 25, 30), (10, 8, 60)])
+def test_pipeline_exact_on_disjoint_cliques(k, size, n):
+    """Alg. 2 end to end where the answer is fixed: k disjoint cliques have lambda_1..k = 0
+    and lambda_k+1 = size/(size-1), so the eigencount stops inside the gap, the filtered
+    features are the clique indicators, and every clique holding a sample is recovered."""
+    from oracle import pipeline
+
+    g = ci.disjoint_cliques(k, size)
+    out = pipeline.csc(g.row_ptr, g.col_idx, k, seed=3, n=n, replicates=5)
+    assert out["est"]["hit"] and 0.0 < out["lam"] < size / (size - 1)
+    assert len(set(g.labels[out["omega"]])) == k
+    assert ari.ari(out["labels"], g.labels) == 1.0
