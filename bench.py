@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f64"])
     ap.add_argument("--interp", default="l4", choices=["l4", "highpass"],
                     help="interpolation regulariser: g(L) = L^4 (default) or the paper's g = 1 - h~ at lambda_k")
+    ap.add_argument("--interp-degree", type=int, default=0,
+                    help="with --interp highpass: degree of h~ inside the CG (default: the filter's m)")
     ap.add_argument("--sampling", default="uniform", choices=["uniform", "variable"],
                     help="uniform sampling of Eq. 4 (default) or variable-density draws with the weighted decoder")
     ap.add_argument("--filter", default="clenshaw", choices=["forward", "clenshaw"],
@@ -282,7 +284,7 @@ def run_ours(args, w, rank, world, local_rank):
 
     def step():
         return csc.csc_cluster(h, k, m=m, d=d, d_pad=d_pad, n=n, storage=storage, seed=args.seed + rank,
-                               flags=fflags)
+                               flags=fflags, m_interp=args.interp_degree)
 
     for _ in range(args.warmup):
         labels, info = step()
@@ -365,7 +367,7 @@ def run_ours(args, w, rank, world, local_rank):
             t0 = time.perf_counter()
             h2 = csc.csc_graph_create(rp_pin.numpy(), ci_pin.numpy(), flags)
             labs, _ = csc.csc_cluster(h2, k, m=m, d=d, d_pad=d_pad, n=n, storage=storage, seed=args.seed + rank,
-                                      flags=fflags)
+                                      flags=fflags, m_interp=args.interp_degree)
             lab_host.copy_(labs)
             torch.cuda.synchronize()
             h2.close()
@@ -400,7 +402,8 @@ def run_ours(args, w, rank, world, local_rank):
                        "l2": "flushed between steps (512 MB write)",
                        "value_basis": "m*nnz*d / device time of the filter stage of each timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "filter": args.filter, "interp": args.interp, "sampling": args.sampling},
+                       "filter": args.filter, "interp": args.interp, "sampling": args.sampling,
+                       "interp_degree": args.interp_degree or m},
             "csc_seconds": ms_step / 1e3,
             "filter_ms": ms_filter,
             "stages_ms": {kk: statistics.mean(x.ms[kk] for x in infos) for kk in infos[0].ms},

@@ -127,6 +127,8 @@ typedef struct {
                               every eigenvalue above the cut-off into the count, which on
                               graphs of ~1e6 nodes can alone reach k: a higher degree
                               (e.g. 4 m) sharpens it for a few extra moment passes      */
+    int32_t  m_interp;     /* CSC_HIGHPASS: degree of h~ inside g = 1 - h~; default m.
+                              Each CG iteration costs m_interp sparse products          */
 } csc_params;
 
 /* Per-stage results and timings of csc_cluster. */

@@ -55,7 +55,7 @@ class csc_params(ctypes.Structure):
                 ("n_probes", c_int32), ("g_power", c_int32), ("gamma", c_double), ("cg_tol", c_double),
                 ("cg_max_iter", c_int32), ("replicates", c_int32), ("km_max_iter", c_int32),
                 ("storage", c_int32), ("seed", c_uint64), ("lambda_k", c_double), ("bracket", P(c_double)),
-                ("flags", c_uint32), ("m_count", c_int32)]
+                ("flags", c_uint32), ("m_count", c_int32), ("m_interp", c_int32)]
 
 
 class csc_batch_info(ctypes.Structure):

@@ -446,12 +446,12 @@ def csc_cluster(g: Graph, k: int, m: int = 0, d: int = 0, d_pad: int = 0, n: int
                 g_power: int = 0, gamma: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0,
                 replicates: int = 0, km_max_iter: int = 0, storage: int = F32, seed: int = 0,
                 lambda_k: float = 0.0, bracket=None, labels_out: Optional[torch.Tensor] = None, flags: int = 0,
-                m_count: int = 0, stream=None):
+                m_count: int = 0, m_interp: int = 0, stream=None):
     """Alg. 2 end to end; zero arguments take the library defaults.  Returns (labels, ClusterInfo)."""
     p = nat.csc_params()
     p.k, p.m, p.d, p.d_pad, p.n, p.n_probes, p.g_power = k, m, d, d_pad, n, n_probes, g_power
     p.gamma, p.cg_tol, p.cg_max_iter, p.replicates, p.km_max_iter = gamma, cg_tol, cg_max_iter, replicates, km_max_iter
-    p.storage, p.seed, p.lambda_k, p.flags, p.m_count = storage, seed, lambda_k, flags, m_count
+    p.storage, p.seed, p.lambda_k, p.flags, p.m_count, p.m_interp = storage, seed, lambda_k, flags, m_count, m_interp
     br_arr = None
     if bracket is not None:
         br_arr = np.ascontiguousarray(bracket, dtype=np.float64)
@@ -571,13 +571,13 @@ def csc_cluster_batched(g: Graph, k, m: int = 0, d: int = 0, d_pad: int = 0, n_p
                         gamma: float = 0.0, cg_tol: float = 0.0, cg_max_iter: int = 0, replicates: int = 0,
                         km_max_iter: int = 0, storage: int = F32, seed: int = 0,
                         labels_out: Optional[torch.Tensor] = None, flags: int = 0, m_count: int = 0,
-                        stream=None):
+                        m_interp: int = 0, stream=None):
     """Alg. 2 for every graph of a batched handle.  Returns (labels, lambda float64[G], BatchInfo)."""
     kk = np.ascontiguousarray(k, dtype=np.int32)
     p = nat.csc_params()
     p.k, p.m, p.d, p.d_pad, p.n, p.n_probes, p.g_power = 0, m, d, d_pad, 0, n_probes, g_power
     p.gamma, p.cg_tol, p.cg_max_iter, p.replicates, p.km_max_iter = gamma, cg_tol, cg_max_iter, replicates, km_max_iter
-    p.storage, p.seed, p.lambda_k, p.flags, p.m_count = storage, seed, 0.0, flags, m_count
+    p.storage, p.seed, p.lambda_k, p.flags, p.m_count, p.m_interp = storage, seed, 0.0, flags, m_count, m_interp
     if labels_out is None:
         labels_out = torch.empty(g.N, dtype=torch.int32, device="cuda")
     lam = np.empty(g.n_graphs, dtype=np.float64)

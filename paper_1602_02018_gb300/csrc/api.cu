@@ -1371,12 +1371,13 @@ csc_status csc_cluster(csc_graph g, const csc_params* p, int32_t* labels_out, cs
     if (st != CSC_OK) return done(st);
     cudaEventRecord(e4, s);
     std::vector<double> hpc;
+    const int m_hp = p->m_interp > 0 ? p->m_interp : m;
     if (p->flags & CSC_HIGHPASS) {
-        hpc.resize(m + 1);
-        cheb_coefficients(lam, m, true, hpc.data());
+        hpc.resize(m_hp + 1);
+        cheb_coefficients(lam, m_hp, true, hpc.data());
     }
     st = run_interpolate(g, idx, slab, n, k, g_power, gamma, cg_tol, cg_max, labels_out, nullptr, &local.cg, s,
-                         nullptr, hpc.empty() ? nullptr : hpc.data(), m, wdraw);
+                         nullptr, hpc.empty() ? nullptr : hpc.data(), m_hp, wdraw);
     if (st != CSC_OK && st != CSC_E_NOT_CONVERGED) return done(st);
     cudaEventRecord(e5, s);
     cudaError_t ce = cudaEventSynchronize(e5);

@@ -432,10 +432,18 @@ csc_status csc_cluster_batched(csc_graph g, const int32_t* k, const csc_params* 
         if (st != CSC_OK) return done(st);
     }
     cudaEventRecord(ev[4], s);
-    // CSC_HIGHPASS: g = 1 - h~ with each graph's own cut-off (the filter's coefficients c)
+    // CSC_HIGHPASS: g = 1 - h~ with each graph's own cut-off, at degree m_interp (default m:
+    // the filter's coefficients c)
     const bool hp = (p->flags & CSC_HIGHPASS) != 0;
+    const int m_hp = p->m_interp > 0 ? p->m_interp : m;
+    std::vector<double> chp;
+    if (hp && m_hp != m) {
+        chp.resize((size_t)G * (m_hp + 1));
+        for (int i = 0; i < G; ++i) cheb_coefficients(lam[i], m_hp, true, chp.data() + (size_t)i * (m_hp + 1));
+    }
     st = run_interpolate(g, idx, slab, n_total, kmax, hp ? 1 : g_power, gamma, cg_tol, cg_max, labels_out, nullptr,
-                         &local.cg, s, G > 1 ? k : nullptr, hp ? c.data() : nullptr, m);
+                         &local.cg, s, G > 1 ? k : nullptr, hp ? (chp.empty() ? c.data() : chp.data()) : nullptr,
+                         m_hp);
     if (st != CSC_OK && st != CSC_E_NOT_CONVERGED) return done(st);
     cudaEventRecord(ev[5], s);
     cudaError_t ce = cudaEventSynchronize(ev[5]);
