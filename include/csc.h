@@ -119,7 +119,7 @@ typedef struct {
     double   lambda_k;     /* > 0: skip step 1 and use this cut-off                   */
     const double* bracket; /* NULL or host {lo, hi}: learned bracket for step 1       */
     uint32_t flags;        /* CSC_CLENSHAW: filter by Clenshaw's recurrence; CSC_HIGHPASS:
-                              interpolate with g = 1 - h~ at lambda_k, degree m;
+                              interpolate with g = 1 - h~ at lambda_k (degree m_interp);
                               CSC_VARDENSITY: csc_coherence_scores, csc_sample_weighted
                               and the weighted decoder in place of uniform sampling     */
     int32_t  m_count;      /* degree of the eigencount filter of step 1 (Sec. 4.3 does
