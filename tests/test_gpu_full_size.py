@@ -1,8 +1,23 @@
 """The filter at the power-law workload's full size (Chung-Lu N = 1e6, degree exponent
 2.1, mean degree 6, RCM-reordered CSR, m = 100, d = 56, Clenshaw form, autotuned launch
-shape as bench.py runs it), checked on sampled outputs: the columns of Y = h~(L) R are
-independent, so the FP64 oracle filters two sampled columns alone (Sec. 2.1 recurrence)
-and they are compared with the GPU's whole-block result."""
+shape as bench.py runs it), checked on sampled outputs the FP64 oracle computes one by one:
+
+* columns: the columns of Y = h~(L) R are independent, so the oracle filters a few sampled
+  columns alone (Sec. 2.1 recurrence);
+* rows: h~(L) is symmetric, so row i of Y is (h~(L) e_i)^T R, and the oracle filters the
+  basis vectors of a few sampled rows to get those rows of Y, then normalises them
+  (Alg. 2 step 4).
+
+Tolerances.  On this graph the pass band below lambda_k = 0.0597 holds about 100 of the
+1e6 eigenvalues, so ||Y|| is about 0.007 ||R|| while every order rounds blocks of the size
+of R.  The storage model of tests/storage_emulation.py (every stored block rounded, FP32
+arithmetic) measures what the storage type alone costs on the same columns; the GPU must
+stay within 1.5 times that.  FP32 storage: the filtered signals Y meet the 1e-5 target
+(the model gives 3.1e-6 over all 56 columns), and the GPU must also meet it outright.  Row
+normalisation divides every row by its filtered energy, which amplifies the same rounding
+to 4.1e-5 in the model over all rows (per-row error at most 2.2e-4); the sampled
+normalised rows are held to 1.5 times that largest per-row error.  BF16 storage is held
+to 1.5 times the model's error on the same columns."""
 import numpy as np
 import pytest
 import torch
@@ -12,6 +27,7 @@ from oracle import chebyshev as och
 from oracle import laplacian as olap
 
 from .helpers import rel
+from .storage_emulation import clenshaw_stored
 
 pytestmark = pytest.mark.gpu
 
@@ -19,6 +35,12 @@ csc = pytest.importorskip("paper_1602_02018_gb300")
 
 N, D, M, LAM = 1_000_000, 56, 100, 0.0597
 COLS = [0, 37]
+ROW_SEED = 5
+N_ROWS = 6
+FP32_TARGET = 1e-5
+# largest per-row error of the normalised features in the FP32 storage model over all
+# 1e6 rows and 56 columns (same graph, signals and cut-off)
+FP32_MODEL_ROW_MAX = 2.2e-4
 
 
 @pytest.fixture(scope="module")
@@ -29,17 +51,49 @@ def c3():
     g = ci.chung_lu(N, exponent=2.1, mean=6.0, seed=0)
     r = ci.gaussian_block(N, D, D, seed=21)
     s = olap.normalized_adjacency(g.row_ptr, g.col_idx)
-    ref = och.cheb_filter(s, r[:, COLS].astype(np.float64), och.filter_coeffs(LAM, M))
-    return g, r, ref
+    c = och.filter_coeffs(LAM, M)
+    ref = och.cheb_filter(s, r[:, COLS].astype(np.float64), c)
+    rows = np.sort(np.random.default_rng(ROW_SEED).choice(N, N_ROWS, replace=False))
+    basis = np.zeros((N, N_ROWS))
+    basis[rows, np.arange(N_ROWS)] = 1.0
+    ref_rows = och.cheb_filter(s, basis, c).T @ r.astype(np.float64)  # rows of Y = h~(L) R
+    return g, r, ref, rows, och.normalize_rows(ref_rows)
 
 
-@pytest.mark.parametrize("storage,tol", [(0, 1e-4), (1, 0.15)])  # F32, BF16 (signal block stored in bf16)
-def test_chung_lu_1e6_sampled_columns(c3, storage, tol):
-    g, r, ref = c3
+@pytest.fixture(scope="module")
+def model_err(c3):
+    """Per-column relative error of the storage model on the sampled columns."""
+    g, r, ref, _, _ = c3
+    c = och.filter_coeffs(LAM, M)
+    out = {}
+    for name in ("f32", "bf16"):
+        y = clenshaw_stored(g.row_ptr, g.col_idx, r[:, COLS], c, name)
+        out[name] = [rel(y[:, i], ref[:, i]) for i in range(len(COLS))]
+    return out
+
+
+@pytest.mark.parametrize("storage,name", [(0, "f32"), (1, "bf16")])  # signal block stored in fp32 / bf16
+def test_chung_lu_1e6_sampled_columns(c3, model_err, storage, name):
+    g, r, ref, _, _ = c3
     with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM) as h:
         y = csc.csc_filter_random_signals(h, LAM, M, D, D, storage=storage, R_in=torch.from_numpy(r).cuda(),
                                           flags=csc.CLENSHAW)
         yc = y[:, COLS].double().cpu().numpy()
     for i in range(len(COLS)):
         err = rel(yc[:, i], ref[:, i])
-        assert err <= tol, f"column {COLS[i]}: relative error {err:.3g}"
+        bound = 1.5 * model_err[name][i]
+        assert err <= bound, f"column {COLS[i]}: relative error {err:.3g} above 1.5 x the {name} storage model's"
+        if name == "f32":
+            assert err <= FP32_TARGET, f"column {COLS[i]}: relative error {err:.3g}"
+    if name == "f32":
+        assert max(model_err["f32"]) <= FP32_TARGET  # the model itself is within the target here
+
+
+def test_chung_lu_1e6_sampled_normalised_rows(c3):
+    g, r, _, rows, ref_f = c3
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM) as h:
+        f = csc.csc_filter_random_signals(h, LAM, M, D, D, R_in=torch.from_numpy(r).cuda(),
+                                          flags=csc.CLENSHAW | csc.NORMALIZE_ROWS)
+        fr = f[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+    err = np.linalg.norm(fr[:, :D] - ref_f, axis=1)
+    assert np.all(err <= 1.5 * FP32_MODEL_ROW_MAX), f"per-row errors {err}"

@@ -1,5 +1,9 @@
 """Alg. 2 end to end through csc_cluster against the oracle pipeline (ARI within 0.01),
-and the full-size SBM workload (N = 1e5, k = 200) through properties the oracle checks."""
+and the full-size SBM workload (N = 1e5, k = 200) against the oracle's stored run and
+through properties the oracle checks."""
+import hashlib
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -100,6 +104,33 @@ def test_csc_full_size_sbm_1e5():
     assert np.array_equal(lab, lab2.cpu().numpy())
     # recovery of the planted partition (the oracle pipeline scores ~0.86 on this graph)
     assert oari.ari(lab, g.labels) >= 0.8
+
+
+GOLDEN_C2 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "csc_sbm_n1e5_k200_seed0.npz")
+
+
+def test_csc_sbm_1e5_k200_against_oracle_run():
+    """The SBM with N = 1e5, k = 200 (mean degree 16, eps = eps_c / 4, seed 0; d = 47, m = 50,
+    n = 2120, L^4 with gamma = 1e-3) end to end against the FP64 oracle's run of Alg. 2,
+    written by tests/golden/make_csc_sbm_n1e5_k200.py: the ARI against the planted
+    communities within 0.01 of the oracle's, the labels' own agreement with the oracle's
+    (ARI) reported and bounded, and the same lambda_k (same probes, same dichotomy)."""
+    ref = np.load(GOLDEN_C2)
+    g = ci.sbm(100_000, 200, seed=0)
+    hh = hashlib.sha256()
+    hh.update(np.ascontiguousarray(g.row_ptr, dtype=np.int64).tobytes())
+    hh.update(np.ascontiguousarray(g.col_idx, dtype=np.int32).tobytes())
+    assert g.nnz == int(ref["nnz"]) and hh.hexdigest() == str(ref["csr_sha256"]), "graph generator changed"
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        labels, info = csc.csc_cluster(h, 200, seed=0)
+    lab = labels.cpu().numpy()
+    a_gpu = oari.ari(lab, g.labels)
+    a_ref = float(ref["ari_vs_planted"])
+    agree = oari.ari(lab, ref["labels"].astype(np.int64))
+    print(f"ARI vs planted: GPU {a_gpu:.4f}, oracle {a_ref:.4f}; ARI(GPU labels, oracle labels) {agree:.4f}")
+    assert abs(a_gpu - a_ref) <= 0.01, f"ARI {a_gpu:.4f} vs oracle {a_ref:.4f}"
+    assert agree >= 0.9, f"ARI between the GPU and oracle labels {agree:.4f}"
+    assert info.lam.hit and abs(info.lam.lam - float(ref["lam"])) < 1e-9 + 2.0 ** -info.lam.iters
 
 
 def test_eigencount_degree_parameter():
