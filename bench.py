@@ -5,9 +5,13 @@ One step = one pass of the whole path of Alg. 2 on one synthetic graph:
 eigencount moments and the lambda_k dichotomy, the Jackson-Chebyshev filter
 of d random signals with row normalisation, uniform sampling, reduced
 k-means (20 replicates), CG interpolation of Eq. 5 (g(L) = L^4) and the
-label rule.  The default workload is the SBM with N = 1e5 nodes, k = 200
-equal communities, mean degree 16, eps = eps_c / 4, d = ceil(4 ln N) = 47
-signals padded to 48 columns, m = 50, n = ceil(2 k ln k) = 2120 samples.
+label rule.  The default workload is the Chung-Lu power-law graph with
+N = 1e6 nodes (degree exponent 2.1, mean degree 6, minimum degree 1), RCM
+reordered, k = 100, d = ceil(4 ln N) = 56 signals, m = 100,
+n = ceil(2 k ln k) = 922 samples: its signal blocks (224 MB each in FP32)
+exceed the 129 MB L2, so the filter's HBM roofline is meaningful there.
+`--workload sbm_n1e5_k200` runs the SBM with N = 1e5, k = 200 (m = 50,
+d = 47 padded to 48, n = 2120), whose working set sits in L2.
 
 value  = Chebyshev-filter throughput m * nnz * d / t_filter (nnz.col/s),
          t_filter the device time of the filter stage inside each timed step
@@ -17,7 +21,9 @@ e2e    = the same work over the end-to-end step through the C ABI with host
          csc_cluster -> labels copied back to pinned host memory.
 
 `--impl reference` times the FP64 oracle (the CPU restatement of the
-method) on a bounded sample of the same workload: one oracle filter pass.
+method) on a bounded sample of the same workload: per step, one oracle
+filter pass over as many signal columns as the host has cores, one column
+per spawned process (the columns are independent).
 Multi-GPU (torchrun): every rank runs its own replica (independent graphs,
 no collective on the data path); value aggregates all ranks' work over the
 slowest rank's time.
@@ -53,10 +59,10 @@ WORKLOADS = {
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sbm_n1e5_k200", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="chung_lu_n1e6_k100", choices=sorted(WORKLOADS))
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f64"])
     ap.add_argument("--interp", default="l4", choices=["l4", "highpass"],
                     help="interpolation regulariser: g(L) = L^4 (default) or the paper's g = 1 - h~ at lambda_k")
@@ -163,22 +169,40 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_traffic(kernel_class: str):
-    """DRAM traffic per launch from the committed ncu summary, if the kernel source is unchanged since."""
+def recorded_traffic(workload: str, kernel_class: str, shape: dict | None):
+    """DRAM traffic per launch from the committed ncu summary of this workload, kernel class and
+    launch shape, if the kernel source is unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
-            rec = json.load(f).get(kernel_class)
+            rec = json.load(f).get(workload, {}).get(kernel_class)
         if not rec:
-            return None, None
+            return None, f"no ncu capture recorded for {kernel_class} on {workload}"
+        want = rec.get("shape")
+        if want and shape and any(shape.get(k) != v for k, v in want.items()):
+            return None, f"ncu capture was of shape {want}, this run tuned {shape}"
         src = os.path.join(ROOT, rec["source"])
         with open(src, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
         if sha != rec["sha256"]:
             return None, "kernel source changed since the ncu capture"
-        return float(rec["bytes_per_launch_full"]), rec.get("note")
+        return float(rec["bytes_per_launch"]), rec.get("note")
     except (OSError, KeyError, ValueError):
         return None, None
+
+
+# The paper's own timings (context, not targets): Matlab R2015a on a laptop with a
+# 2.60 GHz dual-core Intel i7 and 16 GB RAM (Sec. 5); no GPU and no filter throughput.
+PAPER_CONTEXT = [
+    {"what": "SC, eigs of the first 200 eigenvectors", "value": "< 2 min", "workload": "SBM N=1e5, k=200, "
+     "eps=eps_c/4", "hardware": "2.60 GHz Intel i7 dual-core laptop, 16 GB, Matlab R2015a", "source": "Sec. 5.2"},
+    {"what": "SC and power method", "value": "stopped after 20 h", "workload": "SBM N=1e6, k=200",
+     "hardware": "same laptop", "source": "Sec. 5.2"},
+    {"what": "CSC against SC / PM", "value": "SC and PM faster at k=20; CSC up to about 10x faster at k=200",
+     "workload": "SBM, N and k varied, eps=eps_c/4", "hardware": "same laptop", "source": "Sec. 5.2, Fig. 1 f-g"},
+    {"what": "SC on the Amazon graph, k=1000", "value": "eigendecomposition 17 h, k-means stopped after 21 h",
+     "workload": "N=334,863 (dataset not available here)", "hardware": "same laptop", "source": "Sec. 5.3"},
+]
 
 
 def adjusted_rand(a, b) -> float:
@@ -197,61 +221,100 @@ def adjusted_rand(a, b) -> float:
 
 
 # --------------------------------------------------------- CPU oracle sample
-def oracle_filter_sample(g, lam: float, m: int, d: int, seed: int, min_s: float = 10.0, max_runs: int = 5):
-    """Time the oracle's filter stage (Y = h~(L) R, rows normalised) on the full graph."""
-    from oracle import chebyshev as och
+# The oracle's filter stage on the host cores: one spawned process per core (spawned, not
+# forked, so no CUDA state is inherited), each building the FP64 normalized adjacency once
+# and filtering its share of the signal columns; the columns of Y = h~(L) R are independent,
+# so splitting them changes no arithmetic.  A process times only its own filter call; the
+# stage's time is the slowest process's.
+_ORACLE_S = None
+
+
+def _oracle_worker_init(row_ptr, col_idx):
+    global _ORACLE_S
     from oracle import laplacian as olap
 
-    s = olap.normalized_adjacency(g.row_ptr, g.col_idx)
-    r = och.random_signals(g.n, d, d, seed)
-    c = och.filter_coeffs(lam, m)
-    times = []
-    t_all = time.perf_counter()
-    while len(times) < max_runs:
-        t0 = time.perf_counter()
-        och.normalize_rows(och.cheb_filter(s, r, c))
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_all >= min_s:
-            break
-    return times
+    _ORACLE_S = olap.normalized_adjacency(row_ptr, col_idx)
+
+
+def _oracle_worker_filter(task):
+    from oracle import chebyshev as och
+
+    r_cols, coeffs = task
+    t0 = time.perf_counter()
+    y = och.cheb_filter(_ORACLE_S, r_cols.astype("float64"), coeffs)
+    return time.perf_counter() - t0, y
+
+
+class OracleFilter:
+    def __init__(self, g, cores: int):
+        import multiprocessing as mp
+
+        self.cores = max(1, cores)
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_worker_init,
+                                                 initargs=(g.row_ptr, g.col_idx))
+
+    def run(self, r, coeffs):
+        """(seconds, Y) for the oracle filter of the columns of r, split over the processes."""
+        import numpy as np
+
+        parts = [c for c in np.array_split(np.arange(r.shape[1]), self.cores) if len(c)]
+        res = self.pool.map(_oracle_worker_filter, [(np.ascontiguousarray(r[:, c]), coeffs) for c in parts])
+        return max(t for t, _ in res), np.concatenate([y for _, y in res], axis=1)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
 
 
 def run_reference(args, w, rank, world):
     if rank != 0:
         return 0
+    import numpy as np
+
+    from oracle import chebyshev as och
+
     sz = sizes(w)
     g = make_graph(w, args.seed)
     d, m = sz["d"], w["m"]
-    work = float(m) * g.nnz * d
-    # the cut-off used by the oracle sample: the oracle's own lambda_k would cost its
-    # eigencount stage; the filter's cost does not depend on the cut-off value
+    cores = host_cores()
+    cols = min(d, cores)  # one signal column per process
+    work = float(m) * g.nnz * cols
+    # the cut-off of the oracle sample: the filter's cost does not depend on its value
     lam = 0.40625
-    from oracle import chebyshev as och
-    from oracle import laplacian as olap
-
-    s = olap.normalized_adjacency(g.row_ptr, g.col_idx)
-    r = och.random_signals(g.n, d, d, args.seed)
+    r = och.random_signals(g.n, d, d, args.seed)[:, :cols]
     c = och.filter_coeffs(lam, m)
+    of = OracleFilter(g, cores)
     for _ in range(args.warmup):
-        och.normalize_rows(och.cheb_filter(s, r, c))
+        of.run(r, c)
     ts = []
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        och.normalize_rows(och.cheb_filter(s, r, c))
-        ts.append(time.perf_counter() - t0)
+        t, y = of.run(r, c)
+        och.normalize_rows(y)
+        ts.append(t)
+    of.close()
     t = statistics.mean(ts)
     val = work / t
-    sample = (f"oracle Chebyshev filter stage (FP64 scipy, m={m}, d={d}, rows normalised) on the full "
-              f"{args.workload} graph (N={g.n}, nnz={g.nnz}) per step")
+    sample = (f"oracle Chebyshev filter stage (FP64 scipy, m={m}) on {cols} of the d={d} signal columns of the "
+              f"full {args.workload} graph (N={g.n}, nnz={g.nnz}) per step, one column per process on {cores} "
+              f"host cores")
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "N": g.n, "nnz": g.nnz, "k": w["k"], "m": m, "d": d,
                    "d_pad": sz["d_pad"], "n": sz["n"]},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                          "host_cores": os.cpu_count()},
-        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "the oracle's filter stage only; the GPU arm's e2e covers the whole CSC pipeline"},
+        "paper_context": PAPER_CONTEXT,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -311,7 +374,7 @@ def run_ours(args, w, rank, world, local_rank):
     launches = csc.csc_profile_launches()
     # per-kernel CUDA-event durations for the roofline: a second pass of the same steps with
     # every launch bracketed by events on its stream (eager launches, so each kernel is seen)
-    prof_steps = max(3, args.steps // 2)
+    prof_steps = max(2, min(3, args.steps // 2))
     csc.csc_profile_reset()
     csc.csc_profile_enable(True)
     torch.cuda.nvtx.range_push("csc_profiled_pass")  # ncu --nvtx-include selects these launches
@@ -331,25 +394,62 @@ def run_ours(args, w, rank, world, local_rank):
         ms_step, ms_filter = t.tolist()
     value = world * work / (ms_filter / 1e3)
 
-    # roofline of the dominant kernel class (live CUDA-event durations, algorithmic bytes)
+    # roofline of the dominant kernel (live CUDA-event durations, algorithmic bytes).  A unit is
+    # one launch of the row-range kernel together with the launch of the same product over the
+    # heavy rows (degree > 256), which runs just before it on the same stream
     peak, peak_kind = peaks()
-    dom = max(classes.items(), key=lambda kv: kv[1]["ms"])
-    total_ms = sum(v["ms"] for v in classes.values())
+    units = {}
+    for name, c in classes.items():
+        base = name[:-6] if name.endswith("_heavy") else name
+        u = units.setdefault(base, {"launches": 0, "units": 0, "ms": 0.0, "bytes": 0.0})
+        u["launches"] += c["launches"]
+        u["ms"] += c["ms"]
+        u["bytes"] += c["bytes"]
+        if base == name:
+            u["units"] += c["launches"]
+    dom = max(units.items(), key=lambda kv: kv[1]["ms"])
+    total_ms = sum(v["ms"] for v in units.values())
+    tuned = csc.csc_graph_tuned_shapes(h)
+    shape_kind = {"cheb_step": "clenshaw" if args.filter == "clenshaw" else "cheb_step", "cg_lap": "cg",
+                  "cg_lap_ax": "cg", "mom_step": "mom_step"}
+    byte_models = {
+        "cheb_step": ("one Clenshaw order: 4 nnz + 4 (N+1) + 4 N + 4 N d_pad b_X (B_{j+1} gathered once, B_{j+2} "
+                      "and s R read, B_j written; the last order writes Y instead of B_j)")
+        if args.filter == "clenshaw" else
+        "one forward order: 4 nnz + 4 (N+1) + 4 N + 3 N d_pad b_X + 2 N d_pad 4 (X_j gathered once, X_{j-1} read, "
+        "X_{j+1} written, Y read and written)",
+        "cg_lap": "one product of the L-chain: 4 nnz + 4 (N+1) + 4 N + 2 N k_pad 4 (input gathered once, output "
+                  "written)",
+        "cg_lap_ax": "the chain's last product with the mask term: 4 nnz + 4 (N+1) + 8 N + 3 N k_pad 4 + partials",
+    }
 
     def roof(name):
-        c = classes[name]
-        per_launch_bytes = c["bytes"] / c["launches"]
-        avg_ms = c["ms"] / c["launches"]
-        achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
-        traffic, note = recorded_traffic(name)
+        c = units[name]
+        n_units = max(1, c["units"])
+        per_unit = c["bytes"] / n_units
+        unit_ms = c["ms"] / n_units
+        achieved = per_unit / (unit_ms / 1e3) / 1e9
+        shp = next((dict(G=x["G"], NT=x["NT"], threads=x["threads"], P=x["P"], tiles=x["tiles"]) for x in tuned
+                    if x["kernel"] == shape_kind.get(name)), None)
+        traffic, note = recorded_traffic(args.workload, name, shp)
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "traffic": traffic, "traffic_note": note, "algorithmic_bytes_per_launch": per_launch_bytes,
-                "avg_launch_us": avg_ms * 1e3, "launches": c["launches"], "share": c["ms"] / total_ms}
+                "traffic": traffic, "traffic_note": note, "algorithmic_bytes_per_unit": per_unit,
+                "byte_model": byte_models.get(name), "shape": shp,
+                "unit_us": unit_ms * 1e3, "units": c["units"], "launches": c["launches"],
+                "share": c["ms"] / total_ms}
 
     roofline = roof(dom[0])
-    filter_roofline = roof("cheb_step") if "cheb_step" in classes else None
+    filter_roofline = roof("cheb_step") if "cheb_step" in units else None
+    if filter_roofline and args.filter == "clenshaw":
+        # the same time against the forward recurrence's bytes per order (the byte count of the
+        # scope table), which also moves the fp32 accumulator Y twice per order
+        bx = {"f32": 4, "bf16": 2, "f64": 8}[args.storage]
+        by = 8 if args.storage == "f64" else 4
+        fwd = 4.0 * g.nnz + 4.0 * (g.n + 1) + 4.0 * g.n + 3.0 * g.n * d_pad * bx + 2.0 * g.n * d_pad * by
+        filter_roofline["forward_bytes_per_order"] = fwd
+        filter_roofline["frac_forward_bytes"] = fwd / (filter_roofline["unit_us"] / 1e6) / 1e9 / peak
 
     lab = labels.cpu().numpy()
     ari_truth = adjusted_rand(lab, g.labels) if g.labels is not None else None
@@ -361,8 +461,9 @@ def run_ours(args, w, rank, world, local_rank):
         rp_pin = torch.from_numpy(g.row_ptr).pin_memory()
         ci_pin = torch.from_numpy(g.col_idx).pin_memory()
         lab_host = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        e2e_steps = min(args.steps, 3)
         ts = []
-        for i in range(args.warmup + args.steps):
+        for i in range(1 + e2e_steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h2 = csc.csc_graph_create(rp_pin.numpy(), ci_pin.numpy(), flags)
@@ -371,7 +472,7 @@ def run_ours(args, w, rank, world, local_rank):
             lab_host.copy_(labs)
             torch.cuda.synchronize()
             h2.close()
-            if i >= args.warmup:
+            if i >= 1:
                 ts.append(time.perf_counter() - t0)
         t_e2e = statistics.mean(ts)
         if dist:
@@ -381,15 +482,23 @@ def run_ours(args, w, rank, world, local_rank):
         h2d = (g.n + 1) * 4 + g.nnz * 4
         d2h = g.n * 4
         e2e = {"value": world * work / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "csc_seconds": t_e2e,
-               "what": "host CSR -> csc_graph_create (upload, degrees) -> csc_cluster -> labels to pinned host"}
+               "csc_seconds": t_e2e, "steps": e2e_steps, "warmup": 1,
+               "what": "host CSR -> csc_graph_create (upload, degrees, RCM) -> csc_cluster -> labels to pinned host"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        times = oracle_filter_sample(g, last.lam.lam, m, d, args.seed)
-        cpu = {"value": work / statistics.mean(times), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"oracle Chebyshev filter stage (FP64 scipy, m={m}, d={d}, rows normalised) on the full "
-                         f"graph, {len(times)} run(s) of {statistics.mean(times):.2f} s",
+        from oracle import chebyshev as och
+
+        cores = host_cores()
+        r_or = och.random_signals(g.n, d, d, args.seed)
+        of = OracleFilter(g, cores)
+        t_or, y_or = of.run(r_or, och.filter_coeffs(last.lam.lam, m))
+        of.close()
+        och.normalize_rows(y_or)
+        cpu = {"value": work / t_or, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"oracle Chebyshev filter stage (FP64 scipy, m={m}, all d={d} columns, rows normalised) "
+                         f"on the full graph, the columns split over {cores} spawned processes, {t_or:.2f} s "
+                         f"(slowest process)",
                "host_cores": os.cpu_count()}
 
     if rank == 0:
@@ -412,9 +521,10 @@ def run_ours(args, w, rank, world, local_rank):
             "roofline": roofline,
             "filter_roofline": filter_roofline,
             "kernel_classes": {kk: {"launches": v["launches"], "ms": round(v["ms"], 4)} for kk, v in classes.items()},
-            "autotuned_shapes": csc.csc_graph_tuned_shapes(h),
+            "autotuned_shapes": tuned,
             "gpu_launches": launches,
             "roofline_pass": f"{prof_steps} extra steps with per-launch CUDA events (eager launches)",
+            "paper_context": PAPER_CONTEXT,
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
@@ -461,7 +571,9 @@ def run_precision(args, w):
         torch.cuda.synchronize()
         csc.csc_profile_enable(False)
         ms = e0.elapsed_time(e1) / reps
-        c = csc.csc_profile_query()["cheb_step"]
+        q = csc.csc_profile_query()
+        c = {key: q["cheb_step"][key] + q.get("cheb_step_heavy", {}).get(key, 0) for key in ("ms", "bytes")}
+        c["launches"] = q["cheb_step"]["launches"]  # orders (row-range launches)
         peak, _ = peaks()
         per_launch = c["bytes"] / c["launches"]
         avg_s = c["ms"] / c["launches"] / 1e3

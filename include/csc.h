@@ -55,8 +55,8 @@ typedef int32_t csc_status;
 #define CSC_E_OOM              3  /* device or host allocation failed             */
 #define CSC_E_CUDA             4  /* a CUDA runtime call failed (handle poisoned) */
 #define CSC_E_NOT_CONVERGED    5  /* iterative solver hit max_iter; outputs valid */
-#define CSC_E_DEVICE_TIMEOUT   6  /* a bounded device-side wait gave up           */
-#define CSC_E_NUMERIC          7  /* non-finite values detected                   */
+#define CSC_E_DEVICE_TIMEOUT   6  /* reserved: no entry point waits on the device  */
+#define CSC_E_NUMERIC          7  /* non-finite values detected (CSC_CHECK_FINITE) */
 #define CSC_E_UNSUPPORTED      8  /* valid but outside what this build supports   */
 
 /* storage type of the signal blocks */
@@ -78,6 +78,10 @@ typedef int32_t csc_dtype;
 #define CSC_HIGHPASS       8u  /* csc_cluster: interpolate with g = 1 - h~ (Sec. 4.4)  */
 #define CSC_VARDENSITY    16u  /* csc_cluster: variable-density draws (scores ||Y_i||^2)
                                   and the weighted decoder (Sec. 3.2.3, Theorem 3.4)  */
+#define CSC_CHECK_FINITE  32u  /* csc_filter_random_signals: scan R_in (when given)
+                                  before and Y after the filter; csc_cluster: scan the
+                                  filtered features; CSC_E_NUMERIC on NaN or infinity
+                                  (one synchronizing pass per scan)                   */
 
 typedef struct csc_graph_s* csc_graph;
 
@@ -192,7 +196,7 @@ CSC_API csc_status csc_graph_info(csc_graph g, int64_t* N, int64_t* nnz, int32_t
  * graph.  Entry i
  * (0-based) is written to kind, dtype_bytes (4 fp32, 2 bf16, 8 fp64), columns and
  * shape[6] = {lanes per row G, vectors per lane NT, threads per CTA, row ranges P,
- * column tiles, shared-memory window rows (0: none)}.  Host outputs (any may be
+ * column tiles, 0 (reserved)}.  Host outputs (any may be
  * NULL).  CSC_E_INVALID when i is out of range. */
 CSC_API csc_status csc_graph_tuned_shape(csc_graph g, int32_t i, int32_t* kind, int32_t* dtype_bytes,
                                          int32_t* columns, int32_t* shape);
@@ -201,7 +205,7 @@ CSC_API csc_status csc_graph_tuned_shape(csc_graph g, int32_t i, int32_t* kind, 
  * instead of tuning it (reproducible timings; tests of every compiled shape).
  * kind, dtype_bytes, columns and shape[6] as in csc_graph_tuned_shape (host).
  * (G, NT) must be a compiled pair, threads 256 or 512, tiles = ceil(vectors per
- * row / (G NT)); a window (kind 1 only) needs tiles = 1 and fits shared memory.
+ * row / (G NT)), shape[5] = 0.
  * Errors: CSC_E_INVALID (no side effects); an uncompiled (G, NT) surfaces as
  * CSC_E_UNSUPPORTED at the next launch. */
 CSC_API csc_status csc_graph_pin_shape(csc_graph g, int32_t kind, int32_t dtype_bytes, int32_t columns,
@@ -238,13 +242,15 @@ CSC_API csc_status csc_chebyshev_coefficients(double lambda_c, int32_t m, uint32
  *             (padding columns are ignored and treated as zero).
  *   Y_out     device, N * d_pad row-major in original node order: float for
  *             CSC_F32/CSC_BF16, double for CSC_F64.  Padding columns are zero.
- *   flags     CSC_NORMALIZE_ROWS, CSC_NO_JACKSON, CSC_CLENSHAW.  Without
+ *   flags     CSC_NORMALIZE_ROWS, CSC_NO_JACKSON, CSC_CLENSHAW, CSC_CHECK_FINITE.  Without
  *             CSC_CLENSHAW the orders run the three-term forward recurrence
  *             X_{j+1} = 2 (L - I) X_j - X_{j-1} accumulating Y (Sec. 2.1); with it
  *             Clenshaw's recurrence b_j = c_j R + 2 (L - I) b_{j+1} - b_{j+2},
  *             Y = c_0 R + (L - I) b_1 - b_2 (Clenshaw 1955), which needs no Y
  *             traffic until the last order; both give Y up to rounding.
- * Errors: CSC_E_INVALID (no side effects), CSC_E_OOM, CSC_E_CUDA.  Asynchronous. */
+ * Errors: CSC_E_INVALID (no side effects), CSC_E_OOM, CSC_E_CUDA; with
+ * CSC_CHECK_FINITE, CSC_E_NUMERIC when R_in (nothing is filtered then) or Y holds a
+ * NaN or infinity.  Asynchronous, except that each CSC_CHECK_FINITE scan synchronizes. */
 CSC_API csc_status csc_filter_random_signals(csc_graph g, double lambda_c, int32_t m, int32_t d,
                                      int32_t d_pad, uint64_t seed, csc_dtype storage,
                                      const float* R_in, void* Y_out, uint32_t flags,
@@ -399,7 +405,7 @@ CSC_API csc_status csc_sample(int64_t N, int64_t n, uint64_t seed, int64_t* idx_
  * owned by their own allocator (a framework's caching pool, an arena sized at
  * start-up), applications with a fixed device-memory budget, and latency-critical
  * code where cudaMalloc / cudaFree may implicitly synchronize the device.  The
- * paper has no counterpart; this is a deployment variant of Eq. 4's sampling.
+ * paper has no counterpart.
  * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch is one
  * fixed array of 327,936 bytes inside the library, present on every device that
  * loads the library until the process exits.
@@ -523,6 +529,8 @@ CSC_API csc_status csc_interpolate_weighted(csc_graph g, const int64_t* sample_i
 /* csc_cluster -- Alg. 2 end to end on one graph with the parameters above.
  *   labels_out  device int32[N] in original node order.
  *   info        host (may be NULL).  Synchronizes `stream`.
+ * With CSC_CHECK_FINITE in params->flags the filtered features are scanned before
+ * sampling and a NaN or infinity stops the call with CSC_E_NUMERIC.
  * For a batched handle use csc_cluster_batched. */
 CSC_API csc_status csc_cluster(csc_graph g, const csc_params* params, int32_t* labels_out,
                        csc_cluster_info* info, void* stream);

@@ -22,6 +22,7 @@ RCM, CHECK_SYM, DEVICE_INPUT = nat.CSC_RCM, nat.CSC_CHECK_SYM, nat.CSC_DEVICE_IN
 NORMALIZE_ROWS, NO_JACKSON, CLENSHAW, HIGHPASS, VARDENSITY = (nat.CSC_NORMALIZE_ROWS, nat.CSC_NO_JACKSON,
                                                               nat.CSC_CLENSHAW, nat.CSC_HIGHPASS,
                                                               nat.CSC_VARDENSITY)
+CHECK_FINITE = nat.CSC_CHECK_FINITE
 
 
 def _stream(stream) -> ctypes.c_void_p:
@@ -124,16 +125,16 @@ def csc_graph_tuned_shapes(g: Graph) -> list:
                                        shape) != nat.CSC_OK:
             break
         out.append(dict(kernel=kinds.get(kind.value, str(kind.value)), dtype_bytes=db.value, columns=cols.value,
-                        G=shape[0], NT=shape[1], threads=shape[2], P=shape[3], tiles=shape[4], win=shape[5]))
+                        G=shape[0], NT=shape[1], threads=shape[2], P=shape[3], tiles=shape[4]))
         i += 1
     return out
 
 
 def csc_graph_pin_shape(g: Graph, kernel: str, dtype_bytes: int, columns: int, G: int, NT: int, threads: int,
-                        P: int, tiles: int, win: int = 0) -> None:
-    """Fix a launch shape on this handle instead of tuning it."""
+                        P: int, tiles: int, reserved: int = 0) -> None:
+    """Fix a launch shape on this handle instead of tuning it (the sixth entry is reserved: 0)."""
     kind = {"cheb_step": 1, "mom_step": 2, "cg": 3, "clenshaw": 4}[kernel]
-    shape = (ctypes.c_int32 * 6)(G, NT, threads, P, tiles, win)
+    shape = (ctypes.c_int32 * 6)(G, NT, threads, P, tiles, reserved)
     check(lib().csc_graph_pin_shape(g.handle, kind, dtype_bytes, columns, shape), "csc_graph_pin_shape")
 
 
@@ -312,9 +313,17 @@ def csc_estimate_lambda_k_refilter(g: Graph, k: int, m: int = 50, n_probes: int 
     return _lambda_info(info)
 
 
+def _check_index_out(out: torch.Tensor, n: int, name: str) -> None:
+    if not isinstance(out, torch.Tensor) or not out.is_cuda or out.dtype != torch.int64 or not out.is_contiguous():
+        raise ValueError(f"{name}: out must be a contiguous int64 CUDA tensor")
+    if out.numel() < n:
+        raise ValueError(f"{name}: out holds {out.numel()} elements, n = {n} are written")
+
+
 def csc_sample(N: int, n: int, seed: int = 0, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
     if out is None:
         out = torch.empty(n, dtype=torch.int64, device="cuda")
+    _check_index_out(out, n, "csc_sample")
     check(lib().csc_sample(N, n, seed, _dptr(out) if n else None, _stream(stream)), "csc_sample")
     return out
 
@@ -351,6 +360,7 @@ def csc_sample_weighted(score: torch.Tensor, n: int, seed: int = 0, idx_out: Opt
 
 def csc_sample_noalloc(N: int, n: int, seed: int, out: torch.Tensor, stream=None) -> torch.Tensor:
     """csc_sample without any device allocation inside the library (the caller gives `out`)."""
+    _check_index_out(out, n, "csc_sample_noalloc")
     check(lib().csc_sample_noalloc(N, n, seed, _dptr(out) if n else None, _stream(stream)), "csc_sample_noalloc")
     return out
 

@@ -166,6 +166,15 @@ csc_status get_partition(Graph* g, int P, const int32_t** out) {
     CSC_CUDA_TRY(cudaMemcpy(d, bounds.data(), (P + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     g->parts[P] = d;
     g->h_parts[P] = bounds;
+    {
+        // the largest staged CSR slice: row pointers r0 .. r1 and the range's light edges
+        int64_t most = 0;
+        for (int x = 0; x < P; ++x) {
+            const int64_t nr = (int64_t)bounds[x + 1] - bounds[x];
+            if (nr > 0) most = std::max(most, nr + 1 + (rp[bounds[x + 1]] - rp[bounds[x]]));
+        }
+        g->part_smem[P] = (int)(most * 4);
+    }
     int32_t* dg = nullptr;
     e = cudaMalloc(&dg, gblk.size() * sizeof(int32_t));
     if (e != cudaSuccess) {
@@ -176,6 +185,31 @@ csc_status get_partition(Graph* g, int P, const int32_t** out) {
     CSC_CUDA_TRY(cudaMemcpy(dg, gblk.data(), gblk.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     g->part_gblk[P] = dg;
     *out = d;
+    return CSC_OK;
+}
+
+int staged_smem(const Graph* g, int P) {
+    auto it = g->part_smem.find(P);
+    return it == g->part_smem.end() ? 0 : it->second;
+}
+
+csc_status check_staged_smem(int bytes) {
+    if (bytes > kStagedSmemMax) {
+        set_error("a row range's CSR slice needs %d bytes of shared memory (at most %d): use more row ranges",
+                  bytes, kStagedSmemMax);
+        return CSC_E_UNSUPPORTED;
+    }
+    return CSC_OK;
+}
+
+csc_status fit_staged_partition(Graph* g, int P, int64_t max_p, int* out) {
+    for (;;) {
+        const int32_t* pr = nullptr;
+        CSC_TRY(get_partition(g, P, &pr));
+        if (staged_smem(g, P) <= kStagedSmemMax || P >= max_p) break;
+        P = (int)std::min<int64_t>(max_p, 2 * (int64_t)P);
+    }
+    *out = P;
     return CSC_OK;
 }
 
@@ -209,55 +243,6 @@ csc_status get_segments(Graph* g, int P, const int32_t** gblk, const int32_t** g
     return CSC_OK;
 }
 
-csc_status get_windows(Graph* g, int P, int W, const int32_t** out) {
-    auto it = g->wins.find({P, W});
-    if (it != g->wins.end()) {
-        *out = it->second;
-        return CSC_OK;
-    }
-    const int32_t* dp = nullptr;
-    CSC_TRY(get_partition(g, P, &dp));
-    const std::vector<int32_t>& b = g->h_parts[P];
-    const std::vector<int32_t>& rp = g->h_row_ptr;
-    const int64_t N = g->N;
-    std::vector<int32_t> cols_host;
-    CSC_TRY([&]() -> csc_status {
-        cols_host.resize(g->nnz);
-        if (g->nnz)
-            CSC_CUDA_TRY(cudaMemcpy(cols_host.data(), g->col_idx, g->nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
-        return CSC_OK;
-    }());
-    std::vector<int32_t> starts(P), buf;
-    for (int x = 0; x < P; ++x) {
-        buf.assign(cols_host.begin() + rp[b[x]], cols_host.begin() + rp[b[x + 1]]);
-        std::sort(buf.begin(), buf.end());
-        // the window [c, c + W) starting at a neighbour column that holds the most neighbours
-        int64_t best = -1, best_start = b[x];
-        size_t j = 0;
-        for (size_t i = 0; i < buf.size(); ++i) {
-            while (j < buf.size() && buf[j] < (int64_t)buf[i] + W) ++j;
-            if ((int64_t)(j - i) > best) {
-                best = (int64_t)(j - i);
-                best_start = buf[i];
-            }
-        }
-        int64_t w0 = best_start;
-        if (w0 + W > N) w0 = N - W;
-        if (w0 < 0) w0 = 0;
-        starts[x] = (int32_t)w0;
-    }
-    int32_t* d = nullptr;
-    cudaError_t e = cudaMalloc(&d, P * sizeof(int32_t));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        set_error("cudaMalloc for window starts: %s", cudaGetErrorString(e));
-        return CSC_E_OOM;
-    }
-    CSC_CUDA_TRY(cudaMemcpy(d, starts.data(), P * sizeof(int32_t), cudaMemcpyHostToDevice));
-    g->wins[{P, W}] = d;
-    *out = d;
-    return CSC_OK;
-}
 
 // ------------------------------------------------- Jackson-Chebyshev (Sec. 4.3)
 // c_j = g_j gamma_j for the ideal low-pass of Eq. 1 on t = lambda - 1 in [-1, 1]:
@@ -510,9 +495,11 @@ static void free_graph(Graph* g) {
     for (auto& kv : g->parts) cudaFree(kv.second);
     for (auto& kv : g->part_gblk) cudaFree(kv.second);
     cudaFree(g->d_hvy_start);
-    for (auto& kv : g->wins) cudaFree(kv.second);
-    cudaFree(g->dev_err);
     cudaFree(g->heavy);
+    if (g->light_owned) {
+        cudaFree(g->lrp);
+        cudaFree(g->lci);
+    }
     for (auto& e : g->ev)
         if (e) cudaEventDestroy(e);
     if (g->pinned) cudaFreeHost(g->pinned);
@@ -589,6 +576,26 @@ static csc_status upload(Graph* g, const HostCSR& h, const std::vector<int32_t>*
     CSC_CUDA_TRY(cudaMemcpyAsync(g->row_ptr, rp32.data(), (N + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     if (nnz)
         CSC_CUDA_TRY(cudaMemcpyAsync(g->col_idx, h.ci.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    if (heavy.empty()) {
+        g->lrp = g->row_ptr;  // no heavy rows: the CSR is its own light part
+        g->lci = g->col_idx;
+    } else {
+        // compact light CSR: heavy rows keep no edges and are flagged in bit 31
+        const int64_t nl = g->h_light[N];
+        std::vector<int32_t> lrp(N + 1), lci((size_t)std::max<int64_t>(nl, 1));
+        lrp[0] = 0;
+        for (int64_t i = 0; i < N; ++i) {
+            const int64_t a = h.rp[i], b = h.rp[i + 1];
+            const bool hv = b - a > kHeavyRow;
+            if (!hv) std::copy(h.ci.begin() + a, h.ci.begin() + b, lci.begin() + g->h_light[i]);
+            lrp[i + 1] = (int32_t)g->h_light[i + 1] | (hv ? (int32_t)0x80000000u : 0);
+        }
+        g->light_owned = true;
+        CSC_TRY(dev_alloc(&g->lrp, N + 1));
+        CSC_TRY(dev_alloc(&g->lci, lci.size()));
+        CSC_CUDA_TRY(cudaMemcpy(g->lrp, lrp.data(), (N + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CSC_CUDA_TRY(cudaMemcpy(g->lci, lci.data(), lci.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     if (perm) {
         std::vector<int32_t> iperm(N);
         for (int64_t p = 0; p < N; ++p) iperm[(*perm)[p]] = (int32_t)p;
@@ -598,8 +605,6 @@ static csc_status upload(Graph* g, const HostCSR& h, const std::vector<int32_t>*
         CSC_CUDA_TRY(cudaMemcpyAsync(g->iperm, iperm.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     }
     CSC_CUDA_TRY(cudaMallocHost((void**)&g->pinned, 4096 * sizeof(double)));
-    CSC_TRY(dev_alloc(&g->dev_err, 1));
-    CSC_CUDA_TRY(cudaMemsetAsync(g->dev_err, 0, sizeof(int), s));
     for (auto& e : g->ev) CSC_CUDA_TRY(cudaEventCreate(&e));
     CSC_TRY(launch_degrees(g, s));
     CSC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -817,7 +822,7 @@ csc_status csc_graph_tuned_shape(csc_graph g, int32_t i, int32_t* kind, int32_t*
         shape[2] = it->second.threads;
         shape[3] = it->second.P;
         shape[4] = it->second.tiles;
-        shape[5] = it->second.win;
+        shape[5] = 0;  // reserved
     }
     return CSC_OK;
 }
@@ -827,8 +832,7 @@ csc_status csc_graph_pin_shape(csc_graph g, int32_t kind, int32_t dtype_bytes, i
     clear_error();
     CSC_TRY(check_graph(g));
     if (!shape || kind < 1 || kind > 4 || columns < 1 || shape[0] < 1 || shape[1] < 1 ||
-        (shape[2] != 256 && shape[2] != 512) || shape[3] < 1 || shape[4] < 1 || shape[5] < 0 ||
-        (kind != 1 && shape[5] != 0) || (shape[5] > 0 && shape[4] != 1) || shape[5] > g->N) {
+        (shape[2] != 256 && shape[2] != 512) || shape[3] < 1 || shape[4] < 1 || shape[5] != 0) {
         set_error("csc_graph_pin_shape: invalid shape");
         return CSC_E_INVALID;
     }
@@ -844,17 +848,12 @@ csc_status csc_graph_pin_shape(csc_graph g, int32_t kind, int32_t dtype_bytes, i
         set_error("csc_graph_pin_shape: %d column tiles do not match %d columns at G*NT = %d", shape[4], columns, cap);
         return CSC_E_INVALID;
     }
-    if (shape[5] > 0 && 128 + (size_t)shape[5] * columns * elem > 227 * 1024) {
-        set_error("csc_graph_pin_shape: window of %d rows exceeds shared memory", shape[5]);
-        return CSC_E_INVALID;
-    }
     LaunchCfg c;
     c.G = shape[0];
     c.NT = shape[1];
     c.threads = shape[2];
     c.P = shape[3];
     c.tiles = shape[4];
-    c.win = shape[5];
     const uint64_t key = kind == 3 ? ((3ull << 48) | (uint64_t)(uint32_t)columns)
                                    : (((uint64_t)kind << 48) | ((uint64_t)(dtype_bytes & 0xff) << 40) |
                                       (uint64_t)(uint32_t)columns);
@@ -914,8 +913,16 @@ csc_status csc_filter_random_signals(csc_graph g, double lambda_c, int32_t m, in
     }
     std::vector<double> c(m + 1);
     cheb_coefficients(lambda_c, m, (flags & CSC_NO_JACKSON) == 0, c.data());
+    const bool check = (flags & CSC_CHECK_FINITE) != 0;
+    if (check && R_in) {
+        const csc_status sc = run_check_finite(g, R_in, false, g->N, d, d_pad, "R_in", (cudaStream_t)stream);
+        if (sc != CSC_OK) return poison_on_cuda(g, sc);
+    }
     csc_status st = run_filter(g, c.data(), m, d, d_pad, seed, storage, R_in, Y_out,
                                (flags & CSC_NORMALIZE_ROWS) != 0, (cudaStream_t)stream, (flags & CSC_CLENSHAW) != 0);
+    if (st == CSC_OK && check)
+        st = run_check_finite(g, Y_out, storage == CSC_F64, g->N, d, d_pad, "the filtered block Y",
+                              (cudaStream_t)stream);
     return poison_on_cuda(g, st);
 }
 
@@ -1352,6 +1359,8 @@ csc_status csc_cluster(csc_graph g, const csc_params* p, int32_t* labels_out, cs
     std::vector<double> c(m + 1);
     cheb_coefficients(lam, m, true, c.data());
     st = run_filter(g, c.data(), m, d, d_pad, p->seed, storage, nullptr, Y, !vd, s, (p->flags & CSC_CLENSHAW) != 0);
+    if (st == CSC_OK && (p->flags & CSC_CHECK_FINITE))
+        st = run_check_finite(g, Y, storage == CSC_F64, N, d, d_pad, "the filtered features", s);
     if (st != CSC_OK) return done(st);
     // variable density: scores ||Y_i||^2 of the unnormalised rows, then step 4's normalisation
     if (vd) st = run_row_scores(Y, storage == CSC_F64, N, d, d_pad, score, true, g->num_sms, s);
@@ -1384,14 +1393,6 @@ csc_status csc_cluster(csc_graph g, const csc_params* p, int32_t* labels_out, cs
     if (ce != cudaSuccess) {
         set_error("csc_cluster: %s", cudaGetErrorString(ce));
         return done(CSC_E_CUDA);
-    }
-    {
-        int derr = 0;
-        if (cudaMemcpy(&derr, g->dev_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && derr) {
-            cudaMemset(g->dev_err, 0, sizeof(int));
-            set_error("csc_cluster: a bounded device wait gave up (the results were computed without it)");
-            st = CSC_E_DEVICE_TIMEOUT;
-        }
     }
     cudaEventElapsedTime(&local.ms_lambda, e0, e1);
     cudaEventElapsedTime(&local.ms_filter, e1, e2);

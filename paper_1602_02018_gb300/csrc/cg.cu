@@ -100,10 +100,26 @@ struct CgBatch {
 //   WIN (first product, unscaled input p):  v = s (p - D^-1/2 W D^-1/2 p)
 //   !WIN (middle products, scaled input v): v' = v - D^-1 W v
 // so only the first product loads per-edge weights.
+// The row's own entries of a block (this CTA's column tile), loaded before the
+// neighbour sum so their latency overlaps it.
+template <int G, int NT>
+struct RowVecs {
+    float4 v[NT];
+    __device__ __forceinline__ void load(const float* __restrict__ blk, int row, int lane, int col0, int tcols,
+                                         int64_t ld) {
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int cl = (t * G + lane) * 4;
+            if (cl < tcols) v[t] = __ldg(reinterpret_cast<const float4*>(blk + (int64_t)row * ld + col0 + cl));
+        }
+    }
+    __device__ __forceinline__ void get(int t, float (&x)[4]) const { StoreTraits<float>::unraw(v[t], x); }
+};
+
 template <int G, int NT, bool WIN>
 __device__ __forceinline__ void lap_epilogue(int row, int lane, int col0, int tcols, float (&acc)[NT][4],
                                              const float* __restrict__ dinv, const float* __restrict__ invdeg,
-                                             const float* __restrict__ in, float* __restrict__ out, int64_t ld) {
+                                             const RowVecs<G, NT>& in, float* __restrict__ out, int64_t ld) {
     const float di = dinv[row];
     const float sc = di > 0.f ? di : 1.f;
     const float f = WIN ? di : invdeg[row];
@@ -113,7 +129,7 @@ __device__ __forceinline__ void lap_epilogue(int row, int lane, int col0, int tc
         if (cl >= tcols) continue;
         const int64_t o = (int64_t)row * ld + col0 + cl;
         float x[4];
-        StoreTraits<float>::load(in + o, x);
+        in.get(t, x);
 #pragma unroll
         for (int v = 0; v < 4; ++v) x[v] = WIN ? sc * (x[v] - f * acc[t][v]) : x[v] - f * acc[t][v];
         StoreTraits<float>::store(out + o, x);
@@ -123,17 +139,19 @@ __device__ __forceinline__ void lap_epilogue(int row, int lane, int col0, int tc
 // Rows of degree > kHeavyRow are left to lap_heavy_kernel.
 template <int G, int NT, bool WIN>
 __global__ void __launch_bounds__(kCgMaxThreads)
-lap_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ dinv,
+lap_kernel(const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci, const float* __restrict__ dinv,
            const float* __restrict__ invdeg, const float* __restrict__ in, float* __restrict__ out,
            const int32_t* __restrict__ part, int ncols, int64_t ld, CgBatch bt) {
     CG_TILE(G, NT)
-    CG_ROWS(G) {
-        const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
-        if (e1 - e0 > kHeavyRow) continue;
+    extern __shared__ int32_t s_csr[];
+    const StagedCsr sc = stage_csr(lrp, lci, part[blockIdx.x], r1, s_csr);
+    for_each_staged_row(sc, (int)(threadIdx.x / G), (int)(blockDim.x / G), [&](int row, int e0, int e1) {
+        RowVecs<G, NT> x;
+        x.load(in, row, lane, col0, tcols, ld);
         float acc[NT][4];
-        gather_range<float, G, NT, WIN, float>(e0, e1, ci, dinv, in + col0, ld, lane, tcols, acc);
-        lap_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, invdeg, in, out, ld);
-    }
+        gather_staged<float, G, NT, WIN, float>(e0, e1, sc.ci, dinv, in + col0, ld, lane, tcols, acc);
+        lap_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, invdeg, x, out, ld);
+    });
 }
 
 // Heavy rows: one CTA of kHeavyThreads per row (CTA x = heavy row, CTA y = column tile).
@@ -150,7 +168,11 @@ lap_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
     float acc[NT][4];
     gather_heavy<float, G, NT, WIN, float>(__ldg(rp + row), __ldg(rp + row + 1), ci, dinv, in + col0, ld, lane, tcols,
                                            acc);
-    if (threadIdx.x < G) lap_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, invdeg, in, out, ld);
+    if (threadIdx.x < G) {
+        RowVecs<G, NT> x;
+        x.load(in, row, lane, col0, tcols, ld);
+        lap_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, invdeg, x, out, ld);
+    }
 }
 
 // Ap = mask * p + gamma L t with per-column partials of <p, Ap>; the last product of
@@ -158,7 +180,7 @@ lap_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
 template <int G, int NT, bool WIN>
 __device__ __forceinline__ void lap_ax_epilogue(int row, int lane, int col0, int tcols, float (&acc)[NT][4],
                                                 const float* __restrict__ dinv, const float* __restrict__ sqdeg,
-                                                const float* __restrict__ tin, const float* __restrict__ p,
+                                                const RowVecs<G, NT>& tin, const RowVecs<G, NT>& p,
                                                 const float* __restrict__ mask, float gamma, float* __restrict__ Ap,
                                                 int64_t ld, KSum (&dot)[1][NT][4]) {
     const float di = dinv[row];
@@ -170,8 +192,8 @@ __device__ __forceinline__ void lap_ax_epilogue(int row, int lane, int col0, int
         if (cl >= tcols) continue;
         const int64_t o = (int64_t)row * ld + col0 + cl;
         float tt[4], pp[4], a[4];
-        StoreTraits<float>::load(tin + o, tt);
-        StoreTraits<float>::load(p + o, pp);
+        tin.get(t, tt);
+        p.get(t, pp);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             a[v] = mk * pp[v] + gamma * (tt[v] * back - di * acc[t][v]);
@@ -185,19 +207,22 @@ __device__ __forceinline__ void lap_ax_epilogue(int row, int lane, int col0, int
 // row (lap_ax_heavy_kernel); nslots counts both.
 template <int G, int NT, bool WIN>
 __global__ void __launch_bounds__(kCgMaxThreads)
-lap_ax_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ dinv,
+lap_ax_kernel(const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci, const float* __restrict__ dinv,
               const float* __restrict__ sqdeg, const float* __restrict__ tin, const float* __restrict__ p,
               const float* __restrict__ mask, float gamma, float* __restrict__ Ap, const int32_t* __restrict__ part,
               int ncols, int64_t ld, double* __restrict__ partials, int nslots, CgBatch bt) {
     CG_TILE(G, NT)
     KSum dot[1][NT][4];
-    CG_ROWS(G) {
-        const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
-        if (e1 - e0 > kHeavyRow) continue;
+    extern __shared__ int32_t s_csr[];
+    const StagedCsr sc = stage_csr(lrp, lci, part[blockIdx.x], r1, s_csr);
+    for_each_staged_row(sc, (int)(threadIdx.x / G), (int)(blockDim.x / G), [&](int row, int e0, int e1) {
+        RowVecs<G, NT> tv, pv;
+        tv.load(tin, row, lane, col0, tcols, ld);
+        pv.load(p, row, lane, col0, tcols, ld);
         float acc[NT][4];
-        gather_range<float, G, NT, WIN, float>(e0, e1, ci, dinv, tin + col0, ld, lane, tcols, acc);
-        lap_ax_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, sqdeg, tin, p, mask, gamma, Ap, ld, dot);
-    }
+        gather_staged<float, G, NT, WIN, float>(e0, e1, sc.ci, dinv, tin + col0, ld, lane, tcols, acc);
+        lap_ax_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, sqdeg, tv, pv, mask, gamma, Ap, ld, dot);
+    });
     block_column_partials<G, NT, 1>(dot, lane, col0, tcols, ld, partials, blockIdx.x, nslots);
 }
 
@@ -217,8 +242,12 @@ lap_ax_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ 
     gather_heavy<float, G, NT, WIN, float>(__ldg(rp + row), __ldg(rp + row + 1), ci, dinv, tin + col0, ld, lane,
                                            tcols, acc);
     KSum dot[1][NT][4];
-    if (threadIdx.x < G)
-        lap_ax_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, sqdeg, tin, p, mask, gamma, Ap, ld, dot);
+    if (threadIdx.x < G) {
+        RowVecs<G, NT> tv, pv;
+        tv.load(tin, row, lane, col0, tcols, ld);
+        pv.load(p, row, lane, col0, tcols, ld);
+        lap_ax_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, sqdeg, tv, pv, mask, gamma, Ap, ld, dot);
+    }
     block_column_partials<G, NT, 1>(dot, lane, col0, tcols, ld, partials, slot_base + blockIdx.x, nslots);
 }
 
@@ -421,42 +450,58 @@ struct Segs {
     }
 };
 
-// Column sums of block partials of one graph in a fixed order: a 32 x 16 thread
-// block covers 32 columns; thread row y sums slots y, y+16, ... of the graph's
-// row ranges, then (heavy = true) of its heavy rows, coalesced across columns;
-// then the 16 row sums are added in order.  nslots: the stride between the NS
-// quantities' slot arrays.
+// Column sums of block partials of one graph in a fixed order: a 32 x 32 thread
+// block covers 32 columns; thread row y sums slots y, y+32, ... of the graph's row
+// ranges, then (heavy = true) of its heavy rows, coalesced across columns, into four
+// interleaved running sums (slot i of the thread's sequence into sum i mod 4, so four
+// loads are in flight) that are added in order; then the 32 row sums are added in
+// order.  nslots: the stride between the NS quantities' slot arrays.
+constexpr int kReduceRows = 32;
+
 template <int NS>
 __device__ __forceinline__ void reduce_columns(const double* __restrict__ partials, int nslots, const Segs& sg,
                                                bool heavy, int64_t ldp, int j, double (&out)[NS]) {
-    __shared__ double red[NS][16][33];
+    __shared__ double red[NS][kReduceRows][33];
     const int x = threadIdx.x, y = threadIdx.y;
     int b0, b1, h0, h1;
     sg.get(blockIdx.y, b0, b1, h0, h1);
-    double s[NS];
+    double s[NS][4];
 #pragma unroll
-    for (int q = 0; q < NS; ++q) s[q] = 0.0;
-    for (int b = b0 + y; b < b1; b += 16)
+    for (int q = 0; q < NS; ++q)
 #pragma unroll
-        for (int q = 0; q < NS; ++q) s[q] += partials[((int64_t)q * nslots + b) * ldp + j];
-    if (heavy)
-        for (int h = h0 + y; h < h1; h += 16)
+        for (int u = 0; u < 4; ++u) s[q][u] = 0.0;
+    auto sweep = [&](int first, int end, int offset) {
+        int b = first + y;
+        for (; b + 3 * kReduceRows < end; b += 4 * kReduceRows)
 #pragma unroll
-            for (int q = 0; q < NS; ++q) s[q] += partials[((int64_t)q * nslots + sg.P + h) * ldp + j];
+            for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int q = 0; q < NS; ++q) red[q][y][x] = s[q];
+                for (int q = 0; q < NS; ++q)
+                    s[q][u] += partials[((int64_t)q * nslots + offset + b + u * kReduceRows) * ldp + j];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const int bb = b + u * kReduceRows;
+            if (bb < end)
+#pragma unroll
+                for (int q = 0; q < NS; ++q) s[q][u] += partials[((int64_t)q * nslots + offset + bb) * ldp + j];
+        }
+    };
+    sweep(b0, b1, 0);
+    if (heavy) sweep(h0, h1, sg.P);
+#pragma unroll
+    for (int q = 0; q < NS; ++q) red[q][y][x] = ((s[q][0] + s[q][1]) + s[q][2]) + s[q][3];
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
         double t = 0.0;
-        for (int i = 0; i < 16; ++i) t += red[q][i][x];
+        for (int i = 0; i < kReduceRows; ++i) t += red[q][i][x];
         out[q] = t;
     }
 }
 
 // pAp_j = sum of partials (row ranges and heavy rows); alpha_j = rz_j / pAp_j for
 // active columns.  Graph blockIdx.y's column j lives at state index y * ldp + j.
-__global__ void __launch_bounds__(512) cg_alpha_kernel(const double* __restrict__ partials, int nslots, Segs sg,
+__global__ void __launch_bounds__(1024) cg_alpha_kernel(const double* __restrict__ partials, int nslots, Segs sg,
                                                        int k, int64_t ldp, CgState st) {
     const int jc = blockIdx.x * 32 + threadIdx.x;
     double s[1];
@@ -467,7 +512,7 @@ __global__ void __launch_bounds__(512) cg_alpha_kernel(const double* __restrict_
 }
 
 // After an update: rz_new, rr; convergence; beta.  init != 0: first call (sets bn2, active).
-__global__ void __launch_bounds__(512) cg_beta_kernel(const double* __restrict__ partials, int nslots, Segs sg,
+__global__ void __launch_bounds__(1024) cg_beta_kernel(const double* __restrict__ partials, int nslots, Segs sg,
                                                       int k, int64_t ldp, CgState st, double tol2, int init) {
     const int jc = blockIdx.x * 32 + threadIdx.x;
     double s2[2];
@@ -495,7 +540,7 @@ __global__ void __launch_bounds__(512) cg_beta_kernel(const double* __restrict__
     }
 }
 
-__global__ void __launch_bounds__(512) column_sum_kernel(const double* __restrict__ partials, int nslots, Segs sg,
+__global__ void __launch_bounds__(1024) column_sum_kernel(const double* __restrict__ partials, int nslots, Segs sg,
                                                          int k, int64_t ldp, double* __restrict__ out) {
     const int j = blockIdx.x * 32 + threadIdx.x;
     double s[1];
@@ -695,7 +740,11 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                 int P = (g->num_sms * occ * waves + tiles - 1) / tiles;
                 if (P > lim) P = (int)lim;
                 if (P < g->n_graphs) P = g->n_graphs;  // a batch needs a range per graph
-                c.P = P < 1 ? 1 : P;
+                P = P < 1 ? 1 : P;
+                // the CTA's staged CSR slice must fit shared memory: more, shorter ranges if not
+                CSC_TRY(fit_staged_partition(g, P, std::max<int64_t>(lim, g->n_graphs), &P));
+                if (staged_smem(g, P) > kStagedSmemMax) continue;
+                c.P = P;
                 if (!cands.empty() && cands.back().G == c.G && cands.back().NT == c.NT &&
                     cands.back().threads == th && cands.back().P == c.P)
                     continue;
@@ -821,8 +870,8 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                 float ms = 0.f;
                 for (int rep = 0; rep < 4; ++rep) {
                     if (rep == 1) cudaEventRecord(g->ev[0], s);
-                    CG_SWITCH(c, lap_kernel<G_, NT_, false><<<grid, c.threads, 0, s>>>(
-                                     g->row_ptr, g->col_idx, g->dinv, g->invdeg, r, t1, pr, ld, ld, CgBatch()));
+                    CG_SWITCH(c, lap_kernel<G_, NT_, false><<<grid, c.threads, staged_smem(g, c.P), s>>>(
+                                     g->lrp, g->lci, g->dinv, g->invdeg, r, t1, pr, ld, ld, CgBatch()));
                 }
                 cudaEventRecord(g->ev[1], s);
                 CSC_CUDA_TRY(cudaEventSynchronize(g->ev[1]));
@@ -840,6 +889,8 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     }
     const int32_t* rpart = nullptr;
     CSC_TRY(get_partition(g, cfg.P, &rpart));
+    const int csmem = staged_smem(g, cfg.P);  // the CTA's CSR slice (stage_csr)
+    CSC_TRY(check_staged_smem(csmem));
     const dim3 grid(cfg.P, cfg.tiles);
     const int th = cfg.threads;
     const int P = cfg.P;
@@ -874,7 +925,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     // share of the sparse bytes that falls on heavy rows (launched separately)
     const double heavy_frac = g->nnz > 0 ? (double)(g->nnz - g->h_light.back()) / (double)g->nnz : 0.0;
     const dim3 kb(ceil_div(k, 32), nseg);
-    const dim3 rb(32, 16);
+    const dim3 rb(32, kReduceRows);
     CG_SWITCH(cfg, CSC_KLAUNCH("cg_update", blkb + 4.0 * N, s,
                                cg_update_kernel<G_, NT_><<<grid, th, 0, s>>>(x, r, p, Ap, nullptr, gid, pinv, rpart, ld,
                                                                              ld, part, bt_all)));
@@ -909,23 +960,23 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
             const double lb = csr_b + 2 * blkb;
             if (q == 0) {
                 if (H > 0)
-                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * heavy_frac, s,
+                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_heavy", lb * heavy_frac, s,
                                                lap_heavy_kernel<G_, NT_, true><<<hgrid, kHeavyThreads, 0, s>>>(
                                                    g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, g->heavy, ld,
                                                    ld, bb)));
                 CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * (1.0 - heavy_frac), s,
-                                           lap_kernel<G_, NT_, true><<<grid, th, 0, s>>>(
-                                               g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, rpart, ld, ld,
+                                           lap_kernel<G_, NT_, true><<<grid, th, csmem, s>>>(
+                                               g->lrp, g->lci, g->dinv, g->invdeg, cur, o, rpart, ld, ld,
                                                bb)));
             } else {
                 if (H > 0)
-                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * heavy_frac, s,
+                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_heavy", lb * heavy_frac, s,
                                                lap_heavy_kernel<G_, NT_, false><<<hgrid, kHeavyThreads, 0, s>>>(
                                                    g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, g->heavy, ld,
                                                    ld, bb)));
                 CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * (1.0 - heavy_frac), s,
-                                           lap_kernel<G_, NT_, false><<<grid, th, 0, s>>>(
-                                               g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, rpart, ld, ld,
+                                           lap_kernel<G_, NT_, false><<<grid, th, csmem, s>>>(
+                                               g->lrp, g->lci, g->dinv, g->invdeg, cur, o, rpart, ld, ld,
                                                bb)));
             }
             cur = o;
@@ -934,23 +985,23 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         const double ab = csr_b + 4.0 * N + 3 * blkb + scal_ax;
         if (g_power == 1) {
             if (H > 0)
-                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * heavy_frac, s,
+                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax_heavy", ab * heavy_frac, s,
                                            lap_ax_heavy_kernel<G_, NT_, true><<<hgrid, kHeavyThreads, 0, s>>>(
                                                g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma,
                                                Ap, g->heavy, ld, ld, part, P, PH, bb)));
             CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * (1.0 - heavy_frac), s,
-                                       lap_ax_kernel<G_, NT_, true><<<grid, th, 0, s>>>(
-                                           g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
+                                       lap_ax_kernel<G_, NT_, true><<<grid, th, csmem, s>>>(
+                                           g->lrp, g->lci, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
                                            rpart, ld, ld, part, PH, bb)));
         } else {
             if (H > 0)
-                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * heavy_frac, s,
+                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax_heavy", ab * heavy_frac, s,
                                            lap_ax_heavy_kernel<G_, NT_, false><<<hgrid, kHeavyThreads, 0, s>>>(
                                                g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma,
                                                Ap, g->heavy, ld, ld, part, P, PH, bb)));
             CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * (1.0 - heavy_frac), s,
-                                       lap_ax_kernel<G_, NT_, false><<<grid, th, 0, s>>>(
-                                           g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
+                                       lap_ax_kernel<G_, NT_, false><<<grid, th, csmem, s>>>(
+                                           g->lrp, g->lci, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
                                            rpart, ld, ld, part, PH, bb)));
         }
         return CSC_OK;

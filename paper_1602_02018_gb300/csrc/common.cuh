@@ -90,6 +90,7 @@ enum WsSlot {
     WS_COEF,        // per-graph filter coefficients of a batch
     WS_COEF1,       // filter coefficients read by a captured CUDA graph
     WS_XR,          // s R, read by every order of the Clenshaw form
+    WS_CHECK,       // flag word of the non-finite scan (CSC_CHECK_FINITE)
     WS_COUNT
 };
 
@@ -103,7 +104,6 @@ struct Buffer {
 // (one CTA each per tile) and `tiles` column tiles.
 struct LaunchCfg {
     int G = 0, NT = 0, threads = 0, P = 0, tiles = 1;
-    int win = 0;  // rows of the shared-memory neighbour window (0: none)
 };
 
 struct Graph {
@@ -136,16 +136,21 @@ struct Graph {
     int32_t deg_quant[6] = {0, 0, 0, 0, 0, 0};    // degrees at p = 0, .1, .25, .5, .75, 1 (floor(p (N-1)))
     int32_t* heavy = nullptr;                     // device int32[n_heavy]: heavy rows
     int n_heavy = 0;
+    // compact light CSR (device.cuh: stage_csr): lrp int32[N+1] = light edges before each
+    // row, bit 31 of lrp[i+1] set for a heavy row i; lci = the light rows' indices.  Without
+    // heavy rows they alias row_ptr / col_idx (light_owned = false).
+    int32_t* lrp = nullptr;
+    int32_t* lci = nullptr;
+    bool light_owned = false;
     std::map<int, int32_t*> parts;                // P -> device int32[P+1] row-range bounds
     std::map<int, std::vector<int32_t>> h_parts;  // host copies of the bounds
+    std::map<int, int> part_smem;                 // P -> shared-memory bytes of the largest staged range
     std::map<int, int32_t*> part_gblk;            // P -> device int32[G+1]: first range of each graph
     int32_t* d_hvy_start = nullptr;               // device int32[G+1]: first heavy row of each graph
     // captured CUDA graphs of fixed launch sequences (key -> executable, kernel launches)
     bool use_graphs = true;
     cudaStream_t cap_stream = nullptr;
     std::map<std::string, std::pair<cudaGraphExec_t, int64_t>> graphs;
-    std::map<std::pair<int, int>, int32_t*> wins; // (P, W) -> device int32[P] window starts
-    int* dev_err = nullptr;                       // device error word (bounded waits that gave up)
     std::map<uint64_t, LaunchCfg> tuned;          // (kernel kind, dtype, columns) -> shape
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     double* pinned = nullptr;  // small pinned host staging (4096 doubles)
@@ -204,13 +209,22 @@ csc_status replay_graph(Graph* g, const std::string& key, cudaStream_t s, int64_
 
 // P contiguous row ranges of about equal cost (edges + 2 per row); cached per P.
 csc_status get_partition(Graph* g, int P, const int32_t** out);
+// Shared-memory bytes a CTA needs to stage the CSR slice of the largest range of
+// partition P (get_partition must have built it).
+int staged_smem(const Graph* g, int P);
+// Most shared memory a staged CSR slice may take (within the 48 KB a CTA gets without
+// an opt-in, beside the kernels' own reduction arrays of up to 16 KB).
+constexpr int kStagedSmemMax = 30 * 1024;
+csc_status check_staged_smem(int bytes);
+// The smallest row-range count >= P (doubling, at most max_p) whose staged slices fit
+// kStagedSmemMax; builds the partitions it tries.
+csc_status fit_staged_partition(Graph* g, int P, int64_t max_p, int* out);
 // Per-graph segments of partition P: first range of each graph (device int32[G+1]; a
 // batched handle's ranges never straddle graphs) and first heavy row of each graph.
 csc_status get_segments(Graph* g, int P, const int32_t** gblk, const int32_t** ghvy);
 
 // Start rows of the W-row windows (one per row range of partition P) that cover
 // the most neighbour indices of each range; cached per (P, W).
-csc_status get_windows(Graph* g, int P, int W, const int32_t** out);
 
 // Device helpers exported by the kernel translation units -----------------
 
@@ -257,6 +271,10 @@ csc_status run_sample_weighted(const double* score, int64_t N, int64_t n, uint64
                                float* w_out, Graph* scratch_owner, cudaStream_t s);
 csc_status run_row_scores(void* Y, bool y_f64, int64_t N, int d, int ld, double* score, bool normalize,
                           int num_sms, cudaStream_t s);
+// spmm.cu: CSC_E_NUMERIC if any of the first `cols` entries of the `rows` rows (stride ld)
+// of X (fp32, or fp64 when x_f64) is NaN or infinite; synchronizes s.  `what` names X.
+csc_status run_check_finite(Graph* g, const void* X, bool x_f64, int64_t rows, int cols, int ld, const char* what,
+                            cudaStream_t s);
 csc_status run_sample(int64_t N, int64_t n, uint64_t seed, int64_t* idx_out, Graph* scratch_owner,
                       cudaStream_t s);
 csc_status run_gather_rows(const float* X, int64_t N, int ld, const int64_t* idx, int64_t n, int d,

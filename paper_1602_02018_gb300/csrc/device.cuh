@@ -24,14 +24,15 @@ struct StoreTraits;
 template <>
 struct StoreTraits<float> {
     using acc_t = float;
+    using raw_t = float4;  // one 16-byte vector as loaded (prefetched operands)
     static constexpr int VEC = 4;
-    __device__ static inline void load(const float* p, float (&v)[4]) {
-        float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    __device__ static inline raw_t ld_raw(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+    __device__ static inline raw_t ld_raw_cs(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+    __device__ static inline void unraw(const raw_t& q, float (&v)[4]) {
         v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
     }
-    // generic-address load (global or shared memory)
-    __device__ static inline void load_generic(const float* p, float (&v)[4]) {
-        const float4 q = *reinterpret_cast<const float4*>(p);
+    __device__ static inline void load(const float* p, float (&v)[4]) {
+        float4 q = __ldg(reinterpret_cast<const float4*>(p));
         v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
     }
     // streaming load (data read once: X_{j-1}, Y)
@@ -52,7 +53,12 @@ struct StoreTraits<float> {
 template <>
 struct StoreTraits<__nv_bfloat16> {
     using acc_t = float;
+    using raw_t = uint4;
     static constexpr int VEC = 8;
+    __device__ static inline raw_t ld_raw(const __nv_bfloat16* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+    __device__ static inline raw_t ld_raw_cs(const __nv_bfloat16* p) {
+        return __ldcs(reinterpret_cast<const uint4*>(p));
+    }
     __device__ static inline void unpack(const uint4& q, float (&v)[8]) {
         const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
 #pragma unroll
@@ -62,12 +68,9 @@ struct StoreTraits<__nv_bfloat16> {
             v[2 * i + 1] = f.y;
         }
     }
+    __device__ static inline void unraw(const raw_t& q, float (&v)[8]) { unpack(q, v); }
     __device__ static inline void load(const __nv_bfloat16* p, float (&v)[8]) {
         uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
-        unpack(q, v);
-    }
-    __device__ static inline void load_generic(const __nv_bfloat16* p, float (&v)[8]) {
-        const uint4 q = *reinterpret_cast<const uint4*>(p);
         unpack(q, v);
     }
     __device__ static inline void load_cs(const __nv_bfloat16* p, float (&v)[8]) {
@@ -95,13 +98,15 @@ struct StoreTraits<__nv_bfloat16> {
 template <>
 struct StoreTraits<double> {
     using acc_t = double;
+    using raw_t = double2;
     static constexpr int VEC = 2;
-    __device__ static inline void load(const double* p, double (&v)[2]) {
-        double2 q = __ldg(reinterpret_cast<const double2*>(p));
+    __device__ static inline raw_t ld_raw(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
+    __device__ static inline raw_t ld_raw_cs(const double* p) { return __ldcs(reinterpret_cast<const double2*>(p)); }
+    __device__ static inline void unraw(const raw_t& q, double (&v)[2]) {
         v[0] = q.x; v[1] = q.y;
     }
-    __device__ static inline void load_generic(const double* p, double (&v)[2]) {
-        const double2 q = *reinterpret_cast<const double2*>(p);
+    __device__ static inline void load(const double* p, double (&v)[2]) {
+        double2 q = __ldg(reinterpret_cast<const double2*>(p));
         v[0] = q.x; v[1] = q.y;
     }
     __device__ static inline void load_cs(const double* p, double (&v)[2]) {
@@ -191,6 +196,140 @@ __device__ __forceinline__ void acc_vec(double (&acc)[VEC], double w, const doub
     for (int v = 0; v < VEC; ++v) acc[v] = WEIGHTED ? fma(w, x[v], acc[v]) : acc[v] + x[v];
 }
 
+// The rows r0 + first, r0 + first + stride, ... below r1 of a CTA's row range, each
+// passed to body(row, e0, e1) with its edge range [e0, e1) -- rows with more than
+// kHeavyRow edges (common.cuh) are skipped.  The next row's extents are loaded before the current
+// row is processed, so the row-pointer load is off the critical path of the gather.
+template <typename Body>
+__device__ __forceinline__ void for_each_row(const int32_t* __restrict__ rp, int r0, int r1, int stride, Body&& body) {
+    int row = r0;
+    int e0 = 0, e1 = 0;
+    if (row < r1) {
+        e0 = __ldg(rp + row);
+        e1 = __ldg(rp + row + 1);
+    }
+    while (row < r1) {
+        const int nrow = row + stride;
+        int n0 = 0, n1 = 0;
+        if (nrow < r1) {
+            n0 = __ldg(rp + nrow);
+            n1 = __ldg(rp + nrow + 1);
+        }
+        if (e1 - e0 <= kHeavyRow) body(row, e0, e1);
+        row = nrow;
+        e0 = n0;
+        e1 = n1;
+    }
+}
+
+// ------------------------------------------------ CSR slice staged in shared memory
+// The light part of the CSR in a compact form: lrp[i] (i = 0..N) is the number of
+// light-row edges before row i, with bit 31 of lrp[i + 1] set when row i is heavy
+// (its edges, left to the one-CTA-per-row kernels, are not in lci); lci holds the
+// light rows' column indices back to back.  A CTA whose rows are [r0, r1) copies
+// lrp[r0 .. r1] and its rows' indices lci[lrp[r0] .. lrp[r1]) into shared memory with
+// asynchronous copies, so that no index load is on the path of a row's gather.
+constexpr int32_t kHeavyBit = (int32_t)0x80000000u;
+constexpr int32_t kEdgeMask = 0x7fffffff;
+
+__device__ __forceinline__ void cp_async4(int32_t* smem_dst, const int32_t* gmem_src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+struct StagedCsr {
+    const int32_t* rp;  // shared: lrp[r0 .. r1] as loaded (bit 31 = the previous row is heavy)
+    const int32_t* ci;  // shared: the range's light column indices
+    int r0, nr, base;
+};
+
+// Copies the CSR slice of rows [r0, r1) into smem (which must hold (r1 - r0) + 1 +
+// light edges of the range entries) and waits for it with the whole CTA.  Every thread
+// of the CTA must call it.
+__device__ __forceinline__ StagedCsr stage_csr(const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci,
+                                               int r0, int r1, int32_t* smem) {
+    const int nr = r1 > r0 ? r1 - r0 : 0;
+    const int base = nr ? (__ldg(lrp + r0) & kEdgeMask) : 0;
+    const int ne = nr ? (__ldg(lrp + r1) & kEdgeMask) - base : 0;
+    int32_t* s_rp = smem;
+    int32_t* s_ci = smem + nr + 1;
+    for (int i = threadIdx.x; i <= nr && nr; i += blockDim.x) cp_async4(s_rp + i, lrp + r0 + i);
+    for (int k = threadIdx.x; k < ne; k += blockDim.x) cp_async4(s_ci + k, lci + base + k);
+    cp_async_wait_all();
+    __syncthreads();
+    StagedCsr c;
+    c.rp = s_rp;
+    c.ci = s_ci;
+    c.r0 = r0;
+    c.nr = nr;
+    c.base = base;
+    return c;
+}
+
+// Rows first, first + stride, ... of a staged range, each passed to body(row, e0, e1)
+// with its edge range [e0, e1) in c.ci; heavy rows are skipped.
+template <typename Body>
+__device__ __forceinline__ void for_each_staged_row(const StagedCsr& c, int first, int stride, Body&& body) {
+    for (int i = first; i < c.nr; i += stride) {
+        const int32_t v1 = c.rp[i + 1];
+        if (v1 & kHeavyBit) continue;
+        body(c.r0 + i, (c.rp[i] & kEdgeMask) - c.base, v1 - c.base);
+    }
+}
+
+// Neighbour sum of one row whose column indices ci[e .. end) are in shared memory
+// (see gather_range for acc, G, NT and the weights): every lane of a group reads each
+// index itself (one broadcast shared-memory word), so no shuffle or global index load
+// precedes the neighbour-row loads.
+template <typename T, int G, int NT, bool WEIGHTED, typename W>
+__device__ __forceinline__ void gather_staged(int e, const int end, const int32_t* ci, const W* __restrict__ wv,
+                                              const T* __restrict__ X, int64_t ld, int lane, int ncols,
+                                              typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC]) {
+    using Tr = StoreTraits<T>;
+    using A = typename Tr::acc_t;
+    constexpr int VEC = Tr::VEC;
+    // edges in flight per lane: 8 one-vector rows, or 4 rows of NT >= 2 vectors
+    constexpr int B = NT == 1 ? 8 : 4;
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) acc[t][v] = A(0);
+    bool valid[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) valid[t] = ((t * G + lane) * VEC) < ncols;
+    for (; e < end; e += B) {
+        const int cnt = min(B, end - e);
+        const T* rowp[B];
+        A w[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int l = u < cnt ? ci[e + u] : 0;
+            rowp[u] = X + (int64_t)l * ld + lane * VEC;
+            if (WEIGHTED) w[u] = u < cnt ? A(__ldg(wv + l)) : A(0);
+            else w[u] = A(1);
+        }
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            if (!valid[t]) continue;
+            A x[B][VEC];
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                if (u < cnt)
+                    Tr::load(rowp[u] + t * G * VEC, x[u]);
+                else
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) x[u][v] = A(0);
+            }
+#pragma unroll
+            for (int u = 0; u < B; ++u) acc_vec<WEIGHTED, VEC>(acc[t], w[u], x[u]);
+        }
+    }
+}
+
 // Neighbour sum of one row: acc[t][v] = sum_{e in row} w_e * X[col[e], c(t, v)] with
 // c(t, v) = (t * G + lane) * VEC + v, where w_e = wv[col[e]] if WEIGHTED, else 1
 // (the pre-scaled operand form, whose weights are folded into the rows of X).
@@ -199,15 +338,11 @@ __device__ __forceinline__ void acc_vec(double (&acc)[VEC], double w, const doub
 // within the group, so the neighbour-row loads of a chunk issue back to back
 // without a dependent index load in front of each.  Columns >= ncols are
 // skipped (their accumulators stay 0).
-//
-// With SWIN, rows w0 .. w0+wn-1 of X (full rows, row stride ld) are also held
-// in shared memory at swin, and neighbours inside that window are read there.
-template <typename T, int G, int NT, bool WEIGHTED, typename W, bool SWIN = false>
+template <typename T, int G, int NT, bool WEIGHTED, typename W>
 __device__ __forceinline__ void gather_range(int e, const int end, const int32_t* __restrict__ ci,
                                              const W* __restrict__ wv, const T* __restrict__ X, int64_t ld,
                                              int lane, int ncols,
-                                             typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC],
-                                             const T* swin = nullptr, int w0 = 0, int wn = 0) {
+                                             typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC]) {
     using Tr = StoreTraits<T>;
     using A = typename Tr::acc_t;
     constexpr int VEC = Tr::VEC;
@@ -250,22 +385,15 @@ __device__ __forceinline__ void gather_range(int e, const int end, const int32_t
             // one address per neighbour row; the tiles of a lane are fixed offsets from it
             const T* rowp[B];
 #pragma unroll
-            for (int u = 0; u < B; ++u) {
-                if (SWIN && (unsigned)(l[u] - w0) < (unsigned)wn)
-                    rowp[u] = swin + (int64_t)(l[u] - w0) * ld + lane * VEC;  // shared-memory copy
-                else
-                    rowp[u] = X + (int64_t)l[u] * ld + lane * VEC;
-            }
+            for (int u = 0; u < B; ++u) rowp[u] = X + (int64_t)l[u] * ld + lane * VEC;
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
                 if (!valid[t]) continue;
                 A x[B][VEC];
 #pragma unroll
                 for (int u = 0; u < B; ++u) {
-                    if (q0 + u < cnt) {
-                        if (SWIN) Tr::load_generic(rowp[u] + t * G * VEC, x[u]);
-                        else Tr::load(rowp[u] + t * G * VEC, x[u]);
-                    }
+                    if (q0 + u < cnt)
+                        Tr::load(rowp[u] + t * G * VEC, x[u]);
                     else
 #pragma unroll
                         for (int v = 0; v < VEC; ++v) x[u][v] = A(0);
@@ -278,14 +406,12 @@ __device__ __forceinline__ void gather_range(int e, const int end, const int32_t
 }
 
 // The neighbour sum of a whole row (see gather_range).
-template <typename T, int G, int NT, bool WEIGHTED, typename W, bool SWIN = false>
+template <typename T, int G, int NT, bool WEIGHTED, typename W>
 __device__ __forceinline__ void gather_row(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                            const W* __restrict__ wv, const T* __restrict__ X, int64_t ld, int row,
                                            int lane, int ncols,
-                                           typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC],
-                                           const T* swin = nullptr, int w0 = 0, int wn = 0) {
-    gather_range<T, G, NT, WEIGHTED, W, SWIN>(__ldg(rp + row), __ldg(rp + row + 1), ci, wv, X, ld, lane, ncols, acc,
-                                              swin, w0, wn);
+                                           typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC]) {
+    gather_range<T, G, NT, WEIGHTED, W>(__ldg(rp + row), __ldg(rp + row + 1), ci, wv, X, ld, lane, ncols, acc);
 }
 
 // Neighbour sum of a heavy row (see kHeavyRow) by a whole CTA of kHeavyThreads
@@ -331,44 +457,6 @@ __device__ __forceinline__ void gather_heavy(int e0, int e1, const int32_t* __re
                 for (int i = 0; i < WARPS; ++i) s += red[i * TW + (t * G + lane) * VEC + v];
                 acc[t][v] = s;
             }
-}
-
-// ------------------------------------------------------ bulk copies (TMA)
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// global -> shared bulk copy completing on the mbarrier (16-byte aligned, size % 16 == 0)
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-// Bounded wait for phase `parity` of the mbarrier; false if the limit was reached.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int max_tries) {
-    const uint32_t a = smem_addr(bar);
-    for (int i = 0; i < max_tries; ++i) {
-        uint32_t done = 0;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
 }
 
 // ------------------------------------------------------------ generators

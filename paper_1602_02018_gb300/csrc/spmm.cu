@@ -185,18 +185,49 @@ __global__ void copy_in_kernel(T* __restrict__ X, const float* __restrict__ R, i
 // the column tile [y*TW, (y+1)*TW) with TW = G*NT*VEC.  Rows with more than
 // kHeavyRow edges are skipped here and done by the *_heavy kernels.
 
-// The per-row update of one order given the row's neighbour sum acc (column tile col0).
+// Operands of one row of a forward order that do not depend on the gather: Z_0 (first
+// order) or Z_{j-1}, and the accumulator row of Y (not on the first order); loaded
+// before the neighbour sum so their latency overlaps it.
+template <typename T, int G, int NT>
+struct ChebOperands {
+    using A = typename StoreTraits<T>::acc_t;
+    typename StoreTraits<T>::raw_t z[NT];
+    A y[NT][StoreTraits<T>::VEC];
+    __device__ __forceinline__ void load(int row, int lane, int col0, int tcols, int mode, const T* __restrict__ zcur,
+                                         const T* __restrict__ zprev, const A* __restrict__ Y,
+                                         const int32_t* __restrict__ perm, int64_t ld) {
+        using Tr = StoreTraits<T>;
+        constexpr int VEC = Tr::VEC;
+        const bool first = (mode & 1) != 0, keep = (mode & 4) != 0;
+        const int64_t yrow = perm ? (int64_t)perm[row] : (int64_t)row;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int cl = (t * G + lane) * VEC;
+            if (cl >= tcols) continue;
+            const int64_t o = (int64_t)row * ld + col0 + cl;
+            if (first) {
+                z[t] = Tr::ld_raw(zcur + o);
+            } else {
+                z[t] = keep ? Tr::ld_raw(zprev + o) : Tr::ld_raw_cs(zprev + o);
+                if (keep) AccIO<A, VEC>::load(Y + yrow * ld + col0 + cl, y[t]);
+                else AccIO<A, VEC>::load_cs(Y + yrow * ld + col0 + cl, y[t]);
+            }
+        }
+    }
+};
 
+// The per-row update of one order given the row's neighbour sum acc (column tile col0)
+// and the row's prefetched operands op.
 template <typename T, int G, int NT>
 __device__ __forceinline__ void cheb_epilogue(int row, int lane, int col0, int tcols,
                                               typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC],
                                               const typename StoreTraits<T>::acc_t* __restrict__ invdeg,
                                               const typename StoreTraits<T>::acc_t* __restrict__ sqdeg,
-                                              const T* __restrict__ zcur, T* __restrict__ zprev_next,
+                                              T* __restrict__ zprev_next,
                                               typename StoreTraits<T>::acc_t* __restrict__ Y,
                                               const int32_t* __restrict__ perm, int64_t ld,
                                               typename StoreTraits<T>::acc_t c0, typename StoreTraits<T>::acc_t c_next,
-                                              int mode) {
+                                              int mode, const ChebOperands<T, G, NT>& op) {
     using Tr = StoreTraits<T>;
     using A = typename Tr::acc_t;
     constexpr int VEC = Tr::VEC;
@@ -215,7 +246,7 @@ __device__ __forceinline__ void cheb_epilogue(int row, int lane, int col0, int t
         A* y_ptr = Y + yrow * ld + c;
         if (first) {
             A z0[VEC];
-            Tr::load(zcur + (int64_t)row * ld + c, z0);
+            Tr::unraw(op.z[t], z0);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v]);
             Tr::store(zp_ptr, zn);
@@ -224,15 +255,12 @@ __device__ __forceinline__ void cheb_epilogue(int row, int lane, int col0, int t
             for (int v = 0; v < VEC; ++v) y[v] = (c0 * z0[v] + c_next * zn[v]) * back;
         } else {
             A zp[VEC];
-            if (keep) Tr::load(zp_ptr, zp);
-            else Tr::load_cs(zp_ptr, zp);
+            Tr::unraw(op.z[t], zp);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v] - zp[v]);
             Tr::store(zp_ptr, zn);
-            if (keep) AccIO<A, VEC>::load(y_ptr, y);
-            else AccIO<A, VEC>::load_cs(y_ptr, y);
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) y[v] = fma(c_next, zn[v], y[v]) * back;
+            for (int v = 0; v < VEC; ++v) y[v] = fma(c_next, zn[v], op.y[t][v]) * back;
         }
         // Y is read again only by the next order: evict-first keeps Z_j resident in L2
         // (unless everything fits there)
@@ -243,7 +271,7 @@ __device__ __forceinline__ void cheb_epilogue(int row, int lane, int col0, int t
 
 template <typename T, int G, int NT>
 __global__ void __launch_bounds__(512)
-cheb_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+cheb_step_kernel(const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci,
                  const typename StoreTraits<T>::acc_t* __restrict__ invdeg,
                  const typename StoreTraits<T>::acc_t* __restrict__ sqdeg, const T* __restrict__ zcur,
                  T* __restrict__ zprev_next, typename StoreTraits<T>::acc_t* __restrict__ Y,
@@ -262,14 +290,16 @@ cheb_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
         c0 = cg[0];
         c_next = cg[tab.j];
     }
-    for (int row = r0 + (int)(threadIdx.x / G); row < r1; row += (int)(blockDim.x / G)) {
-        const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
-        if (e1 - e0 > kHeavyRow) continue;
+    extern __shared__ int32_t s_csr[];
+    const StagedCsr sc = stage_csr(lrp, lci, r0, r1, s_csr);
+    for_each_staged_row(sc, (int)(threadIdx.x / G), (int)(blockDim.x / G), [&](int row, int e0, int e1) {
+        ChebOperands<T, G, NT> op;
+        op.load(row, lane, col0, tcols, mode, zcur, zprev_next, Y, perm, ld);
         A acc[NT][VEC];
-        gather_range<T, G, NT, false, A>(e0, e1, ci, nullptr, zcur + col0, ld, lane, tcols, acc);
-        cheb_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, sqdeg, zcur, zprev_next, Y, perm, ld, c0, c_next,
-                                mode);
-    }
+        gather_staged<T, G, NT, false, A>(e0, e1, sc.ci, nullptr, zcur + col0, ld, lane, tcols, acc);
+        cheb_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, sqdeg, zprev_next, Y, perm, ld, c0, c_next, mode,
+                                op);
+    });
 }
 
 // Heavy rows: one CTA (kHeavyThreads threads) per row, its groups splitting the edges.
@@ -297,52 +327,11 @@ cheb_step_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict
     A acc[NT][VEC];
     gather_heavy<T, G, NT, false, A>(__ldg(rp + row), __ldg(rp + row + 1), ci, nullptr, zcur + col0, ld, lane, tcols,
                                      acc);
-    if (threadIdx.x < G)
-        cheb_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, sqdeg, zcur, zprev_next, Y, perm, ld, c0, c_next,
-                                mode);
-}
-
-// The same order with a shared-memory neighbour window: the CTA first copies rows
-// win[x] .. win[x]+wn-1 of Z_j (full rows, contiguous in memory) into shared memory
-// with bulk asynchronous copies, then reads the neighbours inside that window
-// there.  The wait on the copies is bounded; a CTA that gives up sets *err and
-// reads every neighbour from global memory instead.
-template <typename T, int G, int NT>
-__global__ void __launch_bounds__(512)
-cheb_step_win_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                     const typename StoreTraits<T>::acc_t* __restrict__ invdeg,
-                     const typename StoreTraits<T>::acc_t* __restrict__ sqdeg, const T* __restrict__ zcur,
-                     T* __restrict__ zprev_next, typename StoreTraits<T>::acc_t* __restrict__ Y,
-                     const int32_t* __restrict__ perm, const int32_t* __restrict__ part, int ncols, int64_t ld,
-                     typename StoreTraits<T>::acc_t c0, typename StoreTraits<T>::acc_t c_next, int mode,
-                     const int32_t* __restrict__ win, int wn, int* __restrict__ err) {
-    using A = typename StoreTraits<T>::acc_t;
-    constexpr int VEC = StoreTraits<T>::VEC;
-    extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-    T* swin = reinterpret_cast<T*>(smem + 128);
-    const int w0 = win[blockIdx.x];
-    const uint32_t total = (uint32_t)((size_t)wn * ld * sizeof(T));
-    if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
-        mbar_expect_tx(bar, total);
-        const char* src = reinterpret_cast<const char*>(zcur + (int64_t)w0 * ld);
-        for (uint32_t off = 0; off < total; off += 65536u)
-            bulk_g2s(reinterpret_cast<char*>(swin) + off, src + off, min(65536u, total - off), bar);
-    }
-    __syncthreads();  // the barrier is initialised before anyone waits on it
-    const bool ok = mbar_wait(bar, 0, 1 << 20);
-    if (!ok) atomicOr(err, 1);
-    const int wuse = ok ? wn : 0;
-    const int lane = threadIdx.x % G;
-    const int r1 = part[blockIdx.x + 1];
-    for (int row = part[blockIdx.x] + (int)(threadIdx.x / G); row < r1; row += (int)(blockDim.x / G)) {
-        const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
-        if (e1 - e0 > kHeavyRow) continue;
-        A acc[NT][VEC];
-        gather_range<T, G, NT, false, A, true>(e0, e1, ci, nullptr, zcur, ld, lane, ncols, acc, swin, w0, wuse);
-        cheb_epilogue<T, G, NT>(row, lane, 0, ncols, acc, invdeg, sqdeg, zcur, zprev_next, Y, perm, ld, c0, c_next,
-                                mode);
+    if (threadIdx.x < G) {
+        ChebOperands<T, G, NT> op;
+        op.load(row, lane, col0, tcols, mode, zcur, zprev_next, Y, perm, ld);
+        cheb_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, sqdeg, zprev_next, Y, perm, ld, c0, c_next, mode,
+                                op);
     }
 }
 
@@ -371,11 +360,36 @@ __global__ void scale_copy_kernel(const T* __restrict__ X, typename StoreTraits<
 // order writes Y (optionally normalised per row when one column tile holds the
 // whole row).
 
+// Operands of one row of a Clenshaw order that do not depend on the gather: s R and
+// B_{j+2} (none on the first order, j = m-1), loaded before the neighbour sum so their
+// latency overlaps it.  mode bits as in clenshaw_epilogue.
+template <typename T, int G, int NT>
+struct ClenOperands {
+    typename StoreTraits<T>::raw_t r[NT], b2[NT];
+    __device__ __forceinline__ void load(int row, int lane, int col0, int tcols, int mode, const T* __restrict__ rs,
+                                         const T* __restrict__ bpp, int64_t ld) {
+        using Tr = StoreTraits<T>;
+        constexpr int VEC = Tr::VEC;
+        const bool first = (mode & 1) != 0, keep = (mode & 4) != 0;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int cl = (t * G + lane) * VEC;
+            if (cl >= tcols) continue;
+            const int64_t o = (int64_t)row * ld + col0 + cl;
+            // s R and B_{j+2} are dead after this order: evict-first unless all fits L2, so
+            // the gathered B_{j+1} and the B_j written here (gathered next) stay resident
+            r[t] = keep ? Tr::ld_raw(rs + o) : Tr::ld_raw_cs(rs + o);
+            if (!first) b2[t] = keep ? Tr::ld_raw(bpp + o) : Tr::ld_raw_cs(bpp + o);
+        }
+    }
+};
+
 // Row epilogue of one Clenshaw order.  mode: 1 = no B_{j+2} (j = m-1), 2 = last
 // order (write Y), 4 = plain caching (working set fits L2), 8 = normalise Y rows
 // (the group's lanes hold the whole row; gmask = the group's lanes).
-// rs: the block s R stored in T (internal row order, stride ld).  LAST: the order
-// j = 0 (writes Y); a separate instantiation so the other orders carry no Y state.
+// op: the row's s R (the block stored in T, internal row order) and B_{j+2}.  LAST:
+// the order j = 0 (writes Y); a separate instantiation so the other orders carry no Y
+// state.
 template <typename T, int G, int NT, bool LAST>
 __device__ __forceinline__ void clenshaw_epilogue(int row, int lane, int col0, int tcols,
                                                   typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC],
@@ -384,11 +398,11 @@ __device__ __forceinline__ void clenshaw_epilogue(int row, int lane, int col0, i
                                                   T* __restrict__ bpp, typename StoreTraits<T>::acc_t* __restrict__ Y,
                                                   const int32_t* __restrict__ perm, int64_t ld,
                                                   typename StoreTraits<T>::acc_t cj, int mode,
-                                                  const T* __restrict__ rs, unsigned gmask) {
+                                                  const ClenOperands<T, G, NT>& op, unsigned gmask) {
     using Tr = StoreTraits<T>;
     using A = typename Tr::acc_t;
     constexpr int VEC = Tr::VEC;
-    const bool first = (mode & 1) != 0, keep = (mode & 4) != 0;
+    const bool first = (mode & 1) != 0;
     constexpr bool last = LAST;
     const A f = (last ? A(-1) : A(-2)) * invdeg[row];
     A out[LAST ? NT : 1][VEC];
@@ -399,17 +413,12 @@ __device__ __forceinline__ void clenshaw_epilogue(int row, int lane, int col0, i
         const int c = col0 + cl;
         const int to = LAST ? t : 0;
         A r[VEC], b2[VEC];
-        // s R and B_{j+2} are dead after this order: evict-first unless all fits L2, so
-        // the gathered B_{j+1} and the B_j written here (gathered next) stay resident
-        if (keep) Tr::load(rs + (int64_t)row * ld + c, r);
-        else Tr::load_cs(rs + (int64_t)row * ld + c, r);
+        Tr::unraw(op.r[t], r);
         if (first) {
 #pragma unroll
             for (int v = 0; v < VEC; ++v) b2[v] = A(0);
-        } else if (keep) {
-            Tr::load(bpp + (int64_t)row * ld + c, b2);
         } else {
-            Tr::load_cs(bpp + (int64_t)row * ld + c, b2);
+            Tr::unraw(op.b2[t], b2);
         }
 #pragma unroll
         for (int v = 0; v < VEC; ++v) out[to][v] = cj * r[v] + f * acc[t][v] - b2[v];
@@ -460,7 +469,7 @@ __device__ __forceinline__ void clenshaw_epilogue(int row, int lane, int col0, i
 
 template <typename T, int G, int NT, bool LAST>
 __global__ void __launch_bounds__(512)
-clenshaw_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+clenshaw_step_kernel(const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci,
                      const typename StoreTraits<T>::acc_t* __restrict__ invdeg,
                      const typename StoreTraits<T>::acc_t* __restrict__ sqdeg,
                      const T* __restrict__ bnext, T* __restrict__ bpp, typename StoreTraits<T>::acc_t* __restrict__ Y,
@@ -480,14 +489,16 @@ clenshaw_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__
     if (tab.c && r0 < r1) cj = (tab.gid ? tab.c + (int64_t)tab.gid[r0] * tab.stride : tab.c)[tab.j];
     const unsigned gmask =
         G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(unsigned)(G - 1)));
-    for (int row = r0 + (int)(threadIdx.x / G); row < r1; row += (int)(blockDim.x / G)) {
-        const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
-        if (e1 - e0 > kHeavyRow) continue;
+    extern __shared__ int32_t s_csr[];
+    const StagedCsr sc = stage_csr(lrp, lci, r0, r1, s_csr);
+    for_each_staged_row(sc, (int)(threadIdx.x / G), (int)(blockDim.x / G), [&](int row, int e0, int e1) {
+        ClenOperands<T, G, NT> op;
+        op.load(row, lane, col0, tcols, mode, rs, bpp, ld);
         A acc[NT][VEC];
-        gather_range<T, G, NT, false, A>(e0, e1, ci, nullptr, bnext + col0, ld, lane, tcols, acc);
-        clenshaw_epilogue<T, G, NT, LAST>(row, lane, col0, tcols, acc, invdeg, sqdeg, bpp, Y, perm, ld, cj, mode, rs,
+        gather_staged<T, G, NT, false, A>(e0, e1, sc.ci, nullptr, bnext + col0, ld, lane, tcols, acc);
+        clenshaw_epilogue<T, G, NT, LAST>(row, lane, col0, tcols, acc, invdeg, sqdeg, bpp, Y, perm, ld, cj, mode, op,
                                           gmask);
-    }
+    });
 }
 
 template <typename T, int G, int NT>
@@ -513,12 +524,14 @@ clenshaw_step_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __rest
                                      acc);
     const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
     if (threadIdx.x < G) {
+        ClenOperands<T, G, NT> op;
+        op.load(row, lane, col0, tcols, mode, rs, bpp, ld);
         if (mode & 2)
             clenshaw_epilogue<T, G, NT, true>(row, lane, col0, tcols, acc, invdeg, sqdeg, bpp, Y, perm, ld, cj, mode,
-                                              rs, gmask);
+                                              op, gmask);
         else
             clenshaw_epilogue<T, G, NT, false>(row, lane, col0, tcols, acc, invdeg, sqdeg, bpp, Y, perm, ld, cj, mode,
-                                               rs, gmask);
+                                               op, gmask);
     }
 }
 
@@ -553,12 +566,30 @@ __global__ void normalize_kernel(A* __restrict__ Y, int32_t N, int d, int ld, do
 // sum_i d_i <Z_a, Z_b>_i (d_i -> 1 for an isolated node):
 //   first: s0 = <X0,X0>, s1 = <X1,X0>, s2 = <X1,X1>
 //   later: s1 = <X_{j+1},X_j>, s2 = <X_{j+1},X_{j+1}>
+// The row's Z_j and Z_{j-1} (not on the first step), loaded before the neighbour sum.
+template <typename T, int NT>
+struct MomOperands {
+    typename StoreTraits<T>::raw_t zc[NT], zp[NT];
+    __device__ __forceinline__ void load(int row, int lane, int G, int col0, int tcols, int first,
+                                         const T* __restrict__ zcur, const T* __restrict__ zprev, int64_t ld) {
+        using Tr = StoreTraits<T>;
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int cl = (t * G + lane) * Tr::VEC;
+            if (cl >= tcols) continue;
+            const int64_t o = (int64_t)row * ld + col0 + cl;
+            zc[t] = Tr::ld_raw(zcur + o);
+            if (!first) zp[t] = Tr::ld_raw_cs(zprev + o);
+        }
+    }
+};
+
 // One row of the moment step: Z_{j+1} of the row's columns of this tile, and the
 // row's fp32 products <z_c, z_c>, <z_n, z_c>, <z_n, z_n> summed over them.
 template <typename T, int G, int NT>
 __device__ __forceinline__ void mom_epilogue(int row, int lane, int col0, int tcols, float (&acc)[NT][StoreTraits<T>::VEC],
-                                             const float* __restrict__ invdeg, const T* __restrict__ zcur,
-                                             T* __restrict__ zprev_next, int64_t ld, int first, float& p0, float& p1,
+                                             const float* __restrict__ invdeg, T* __restrict__ zprev_next, int64_t ld,
+                                             int first, const MomOperands<T, NT>& op, float& p0, float& p1,
                                              float& p2) {
     using Tr = StoreTraits<T>;
     constexpr int VEC = Tr::VEC;
@@ -570,14 +601,14 @@ __device__ __forceinline__ void mom_epilogue(int row, int lane, int col0, int tc
         if (cl >= tcols) continue;
         const int c = col0 + cl;
         float zc[VEC], zn[VEC];
-        Tr::load(zcur + (int64_t)row * ld + c, zc);
+        Tr::unraw(op.zc[t], zc);
         T* zp_ptr = zprev_next + (int64_t)row * ld + c;
         if (first) {
 #pragma unroll
             for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v]);
         } else {
             float zp[VEC];
-            Tr::load_cs(zp_ptr, zp);
+            Tr::unraw(op.zp[t], zp);
 #pragma unroll
             for (int v = 0; v < VEC; ++v) zn[v] = Tr::round(f * acc[t][v] - zp[v]);
         }
@@ -612,7 +643,7 @@ __device__ __forceinline__ void mom_block_partials(double s0, double s1, double 
 
 template <typename T, int G, int NT>
 __global__ void __launch_bounds__(512)
-mom_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const float* __restrict__ invdeg,
+mom_step_kernel(const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci, const float* __restrict__ invdeg,
                 const int32_t* __restrict__ deg, const T* __restrict__ zcur, T* __restrict__ zprev_next,
                 const int32_t* __restrict__ part, int ncols, int64_t ld, int first, double* __restrict__ partials) {
     constexpr int VEC = StoreTraits<T>::VEC;
@@ -622,19 +653,21 @@ mom_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, 
     const int tcols = min(TW, ncols - col0);
     const int r1 = part[blockIdx.x + 1];
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int row = part[blockIdx.x] + (int)(threadIdx.x / G); row < r1; row += (int)(blockDim.x / G)) {
-        const int e0 = __ldg(rp + row), e1 = __ldg(rp + row + 1);
-        if (e1 - e0 > kHeavyRow) continue;
+    extern __shared__ int32_t s_csr[];
+    const StagedCsr sc = stage_csr(lrp, lci, part[blockIdx.x], r1, s_csr);
+    for_each_staged_row(sc, (int)(threadIdx.x / G), (int)(blockDim.x / G), [&](int row, int e0, int e1) {
+        MomOperands<T, NT> op;
+        op.load(row, lane, G, col0, tcols, first, zcur, zprev_next, ld);
         float acc[NT][VEC];
-        gather_range<T, G, NT, false, float>(e0, e1, ci, nullptr, zcur + col0, ld, lane, tcols, acc);
+        gather_staged<T, G, NT, false, float>(e0, e1, sc.ci, nullptr, zcur + col0, ld, lane, tcols, acc);
         float p0, p1, p2;
-        mom_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, zcur, zprev_next, ld, first, p0, p1, p2);
-        const int dg = deg[row];
-        const double wr = dg > 0 ? (double)dg : 1.0;
+        mom_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, zprev_next, ld, first, op, p0, p1, p2);
+        // the row's degree (d_i of the X-space inner product) is its edge count
+        const double wr = e1 > e0 ? (double)(e1 - e0) : 1.0;
         s0 += wr * (double)p0;
         s1 += wr * (double)p1;
         s2 += wr * (double)p2;
-    }
+    });
     mom_block_partials(s0, s1, s2, (int64_t)blockIdx.y * gridDim.x + blockIdx.x, partials);
 }
 
@@ -656,8 +689,10 @@ mom_step_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict_
                                          tcols, acc);
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     if (threadIdx.x < G) {
+        MomOperands<T, NT> op;
+        op.load(row, lane, G, col0, tcols, first, zcur, zprev_next, ld);
         float p0, p1, p2;
-        mom_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, zcur, zprev_next, ld, first, p0, p1, p2);
+        mom_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, zprev_next, ld, first, op, p0, p1, p2);
         const double wr = (double)deg[row];
         s0 = wr * (double)p0;
         s1 = wr * (double)p1;
@@ -772,6 +807,8 @@ static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur
     if (ws <= kKeepL2Fraction * (double)g->l2_bytes) mode |= 4;
     const int32_t* part = nullptr;
     CSC_TRY(get_partition(g, cfg.P, &part));
+    const int smem = staged_smem(g, cfg.P);  // the CTA's CSR slice (stage_csr)
+    CSC_TRY(check_staged_smem(smem));
     const dim3 grid(cfg.P, cfg.tiles);
     // algorithmic bytes of one order: CSR + row factors, Z_j gathered once, Z_{j-1} read and
     // Z_{j+1} written (first order: Z_0 read, Z_1 written), Y written or read+written;
@@ -783,33 +820,15 @@ static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur
     const double heavy_frac = g->n_heavy ? (heavy_edges + g->n_heavy) / ((double)g->nnz + g->N) : 0.0;
     const double bytes = all_bytes * (1.0 - heavy_frac);
     if (g->n_heavy > 0) {
-        const dim3 hgrid(g->n_heavy, cfg.win > 0 ? 1 : cfg.tiles);
-        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * heavy_frac, s,
+        const dim3 hgrid(g->n_heavy, cfg.tiles);
+        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step_heavy", all_bytes * heavy_frac, s,
                                           cheb_step_heavy_kernel<T, GG, NN><<<hgrid, kHeavyThreads, 0, s>>>(
                                               g->row_ptr, g->col_idx, idg, sqd, xcur, xpn, Y, g->perm, g->heavy,
                                               ncols, ld, (A)c0, (A)cn, mode, tab)));
     }
-    if (cfg.win > 0) {
-        if (tab.c) {
-            set_error("per-graph coefficients need a launch shape without a neighbour window");
-            return CSC_E_UNSUPPORTED;
-        }
-        const int32_t* win = nullptr;
-        CSC_TRY(get_windows(g, cfg.P, cfg.win, &win));
-        const size_t smem = 128 + (size_t)cfg.win * ld * sizeof(T);
-        CSC_SHAPE_SWITCH(cfg, {
-            CSC_CUDA_TRY(cudaFuncSetAttribute(cheb_step_win_kernel<T, GG, NN>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            CSC_KLAUNCH("cheb_step", bytes, s,
-                        cheb_step_win_kernel<T, GG, NN><<<grid, cfg.threads, smem, s>>>(
-                            g->row_ptr, g->col_idx, idg, sqd, xcur, xpn, Y, g->perm, part, ncols, ld, (A)c0, (A)cn,
-                            mode, win, cfg.win, g->dev_err));
-        });
-        return CSC_OK;
-    }
     CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", bytes, s,
-                                      cheb_step_kernel<T, GG, NN><<<grid, cfg.threads, 0, s>>>(
-                                          g->row_ptr, g->col_idx, idg, sqd, xcur, xpn, Y, g->perm, part, ncols, ld,
+                                      cheb_step_kernel<T, GG, NN><<<grid, cfg.threads, smem, s>>>(
+                                          g->lrp, g->lci, idg, sqd, xcur, xpn, Y, g->perm, part, ncols, ld,
                                           (A)c0, (A)cn, mode, tab)));
     return CSC_OK;
 }
@@ -834,6 +853,8 @@ static csc_status launch_clenshaw_step(Graph* g, const LaunchCfg& cfg, const T* 
     if (ws <= kKeepL2Fraction * (double)g->l2_bytes) mode |= 4;
     const int32_t* part = nullptr;
     CSC_TRY(get_partition(g, cfg.P, &part));
+    const int smem = staged_smem(g, cfg.P);  // the CTA's CSR slice (stage_csr)
+    CSC_TRY(check_staged_smem(smem));
     const dim3 grid(cfg.P, cfg.tiles);
     // algorithmic bytes of one order: CSR + row factors, B_{j+1} gathered once, B_{j+2} read
     // (not on the first order), B_j written (not on the last), Y written (last), s R read
@@ -846,20 +867,20 @@ static csc_status launch_clenshaw_step(Graph* g, const LaunchCfg& cfg, const T* 
     const double heavy_frac = g->n_heavy ? (heavy_edges + g->n_heavy) / ((double)g->nnz + g->N) : 0.0;
     if (g->n_heavy > 0) {
         const dim3 hgrid(g->n_heavy, cfg.tiles);
-        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * heavy_frac, s,
+        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step_heavy", all_bytes * heavy_frac, s,
                                           clenshaw_step_heavy_kernel<T, GG, NN><<<hgrid, kHeavyThreads, 0, s>>>(
                                               g->row_ptr, g->col_idx, idg, sqd, bnext, bpp, Y, perm, g->heavy,
                                               ncols, ld, (A)cj, mode, tab, rs)));
     }
     if (last) {
         CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * (1.0 - heavy_frac), s,
-                                          clenshaw_step_kernel<T, GG, NN, true><<<grid, cfg.threads, 0, s>>>(
-                                              g->row_ptr, g->col_idx, idg, sqd, bnext, bpp, Y, perm, part, ncols,
+                                          clenshaw_step_kernel<T, GG, NN, true><<<grid, cfg.threads, smem, s>>>(
+                                              g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm, part, ncols,
                                               ld, (A)cj, mode, tab, rs)));
     } else {
         CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * (1.0 - heavy_frac), s,
-                                          clenshaw_step_kernel<T, GG, NN, false><<<grid, cfg.threads, 0, s>>>(
-                                              g->row_ptr, g->col_idx, idg, sqd, bnext, bpp, Y, perm, part, ncols,
+                                          clenshaw_step_kernel<T, GG, NN, false><<<grid, cfg.threads, smem, s>>>(
+                                              g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm, part, ncols,
                                               ld, (A)cj, mode, tab, rs)));
     }
     return CSC_OK;
@@ -871,18 +892,20 @@ static csc_status launch_mom_step(Graph* g, const LaunchCfg& cfg, const T* xcur,
     const double bytes = 4.0 * g->nnz + 8.0 * g->N + 4.0 + (first ? 2.0 : 3.0) * (double)g->N * ncols * sizeof(T);
     const int32_t* part = nullptr;
     CSC_TRY(get_partition(g, cfg.P, &part));
+    const int smem = staged_smem(g, cfg.P);  // the CTA's CSR slice (stage_csr)
+    CSC_TRY(check_staged_smem(smem));
     const dim3 grid(cfg.P, cfg.tiles);
     if (g->n_heavy > 0) {
         // heavy rows' partial sums go to the slots after the row-range blocks'
         const dim3 hgrid(g->n_heavy, cfg.tiles);
-        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("mom_step", 0.0, s,
+        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("mom_step_heavy", 0.0, s,
                                           mom_step_heavy_kernel<T, GG, NN><<<hgrid, kHeavyThreads, 0, s>>>(
                                               g->row_ptr, g->col_idx, g->invdeg, g->deg, xcur, xpn, g->heavy, ncols,
                                               ld, first, partials, (int64_t)cfg.P * cfg.tiles)));
     }
     CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("mom_step", bytes, s,
-                                      mom_step_kernel<T, GG, NN><<<grid, cfg.threads, 0, s>>>(
-                                          g->row_ptr, g->col_idx, g->invdeg, g->deg, xcur, xpn, part, ncols, ld,
+                                      mom_step_kernel<T, GG, NN><<<grid, cfg.threads, smem, s>>>(
+                                          g->lrp, g->lci, g->invdeg, g->deg, xcur, xpn, part, ncols, ld,
                                           first, partials)));
     return CSC_OK;
 }
@@ -899,22 +922,12 @@ static int occupancy(K kernel, int threads) {
 }
 
 template <typename T>
-static int kernel_occupancy(int kind, const TileShape& sh, int threads, size_t win_smem = 0) {
+static int kernel_occupancy(int kind, const TileShape& sh, int threads) {
     int occ = 1;
     auto f = [&](auto kptr) { occ = occupancy(kptr, threads); };
-    auto fw = [&](auto kptr) {
-        cudaFuncSetAttribute(kptr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)win_smem);
-        int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kptr, threads, win_smem) != cudaSuccess) {
-            cudaGetLastError();
-            n = 0;
-        }
-        occ = n;
-    };
 #define CSC_OCC_CASE(GG, NN)                                                             \
     if (sh.G == GG && sh.NT == NN) {                                                     \
-        if (kind == KK_CHEB && win_smem) fw(cheb_step_win_kernel<T, GG, NN>);           \
-        else if (kind == KK_CHEB) f(cheb_step_kernel<T, GG, NN>);                        \
+        if (kind == KK_CHEB) f(cheb_step_kernel<T, GG, NN>);                             \
         else if (kind == KK_CLEN) f(clenshaw_step_kernel<T, GG, NN, false>);             \
         else if constexpr (sizeof(T) <= 4) f(mom_step_kernel<T, GG, NN>);               \
     }
@@ -958,32 +971,16 @@ static std::vector<LaunchCfg> candidates(Graph* g, int kind, int nv) {
                 int P = (g->num_sms * occ * waves + tiles - 1) / tiles;
                 if (P > max_p) P = (int)max_p;
                 if (P < g->n_graphs) P = g->n_graphs;  // a batch needs a range per graph
-                c.P = P < 1 ? 1 : P;
+                P = P < 1 ? 1 : P;
+                // the CTA's staged CSR slice must fit shared memory: more, shorter ranges if not
+                if (fit_staged_partition(g, P, std::max<int64_t>(max_p, g->n_graphs), &P) != CSC_OK ||
+                    staged_smem(g, P) > kStagedSmemMax)
+                    continue;
+                c.P = P;
                 if (!out.empty() && out.back().G == c.G && out.back().NT == c.NT && out.back().threads == th &&
                     out.back().P == c.P)
                     continue;
                 out.push_back(c);
-            }
-            // shared-memory neighbour windows (single column tile): up to ~64 / 100 / 200 KB
-            if (kind == KK_CHEB && tiles == 1 && g->n_graphs <= 1) {
-                const size_t row_bytes = (size_t)nv * 16;
-                for (size_t budget : {64 * 1024, 100 * 1024, 200 * 1024}) {
-                    int64_t W = (int64_t)((budget - 128) / row_bytes);
-                    if (W > g->N) W = g->N;
-                    if (W < 64) continue;
-                    const size_t smem = 128 + (size_t)W * row_bytes;
-                    const int wocc = kernel_occupancy<T>(kind, sh, th, smem);
-                    if (wocc < 1) continue;
-                    LaunchCfg cw = c;
-                    cw.win = (int)W;
-                    for (int waves = 1; waves <= 2; waves *= 2) {
-                        int P = g->num_sms * wocc * waves;
-                        if (P > max_p) P = (int)max_p;
-                        cw.P = P < 1 ? 1 : P;
-                        out.push_back(cw);
-                    }
-                    if (W == g->N) break;
-                }
             }
         }
     }
@@ -1133,7 +1130,7 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
             }
             return CSC_OK;
         };
-        if (!tab.c && graphs && cfg.win == 0) {
+        if (!tab.c && graphs) {
             // coefficients to a device array the graph reads (stream-ordered before the replay)
             std::vector<A> hc(m + 1);
             for (int j = 0; j <= m; ++j) hc[j] = (A)c[j];
@@ -1334,6 +1331,45 @@ csc_status run_row_scores(void* Y, bool y_f64, int64_t N, int d, int ld, double*
         CSC_KLAUNCH("normalize", bytes, s,
                     normalize_kernel<float><<<grid, 256, 0, s>>>((float*)Y, (int32_t)N, d, ld, score,
                                                                  normalize ? 1 : 0));
+    }
+    return CSC_OK;
+}
+
+// Non-finite scan: *flag = 1 when any of the first `cols` entries of a row is NaN or
+// infinite (every writer stores the same value).
+template <typename A>
+__global__ void finite_scan_kernel(const A* __restrict__ X, int64_t rows, int cols, int ld, int* __restrict__ flag) {
+    const int64_t total = rows * (int64_t)cols;
+    int bad = 0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / cols;
+        const int c = (int)(t - r * cols);
+        if (!isfinite(X[r * ld + c])) bad = 1;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *flag = 1;
+}
+
+csc_status run_check_finite(Graph* g, const void* X, bool x_f64, int64_t rows, int cols, int ld, const char* what,
+                            cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return CSC_OK;
+    void* fw = nullptr;
+    CSC_TRY(ws_get(g, WS_CHECK, sizeof(int), &fw));
+    int* flag = (int*)fw;
+    CSC_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    int grid = (int)std::min<int64_t>(ceil_div(rows * cols, 256), (int64_t)g->num_sms * 8);
+    const double bytes = (double)rows * cols * (x_f64 ? 8.0 : 4.0);
+    if (x_f64)
+        CSC_KLAUNCH("check_finite", bytes, s,
+                    finite_scan_kernel<double><<<grid, 256, 0, s>>>((const double*)X, rows, cols, ld, flag));
+    else
+        CSC_KLAUNCH("check_finite", bytes, s,
+                    finite_scan_kernel<float><<<grid, 256, 0, s>>>((const float*)X, rows, cols, ld, flag));
+    int* h = (int*)g->pinned;
+    CSC_CUDA_TRY(cudaMemcpyAsync(h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CSC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (*h) {
+        set_error("non-finite values (NaN or infinity) in %s", what);
+        return CSC_E_NUMERIC;
     }
     return CSC_OK;
 }

@@ -39,3 +39,20 @@ def test_status_strings_and_version(built):
     assert L.csc_status_str(0) == b"CSC_OK"
     assert L.csc_status_str(5) == b"CSC_E_NOT_CONVERGED"
     assert b"sm_103a" in L.csc_version()
+
+
+def test_header_constants_match_binding():
+    """Every status code and flag #define of include/csc.h has the same value in the binding."""
+    import os
+    import re
+
+    from paper_1602_02018_gb300 import _native
+
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "csc.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(CSC_[A-Z0-9_]+)\s+(\d+)u?\b", hdr)}
+    for name in ("CSC_E_NUMERIC", "CSC_CHECK_FINITE", "CSC_CLENSHAW", "CSC_HIGHPASS", "CSC_VARDENSITY",
+                 "CSC_E_UNSUPPORTED", "CSC_E_NOT_CONVERGED"):
+        assert name in defs, name
+    for name, value in defs.items():
+        if hasattr(_native, name):
+            assert getattr(_native, name) == value, name

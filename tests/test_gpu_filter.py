@@ -171,36 +171,31 @@ SHAPES = [(2, 1), (2, 2), (2, 3), (4, 1), (4, 2), (4, 3), (8, 1), (8, 2), (8, 3)
 
 @pytest.mark.parametrize("G,NT", SHAPES)
 @pytest.mark.parametrize("threads", [256, 512])
-@pytest.mark.parametrize("win", [0, 300])
-def test_every_compiled_shape_f32(G, NT, threads, win):
-    """Each compiled (lanes per row, vectors per lane) pair, CTA size and the shared-memory
-    window variant give the oracle's filter (ragged row ranges: P = 37)."""
+def test_every_compiled_shape_f32(G, NT, threads):
+    """Each compiled (lanes per row, vectors per lane) pair and CTA size gives the oracle's
+    filter (ragged row ranges: P = 37)."""
     g = GRAPHS[6][1]
     d, d_pad, m, lam = 47, 48, 20, 0.43
     tiles = -(-(d_pad // 4) // (G * NT))
-    if win and tiles != 1:
-        pytest.skip("windows need a single column tile")
     r = ci.gaussian_block(g.n, d, d_pad, seed=3)
     ref = _oracle_filter(g, r.astype(np.float64), lam, m)
     with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM) as h:
-        csc.csc_graph_pin_shape(h, "cheb_step", 4, d_pad, G, NT, threads, 37, tiles, win)
+        csc.csc_graph_pin_shape(h, "cheb_step", 4, d_pad, G, NT, threads, 37, tiles)
         y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, R_in=torch.from_numpy(r).cuda(), flags=0).cpu().numpy()
     assert rel(y, ref) <= 1e-5
 
 
-@pytest.mark.parametrize("G,NT,win", [(2, 3, 0), (8, 1, 0), (2, 3, 200), (4, 2, 999)])
+@pytest.mark.parametrize("G,NT", [(2, 3), (8, 1), (4, 2), (16, 1)])
 @pytest.mark.parametrize("storage,tol", [(1, 5e-2), (2, 1e-12)])
-def test_shapes_bf16_f64(G, NT, win, storage, tol):
+def test_shapes_bf16_f64(G, NT, storage, tol):
     g = GRAPHS[6][1]
     d, d_pad, m, lam = 28, 32, 15, 0.5
     vec = 8 if storage == 1 else 2
     tiles = -(-(d_pad // vec) // (G * NT))
-    if win and tiles != 1:
-        pytest.skip("windows need a single column tile")
     r = ci.gaussian_block(g.n, d, d_pad, seed=4)
     ref = _oracle_filter(g, r.astype(np.float64), lam, m)
     with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
-        csc.csc_graph_pin_shape(h, "cheb_step", 2 if storage == 1 else 8, d_pad, G, NT, 256, 29, tiles, win)
+        csc.csc_graph_pin_shape(h, "cheb_step", 2 if storage == 1 else 8, d_pad, G, NT, 256, 29, tiles)
         y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, storage=storage, R_in=torch.from_numpy(r).cuda(),
                                           flags=0).cpu().numpy()
     assert rel(y, ref) <= tol
@@ -214,7 +209,9 @@ def test_pin_shape_rejects_bad_shapes():
         with pytest.raises(csc.CscError):
             csc.csc_graph_pin_shape(h, "cheb_step", 4, 48, 4, 1, 256, 10, 1, 0)   # tiles
         with pytest.raises(csc.CscError):
-            csc.csc_graph_pin_shape(h, "cg", 4, 200, 32, 2, 256, 10, 1, 50)       # window on CG
+            csc.csc_graph_pin_shape(h, "cg", 4, 200, 32, 2, 256, 10, 1, 50)       # reserved entry not 0
+        with pytest.raises(csc.CscError):
+            csc.csc_graph_pin_shape(h, "cheb_step", 4, 48, 4, 3, 256, 10, 1, 300)  # reserved entry not 0
 
 
 def test_graph_replay_matches_eager_launches():

@@ -19,6 +19,7 @@ from .helpers import rel
 pytestmark = pytest.mark.gpu
 
 csc = pytest.importorskip("paper_1602_02018_gb300")
+from paper_1602_02018_gb300 import _native as nat  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -309,3 +310,42 @@ def test_cluster_highpass_interp_degree():
     assert i20.lam.lam == i50.lam.lam
     a20 = oari.ari(l20.cpu().numpy(), g.labels)
     assert a20 >= 0.8 and 20 * i20.cg.iters < 50 * i50.cg.iters
+
+
+def test_check_finite_reports_non_finite_signals():
+    """CSC_CHECK_FINITE: a NaN planted on the host in R_in is reported as CSC_E_NUMERIC before
+    any filtering; without the flag it flows into Y; a clean block passes and the handle
+    stays usable, including csc_cluster with the flag."""
+    g = ci.sbm(1000, 20, seed=0)
+    r = ci.gaussian_block(g.n, 28, 32, seed=1)
+    r[17, 3] = np.nan
+    with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+        y = csc.csc_filter_random_signals(h, 0.4, 20, 28, 32, R_in=torch.from_numpy(r).cuda(), flags=0)
+        assert torch.isnan(y).any()
+        with pytest.raises(csc.CscError) as e:
+            csc.csc_filter_random_signals(h, 0.4, 20, 28, 32, R_in=torch.from_numpy(r).cuda(),
+                                          flags=csc.CHECK_FINITE)
+        assert e.value.status == nat.CSC_E_NUMERIC
+        r[17, 3] = np.inf
+        with pytest.raises(csc.CscError) as e:
+            csc.csc_filter_random_signals(h, 0.4, 20, 28, 32, R_in=torch.from_numpy(r).cuda(),
+                                          flags=csc.CHECK_FINITE | csc.CLENSHAW)
+        assert e.value.status == nat.CSC_E_NUMERIC
+        r[17, 3] = 0.5
+        y = csc.csc_filter_random_signals(h, 0.4, 20, 28, 32, R_in=torch.from_numpy(r).cuda(),
+                                          flags=csc.CHECK_FINITE | csc.NORMALIZE_ROWS)
+        assert torch.isfinite(y).all()
+        labels, _ = csc.csc_cluster(h, 20, seed=0, flags=csc.CHECK_FINITE)
+        assert oari.ari(labels.cpu().numpy(), g.labels) > 0.8
+
+
+def test_sampling_wrappers_reject_short_or_mistyped_buffers():
+    for fn in (csc.csc_sample, csc.csc_sample_noalloc):
+        with pytest.raises(ValueError):
+            fn(1000, 120, 0, torch.empty(120, dtype=torch.int32, device="cuda"))
+        with pytest.raises(ValueError):
+            fn(1000, 120, 0, torch.empty(119, dtype=torch.int64, device="cuda"))
+        out = torch.full((121,), -1, dtype=torch.int64, device="cuda")
+        fn(1000, 120, 0, out)
+        assert torch.equal(out[:120].cpu(), torch.from_numpy(osamp.sample(1000, 120, 0)))
+        assert int(out[120]) == -1

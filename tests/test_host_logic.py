@@ -101,3 +101,18 @@ def test_sweep_tables_format():
     text = fs.format_tables(res, 3)
     for needle in ("Fig. 1 a", "Fig. 1 d", "Fig. 1 e", "Heterogeneous SBM", "Fig. 1 f-g", "SC (Alg. 1"):
         assert needle in text
+
+
+def test_sampling_wrappers_reject_bad_output_buffers():
+    """The sampling wrappers check the caller's index buffer before any native call: it must be a
+    contiguous int64 CUDA tensor of at least n elements (anything else would be written past)."""
+    import pytest
+    import torch
+
+    import paper_1602_02018_gb300 as csc
+
+    for fn in (csc.csc_sample, csc.csc_sample_noalloc):
+        with pytest.raises(ValueError):
+            fn(100, 10, 0, torch.empty(10, dtype=torch.int64))  # host memory
+        with pytest.raises(ValueError):
+            fn(100, 10, 0, torch.empty(10, dtype=torch.int32))
