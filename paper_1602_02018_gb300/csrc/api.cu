@@ -492,6 +492,9 @@ static void free_graph(Graph* g) {
     for (auto& b : g->ws) cudaFree(b.ptr);
     for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second.first);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    if (g->side_stream) cudaStreamDestroy(g->side_stream);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    if (g->ev_join) cudaEventDestroy(g->ev_join);
     for (auto& kv : g->parts) cudaFree(kv.second);
     for (auto& kv : g->part_gblk) cudaFree(kv.second);
     cudaFree(g->d_hvy_start);

@@ -450,62 +450,90 @@ struct Segs {
     }
 };
 
-// Column sums of block partials of one graph in a fixed order: a 32 x 32 thread
-// block covers 32 columns; thread row y sums slots y, y+32, ... of the graph's row
-// ranges, then (heavy = true) of its heavy rows, coalesced across columns, into four
-// interleaved running sums (slot i of the thread's sequence into sum i mod 4, so four
-// loads are in flight) that are added in order; then the 32 row sums are added in
-// order.  nslots: the stride between the NS quantities' slot arrays.
+// Column sums of block partials of one graph in a fixed order.  The graph's slots (its
+// row ranges, then with heavy = true its heavy rows) are cut into gridDim.z slices of
+// consecutive slots; a 32 x 32 thread block covers 32 columns of one slice: thread row y
+// sums slots y, y+32, ... of the slice into four interleaved running sums (slot i of its
+// sequence into sum i mod 4, so four loads are in flight) added in order, then the 32
+// row sums are added in order.  The slices' sums go to lvl2; the block that completes a
+// column chunk last (an atomic count per chunk; no block waits for another) adds them
+// in slice order and returns true with the totals in out (threads with y == 0).  The
+// result does not depend on which block is last.  nslots: the stride between the NS
+// quantities' slot arrays.
 constexpr int kReduceRows = 32;
+constexpr int kSliceSlots = 256;  // slots per slice (8 per thread row)
 
 template <int NS>
-__device__ __forceinline__ void reduce_columns(const double* __restrict__ partials, int nslots, const Segs& sg,
-                                               bool heavy, int64_t ldp, int j, double (&out)[NS]) {
+__device__ __forceinline__ bool reduce_columns(const double* __restrict__ partials, int nslots, const Segs& sg,
+                                               bool heavy, int64_t ldp, int j, double* __restrict__ lvl2,
+                                               int* __restrict__ counters, double (&out)[NS]) {
     __shared__ double red[NS][kReduceRows][33];
+    __shared__ int s_last;
     const int x = threadIdx.x, y = threadIdx.y;
     int b0, b1, h0, h1;
     sg.get(blockIdx.y, b0, b1, h0, h1);
+    const int nb = b1 - b0, total = nb + (heavy ? h1 - h0 : 0);
+    const int z = blockIdx.z, S = gridDim.z;
+    const int l0 = (int)((int64_t)total * z / S), l1 = (int)((int64_t)total * (z + 1) / S);
+    // list position l -> slot: row ranges first, then heavy rows (slots P + h)
+    auto slot = [&](int l) { return l < nb ? b0 + l : sg.P + h0 + (l - nb); };
     double s[NS][4];
 #pragma unroll
     for (int q = 0; q < NS; ++q)
 #pragma unroll
         for (int u = 0; u < 4; ++u) s[q][u] = 0.0;
-    auto sweep = [&](int first, int end, int offset) {
-        int b = first + y;
-        for (; b + 3 * kReduceRows < end; b += 4 * kReduceRows)
+    int l = l0 + y;
+    for (; l + 3 * kReduceRows < l1; l += 4 * kReduceRows)
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int q = 0; q < NS; ++q)
-                    s[q][u] += partials[((int64_t)q * nslots + offset + b + u * kReduceRows) * ldp + j];
+            for (int q = 0; q < NS; ++q)
+                s[q][u] += partials[((int64_t)q * nslots + slot(l + u * kReduceRows)) * ldp + j];
 #pragma unroll
-        for (int u = 0; u < 3; ++u) {
-            const int bb = b + u * kReduceRows;
-            if (bb < end)
+    for (int u = 0; u < 3; ++u) {
+        const int ll = l + u * kReduceRows;
+        if (ll < l1)
 #pragma unroll
-                for (int q = 0; q < NS; ++q) s[q][u] += partials[((int64_t)q * nslots + offset + bb) * ldp + j];
-        }
-    };
-    sweep(b0, b1, 0);
-    if (heavy) sweep(h0, h1, sg.P);
+            for (int q = 0; q < NS; ++q) s[q][u] += partials[((int64_t)q * nslots + slot(ll)) * ldp + j];
+    }
 #pragma unroll
     for (int q = 0; q < NS; ++q) red[q][y][x] = ((s[q][0] + s[q][1]) + s[q][2]) + s[q][3];
     __syncthreads();
+    const int64_t chunk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    if (y == 0) {
 #pragma unroll
-    for (int q = 0; q < NS; ++q) {
-        double t = 0.0;
-        for (int i = 0; i < kReduceRows; ++i) t += red[q][i][x];
-        out[q] = t;
+        for (int q = 0; q < NS; ++q) {
+            double t = 0.0;
+            for (int i = 0; i < kReduceRows; ++i) t += red[q][i][x];
+            lvl2[((chunk * S + z) * NS + q) * 32 + x] = t;
+        }
     }
+    __threadfence();
+    __syncthreads();
+    if (x == 0 && y == 0) s_last = atomicAdd(counters + chunk, 1) == S - 1;
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    if (y == 0) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            double t = 0.0;
+            for (int zz = 0; zz < S; ++zz) t += __ldcg(lvl2 + ((chunk * S + zz) * NS + q) * 32 + x);
+            out[q] = t;
+        }
+        if (x == 0) counters[chunk] = 0;  // ready for the next launch
+    }
+    return true;
 }
 
 // pAp_j = sum of partials (row ranges and heavy rows); alpha_j = rz_j / pAp_j for
 // active columns.  Graph blockIdx.y's column j lives at state index y * ldp + j.
 __global__ void __launch_bounds__(1024) cg_alpha_kernel(const double* __restrict__ partials, int nslots, Segs sg,
-                                                       int k, int64_t ldp, CgState st) {
+                                                       int k, int64_t ldp, CgState st, double* __restrict__ lvl2,
+                                                       int* __restrict__ counters) {
     const int jc = blockIdx.x * 32 + threadIdx.x;
     double s[1];
-    reduce_columns<1>(partials, nslots, sg, true, ldp, jc < k ? jc : 0, s);
+    if (!reduce_columns<1>(partials, nslots, sg, true, ldp, jc < k ? jc : 0, lvl2, counters, s)) return;
     if (threadIdx.y != 0 || jc >= sg.kg(blockIdx.y, k)) return;
     const int64_t j = (int64_t)blockIdx.y * ldp + jc;
     st.alpha[j] = (st.active[j] && s[0] != 0.0) ? st.rz[j] / s[0] : 0.0;
@@ -513,10 +541,11 @@ __global__ void __launch_bounds__(1024) cg_alpha_kernel(const double* __restrict
 
 // After an update: rz_new, rr; convergence; beta.  init != 0: first call (sets bn2, active).
 __global__ void __launch_bounds__(1024) cg_beta_kernel(const double* __restrict__ partials, int nslots, Segs sg,
-                                                      int k, int64_t ldp, CgState st, double tol2, int init) {
+                                                      int k, int64_t ldp, CgState st, double tol2, int init,
+                                                      double* __restrict__ lvl2, int* __restrict__ counters) {
     const int jc = blockIdx.x * 32 + threadIdx.x;
     double s2[2];
-    reduce_columns<2>(partials, nslots, sg, false, ldp, jc < k ? jc : 0, s2);
+    if (!reduce_columns<2>(partials, nslots, sg, false, ldp, jc < k ? jc : 0, lvl2, counters, s2)) return;
     if (threadIdx.y != 0 || jc >= sg.kg(blockIdx.y, k)) return;
     const int64_t j = (int64_t)blockIdx.y * ldp + jc;
     int act = st.active[j];
@@ -541,10 +570,11 @@ __global__ void __launch_bounds__(1024) cg_beta_kernel(const double* __restrict_
 }
 
 __global__ void __launch_bounds__(1024) column_sum_kernel(const double* __restrict__ partials, int nslots, Segs sg,
-                                                         int k, int64_t ldp, double* __restrict__ out) {
+                                                         int k, int64_t ldp, double* __restrict__ out,
+                                                         double* __restrict__ lvl2, int* __restrict__ counters) {
     const int j = blockIdx.x * 32 + threadIdx.x;
     double s[1];
-    reduce_columns<1>(partials, nslots, sg, false, ldp, j < k ? j : 0, s);
+    if (!reduce_columns<1>(partials, nslots, sg, false, ldp, j < k ? j : 0, lvl2, counters, s)) return;
     if (threadIdx.y == 0 && j < sg.kg(blockIdx.y, k)) out[(int64_t)blockIdx.y * ldp + j] = s[0];
 }
 
@@ -789,6 +819,11 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const size_t sl = (size_t)nseg * ld;  // per-(graph, column) state length
     const size_t o_state = take(sl * 8 * 8 + sl * 4 + 64);
     const size_t o_gk = take((size_t)nseg * 4 * 3);
+    // sliced column reductions (reduce_columns): per column chunk, slice sums and a count
+    const int nchunks = ceil_div(k, 32) * nseg;
+    const int max_slices = std::max(1, ceil_div(max_p + (int)g->n_heavy, kSliceSlots));
+    const size_t o_lvl2 = take((size_t)nchunks * max_slices * 2 * 32 * 8);
+    const size_t o_cnt = take((size_t)nchunks * 4);
     void* base = nullptr;
     CSC_TRY(ws_get(g, WS_CG, off, &base));
     char* b = (char*)base;
@@ -816,6 +851,8 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     st.active = (int*)(sd + 8 * sl);
     st.n_active = st.active + sl;
     int* bad = st.n_active + 1;
+    double* lvl2 = (double*)(b + o_lvl2);
+    int* red_cnt = (int*)(b + o_cnt);
     int32_t* d_gk = nullptr;
     const int32_t* gid = nullptr;
     CgBatch bt, bt_all;  // bt also skips finished graphs; bt_all only narrows the columns
@@ -837,6 +874,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         CSC_CUDA_TRY(cudaMemsetAsync(Ap, 0, blk, s));
     }
     CSC_CUDA_TRY(cudaMemsetAsync(sd, 0, sl * 8 * 8 + sl * 4, s));
+    CSC_CUDA_TRY(cudaMemsetAsync(red_cnt, 0, (size_t)nchunks * 4, s));
 
     // zero x, r, mask; slab = -1
     CSC_CUDA_TRY(cudaMemsetAsync(x, 0, blk, s));
@@ -924,13 +962,15 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const double scal_ax = 8.0 * PH * ld;
     // share of the sparse bytes that falls on heavy rows (launched separately)
     const double heavy_frac = g->nnz > 0 ? (double)(g->nnz - g->h_light.back()) / (double)g->nnz : 0.0;
-    const dim3 kb(ceil_div(k, 32), nseg);
+    // reductions over P slots (updates, residual, norms) and P + H slots (<p, A p>)
+    const dim3 kb(ceil_div(k, 32), nseg, std::max(1, ceil_div(P, kSliceSlots)));
+    const dim3 kb_ax(ceil_div(k, 32), nseg, std::max(1, ceil_div(PH, kSliceSlots)));
     const dim3 rb(32, kReduceRows);
     CG_SWITCH(cfg, CSC_KLAUNCH("cg_update", blkb + 4.0 * N, s,
                                cg_update_kernel<G_, NT_><<<grid, th, 0, s>>>(x, r, p, Ap, nullptr, gid, pinv, rpart, ld,
                                                                              ld, part, bt_all)));
     CSC_KLAUNCH("cg_scalar", 2 * scal_b, s,
-                cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, st, rel_tol * rel_tol, 1));
+                cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, st, rel_tol * rel_tol, 1, lvl2, red_cnt));
     CG_SWITCH(cfg, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
                                cg_pupdate_kernel<G_, NT_><<<grid, th, 0, s>>>(r, p, st.beta, gid, pinv, rpart, ld,
                                                                               ld, bt)));
@@ -950,7 +990,8 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                                                                                  ld, ld, part, bb)));
             return CSC_OK;
         }
-        // t = L^(p-1) in, then Ap = mask*in + gamma * L t with <in, Ap> partials
+        // t = L^(p-1) in, then Ap = mask*in + gamma * L t with <in, Ap> partials; each product's
+        // heavy-row launch runs beside its row-range launch (fork_join)
         const float* cur = in;
         float* bufs[2] = {t1, t2};
         for (int q = 0; q < g_power - 1; ++q) {
@@ -958,67 +999,80 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
             // CSR + row factors, the input block gathered once, the output block written;
             // heavy rows (if any) in their own launch, bytes split by their edge share
             const double lb = csr_b + 2 * blkb;
-            if (q == 0) {
-                if (H > 0)
-                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_heavy", lb * heavy_frac, s,
-                                               lap_heavy_kernel<G_, NT_, true><<<hgrid, kHeavyThreads, 0, s>>>(
+            const bool win = q == 0;
+            auto heavy = [&](cudaStream_t st) -> csc_status {
+                if (win)
+                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_heavy", lb * heavy_frac, st,
+                                               lap_heavy_kernel<G_, NT_, true><<<hgrid, kHeavyThreads, 0, st>>>(
                                                    g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, g->heavy, ld,
                                                    ld, bb)));
-                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * (1.0 - heavy_frac), s,
-                                           lap_kernel<G_, NT_, true><<<grid, th, csmem, s>>>(
-                                               g->lrp, g->lci, g->dinv, g->invdeg, cur, o, rpart, ld, ld,
-                                               bb)));
-            } else {
-                if (H > 0)
-                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_heavy", lb * heavy_frac, s,
-                                               lap_heavy_kernel<G_, NT_, false><<<hgrid, kHeavyThreads, 0, s>>>(
+                else
+                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_heavy", lb * heavy_frac, st,
+                                               lap_heavy_kernel<G_, NT_, false><<<hgrid, kHeavyThreads, 0, st>>>(
                                                    g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, g->heavy, ld,
                                                    ld, bb)));
-                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * (1.0 - heavy_frac), s,
-                                           lap_kernel<G_, NT_, false><<<grid, th, csmem, s>>>(
-                                               g->lrp, g->lci, g->dinv, g->invdeg, cur, o, rpart, ld, ld,
-                                               bb)));
-            }
+                return CSC_OK;
+            };
+            auto light = [&](cudaStream_t st) -> csc_status {
+                if (win)
+                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * (1.0 - heavy_frac), st,
+                                               lap_kernel<G_, NT_, true><<<grid, th, csmem, st>>>(
+                                                   g->lrp, g->lci, g->dinv, g->invdeg, cur, o, rpart, ld, ld, bb)));
+                else
+                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * (1.0 - heavy_frac), st,
+                                               lap_kernel<G_, NT_, false><<<grid, th, csmem, st>>>(
+                                                   g->lrp, g->lci, g->dinv, g->invdeg, cur, o, rpart, ld, ld, bb)));
+                return CSC_OK;
+            };
+            CSC_TRY(fork_join(g, s, H > 0, heavy, light));
             cur = o;
         }
         // CSR + row factors + mask, t gathered once, p read, Ap written
         const double ab = csr_b + 4.0 * N + 3 * blkb + scal_ax;
-        if (g_power == 1) {
-            if (H > 0)
-                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax_heavy", ab * heavy_frac, s,
-                                           lap_ax_heavy_kernel<G_, NT_, true><<<hgrid, kHeavyThreads, 0, s>>>(
+        const bool win = g_power == 1;
+        auto heavy = [&](cudaStream_t st) -> csc_status {
+            if (win)
+                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax_heavy", ab * heavy_frac, st,
+                                           lap_ax_heavy_kernel<G_, NT_, true><<<hgrid, kHeavyThreads, 0, st>>>(
                                                g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma,
                                                Ap, g->heavy, ld, ld, part, P, PH, bb)));
-            CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * (1.0 - heavy_frac), s,
-                                       lap_ax_kernel<G_, NT_, true><<<grid, th, csmem, s>>>(
-                                           g->lrp, g->lci, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
-                                           rpart, ld, ld, part, PH, bb)));
-        } else {
-            if (H > 0)
-                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax_heavy", ab * heavy_frac, s,
-                                           lap_ax_heavy_kernel<G_, NT_, false><<<hgrid, kHeavyThreads, 0, s>>>(
+            else
+                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax_heavy", ab * heavy_frac, st,
+                                           lap_ax_heavy_kernel<G_, NT_, false><<<hgrid, kHeavyThreads, 0, st>>>(
                                                g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma,
                                                Ap, g->heavy, ld, ld, part, P, PH, bb)));
-            CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * (1.0 - heavy_frac), s,
-                                       lap_ax_kernel<G_, NT_, false><<<grid, th, csmem, s>>>(
-                                           g->lrp, g->lci, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
-                                           rpart, ld, ld, part, PH, bb)));
-        }
-        return CSC_OK;
+            return CSC_OK;
+        };
+        auto light = [&](cudaStream_t st) -> csc_status {
+            if (win)
+                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * (1.0 - heavy_frac), st,
+                                           lap_ax_kernel<G_, NT_, true><<<grid, th, csmem, st>>>(
+                                               g->lrp, g->lci, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
+                                               rpart, ld, ld, part, PH, bb)));
+            else
+                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * (1.0 - heavy_frac), st,
+                                           lap_ax_kernel<G_, NT_, false><<<grid, th, csmem, st>>>(
+                                               g->lrp, g->lci, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
+                                               rpart, ld, ld, part, PH, bb)));
+            return CSC_OK;
+        };
+        return fork_join(g, s, H > 0, heavy, light);
     };
     // `count` CG iterations; between convergence checks they replay as one CUDA graph
     // when no per-launch timing is asked for
     auto iterations = [&](cudaStream_t s, int count) -> csc_status {
         for (int q = 0; q < count; ++q) {
             CSC_TRY(apply_A(p, bt, s));
-            CSC_KLAUNCH("cg_scalar", scal_ax, s, cg_alpha_kernel<<<kb, rb, 0, s>>>(part, PH, sg, k, ld, st));
+            CSC_KLAUNCH("cg_scalar", scal_ax, s,
+                        cg_alpha_kernel<<<kb_ax, rb, 0, s>>>(part, PH, sg, k, ld, st, lvl2, red_cnt));
             // x, r, p, Ap read; x, r written
             CG_SWITCH(cfg, CSC_KLAUNCH("cg_update", 6 * blkb + 4.0 * N + 2 * scal_b, s,
                                        cg_update_kernel<G_, NT_><<<grid, th, 0, s>>>(x, r, p, Ap, st.alpha, gid, pinv,
                                                                                      rpart, ld, ld, part, bt)));
             CSC_TRY(reset_active(s));
             CSC_KLAUNCH("cg_scalar", 2 * scal_b, s,
-                        cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, st, rel_tol * rel_tol, 0));
+                        cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, st, rel_tol * rel_tol, 0, lvl2,
+                                                         red_cnt));
             CG_SWITCH(cfg, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
                                        cg_pupdate_kernel<G_, NT_><<<grid, th, 0, s>>>(r, p, st.beta, gid, pinv, rpart,
                                                                                       ld, ld, bt)));
@@ -1050,11 +1104,13 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     CG_SWITCH(cfg, CSC_KLAUNCH("cg_residual", blkb + 4.0 * N, s,
                                residual_kernel<G_, NT_><<<grid, th, 0, s>>>(Ap, slab, bfull, rpart, ld, ld, part,
                                                                             bt_all)));
-    CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, st.rr));
+    CSC_KLAUNCH("cg_scalar", scal_b, s,
+                column_sum_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, st.rr, lvl2, red_cnt));
     // labels
     CG_SWITCH(cfg, CSC_KLAUNCH("label_norms", blkb, s,
                                colnorm_kernel<G_, NT_><<<grid, th, 0, s>>>(x, rpart, ld, ld, part, bt_all)));
-    CSC_KLAUNCH("cg_scalar", scal_b, s, column_sum_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, norm2));
+    CSC_KLAUNCH("cg_scalar", scal_b, s,
+                column_sum_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, norm2, lvl2, red_cnt));
     CSC_KLAUNCH("label_argmax", 24.0 * sl, s,
                 label_scale_kernel<<<ceil_div((int64_t)sl, 256), 256, 0, s>>>(norm2, (int64_t)sl, nrm, rnrm));
     {

@@ -150,6 +150,9 @@ struct Graph {
     // captured CUDA graphs of fixed launch sequences (key -> executable, kernel launches)
     bool use_graphs = true;
     cudaStream_t cap_stream = nullptr;
+    // side stream and events of fork_join (heavy-row launches beside the row ranges)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::map<std::string, std::pair<cudaGraphExec_t, int64_t>> graphs;
     std::map<uint64_t, LaunchCfg> tuned;          // (kernel kind, dtype, columns) -> shape
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -205,6 +208,31 @@ csc_status replay_graph(Graph* g, const std::string& key, cudaStream_t s, int64_
     count_launches(it->second.second);
     *launches = it->second.second;
     return CSC_OK;
+}
+
+// Runs heavy(stream) on the handle's side stream alongside light(s) -- the heavy-row
+// launch and the row-range launch of one product write disjoint rows -- and makes s wait
+// for both; inside a capture this records two parallel branches.  With per-launch timing
+// on, or without heavy rows, the launches run one after the other on s.
+template <typename H, typename L>
+csc_status fork_join(Graph* g, cudaStream_t s, bool has_heavy, H&& heavy, L&& light) {
+    if (!has_heavy) return light(s);
+    if (g_prof_enabled) {
+        CSC_TRY(heavy(s));
+        return light(s);
+    }
+    if (!g->side_stream) {
+        CSC_CUDA_TRY(cudaStreamCreateWithFlags(&g->side_stream, cudaStreamNonBlocking));
+        CSC_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+        CSC_CUDA_TRY(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+    }
+    CSC_CUDA_TRY(cudaEventRecord(g->ev_fork, s));
+    CSC_CUDA_TRY(cudaStreamWaitEvent(g->side_stream, g->ev_fork, 0));
+    const csc_status hs = heavy(g->side_stream);
+    CSC_CUDA_TRY(cudaEventRecord(g->ev_join, g->side_stream));
+    const csc_status ls = light(s);
+    CSC_CUDA_TRY(cudaStreamWaitEvent(s, g->ev_join, 0));
+    return hs != CSC_OK ? hs : ls;
 }
 
 // P contiguous row ranges of about equal cost (edges + 2 per row); cached per P.

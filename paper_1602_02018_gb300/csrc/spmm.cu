@@ -366,11 +366,14 @@ __global__ void scale_copy_kernel(const T* __restrict__ X, typename StoreTraits<
 template <typename T, int G, int NT>
 struct ClenOperands {
     typename StoreTraits<T>::raw_t r[NT], b2[NT];
+    typename StoreTraits<T>::acc_t inv;  // 1 / d_i (0 for an isolated node)
     __device__ __forceinline__ void load(int row, int lane, int col0, int tcols, int mode, const T* __restrict__ rs,
-                                         const T* __restrict__ bpp, int64_t ld) {
+                                         const T* __restrict__ bpp, int64_t ld,
+                                         const typename StoreTraits<T>::acc_t* __restrict__ invdeg) {
         using Tr = StoreTraits<T>;
         constexpr int VEC = Tr::VEC;
         const bool first = (mode & 1) != 0, keep = (mode & 4) != 0;
+        inv = invdeg[row];
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
             const int cl = (t * G + lane) * VEC;
@@ -404,7 +407,7 @@ __device__ __forceinline__ void clenshaw_epilogue(int row, int lane, int col0, i
     constexpr int VEC = Tr::VEC;
     const bool first = (mode & 1) != 0;
     constexpr bool last = LAST;
-    const A f = (last ? A(-1) : A(-2)) * invdeg[row];
+    const A f = (last ? A(-1) : A(-2)) * op.inv;
     A out[LAST ? NT : 1][VEC];
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
@@ -493,7 +496,7 @@ clenshaw_step_kernel(const int32_t* __restrict__ lrp, const int32_t* __restrict_
     const StagedCsr sc = stage_csr(lrp, lci, r0, r1, s_csr);
     for_each_staged_row(sc, (int)(threadIdx.x / G), (int)(blockDim.x / G), [&](int row, int e0, int e1) {
         ClenOperands<T, G, NT> op;
-        op.load(row, lane, col0, tcols, mode, rs, bpp, ld);
+        op.load(row, lane, col0, tcols, mode, rs, bpp, ld, invdeg);
         A acc[NT][VEC];
         gather_staged<T, G, NT, false, A>(e0, e1, sc.ci, nullptr, bnext + col0, ld, lane, tcols, acc);
         clenshaw_epilogue<T, G, NT, LAST>(row, lane, col0, tcols, acc, invdeg, sqdeg, bpp, Y, perm, ld, cj, mode, op,
@@ -525,7 +528,7 @@ clenshaw_step_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __rest
     const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
     if (threadIdx.x < G) {
         ClenOperands<T, G, NT> op;
-        op.load(row, lane, col0, tcols, mode, rs, bpp, ld);
+        op.load(row, lane, col0, tcols, mode, rs, bpp, ld, invdeg);
         if (mode & 2)
             clenshaw_epilogue<T, G, NT, true>(row, lane, col0, tcols, acc, invdeg, sqdeg, bpp, Y, perm, ld, cj, mode,
                                               op, gmask);
@@ -819,21 +822,25 @@ static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur
     const double heavy_edges = (double)g->nnz - (double)g->h_light[g->N];
     const double heavy_frac = g->n_heavy ? (heavy_edges + g->n_heavy) / ((double)g->nnz + g->N) : 0.0;
     const double bytes = all_bytes * (1.0 - heavy_frac);
-    if (g->n_heavy > 0) {
-        const dim3 hgrid(g->n_heavy, cfg.tiles);
-        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step_heavy", all_bytes * heavy_frac, s,
-                                          cheb_step_heavy_kernel<T, GG, NN><<<hgrid, kHeavyThreads, 0, s>>>(
+    const dim3 hgrid(g->n_heavy > 0 ? g->n_heavy : 1, cfg.tiles);
+    auto heavy = [&](cudaStream_t st) -> csc_status {
+        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step_heavy", all_bytes * heavy_frac, st,
+                                          cheb_step_heavy_kernel<T, GG, NN><<<hgrid, kHeavyThreads, 0, st>>>(
                                               g->row_ptr, g->col_idx, idg, sqd, xcur, xpn, Y, g->perm, g->heavy,
                                               ncols, ld, (A)c0, (A)cn, mode, tab)));
-    }
-    CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", bytes, s,
-                                      cheb_step_kernel<T, GG, NN><<<grid, cfg.threads, smem, s>>>(
-                                          g->lrp, g->lci, idg, sqd, xcur, xpn, Y, g->perm, part, ncols, ld,
-                                          (A)c0, (A)cn, mode, tab)));
-    return CSC_OK;
+        return CSC_OK;
+    };
+    auto light = [&](cudaStream_t st) -> csc_status {
+        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", bytes, st,
+                                          cheb_step_kernel<T, GG, NN><<<grid, cfg.threads, smem, st>>>(
+                                              g->lrp, g->lci, idg, sqd, xcur, xpn, Y, g->perm, part, ncols, ld,
+                                              (A)c0, (A)cn, mode, tab)));
+        return CSC_OK;
+    };
+    return fork_join(g, s, g->n_heavy > 0, heavy, light);
 }
 
-// One Clenshaw order (see clenshaw_step_kernel): heavy rows first, then the row ranges.
+// One Clenshaw order (see clenshaw_step_kernel): the heavy rows beside the row ranges.
 template <typename T>
 static csc_status launch_clenshaw_step(Graph* g, const LaunchCfg& cfg, const T* bnext, T* bpp,
                                        typename StoreTraits<T>::acc_t* Y, int ncols, int64_t ld, double cj, int mode,
@@ -865,25 +872,29 @@ static csc_status launch_clenshaw_step(Graph* g, const LaunchCfg& cfg, const T* 
                              (last ? nx * sizeof(A) : 0.0);
     const double heavy_edges = (double)g->nnz - (double)g->h_light[g->N];
     const double heavy_frac = g->n_heavy ? (heavy_edges + g->n_heavy) / ((double)g->nnz + g->N) : 0.0;
-    if (g->n_heavy > 0) {
-        const dim3 hgrid(g->n_heavy, cfg.tiles);
-        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step_heavy", all_bytes * heavy_frac, s,
-                                          clenshaw_step_heavy_kernel<T, GG, NN><<<hgrid, kHeavyThreads, 0, s>>>(
+    const dim3 hgrid(g->n_heavy > 0 ? g->n_heavy : 1, cfg.tiles);
+    auto heavy = [&](cudaStream_t st) -> csc_status {
+        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step_heavy", all_bytes * heavy_frac, st,
+                                          clenshaw_step_heavy_kernel<T, GG, NN><<<hgrid, kHeavyThreads, 0, st>>>(
                                               g->row_ptr, g->col_idx, idg, sqd, bnext, bpp, Y, perm, g->heavy,
                                               ncols, ld, (A)cj, mode, tab, rs)));
-    }
-    if (last) {
-        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * (1.0 - heavy_frac), s,
-                                          clenshaw_step_kernel<T, GG, NN, true><<<grid, cfg.threads, smem, s>>>(
-                                              g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm, part, ncols,
-                                              ld, (A)cj, mode, tab, rs)));
-    } else {
-        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * (1.0 - heavy_frac), s,
-                                          clenshaw_step_kernel<T, GG, NN, false><<<grid, cfg.threads, smem, s>>>(
-                                              g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm, part, ncols,
-                                              ld, (A)cj, mode, tab, rs)));
-    }
-    return CSC_OK;
+        return CSC_OK;
+    };
+    auto light = [&](cudaStream_t st) -> csc_status {
+        if (last) {
+            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * (1.0 - heavy_frac), st,
+                                              clenshaw_step_kernel<T, GG, NN, true><<<grid, cfg.threads, smem, st>>>(
+                                                  g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm, part, ncols,
+                                                  ld, (A)cj, mode, tab, rs)));
+        } else {
+            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * (1.0 - heavy_frac), st,
+                                              clenshaw_step_kernel<T, GG, NN, false><<<grid, cfg.threads, smem, st>>>(
+                                                  g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm, part, ncols,
+                                                  ld, (A)cj, mode, tab, rs)));
+        }
+        return CSC_OK;
+    };
+    return fork_join(g, s, g->n_heavy > 0, heavy, light);
 }
 
 template <typename T>
@@ -895,19 +906,23 @@ static csc_status launch_mom_step(Graph* g, const LaunchCfg& cfg, const T* xcur,
     const int smem = staged_smem(g, cfg.P);  // the CTA's CSR slice (stage_csr)
     CSC_TRY(check_staged_smem(smem));
     const dim3 grid(cfg.P, cfg.tiles);
-    if (g->n_heavy > 0) {
-        // heavy rows' partial sums go to the slots after the row-range blocks'
-        const dim3 hgrid(g->n_heavy, cfg.tiles);
-        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("mom_step_heavy", 0.0, s,
-                                          mom_step_heavy_kernel<T, GG, NN><<<hgrid, kHeavyThreads, 0, s>>>(
+    // heavy rows' partial sums go to the slots after the row-range blocks'
+    const dim3 hgrid(g->n_heavy > 0 ? g->n_heavy : 1, cfg.tiles);
+    auto heavy = [&](cudaStream_t st) -> csc_status {
+        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("mom_step_heavy", 0.0, st,
+                                          mom_step_heavy_kernel<T, GG, NN><<<hgrid, kHeavyThreads, 0, st>>>(
                                               g->row_ptr, g->col_idx, g->invdeg, g->deg, xcur, xpn, g->heavy, ncols,
                                               ld, first, partials, (int64_t)cfg.P * cfg.tiles)));
-    }
-    CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("mom_step", bytes, s,
-                                      mom_step_kernel<T, GG, NN><<<grid, cfg.threads, smem, s>>>(
-                                          g->lrp, g->lci, g->invdeg, g->deg, xcur, xpn, part, ncols, ld,
-                                          first, partials)));
-    return CSC_OK;
+        return CSC_OK;
+    };
+    auto light = [&](cudaStream_t st) -> csc_status {
+        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("mom_step", bytes, st,
+                                          mom_step_kernel<T, GG, NN><<<grid, cfg.threads, smem, st>>>(
+                                              g->lrp, g->lci, g->invdeg, g->deg, xcur, xpn, part, ncols, ld,
+                                              first, partials)));
+        return CSC_OK;
+    };
+    return fork_join(g, s, g->n_heavy > 0, heavy, light);
 }
 
 // Resident CTAs per SM for a kernel at a block size.
