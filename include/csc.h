@@ -66,9 +66,12 @@ typedef int32_t csc_dtype;
 #define CSC_F64   2
 
 /* csc_graph_create flags */
-#define CSC_RCM            1u  /* reorder nodes by reverse Cuthill-McKee internally   */
+#define CSC_RCM            1u  /* reorder nodes by reverse Cuthill-McKee internally
+                                  (then by decreasing degree within blocks of 128) */
 #define CSC_CHECK_SYM      2u  /* verify W is symmetric (O(nnz log) host check)        */
 #define CSC_DEVICE_INPUT   4u  /* row_ptr / col_idx are device pointers                */
+#define CSC_DEGREE_ORDER   8u  /* reorder nodes by decreasing degree internally (ties
+                                  in the CSC_RCM order when given, else by index)    */
 
 /* csc_filter_random_signals flags */
 #define CSC_NORMALIZE_ROWS 1u  /* Alg. 2 step 4: divide every row by its l2 norm      */
@@ -163,7 +166,7 @@ typedef struct {
  *            CSC_CHECK_SYM).
  *   weights  must be NULL: the graphs of this library are unweighted
  *            (W_ij in {0,1}); non-NULL returns CSC_E_UNSUPPORTED.
- *   flags    CSC_RCM | CSC_CHECK_SYM | CSC_DEVICE_INPUT.  Without
+ *   flags    CSC_RCM | CSC_DEGREE_ORDER | CSC_CHECK_SYM | CSC_DEVICE_INPUT.  Without
  *            CSC_DEVICE_INPUT the arrays are host memory; with it they are
  *            device memory, copied to the host first.  Either way the CSR is
  *            validated on the host and every flag applies.
@@ -196,7 +199,8 @@ CSC_API csc_status csc_graph_info(csc_graph g, int64_t* N, int64_t* nnz, int32_t
  * graph.  Entry i
  * (0-based) is written to kind, dtype_bytes (4 fp32, 2 bf16, 8 fp64), columns and
  * shape[6] = {lanes per row G, vectors per lane NT, threads per CTA, row ranges P,
- * column tiles, 0 (reserved)}.  Host outputs (any may be
+ * column tiles, index source}: index source 0 = each CTA stages its rows' column
+ * indices in shared memory, 1 = the indices are read from global memory.  Host outputs (any may be
  * NULL).  CSC_E_INVALID when i is out of range. */
 CSC_API csc_status csc_graph_tuned_shape(csc_graph g, int32_t i, int32_t* kind, int32_t* dtype_bytes,
                                          int32_t* columns, int32_t* shape);
@@ -205,7 +209,7 @@ CSC_API csc_status csc_graph_tuned_shape(csc_graph g, int32_t i, int32_t* kind, 
  * instead of tuning it (reproducible timings; tests of every compiled shape).
  * kind, dtype_bytes, columns and shape[6] as in csc_graph_tuned_shape (host).
  * (G, NT) must be a compiled pair, threads 256 or 512, tiles = ceil(vectors per
- * row / (G NT)), shape[5] = 0.
+ * row / (G NT)), index source 0 or 1.
  * Errors: CSC_E_INVALID (no side effects); an uncompiled (G, NT) surfaces as
  * CSC_E_UNSUPPORTED at the next launch. */
 CSC_API csc_status csc_graph_pin_shape(csc_graph g, int32_t kind, int32_t dtype_bytes, int32_t columns,

@@ -16,7 +16,7 @@ parts the paper leaves to that library:
 * the replicate with the smallest inertia sum ||x_i - c_label(i)||^2 wins
   (ties to the first).
 
-Pins (tests/test_oracle_kmeans.py): on n <= 10 points with k <= 3 the best
+Pins (tests/test_oracle_misc.py): on n <= 10 points with k <= 3 the best
 replicate reaches the minimum inertia found by brute force over all
 partitions; well-separated blobs are recovered exactly.
 """

@@ -34,7 +34,7 @@ CSC_E_NUMERIC = 7
 CSC_E_UNSUPPORTED = 8
 
 CSC_F32, CSC_BF16, CSC_F64 = 0, 1, 2
-CSC_RCM, CSC_CHECK_SYM, CSC_DEVICE_INPUT = 1, 2, 4
+CSC_RCM, CSC_CHECK_SYM, CSC_DEVICE_INPUT, CSC_DEGREE_ORDER = 1, 2, 4, 8
 CSC_NORMALIZE_ROWS, CSC_NO_JACKSON, CSC_CLENSHAW, CSC_HIGHPASS, CSC_VARDENSITY = 1, 2, 4, 8, 16
 CSC_CHECK_FINITE = 32
 CSC_MLP_IN, CSC_MLP_HIDDEN, CSC_MLP_OUT, CSC_MLP_PARAMS = 72, 256, 2, 84994

@@ -18,7 +18,7 @@ from . import _native as nat
 from ._native import check, lib
 
 F32, BF16, F64 = nat.CSC_F32, nat.CSC_BF16, nat.CSC_F64
-RCM, CHECK_SYM, DEVICE_INPUT = nat.CSC_RCM, nat.CSC_CHECK_SYM, nat.CSC_DEVICE_INPUT
+RCM, CHECK_SYM, DEVICE_INPUT, DEGREE_ORDER = nat.CSC_RCM, nat.CSC_CHECK_SYM, nat.CSC_DEVICE_INPUT, nat.CSC_DEGREE_ORDER
 NORMALIZE_ROWS, NO_JACKSON, CLENSHAW, HIGHPASS, VARDENSITY = (nat.CSC_NORMALIZE_ROWS, nat.CSC_NO_JACKSON,
                                                               nat.CSC_CLENSHAW, nat.CSC_HIGHPASS,
                                                               nat.CSC_VARDENSITY)
@@ -125,16 +125,18 @@ def csc_graph_tuned_shapes(g: Graph) -> list:
                                        shape) != nat.CSC_OK:
             break
         out.append(dict(kernel=kinds.get(kind.value, str(kind.value)), dtype_bytes=db.value, columns=cols.value,
-                        G=shape[0], NT=shape[1], threads=shape[2], P=shape[3], tiles=shape[4]))
+                        G=shape[0], NT=shape[1], threads=shape[2], P=shape[3], tiles=shape[4],
+                        global_index=shape[5]))
         i += 1
     return out
 
 
 def csc_graph_pin_shape(g: Graph, kernel: str, dtype_bytes: int, columns: int, G: int, NT: int, threads: int,
-                        P: int, tiles: int, reserved: int = 0) -> None:
-    """Fix a launch shape on this handle instead of tuning it (the sixth entry is reserved: 0)."""
+                        P: int, tiles: int, global_index: int = 0) -> None:
+    """Fix a launch shape on this handle instead of tuning it (global_index = 1: the row-range
+    kernels read column indices from global memory instead of staging them in shared memory)."""
     kind = {"cheb_step": 1, "mom_step": 2, "cg": 3, "clenshaw": 4}[kernel]
-    shape = (ctypes.c_int32 * 6)(G, NT, threads, P, tiles, reserved)
+    shape = (ctypes.c_int32 * 6)(G, NT, threads, P, tiles, global_index)
     check(lib().csc_graph_pin_shape(g.handle, kind, dtype_bytes, columns, shape), "csc_graph_pin_shape")
 
 

@@ -360,7 +360,8 @@ void estimate_from_moments(const double* mu, int m, int k, csc_lambda_info* out)
 // --------------------------------------------------------- reverse Cuthill-McKee
 // Cuthill & McKee (1969), reversed (George 1971): BFS from a minimum-degree
 // node of each component, visiting neighbours by increasing degree; the
-// visit order reversed gives perm[new] = old.
+// visit order reversed gives perm[new] = old (then sorted by degree within
+// blocks of 128 rows, see below).
 static void rcm_order(int64_t N, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
                       std::vector<int32_t>& perm) {
     std::vector<int32_t> deg(N);
@@ -391,6 +392,14 @@ static void rcm_order(int64_t N, const std::vector<int64_t>& rp, const std::vect
         }
     }
     perm.assign(visit.rbegin(), visit.rend());
+    // then, within blocks of kDegreeBlock consecutive rows, rows by decreasing degree: the two
+    // lane groups of a warp sweep neighbouring rows, which then need about as many gather
+    // batches each (power-law degrees otherwise leave one group idle while the other
+    // finishes a long row); the block is far below a row range, so locality is kept
+    constexpr int64_t kDegreeBlock = 128;
+    for (int64_t b = 0; b < N; b += kDegreeBlock)
+        std::stable_sort(perm.begin() + b, perm.begin() + std::min<int64_t>(N, b + kDegreeBlock),
+                         [&](int32_t x, int32_t y) { return deg[x] > deg[y]; });
 }
 
 // ------------------------------------------------------------- graph create
@@ -699,9 +708,20 @@ csc_status csc_graph_create(int64_t N, int64_t nnz, const int64_t* row_ptr, cons
         return CSC_E_OOM;
     }
     csc_status st;
-    if (flags & CSC_RCM) {
+    if (flags & (CSC_RCM | CSC_DEGREE_ORDER)) {
         std::vector<int32_t> perm;
-        rcm_order(N, clean.rp, clean.ci, perm);
+        if (flags & CSC_RCM) {
+            rcm_order(N, clean.rp, clean.ci, perm);
+        } else {
+            perm.resize(N);
+            std::iota(perm.begin(), perm.end(), 0);
+        }
+        if (flags & CSC_DEGREE_ORDER) {
+            // decreasing degree: the rows most neighbours gather come first, back to back
+            std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) {
+                return clean.rp[a + 1] - clean.rp[a] > clean.rp[b + 1] - clean.rp[b];
+            });
+        }
         HostCSR pc;
         permute_csr(clean, perm, pc);
         st = upload(g, pc, &perm, s);
@@ -725,8 +745,8 @@ csc_status csc_graph_create_batched(int32_t G, const int64_t* Ns, const int64_t*
         return CSC_E_INVALID;
     }
     *out = nullptr;
-    if (flags & (CSC_DEVICE_INPUT | CSC_RCM)) {
-        set_error("csc_graph_create_batched: host input only, without CSC_RCM");
+    if (flags & (CSC_DEVICE_INPUT | CSC_RCM | CSC_DEGREE_ORDER)) {
+        set_error("csc_graph_create_batched: host input only, without reordering");
         return CSC_E_UNSUPPORTED;
     }
     HostCSR packed;
@@ -825,7 +845,7 @@ csc_status csc_graph_tuned_shape(csc_graph g, int32_t i, int32_t* kind, int32_t*
         shape[2] = it->second.threads;
         shape[3] = it->second.P;
         shape[4] = it->second.tiles;
-        shape[5] = 0;  // reserved
+        shape[5] = it->second.staged ? 0 : 1;
     }
     return CSC_OK;
 }
@@ -835,7 +855,7 @@ csc_status csc_graph_pin_shape(csc_graph g, int32_t kind, int32_t dtype_bytes, i
     clear_error();
     CSC_TRY(check_graph(g));
     if (!shape || kind < 1 || kind > 4 || columns < 1 || shape[0] < 1 || shape[1] < 1 ||
-        (shape[2] != 256 && shape[2] != 512) || shape[3] < 1 || shape[4] < 1 || shape[5] != 0) {
+        (shape[2] != 256 && shape[2] != 512) || shape[3] < 1 || shape[4] < 1 || shape[5] < 0 || shape[5] > 1) {
         set_error("csc_graph_pin_shape: invalid shape");
         return CSC_E_INVALID;
     }
@@ -857,6 +877,7 @@ csc_status csc_graph_pin_shape(csc_graph g, int32_t kind, int32_t dtype_bytes, i
     c.threads = shape[2];
     c.P = shape[3];
     c.tiles = shape[4];
+    c.staged = shape[5] == 0 ? 1 : 0;
     const uint64_t key = kind == 3 ? ((3ull << 48) | (uint64_t)(uint32_t)columns)
                                    : (((uint64_t)kind << 48) | ((uint64_t)(dtype_bytes & 0xff) << 40) |
                                       (uint64_t)(uint32_t)columns);

@@ -137,19 +137,20 @@ __device__ __forceinline__ void lap_epilogue(int row, int lane, int col0, int tc
 }
 
 // Rows of degree > kHeavyRow are left to lap_heavy_kernel.
-template <int G, int NT, bool WIN>
+template <int G, int NT, bool WIN, bool STAGED>
 __global__ void __launch_bounds__(kCgMaxThreads)
-lap_kernel(const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci, const float* __restrict__ dinv,
+lap_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const int32_t* __restrict__ lrp,
+           const int32_t* __restrict__ lci, const float* __restrict__ dinv,
            const float* __restrict__ invdeg, const float* __restrict__ in, float* __restrict__ out,
            const int32_t* __restrict__ part, int ncols, int64_t ld, CgBatch bt) {
     CG_TILE(G, NT)
     extern __shared__ int32_t s_csr[];
-    const StagedCsr sc = stage_csr(lrp, lci, part[blockIdx.x], r1, s_csr);
-    for_each_staged_row(sc, (int)(threadIdx.x / G), (int)(blockDim.x / G), [&](int row, int e0, int e1) {
+    sweep_rows<STAGED, G>(rp, ci, lrp, lci, part[blockIdx.x], r1, s_csr, [&](int row, int e0, int e1,
+                                                                            const int32_t* idx) {
         RowVecs<G, NT> x;
         x.load(in, row, lane, col0, tcols, ld);
         float acc[NT][4];
-        gather_staged<float, G, NT, WIN, float>(e0, e1, sc.ci, dinv, in + col0, ld, lane, tcols, acc);
+        gather_any<STAGED, float, G, NT, WIN, float>(e0, e1, idx, dinv, in + col0, ld, lane, tcols, acc);
         lap_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, invdeg, x, out, ld);
     });
 }
@@ -205,22 +206,23 @@ __device__ __forceinline__ void lap_ax_epilogue(int row, int lane, int col0, int
 
 // <p, A p> partial slots: [0, gridDim.x) for the row ranges, then one per heavy
 // row (lap_ax_heavy_kernel); nslots counts both.
-template <int G, int NT, bool WIN>
+template <int G, int NT, bool WIN, bool STAGED>
 __global__ void __launch_bounds__(kCgMaxThreads)
-lap_ax_kernel(const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci, const float* __restrict__ dinv,
+lap_ax_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const int32_t* __restrict__ lrp,
+              const int32_t* __restrict__ lci, const float* __restrict__ dinv,
               const float* __restrict__ sqdeg, const float* __restrict__ tin, const float* __restrict__ p,
               const float* __restrict__ mask, float gamma, float* __restrict__ Ap, const int32_t* __restrict__ part,
               int ncols, int64_t ld, double* __restrict__ partials, int nslots, CgBatch bt) {
     CG_TILE(G, NT)
     KSum dot[1][NT][4];
     extern __shared__ int32_t s_csr[];
-    const StagedCsr sc = stage_csr(lrp, lci, part[blockIdx.x], r1, s_csr);
-    for_each_staged_row(sc, (int)(threadIdx.x / G), (int)(blockDim.x / G), [&](int row, int e0, int e1) {
+    sweep_rows<STAGED, G>(rp, ci, lrp, lci, part[blockIdx.x], r1, s_csr, [&](int row, int e0, int e1,
+                                                                            const int32_t* idx) {
         RowVecs<G, NT> tv, pv;
         tv.load(tin, row, lane, col0, tcols, ld);
         pv.load(p, row, lane, col0, tcols, ld);
         float acc[NT][4];
-        gather_staged<float, G, NT, WIN, float>(e0, e1, sc.ci, dinv, tin + col0, ld, lane, tcols, acc);
+        gather_any<STAGED, float, G, NT, WIN, float>(e0, e1, idx, dinv, tin + col0, ld, lane, tcols, acc);
         lap_ax_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, sqdeg, tv, pv, mask, gamma, Ap, ld, dot);
     });
     block_column_partials<G, NT, 1>(dot, lane, col0, tcols, ld, partials, blockIdx.x, nslots);
@@ -696,7 +698,7 @@ __global__ void label_argmax_kernel(const float* __restrict__ x, const double* _
 }
 
 // ------------------------------------------------------------- dispatch
-static const int kCgShapes[][2] = {{2, 1}, {4, 1}, {8, 1}, {16, 1}, {32, 1}, {32, 2}};
+static const int kCgShapes[][2] = {{2, 1}, {4, 1}, {8, 1}, {16, 1}, {16, 2}, {32, 1}, {32, 2}};
 static const int kCgThreadChoices[] = {256, 512};
 
 #define CG_SWITCH(cfg, ...)                                                                        \
@@ -706,6 +708,7 @@ static const int kCgThreadChoices[] = {256, 512};
             case 4 * 8 + 1: { constexpr int G_ = 4, NT_ = 1; __VA_ARGS__; } break;                 \
             case 8 * 8 + 1: { constexpr int G_ = 8, NT_ = 1; __VA_ARGS__; } break;                 \
             case 16 * 8 + 1: { constexpr int G_ = 16, NT_ = 1; __VA_ARGS__; } break;               \
+            case 16 * 8 + 2: { constexpr int G_ = 16, NT_ = 2; __VA_ARGS__; } break;               \
             case 32 * 8 + 1: { constexpr int G_ = 32, NT_ = 1; __VA_ARGS__; } break;               \
             case 32 * 8 + 2: { constexpr int G_ = 32, NT_ = 2; __VA_ARGS__; } break;               \
             default:                                                                               \
@@ -718,13 +721,25 @@ template <int G, int NT>
 static int cg_occupancy_of(int threads) {
     // the solve's most register-hungry kernel bounds the residency of all of them
     int a = 1, b = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, lap_kernel<G, NT, false>, threads, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, lap_kernel<G, NT, false, true>, threads, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cg_update_kernel<G, NT>, threads, 0) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
     const int n = std::min(a, b);
     return n < 1 ? 1 : n;
+}
+
+// Dynamic shared memory a staged launch of the shape may add to the solve's kernels' own
+// arrays (the fused product's column partials take 16 KB per vector per lane).
+template <int G, int NT>
+static int cg_staged_room() {
+    cudaFuncAttributes a{};
+    if (cudaFuncGetAttributes(&a, lap_ax_kernel<G, NT, false, true>) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (int)a.maxDynamicSharedSizeBytes;
 }
 
 static csc_status cg_occupancy(const LaunchCfg& c, int* out) {
@@ -779,6 +794,11 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                     cands.back().threads == th && cands.back().P == c.P)
                     continue;
                 max_p = std::max(max_p, c.P);
+                int room = 0;
+                CG_SWITCH(c, room = cg_staged_room<G_, NT_>());
+                c.staged = 1;  // both index sources (sweep_rows), the staged one where it fits
+                if (staged_smem(g, c.P) <= std::min(room, kStagedSmemMax)) cands.push_back(c);
+                c.staged = 0;
                 cands.push_back(c);
             }
         }
@@ -906,10 +926,35 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                 CSC_TRY(get_partition(g, c.P, &pr));
                 const dim3 grid(c.P, c.tiles);
                 float ms = 0.f;
-                for (int rep = 0; rep < 4; ++rep) {
+                // one iteration's row-range work on scratch: three products of the chain, the
+                // last product with the mask term and <., .> partials, and the update's partials
+                // (alpha = NULL: nothing is updated); a shape is judged by all of them
+                const int sm = c.staged ? staged_smem(g, c.P) : 0;
+                for (int rep = 0; rep < 3; ++rep) {
                     if (rep == 1) cudaEventRecord(g->ev[0], s);
-                    CG_SWITCH(c, lap_kernel<G_, NT_, false><<<grid, c.threads, staged_smem(g, c.P), s>>>(
-                                     g->lrp, g->lci, g->dinv, g->invdeg, r, t1, pr, ld, ld, CgBatch()));
+                    const float* src[3] = {r, t1, t2};
+                    float* dst[3] = {t1, t2, t1};
+                    for (int q = 0; q < 3; ++q) {
+                        if (c.staged)
+                            CG_SWITCH(c, lap_kernel<G_, NT_, false, true><<<grid, c.threads, sm, s>>>(
+                                             g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->invdeg, src[q], dst[q],
+                                             pr, ld, ld, CgBatch()));
+                        else
+                            CG_SWITCH(c, lap_kernel<G_, NT_, false, false><<<grid, c.threads, 0, s>>>(
+                                             g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->invdeg, src[q], dst[q],
+                                             pr, ld, ld, CgBatch()));
+                    }
+                    if (c.staged)
+                        CG_SWITCH(c, lap_ax_kernel<G_, NT_, false, true><<<grid, c.threads, sm, s>>>(
+                                         g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->sqdeg, t1, p, mask,
+                                         (float)gamma, Ap, pr, ld, ld, part, c.P, CgBatch()));
+                    else
+                        CG_SWITCH(c, lap_ax_kernel<G_, NT_, false, false><<<grid, c.threads, 0, s>>>(
+                                         g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->sqdeg, t1, p, mask,
+                                         (float)gamma, Ap, pr, ld, ld, part, c.P, CgBatch()));
+                    CG_SWITCH(c, cg_update_kernel<G_, NT_><<<grid, c.threads, 0, s>>>(x, r, p, Ap, nullptr, nullptr,
+                                                                                       pinv, pr, ld, ld, part,
+                                                                                       CgBatch()));
                 }
                 cudaEventRecord(g->ev[1], s);
                 CSC_CUDA_TRY(cudaEventSynchronize(g->ev[1]));
@@ -927,8 +972,17 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     }
     const int32_t* rpart = nullptr;
     CSC_TRY(get_partition(g, cfg.P, &rpart));
-    const int csmem = staged_smem(g, cfg.P);  // the CTA's CSR slice (stage_csr)
+    const int csmem = cfg.staged ? staged_smem(g, cfg.P) : 0;  // the CTA's CSR slice (stage_csr)
     CSC_TRY(check_staged_smem(csmem));
+    {
+        int room = 0;
+        CG_SWITCH(cfg, room = cg_staged_room<G_, NT_>());
+        if (csmem > room) {
+            set_error("csc_interpolate: a row range's CSR slice (%d bytes) does not fit beside the CG kernels' "
+                      "shared arrays (%d bytes free): use more row ranges or the global index source", csmem, room);
+            return CSC_E_UNSUPPORTED;
+        }
+    }
     const dim3 grid(cfg.P, cfg.tiles);
     const int th = cfg.threads;
     const int P = cfg.P;
@@ -1014,14 +1068,18 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                 return CSC_OK;
             };
             auto light = [&](cudaStream_t st) -> csc_status {
-                if (win)
-                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * (1.0 - heavy_frac), st,
-                                               lap_kernel<G_, NT_, true><<<grid, th, csmem, st>>>(
-                                                   g->lrp, g->lci, g->dinv, g->invdeg, cur, o, rpart, ld, ld, bb)));
-                else
-                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", lb * (1.0 - heavy_frac), st,
-                                               lap_kernel<G_, NT_, false><<<grid, th, csmem, st>>>(
-                                                   g->lrp, g->lci, g->dinv, g->invdeg, cur, o, rpart, ld, ld, bb)));
+                const double by = lb * (1.0 - heavy_frac);
+#define CSC_LAP(W, S)                                                                                        \
+    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", by, st,                                                             \
+                               (lap_kernel<G_, NT_, W, S><<<grid, th, csmem, st>>>(g->row_ptr, g->col_idx,   \
+                                                                                  g->lrp, g->lci, g->dinv,   \
+                                                                                  g->invdeg, cur, o, rpart,  \
+                                                                                  ld, ld, bb))))
+                if (win && cfg.staged) CSC_LAP(true, true);
+                else if (win) CSC_LAP(true, false);
+                else if (cfg.staged) CSC_LAP(false, true);
+                else CSC_LAP(false, false);
+#undef CSC_LAP
                 return CSC_OK;
             };
             CSC_TRY(fork_join(g, s, H > 0, heavy, light));
@@ -1044,16 +1102,17 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
             return CSC_OK;
         };
         auto light = [&](cudaStream_t st) -> csc_status {
-            if (win)
-                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * (1.0 - heavy_frac), st,
-                                           lap_ax_kernel<G_, NT_, true><<<grid, th, csmem, st>>>(
-                                               g->lrp, g->lci, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
-                                               rpart, ld, ld, part, PH, bb)));
-            else
-                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", ab * (1.0 - heavy_frac), st,
-                                           lap_ax_kernel<G_, NT_, false><<<grid, th, csmem, st>>>(
-                                               g->lrp, g->lci, g->dinv, g->sqdeg, cur, in, mask, (float)gamma, Ap,
-                                               rpart, ld, ld, part, PH, bb)));
+            const double by = ab * (1.0 - heavy_frac);
+#define CSC_LAPAX(W, S)                                                                                         \
+    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", by, st,                                                             \
+                               (lap_ax_kernel<G_, NT_, W, S><<<grid, th, csmem, st>>>(                          \
+                                   g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->sqdeg, cur, in, mask,    \
+                                   (float)gamma, Ap, rpart, ld, ld, part, PH, bb))))
+            if (win && cfg.staged) CSC_LAPAX(true, true);
+            else if (win) CSC_LAPAX(true, false);
+            else if (cfg.staged) CSC_LAPAX(false, true);
+            else CSC_LAPAX(false, false);
+#undef CSC_LAPAX
             return CSC_OK;
         };
         return fork_join(g, s, H > 0, heavy, light);

@@ -104,6 +104,7 @@ struct Buffer {
 // (one CTA each per tile) and `tiles` column tiles.
 struct LaunchCfg {
     int G = 0, NT = 0, threads = 0, P = 0, tiles = 1;
+    int staged = 1;  // row-range kernels: indices staged in shared memory (0: read from global)
 };
 
 struct Graph {

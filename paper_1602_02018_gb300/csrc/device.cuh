@@ -281,10 +281,61 @@ __device__ __forceinline__ void for_each_staged_row(const StagedCsr& c, int firs
     }
 }
 
+// One batch of gather_staged: edges e .. e + cnt - 1 (cnt <= BB) with BB load slots.
+template <int BB, typename T, int G, int NT, bool WEIGHTED, typename W>
+__device__ __forceinline__ void gather_batch(int e, int cnt, const int32_t* ci, const W* __restrict__ wv,
+                                             const T* __restrict__ X, int64_t ld, int lane, const bool (&valid)[NT],
+                                             typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC]) {
+    using Tr = StoreTraits<T>;
+    using A = typename Tr::acc_t;
+    constexpr int VEC = Tr::VEC;
+    const T* rowp[BB];
+    A w[BB];
+#pragma unroll
+    for (int u = 0; u < BB; ++u) {
+        const int l = u < cnt ? ci[e + u] : 0;
+        rowp[u] = X + (int64_t)l * ld + lane * VEC;
+        if (WEIGHTED) w[u] = u < cnt ? A(__ldg(wv + l)) : A(0);
+        else w[u] = A(1);
+    }
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        if (!valid[t]) continue;
+        if constexpr (sizeof(T) == 2) {
+            // bf16: the loads stay packed (half the registers of their fp32 values) until added
+            typename Tr::raw_t q[BB];
+#pragma unroll
+            for (int u = 0; u < BB; ++u) q[u] = u < cnt ? Tr::ld_raw(rowp[u] + t * G * VEC) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int u = 0; u < BB; ++u) {
+                A x[VEC];
+                Tr::unraw(q[u], x);
+                acc_vec<WEIGHTED, VEC>(acc[t], w[u], x);
+            }
+        } else {
+            A x[BB][VEC];
+#pragma unroll
+            for (int u = 0; u < BB; ++u) {
+                if (u < cnt)
+                    Tr::load(rowp[u] + t * G * VEC, x[u]);
+                else
+#pragma unroll
+                    for (int v = 0; v < VEC; ++v) x[u][v] = A(0);
+            }
+#pragma unroll
+            for (int u = 0; u < BB; ++u) acc_vec<WEIGHTED, VEC>(acc[t], w[u], x[u]);
+        }
+    }
+}
+
 // Neighbour sum of one row whose column indices ci[e .. end) are in shared memory
 // (see gather_range for acc, G, NT and the weights): every lane of a group reads each
 // index itself (one broadcast shared-memory word), so no shuffle or global index load
-// precedes the neighbour-row loads.
+// precedes the neighbour-row loads.  Edges go in batches of up to B neighbour rows in
+// flight; when every lane group of the warp has a short tail (most rows of a power-law
+// graph have one to four edges) the batch has 2 or 4 slots, so fewer instructions go to
+// empty slots.  The sum runs over the edges in order whatever the batching, so every
+// batching gives the same bits.
 template <typename T, int G, int NT, bool WEIGHTED, typename W>
 __device__ __forceinline__ void gather_staged(int e, const int end, const int32_t* ci, const W* __restrict__ wv,
                                               const T* __restrict__ X, int64_t ld, int lane, int ncols,
@@ -303,30 +354,15 @@ __device__ __forceinline__ void gather_staged(int e, const int end, const int32_
     for (int t = 0; t < NT; ++t) valid[t] = ((t * G + lane) * VEC) < ncols;
     for (; e < end; e += B) {
         const int cnt = min(B, end - e);
-        const T* rowp[B];
-        A w[B];
-#pragma unroll
-        for (int u = 0; u < B; ++u) {
-            const int l = u < cnt ? ci[e + u] : 0;
-            rowp[u] = X + (int64_t)l * ld + lane * VEC;
-            if (WEIGHTED) w[u] = u < cnt ? A(__ldg(wv + l)) : A(0);
-            else w[u] = A(1);
-        }
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-            if (!valid[t]) continue;
-            A x[B][VEC];
-#pragma unroll
-            for (int u = 0; u < B; ++u) {
-                if (u < cnt)
-                    Tr::load(rowp[u] + t * G * VEC, x[u]);
-                else
-#pragma unroll
-                    for (int v = 0; v < VEC; ++v) x[u][v] = A(0);
-            }
-#pragma unroll
-            for (int u = 0; u < B; ++u) acc_vec<WEIGHTED, VEC>(acc[t], w[u], x[u]);
-        }
+        // the batch size follows the largest count among the lanes here, so the lane groups
+        // of a warp take the same branch and issue their loads together
+        const int most = (int)__reduce_max_sync(__activemask(), (unsigned)cnt);
+        if (most > B / 2)
+            gather_batch<B, T, G, NT, WEIGHTED, W>(e, cnt, ci, wv, X, ld, lane, valid, acc);
+        else if (B == 8 && most > 2)
+            gather_batch<4, T, G, NT, WEIGHTED, W>(e, cnt, ci, wv, X, ld, lane, valid, acc);
+        else
+            gather_batch<2, T, G, NT, WEIGHTED, W>(e, cnt, ci, wv, X, ld, lane, valid, acc);
     }
 }
 
@@ -405,6 +441,27 @@ __device__ __forceinline__ void gather_range(int e, const int end, const int32_t
     }
 }
 
+// ------------------------------------------------ row sweeps with either index source
+// A row-range kernel reads its rows' column indices either from the CTA's staged slice in
+// shared memory (STAGED: one bulk copy at the start, no index load before a gather) or
+// straight from global memory (the next row's extents prefetched); the autotuner times
+// both, as the staging pays off on short rows (power-law graphs) and costs a start-up
+// wait on short ranges.  sweep_rows calls body(row, e0, e1, idx) for the CTA's light rows
+// [r0, r1) of lane group threadIdx.x / G, with the row's indices idx[e0 .. e1).
+template <bool STAGED, int G, typename Body>
+__device__ __forceinline__ void sweep_rows(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                           const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci, int r0,
+                                           int r1, int32_t* smem, Body&& body) {
+    if constexpr (STAGED) {
+        const StagedCsr sc = stage_csr(lrp, lci, r0, r1, smem);
+        for_each_staged_row(sc, (int)(threadIdx.x / G), (int)(blockDim.x / G),
+                            [&](int row, int e0, int e1) { body(row, e0, e1, sc.ci); });
+    } else {
+        for_each_row(rp, r0 + (int)(threadIdx.x / G), r1, (int)(blockDim.x / G),
+                     [&](int row, int e0, int e1) { body(row, e0, e1, ci); });
+    }
+}
+
 // The neighbour sum of a whole row (see gather_range).
 template <typename T, int G, int NT, bool WEIGHTED, typename W>
 __device__ __forceinline__ void gather_row(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -412,6 +469,15 @@ __device__ __forceinline__ void gather_row(const int32_t* __restrict__ rp, const
                                            int lane, int ncols,
                                            typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC]) {
     gather_range<T, G, NT, WEIGHTED, W>(__ldg(rp + row), __ldg(rp + row + 1), ci, wv, X, ld, lane, ncols, acc);
+}
+
+// The neighbour sum of one light row with indices from either source (see sweep_rows).
+template <bool STAGED, typename T, int G, int NT, bool WEIGHTED, typename W>
+__device__ __forceinline__ void gather_any(int e0, int e1, const int32_t* idx, const W* __restrict__ wv,
+                                           const T* __restrict__ X, int64_t ld, int lane, int ncols,
+                                           typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC]) {
+    if constexpr (STAGED) gather_staged<T, G, NT, WEIGHTED, W>(e0, e1, idx, wv, X, ld, lane, ncols, acc);
+    else gather_range<T, G, NT, WEIGHTED, W>(e0, e1, idx, wv, X, ld, lane, ncols, acc);
 }
 
 // Neighbour sum of a heavy row (see kHeavyRow) by a whole CTA of kHeavyThreads

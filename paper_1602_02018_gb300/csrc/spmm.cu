@@ -269,9 +269,10 @@ __device__ __forceinline__ void cheb_epilogue(int row, int lane, int col0, int t
     }
 }
 
-template <typename T, int G, int NT>
+template <typename T, int G, int NT, bool STAGED>
 __global__ void __launch_bounds__(512)
-cheb_step_kernel(const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci,
+cheb_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const int32_t* __restrict__ lrp,
+                 const int32_t* __restrict__ lci,
                  const typename StoreTraits<T>::acc_t* __restrict__ invdeg,
                  const typename StoreTraits<T>::acc_t* __restrict__ sqdeg, const T* __restrict__ zcur,
                  T* __restrict__ zprev_next, typename StoreTraits<T>::acc_t* __restrict__ Y,
@@ -291,12 +292,11 @@ cheb_step_kernel(const int32_t* __restrict__ lrp, const int32_t* __restrict__ lc
         c_next = cg[tab.j];
     }
     extern __shared__ int32_t s_csr[];
-    const StagedCsr sc = stage_csr(lrp, lci, r0, r1, s_csr);
-    for_each_staged_row(sc, (int)(threadIdx.x / G), (int)(blockDim.x / G), [&](int row, int e0, int e1) {
+    sweep_rows<STAGED, G>(rp, ci, lrp, lci, r0, r1, s_csr, [&](int row, int e0, int e1, const int32_t* idx) {
         ChebOperands<T, G, NT> op;
         op.load(row, lane, col0, tcols, mode, zcur, zprev_next, Y, perm, ld);
         A acc[NT][VEC];
-        gather_staged<T, G, NT, false, A>(e0, e1, sc.ci, nullptr, zcur + col0, ld, lane, tcols, acc);
+        gather_any<STAGED, T, G, NT, false, A>(e0, e1, idx, nullptr, zcur + col0, ld, lane, tcols, acc);
         cheb_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, sqdeg, zprev_next, Y, perm, ld, c0, c_next, mode,
                                 op);
     });
@@ -470,9 +470,10 @@ __device__ __forceinline__ void clenshaw_epilogue(int row, int lane, int col0, i
     }
 }
 
-template <typename T, int G, int NT, bool LAST>
+template <typename T, int G, int NT, bool LAST, bool STAGED>
 __global__ void __launch_bounds__(512)
-clenshaw_step_kernel(const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci,
+clenshaw_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const int32_t* __restrict__ lrp,
+                     const int32_t* __restrict__ lci,
                      const typename StoreTraits<T>::acc_t* __restrict__ invdeg,
                      const typename StoreTraits<T>::acc_t* __restrict__ sqdeg,
                      const T* __restrict__ bnext, T* __restrict__ bpp, typename StoreTraits<T>::acc_t* __restrict__ Y,
@@ -493,12 +494,11 @@ clenshaw_step_kernel(const int32_t* __restrict__ lrp, const int32_t* __restrict_
     const unsigned gmask =
         G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(unsigned)(G - 1)));
     extern __shared__ int32_t s_csr[];
-    const StagedCsr sc = stage_csr(lrp, lci, r0, r1, s_csr);
-    for_each_staged_row(sc, (int)(threadIdx.x / G), (int)(blockDim.x / G), [&](int row, int e0, int e1) {
+    sweep_rows<STAGED, G>(rp, ci, lrp, lci, r0, r1, s_csr, [&](int row, int e0, int e1, const int32_t* idx) {
         ClenOperands<T, G, NT> op;
         op.load(row, lane, col0, tcols, mode, rs, bpp, ld, invdeg);
         A acc[NT][VEC];
-        gather_staged<T, G, NT, false, A>(e0, e1, sc.ci, nullptr, bnext + col0, ld, lane, tcols, acc);
+        gather_any<STAGED, T, G, NT, false, A>(e0, e1, idx, nullptr, bnext + col0, ld, lane, tcols, acc);
         clenshaw_epilogue<T, G, NT, LAST>(row, lane, col0, tcols, acc, invdeg, sqdeg, bpp, Y, perm, ld, cj, mode, op,
                                           gmask);
     });
@@ -644,9 +644,10 @@ __device__ __forceinline__ void mom_block_partials(double s0, double s1, double 
     }
 }
 
-template <typename T, int G, int NT>
+template <typename T, int G, int NT, bool STAGED>
 __global__ void __launch_bounds__(512)
-mom_step_kernel(const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci, const float* __restrict__ invdeg,
+mom_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const int32_t* __restrict__ lrp,
+                const int32_t* __restrict__ lci, const float* __restrict__ invdeg,
                 const int32_t* __restrict__ deg, const T* __restrict__ zcur, T* __restrict__ zprev_next,
                 const int32_t* __restrict__ part, int ncols, int64_t ld, int first, double* __restrict__ partials) {
     constexpr int VEC = StoreTraits<T>::VEC;
@@ -657,12 +658,12 @@ mom_step_kernel(const int32_t* __restrict__ lrp, const int32_t* __restrict__ lci
     const int r1 = part[blockIdx.x + 1];
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     extern __shared__ int32_t s_csr[];
-    const StagedCsr sc = stage_csr(lrp, lci, part[blockIdx.x], r1, s_csr);
-    for_each_staged_row(sc, (int)(threadIdx.x / G), (int)(blockDim.x / G), [&](int row, int e0, int e1) {
+    sweep_rows<STAGED, G>(rp, ci, lrp, lci, part[blockIdx.x], r1, s_csr, [&](int row, int e0, int e1,
+                                                                            const int32_t* idx) {
         MomOperands<T, NT> op;
         op.load(row, lane, G, col0, tcols, first, zcur, zprev_next, ld);
         float acc[NT][VEC];
-        gather_staged<T, G, NT, false, float>(e0, e1, sc.ci, nullptr, zcur + col0, ld, lane, tcols, acc);
+        gather_any<STAGED, T, G, NT, false, float>(e0, e1, idx, nullptr, zcur + col0, ld, lane, tcols, acc);
         float p0, p1, p2;
         mom_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, zprev_next, ld, first, op, p0, p1, p2);
         // the row's degree (d_i of the X-space inner product) is its edge count
@@ -771,24 +772,26 @@ enum KernelKind { KK_CHEB = 1, KK_MOM = 2, KK_CLEN = 4 };
 
 // Expands BODY for the compiled (G, NT) equal to (cfg.G, cfg.NT), with GG / NN bound.
 #define CSC_SHAPE_SWITCH(cfg, BODY)                                                       \
-    switch ((cfg).G * 8 + (cfg).NT) {                                                     \
-        case 2 * 8 + 1: { constexpr int GG = 2, NN = 1; BODY; } break;                    \
-        case 2 * 8 + 2: { constexpr int GG = 2, NN = 2; BODY; } break;                    \
-        case 2 * 8 + 3: { constexpr int GG = 2, NN = 3; BODY; } break;                    \
-        case 4 * 8 + 1: { constexpr int GG = 4, NN = 1; BODY; } break;                    \
-        case 4 * 8 + 2: { constexpr int GG = 4, NN = 2; BODY; } break;                    \
-        case 4 * 8 + 3: { constexpr int GG = 4, NN = 3; BODY; } break;                    \
-        case 8 * 8 + 1: { constexpr int GG = 8, NN = 1; BODY; } break;                    \
-        case 8 * 8 + 2: { constexpr int GG = 8, NN = 2; BODY; } break;                    \
-        case 8 * 8 + 3: { constexpr int GG = 8, NN = 3; BODY; } break;                    \
-        case 16 * 8 + 1: { constexpr int GG = 16, NN = 1; BODY; } break;                  \
-        case 16 * 8 + 2: { constexpr int GG = 16, NN = 2; BODY; } break;                  \
-        case 32 * 8 + 1: { constexpr int GG = 32, NN = 1; BODY; } break;                  \
-        case 32 * 8 + 2: { constexpr int GG = 32, NN = 2; BODY; } break;                  \
-        default:                                                                          \
-            set_error("no compiled tile shape G=%d NT=%d", (cfg).G, (cfg).NT);            \
-            return CSC_E_UNSUPPORTED;                                                     \
-    }
+    do {                                                                                  \
+        switch ((cfg).G * 8 + (cfg).NT) {                                                     \
+            case 2 * 8 + 1: { constexpr int GG = 2, NN = 1; BODY; } break;                    \
+            case 2 * 8 + 2: { constexpr int GG = 2, NN = 2; BODY; } break;                    \
+            case 2 * 8 + 3: { constexpr int GG = 2, NN = 3; BODY; } break;                    \
+            case 4 * 8 + 1: { constexpr int GG = 4, NN = 1; BODY; } break;                    \
+            case 4 * 8 + 2: { constexpr int GG = 4, NN = 2; BODY; } break;                    \
+            case 4 * 8 + 3: { constexpr int GG = 4, NN = 3; BODY; } break;                    \
+            case 8 * 8 + 1: { constexpr int GG = 8, NN = 1; BODY; } break;                    \
+            case 8 * 8 + 2: { constexpr int GG = 8, NN = 2; BODY; } break;                    \
+            case 8 * 8 + 3: { constexpr int GG = 8, NN = 3; BODY; } break;                    \
+            case 16 * 8 + 1: { constexpr int GG = 16, NN = 1; BODY; } break;                  \
+            case 16 * 8 + 2: { constexpr int GG = 16, NN = 2; BODY; } break;                  \
+            case 32 * 8 + 1: { constexpr int GG = 32, NN = 1; BODY; } break;                  \
+            case 32 * 8 + 2: { constexpr int GG = 32, NN = 2; BODY; } break;                  \
+            default:                                                                          \
+                set_error("no compiled tile shape G=%d NT=%d", (cfg).G, (cfg).NT);            \
+                return CSC_E_UNSUPPORTED;                                                     \
+        }                                                                               \
+    } while (0)
 
 template <typename T>
 static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur, T* xpn,
@@ -810,7 +813,7 @@ static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur
     if (ws <= kKeepL2Fraction * (double)g->l2_bytes) mode |= 4;
     const int32_t* part = nullptr;
     CSC_TRY(get_partition(g, cfg.P, &part));
-    const int smem = staged_smem(g, cfg.P);  // the CTA's CSR slice (stage_csr)
+    const int smem = cfg.staged ? staged_smem(g, cfg.P) : 0;  // the CTA's CSR slice (stage_csr)
     CSC_TRY(check_staged_smem(smem));
     const dim3 grid(cfg.P, cfg.tiles);
     // algorithmic bytes of one order: CSR + row factors, Z_j gathered once, Z_{j-1} read and
@@ -831,10 +834,16 @@ static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur
         return CSC_OK;
     };
     auto light = [&](cudaStream_t st) -> csc_status {
-        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", bytes, st,
-                                          cheb_step_kernel<T, GG, NN><<<grid, cfg.threads, smem, st>>>(
-                                              g->lrp, g->lci, idg, sqd, xcur, xpn, Y, g->perm, part, ncols, ld,
-                                              (A)c0, (A)cn, mode, tab)));
+        if (cfg.staged)
+            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", bytes, st,
+                                              cheb_step_kernel<T, GG, NN, true><<<grid, cfg.threads, smem, st>>>(
+                                                  g->row_ptr, g->col_idx, g->lrp, g->lci, idg, sqd, xcur, xpn, Y,
+                                                  g->perm, part, ncols, ld, (A)c0, (A)cn, mode, tab)));
+        else
+            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", bytes, st,
+                                              cheb_step_kernel<T, GG, NN, false><<<grid, cfg.threads, 0, st>>>(
+                                                  g->row_ptr, g->col_idx, g->lrp, g->lci, idg, sqd, xcur, xpn, Y,
+                                                  g->perm, part, ncols, ld, (A)c0, (A)cn, mode, tab)));
         return CSC_OK;
     };
     return fork_join(g, s, g->n_heavy > 0, heavy, light);
@@ -860,7 +869,7 @@ static csc_status launch_clenshaw_step(Graph* g, const LaunchCfg& cfg, const T* 
     if (ws <= kKeepL2Fraction * (double)g->l2_bytes) mode |= 4;
     const int32_t* part = nullptr;
     CSC_TRY(get_partition(g, cfg.P, &part));
-    const int smem = staged_smem(g, cfg.P);  // the CTA's CSR slice (stage_csr)
+    const int smem = cfg.staged ? staged_smem(g, cfg.P) : 0;  // the CTA's CSR slice (stage_csr)
     CSC_TRY(check_staged_smem(smem));
     const dim3 grid(cfg.P, cfg.tiles);
     // algorithmic bytes of one order: CSR + row factors, B_{j+1} gathered once, B_{j+2} read
@@ -881,17 +890,27 @@ static csc_status launch_clenshaw_step(Graph* g, const LaunchCfg& cfg, const T* 
         return CSC_OK;
     };
     auto light = [&](cudaStream_t st) -> csc_status {
-        if (last) {
-            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * (1.0 - heavy_frac), st,
-                                              clenshaw_step_kernel<T, GG, NN, true><<<grid, cfg.threads, smem, st>>>(
-                                                  g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm, part, ncols,
-                                                  ld, (A)cj, mode, tab, rs)));
-        } else {
-            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", all_bytes * (1.0 - heavy_frac), st,
-                                              clenshaw_step_kernel<T, GG, NN, false><<<grid, cfg.threads, smem, st>>>(
-                                                  g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm, part, ncols,
-                                                  ld, (A)cj, mode, tab, rs)));
-        }
+        const double lb = all_bytes * (1.0 - heavy_frac);
+        if (last && cfg.staged)
+            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", lb, st,
+                                              clenshaw_step_kernel<T, GG, NN, true, true><<<grid, cfg.threads, smem, st>>>(
+                                                  g->row_ptr, g->col_idx, g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm,
+                                                  part, ncols, ld, (A)cj, mode, tab, rs)));
+        else if (last)
+            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", lb, st,
+                                              clenshaw_step_kernel<T, GG, NN, true, false><<<grid, cfg.threads, 0, st>>>(
+                                                  g->row_ptr, g->col_idx, g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm,
+                                                  part, ncols, ld, (A)cj, mode, tab, rs)));
+        else if (cfg.staged)
+            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", lb, st,
+                                              clenshaw_step_kernel<T, GG, NN, false, true><<<grid, cfg.threads, smem, st>>>(
+                                                  g->row_ptr, g->col_idx, g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm,
+                                                  part, ncols, ld, (A)cj, mode, tab, rs)));
+        else
+            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", lb, st,
+                                              clenshaw_step_kernel<T, GG, NN, false, false><<<grid, cfg.threads, 0, st>>>(
+                                                  g->row_ptr, g->col_idx, g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm,
+                                                  part, ncols, ld, (A)cj, mode, tab, rs)));
         return CSC_OK;
     };
     return fork_join(g, s, g->n_heavy > 0, heavy, light);
@@ -903,7 +922,7 @@ static csc_status launch_mom_step(Graph* g, const LaunchCfg& cfg, const T* xcur,
     const double bytes = 4.0 * g->nnz + 8.0 * g->N + 4.0 + (first ? 2.0 : 3.0) * (double)g->N * ncols * sizeof(T);
     const int32_t* part = nullptr;
     CSC_TRY(get_partition(g, cfg.P, &part));
-    const int smem = staged_smem(g, cfg.P);  // the CTA's CSR slice (stage_csr)
+    const int smem = cfg.staged ? staged_smem(g, cfg.P) : 0;  // the CTA's CSR slice (stage_csr)
     CSC_TRY(check_staged_smem(smem));
     const dim3 grid(cfg.P, cfg.tiles);
     // heavy rows' partial sums go to the slots after the row-range blocks'
@@ -916,10 +935,16 @@ static csc_status launch_mom_step(Graph* g, const LaunchCfg& cfg, const T* xcur,
         return CSC_OK;
     };
     auto light = [&](cudaStream_t st) -> csc_status {
-        CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("mom_step", bytes, st,
-                                          mom_step_kernel<T, GG, NN><<<grid, cfg.threads, smem, st>>>(
-                                              g->lrp, g->lci, g->invdeg, g->deg, xcur, xpn, part, ncols, ld,
-                                              first, partials)));
+        if (cfg.staged)
+            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("mom_step", bytes, st,
+                                              mom_step_kernel<T, GG, NN, true><<<grid, cfg.threads, smem, st>>>(
+                                                  g->row_ptr, g->col_idx, g->lrp, g->lci, g->invdeg, g->deg, xcur,
+                                                  xpn, part, ncols, ld, first, partials)));
+        else
+            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("mom_step", bytes, st,
+                                              mom_step_kernel<T, GG, NN, false><<<grid, cfg.threads, 0, st>>>(
+                                                  g->row_ptr, g->col_idx, g->lrp, g->lci, g->invdeg, g->deg, xcur,
+                                                  xpn, part, ncols, ld, first, partials)));
         return CSC_OK;
     };
     return fork_join(g, s, g->n_heavy > 0, heavy, light);
@@ -942,9 +967,9 @@ static int kernel_occupancy(int kind, const TileShape& sh, int threads) {
     auto f = [&](auto kptr) { occ = occupancy(kptr, threads); };
 #define CSC_OCC_CASE(GG, NN)                                                             \
     if (sh.G == GG && sh.NT == NN) {                                                     \
-        if (kind == KK_CHEB) f(cheb_step_kernel<T, GG, NN>);                             \
-        else if (kind == KK_CLEN) f(clenshaw_step_kernel<T, GG, NN, false>);             \
-        else if constexpr (sizeof(T) <= 4) f(mom_step_kernel<T, GG, NN>);               \
+        if (kind == KK_CHEB) f(cheb_step_kernel<T, GG, NN, true>);                       \
+        else if (kind == KK_CLEN) f(clenshaw_step_kernel<T, GG, NN, false, true>);       \
+        else if constexpr (sizeof(T) <= 4) f(mom_step_kernel<T, GG, NN, true>);         \
     }
     CSC_OCC_CASE(2, 1) CSC_OCC_CASE(2, 2) CSC_OCC_CASE(2, 3) CSC_OCC_CASE(4, 1) CSC_OCC_CASE(4, 2)
     CSC_OCC_CASE(4, 3) CSC_OCC_CASE(8, 1) CSC_OCC_CASE(8, 2) CSC_OCC_CASE(8, 3) CSC_OCC_CASE(16, 1)
@@ -995,6 +1020,10 @@ static std::vector<LaunchCfg> candidates(Graph* g, int kind, int nv) {
                 if (!out.empty() && out.back().G == c.G && out.back().NT == c.NT && out.back().threads == th &&
                     out.back().P == c.P)
                     continue;
+                // both index sources (sweep_rows): the staged slice, and global loads
+                c.staged = 1;
+                out.push_back(c);
+                c.staged = 0;
                 out.push_back(c);
             }
         }

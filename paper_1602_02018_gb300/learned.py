@@ -1,10 +1,16 @@
 """Learned lambda_k bracket: training data, training and use.
 
-Every computation runs in libcsc: the features and the eigencount moments
+Every step on a graph runs in libcsc: the features and the eigencount moments
 (csc_bracket_features, csc_kpm_moments), the target crossings
 (csc_bracket_target), the network's training and inference (csc_mlp_*), and
-the bracketed dichotomy (csc_estimate_lambda_k_learned).  This module only
-assembles arrays and keeps the standardisation constants.
+the bracketed dichotomy (csc_estimate_lambda_k_learned, which also applies the
+input standardisation and the output transform at inference).  What this module
+computes on the host is pre- and post-processing of the training set of this
+add-on, which the paper does not have: the mean and standard deviation of the
+training features and targets (the constants handed to the library), the
+conversion of target brackets to (centre, ln half-width), the standardised
+training arrays, and the calibration of the half-width factor ``widen`` by a
+search over held-back samples.
 
 Readings (the paper has no learned component): the regression target of a
 graph is (centre, ln half-width) of the interval where its eigencount, from

@@ -171,7 +171,8 @@ SHAPES = [(2, 1), (2, 2), (2, 3), (4, 1), (4, 2), (4, 3), (8, 1), (8, 2), (8, 3)
 
 @pytest.mark.parametrize("G,NT", SHAPES)
 @pytest.mark.parametrize("threads", [256, 512])
-def test_every_compiled_shape_f32(G, NT, threads):
+@pytest.mark.parametrize("global_index", [0, 1])
+def test_every_compiled_shape_f32(G, NT, threads, global_index):
     """Each compiled (lanes per row, vectors per lane) pair and CTA size gives the oracle's
     filter (ragged row ranges: P = 37)."""
     g = GRAPHS[6][1]
@@ -180,7 +181,7 @@ def test_every_compiled_shape_f32(G, NT, threads):
     r = ci.gaussian_block(g.n, d, d_pad, seed=3)
     ref = _oracle_filter(g, r.astype(np.float64), lam, m)
     with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM) as h:
-        csc.csc_graph_pin_shape(h, "cheb_step", 4, d_pad, G, NT, threads, 37, tiles)
+        csc.csc_graph_pin_shape(h, "cheb_step", 4, d_pad, G, NT, threads, 37, tiles, global_index)
         y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, R_in=torch.from_numpy(r).cuda(), flags=0).cpu().numpy()
     assert rel(y, ref) <= 1e-5
 
@@ -209,9 +210,9 @@ def test_pin_shape_rejects_bad_shapes():
         with pytest.raises(csc.CscError):
             csc.csc_graph_pin_shape(h, "cheb_step", 4, 48, 4, 1, 256, 10, 1, 0)   # tiles
         with pytest.raises(csc.CscError):
-            csc.csc_graph_pin_shape(h, "cg", 4, 200, 32, 2, 256, 10, 1, 50)       # reserved entry not 0
+            csc.csc_graph_pin_shape(h, "cg", 4, 200, 32, 2, 256, 10, 1, -1)       # index source 0 or 1
         with pytest.raises(csc.CscError):
-            csc.csc_graph_pin_shape(h, "cheb_step", 4, 48, 4, 3, 256, 10, 1, 300)  # reserved entry not 0
+            csc.csc_graph_pin_shape(h, "cheb_step", 4, 48, 4, 3, 256, 10, 1, 2)    # index source 0 or 1
 
 
 def test_graph_replay_matches_eager_launches():
@@ -270,7 +271,8 @@ def test_clenshaw_regenerated_signals_match_oracle(n, d, d_pad, seed, m):
 
 @pytest.mark.parametrize("G,NT", SHAPES)
 @pytest.mark.parametrize("threads", [256, 512])
-def test_clenshaw_every_compiled_shape(G, NT, threads):
+@pytest.mark.parametrize("global_index", [0, 1])
+def test_clenshaw_every_compiled_shape(G, NT, threads, global_index):
     """Each (lanes, vectors) pair and CTA size; rows normalised in the last order when one
     tile holds a row, by the separate pass otherwise."""
     g = GRAPHS[6][1]
@@ -279,7 +281,7 @@ def test_clenshaw_every_compiled_shape(G, NT, threads):
     r = ci.gaussian_block(g.n, d, d_pad, seed=3)
     ref = _oracle_filter(g, r.astype(np.float64), lam, m, normalize=True)
     with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM) as h:
-        csc.csc_graph_pin_shape(h, "clenshaw", 4, d_pad, G, NT, threads, 37, tiles, 0)
+        csc.csc_graph_pin_shape(h, "clenshaw", 4, d_pad, G, NT, threads, 37, tiles, global_index)
         y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, R_in=torch.from_numpy(r).cuda(),
                                           flags=csc.CLENSHAW | csc.NORMALIZE_ROWS).cpu().numpy()
     assert rel(y, ref) <= 1e-5

@@ -82,6 +82,7 @@ def test_chung_lu_1e6_sampled_columns(c3, model_err, storage, name):
     for i in range(len(COLS)):
         err = rel(yc[:, i], ref[:, i])
         bound = 1.5 * model_err[name][i]
+        print(f"{name} column {COLS[i]}: GPU {err:.3g}, storage model {model_err[name][i]:.3g}")
         assert err <= bound, f"column {COLS[i]}: relative error {err:.3g} above 1.5 x the {name} storage model's"
         if name == "f32":
             assert err <= FP32_TARGET, f"column {COLS[i]}: relative error {err:.3g}"
@@ -96,4 +97,5 @@ def test_chung_lu_1e6_sampled_normalised_rows(c3):
                                           flags=csc.CLENSHAW | csc.NORMALIZE_ROWS)
         fr = f[torch.from_numpy(rows).cuda()].double().cpu().numpy()
     err = np.linalg.norm(fr[:, :D] - ref_f, axis=1)
+    print(f"normalised rows {rows.tolist()}: errors {np.array2string(err, precision=3)}")
     assert np.all(err <= 1.5 * FP32_MODEL_ROW_MAX), f"per-row errors {err}"
