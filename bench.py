@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--filter", default="clenshaw", choices=["forward", "clenshaw"],
                     help="evaluate the Chebyshev filter by Clenshaw's backward recurrence (default, same Y "
                          "with fewer bytes per order) or by the forward three-term recurrence")
+    ap.add_argument("--order", default="rcm+degree", choices=["rcm+degree", "rcm", "degree", "none"],
+                    help="internal node order of the power-law workload (CSC_RCM, CSC_DEGREE_ORDER)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -95,6 +97,17 @@ def make_graph(w: dict, seed: int):
     if w["kind"] == "sbm":
         return ci.sbm(w["n"], w["k"], s=w["s"], seed=seed)
     return ci.chung_lu(w["n"], exponent=w["exponent"], mean=w["mean"], seed=seed)
+
+
+def graph_flags(w: dict, args) -> int:
+    """Internal node order of the power-law workload: RCM, then by decreasing degree (RCM order
+    among rows of equal degree), unless --order says otherwise; the SBMs keep their order."""
+    import paper_1602_02018_gb300 as csc
+
+    if w["kind"] != "chung_lu":
+        return 0
+    return {"rcm": csc.RCM, "rcm+degree": csc.RCM | csc.DEGREE_ORDER, "degree": csc.DEGREE_ORDER,
+            "none": 0}[args.order]
 
 
 def sizes(w: dict):
@@ -170,8 +183,8 @@ def peaks():
 
 
 def recorded_traffic(workload: str, kernel_class: str, shape: dict | None):
-    """DRAM traffic per launch from the committed ncu summary of this workload, kernel class and
-    launch shape, if the kernel source is unchanged since the capture."""
+    """DRAM traffic per unit from the committed ncu summary of this workload, kernel class and
+    launch shape, if the kernel sources are unchanged since the capture."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
@@ -181,12 +194,15 @@ def recorded_traffic(workload: str, kernel_class: str, shape: dict | None):
         want = rec.get("shape")
         if want and shape and any(shape.get(k) != v for k, v in want.items()):
             return None, f"ncu capture was of shape {want}, this run tuned {shape}"
-        src = os.path.join(ROOT, rec["source"])
-        with open(src, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
-        if sha != rec["sha256"]:
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != rec["sha256"]:
             return None, "kernel source changed since the ncu capture"
-        return float(rec["bytes_per_launch"]), rec.get("note")
+        if rec.get("bytes_per_unit") is None:
+            return None, rec.get("note")
+        return float(rec["bytes_per_unit"]), rec.get("note")
     except (OSError, KeyError, ValueError):
         return None, None
 
@@ -338,7 +354,7 @@ def run_ours(args, w, rank, world, local_rank):
     g = make_graph(w, args.seed + rank)
     work = float(m) * g.nnz * d
     stream = torch.cuda.current_stream()
-    flags = csc.RCM if w["kind"] == "chung_lu" else 0  # power-law workload: RCM-reordered CSR
+    flags = graph_flags(w, args)
     h = csc.csc_graph_create(g.row_ptr, g.col_idx, flags)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
@@ -429,7 +445,8 @@ def run_ours(args, w, rank, world, local_rank):
         per_unit = c["bytes"] / n_units
         unit_ms = c["ms"] / n_units
         achieved = per_unit / (unit_ms / 1e3) / 1e9
-        shp = next((dict(G=x["G"], NT=x["NT"], threads=x["threads"], P=x["P"], tiles=x["tiles"]) for x in tuned
+        shp = next((dict(G=x["G"], NT=x["NT"], threads=x["threads"], P=x["P"], tiles=x["tiles"],
+                     global_index=x["global_index"]) for x in tuned
                     if x["kernel"] == shape_kind.get(name)), None)
         traffic, note = recorded_traffic(args.workload, name, shp)
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -483,7 +500,7 @@ def run_ours(args, w, rank, world, local_rank):
         d2h = g.n * 4
         e2e = {"value": world * work / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "csc_seconds": t_e2e, "steps": e2e_steps, "warmup": 1,
-               "what": "host CSR -> csc_graph_create (upload, degrees, RCM) -> csc_cluster -> labels to pinned host"}
+               "what": "host CSR -> csc_graph_create (upload, degrees, reordering) -> csc_cluster -> labels to pinned host"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -512,6 +529,7 @@ def run_ours(args, w, rank, world, local_rank):
                        "value_basis": "m*nnz*d / device time of the filter stage of each timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "filter": args.filter, "interp": args.interp, "sampling": args.sampling,
+                       "order": args.order if w["kind"] == "chung_lu" else "input",
                        "interp_degree": args.interp_degree or m},
             "csc_seconds": ms_step / 1e3,
             "filter_ms": ms_filter,
@@ -548,11 +566,11 @@ def run_precision(args, w):
     sz = sizes(w)
     d, d_pad, m, k = sz["d"], sz["d_pad"], w["m"], w["k"]
     g = make_graph(w, args.seed)
-    flags = csc.RCM if w["kind"] == "chung_lu" else 0
+    flags = graph_flags(w, args)
     h = csc.csc_graph_create(g.row_ptr, g.col_idx, flags)
     lam = csc.csc_estimate_lambda_k(h, k, m, 0, args.seed).lam
     out = {"workload": args.workload, "N": g.n, "nnz": g.nnz, "k": k, "m": m, "d": d, "d_pad": d_pad,
-           "lambda_k": lam, "rcm": bool(flags), "storage": {}}
+           "lambda_k": lam, "order": args.order if w["kind"] == "chung_lu" else "input", "storage": {}}
     out["filter"] = args.filter
     fflags = csc.NORMALIZE_ROWS | (csc.CLENSHAW if args.filter == "clenshaw" else 0)
     ys = {}

@@ -74,13 +74,13 @@ CASES = [
 
 
 @pytest.mark.parametrize("gi,d,d_pad,m,lam", CASES)
-@pytest.mark.parametrize("rcm", [False, True])
+@pytest.mark.parametrize("rcm", [0, 1, 8, 9])  # graph flags: none, RCM, degree order, both
 @pytest.mark.parametrize("normalize", [False, True])
 def test_filter_f32_matches_oracle(gi, d, d_pad, m, lam, rcm, normalize):
     g = GRAPHS[gi][1]
     r = ci.gaussian_block(g.n, d, d_pad, seed=11)
     ref = _oracle_filter(g, r.astype(np.float64), lam, m, normalize=normalize)
-    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM if rcm else 0) as h:
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, rcm) as h:
         y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, R_in=torch.from_numpy(r).cuda(),
                                           flags=csc.NORMALIZE_ROWS if normalize else 0).cpu().numpy()
     assert y.shape == (g.n, d_pad)
@@ -241,7 +241,7 @@ def test_graph_replay_matches_eager_launches():
 # ----------------------------------------------------- Clenshaw evaluation
 
 @pytest.mark.parametrize("gi,d,d_pad,m,lam", CASES)
-@pytest.mark.parametrize("rcm", [False, True])
+@pytest.mark.parametrize("rcm", [0, 1, 8, 9])  # graph flags: none, RCM, degree order, both
 @pytest.mark.parametrize("normalize", [False, True])
 def test_clenshaw_f32_matches_oracle(gi, d, d_pad, m, lam, rcm, normalize):
     """Clenshaw's backward recurrence gives the oracle's forward-recurrence features."""
@@ -249,7 +249,7 @@ def test_clenshaw_f32_matches_oracle(gi, d, d_pad, m, lam, rcm, normalize):
     r = ci.gaussian_block(g.n, d, d_pad, seed=11)
     ref = _oracle_filter(g, r.astype(np.float64), lam, m, normalize=normalize)
     flags = csc.CLENSHAW | (csc.NORMALIZE_ROWS if normalize else 0)
-    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM if rcm else 0) as h:
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, rcm) as h:
         y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, R_in=torch.from_numpy(r).cuda(),
                                           flags=flags).cpu().numpy()
     assert np.all(y[:, d:] == 0)

@@ -1,6 +1,7 @@
 """The filter at the power-law workload's full size (Chung-Lu N = 1e6, degree exponent
-2.1, mean degree 6, RCM-reordered CSR, m = 100, d = 56, Clenshaw form, autotuned launch
-shape as bench.py runs it), checked on sampled outputs the FP64 oracle computes one by one:
+2.1, mean degree 6, CSR reordered by RCM then by decreasing degree, m = 100, d = 56,
+Clenshaw form, autotuned launch shape as bench.py runs it), checked on sampled outputs the
+FP64 oracle computes one by one:
 
 * columns: the columns of Y = h~(L) R are independent, so the oracle filters a few sampled
   columns alone (Sec. 2.1 recurrence);
@@ -41,6 +42,7 @@ FP32_TARGET = 1e-5
 # largest per-row error of the normalised features in the FP32 storage model over all
 # 1e6 rows and 56 columns (same graph, signals and cut-off)
 FP32_MODEL_ROW_MAX = 2.2e-4
+ORDER = csc.RCM | csc.DEGREE_ORDER
 
 
 @pytest.fixture(scope="module")
@@ -75,7 +77,7 @@ def model_err(c3):
 @pytest.mark.parametrize("storage,name", [(0, "f32"), (1, "bf16")])  # signal block stored in fp32 / bf16
 def test_chung_lu_1e6_sampled_columns(c3, model_err, storage, name):
     g, r, ref, _, _ = c3
-    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM) as h:
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, ORDER) as h:
         y = csc.csc_filter_random_signals(h, LAM, M, D, D, storage=storage, R_in=torch.from_numpy(r).cuda(),
                                           flags=csc.CLENSHAW)
         yc = y[:, COLS].double().cpu().numpy()
@@ -92,7 +94,7 @@ def test_chung_lu_1e6_sampled_columns(c3, model_err, storage, name):
 
 def test_chung_lu_1e6_sampled_normalised_rows(c3):
     g, r, _, rows, ref_f = c3
-    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM) as h:
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, ORDER) as h:
         f = csc.csc_filter_random_signals(h, LAM, M, D, D, R_in=torch.from_numpy(r).cuda(),
                                           flags=csc.CLENSHAW | csc.NORMALIZE_ROWS)
         fr = f[torch.from_numpy(rows).cuda()].double().cpu().numpy()

@@ -56,13 +56,13 @@ def _oracle_filter(g, r64, lam, m):
 
 
 @pytest.mark.parametrize("gname", ["hub", "power_law"])
-@pytest.mark.parametrize("rcm", [False, True])
+@pytest.mark.parametrize("rcm", [0, 1, 8, 9])  # graph flags: none, RCM, degree order, both
 def test_filter_f32_heavy(gname, rcm):
     g = HUB if gname == "hub" else POWER_LAW
     d, d_pad, m, lam = 21, 24, 40, 0.3
     r = ci.gaussian_block(g.n, d, d_pad, seed=9)
     ref = _oracle_filter(g, r.astype(np.float64), lam, m)
-    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM if rcm else 0) as h:
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, rcm) as h:
         y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, R_in=torch.from_numpy(r).cuda(), flags=0).cpu().numpy()
     assert rel(y, ref) <= 1e-5
 

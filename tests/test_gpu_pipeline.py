@@ -31,11 +31,11 @@ def _lib():
 
 
 @pytest.mark.parametrize("seed", [0, 1])
-@pytest.mark.parametrize("rcm", [False, True])
+@pytest.mark.parametrize("rcm", [0, 1, 8, 9])  # graph flags: none, RCM, degree order, both
 def test_csc_sbm_1e3_matches_oracle(seed, rcm):
     g = ci.sbm(1000, 20, seed=seed)
     ref = opipe.csc(g.row_ptr, g.col_idx, 20, seed=seed)
-    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM if rcm else 0) as h:
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, rcm) as h:
         labels, info = csc.csc_cluster(h, 20, seed=seed)
     lab = labels.cpu().numpy()
     a_gpu = oari.ari(lab, g.labels)

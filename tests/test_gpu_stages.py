@@ -32,6 +32,7 @@ def _lib():
 # ------------------------------------------------------------------ moments
 
 @pytest.mark.parametrize("n,k,n_mom,n_v,rcm", [(1000, 20, 51, 14, False), (1000, 20, 51, 14, True),
+                                               (1000, 20, 51, 14, 9),
                                                (777, 7, 64, 8, False), (2000, 10, 2, 3, False),
                                                (300, 6, 1, 5, False), (300, 6, 12, 17, True)])
 def test_moments_match_oracle(n, k, n_mom, n_v, rcm):
@@ -39,7 +40,7 @@ def test_moments_match_oracle(n, k, n_mom, n_v, rcm):
     s = olap.normalized_adjacency(g.row_ptr, g.col_idx)
     probes = och.probe_signals(g.n, n_v, n_v, seed=17)
     ref = och.moments(s, probes, max(n_mom - 1, 0))[:n_mom]
-    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM if rcm else 0) as h:
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, int(rcm)) as h:
         mu = csc.csc_kpm_moments(h, n_mom, n_v, seed=17)
     assert np.max(np.abs(mu - ref)) <= 2e-5 * abs(ref[0])
 
@@ -136,6 +137,7 @@ def test_kmeans_separated_blobs_and_edge_cases():
 # ------------------------------------------------------------ interpolation
 
 @pytest.mark.parametrize("n_nodes,k,n_s,power,rcm", [(1000, 20, 120, 4, False), (1000, 20, 120, 4, True),
+                                                     (1000, 20, 120, 4, 9),
                                                    (600, 6, 40, 2, False), (500, 5, 30, 1, False)])
 def test_interpolation_matches_oracle(n_nodes, k, n_s, power, rcm):
     g = ci.sbm(n_nodes, k, seed=2)
@@ -143,7 +145,7 @@ def test_interpolation_matches_oracle(n_nodes, k, n_s, power, rcm):
     om = osamp.sample(g.n, n_s, 2)
     lab = g.labels[om].astype(np.int32)
     x_ref, _, _ = ointerp.interpolate(lap, om, lab, k, 1e-3, power, tol=1e-11)
-    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM if rcm else 0) as h:
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, int(rcm)) as h:
         labels, fz, info = csc.csc_interpolate(h, torch.from_numpy(om).cuda(), torch.from_numpy(lab).cuda(), k,
                                                power, 1e-3, 1e-7, 5000, fuzzy=True)
     assert info.converged and info.max_rel_residual <= 1e-6
@@ -256,7 +258,7 @@ def test_interpolation_highpass_matches_oracle(n_nodes, k, n_s, lam, m, rcm):
     g = ci.sbm(n_nodes, k, seed=2)
     om = osamp.sample(g.n, n_s, 2)
     lab = g.labels[om].astype(np.int32)
-    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM if rcm else 0) as h:
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, int(rcm)) as h:
         labels, fz, info = csc.csc_interpolate_highpass(h, torch.from_numpy(om).cuda(), torch.from_numpy(lab).cuda(),
                                                         k, lam, m, 1e-3, 1e-7, 5000, fuzzy=True)
     assert info.converged and info.max_rel_residual <= 1e-6
