@@ -603,15 +603,21 @@ def run_precision(args, w):
         out["storage"][name]["rel_err_vs_f64"] = float(torch.linalg.norm(ys[name] - ys["f64"]) /
                                                        torch.linalg.norm(ys["f64"]))
     labs = {}
-    for name, st in (("f32", csc.F32), ("bf16", csc.BF16)):
+    runs = (("f64", csc.F64, args.seed), ("f32", csc.F32, args.seed), ("bf16", csc.BF16, args.seed),
+            ("f32_seed+1", csc.F32, args.seed + 1))
+    for name, st, seed in runs:
         t0 = time.perf_counter()
-        lab, info = csc.csc_cluster(h, k, m=m, d=d, d_pad=d_pad, storage=st, seed=args.seed,
+        lab, info = csc.csc_cluster(h, k, m=m, d=d, d_pad=d_pad, storage=st, seed=seed,
                                     flags=csc.CLENSHAW if args.filter == "clenshaw" else 0)
         torch.cuda.synchronize()
-        out["storage"][name]["csc_seconds"] = time.perf_counter() - t0
+        out["storage"].setdefault(name, {})["csc_seconds"] = time.perf_counter() - t0
         out["storage"][name]["cg_iters"] = info.cg.iters
         labs[name] = lab.cpu().numpy()
     out["ari_bf16_vs_f32_labels"] = adjusted_rand(labs["bf16"], labs["f32"])
+    out["ari_f32_vs_f64_labels"] = adjusted_rand(labs["f32"], labs["f64"])
+    out["ari_bf16_vs_f64_labels"] = adjusted_rand(labs["bf16"], labs["f64"])
+    # the method's own randomness: the same storage with another signal block and sample
+    out["ari_f32_seed_vs_seed+1_labels"] = adjusted_rand(labs["f32"], labs["f32_seed+1"])
     if g.labels is not None:
         out["ari_vs_planted"] = {name: adjusted_rand(lab, g.labels) for name, lab in labs.items()}
     out["autotuned_shapes"] = csc.csc_graph_tuned_shapes(h)

@@ -697,6 +697,29 @@ __global__ void label_argmax_kernel(const float* __restrict__ x, const double* _
     }
 }
 
+// Column compaction of the CG blocks: in each of a, b, c (N x ld, row-major) the
+// columns [0, kw) of every row become old[src[s]] at slot s.  One warp per row copies
+// the row's kw entries to its slice of shared memory before writing them back, so the
+// permutation is done in place.
+__global__ void permute_columns_kernel(float* __restrict__ a, float* __restrict__ b, float* __restrict__ c,
+                                       const int32_t* __restrict__ src, int kw, int64_t ld, int32_t N) {
+    extern __shared__ float s_row[];
+    const int lane = threadIdx.x & 31;
+    float* buf = s_row + (threadIdx.x >> 5) * kw;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < N; row += nw) {
+        float* blocks[3] = {a, b, c};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            float* v = blocks[q] + row * ld;
+            for (int j = lane; j < kw; j += 32) buf[j] = v[j];
+            __syncwarp();
+            for (int j = lane; j < kw; j += 32) v[j] = buf[src[j]];
+            __syncwarp();
+        }
+    }
+}
+
 // ------------------------------------------------------------- dispatch
 static const int kCgShapes[][2] = {{2, 1}, {4, 1}, {8, 1}, {16, 1}, {16, 2}, {32, 1}, {32, 2}};
 static const int kCgThreadChoices[] = {256, 512};
@@ -844,6 +867,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const int max_slices = std::max(1, ceil_div(max_p + (int)g->n_heavy, kSliceSlots));
     const size_t o_lvl2 = take((size_t)nchunks * max_slices * 2 * 32 * 8);
     const size_t o_cnt = take((size_t)nchunks * 4);
+    const size_t o_src = take((size_t)ld * 4);  // column permutation of a compaction
     void* base = nullptr;
     CSC_TRY(ws_get(g, WS_CG, off, &base));
     char* b = (char*)base;
@@ -873,6 +897,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     int* bad = st.n_active + 1;
     double* lvl2 = (double*)(b + o_lvl2);
     int* red_cnt = (int*)(b + o_cnt);
+    int32_t* d_src = (int32_t*)(b + o_src);
     int32_t* d_gk = nullptr;
     const int32_t* gid = nullptr;
     CgBatch bt, bt_all;  // bt also skips finished graphs; bt_all only narrows the columns
@@ -1010,15 +1035,15 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     };
 
     // algorithmic bytes per launch of each CG kernel (fp32 N x ld blocks)
-    const double blkb = (double)N * ld * 4.0;
+    double blkb = (double)N * ld * 4.0;
     const double csr_b = 4.0 * g->nnz + 4.0 * (N + 1) + 4.0 * N;
-    const double scal_b = 8.0 * P * ld;
-    const double scal_ax = 8.0 * PH * ld;
+    double scal_b = 8.0 * P * ld;
+    double scal_ax = 8.0 * PH * ld;
     // share of the sparse bytes that falls on heavy rows (launched separately)
     const double heavy_frac = g->nnz > 0 ? (double)(g->nnz - g->h_light.back()) / (double)g->nnz : 0.0;
     // reductions over P slots (updates, residual, norms) and P + H slots (<p, A p>)
-    const dim3 kb(ceil_div(k, 32), nseg, std::max(1, ceil_div(P, kSliceSlots)));
-    const dim3 kb_ax(ceil_div(k, 32), nseg, std::max(1, ceil_div(PH, kSliceSlots)));
+    dim3 kb(ceil_div(k, 32), nseg, std::max(1, ceil_div(P, kSliceSlots)));
+    dim3 kb_ax(ceil_div(k, 32), nseg, std::max(1, ceil_div(PH, kSliceSlots)));
     const dim3 rb(32, kReduceRows);
     CG_SWITCH(cfg, CSC_KLAUNCH("cg_update", blkb + 4.0 * N, s,
                                cg_update_kernel<G_, NT_><<<grid, th, 0, s>>>(x, r, p, Ap, nullptr, gid, pinv, rpart, ld,
@@ -1036,12 +1061,44 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                   "weight not finite and positive");
         return CSC_E_INVALID;
     }
+    // Column compaction (one graph, g = L^p): a column whose CG has converged keeps its x
+    // and leaves the iteration.  At a convergence check that finds at least 8 slots (or
+    // half of them) idle, the active columns move to the front slots (x, r, p permuted in
+    // place, their scalars on the host) and every kernel of the following iterations covers
+    // the first kw slots only, with a launch shape narrowed to that width; slot_col[s] is
+    // the column held in slot s.  Each column's arithmetic is unchanged by its slot.
+    const bool compact = !hp && nseg == 1 && ld <= 1024;
+    int kw = ld;          // slots the iterations cover
+    int kcols = k;        // columns the scalar kernels cover (slots past them are idle)
+    LaunchCfg wcfg = cfg; // launch shape of the iterations at width kw
+    dim3 wgrid = grid, whgrid = hgrid;
+    std::vector<int> slot_col(ld);
+    for (int j = 0; j < ld; ++j) slot_col[j] = j;
+    auto set_width = [&](int w) {
+        kw = w;
+        kcols = w < ld ? w : k;
+        wcfg = cfg;
+        const int nvw = ceil_div(w, 4);
+        if (2 * nvw <= cfg.G * cfg.NT) {  // the tuned tile is at least twice too wide: narrower groups
+            int G2 = 2;
+            while (G2 < nvw && G2 < 32) G2 *= 2;
+            wcfg.G = G2;
+            wcfg.NT = 1;
+        }
+        wcfg.tiles = ceil_div(nvw, wcfg.G * wcfg.NT);
+        wgrid = dim3(cfg.P, wcfg.tiles);
+        whgrid = dim3(H > 0 ? H : 1, wcfg.tiles);
+        blkb = (double)N * w * 4.0;
+        scal_b = 8.0 * P * w;
+        scal_ax = 8.0 * PH * w;
+        kb.x = kb_ax.x = ceil_div(kcols, 32);
+    };
     auto apply_A = [&](const float* in, const CgBatch& bb, cudaStream_t s) -> csc_status {
         if (hp) {
             CSC_TRY(poly_apply(g, op, in, t1, s));
-            CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", 4.0 * N + 3 * blkb + scal_b, s,
-                                       hp_ax_kernel<G_, NT_><<<grid, th, 0, s>>>(in, t1, mask, (float)gamma, Ap, rpart,
-                                                                                 ld, ld, part, bb)));
+            CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax", 4.0 * N + 3 * blkb + scal_b, s,
+                                       hp_ax_kernel<G_, NT_><<<wgrid, th, 0, s>>>(in, t1, mask, (float)gamma, Ap, rpart,
+                                                                                 kw, ld, part, bb)));
             return CSC_OK;
         }
         // t = L^(p-1) in, then Ap = mask*in + gamma * L t with <in, Ap> partials; each product's
@@ -1056,13 +1113,13 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
             const bool win = q == 0;
             auto heavy = [&](cudaStream_t st) -> csc_status {
                 if (win)
-                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_heavy", lb * heavy_frac, st,
-                                               lap_heavy_kernel<G_, NT_, true><<<hgrid, kHeavyThreads, 0, st>>>(
+                    CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_heavy", lb * heavy_frac, st,
+                                               lap_heavy_kernel<G_, NT_, true><<<whgrid, kHeavyThreads, 0, st>>>(
                                                    g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, g->heavy, ld,
                                                    ld, bb)));
                 else
-                    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_heavy", lb * heavy_frac, st,
-                                               lap_heavy_kernel<G_, NT_, false><<<hgrid, kHeavyThreads, 0, st>>>(
+                    CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_heavy", lb * heavy_frac, st,
+                                               lap_heavy_kernel<G_, NT_, false><<<whgrid, kHeavyThreads, 0, st>>>(
                                                    g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, g->heavy, ld,
                                                    ld, bb)));
                 return CSC_OK;
@@ -1070,14 +1127,14 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
             auto light = [&](cudaStream_t st) -> csc_status {
                 const double by = lb * (1.0 - heavy_frac);
 #define CSC_LAP(W, S)                                                                                        \
-    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap", by, st,                                                             \
-                               (lap_kernel<G_, NT_, W, S><<<grid, th, csmem, st>>>(g->row_ptr, g->col_idx,   \
+    CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap", by, st,                                                             \
+                               (lap_kernel<G_, NT_, W, S><<<wgrid, th, csmem, st>>>(g->row_ptr, g->col_idx,   \
                                                                                   g->lrp, g->lci, g->dinv,   \
                                                                                   g->invdeg, cur, o, rpart,  \
-                                                                                  ld, ld, bb))))
-                if (win && cfg.staged) CSC_LAP(true, true);
+                                                                                  kw, ld, bb))))
+                if (win && wcfg.staged) CSC_LAP(true, true);
                 else if (win) CSC_LAP(true, false);
-                else if (cfg.staged) CSC_LAP(false, true);
+                else if (wcfg.staged) CSC_LAP(false, true);
                 else CSC_LAP(false, false);
 #undef CSC_LAP
                 return CSC_OK;
@@ -1090,27 +1147,27 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         const bool win = g_power == 1;
         auto heavy = [&](cudaStream_t st) -> csc_status {
             if (win)
-                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax_heavy", ab * heavy_frac, st,
-                                           lap_ax_heavy_kernel<G_, NT_, true><<<hgrid, kHeavyThreads, 0, st>>>(
+                CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax_heavy", ab * heavy_frac, st,
+                                           lap_ax_heavy_kernel<G_, NT_, true><<<whgrid, kHeavyThreads, 0, st>>>(
                                                g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma,
-                                               Ap, g->heavy, ld, ld, part, P, PH, bb)));
+                                               Ap, g->heavy, kw, ld, part, P, PH, bb)));
             else
-                CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax_heavy", ab * heavy_frac, st,
-                                           lap_ax_heavy_kernel<G_, NT_, false><<<hgrid, kHeavyThreads, 0, st>>>(
+                CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax_heavy", ab * heavy_frac, st,
+                                           lap_ax_heavy_kernel<G_, NT_, false><<<whgrid, kHeavyThreads, 0, st>>>(
                                                g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma,
-                                               Ap, g->heavy, ld, ld, part, P, PH, bb)));
+                                               Ap, g->heavy, kw, ld, part, P, PH, bb)));
             return CSC_OK;
         };
         auto light = [&](cudaStream_t st) -> csc_status {
             const double by = ab * (1.0 - heavy_frac);
 #define CSC_LAPAX(W, S)                                                                                         \
-    CG_SWITCH(cfg, CSC_KLAUNCH("cg_lap_ax", by, st,                                                             \
-                               (lap_ax_kernel<G_, NT_, W, S><<<grid, th, csmem, st>>>(                          \
+    CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax", by, st,                                                             \
+                               (lap_ax_kernel<G_, NT_, W, S><<<wgrid, th, csmem, st>>>(                          \
                                    g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->sqdeg, cur, in, mask,    \
-                                   (float)gamma, Ap, rpart, ld, ld, part, PH, bb))))
-            if (win && cfg.staged) CSC_LAPAX(true, true);
+                                   (float)gamma, Ap, rpart, kw, ld, part, PH, bb))))
+            if (win && wcfg.staged) CSC_LAPAX(true, true);
             else if (win) CSC_LAPAX(true, false);
-            else if (cfg.staged) CSC_LAPAX(false, true);
+            else if (wcfg.staged) CSC_LAPAX(false, true);
             else CSC_LAPAX(false, false);
 #undef CSC_LAPAX
             return CSC_OK;
@@ -1123,18 +1180,18 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         for (int q = 0; q < count; ++q) {
             CSC_TRY(apply_A(p, bt, s));
             CSC_KLAUNCH("cg_scalar", scal_ax, s,
-                        cg_alpha_kernel<<<kb_ax, rb, 0, s>>>(part, PH, sg, k, ld, st, lvl2, red_cnt));
+                        cg_alpha_kernel<<<kb_ax, rb, 0, s>>>(part, PH, sg, kcols, ld, st, lvl2, red_cnt));
             // x, r, p, Ap read; x, r written
-            CG_SWITCH(cfg, CSC_KLAUNCH("cg_update", 6 * blkb + 4.0 * N + 2 * scal_b, s,
-                                       cg_update_kernel<G_, NT_><<<grid, th, 0, s>>>(x, r, p, Ap, st.alpha, gid, pinv,
-                                                                                     rpart, ld, ld, part, bt)));
+            CG_SWITCH(wcfg, CSC_KLAUNCH("cg_update", 6 * blkb + 4.0 * N + 2 * scal_b, s,
+                                       cg_update_kernel<G_, NT_><<<wgrid, th, 0, s>>>(x, r, p, Ap, st.alpha, gid, pinv,
+                                                                                     rpart, kw, ld, part, bt)));
             CSC_TRY(reset_active(s));
             CSC_KLAUNCH("cg_scalar", 2 * scal_b, s,
-                        cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, sg, k, ld, st, rel_tol * rel_tol, 0, lvl2,
+                        cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, sg, kcols, ld, st, rel_tol * rel_tol, 0, lvl2,
                                                          red_cnt));
-            CG_SWITCH(cfg, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
-                                       cg_pupdate_kernel<G_, NT_><<<grid, th, 0, s>>>(r, p, st.beta, gid, pinv, rpart,
-                                                                                      ld, ld, bt)));
+            CG_SWITCH(wcfg, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
+                                       cg_pupdate_kernel<G_, NT_><<<wgrid, th, 0, s>>>(r, p, st.beta, gid, pinv, rpart,
+                                                                                      kw, ld, bt)));
         }
         return CSC_OK;
     };
@@ -1145,8 +1202,9 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         const int batch = std::min(check_every, max_iter - it);
         if (!g_prof_enabled && g->use_graphs) {
             char key[320];
-            snprintf(key, sizeof(key), "cg:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%.17g:%.17g:%p:%p:%p:%p:%p:%p", batch, ld,
-                     k, nseg, g_power, hp ? hp_m : -1, cfg.G, cfg.NT, cfg.threads, cfg.P, cfg.tiles, gamma, rel_tol,
+            snprintf(key, sizeof(key), "cg:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%.17g:%.17g:%p:%p:%p:%p:%p:%p",
+                     batch, ld, k, kw, nseg, g_power, hp ? hp_m : -1, wcfg.G, wcfg.NT, wcfg.threads, wcfg.P, wcfg.tiles,
+                     wcfg.staged, gamma, rel_tol,
                      (void*)x, (void*)sd, (void*)part, (void*)d_gk, (const void*)sg.gblk, (const void*)op.coef);
             int64_t launches = 0;
             CSC_TRY(replay_graph(g, key, s, &launches, [&](cudaStream_t cap) { return iterations(cap, batch); }));
@@ -1157,6 +1215,72 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         CSC_CUDA_TRY(cudaMemcpyAsync(h_active, st.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
         CSC_CUDA_TRY(cudaStreamSynchronize(s));
         converged = h_active[0] == 0;
+        const int want = ((h_active[0] + 3) / 4) * 4;
+        if (compact && !converged && it < max_iter && (want <= kw - 8 || 2 * want <= kw)) {
+            // the active slots first, in slot order, then the idle ones; per-slot scalars
+            // follow on the host
+            std::vector<int> act(kw);
+            std::vector<double> sc((size_t)5 * kw);
+            double* cols[5] = {st.rz, st.bn2, st.alpha, st.beta, st.rr};
+            CSC_CUDA_TRY(cudaMemcpyAsync(act.data(), st.active, (size_t)kw * sizeof(int), cudaMemcpyDeviceToHost, s));
+            for (int q = 0; q < 5; ++q)
+                CSC_CUDA_TRY(cudaMemcpyAsync(sc.data() + (size_t)q * kw, cols[q], (size_t)kw * sizeof(double),
+                                             cudaMemcpyDeviceToHost, s));
+            CSC_CUDA_TRY(cudaStreamSynchronize(s));
+            std::vector<int32_t> src;
+            src.reserve(kw);
+            for (int j = 0; j < kw; ++j)
+                if (act[j]) src.push_back(j);
+            for (int j = 0; j < kw; ++j)
+                if (!act[j]) src.push_back(j);
+            std::vector<int> col2(kw), act2(kw);
+            std::vector<double> sc2((size_t)5 * kw);
+            for (int j = 0; j < kw; ++j) {
+                col2[j] = slot_col[src[j]];
+                act2[j] = act[src[j]];
+                for (int q = 0; q < 5; ++q) sc2[(size_t)q * kw + j] = sc[(size_t)q * kw + src[j]];
+            }
+            std::copy(col2.begin(), col2.end(), slot_col.begin());
+            CSC_CUDA_TRY(cudaMemcpyAsync(d_src, src.data(), (size_t)kw * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            CSC_CUDA_TRY(cudaMemcpyAsync(st.active, act2.data(), (size_t)kw * sizeof(int), cudaMemcpyHostToDevice, s));
+            for (int q = 0; q < 5; ++q)
+                CSC_CUDA_TRY(cudaMemcpyAsync(cols[q], sc2.data() + (size_t)q * kw, (size_t)kw * sizeof(double),
+                                             cudaMemcpyHostToDevice, s));
+            CSC_KLAUNCH("cg_compact", 6.0 * N * kw * 4, s,
+                        permute_columns_kernel<<<(int)std::min<int64_t>(ceil_div(N, 8), g->num_sms * 16), 256,
+                                                 8 * kw * sizeof(float), s>>>(x, r, p, d_src, kw, ld, N));
+            // the host vectors above are released when this scope ends: wait for the copies
+            CSC_CUDA_TRY(cudaStreamSynchronize(s));
+            set_width(want);
+        }
+    }
+    if (compact) {
+        // back to column order: slot s of x holds column slot_col[s]; the idle slots past
+        // kw were never touched after their column finished
+        bool moved = false;
+        for (int j = 0; j < ld; ++j) moved |= slot_col[j] != j;
+        if (moved) {
+            std::vector<int32_t> src(ld);
+            for (int j = 0; j < ld; ++j) src[slot_col[j]] = j;
+            std::vector<double> sc((size_t)2 * ld), sc2((size_t)2 * ld);
+            double* cols[2] = {st.bn2, st.rr};
+            for (int q = 0; q < 2; ++q)
+                CSC_CUDA_TRY(cudaMemcpyAsync(sc.data() + (size_t)q * ld, cols[q], (size_t)ld * sizeof(double),
+                                             cudaMemcpyDeviceToHost, s));
+            CSC_CUDA_TRY(cudaMemcpyAsync(d_src, src.data(), (size_t)ld * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            CSC_CUDA_TRY(cudaStreamSynchronize(s));
+            for (int q = 0; q < 2; ++q)
+                for (int j = 0; j < ld; ++j) sc2[(size_t)q * ld + j] = sc[(size_t)q * ld + src[j]];
+            for (int q = 0; q < 2; ++q)
+                CSC_CUDA_TRY(cudaMemcpyAsync(cols[q], sc2.data() + (size_t)q * ld, (size_t)ld * sizeof(double),
+                                             cudaMemcpyHostToDevice, s));
+            // r and p are dead: they take the same permutation only because the kernel moves three blocks
+            CSC_KLAUNCH("cg_compact", 6.0 * N * ld * 4, s,
+                        permute_columns_kernel<<<(int)std::min<int64_t>(ceil_div(N, 8), g->num_sms * 16), 256,
+                                                 8 * ld * sizeof(float), s>>>(x, r, p, d_src, ld, ld, N));
+            CSC_CUDA_TRY(cudaStreamSynchronize(s));
+        }
+        set_width(ld);
     }
     // true residual ||b - A x|| / ||b|| per column
     CSC_TRY(apply_A(x, bt_all, s));

@@ -231,6 +231,35 @@ def test_interpolation_graph_replay_matches_eager():
     assert torch.equal(f0, f1) and torch.equal(f1, f2) and torch.equal(l0, l2)
 
 
+def test_interpolation_column_compaction():
+    """Columns whose CG has converged leave the iteration (the active ones are moved to the
+    front slots): on a power-law graph the columns converge hundreds of iterations apart,
+    so the solve compacts; every column must still meet the residual target (recomputed by
+    the oracle), keep its place, and the replayed graphs must give the eager bits."""
+    g = ci.chung_lu(20_000, exponent=2.1, mean=6.0, seed=3)
+    lap = olap.laplacian(g.row_ptr, g.col_idx)
+    k, n_s = 40, 296
+    om = osamp.sample(g.n, n_s, 4)
+    lab = (np.arange(n_s) % k).astype(np.int32)  # every cluster sampled
+    omd, labd = torch.from_numpy(om).cuda(), torch.from_numpy(lab).cuda()
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM | csc.DEGREE_ORDER) as h:
+        csc.csc_profile_reset()
+        csc.csc_profile_enable(True)
+        l0, f0, i0 = csc.csc_interpolate(h, omd, labd, k, fuzzy=True, max_iter=5000)
+        csc.csc_profile_enable(False)
+        q = csc.csc_profile_query()
+        l1, f1, i1 = csc.csc_interpolate(h, omd, labd, k, fuzzy=True, max_iter=5000)
+    assert q.get("cg_compact", {}).get("launches", 0) >= 2  # at least one compaction and the way back
+    assert i0.converged and i0.iters == i1.iters
+    assert torch.equal(f0, f1) and torch.equal(l0, l1)
+    x = f0.cpu().numpy().astype(np.float64)
+    b = ointerp.rhs(g.n, om, lab, k)
+    res = ointerp.apply_system(lap, ointerp.mask(g.n, om), 1e-3, 4, x) - b
+    rres = np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)
+    assert np.max(rres) <= 3e-6, rres
+    assert np.array_equal(l0.cpu().numpy(), ointerp.labels_from_indicators(f0.cpu().numpy()))
+
+
 # ------------------------------------------- interpolation with g = 1 - h~
 
 def _check_highpass(g, om, lab, k, lam, m, gamma, fz, dense=True):
