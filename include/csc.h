@@ -199,9 +199,11 @@ CSC_API csc_status csc_graph_info(csc_graph g, int64_t* N, int64_t* nnz, int32_t
  * graph.  Entry i
  * (0-based) is written to kind, dtype_bytes (4 fp32, 2 bf16, 8 fp64), columns and
  * shape[6] = {lanes per row G, vectors per lane NT, threads per CTA, row ranges P,
- * column tiles, index source}: index source 0 = each CTA stages its rows' column
- * indices in shared memory, 1 = the indices are read from global memory.  Host outputs (any may be
- * NULL).  CSC_E_INVALID when i is out of range. */
+ * column tiles, variant}: variant bit 0 = the index source (0: each CTA stages its
+ * rows' column indices in shared memory, 1: the indices are read from global memory),
+ * bit 1 = the lean form of the Clenshaw orders and CG products (NT = 1, 256 threads:
+ * at most 4 neighbour rows in flight per lane, 5 CTAs per SM instead of 4).  Host
+ * outputs (any may be NULL).  CSC_E_INVALID when i is out of range. */
 CSC_API csc_status csc_graph_tuned_shape(csc_graph g, int32_t i, int32_t* kind, int32_t* dtype_bytes,
                                          int32_t* columns, int32_t* shape);
 
@@ -209,7 +211,8 @@ CSC_API csc_status csc_graph_tuned_shape(csc_graph g, int32_t i, int32_t* kind, 
  * instead of tuning it (reproducible timings; tests of every compiled shape).
  * kind, dtype_bytes, columns and shape[6] as in csc_graph_tuned_shape (host).
  * (G, NT) must be a compiled pair, threads 256 or 512, tiles = ceil(vectors per
- * row / (G NT)), index source 0 or 1.
+ * row / (G NT)), variant 0 .. 3 (the lean bit only for kinds 3 and 4 with NT = 1 and
+ * 256 threads).
  * Errors: CSC_E_INVALID (no side effects); an uncompiled (G, NT) surfaces as
  * CSC_E_UNSUPPORTED at the next launch. */
 CSC_API csc_status csc_graph_pin_shape(csc_graph g, int32_t kind, int32_t dtype_bytes, int32_t columns,
@@ -265,9 +268,10 @@ CSC_API csc_status csc_filter_random_signals(csc_graph g, double lambda_c, int32
  * r_l ~ N(0, 1) drawn by Philox (key = (seed, stream "probes")), computed with
  * ceil((n_moments-1)/2) sparse block products using T_2j = 2 T_j^2 - T_0 and
  * T_2j+1 = 2 T_j+1 T_j - T_1, reductions in fp64.
+ *   n_probes 0 -> ceil(2 ln N) (Sec. 4.3).
  *   storage  CSC_F32 or CSC_BF16 for the probe block.
  *   mu_out   host double[n_moments].  Synchronizes `stream`.
- * Errors: CSC_E_INVALID (n_moments < 1, n_probes < 1). */
+ * Errors: CSC_E_INVALID (n_moments < 1, n_probes < 0). */
 CSC_API csc_status csc_kpm_moments(csc_graph g, int32_t n_moments, int32_t n_probes, uint64_t seed,
                            csc_dtype storage, double* mu_out, void* stream);
 
@@ -366,6 +370,43 @@ CSC_API csc_status csc_mlp_adam_step(float* params, const float* grad, float* m,
  * epoch.  Synchronizes `stream`. */
 CSC_API csc_status csc_mlp_train(float* params, const float* X, const float* T, int32_t n, int32_t epochs,
                                  int32_t batch, float lr, uint64_t seed, double* epoch_loss, void* stream);
+
+/* csc_bracket_fit -- fits the bracket predictor that csc_estimate_lambda_k_learned
+ * uses (the paper has no learned component; this is the training side of that add-on):
+ *   1. targets (centre, ln half-width) = ((lo + hi) / 2, ln max((hi - lo) / 2, 1e-12))
+ *      of each sample's target bracket (from csc_bracket_target);
+ *   2. the last round(val_frac * n) samples (ties to even; none when n < 10) are held
+ *      back, the others fitted: norm_out = their feature mean [72] and standard
+ *      deviation [72] (population), target mean [2] and standard deviation [2] (a zero
+ *      spread taken as 1), as fp32;
+ *   3. the standardised fitted features (as at inference: (x - mean) / std in fp32, 0
+ *      for a zero-spread feature) and targets train a network from csc_mlp_init(seed)
+ *      by csc_mlp_train(epochs, batch, lr, seed);
+ *   4. widen_out = the half-width factor calibrated on the held-back samples (on the
+ *      fitted ones when none is held back): widen_rule 0 -> the factor 0.25 * 2^(j/4),
+ *      j = 0..56, whose started halving (see csc_estimate_lambda_k_learned) takes the
+ *      fewest eigencount evaluations on average when the accepted cut-offs are
+ *      exactly the target bracket (first one on ties); widen_rule 1 -> the smallest
+ *      factor with which a `coverage` share of the predicted intervals meet their
+ *      target brackets (linear interpolation between order statistics), at least 1.
+ * feats: host float[n x 72] (csc_bracket_features); brackets: host double[n x 2] with
+ * lo <= hi.  params: device float[CSC_MLP_PARAMS] (overwritten).  norm_out: host
+ * float[148].  n_fit_out, epoch_loss (host double[epochs]): NULL or outputs.
+ * Errors: CSC_E_INVALID (no side effects), CSC_E_OOM, CSC_E_CUDA.  Synchronizes
+ * `stream`. */
+CSC_API csc_status csc_bracket_fit(const float* feats, const double* brackets, int32_t n, double val_frac,
+                                   int32_t epochs, int32_t batch, float lr, uint64_t seed, int32_t widen_rule,
+                                   double coverage, float* params, float* norm_out, double* widen_out,
+                                   int32_t* n_fit_out, double* epoch_loss, void* stream);
+
+/* csc_bracket_predict -- the predictor on n feature rows (host float[n x 72]):
+ * targets_out (host double[n x 2] or NULL) = (centre, ln half-width) as the network
+ * gives them after the standardisation of norm; brackets_out (host double[n x 2] or
+ * NULL) = centre -+ widen * exp(min(ln half-width, 10)) clipped to [0, 2], the
+ * bracket csc_estimate_lambda_k_learned starts from.  params: device.  norm: host
+ * float[148] from csc_bracket_fit.  Synchronizes `stream`. */
+CSC_API csc_status csc_bracket_predict(const float* params, const float* norm, double widen, const float* feats,
+                                       int32_t n, double* targets_out, double* brackets_out, void* stream);
 
 /* csc_estimate_lambda_k_learned -- Alg. 2 step 1 with a predicted bracket:
  *   1. csc_bracket_features (one moment pass over 8 probes, 64 moments);

@@ -93,6 +93,9 @@ _SIGNATURES = {
     "csc_mlp_adam_step": [c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_float, c_void_p],
     "csc_mlp_train": [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32, c_float, c_uint64, c_void_p,
                       c_void_p],
+    "csc_bracket_fit": [c_void_p, c_void_p, c_int32, c_double, c_int32, c_int32, c_float, c_uint64, c_int32,
+                        c_double, c_void_p, c_void_p, P(c_double), P(c_int32), c_void_p, c_void_p],
+    "csc_bracket_predict": [c_void_p, c_void_p, c_double, c_void_p, c_int32, c_void_p, c_void_p, c_void_p],
     "csc_estimate_lambda_k_learned": [c_void_p, c_int32, c_int32, c_int32, c_uint64, c_void_p, c_void_p, c_double,
                                       c_uint32, P(csc_lambda_info), c_void_p, c_void_p],
     "csc_estimate_lambda_k_refilter": [c_void_p, c_int32, c_int32, c_int32, c_uint64, c_void_p,

@@ -126,17 +126,18 @@ def csc_graph_tuned_shapes(g: Graph) -> list:
             break
         out.append(dict(kernel=kinds.get(kind.value, str(kind.value)), dtype_bytes=db.value, columns=cols.value,
                         G=shape[0], NT=shape[1], threads=shape[2], P=shape[3], tiles=shape[4],
-                        global_index=shape[5]))
+                        global_index=shape[5] & 1, lean=(shape[5] >> 1) & 1))
         i += 1
     return out
 
 
 def csc_graph_pin_shape(g: Graph, kernel: str, dtype_bytes: int, columns: int, G: int, NT: int, threads: int,
-                        P: int, tiles: int, global_index: int = 0) -> None:
+                        P: int, tiles: int, global_index: int = 0, lean: int = 0) -> None:
     """Fix a launch shape on this handle instead of tuning it (global_index = 1: the row-range
-    kernels read column indices from global memory instead of staging them in shared memory)."""
+    kernels read column indices from global memory instead of staging them in shared memory;
+    lean = 1: the lean form of the Clenshaw and CG kernels, NT = 1 and 256 threads)."""
     kind = {"cheb_step": 1, "mom_step": 2, "cg": 3, "clenshaw": 4}[kernel]
-    shape = (ctypes.c_int32 * 6)(G, NT, threads, P, tiles, global_index)
+    shape = (ctypes.c_int32 * 6)(G, NT, threads, P, tiles, global_index + 2 * lean)  # checked by the library
     check(lib().csc_graph_pin_shape(g.handle, kind, dtype_bytes, columns, shape), "csc_graph_pin_shape")
 
 
@@ -283,6 +284,43 @@ def csc_mlp_train(params: torch.Tensor, X: torch.Tensor, T: torch.Tensor, epochs
     check(lib().csc_mlp_train(_dptr(params), _dptr(X), _dptr(T), n, epochs, batch, lr, seed, _hptr(hist),
                               _stream(stream)), "csc_mlp_train")
     return hist[:epochs]
+
+
+def csc_bracket_fit(feats: np.ndarray, brackets: np.ndarray, val_frac: float = 0.15, epochs: int = 300,
+                    batch: int = 32, lr: float = 1e-3, seed: int = 0, widen_rule: int = 0, coverage: float = 0.9,
+                    params: Optional[torch.Tensor] = None, stream=None):
+    """(params device float[MLP_PARAMS], norm float32[148], widen, n_fit, epoch losses float64[epochs])."""
+    feats = np.ascontiguousarray(feats, dtype=np.float32)
+    brackets = np.ascontiguousarray(brackets, dtype=np.float64)
+    n = feats.shape[0]
+    if feats.shape != (n, nat.CSC_MLP_IN) or brackets.shape != (n, 2):
+        raise ValueError("feats must be n x 72 and brackets n x 2")
+    if params is None:
+        params = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+    _f32_dev(params, (MLP_PARAMS,), "params")
+    norm = np.empty(2 * nat.CSC_MLP_IN + 2 * nat.CSC_MLP_OUT, dtype=np.float32)
+    hist = np.zeros(max(epochs, 1), dtype=np.float64)
+    widen = ctypes.c_double()
+    n_fit = ctypes.c_int32()
+    check(lib().csc_bracket_fit(_hptr(feats), _hptr(brackets), n, val_frac, epochs, batch, lr, seed, widen_rule,
+                                coverage, _dptr(params), _hptr(norm), ctypes.byref(widen), ctypes.byref(n_fit),
+                                _hptr(hist), _stream(stream)), "csc_bracket_fit")
+    return params, norm, widen.value, n_fit.value, hist[:epochs]
+
+
+def csc_bracket_predict(params: torch.Tensor, norm: np.ndarray, widen: float, feats: np.ndarray, stream=None):
+    """(targets float64[n x 2] = (centre, ln half-width), brackets float64[n x 2])."""
+    _f32_dev(params, (MLP_PARAMS,), "params")
+    norm = np.ascontiguousarray(norm, dtype=np.float32)
+    feats = np.ascontiguousarray(feats, dtype=np.float32)
+    n = feats.shape[0]
+    if feats.shape != (n, nat.CSC_MLP_IN) or norm.shape != (2 * nat.CSC_MLP_IN + 2 * nat.CSC_MLP_OUT,):
+        raise ValueError("feats must be n x 72 and norm hold 148 floats")
+    t = np.empty((n, 2), dtype=np.float64)
+    b = np.empty((n, 2), dtype=np.float64)
+    check(lib().csc_bracket_predict(_dptr(params), _hptr(norm), widen, _hptr(feats), n, _hptr(t), _hptr(b),
+                                    _stream(stream)), "csc_bracket_predict")
+    return t, b
 
 
 def csc_estimate_lambda_k_learned(g: Graph, k: int, params: torch.Tensor, norm: np.ndarray, m: int = 50,

@@ -845,7 +845,7 @@ csc_status csc_graph_tuned_shape(csc_graph g, int32_t i, int32_t* kind, int32_t*
         shape[2] = it->second.threads;
         shape[3] = it->second.P;
         shape[4] = it->second.tiles;
-        shape[5] = it->second.staged ? 0 : 1;
+        shape[5] = (it->second.staged ? 0 : 1) | (it->second.lean ? 2 : 0);
     }
     return CSC_OK;
 }
@@ -855,8 +855,13 @@ csc_status csc_graph_pin_shape(csc_graph g, int32_t kind, int32_t dtype_bytes, i
     clear_error();
     CSC_TRY(check_graph(g));
     if (!shape || kind < 1 || kind > 4 || columns < 1 || shape[0] < 1 || shape[1] < 1 ||
-        (shape[2] != 256 && shape[2] != 512) || shape[3] < 1 || shape[4] < 1 || shape[5] < 0 || shape[5] > 1) {
+        (shape[2] != 256 && shape[2] != 512) || shape[3] < 1 || shape[4] < 1 || shape[5] < 0 || shape[5] > 3) {
         set_error("csc_graph_pin_shape: invalid shape");
+        return CSC_E_INVALID;
+    }
+    if ((shape[5] & 2) && ((kind != 3 && kind != 4) || shape[1] != 1 || shape[2] != 256)) {
+        set_error("csc_graph_pin_shape: the lean form exists for the CG products and Clenshaw orders with NT = 1 "
+                  "and 256 threads");
         return CSC_E_INVALID;
     }
     const int vec_bytes = 16;
@@ -877,7 +882,8 @@ csc_status csc_graph_pin_shape(csc_graph g, int32_t kind, int32_t dtype_bytes, i
     c.threads = shape[2];
     c.P = shape[3];
     c.tiles = shape[4];
-    c.staged = shape[5] == 0 ? 1 : 0;
+    c.staged = (shape[5] & 1) ? 0 : 1;
+    c.lean = (shape[5] & 2) ? 1 : 0;
     const uint64_t key = kind == 3 ? ((3ull << 48) | (uint64_t)(uint32_t)columns)
                                    : (((uint64_t)kind << 48) | ((uint64_t)(dtype_bytes & 0xff) << 40) |
                                       (uint64_t)(uint32_t)columns);
@@ -954,10 +960,11 @@ csc_status csc_kpm_moments(csc_graph g, int32_t n_moments, int32_t n_probes, uin
                            double* mu_out, void* stream) {
     clear_error();
     CSC_TRY(check_graph(g));
-    if (n_moments < 1 || n_probes < 1 || !mu_out || n_moments > 4096) {
-        set_error("csc_kpm_moments: need 1 <= n_moments <= 4096, n_probes >= 1, mu_out != NULL");
+    if (n_moments < 1 || n_probes < 0 || !mu_out || n_moments > 4096) {
+        set_error("csc_kpm_moments: need 1 <= n_moments <= 4096, n_probes >= 0, mu_out != NULL");
         return CSC_E_INVALID;
     }
+    if (n_probes == 0) n_probes = g->N > 1 ? (int)ceil(2.0 * log((double)g->N)) : 1;  // Sec. 4.3: 2 log N
     return poison_on_cuda(g, run_moments(g, n_moments, n_probes, seed, storage, mu_out, nullptr,
                                          (cudaStream_t)stream));
 }

@@ -137,8 +137,8 @@ __device__ __forceinline__ void lap_epilogue(int row, int lane, int col0, int tc
 }
 
 // Rows of degree > kHeavyRow are left to lap_heavy_kernel.
-template <int G, int NT, bool WIN, bool STAGED>
-__global__ void __launch_bounds__(kCgMaxThreads)
+template <int G, int NT, bool WIN, bool STAGED, bool LEAN>
+__global__ void __launch_bounds__(LEAN ? 256 : kCgMaxThreads, LEAN ? 5 : 0)
 lap_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const int32_t* __restrict__ lrp,
            const int32_t* __restrict__ lci, const float* __restrict__ dinv,
            const float* __restrict__ invdeg, const float* __restrict__ in, float* __restrict__ out,
@@ -150,7 +150,7 @@ lap_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const
         RowVecs<G, NT> x;
         x.load(in, row, lane, col0, tcols, ld);
         float acc[NT][4];
-        gather_any<STAGED, float, G, NT, WIN, float>(e0, e1, idx, dinv, in + col0, ld, lane, tcols, acc);
+        gather_any<STAGED, float, G, NT, WIN, float, LEAN>(e0, e1, idx, dinv, in + col0, ld, lane, tcols, acc);
         lap_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, invdeg, x, out, ld);
     });
 }
@@ -206,8 +206,8 @@ __device__ __forceinline__ void lap_ax_epilogue(int row, int lane, int col0, int
 
 // <p, A p> partial slots: [0, gridDim.x) for the row ranges, then one per heavy
 // row (lap_ax_heavy_kernel); nslots counts both.
-template <int G, int NT, bool WIN, bool STAGED>
-__global__ void __launch_bounds__(kCgMaxThreads)
+template <int G, int NT, bool WIN, bool STAGED, bool LEAN>
+__global__ void __launch_bounds__(LEAN ? 256 : kCgMaxThreads, LEAN ? 5 : 0)
 lap_ax_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const int32_t* __restrict__ lrp,
               const int32_t* __restrict__ lci, const float* __restrict__ dinv,
               const float* __restrict__ sqdeg, const float* __restrict__ tin, const float* __restrict__ p,
@@ -222,7 +222,7 @@ lap_ax_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, co
         tv.load(tin, row, lane, col0, tcols, ld);
         pv.load(p, row, lane, col0, tcols, ld);
         float acc[NT][4];
-        gather_any<STAGED, float, G, NT, WIN, float>(e0, e1, idx, dinv, tin + col0, ld, lane, tcols, acc);
+        gather_any<STAGED, float, G, NT, WIN, float, LEAN>(e0, e1, idx, dinv, tin + col0, ld, lane, tcols, acc);
         lap_ax_epilogue<G, NT, WIN>(row, lane, col0, tcols, acc, dinv, sqdeg, tv, pv, mask, gamma, Ap, ld, dot);
     });
     block_column_partials<G, NT, 1>(dot, lane, col0, tcols, ld, partials, blockIdx.x, nslots);
@@ -741,10 +741,23 @@ static const int kCgThreadChoices[] = {256, 512};
     } while (0)
 
 template <int G, int NT>
-static int cg_occupancy_of(int threads) {
-    // the solve's most register-hungry kernel bounds the residency of all of them
+static int cg_occupancy_of(int threads, bool lean) {
+    // the solve's most register-hungry kernel bounds the residency of all of them (the lean
+    // form: its products, which take most of the time)
     int a = 1, b = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, lap_kernel<G, NT, false, true>, threads, 0) != cudaSuccess ||
+    cudaError_t e;
+    if constexpr (NT == 1) {
+        if (lean) {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, lap_kernel<G, NT, false, true, true>, threads, 0);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return 1;
+            }
+            return a < 1 ? 1 : a;
+        }
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, lap_kernel<G, NT, false, true, false>, threads, 0) !=
+            cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cg_update_kernel<G, NT>, threads, 0) != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -753,12 +766,63 @@ static int cg_occupancy_of(int threads) {
     return n < 1 ? 1 : n;
 }
 
+// Row-range launches of one product of the L-chain and of the last product, in the shape's
+// index source and form (LaunchCfg::staged, LaunchCfg::lean; the lean form has NT = 1).
+template <int G, int NT, bool WIN>
+static void lap_rows(const LaunchCfg& c, dim3 grid, int smem, cudaStream_t s, const Graph* g, const float* in,
+                     float* out, const int32_t* part, int ncols, int64_t ld, const CgBatch& bt) {
+    if constexpr (NT == 1) {
+        if (c.lean) {
+            if (c.staged)
+                lap_kernel<G, NT, WIN, true, true><<<grid, c.threads, smem, s>>>(
+                    g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->invdeg, in, out, part, ncols, ld, bt);
+            else
+                lap_kernel<G, NT, WIN, false, true><<<grid, c.threads, 0, s>>>(
+                    g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->invdeg, in, out, part, ncols, ld, bt);
+            return;
+        }
+    }
+    if (c.staged)
+        lap_kernel<G, NT, WIN, true, false><<<grid, c.threads, smem, s>>>(
+            g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->invdeg, in, out, part, ncols, ld, bt);
+    else
+        lap_kernel<G, NT, WIN, false, false><<<grid, c.threads, 0, s>>>(
+            g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->invdeg, in, out, part, ncols, ld, bt);
+}
+
+template <int G, int NT, bool WIN>
+static void lap_ax_rows(const LaunchCfg& c, dim3 grid, int smem, cudaStream_t s, const Graph* g, const float* tin,
+                        const float* p, const float* mask, float gamma, float* Ap, const int32_t* part, int ncols,
+                        int64_t ld, double* partials, int nslots, const CgBatch& bt) {
+    if constexpr (NT == 1) {
+        if (c.lean) {
+            if (c.staged)
+                lap_ax_kernel<G, NT, WIN, true, true><<<grid, c.threads, smem, s>>>(
+                    g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->sqdeg, tin, p, mask, gamma, Ap, part, ncols,
+                    ld, partials, nslots, bt);
+            else
+                lap_ax_kernel<G, NT, WIN, false, true><<<grid, c.threads, 0, s>>>(
+                    g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->sqdeg, tin, p, mask, gamma, Ap, part, ncols,
+                    ld, partials, nslots, bt);
+            return;
+        }
+    }
+    if (c.staged)
+        lap_ax_kernel<G, NT, WIN, true, false><<<grid, c.threads, smem, s>>>(
+            g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->sqdeg, tin, p, mask, gamma, Ap, part, ncols, ld,
+            partials, nslots, bt);
+    else
+        lap_ax_kernel<G, NT, WIN, false, false><<<grid, c.threads, 0, s>>>(
+            g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->sqdeg, tin, p, mask, gamma, Ap, part, ncols, ld,
+            partials, nslots, bt);
+}
+
 // Dynamic shared memory a staged launch of the shape may add to the solve's kernels' own
 // arrays (the fused product's column partials take 16 KB per vector per lane).
 template <int G, int NT>
 static int cg_staged_room() {
     cudaFuncAttributes a{};
-    if (cudaFuncGetAttributes(&a, lap_ax_kernel<G, NT, false, true>) != cudaSuccess) {
+    if (cudaFuncGetAttributes(&a, lap_ax_kernel<G, NT, false, true, false>) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -766,7 +830,7 @@ static int cg_staged_room() {
 }
 
 static csc_status cg_occupancy(const LaunchCfg& c, int* out) {
-    CG_SWITCH(c, *out = cg_occupancy_of<G_, NT_>(c.threads));
+    CG_SWITCH(c, *out = cg_occupancy_of<G_, NT_>(c.threads, c.lean != 0));
     return CSC_OK;
 }
 
@@ -794,37 +858,40 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         const int tiles = (nv + cap - 1) / cap;
         const int waste = tiles * cap - nv;
         if (tiles > 64 || (3 * waste > tiles * cap && waste > min_waste)) continue;
-        for (int th : kCgThreadChoices) {
-            LaunchCfg c;
-            c.G = sh[0];
-            c.NT = sh[1];
-            c.threads = th;
-            c.tiles = tiles;
-            int occ = 1;
-            CSC_TRY(cg_occupancy(c, &occ));
-            const int64_t lim = (N + (th / c.G) - 1) / (th / c.G);
-            // one to eight waves of resident CTAs (shorter row ranges balance uneven SMs)
-            for (int waves = 1; waves <= 8; waves *= 2) {
-                int P = (g->num_sms * occ * waves + tiles - 1) / tiles;
-                if (P > lim) P = (int)lim;
-                if (P < g->n_graphs) P = g->n_graphs;  // a batch needs a range per graph
-                P = P < 1 ? 1 : P;
-                // the CTA's staged CSR slice must fit shared memory: more, shorter ranges if not
-                CSC_TRY(fit_staged_partition(g, P, std::max<int64_t>(lim, g->n_graphs), &P));
-                if (staged_smem(g, P) > kStagedSmemMax) continue;
-                c.P = P;
-                if (!cands.empty() && cands.back().G == c.G && cands.back().NT == c.NT &&
-                    cands.back().threads == th && cands.back().P == c.P)
-                    continue;
-                max_p = std::max(max_p, c.P);
-                int room = 0;
-                CG_SWITCH(c, room = cg_staged_room<G_, NT_>());
-                c.staged = 1;  // both index sources (sweep_rows), the staged one where it fits
-                if (staged_smem(g, c.P) <= std::min(room, kStagedSmemMax)) cands.push_back(c);
-                c.staged = 0;
-                cands.push_back(c);
+        for (int th : kCgThreadChoices)
+            for (int lean = 0; lean <= 1; ++lean) {
+                if (lean && (sh[1] != 1 || th != 256)) continue;  // the lean form: NT = 1, 256 threads
+                LaunchCfg c;
+                c.G = sh[0];
+                c.NT = sh[1];
+                c.threads = th;
+                c.tiles = tiles;
+                c.lean = lean;
+                int occ = 1;
+                CSC_TRY(cg_occupancy(c, &occ));
+                const int64_t lim = (N + (th / c.G) - 1) / (th / c.G);
+                // one to eight waves of resident CTAs (shorter row ranges balance uneven SMs)
+                for (int waves = 1; waves <= 8; waves *= 2) {
+                    int P = (g->num_sms * occ * waves + tiles - 1) / tiles;
+                    if (P > lim) P = (int)lim;
+                    if (P < g->n_graphs) P = g->n_graphs;  // a batch needs a range per graph
+                    P = P < 1 ? 1 : P;
+                    // the CTA's staged CSR slice must fit shared memory: more, shorter ranges if not
+                    CSC_TRY(fit_staged_partition(g, P, std::max<int64_t>(lim, g->n_graphs), &P));
+                    if (staged_smem(g, P) > kStagedSmemMax) continue;
+                    c.P = P;
+                    if (!cands.empty() && cands.back().G == c.G && cands.back().NT == c.NT &&
+                        cands.back().threads == th && cands.back().lean == lean && cands.back().P == c.P)
+                        continue;
+                    max_p = std::max(max_p, c.P);
+                    int room = 0;
+                    CG_SWITCH(c, room = cg_staged_room<G_, NT_>());
+                    c.staged = 1;  // both index sources (sweep_rows), the staged one where it fits
+                    if (staged_smem(g, c.P) <= std::min(room, kStagedSmemMax)) cands.push_back(c);
+                    c.staged = 0;
+                    cands.push_back(c);
+                }
             }
-        }
     }
     if (cands.empty()) {
         set_error("csc_interpolate: no launch shape for k = %d", k);
@@ -959,24 +1026,11 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                     if (rep == 1) cudaEventRecord(g->ev[0], s);
                     const float* src[3] = {r, t1, t2};
                     float* dst[3] = {t1, t2, t1};
-                    for (int q = 0; q < 3; ++q) {
-                        if (c.staged)
-                            CG_SWITCH(c, lap_kernel<G_, NT_, false, true><<<grid, c.threads, sm, s>>>(
-                                             g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->invdeg, src[q], dst[q],
-                                             pr, ld, ld, CgBatch()));
-                        else
-                            CG_SWITCH(c, lap_kernel<G_, NT_, false, false><<<grid, c.threads, 0, s>>>(
-                                             g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->invdeg, src[q], dst[q],
-                                             pr, ld, ld, CgBatch()));
-                    }
-                    if (c.staged)
-                        CG_SWITCH(c, lap_ax_kernel<G_, NT_, false, true><<<grid, c.threads, sm, s>>>(
-                                         g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->sqdeg, t1, p, mask,
-                                         (float)gamma, Ap, pr, ld, ld, part, c.P, CgBatch()));
-                    else
-                        CG_SWITCH(c, lap_ax_kernel<G_, NT_, false, false><<<grid, c.threads, 0, s>>>(
-                                         g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->sqdeg, t1, p, mask,
-                                         (float)gamma, Ap, pr, ld, ld, part, c.P, CgBatch()));
+                    for (int q = 0; q < 3; ++q)
+                        CG_SWITCH(c, lap_rows<G_, NT_, false>(c, grid, sm, s, g, src[q], dst[q], pr, ld, ld,
+                                                              CgBatch()));
+                    CG_SWITCH(c, lap_ax_rows<G_, NT_, false>(c, grid, sm, s, g, t1, p, mask, (float)gamma, Ap, pr, ld,
+                                                             ld, part, c.P, CgBatch()));
                     CG_SWITCH(c, cg_update_kernel<G_, NT_><<<grid, c.threads, 0, s>>>(x, r, p, Ap, nullptr, nullptr,
                                                                                        pinv, pr, ld, ld, part,
                                                                                        CgBatch()));
@@ -1126,17 +1180,14 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
             };
             auto light = [&](cudaStream_t st) -> csc_status {
                 const double by = lb * (1.0 - heavy_frac);
-#define CSC_LAP(W, S)                                                                                        \
-    CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap", by, st,                                                             \
-                               (lap_kernel<G_, NT_, W, S><<<wgrid, th, csmem, st>>>(g->row_ptr, g->col_idx,   \
-                                                                                  g->lrp, g->lci, g->dinv,   \
-                                                                                  g->invdeg, cur, o, rpart,  \
-                                                                                  kw, ld, bb))))
-                if (win && wcfg.staged) CSC_LAP(true, true);
-                else if (win) CSC_LAP(true, false);
-                else if (wcfg.staged) CSC_LAP(false, true);
-                else CSC_LAP(false, false);
-#undef CSC_LAP
+                if (win)
+                    CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap", by, st,
+                                                lap_rows<G_, NT_, true>(wcfg, wgrid, csmem, st, g, cur, o, rpart, kw,
+                                                                        ld, bb)));
+                else
+                    CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap", by, st,
+                                                lap_rows<G_, NT_, false>(wcfg, wgrid, csmem, st, g, cur, o, rpart, kw,
+                                                                         ld, bb)));
                 return CSC_OK;
             };
             CSC_TRY(fork_join(g, s, H > 0, heavy, light));
@@ -1160,16 +1211,15 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         };
         auto light = [&](cudaStream_t st) -> csc_status {
             const double by = ab * (1.0 - heavy_frac);
-#define CSC_LAPAX(W, S)                                                                                         \
-    CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax", by, st,                                                             \
-                               (lap_ax_kernel<G_, NT_, W, S><<<wgrid, th, csmem, st>>>(                          \
-                                   g->row_ptr, g->col_idx, g->lrp, g->lci, g->dinv, g->sqdeg, cur, in, mask,    \
-                                   (float)gamma, Ap, rpart, kw, ld, part, PH, bb))))
-            if (win && wcfg.staged) CSC_LAPAX(true, true);
-            else if (win) CSC_LAPAX(true, false);
-            else if (wcfg.staged) CSC_LAPAX(false, true);
-            else CSC_LAPAX(false, false);
-#undef CSC_LAPAX
+            if (win)
+                CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax", by, st,
+                                            lap_ax_rows<G_, NT_, true>(wcfg, wgrid, csmem, st, g, cur, in, mask,
+                                                                       (float)gamma, Ap, rpart, kw, ld, part, PH, bb)));
+            else
+                CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax", by, st,
+                                            lap_ax_rows<G_, NT_, false>(wcfg, wgrid, csmem, st, g, cur, in, mask,
+                                                                        (float)gamma, Ap, rpart, kw, ld, part, PH,
+                                                                        bb)));
             return CSC_OK;
         };
         return fork_join(g, s, H > 0, heavy, light);
@@ -1204,7 +1254,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
             char key[320];
             snprintf(key, sizeof(key), "cg:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%.17g:%.17g:%p:%p:%p:%p:%p:%p",
                      batch, ld, k, kw, nseg, g_power, hp ? hp_m : -1, wcfg.G, wcfg.NT, wcfg.threads, wcfg.P, wcfg.tiles,
-                     wcfg.staged, gamma, rel_tol,
+                     wcfg.staged * 2 + wcfg.lean, gamma, rel_tol,
                      (void*)x, (void*)sd, (void*)part, (void*)d_gk, (const void*)sg.gblk, (const void*)op.coef);
             int64_t launches = 0;
             CSC_TRY(replay_graph(g, key, s, &launches, [&](cudaStream_t cap) { return iterations(cap, batch); }));

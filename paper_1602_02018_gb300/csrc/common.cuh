@@ -105,6 +105,10 @@ struct Buffer {
 struct LaunchCfg {
     int G = 0, NT = 0, threads = 0, P = 0, tiles = 1;
     int staged = 1;  // row-range kernels: indices staged in shared memory (0: read from global)
+    // Clenshaw and CG row-range kernels, NT = 1 and 256 threads only: the lean form, with at
+    // most 4 neighbour rows in flight per lane and a launch bound of 5 CTAs per SM (48
+    // registers instead of 60), trading loads in flight per warp for resident warps
+    int lean = 0;
 };
 
 struct Graph {

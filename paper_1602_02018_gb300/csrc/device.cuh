@@ -336,15 +336,16 @@ __device__ __forceinline__ void gather_batch(int e, int cnt, const int32_t* ci, 
 // graph have one to four edges) the batch has 2 or 4 slots, so fewer instructions go to
 // empty slots.  The sum runs over the edges in order whatever the batching, so every
 // batching gives the same bits.
-template <typename T, int G, int NT, bool WEIGHTED, typename W>
+template <typename T, int G, int NT, bool WEIGHTED, typename W, bool LEAN = false>
 __device__ __forceinline__ void gather_staged(int e, const int end, const int32_t* ci, const W* __restrict__ wv,
                                               const T* __restrict__ X, int64_t ld, int lane, int ncols,
                                               typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC]) {
     using Tr = StoreTraits<T>;
     using A = typename Tr::acc_t;
     constexpr int VEC = Tr::VEC;
-    // edges in flight per lane: 8 one-vector rows, or 4 rows of NT >= 2 vectors
-    constexpr int B = NT == 1 ? 8 : 4;
+    // edges in flight per lane: 8 one-vector rows, or 4 rows of NT >= 2 vectors (or in the
+    // lean form, LaunchCfg::lean)
+    constexpr int B = (NT == 1 && !LEAN) ? 8 : 4;
 #pragma unroll
     for (int t = 0; t < NT; ++t)
 #pragma unroll
@@ -374,7 +375,7 @@ __device__ __forceinline__ void gather_staged(int e, const int end, const int32_
 // within the group, so the neighbour-row loads of a chunk issue back to back
 // without a dependent index load in front of each.  Columns >= ncols are
 // skipped (their accumulators stay 0).
-template <typename T, int G, int NT, bool WEIGHTED, typename W>
+template <typename T, int G, int NT, bool WEIGHTED, typename W, bool LEAN = false>
 __device__ __forceinline__ void gather_range(int e, const int end, const int32_t* __restrict__ ci,
                                              const W* __restrict__ wv, const T* __restrict__ X, int64_t ld,
                                              int lane, int ncols,
@@ -404,8 +405,9 @@ __device__ __forceinline__ void gather_range(int e, const int end, const int32_t
             if (WEIGHTED) wi[j] = ok ? A(__ldg(wv + li[j])) : A(0);
         }
         const int cnt = min(CH, end - e);
-        // edges in flight per lane: 8 one-vector rows, or 4 rows of NT >= 2 vectors
-        constexpr int B = NT == 1 ? 8 : 4;
+        // edges in flight per lane: 8 one-vector rows, or 4 rows of NT >= 2 vectors (or in
+        // the lean form, LaunchCfg::lean)
+        constexpr int B = (NT == 1 && !LEAN) ? 8 : 4;
 #pragma unroll
         for (int q0 = 0; q0 < CH; q0 += B) {
             if (q0 >= cnt) break;
@@ -472,12 +474,12 @@ __device__ __forceinline__ void gather_row(const int32_t* __restrict__ rp, const
 }
 
 // The neighbour sum of one light row with indices from either source (see sweep_rows).
-template <bool STAGED, typename T, int G, int NT, bool WEIGHTED, typename W>
+template <bool STAGED, typename T, int G, int NT, bool WEIGHTED, typename W, bool LEAN = false>
 __device__ __forceinline__ void gather_any(int e0, int e1, const int32_t* idx, const W* __restrict__ wv,
                                            const T* __restrict__ X, int64_t ld, int lane, int ncols,
                                            typename StoreTraits<T>::acc_t (&acc)[NT][StoreTraits<T>::VEC]) {
-    if constexpr (STAGED) gather_staged<T, G, NT, WEIGHTED, W>(e0, e1, idx, wv, X, ld, lane, ncols, acc);
-    else gather_range<T, G, NT, WEIGHTED, W>(e0, e1, idx, wv, X, ld, lane, ncols, acc);
+    if constexpr (STAGED) gather_staged<T, G, NT, WEIGHTED, W, LEAN>(e0, e1, idx, wv, X, ld, lane, ncols, acc);
+    else gather_range<T, G, NT, WEIGHTED, W, LEAN>(e0, e1, idx, wv, X, ld, lane, ncols, acc);
 }
 
 // Neighbour sum of a heavy row (see kHeavyRow) by a whole CTA of kHeavyThreads

@@ -11,6 +11,7 @@
 // these kernels are latency-bound by design and use plain FMA pipes.
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -384,4 +385,249 @@ extern "C" CSC_API csc_status csc_mlp_train(float* params, const float* X, const
     cudaFree(d_loss);
     if (st != CSC_OK) set_error("csc_mlp_train: CUDA error during training");
     return st;
+}
+
+// ------------------------------------------------------------ bracket predictor fit
+// The training-set arithmetic of the learned lambda_k bracket (an add-on the paper does
+// not have): targets (centre, ln half-width) of the target brackets, standardisation
+// constants of the fitted samples, the network's training, and the calibration of the
+// half-width factor on the held-back samples.
+namespace csc {
+namespace {
+
+// the network input of one feature row: the standardisation csc_estimate_lambda_k_learned
+// applies at inference (fp32, a feature of zero spread maps to 0)
+void standardise_row(const float* f, const float* norm, float* out) {
+    for (int i = 0; i < CSC_MLP_IN; ++i) {
+        const float sd = norm[CSC_MLP_IN + i];
+        out[i] = sd > 0.f ? (f[i] - norm[i]) / sd : 0.f;
+    }
+}
+
+// Eigencount evaluations that the halving started from a prediction (centre c, half-width
+// hw) spends when the accepted cut-offs are exactly [lo, hi] (the count rounds to k inside,
+// exceeds it above, falls short below): the centre decides the side, the predicted end on
+// that side comes next, then halving inside the prediction or on the rest of [0, 2], as
+// csc_estimate_lambda_k_learned searches.
+int search_evaluations(double c, double hw, double lo, double hi) {
+    auto side = [&](double x) { return (lo <= x && x <= hi) ? 0 : (x > hi ? 1 : -1); };
+    auto halve = [&](double a, double b, int n) {
+        for (int it = 1; it <= 60; ++it) {
+            const double mid = 0.5 * (a + b);
+            const int sd = side(mid);
+            if (sd == 0) return n + it;
+            if (sd > 0) b = mid; else a = mid;
+            if (b - a < 1e-12 || it == 60) return n + it + 1;
+        }
+        return n + 60;
+    };
+    c = std::min(2.0, std::max(0.0, c));
+    const int sc = side(c);
+    if (sc == 0) return 1;
+    const double e = sc > 0 ? std::max(0.0, c - hw) : std::min(2.0, c + hw);
+    const int se = side(e);
+    if (se == 0) return 2;
+    if (sc > 0) return se < 0 ? halve(e, c, 2) : halve(0.0, e, 2);
+    return se > 0 ? halve(c, e, 2) : halve(e, 2.0, 2);
+}
+
+// (centre, ln half-width) of n feature rows through the network, kMaxBatch rows at a time
+csc_status predict_targets(const float* params, const float* norm, const float* feats, int n, double* t,
+                           cudaStream_t s) {
+    const int cb = std::min(n, kMaxBatch);
+    std::vector<float> x((size_t)cb * CSC_MLP_IN), y((size_t)cb * CSC_MLP_OUT);
+    float *dx = nullptr, *dy = nullptr;
+    CSC_CUDA_TRY(cudaMalloc(&dx, x.size() * sizeof(float)));
+    if (cudaMalloc(&dy, y.size() * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dx);
+        set_error("bracket prediction: cudaMalloc failed");
+        return CSC_E_OOM;
+    }
+    csc_status st = CSC_OK;
+    const float* tm = norm + 2 * CSC_MLP_IN;  // target mean [2], target std [2]
+    for (int b0 = 0; b0 < n && st == CSC_OK; b0 += cb) {
+        const int b = std::min(cb, n - b0);
+        for (int i = 0; i < b; ++i)
+            standardise_row(feats + (size_t)(b0 + i) * CSC_MLP_IN, norm, x.data() + (size_t)i * CSC_MLP_IN);
+        if (cudaMemcpyAsync(dx, x.data(), (size_t)b * CSC_MLP_IN * sizeof(float), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess) {
+            st = CSC_E_CUDA;
+            break;
+        }
+        st = mlp_forward_device(params, dx, b, dy, s);
+        if (st != CSC_OK) break;
+        if (cudaMemcpyAsync(y.data(), dy, (size_t)b * CSC_MLP_OUT * sizeof(float), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            st = CSC_E_CUDA;
+            break;
+        }
+        for (int i = 0; i < b; ++i) {
+            t[2 * (size_t)(b0 + i)] = (double)y[2 * (size_t)i] * tm[2] + tm[0];
+            t[2 * (size_t)(b0 + i) + 1] = (double)y[2 * (size_t)i + 1] * tm[3] + tm[1];
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(dx);
+    cudaFree(dy);
+    if (st == CSC_E_CUDA) set_error("bracket prediction: CUDA error");
+    return st;
+}
+
+}  // namespace
+}  // namespace csc
+
+extern "C" CSC_API csc_status csc_bracket_fit(const float* feats, const double* brackets, int32_t n,
+                                              double val_frac, int32_t epochs, int32_t batch, float lr,
+                                              uint64_t seed, int32_t widen_rule, double coverage, float* params,
+                                              float* norm_out, double* widen_out, int32_t* n_fit_out,
+                                              double* epoch_loss, void* stream) {
+    clear_error();
+    if (!feats || !brackets || n < 2 || !(val_frac >= 0.0 && val_frac < 1.0) || epochs < 0 || batch < 1 ||
+        batch > kMaxBatch || !(lr > 0.f) || (widen_rule != 0 && widen_rule != 1) ||
+        !(coverage > 0.0 && coverage <= 1.0) || !params || !norm_out || !widen_out) {
+        set_error("csc_bracket_fit: invalid arguments (n=%d epochs=%d batch=%d rule=%d)", n, epochs, batch,
+                  widen_rule);
+        return CSC_E_INVALID;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (!(brackets[2 * i] <= brackets[2 * i + 1])) {
+            set_error("csc_bracket_fit: bracket %lld has lo > hi", (long long)i);
+            return CSC_E_INVALID;
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    // held-back share rounded half to even; none below 10 samples
+    const int n_val = n >= 10 ? (int)nearbyint(val_frac * n) : 0;
+    const int n_fit = n - n_val;
+    if (n_fit < 1) {
+        set_error("csc_bracket_fit: no sample left to fit");
+        return CSC_E_INVALID;
+    }
+    // targets (centre, ln half-width) and the standardisation of the fitted samples
+    std::vector<double> t((size_t)2 * n);
+    for (int i = 0; i < n; ++i) {
+        const double lo = brackets[2 * (size_t)i], hi = brackets[2 * (size_t)i + 1];
+        t[2 * (size_t)i] = 0.5 * (lo + hi);
+        t[2 * (size_t)i + 1] = log(std::max(0.5 * (hi - lo), 1e-12));
+    }
+    std::vector<double> fm(CSC_MLP_IN, 0.0), fs(CSC_MLP_IN, 0.0), tmean(2, 0.0), tstd(2, 0.0);
+    for (int i = 0; i < n_fit; ++i) {
+        for (int j = 0; j < CSC_MLP_IN; ++j) fm[j] += feats[(size_t)i * CSC_MLP_IN + j];
+        for (int j = 0; j < 2; ++j) tmean[j] += t[2 * (size_t)i + j];
+    }
+    for (int j = 0; j < CSC_MLP_IN; ++j) fm[j] /= n_fit;
+    for (int j = 0; j < 2; ++j) tmean[j] /= n_fit;
+    for (int i = 0; i < n_fit; ++i) {
+        for (int j = 0; j < CSC_MLP_IN; ++j) {
+            const double v = feats[(size_t)i * CSC_MLP_IN + j] - fm[j];
+            fs[j] += v * v;
+        }
+        for (int j = 0; j < 2; ++j) {
+            const double v = t[2 * (size_t)i + j] - tmean[j];
+            tstd[j] += v * v;
+        }
+    }
+    for (int j = 0; j < CSC_MLP_IN; ++j) fs[j] = sqrt(fs[j] / n_fit);
+    for (int j = 0; j < 2; ++j) {
+        tstd[j] = sqrt(tstd[j] / n_fit);
+        if (!(tstd[j] > 0.0)) tstd[j] = 1.0;
+    }
+    for (int j = 0; j < CSC_MLP_IN; ++j) {
+        norm_out[j] = (float)fm[j];
+        norm_out[CSC_MLP_IN + j] = (float)fs[j];
+    }
+    for (int j = 0; j < 2; ++j) {
+        norm_out[2 * CSC_MLP_IN + j] = (float)tmean[j];
+        norm_out[2 * CSC_MLP_IN + 2 + j] = (float)tstd[j];
+    }
+    // standardised training arrays on the device, then minibatch Adam from a fresh network
+    std::vector<float> x((size_t)n_fit * CSC_MLP_IN), y((size_t)n_fit * 2);
+    for (int i = 0; i < n_fit; ++i) {
+        standardise_row(feats + (size_t)i * CSC_MLP_IN, norm_out, x.data() + (size_t)i * CSC_MLP_IN);
+        for (int j = 0; j < 2; ++j) y[2 * (size_t)i + j] = (float)((t[2 * (size_t)i + j] - tmean[j]) / tstd[j]);
+    }
+    float *dx = nullptr, *dy = nullptr;
+    CSC_CUDA_TRY(cudaMalloc(&dx, x.size() * sizeof(float)));
+    if (cudaMalloc(&dy, y.size() * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(dx);
+        set_error("csc_bracket_fit: cudaMalloc failed");
+        return CSC_E_OOM;
+    }
+    csc_status st = CSC_OK;
+    if (cudaMemcpyAsync(dx, x.data(), x.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dy, y.data(), y.size() * sizeof(float), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = CSC_E_CUDA;
+    if (st == CSC_OK) st = csc_mlp_init(params, seed, stream);
+    if (st == CSC_OK) st = csc_mlp_train(params, dx, dy, n_fit, epochs, batch, lr, seed, epoch_loss, stream);
+    cudaStreamSynchronize(s);
+    cudaFree(dx);
+    cudaFree(dy);
+    if (st != CSC_OK) return st;
+    // the half-width factor, calibrated on the held-back samples (the fitted ones if none)
+    const int c0 = n_val ? n_fit : 0, nc = n_val ? n_val : n_fit;
+    std::vector<double> pt((size_t)2 * nc);
+    CSC_TRY(predict_targets(params, norm_out, feats + (size_t)c0 * CSC_MLP_IN, nc, pt.data(), s));
+    const double* br = brackets + 2 * (size_t)c0;
+    double widen = 1.0;
+    if (widen_rule == 1) {
+        // the smallest factor at which a `coverage` share of the predictions meet their brackets
+        std::vector<double> need(nc);
+        for (int i = 0; i < nc; ++i) {
+            const double c = pt[2 * (size_t)i], hw = exp(pt[2 * (size_t)i + 1]);
+            const double lo = br[2 * (size_t)i], hi = br[2 * (size_t)i + 1];
+            const double dist = c < lo ? lo - c : (c > hi ? c - hi : 0.0);
+            need[i] = dist / hw;
+        }
+        std::sort(need.begin(), need.end());
+        const double pos = coverage * (nc - 1);
+        const int i0 = (int)floor(pos), i1 = std::min(nc - 1, i0 + 1);
+        const double q = need[i0] + (pos - i0) * (need[i1] - need[i0]);
+        widen = std::max(1.0, q);
+    } else {
+        // the factor on the grid 0.25 * 2^(j/4), j = 0..56, with the fewest mean evaluations
+        double best = 1e300;
+        for (int j = 0; j <= 56; ++j) {
+            const double w = 0.25 * exp2(j / 4.0);
+            double cost = 0.0;
+            for (int i = 0; i < nc; ++i)
+                cost += search_evaluations(pt[2 * (size_t)i], w * exp(std::min(pt[2 * (size_t)i + 1], 10.0)),
+                                           br[2 * (size_t)i], br[2 * (size_t)i + 1]);
+            cost /= nc;
+            if (cost < best) {
+                best = cost;
+                widen = w;
+            }
+        }
+    }
+    *widen_out = widen;
+    if (n_fit_out) *n_fit_out = n_fit;
+    return CSC_OK;
+}
+
+extern "C" CSC_API csc_status csc_bracket_predict(const float* params, const float* norm, double widen,
+                                                  const float* feats, int32_t n, double* targets_out,
+                                                  double* brackets_out, void* stream) {
+    clear_error();
+    if (!params || !norm || !feats || n < 1 || !(widen > 0.0) || (!targets_out && !brackets_out)) {
+        set_error("csc_bracket_predict: invalid arguments (n=%d)", n);
+        return CSC_E_INVALID;
+    }
+    std::vector<double> t((size_t)2 * n);
+    CSC_TRY(predict_targets(params, norm, feats, n, t.data(), (cudaStream_t)stream));
+    for (int i = 0; i < n; ++i) {
+        const double c = t[2 * (size_t)i], lnhw = t[2 * (size_t)i + 1];
+        if (targets_out) {
+            targets_out[2 * (size_t)i] = c;
+            targets_out[2 * (size_t)i + 1] = lnhw;
+        }
+        if (brackets_out) {
+            // as csc_estimate_lambda_k_learned: widen * exp(ln half-width), clipped to [0, 2]
+            const double hw = widen * exp(std::min(lnhw, 10.0));
+            brackets_out[2 * (size_t)i] = std::max(0.0, c - hw);
+            brackets_out[2 * (size_t)i + 1] = std::min(2.0, c + hw);
+        }
+    }
+    return CSC_OK;
 }

@@ -443,8 +443,8 @@ static csc_status launch_cheb_step(Graph* g, const LaunchCfg& cfg, const T* xcur
 }
 
 template <typename T>
-static int kernel_occupancy(int kind, const TileShape& sh, int threads) {
-    if (kind == KK_CLEN) return clenshaw_occupancy<T>(sh, threads);
+static int kernel_occupancy(int kind, const TileShape& sh, int threads, bool lean = false) {
+    if (kind == KK_CLEN) return clenshaw_occupancy<T>(sh, threads, lean);
     if (kind == KK_MOM) {
         if constexpr (sizeof(T) <= 4) return mom_occupancy<T>(sh, threads);
         return 1;
@@ -480,33 +480,38 @@ static std::vector<LaunchCfg> candidates(Graph* g, int kind, int nv) {
         const int waste = tiles * cap - nv;
         if (3 * waste > tiles * cap && waste > min_waste) continue;
         for (int th : kThreadChoices) {
-            LaunchCfg c;
-            c.G = sh.G;
-            c.NT = sh.NT;
-            c.threads = th;
-            c.tiles = tiles;
-            const int occ = kernel_occupancy<T>(kind, sh, th);
-            const int64_t max_p = (g->N + (th / sh.G) - 1) / (th / sh.G);  // at least one row per group
-            // one to eight waves of resident CTAs: more, shorter row ranges balance SMs that
-            // run at different speeds (distance to the memory holding their rows)
-            for (int waves = 1; waves <= 8; waves *= 2) {
-                int P = (g->num_sms * occ * waves + tiles - 1) / tiles;
-                if (P > max_p) P = (int)max_p;
-                if (P < g->n_graphs) P = g->n_graphs;  // a batch needs a range per graph
-                P = P < 1 ? 1 : P;
-                // the CTA's staged CSR slice must fit shared memory: more, shorter ranges if not
-                if (fit_staged_partition(g, P, std::max<int64_t>(max_p, g->n_graphs), &P) != CSC_OK ||
-                    staged_smem(g, P) > kStagedSmemMax)
-                    continue;
-                c.P = P;
-                if (!out.empty() && out.back().G == c.G && out.back().NT == c.NT && out.back().threads == th &&
-                    out.back().P == c.P)
-                    continue;
-                // both index sources (sweep_rows): the staged slice, and global loads
-                c.staged = 1;
-                out.push_back(c);
-                c.staged = 0;
-                out.push_back(c);
+            // the lean form (LaunchCfg::lean) exists for the Clenshaw orders, NT = 1, 256 threads
+            for (int lean = 0; lean <= 1; ++lean) {
+                if (lean && !(kind == KK_CLEN && sh.NT == 1 && th == 256)) continue;
+                LaunchCfg c;
+                c.G = sh.G;
+                c.NT = sh.NT;
+                c.threads = th;
+                c.tiles = tiles;
+                c.lean = lean;
+                const int occ = kernel_occupancy<T>(kind, sh, th, lean != 0);
+                const int64_t max_p = (g->N + (th / sh.G) - 1) / (th / sh.G);  // at least one row per group
+                // one to eight waves of resident CTAs: more, shorter row ranges balance SMs that
+                // run at different speeds (distance to the memory holding their rows)
+                for (int waves = 1; waves <= 8; waves *= 2) {
+                    int P = (g->num_sms * occ * waves + tiles - 1) / tiles;
+                    if (P > max_p) P = (int)max_p;
+                    if (P < g->n_graphs) P = g->n_graphs;  // a batch needs a range per graph
+                    P = P < 1 ? 1 : P;
+                    // the CTA's staged CSR slice must fit shared memory: more, shorter ranges if not
+                    if (fit_staged_partition(g, P, std::max<int64_t>(max_p, g->n_graphs), &P) != CSC_OK ||
+                        staged_smem(g, P) > kStagedSmemMax)
+                        continue;
+                    c.P = P;
+                    if (!out.empty() && out.back().G == c.G && out.back().NT == c.NT &&
+                        out.back().threads == th && out.back().lean == lean && out.back().P == c.P)
+                        continue;
+                    // both index sources (sweep_rows): the staged slice, and global loads
+                    c.staged = 1;
+                    out.push_back(c);
+                    c.staged = 0;
+                    out.push_back(c);
+                }
             }
         }
     }
@@ -719,9 +724,9 @@ static csc_status filter_typed(Graph* g, const double* c, int m, int d, int d_pa
         };
         if (graphs) {
             char key[320];
-            snprintf(key, sizeof(key), "clen:%zu:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p", sizeof(T), d_pad, m, d,
-                     (int)fused_norm, cfg.G, cfg.NT, cfg.threads, cfg.P, cfg.tiles, cfg.staged, (const void*)RS,
-                     (void*)X[0], (void*)X[1], (void*)Y, (const void*)tab.c);
+            snprintf(key, sizeof(key), "clen:%zu:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%p:%p:%p:%p:%p", sizeof(T), d_pad, m,
+                     d, (int)fused_norm, cfg.G, cfg.NT, cfg.threads, cfg.P, cfg.tiles, cfg.staged, cfg.lean,
+                     (const void*)RS, (void*)X[0], (void*)X[1], (void*)Y, (const void*)tab.c);
             int64_t launches = 0;
             const int32_t* pr = nullptr;
             CSC_TRY(get_partition(g, cfg.P, &pr));  // before the capture

@@ -106,7 +106,7 @@ csc_status launch_clenshaw_step(Graph* g, const LaunchCfg& cfg, const T* bnext, 
                                 const T* rs, cudaStream_t s, CoefTab<typename StoreTraits<T>::acc_t> tab = {},
                                 bool internal = false);
 template <typename T>
-int clenshaw_occupancy(const TileShape& sh, int threads);
+int clenshaw_occupancy(const TileShape& sh, int threads, bool lean);
 
 // One eigencount moment step (spmm_moments.cu); float and __nv_bfloat16 storage.
 template <typename T>

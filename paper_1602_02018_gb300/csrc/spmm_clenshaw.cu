@@ -126,8 +126,8 @@ __device__ __forceinline__ void clenshaw_epilogue(int row, int lane, int col0, i
     }
 }
 
-template <typename T, int G, int NT, bool LAST, bool STAGED>
-__global__ void __launch_bounds__(512)
+template <typename T, int G, int NT, bool LAST, bool STAGED, bool LEAN>
+__global__ void __launch_bounds__(LEAN ? 256 : 512, LEAN ? 5 : 0)
 clenshaw_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const int32_t* __restrict__ lrp,
                      const int32_t* __restrict__ lci,
                      const typename StoreTraits<T>::acc_t* __restrict__ invdeg,
@@ -154,7 +154,7 @@ clenshaw_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__
         ClenOperands<T, G, NT> op;
         op.load(row, lane, col0, tcols, mode, rs, bpp, ld, invdeg);
         A acc[NT][VEC];
-        gather_any<STAGED, T, G, NT, false, A>(e0, e1, idx, nullptr, bnext + col0, ld, lane, tcols, acc);
+        gather_any<STAGED, T, G, NT, false, A, LEAN>(e0, e1, idx, nullptr, bnext + col0, ld, lane, tcols, acc);
         clenshaw_epilogue<T, G, NT, LAST>(row, lane, col0, tcols, acc, invdeg, sqdeg, bpp, Y, perm, ld, cj, mode, op,
                                           gmask);
     });
@@ -236,36 +236,47 @@ csc_status launch_clenshaw_step(Graph* g, const LaunchCfg& cfg, const T* bnext, 
     };
     auto light = [&](cudaStream_t st) -> csc_status {
         const double lb = all_bytes * (1.0 - heavy_frac);
-        if (last && cfg.staged)
-            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", lb, st,
-                                              clenshaw_step_kernel<T, GG, NN, true, true><<<grid, cfg.threads, smem, st>>>(
-                                                  g->row_ptr, g->col_idx, g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm,
-                                                  part, ncols, ld, (A)cj, mode, tab, rs)));
-        else if (last)
-            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", lb, st,
-                                              clenshaw_step_kernel<T, GG, NN, true, false><<<grid, cfg.threads, 0, st>>>(
-                                                  g->row_ptr, g->col_idx, g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm,
-                                                  part, ncols, ld, (A)cj, mode, tab, rs)));
-        else if (cfg.staged)
-            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", lb, st,
-                                              clenshaw_step_kernel<T, GG, NN, false, true><<<grid, cfg.threads, smem, st>>>(
-                                                  g->row_ptr, g->col_idx, g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm,
-                                                  part, ncols, ld, (A)cj, mode, tab, rs)));
-        else
-            CSC_SHAPE_SWITCH(cfg, CSC_KLAUNCH("cheb_step", lb, st,
-                                              clenshaw_step_kernel<T, GG, NN, false, false><<<grid, cfg.threads, 0, st>>>(
-                                                  g->row_ptr, g->col_idx, g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm,
-                                                  part, ncols, ld, (A)cj, mode, tab, rs)));
+        // the lean form is compiled for NT = 1 only (LaunchCfg::lean)
+#define CSC_CLEN(LASTV, STG, LN)                                                                              \
+    CSC_SHAPE_SWITCH(cfg, if constexpr (!(LN) || NN == 1) {                                                   \
+        CSC_KLAUNCH("cheb_step", lb, st,                                                                      \
+                    (clenshaw_step_kernel<T, GG, NN, LASTV, STG, LN><<<grid, cfg.threads, (STG) ? smem : 0, st>>>( \
+                        g->row_ptr, g->col_idx, g->lrp, g->lci, idg, sqd, bnext, bpp, Y, perm, part, ncols, ld,    \
+                        (A)cj, mode, tab, rs)));                                                              \
+    } else {                                                                                                  \
+        set_error("the lean Clenshaw kernel needs NT = 1");                                                   \
+        return CSC_E_UNSUPPORTED;                                                                             \
+    })
+        if (cfg.lean) {
+            if (last && cfg.staged) CSC_CLEN(true, true, true);
+            else if (last) CSC_CLEN(true, false, true);
+            else if (cfg.staged) CSC_CLEN(false, true, true);
+            else CSC_CLEN(false, false, true);
+        } else {
+            if (last && cfg.staged) CSC_CLEN(true, true, false);
+            else if (last) CSC_CLEN(true, false, false);
+            else if (cfg.staged) CSC_CLEN(false, true, false);
+            else CSC_CLEN(false, false, false);
+        }
+#undef CSC_CLEN
         return CSC_OK;
     };
     return fork_join(g, s, g->n_heavy > 0, heavy, light);
 }
 
 template <typename T>
-int clenshaw_occupancy(const TileShape& sh, int threads) {
+int clenshaw_occupancy(const TileShape& sh, int threads, bool lean) {
     int occ = 1;
+    if (lean) {
+        if (sh.NT != 1) return 1;
+#define CSC_OCC_LEAN(GG) \
+    if (sh.G == GG) occ = occupancy(clenshaw_step_kernel<T, GG, 1, false, true, true>, threads);
+        CSC_OCC_LEAN(2) CSC_OCC_LEAN(4) CSC_OCC_LEAN(8) CSC_OCC_LEAN(16) CSC_OCC_LEAN(32)
+#undef CSC_OCC_LEAN
+        return occ;
+    }
 #define CSC_OCC_CASE(GG, NN) \
-    if (sh.G == GG && sh.NT == NN) occ = occupancy(clenshaw_step_kernel<T, GG, NN, false, true>, threads);
+    if (sh.G == GG && sh.NT == NN) occ = occupancy(clenshaw_step_kernel<T, GG, NN, false, true, false>, threads);
     CSC_OCC_CASE(2, 1) CSC_OCC_CASE(2, 2) CSC_OCC_CASE(2, 3) CSC_OCC_CASE(4, 1) CSC_OCC_CASE(4, 2)
     CSC_OCC_CASE(4, 3) CSC_OCC_CASE(8, 1) CSC_OCC_CASE(8, 2) CSC_OCC_CASE(8, 3) CSC_OCC_CASE(16, 1)
     CSC_OCC_CASE(16, 2) CSC_OCC_CASE(32, 1) CSC_OCC_CASE(32, 2)
@@ -278,7 +289,7 @@ int clenshaw_occupancy(const TileShape& sh, int threads) {
                                                 typename StoreTraits<T>::acc_t*, int, int64_t, double, int,     \
                                                 const T*, cudaStream_t, CoefTab<typename StoreTraits<T>::acc_t>, \
                                                 bool);                                                          \
-    template int clenshaw_occupancy<T>(const TileShape&, int);
+    template int clenshaw_occupancy<T>(const TileShape&, int, bool);
 CSC_INST(float)
 CSC_INST(__nv_bfloat16)
 CSC_INST(double)

@@ -213,6 +213,12 @@ def test_pin_shape_rejects_bad_shapes():
             csc.csc_graph_pin_shape(h, "cg", 4, 200, 32, 2, 256, 10, 1, -1)       # index source 0 or 1
         with pytest.raises(csc.CscError):
             csc.csc_graph_pin_shape(h, "cheb_step", 4, 48, 4, 3, 256, 10, 1, 2)    # index source 0 or 1
+        with pytest.raises(csc.CscError):
+            csc.csc_graph_pin_shape(h, "cheb_step", 4, 48, 4, 3, 256, 10, 1, 0, 1)  # lean: Clenshaw and CG only
+        with pytest.raises(csc.CscError):
+            csc.csc_graph_pin_shape(h, "clenshaw", 4, 48, 4, 3, 256, 10, 1, 0, 1)   # lean: NT = 1 only
+        with pytest.raises(csc.CscError):
+            csc.csc_graph_pin_shape(h, "cg", 4, 48, 16, 1, 512, 10, 1, 0, 1)        # lean: 256 threads only
 
 
 def test_graph_replay_matches_eager_launches():
@@ -285,6 +291,29 @@ def test_clenshaw_every_compiled_shape(G, NT, threads, global_index):
         y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, R_in=torch.from_numpy(r).cuda(),
                                           flags=csc.CLENSHAW | csc.NORMALIZE_ROWS).cpu().numpy()
     assert rel(y, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("G", [2, 4, 8, 16, 32])
+@pytest.mark.parametrize("global_index", [0, 1])
+@pytest.mark.parametrize("storage,tol", [(0, 1e-5), (1, 5e-2)])
+def test_clenshaw_lean_form(G, global_index, storage, tol):
+    """The lean form (at most 4 neighbour rows in flight per lane, 5 CTAs of 256 threads per
+    SM) of every one-vector shape, both index sources, fp32 and bf16 storage; the tuned-shape
+    report gives the pinned variant back."""
+    g = GRAPHS[6][1]
+    d, d_pad, m, lam = 47, 48, 20, 0.43
+    vec = 8 if storage == 1 else 4
+    tiles = -(-(d_pad // vec) // G)
+    r = ci.gaussian_block(g.n, d, d_pad, seed=3)
+    ref = _oracle_filter(g, r.astype(np.float64), lam, m, normalize=True)
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM) as h:
+        csc.csc_graph_pin_shape(h, "clenshaw", 2 if storage == 1 else 4, d_pad, G, 1, 256, 37, tiles, global_index,
+                                lean=1)
+        shapes = csc.csc_graph_tuned_shapes(h)
+        y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, storage=storage, R_in=torch.from_numpy(r).cuda(),
+                                          flags=csc.CLENSHAW | csc.NORMALIZE_ROWS).cpu().numpy()
+    assert [x["lean"] for x in shapes] == [1] and shapes[0]["global_index"] == global_index
+    assert rel(y, ref) <= tol
 
 
 @pytest.mark.parametrize("storage,tol", [(1, 5e-2), (2, 1e-12)])

@@ -107,8 +107,8 @@ def test_moments_heavy(gname):
 
 
 @pytest.mark.parametrize("power", [1, 2, 4])
-@pytest.mark.parametrize("G,NT,threads", [(2, 1, 256), (8, 1, 512), (32, 2, 256)])
-def test_interpolation_heavy(power, G, NT, threads):
+@pytest.mark.parametrize("G,NT,threads,lean", [(2, 1, 256, 0), (8, 1, 512, 0), (32, 2, 256, 0), (8, 1, 256, 1)])
+def test_interpolation_heavy(power, G, NT, threads, lean):
     """CG on the hub graph: the first product of the chain (weighted) and the fused
     A p product both take the heavy-row path; <p, A p> sums their partials."""
     g = HUB
@@ -119,7 +119,7 @@ def test_interpolation_heavy(power, G, NT, threads):
     x_ref, _, _ = ointerp.interpolate(lap, om, lab, k, 1e-3, power, tol=1e-11)
     tiles = -(-(ld // 4) // (G * NT))
     with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
-        csc.csc_graph_pin_shape(h, "cg", 4, ld, G, NT, threads, 19, tiles, 0)
+        csc.csc_graph_pin_shape(h, "cg", 4, ld, G, NT, threads, 19, tiles, 0, lean)
         labels, fz, info = csc.csc_interpolate(h, torch.from_numpy(om).cuda(), torch.from_numpy(lab).cuda(), k,
                                                power, 1e-3, 1e-7, 5000, fuzzy=True)
     assert info.converged and info.max_rel_residual <= 1e-6

@@ -191,14 +191,48 @@ def test_training_reduces_loss(trained):
 
 
 def test_held_out_coverage(trained):
-    from paper_1602_02018_gb300 import learned
-
     nt = trained["n_train"]
     pred = trained["model"].predict_brackets(trained["feats"][nt:])
-    cov = learned.covered(pred, trained["brs"][nt:])
+    br = trained["brs"][nt:]
+    cov = (pred[:, 0] <= br[:, 1]) & (pred[:, 1] >= br[:, 0])  # prediction meets the target bracket
     assert cov.mean() >= 0.7
     # narrower than the dichotomy's [0, 2]
     assert np.median(pred[:, 1] - pred[:, 0]) < 0.5
+
+
+def test_prediction_is_the_bracket_the_estimate_starts_from(trained):
+    """csc_bracket_predict gives, from a graph's features, the bracket that
+    csc_estimate_lambda_k_learned computes inside for the same graph."""
+    nt = trained["n_train"]
+    model = trained["model"]
+    pred = model.predict_brackets(trained["feats"][nt:nt + 8])
+    for i, (g, k) in enumerate(trained["graphs"][nt:nt + 8]):
+        with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
+            _, br = model.estimate(h, k, 50, 0, 0)
+        assert np.allclose(br, pred[i], rtol=0, atol=1e-9), (br, pred[i])
+
+
+def test_fit_coverage_rule_meets_its_share(trained):
+    """widen_rule "coverage": with the calibrated factor, at least the asked share of the
+    held-back samples' predicted intervals meet their target brackets; the fitted and
+    held-back split follows val_frac."""
+    from paper_1602_02018_gb300 import learned
+
+    nt = trained["n_train"]
+    feats, brs = trained["feats"][:nt], trained["brs"][:nt]
+    model = learned.BracketModel.fit(feats, brs, epochs=60, batch=32, lr=1e-3, seed=1, coverage=0.8,
+                                     widen_rule="coverage")
+    assert model.n_val == round(0.15 * nt) and model.n_fit + model.n_val == nt and model.widen >= 1.0
+    pred = model.predict_brackets(feats[model.n_fit:])
+    br = brs[model.n_fit:]
+    cov = (pred[:, 0] <= br[:, 1]) & (pred[:, 1] >= br[:, 0])
+    # the interpolated 0.8 quantile of the needed factors lies at or above the
+    # floor(0.8 (n - 1)) + 1 smallest of them
+    n = len(br)
+    assert cov.sum() >= np.floor(0.8 * (n - 1)) + 1
+    t = model.predict_targets(feats[model.n_fit:])
+    hw = model.widen * np.exp(np.minimum(t[:, 1], 10.0))
+    assert np.allclose(pred[:, 0], np.maximum(0.0, t[:, 0] - hw)) and np.allclose(pred[:, 1], np.minimum(2.0, t[:, 0] + hw))
 
 
 def test_gain_over_the_paper_literal_dichotomy(trained):

@@ -196,10 +196,11 @@ def test_interpolation_bad_label_rejected():
             csc.csc_interpolate(h, torch.from_numpy(om).cuda(), torch.from_numpy(lab).cuda(), 5)
 
 
-@pytest.mark.parametrize("G,NT", [(2, 1), (4, 1), (8, 1), (16, 1), (16, 2), (32, 1), (32, 2)])
+@pytest.mark.parametrize("G,NT,lean", [(2, 1, 0), (4, 1, 0), (8, 1, 0), (16, 1, 0), (16, 2, 0), (32, 1, 0), (32, 2, 0),
+                                       (2, 1, 1), (4, 1, 1), (8, 1, 1), (16, 1, 1), (32, 1, 1)])
 @pytest.mark.parametrize("threads", [256, 512])
 @pytest.mark.parametrize("global_index", [0, 1])
-def test_interpolation_every_cg_shape(G, NT, threads, global_index):
+def test_interpolation_every_cg_shape(G, NT, lean, threads, global_index):
     g = ci.sbm(600, 6, seed=2)
     lap = olap.laplacian(g.row_ptr, g.col_idx)
     om = osamp.sample(g.n, 40, 2)
@@ -207,8 +208,10 @@ def test_interpolation_every_cg_shape(G, NT, threads, global_index):
     k, ld = 6, 8
     tiles = -(-(ld // 4) // (G * NT))
     x_ref, _, _ = ointerp.interpolate(lap, om, lab, k, 1e-3, 4, tol=1e-11)
+    if lean and threads != 256:
+        pytest.skip("the lean form runs 256 threads")
     with csc.csc_graph_create(g.row_ptr, g.col_idx) as h:
-        csc.csc_graph_pin_shape(h, "cg", 4, ld, G, NT, threads, 23, tiles, global_index)
+        csc.csc_graph_pin_shape(h, "cg", 4, ld, G, NT, threads, 23, tiles, global_index, lean)
         labels, fz, info = csc.csc_interpolate(h, torch.from_numpy(om).cuda(), torch.from_numpy(lab).cuda(), k,
                                                4, 1e-3, 1e-7, 5000, fuzzy=True)
     assert info.converged
