@@ -358,6 +358,19 @@ static void dichotomy(const double* mu, int m, int k, double lo, double hi, csc_
 void estimate_from_moments(const double* mu, int m, int k, csc_lambda_info* out) { dichotomy(mu, m, k, 0.0, 2.0, out); }
 
 // --------------------------------------------------------- reverse Cuthill-McKee
+// Stable counting sort of ids by a small integer key (degrees): the same order as a stable
+// comparison sort by that key, in O(N + max key) without per-call allocations.
+static void stable_sort_by_key(std::vector<int32_t>& ids, const std::vector<int32_t>& key, bool decreasing) {
+    int32_t kmax = 0;
+    for (int32_t v : ids) kmax = std::max(kmax, key[v]);
+    std::vector<int64_t> start((size_t)kmax + 2, 0);
+    for (int32_t v : ids) ++start[(size_t)(decreasing ? kmax - key[v] : key[v]) + 1];
+    for (size_t b = 1; b < start.size(); ++b) start[b] += start[b - 1];
+    std::vector<int32_t> out(ids.size());
+    for (int32_t v : ids) out[(size_t)start[(size_t)(decreasing ? kmax - key[v] : key[v])]++] = v;
+    ids.swap(out);
+}
+
 // Cuthill & McKee (1969), reversed (George 1971): BFS from a minimum-degree
 // node of each component, visiting neighbours by increasing degree; the
 // visit order reversed gives perm[new] = old (then sorted by degree within
@@ -368,7 +381,7 @@ static void rcm_order(int64_t N, const std::vector<int64_t>& rp, const std::vect
     for (int64_t i = 0; i < N; ++i) deg[i] = (int32_t)(rp[i + 1] - rp[i]);
     std::vector<int32_t> order(N);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return deg[a] < deg[b]; });
+    stable_sort_by_key(order, deg, false);
     std::vector<char> seen(N, 0);
     std::vector<int32_t> visit;
     visit.reserve(N);
@@ -387,7 +400,18 @@ static void rcm_order(int64_t N, const std::vector<int64_t>& rp, const std::vect
                     seen[ci[e]] = 1;
                     nb.push_back(ci[e]);
                 }
-            std::stable_sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) { return deg[a] < deg[b]; });
+            // neighbours by increasing degree, ties in index order (a stable sort); short
+            // lists by insertion, which allocates nothing
+            if (nb.size() <= 32) {
+                for (size_t i = 1; i < nb.size(); ++i) {
+                    const int32_t v = nb[i];
+                    size_t j = i;
+                    for (; j > 0 && deg[nb[j - 1]] > deg[v]; --j) nb[j] = nb[j - 1];
+                    nb[j] = v;
+                }
+            } else {
+                std::stable_sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) { return deg[a] < deg[b]; });
+            }
             visit.insert(visit.end(), nb.begin(), nb.end());
         }
     }
@@ -718,9 +742,9 @@ csc_status csc_graph_create(int64_t N, int64_t nnz, const int64_t* row_ptr, cons
         }
         if (flags & CSC_DEGREE_ORDER) {
             // decreasing degree: the rows most neighbours gather come first, back to back
-            std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) {
-                return clean.rp[a + 1] - clean.rp[a] > clean.rp[b + 1] - clean.rp[b];
-            });
+            std::vector<int32_t> deg(N);
+            for (int64_t i = 0; i < N; ++i) deg[i] = (int32_t)(clean.rp[i + 1] - clean.rp[i]);
+            stable_sort_by_key(perm, deg, true);
         }
         HostCSR pc;
         permute_csr(clean, perm, pc);

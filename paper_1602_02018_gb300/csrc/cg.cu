@@ -697,26 +697,28 @@ __global__ void label_argmax_kernel(const float* __restrict__ x, const double* _
     }
 }
 
-// Column compaction of the CG blocks: in each of a, b, c (N x ld, row-major) the
-// columns [0, kw) of every row become old[src[s]] at slot s.  One warp per row copies
-// the row's kw entries to its slice of shared memory before writing them back, so the
-// permutation is done in place.
-__global__ void permute_columns_kernel(float* __restrict__ a, float* __restrict__ b, float* __restrict__ c,
-                                       const int32_t* __restrict__ src, int kw, int64_t ld, int32_t N) {
-    extern __shared__ float s_row[];
+// Column compaction of the CG blocks, into dense blocks of the new width: for every row,
+// slot s < nw of the new x, r, p (row stride ln) takes slot src[s] of the old ones (row
+// stride lo), and the x of each column leaving the iteration (old slot lv_slot[q]) goes to
+// column lv_col[q] of xf, the solution in column order (row stride ldf).  One warp per row;
+// out of place.
+__global__ void compact_columns_kernel(const float* __restrict__ ox, const float* __restrict__ orr,
+                                       const float* __restrict__ op, int lo, float* __restrict__ nx,
+                                       float* __restrict__ nr, float* __restrict__ np, int ln,
+                                       const int32_t* __restrict__ src, int nw, const int32_t* __restrict__ lv_slot,
+                                       const int32_t* __restrict__ lv_col, int nlv, float* __restrict__ xf, int ldf,
+                                       int32_t N) {
     const int lane = threadIdx.x & 31;
-    float* buf = s_row + (threadIdx.x >> 5) * kw;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < N; row += nw) {
-        float* blocks[3] = {a, b, c};
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            float* v = blocks[q] + row * ld;
-            for (int j = lane; j < kw; j += 32) buf[j] = v[j];
-            __syncwarp();
-            for (int j = lane; j < kw; j += 32) v[j] = buf[src[j]];
-            __syncwarp();
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < N; row += nwarps) {
+        const int64_t o = row * lo, n = row * ln;
+        for (int j = lane; j < nw; j += 32) {
+            const int sj = src[j];
+            nx[n + j] = ox[o + sj];
+            nr[n + j] = orr[o + sj];
+            np[n + j] = op[o + sj];
         }
+        for (int q = lane; q < nlv; q += 32) xf[row * ldf + lv_col[q]] = ox[o + lv_slot[q]];
     }
 }
 
@@ -934,7 +936,9 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     const int max_slices = std::max(1, ceil_div(max_p + (int)g->n_heavy, kSliceSlots));
     const size_t o_lvl2 = take((size_t)nchunks * max_slices * 2 * 32 * 8);
     const size_t o_cnt = take((size_t)nchunks * 4);
-    const size_t o_src = take((size_t)ld * 4);  // column permutation of a compaction
+    const size_t o_src = take((size_t)3 * ld * 4);  // slot maps of a compaction
+    const bool compact = !hp && nseg == 1 && ld <= 1024;  // column compaction (see below)
+    const size_t o_xf = take(compact ? blk : 0);          // the solution in column order
     void* base = nullptr;
     CSC_TRY(ws_get(g, WS_CG, off, &base));
     char* b = (char*)base;
@@ -965,6 +969,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     double* lvl2 = (double*)(b + o_lvl2);
     int* red_cnt = (int*)(b + o_cnt);
     int32_t* d_src = (int32_t*)(b + o_src);
+    float* xf = compact ? (float*)(b + o_xf) : nullptr;
     int32_t* d_gk = nullptr;
     const int32_t* gid = nullptr;
     CgBatch bt, bt_all;  // bt also skips finished graphs; bt_all only narrows the columns
@@ -1117,12 +1122,16 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     }
     // Column compaction (one graph, g = L^p): a column whose CG has converged keeps its x
     // and leaves the iteration.  At a convergence check that finds at least 8 slots (or
-    // half of them) idle, the active columns move to the front slots (x, r, p permuted in
-    // place, their scalars on the host) and every kernel of the following iterations covers
-    // the first kw slots only, with a launch shape narrowed to that width; slot_col[s] is
-    // the column held in slot s.  Each column's arithmetic is unchanged by its slot.
-    const bool compact = !hp && nseg == 1 && ld <= 1024;
+    // half of them) idle, x, r and p are rewritten as dense blocks of the columns still
+    // iterating (row stride kw: the rows stay contiguous in memory), the x of the columns
+    // leaving goes to xf in column order, their scalars follow on the host, and every kernel
+    // of the following iterations covers the kw slots only, with a launch shape narrowed to
+    // that width; slot_col[s] is the column held in slot s.  Each column's arithmetic is
+    // unchanged by its slot.
     int kw = ld;          // slots the iterations cover
+    int lw = ld;          // row stride of the iteration blocks (kw once compacted)
+    bool compacted = false;
+    std::vector<double> bn2_col(ld, 0.0);  // ||b_j||^2 by column, kept on the host
     int kcols = k;        // columns the scalar kernels cover (slots past them are idle)
     LaunchCfg wcfg = cfg; // launch shape of the iterations at width kw
     dim3 wgrid = grid, whgrid = hgrid;
@@ -1152,7 +1161,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
             CSC_TRY(poly_apply(g, op, in, t1, s));
             CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax", 4.0 * N + 3 * blkb + scal_b, s,
                                        hp_ax_kernel<G_, NT_><<<wgrid, th, 0, s>>>(in, t1, mask, (float)gamma, Ap, rpart,
-                                                                                 kw, ld, part, bb)));
+                                                                                 kw, lw, part, bb)));
             return CSC_OK;
         }
         // t = L^(p-1) in, then Ap = mask*in + gamma * L t with <in, Ap> partials; each product's
@@ -1169,13 +1178,13 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                 if (win)
                     CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_heavy", lb * heavy_frac, st,
                                                lap_heavy_kernel<G_, NT_, true><<<whgrid, kHeavyThreads, 0, st>>>(
-                                                   g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, g->heavy, ld,
-                                                   ld, bb)));
+                                                   g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, g->heavy, kw,
+                                                   lw, bb)));
                 else
                     CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_heavy", lb * heavy_frac, st,
                                                lap_heavy_kernel<G_, NT_, false><<<whgrid, kHeavyThreads, 0, st>>>(
-                                                   g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, g->heavy, ld,
-                                                   ld, bb)));
+                                                   g->row_ptr, g->col_idx, g->dinv, g->invdeg, cur, o, g->heavy, kw,
+                                                   lw, bb)));
                 return CSC_OK;
             };
             auto light = [&](cudaStream_t st) -> csc_status {
@@ -1183,11 +1192,11 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                 if (win)
                     CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap", by, st,
                                                 lap_rows<G_, NT_, true>(wcfg, wgrid, csmem, st, g, cur, o, rpart, kw,
-                                                                        ld, bb)));
+                                                                        lw, bb)));
                 else
                     CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap", by, st,
                                                 lap_rows<G_, NT_, false>(wcfg, wgrid, csmem, st, g, cur, o, rpart, kw,
-                                                                         ld, bb)));
+                                                                         lw, bb)));
                 return CSC_OK;
             };
             CSC_TRY(fork_join(g, s, H > 0, heavy, light));
@@ -1201,12 +1210,12 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                 CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax_heavy", ab * heavy_frac, st,
                                            lap_ax_heavy_kernel<G_, NT_, true><<<whgrid, kHeavyThreads, 0, st>>>(
                                                g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma,
-                                               Ap, g->heavy, kw, ld, part, P, PH, bb)));
+                                               Ap, g->heavy, kw, lw, part, P, PH, bb)));
             else
                 CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax_heavy", ab * heavy_frac, st,
                                            lap_ax_heavy_kernel<G_, NT_, false><<<whgrid, kHeavyThreads, 0, st>>>(
                                                g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma,
-                                               Ap, g->heavy, kw, ld, part, P, PH, bb)));
+                                               Ap, g->heavy, kw, lw, part, P, PH, bb)));
             return CSC_OK;
         };
         auto light = [&](cudaStream_t st) -> csc_status {
@@ -1214,11 +1223,11 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
             if (win)
                 CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax", by, st,
                                             lap_ax_rows<G_, NT_, true>(wcfg, wgrid, csmem, st, g, cur, in, mask,
-                                                                       (float)gamma, Ap, rpart, kw, ld, part, PH, bb)));
+                                                                       (float)gamma, Ap, rpart, kw, lw, part, PH, bb)));
             else
                 CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax", by, st,
                                             lap_ax_rows<G_, NT_, false>(wcfg, wgrid, csmem, st, g, cur, in, mask,
-                                                                        (float)gamma, Ap, rpart, kw, ld, part, PH,
+                                                                        (float)gamma, Ap, rpart, kw, lw, part, PH,
                                                                         bb)));
             return CSC_OK;
         };
@@ -1230,18 +1239,18 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         for (int q = 0; q < count; ++q) {
             CSC_TRY(apply_A(p, bt, s));
             CSC_KLAUNCH("cg_scalar", scal_ax, s,
-                        cg_alpha_kernel<<<kb_ax, rb, 0, s>>>(part, PH, sg, kcols, ld, st, lvl2, red_cnt));
+                        cg_alpha_kernel<<<kb_ax, rb, 0, s>>>(part, PH, sg, kcols, lw, st, lvl2, red_cnt));
             // x, r, p, Ap read; x, r written
             CG_SWITCH(wcfg, CSC_KLAUNCH("cg_update", 6 * blkb + 4.0 * N + 2 * scal_b, s,
                                        cg_update_kernel<G_, NT_><<<wgrid, th, 0, s>>>(x, r, p, Ap, st.alpha, gid, pinv,
-                                                                                     rpart, kw, ld, part, bt)));
+                                                                                     rpart, kw, lw, part, bt)));
             CSC_TRY(reset_active(s));
             CSC_KLAUNCH("cg_scalar", 2 * scal_b, s,
-                        cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, sg, kcols, ld, st, rel_tol * rel_tol, 0, lvl2,
+                        cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, sg, kcols, lw, st, rel_tol * rel_tol, 0, lvl2,
                                                          red_cnt));
             CG_SWITCH(wcfg, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
                                        cg_pupdate_kernel<G_, NT_><<<wgrid, th, 0, s>>>(r, p, st.beta, gid, pinv, rpart,
-                                                                                      kw, ld, bt)));
+                                                                                      kw, lw, bt)));
         }
         return CSC_OK;
     };
@@ -1267,8 +1276,8 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         converged = h_active[0] == 0;
         const int want = ((h_active[0] + 3) / 4) * 4;
         if (compact && !converged && it < max_iter && (want <= kw - 8 || 2 * want <= kw)) {
-            // the active slots first, in slot order, then the idle ones; per-slot scalars
-            // follow on the host
+            // new slots: the active ones in slot order, then idle ones up to the width `want`
+            // (they stay frozen); the other idle slots leave, their x going to xf
             std::vector<int> act(kw);
             std::vector<double> sc((size_t)5 * kw);
             double* cols[5] = {st.rz, st.bn2, st.alpha, st.beta, st.rr};
@@ -1277,61 +1286,76 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                 CSC_CUDA_TRY(cudaMemcpyAsync(sc.data() + (size_t)q * kw, cols[q], (size_t)kw * sizeof(double),
                                              cudaMemcpyDeviceToHost, s));
             CSC_CUDA_TRY(cudaStreamSynchronize(s));
-            std::vector<int32_t> src;
-            src.reserve(kw);
+            for (int j = 0; j < kw; ++j) bn2_col[slot_col[j]] = sc[(size_t)kw + j];
+            int n_act = 0;
+            for (int j = 0; j < kw; ++j) n_act += act[j] ? 1 : 0;
+            const int want_w = std::max(want, ((n_act + 3) / 4) * 4);  // every active slot is kept
+            std::vector<int32_t> maps;  // [src (want_w) | leaving slots | their columns]
+            maps.reserve((size_t)2 * kw);
             for (int j = 0; j < kw; ++j)
-                if (act[j]) src.push_back(j);
+                if (act[j]) maps.push_back(j);
+            std::vector<int32_t> leave;
             for (int j = 0; j < kw; ++j)
-                if (!act[j]) src.push_back(j);
-            std::vector<int> col2(kw), act2(kw);
-            std::vector<double> sc2((size_t)5 * kw);
-            for (int j = 0; j < kw; ++j) {
-                col2[j] = slot_col[src[j]];
-                act2[j] = act[src[j]];
-                for (int q = 0; q < 5; ++q) sc2[(size_t)q * kw + j] = sc[(size_t)q * kw + src[j]];
+                if (!act[j]) {
+                    if ((int)maps.size() < want_w) maps.push_back(j);
+                    else leave.push_back(j);
+                }
+            const int nlv = (int)leave.size();
+            std::vector<int> col2(want_w), act2(want_w);
+            std::vector<double> sc2((size_t)5 * want_w);
+            for (int j = 0; j < want_w; ++j) {
+                col2[j] = slot_col[maps[j]];
+                act2[j] = act[maps[j]];
+                for (int q = 0; q < 5; ++q) sc2[(size_t)q * want_w + j] = sc[(size_t)q * kw + maps[j]];
             }
+            for (int q = 0; q < nlv; ++q) maps.push_back(leave[q]);
+            for (int q = 0; q < nlv; ++q) maps.push_back(slot_col[leave[q]]);
             std::copy(col2.begin(), col2.end(), slot_col.begin());
-            CSC_CUDA_TRY(cudaMemcpyAsync(d_src, src.data(), (size_t)kw * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-            CSC_CUDA_TRY(cudaMemcpyAsync(st.active, act2.data(), (size_t)kw * sizeof(int), cudaMemcpyHostToDevice, s));
+            CSC_CUDA_TRY(cudaMemcpyAsync(d_src, maps.data(), maps.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            CSC_CUDA_TRY(
+                cudaMemcpyAsync(st.active, act2.data(), (size_t)want_w * sizeof(int), cudaMemcpyHostToDevice, s));
             for (int q = 0; q < 5; ++q)
-                CSC_CUDA_TRY(cudaMemcpyAsync(cols[q], sc2.data() + (size_t)q * kw, (size_t)kw * sizeof(double),
-                                             cudaMemcpyHostToDevice, s));
-            CSC_KLAUNCH("cg_compact", 6.0 * N * kw * 4, s,
-                        permute_columns_kernel<<<(int)std::min<int64_t>(ceil_div(N, 8), g->num_sms * 16), 256,
-                                                 8 * kw * sizeof(float), s>>>(x, r, p, d_src, kw, ld, N));
+                CSC_CUDA_TRY(cudaMemcpyAsync(cols[q], sc2.data() + (size_t)q * want_w,
+                                             (size_t)want_w * sizeof(double), cudaMemcpyHostToDevice, s));
+            // t1, t2 and Ap hold nothing between iterations: they take the dense blocks, and the
+            // old x, r, p become the scratch
+            CSC_KLAUNCH("cg_compact", 4.0 * N * (3.0 * kw + 3.0 * want_w + 2.0 * nlv), s,
+                        compact_columns_kernel<<<(int)std::min<int64_t>(ceil_div(N, 8), g->num_sms * 16), 256, 0,
+                                                 s>>>(x, r, p, lw, t1, t2, Ap, want_w, d_src, want_w, d_src + want_w,
+                                                      d_src + want_w + nlv, nlv, xf, ld, N));
+            std::swap(x, t1);
+            std::swap(r, t2);
+            std::swap(p, Ap);
             // the host vectors above are released when this scope ends: wait for the copies
             CSC_CUDA_TRY(cudaStreamSynchronize(s));
-            set_width(want);
+            compacted = true;
+            lw = want_w;
+            set_width(want_w);
         }
     }
-    if (compact) {
-        // back to column order: slot s of x holds column slot_col[s]; the idle slots past
-        // kw were never touched after their column finished
-        bool moved = false;
-        for (int j = 0; j < ld; ++j) moved |= slot_col[j] != j;
-        if (moved) {
-            std::vector<int32_t> src(ld);
-            for (int j = 0; j < ld; ++j) src[slot_col[j]] = j;
-            std::vector<double> sc((size_t)2 * ld), sc2((size_t)2 * ld);
-            double* cols[2] = {st.bn2, st.rr};
-            for (int q = 0; q < 2; ++q)
-                CSC_CUDA_TRY(cudaMemcpyAsync(sc.data() + (size_t)q * ld, cols[q], (size_t)ld * sizeof(double),
-                                             cudaMemcpyDeviceToHost, s));
-            CSC_CUDA_TRY(cudaMemcpyAsync(d_src, src.data(), (size_t)ld * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-            CSC_CUDA_TRY(cudaStreamSynchronize(s));
-            for (int q = 0; q < 2; ++q)
-                for (int j = 0; j < ld; ++j) sc2[(size_t)q * ld + j] = sc[(size_t)q * ld + src[j]];
-            for (int q = 0; q < 2; ++q)
-                CSC_CUDA_TRY(cudaMemcpyAsync(cols[q], sc2.data() + (size_t)q * ld, (size_t)ld * sizeof(double),
-                                             cudaMemcpyHostToDevice, s));
-            // r and p are dead: they take the same permutation only because the kernel moves three blocks
-            CSC_KLAUNCH("cg_compact", 6.0 * N * ld * 4, s,
-                        permute_columns_kernel<<<(int)std::min<int64_t>(ceil_div(N, 8), g->num_sms * 16), 256,
-                                                 8 * ld * sizeof(float), s>>>(x, r, p, d_src, ld, ld, N));
-            CSC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (compacted) {
+        // the columns still in slots go to xf too, which then holds every column's x; the
+        // final residual and the labels run on it at full width
+        std::vector<double> sc(kw);
+        CSC_CUDA_TRY(cudaMemcpyAsync(sc.data(), st.bn2, (size_t)kw * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CSC_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int j = 0; j < kw; ++j) bn2_col[slot_col[j]] = sc[j];
+        std::vector<int32_t> maps((size_t)2 * kw);
+        for (int j = 0; j < kw; ++j) {
+            maps[j] = j;
+            maps[(size_t)kw + j] = slot_col[j];
         }
-        set_width(ld);
+        CSC_CUDA_TRY(cudaMemcpyAsync(d_src, maps.data(), maps.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        CSC_CUDA_TRY(cudaMemcpyAsync(st.bn2, bn2_col.data(), (size_t)ld * sizeof(double), cudaMemcpyHostToDevice, s));
+        CSC_KLAUNCH("cg_compact", 8.0 * N * kw, s,
+                    compact_columns_kernel<<<(int)std::min<int64_t>(ceil_div(N, 8), g->num_sms * 16), 256, 0, s>>>(
+                        x, r, p, lw, t1, t2, Ap, 0, d_src, 0, d_src, d_src + kw, kw, xf, ld, N));
+        CSC_CUDA_TRY(cudaStreamSynchronize(s));
+        x = xf;
+        lw = ld;
+        for (int j = 0; j < ld; ++j) slot_col[j] = j;
     }
+    if (compact) set_width(ld);
     // true residual ||b - A x|| / ||b|| per column
     CSC_TRY(apply_A(x, bt_all, s));
     CG_SWITCH(cfg, CSC_KLAUNCH("cg_residual", blkb + 4.0 * N, s,
