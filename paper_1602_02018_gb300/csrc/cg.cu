@@ -1121,8 +1121,8 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         return CSC_E_INVALID;
     }
     // Column compaction (one graph, g = L^p): a column whose CG has converged keeps its x
-    // and leaves the iteration.  At a convergence check that finds at least 8 slots (or
-    // half of them) idle, x, r and p are rewritten as dense blocks of the columns still
+    // and leaves the iteration.  At a convergence check that finds at least 4 slots idle
+    // (one 16-byte vector per row), x, r and p are rewritten as dense blocks of the columns still
     // iterating (row stride kw: the rows stay contiguous in memory), the x of the columns
     // leaving goes to xf in column order, their scalars follow on the host, and every kernel
     // of the following iterations covers the kw slots only, with a launch shape narrowed to
@@ -1275,7 +1275,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         CSC_CUDA_TRY(cudaStreamSynchronize(s));
         converged = h_active[0] == 0;
         const int want = ((h_active[0] + 3) / 4) * 4;
-        if (compact && !converged && it < max_iter && (want <= kw - 8 || 2 * want <= kw)) {
+        if (compact && !converged && it < max_iter && want <= kw - 4) {
             // new slots: the active ones in slot order, then idle ones up to the width `want`
             // (they stay frozen); the other idle slots leave, their x going to xf
             std::vector<int> act(kw);

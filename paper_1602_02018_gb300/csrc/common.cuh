@@ -181,7 +181,7 @@ csc_status replay_graph(Graph* g, const std::string& key, cudaStream_t s, int64_
     auto it = g->graphs.find(key);
     if (it == g->graphs.end()) {
         if (!g->cap_stream) CSC_CUDA_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
-        if (g->graphs.size() >= 32) {  // bound the cache
+        if (g->graphs.size() >= 64) {  // bound the cache
             for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second.first);
             g->graphs.clear();
         }
