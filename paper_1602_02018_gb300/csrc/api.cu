@@ -14,6 +14,8 @@
 #include <new>
 #include <numeric>
 #include <string>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -499,12 +501,34 @@ static void permute_csr(const HostCSR& in, const std::vector<int32_t>& perm, Hos
         const int32_t o = perm[p];
         out.rp[p + 1] = out.rp[p] + (in.rp[o + 1] - in.rp[o]);
     }
-    for (int64_t p = 0; p < N; ++p) {
-        const int32_t o = perm[p];
-        int64_t w = out.rp[p];
-        for (int64_t e = in.rp[o]; e < in.rp[o + 1]; ++e) out.ci[w++] = iperm[in.ci[e]];
-        std::sort(out.ci.begin() + out.rp[p], out.ci.begin() + out.rp[p + 1]);
+    // rows relabelled and sorted independently: split over the host's cores in contiguous
+    // chunks of rows (the result does not depend on the split)
+    auto rows = [&](int64_t p0, int64_t p1) {
+        for (int64_t p = p0; p < p1; ++p) {
+            const int32_t o = perm[p];
+            int64_t w = out.rp[p];
+            for (int64_t e = in.rp[o]; e < in.rp[o + 1]; ++e) out.ci[w++] = iperm[in.ci[e]];
+            std::sort(out.ci.begin() + out.rp[p], out.ci.begin() + out.rp[p + 1]);
+        }
+    };
+    const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), N / 65536));
+    if (nt <= 1) {
+        rows(0, N);
+        return;
     }
+    std::vector<std::thread> pool;
+    try {
+        for (int64_t t = 1; t < nt; ++t) pool.emplace_back(rows, N * t / nt, N * (t + 1) / nt);
+    } catch (const std::system_error&) {
+        // no more threads: the rest of the rows on this one
+        for (auto& th : pool) th.join();
+        const int64_t done = (int64_t)pool.size();
+        rows(0, N / nt);
+        rows(N * (done + 1) / nt, N);
+        return;
+    }
+    rows(0, N / nt);
+    for (auto& th : pool) th.join();
 }
 
 static void free_graph(Graph* g) {
