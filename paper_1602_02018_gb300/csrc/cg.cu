@@ -41,28 +41,42 @@ struct KSum {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-// Per-block, per-column fp64 partial sums of NS quantities: threads of equal lane
-// across the block's row groups are summed in group order and written to
-// partials[(q * nslots + slot) * ldp + col0 + c].
+// Per-block, per-column fp64 partial sums of NS quantities, written to
+// partials[(q * nslots + slot) * ldp + col0 + c]: the lane groups of a warp (lanes of
+// equal lane % G) are added by a shuffle butterfly, then the warps' sums in warp order,
+// so the work per column does not grow with the number of row groups (narrow tiles have
+// up to 256 of them).  Every thread of the block must call it.
 template <int G, int NT, int NS>
 __device__ __forceinline__ void block_column_partials(KSum (&acc)[NS][NT][4], int lane, int col0, int tcols,
                                                       int64_t ldp, double* __restrict__ partials, int64_t slot,
                                                       int64_t nslots) {
-    constexpr int MAXGROUPS = kCgMaxThreads / G;
+    constexpr int MAXWARPS = kCgMaxThreads / 32;
     constexpr int COLS = G * NT * 4;
-    __shared__ double red[MAXGROUPS * COLS];
-    const int groups = blockDim.x / G;
-    const int grp = threadIdx.x / G;
+    __shared__ double red[MAXWARPS * COLS];
+    const int warps = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5;
     for (int q = 0; q < NS; ++q) {
-        __syncthreads();
+        double v[NT][4];
 #pragma unroll
         for (int t = 0; t < NT; ++t)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) red[grp * COLS + (t * G + lane) * 4 + v] = acc[q][t][v].value();
+            for (int u = 0; u < 4; ++u) v[t][u] = acc[q][t][u].value();
+#pragma unroll
+        for (int o = G; o < 32; o <<= 1)
+#pragma unroll
+            for (int t = 0; t < NT; ++t)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[t][u] += __shfl_xor_sync(0xffffffffu, v[t][u], o);
+        __syncthreads();
+        if ((threadIdx.x & 31) < G)
+#pragma unroll
+            for (int t = 0; t < NT; ++t)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) red[w * COLS + (t * G + lane) * 4 + u] = v[t][u];
         __syncthreads();
         for (int c = threadIdx.x; c < COLS && c < tcols; c += blockDim.x) {
             double sum = 0.0;
-            for (int i = 0; i < groups; ++i) sum += red[i * COLS + c];
+            for (int i = 0; i < warps; ++i) sum += red[i * COLS + c];
             partials[((int64_t)q * nslots + slot) * ldp + col0 + c] = sum;
         }
     }
