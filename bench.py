@@ -210,6 +210,18 @@ def recorded_traffic(workload: str, kernel_class: str, shape: dict | None):
         return None, None
 
 
+def max_over_ranks(vals, dist, device: str) -> list:
+    """Each value's largest over the ranks (the slowest rank's time); the values themselves
+    with one process.  Every rank of the group must call it with as many values."""
+    if not dist:
+        return [float(v) for v in vals]
+    import torch
+
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def pin_shapes(h, path: str) -> None:
     """Pin on handle h the launch shapes of a previous bench line (its autotuned_shapes)."""
     import paper_1602_02018_gb300 as csc
@@ -420,10 +432,7 @@ def run_ours(args, w, rank, world, local_rank):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     filt_ms = [x.ms["filter"] for x in infos]
     ms_step, ms_filter = statistics.mean(step_ms), statistics.mean(filt_ms)
-    if dist:
-        t = torch.tensor([ms_step, ms_filter], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step, ms_filter = t.tolist()
+    ms_step, ms_filter = max_over_ranks([ms_step, ms_filter], dist, "cuda")
     value = world * work / (ms_filter / 1e3)
 
     # roofline of the dominant kernel (live CUDA-event durations, algorithmic bytes).  A unit is
@@ -483,6 +492,16 @@ def run_ours(args, w, rank, world, local_rank):
         fwd = 4.0 * g.nnz + 4.0 * (g.n + 1) + 4.0 * g.n + 3.0 * g.n * d_pad * bx + 2.0 * g.n * d_pad * by
         filter_roofline["forward_bytes_per_order"] = fwd
         filter_roofline["frac_forward_bytes"] = fwd / (filter_roofline["unit_us"] / 1e6) / 1e9 / peak
+    if filter_roofline:
+        # the same unit timed inside the timed region itself: the replayed filter stage (the m
+        # orders, each row-range launch beside its heavy-row launch, plus the signal generation
+        # and the fused normalisation) over m -- an upper bound on the time per order as run
+        stage_us = ms_filter / m * 1e3
+        filter_roofline["stage_unit_us"] = stage_us
+        filter_roofline["frac_stage"] = filter_roofline["algorithmic_bytes_per_unit"] / (stage_us / 1e6) / 1e9 / peak
+        if "forward_bytes_per_order" in filter_roofline:
+            filter_roofline["frac_forward_bytes_stage"] = (filter_roofline["forward_bytes_per_order"] /
+                                                           (stage_us / 1e6) / 1e9 / peak)
 
     lab = labels.cpu().numpy()
     ari_truth = adjusted_rand(lab, g.labels) if g.labels is not None else None
@@ -510,11 +529,7 @@ def run_ours(args, w, rank, world, local_rank):
             if i >= 1:
                 ts.append(time.perf_counter() - t0)
                 tcs.append(tc - t0)
-        t_e2e = statistics.mean(ts)
-        if dist:
-            t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = t.item()
+        t_e2e = max_over_ranks([statistics.mean(ts)], dist, "cuda")[0]
         h2d = (g.n + 1) * 4 + g.nnz * 4
         d2h = g.n * 4
         e2e = {"value": world * work / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
