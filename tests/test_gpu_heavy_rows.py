@@ -81,6 +81,26 @@ def test_filter_pinned_shapes_heavy(G, NT, threads):
     assert rel(y, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("gname", ["hub", "power_law"])
+@pytest.mark.parametrize("G", [2, 8, 16, 32])
+@pytest.mark.parametrize("storage,tol", [(0, 1e-5), (1, 5e-2)])
+def test_clenshaw_lean_heavy(gname, G, storage, tol):
+    """The lean Clenshaw form's row ranges beside the heavy-row launch, on graphs with hubs:
+    every order (the first, the middle ones, the last with its normalisation) against the
+    oracle, in fp32 and bf16 storage."""
+    g = HUB if gname == "hub" else POWER_LAW
+    d, d_pad, m, lam = 47, 48, 20, 0.43
+    vec = 8 if storage == 1 else 4
+    tiles = -(-(d_pad // vec) // G)
+    r = ci.gaussian_block(g.n, d, d_pad, seed=3)
+    ref = och.normalize_rows(_oracle_filter(g, r.astype(np.float64), lam, m))
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM | csc.DEGREE_ORDER) as h:
+        csc.csc_graph_pin_shape(h, "clenshaw", 2 if storage == 1 else 4, d_pad, G, 1, 256, 41, tiles, 0, lean=1)
+        y = csc.csc_filter_random_signals(h, lam, m, d, d_pad, storage=storage, R_in=torch.from_numpy(r).cuda(),
+                                          flags=csc.CLENSHAW | csc.NORMALIZE_ROWS).cpu().numpy()
+    assert rel(y, ref) <= tol
+
+
 @pytest.mark.parametrize("storage,tol", [(1, 5e-2), (2, 1e-12)])
 def test_filter_bf16_f64_heavy(storage, tol):
     g = POWER_LAW
