@@ -6,9 +6,9 @@ eigencount moments and the lambda_k dichotomy, the Jackson-Chebyshev filter
 of d random signals with row normalisation, uniform sampling, reduced
 k-means (20 replicates), CG interpolation of Eq. 5 (g(L) = L^4) and the
 label rule.  The default workload is the Chung-Lu power-law graph with
-N = 1e6 nodes (degree exponent 2.1, mean degree 6, minimum degree 1), RCM
-reordered, k = 100, d = ceil(4 ln N) = 56 signals, m = 100,
-n = ceil(2 k ln k) = 922 samples: its signal blocks (224 MB each in FP32)
+N = 1e6 nodes (degree exponent 2.1, mean degree 6, minimum degree 1), rows in
+decreasing degree with RCM order among equal degrees, k = 100, d = ceil(4 ln N)
+= 56 signals, m = 100, n = ceil(2 k ln k) = 922 samples: its signal blocks (224 MB each in FP32)
 exceed the 129 MB L2, so the filter's HBM roofline is meaningful there.
 `--workload sbm_n1e5_k200` runs the SBM with N = 1e5, k = 200 (m = 50,
 d = 47 padded to 48, n = 2120), whose working set sits in L2.
@@ -17,7 +17,7 @@ value  = Chebyshev-filter throughput m * nnz * d / t_filter (nnz.col/s),
          t_filter the device time of the filter stage inside each timed step
          (graph resident in HBM, L2 flushed between steps).
 e2e    = the same work over the end-to-end step through the C ABI with host
-         buffers: host CSR -> csc_graph_create (upload + degrees) ->
+         buffers: host CSR -> csc_graph_create (node order, upload, degrees) ->
          csc_cluster -> labels copied back to pinned host memory.
 
 `--impl reference` times the FP64 oracle (the CPU restatement of the
