@@ -11,10 +11,13 @@
 // first of them loads per-edge weights (see lap_kernel).
 // Preconditioner: diag(M^T M) + gamma (diag(L) = 1).
 // Labels: node i -> argmax_j x_j(i) / ||x_j|| (ties to the lowest j).
+// Columns whose CG has converged leave the iteration: the blocks are rewritten as
+// dense blocks of the columns still iterating (column compaction, run_interpolate).
 //
 // Launch shape (every kernel of one solve): CTA x sweeps the contiguous row
 // range [part[x], part[x+1]) with G lanes per row; CTA y covers the column tile
-// [y*TW, (y+1)*TW), TW = 4*G*NT.  The shape is tuned once per graph and k.
+// [y*TW, (y+1)*TW), TW = 4*G*NT.  The shape is tuned once per graph and k, and
+// narrowed with the compacted width.
 #include <math.h>
 #include <stdio.h>
 
