@@ -470,9 +470,11 @@ def run_ours(args, w, rank, world, local_rank):
         per_unit = c["bytes"] / n_units
         unit_ms = c["ms"] / n_units
         achieved = per_unit / (unit_ms / 1e3) / 1e9
-        shp = next((dict(G=x["G"], NT=x["NT"], threads=x["threads"], P=x["P"], tiles=x["tiles"],
-                     global_index=x["global_index"], lean=x.get("lean", 0)) for x in tuned
-                    if x["kernel"] == shape_kind.get(name)), None)
+        # the shape at the class's full width (a compacted CG solve also tunes its narrower widths)
+        mine = [x for x in tuned if x["kernel"] == shape_kind.get(name)]
+        x = max(mine, key=lambda x: x["columns"]) if mine else None
+        shp = None if x is None else dict(G=x["G"], NT=x["NT"], threads=x["threads"], P=x["P"], tiles=x["tiles"],
+                                          global_index=x["global_index"], lean=x.get("lean", 0))
         traffic, note = recorded_traffic(args.workload, name, shp)
         if name == "cheb_step" and args.interp == "highpass":
             # the class then also holds the interpolation's h~ orders on the k columns

@@ -4,8 +4,8 @@
 // (M^T M + gamma L^p) x_j = M^T c_j^r.  All k systems are solved together by
 // Jacobi-preconditioned conjugate gradients on an N x k row-major fp32 block
 // (one independent CG per column; per-column inner products summed in
-// compensated fp32 per thread and in fp64 across threads and blocks, in a
-// fixed order).  A p = mask * p + gamma L^p p is computed with p sparse
+// compensated fp32 per thread, as error-free fp32 pairs across the threads of a
+// block and in fp64 across blocks, in a fixed order).  A p = mask * p + gamma L^p p is computed with p sparse
 // passes, the last one fused with the mask term and the <p, A p> partials.
 // The products by L run in the pre-scaled form v = D^-1/2 t, so only the
 // first of them loads per-edge weights (see lap_kernel).
@@ -31,58 +31,70 @@ namespace csc {
 
 constexpr int kCgMaxThreads = 512;
 
-// Compensated (Kahan) fp32 accumulation: per-thread column sums stay in fp32
-// registers (fp64 arithmetic is scarce on this part) with a running error term.
-struct KSum {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x) {
-        const float y = x - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
-
-// Per-block, per-column fp64 partial sums of NS quantities, written to
+// Per-block, per-column partial sums of NS quantities, written as fp64 to
 // partials[(q * nslots + slot) * ldp + col0 + c]: the lane groups of a warp (lanes of
 // equal lane % G) are added by a shuffle butterfly, then the warps' sums in warp order,
 // so the work per column does not grow with the number of row groups (narrow tiles have
-// up to 256 of them).  Every thread of the block must call it.
+// up to 256 of them).  Both stages add float pairs (FF), so no thread issues an fp64
+// instruction; one fp64 value per column leaves the block.  Every thread of the block
+// must call it.
 template <int G, int NT, int NS>
 __device__ __forceinline__ void block_column_partials(KSum (&acc)[NS][NT][4], int lane, int col0, int tcols,
                                                       int64_t ldp, double* __restrict__ partials, int64_t slot,
                                                       int64_t nslots) {
     constexpr int MAXWARPS = kCgMaxThreads / 32;
     constexpr int COLS = G * NT * 4;
-    __shared__ double red[MAXWARPS * COLS];
+    __shared__ float2 red[MAXWARPS * COLS];
     const int warps = blockDim.x >> 5;
     const int w = threadIdx.x >> 5;
     for (int q = 0; q < NS; ++q) {
-        double v[NT][4];
+        FF v[NT][4];
 #pragma unroll
         for (int t = 0; t < NT; ++t)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[t][u] = acc[q][t][u].value();
+            for (int u = 0; u < 4; ++u) v[t][u] = acc[q][t][u].pair();
 #pragma unroll
         for (int o = G; o < 32; o <<= 1)
 #pragma unroll
             for (int t = 0; t < NT; ++t)
 #pragma unroll
-                for (int u = 0; u < 4; ++u) v[t][u] += __shfl_xor_sync(0xffffffffu, v[t][u], o);
+                for (int u = 0; u < 4; ++u) {
+                    const float bh = __shfl_xor_sync(0xffffffffu, v[t][u].hi, o);
+                    const float bl = __shfl_xor_sync(0xffffffffu, v[t][u].lo, o);
+                    v[t][u] = ff_add(v[t][u], FF{bh, bl});
+                }
         __syncthreads();
         if ((threadIdx.x & 31) < G)
 #pragma unroll
             for (int t = 0; t < NT; ++t)
 #pragma unroll
-                for (int u = 0; u < 4; ++u) red[w * COLS + (t * G + lane) * 4 + u] = v[t][u];
+                for (int u = 0; u < 4; ++u)
+                    red[w * COLS + (t * G + lane) * 4 + u] = make_float2(v[t][u].hi, v[t][u].lo);
         __syncthreads();
         for (int c = threadIdx.x; c < COLS && c < tcols; c += blockDim.x) {
-            double sum = 0.0;
-            for (int i = 0; i < warps; ++i) sum += red[i * COLS + c];
-            partials[((int64_t)q * nslots + slot) * ldp + col0 + c] = sum;
+            FF sum{0.f, 0.f};
+            for (int i = 0; i < warps; ++i) {
+                const float2 e = red[i * COLS + c];
+                sum = ff_add(sum, FF{e.x, e.y});
+            }
+            partials[((int64_t)q * nslots + slot) * ldp + col0 + c] = sum.value();
         }
     }
+}
+
+// The fp64 per-column scalars (alpha, beta) of this CTA's column tile as fp32, each
+// converted once per CTA into shared memory.  Every thread of the block must call it.
+template <int G, int NT>
+__device__ __forceinline__ void tile_scalars(const double* __restrict__ src, int tcols, float (&out)[NT][4],
+                                             int lane) {
+    constexpr int COLS = G * NT * 4;
+    __shared__ float s_col[COLS];
+    for (int c = threadIdx.x; c < COLS; c += blockDim.x) s_col[c] = (src && c < tcols) ? (float)src[c] : 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) out[t][v] = s_col[(t * G + lane) * 4 + v];
 }
 
 // Batch view of the CG kernels (all members NULL for one graph): gid = graph of
@@ -313,13 +325,7 @@ cg_update_kernel(float* __restrict__ x, float* __restrict__ r, const float* __re
     float al[NT][4];
     // the columns' scalars of this range's graph (a batch's ranges lie inside one graph)
     const int64_t sg = (gid && part[blockIdx.x] < r1) ? (int64_t)gid[part[blockIdx.x]] * ld : 0;
-#pragma unroll
-    for (int t = 0; t < NT; ++t)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int c = (t * G + lane) * 4 + v;
-            al[t][v] = (alpha && c < tcols) ? (float)alpha[sg + col0 + c] : 0.f;
-        }
+    tile_scalars<G, NT>(alpha ? alpha + sg + col0 : nullptr, tcols, al, lane);
     CG_ROWS(G) {
         const float pi = pinv[row];
 #pragma unroll
@@ -362,13 +368,7 @@ cg_pupdate_kernel(const float* __restrict__ r, float* __restrict__ p, const doub
     CG_TILE(G, NT)
     float be[NT][4];
     const int64_t sg = (gid && part[blockIdx.x] < r1) ? (int64_t)gid[part[blockIdx.x]] * ld : 0;
-#pragma unroll
-    for (int t = 0; t < NT; ++t)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int c = (t * G + lane) * 4 + v;
-            be[t][v] = c < tcols ? (float)beta[sg + col0 + c] : 0.f;
-        }
+    tile_scalars<G, NT>(beta + sg + col0, tcols, be, lane);
     CG_ROWS(G) {
         const float pi = pinv[row];
 #pragma unroll
@@ -853,19 +853,12 @@ static csc_status cg_occupancy(const LaunchCfg& c, int* out) {
     return CSC_OK;
 }
 
-csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* sample_labels, int64_t n, int k,
-                           int g_power, double gamma, double rel_tol, int max_iter, int32_t* labels_out,
-                           float* fuzzy_out, csc_cg_info* info, cudaStream_t s, const int32_t* k_graphs,
-                           const double* hp_coef, int hp_m, const float* sample_w) {
-    const int32_t N = (int32_t)g->N;
-    // one independent set of k systems per graph of a batch (k_graphs: each graph's k)
-    const int nseg = (k_graphs && g->n_graphs > 1) ? g->n_graphs : 1;
-    const bool hp = hp_coef != nullptr;  // g = 1 - h~ instead of L^p (per graph for a batch)
-    const int ld = ((k + 3) / 4) * 4;
-    const int nv = ld / 4;
-    // candidate shapes: column tiles of 4*G*NT floats with at most a third idle
-    std::vector<LaunchCfg> cands;
-    int max_p = 1;
+// Candidate launch shapes of the CG kernels for nv 16-byte vectors per row: column tiles
+// of 4*G*NT floats with at most a third idle (only_G > 0: lane groups of only_G, NT = 1),
+// one to eight waves of resident CTAs (at most p_cap row ranges when p_cap > 0); *max_p
+// grows to the largest row-range count.
+static csc_status cg_candidates(Graph* g, int64_t N, int nv, int p_cap, int only_G, std::vector<LaunchCfg>* out,
+                                int* max_p) {
     int min_waste = 1 << 30;  // narrow blocks (k <= 4) keep the least-waste shapes
     for (const auto& sh : kCgShapes) {
         const int cap = sh[0] * sh[1];
@@ -876,7 +869,9 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         const int cap = sh[0] * sh[1];
         const int tiles = (nv + cap - 1) / cap;
         const int waste = tiles * cap - nv;
-        if (tiles > 64 || (3 * waste > tiles * cap && waste > min_waste)) continue;
+        if (only_G > 0 ? (sh[0] != only_G || sh[1] != 1)
+                       : (tiles > 64 || (3 * waste > tiles * cap && waste > min_waste)))
+            continue;
         for (int th : kCgThreadChoices)
             for (int lean = 0; lean <= 1; ++lean) {
                 if (lean && (sh[1] != 1 || th != 256)) continue;  // the lean form: NT = 1, 256 threads
@@ -897,21 +892,37 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                     P = P < 1 ? 1 : P;
                     // the CTA's staged CSR slice must fit shared memory: more, shorter ranges if not
                     CSC_TRY(fit_staged_partition(g, P, std::max<int64_t>(lim, g->n_graphs), &P));
-                    if (staged_smem(g, P) > kStagedSmemMax) continue;
+                    if (staged_smem(g, P) > kStagedSmemMax || (p_cap > 0 && P > p_cap)) continue;
                     c.P = P;
-                    if (!cands.empty() && cands.back().G == c.G && cands.back().NT == c.NT &&
-                        cands.back().threads == th && cands.back().lean == lean && cands.back().P == c.P)
+                    if (!out->empty() && out->back().G == c.G && out->back().NT == c.NT &&
+                        out->back().threads == th && out->back().lean == lean && out->back().P == c.P)
                         continue;
-                    max_p = std::max(max_p, c.P);
+                    *max_p = std::max(*max_p, c.P);
                     int room = 0;
                     CG_SWITCH(c, room = cg_staged_room<G_, NT_>());
                     c.staged = 1;  // both index sources (sweep_rows), the staged one where it fits
-                    if (staged_smem(g, c.P) <= std::min(room, kStagedSmemMax)) cands.push_back(c);
+                    if (staged_smem(g, c.P) <= std::min(room, kStagedSmemMax)) out->push_back(c);
                     c.staged = 0;
-                    cands.push_back(c);
+                    out->push_back(c);
                 }
             }
     }
+    return CSC_OK;
+}
+
+csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* sample_labels, int64_t n, int k,
+                           int g_power, double gamma, double rel_tol, int max_iter, int32_t* labels_out,
+                           float* fuzzy_out, csc_cg_info* info, cudaStream_t s, const int32_t* k_graphs,
+                           const double* hp_coef, int hp_m, const float* sample_w) {
+    const int32_t N = (int32_t)g->N;
+    // one independent set of k systems per graph of a batch (k_graphs: each graph's k)
+    const int nseg = (k_graphs && g->n_graphs > 1) ? g->n_graphs : 1;
+    const bool hp = hp_coef != nullptr;  // g = 1 - h~ instead of L^p (per graph for a batch)
+    const int ld = ((k + 3) / 4) * 4;
+    const int nv = ld / 4;
+    std::vector<LaunchCfg> cands;
+    int max_p = 1;
+    CSC_TRY(cg_candidates(g, N, nv, 0, 0, &cands, &max_p));
     if (cands.empty()) {
         set_error("csc_interpolate: no launch shape for k = %d", k);
         return CSC_E_UNSUPPORTED;
@@ -1023,53 +1034,55 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     if (bfull) CSC_CUDA_TRY(cudaMemcpyAsync(bfull, r, blk, cudaMemcpyDeviceToDevice, s));
     CSC_KLAUNCH("cg_setup", 8.0 * N, s, precond_kernel<<<ceil_div(N, 256), 256, 0, s>>>(mask, (float)gamma, pinv, N));
 
-    // launch shape: tuned on the middle product of the chain (the dominant kernel),
-    // reading r and writing scratch; shared by every kernel of the solve
-    LaunchCfg cfg;
-    {
-        const uint64_t key = tkey;
-        if (have_known) {
-            cfg = known;
-        } else {
-            const bool prof = g_prof_enabled;
-            g_prof_enabled = false;  // tuning launches are not part of the measured work
-            float best_ms = 1e30f;
-            cfg = cands[0];
-            for (const LaunchCfg& c : cands) {
-                const int32_t* pr = nullptr;
-                CSC_TRY(get_partition(g, c.P, &pr));
-                const dim3 grid(c.P, c.tiles);
-                float ms = 0.f;
-                // one iteration's row-range work on scratch: three products of the chain, the
-                // last product with the mask term and <., .> partials, and the update's partials
-                // (alpha = NULL: nothing is updated); a shape is judged by all of them
-                const int sm = c.staged ? staged_smem(g, c.P) : 0;
-                for (int rep = 0; rep < 3; ++rep) {
-                    if (rep == 1) cudaEventRecord(g->ev[0], s);
-                    const float* src[3] = {r, t1, t2};
-                    float* dst[3] = {t1, t2, t1};
-                    for (int q = 0; q < 3; ++q)
-                        CG_SWITCH(c, lap_rows<G_, NT_, false>(c, grid, sm, s, g, src[q], dst[q], pr, ld, ld,
-                                                              CgBatch()));
-                    CG_SWITCH(c, lap_ax_rows<G_, NT_, false>(c, grid, sm, s, g, t1, p, mask, (float)gamma, Ap, pr, ld,
-                                                             ld, part, c.P, CgBatch()));
-                    CG_SWITCH(c, cg_update_kernel<G_, NT_><<<grid, c.threads, 0, s>>>(x, r, p, Ap, nullptr, nullptr,
-                                                                                       pinv, pr, ld, ld, part,
-                                                                                       CgBatch()));
-                }
-                cudaEventRecord(g->ev[1], s);
-                CSC_CUDA_TRY(cudaEventSynchronize(g->ev[1]));
-                CSC_CUDA_TRY(cudaGetLastError());
-                cudaEventElapsedTime(&ms, g->ev[0], g->ev[1]);
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    cfg = c;
-                }
+    // launch shapes are tuned on one iteration's row-range work at `cols` columns (row
+    // stride cols): three products of the chain, the last product with the mask term and
+    // <., .> partials, and the update's partials (alpha = NULL: nothing is updated).  It
+    // reads r, p, x and writes only t1, t2, Ap and the partials, which hold nothing between
+    // iterations, so a compacted solve can tune its new width in place.
+    auto tune = [&](const std::vector<LaunchCfg>& cs, int cols, LaunchCfg* best) -> csc_status {
+        struct ProfOff {  // tuning launches are not part of the measured work
+            bool prev = g_prof_enabled;
+            ProfOff() { g_prof_enabled = false; }
+            ~ProfOff() { g_prof_enabled = prev; }
+        } off;
+        float best_ms = 1e30f;
+        *best = cs[0];
+        for (const LaunchCfg& c : cs) {
+            const int32_t* pr = nullptr;
+            CSC_TRY(get_partition(g, c.P, &pr));
+            const dim3 grid(c.P, c.tiles);
+            float ms = 0.f;
+            const int sm = c.staged ? staged_smem(g, c.P) : 0;
+            for (int rep = 0; rep < 3; ++rep) {
+                if (rep == 1) cudaEventRecord(g->ev[0], s);
+                const float* src[3] = {r, t1, t2};
+                float* dst[3] = {t1, t2, t1};
+                for (int q = 0; q < 3; ++q)
+                    CG_SWITCH(c, lap_rows<G_, NT_, false>(c, grid, sm, s, g, src[q], dst[q], pr, cols, cols,
+                                                          CgBatch()));
+                CG_SWITCH(c, lap_ax_rows<G_, NT_, false>(c, grid, sm, s, g, t1, p, mask, (float)gamma, Ap, pr, cols,
+                                                         cols, part, c.P, CgBatch()));
+                CG_SWITCH(c, cg_update_kernel<G_, NT_><<<grid, c.threads, 0, s>>>(x, r, p, Ap, nullptr, nullptr, pinv,
+                                                                                   pr, cols, cols, part, CgBatch()));
             }
-            g_prof_enabled = prof;
-            g->tuned[key] = cfg;
-            tune_cache_put(g, key, cfg);
+            cudaEventRecord(g->ev[1], s);
+            CSC_CUDA_TRY(cudaEventSynchronize(g->ev[1]));
+            CSC_CUDA_TRY(cudaGetLastError());
+            cudaEventElapsedTime(&ms, g->ev[0], g->ev[1]);
+            if (ms < best_ms) {
+                best_ms = ms;
+                *best = c;
+            }
         }
+        return CSC_OK;
+    };
+    LaunchCfg cfg;
+    if (have_known) {
+        cfg = known;
+    } else {
+        CSC_TRY(tune(cands, ld, &cfg));
+        g->tuned[tkey] = cfg;
+        tune_cache_put(g, tkey, cfg);
     }
     const int32_t* rpart = nullptr;
     CSC_TRY(get_partition(g, cfg.P, &rpart));
@@ -1152,33 +1165,84 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
     int kcols = k;        // columns the scalar kernels cover (slots past them are idle)
     LaunchCfg wcfg = cfg; // launch shape of the iterations at width kw
     dim3 wgrid = grid, whgrid = hgrid;
+    int wP = P, wPH = PH, wcsmem = csmem;  // its row ranges, partial slots and staged slice
+    const int32_t* wpart = rpart;
+    Segs wsg = sg;  // the scalar kernels' slot layout at that shape
     std::vector<int> slot_col(ld);
     for (int j = 0; j < ld; ++j) slot_col[j] = j;
-    auto set_width = [&](int w) {
+    auto set_width = [&](int w) -> csc_status {
         kw = w;
         kcols = w < ld ? w : k;
         wcfg = cfg;
         const int nvw = ceil_div(w, 4);
-        if (2 * nvw <= cfg.G * cfg.NT) {  // the tuned tile is at least twice too wide: narrower groups
-            int G2 = 2;
-            while (G2 < nvw && G2 < 32) G2 *= 2;
-            wcfg.G = G2;
-            wcfg.NT = 1;
+        // lane groups of the next power of two of the width's vectors (NT = 1, one column
+        // tile up to 128 columns)
+        int G2 = 2;
+        while (G2 < nvw && G2 < 32) G2 *= 2;
+        if (w < ld) {
+            // row ranges, threads and kernel form of a compacted width: pinned or tuned
+            // earlier, else tuned now on the compacted blocks with those lane groups and at
+            // most max_p row ranges (the partials are sized for them); their cost per
+            // iteration grows with the row-range count as the width shrinks
+            const uint64_t wkey = (3ull << 48) | (uint64_t)(uint32_t)w;
+            LaunchCfg c;
+            bool have = false;
+            auto it = g->tuned.find(wkey);
+            if (it != g->tuned.end()) {
+                c = it->second;
+                have = true;
+            } else if (tune_cache_get(g, wkey, &c)) {
+                have = true;
+            }
+            if (have && c.P > max_p) have = false;
+            if (!have) {
+                std::vector<LaunchCfg> wc;
+                int wmax = 1;
+                CSC_TRY(cg_candidates(g, N, nvw, max_p, G2, &wc, &wmax));
+                if (!wc.empty()) {
+                    CSC_TRY(tune(wc, w, &c));
+                    have = true;
+                }
+            }
+            if (have) {
+                g->tuned[wkey] = c;
+                tune_cache_put(g, wkey, c);
+                wcfg = c;
+            } else if (2 * nvw <= cfg.G * cfg.NT) {  // no candidate: narrower lane groups of the tuned shape
+                wcfg.G = G2;
+                wcfg.NT = 1;
+            }
         }
         wcfg.tiles = ceil_div(nvw, wcfg.G * wcfg.NT);
-        wgrid = dim3(cfg.P, wcfg.tiles);
+        wP = wcfg.P;
+        wPH = wP + H;
+        wsg.P = wP;
+        CSC_TRY(get_partition(g, wP, &wpart));
+        wcsmem = wcfg.staged ? staged_smem(g, wP) : 0;
+        CSC_TRY(check_staged_smem(wcsmem));
+        int room = 0;
+        CG_SWITCH(wcfg, room = cg_staged_room<G_, NT_>());
+        if (wcsmem > room) {
+            set_error("csc_interpolate: a row range's CSR slice (%d bytes) does not fit beside the CG kernels' "
+                      "shared arrays (%d bytes free) at %d columns", wcsmem, room, w);
+            return CSC_E_UNSUPPORTED;
+        }
+        wgrid = dim3(wP, wcfg.tiles);
         whgrid = dim3(H > 0 ? H : 1, wcfg.tiles);
         blkb = (double)N * w * 4.0;
-        scal_b = 8.0 * P * w;
-        scal_ax = 8.0 * PH * w;
+        scal_b = 8.0 * wP * w;
+        scal_ax = 8.0 * wPH * w;
         kb.x = kb_ax.x = ceil_div(kcols, 32);
+        kb.z = std::max(1, ceil_div(wP, kSliceSlots));
+        kb_ax.z = std::max(1, ceil_div(wPH, kSliceSlots));
+        return CSC_OK;
     };
     auto apply_A = [&](const float* in, const CgBatch& bb, cudaStream_t s) -> csc_status {
         if (hp) {
             CSC_TRY(poly_apply(g, op, in, t1, s));
             CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax", 4.0 * N + 3 * blkb + scal_b, s,
-                                       hp_ax_kernel<G_, NT_><<<wgrid, th, 0, s>>>(in, t1, mask, (float)gamma, Ap, rpart,
-                                                                                 kw, lw, part, bb)));
+                                       hp_ax_kernel<G_, NT_><<<wgrid, wcfg.threads, 0, s>>>(
+                                           in, t1, mask, (float)gamma, Ap, wpart, kw, lw, part, bb)));
             return CSC_OK;
         }
         // t = L^(p-1) in, then Ap = mask*in + gamma * L t with <in, Ap> partials; each product's
@@ -1208,11 +1272,11 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                 const double by = lb * (1.0 - heavy_frac);
                 if (win)
                     CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap", by, st,
-                                                lap_rows<G_, NT_, true>(wcfg, wgrid, csmem, st, g, cur, o, rpart, kw,
+                                                lap_rows<G_, NT_, true>(wcfg, wgrid, wcsmem, st, g, cur, o, wpart, kw,
                                                                         lw, bb)));
                 else
                     CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap", by, st,
-                                                lap_rows<G_, NT_, false>(wcfg, wgrid, csmem, st, g, cur, o, rpart, kw,
+                                                lap_rows<G_, NT_, false>(wcfg, wgrid, wcsmem, st, g, cur, o, wpart, kw,
                                                                          lw, bb)));
                 return CSC_OK;
             };
@@ -1227,24 +1291,25 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                 CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax_heavy", ab * heavy_frac, st,
                                            lap_ax_heavy_kernel<G_, NT_, true><<<whgrid, kHeavyThreads, 0, st>>>(
                                                g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma,
-                                               Ap, g->heavy, kw, lw, part, P, PH, bb)));
+                                               Ap, g->heavy, kw, lw, part, wP, wPH, bb)));
             else
                 CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax_heavy", ab * heavy_frac, st,
                                            lap_ax_heavy_kernel<G_, NT_, false><<<whgrid, kHeavyThreads, 0, st>>>(
                                                g->row_ptr, g->col_idx, g->dinv, g->sqdeg, cur, in, mask, (float)gamma,
-                                               Ap, g->heavy, kw, lw, part, P, PH, bb)));
+                                               Ap, g->heavy, kw, lw, part, wP, wPH, bb)));
             return CSC_OK;
         };
         auto light = [&](cudaStream_t st) -> csc_status {
             const double by = ab * (1.0 - heavy_frac);
             if (win)
                 CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax", by, st,
-                                            lap_ax_rows<G_, NT_, true>(wcfg, wgrid, csmem, st, g, cur, in, mask,
-                                                                       (float)gamma, Ap, rpart, kw, lw, part, PH, bb)));
+                                            lap_ax_rows<G_, NT_, true>(wcfg, wgrid, wcsmem, st, g, cur, in, mask,
+                                                                       (float)gamma, Ap, wpart, kw, lw, part, wPH,
+                                                                       bb)));
             else
                 CG_SWITCH(wcfg, CSC_KLAUNCH("cg_lap_ax", by, st,
-                                            lap_ax_rows<G_, NT_, false>(wcfg, wgrid, csmem, st, g, cur, in, mask,
-                                                                        (float)gamma, Ap, rpart, kw, lw, part, PH,
+                                            lap_ax_rows<G_, NT_, false>(wcfg, wgrid, wcsmem, st, g, cur, in, mask,
+                                                                        (float)gamma, Ap, wpart, kw, lw, part, wPH,
                                                                         bb)));
             return CSC_OK;
         };
@@ -1256,18 +1321,18 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         for (int q = 0; q < count; ++q) {
             CSC_TRY(apply_A(p, bt, s));
             CSC_KLAUNCH("cg_scalar", scal_ax, s,
-                        cg_alpha_kernel<<<kb_ax, rb, 0, s>>>(part, PH, sg, kcols, lw, st, lvl2, red_cnt));
+                        cg_alpha_kernel<<<kb_ax, rb, 0, s>>>(part, wPH, wsg, kcols, lw, st, lvl2, red_cnt));
             // x, r, p, Ap read; x, r written
             CG_SWITCH(wcfg, CSC_KLAUNCH("cg_update", 6 * blkb + 4.0 * N + 2 * scal_b, s,
-                                       cg_update_kernel<G_, NT_><<<wgrid, th, 0, s>>>(x, r, p, Ap, st.alpha, gid, pinv,
-                                                                                     rpart, kw, lw, part, bt)));
+                                       cg_update_kernel<G_, NT_><<<wgrid, wcfg.threads, 0, s>>>(
+                                           x, r, p, Ap, st.alpha, gid, pinv, wpart, kw, lw, part, bt)));
             CSC_TRY(reset_active(s));
             CSC_KLAUNCH("cg_scalar", 2 * scal_b, s,
-                        cg_beta_kernel<<<kb, rb, 0, s>>>(part, P, sg, kcols, lw, st, rel_tol * rel_tol, 0, lvl2,
+                        cg_beta_kernel<<<kb, rb, 0, s>>>(part, wP, wsg, kcols, lw, st, rel_tol * rel_tol, 0, lvl2,
                                                          red_cnt));
             CG_SWITCH(wcfg, CSC_KLAUNCH("cg_pupdate", 3 * blkb + 4.0 * N, s,
-                                       cg_pupdate_kernel<G_, NT_><<<wgrid, th, 0, s>>>(r, p, st.beta, gid, pinv, rpart,
-                                                                                      kw, lw, bt)));
+                                       cg_pupdate_kernel<G_, NT_><<<wgrid, wcfg.threads, 0, s>>>(
+                                           r, p, st.beta, gid, pinv, wpart, kw, lw, bt)));
         }
         return CSC_OK;
     };
@@ -1347,7 +1412,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
             CSC_CUDA_TRY(cudaStreamSynchronize(s));
             compacted = true;
             lw = want_w;
-            set_width(want_w);
+            CSC_TRY(set_width(want_w));
         }
     }
     if (compacted) {
@@ -1372,7 +1437,7 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
         lw = ld;
         for (int j = 0; j < ld; ++j) slot_col[j] = j;
     }
-    if (compact) set_width(ld);
+    if (compact) CSC_TRY(set_width(ld));
     // true residual ||b - A x|| / ||b|| per column
     CSC_TRY(apply_A(x, bt_all, s));
     CG_SWITCH(cfg, CSC_KLAUNCH("cg_residual", blkb + 4.0 * N, s,

@@ -570,6 +570,44 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t t) {
 }
 
 // ------------------------------------------------------------ reductions
+// fp64 instructions issue at a small fraction of the fp32 rate on this part, so sums
+// that need more than fp32 accuracy run on fp32 pairs: per thread a compensated (Kahan)
+// sum, between threads an unevaluated pair hi + lo added with Knuth's error-free
+// two-sum (about 48 significant bits), converted to fp64 once per block.
+struct FF {
+    float hi, lo;
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// (a.hi + a.lo) + (b.hi + b.lo): two-sum of the high parts, the low parts and the
+// rounding error added to it, renormalised.  No products, so no FMA contraction applies.
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const float s = a.hi + b.hi;
+    const float bv = s - a.hi;
+    const float err = (a.hi - (s - bv)) + (b.hi - bv);
+    const float t = err + (a.lo + b.lo);
+    const float h = s + t;
+    return FF{h, t - (h - s)};
+}
+
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ FF pair() const { return FF{s, -c}; }
+};
+
+__device__ __forceinline__ FF warp_sum_ff(FF v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = ff_add(v, FF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+    return v;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

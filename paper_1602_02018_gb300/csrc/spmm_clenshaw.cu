@@ -90,23 +90,25 @@ __device__ __forceinline__ void clenshaw_epilogue(int row, int lane, int col0, i
     }
     if constexpr (!LAST) return;
     else {
+    // the row norm in the accumulator type (fp32 for fp32 and bf16 storage: fp64
+    // instructions issue at a small fraction of the fp32 rate on this part)
     const A back = sqdeg[row];
-    double inv = 1.0;
+    A inv = A(1);
     if (mode & 8) {
-        double ss = 0.0;
+        A ss = A(0);
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
             const int cl = (t * G + lane) * VEC;
             if (cl >= tcols) continue;
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
-                const double y = (double)(out[t][v] * back);
+                const A y = out[t][v] * back;
                 ss += y * y;
             }
         }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) ss += __shfl_xor_sync(gmask, ss, o, G);
-        if (ss > 0.0) inv = 1.0 / sqrt(ss);
+        if (ss > A(0)) inv = A(1) / sqrt(ss);
     }
     const int64_t yrow = perm ? (int64_t)perm[row] : (int64_t)row;
 #pragma unroll
@@ -116,7 +118,7 @@ __device__ __forceinline__ void clenshaw_epilogue(int row, int lane, int col0, i
         A y[VEC];
         if (mode & 8) {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) y[v] = (A)((double)(out[t][v] * back) * inv);
+            for (int v = 0; v < VEC; ++v) y[v] = (out[t][v] * back) * inv;
         } else {
 #pragma unroll
             for (int v = 0; v < VEC; ++v) y[v] = out[t][v] * back;

@@ -66,22 +66,26 @@ __device__ __forceinline__ void mom_epilogue(int row, int lane, int col0, int tc
     }
 }
 
-// Block partials of three fp64 sums -> partials[slot * 3 + q].
-__device__ __forceinline__ void mom_block_partials(double s0, double s1, double s2, int64_t slot,
-                                                   double* __restrict__ partials) {
-    __shared__ double red[3][32];
-    s0 = warp_sum(s0);
-    s1 = warp_sum(s1);
-    s2 = warp_sum(s2);
+// Block partials of the three sums -> partials[slot * 3 + q]: the threads' compensated
+// fp32 sums added as fp32 pairs across the block (no fp64 instruction per thread) and
+// converted to fp64 once.
+__device__ __forceinline__ void mom_block_partials(const KSum (&s)[3], int64_t slot, double* __restrict__ partials) {
+    __shared__ float2 red[3][32];
+    FF v[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) v[q] = warp_sum_ff(s[q].pair());
     const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        red[0][w] = s0; red[1][w] = s1; red[2][w] = s2;
-    }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) red[q][w] = make_float2(v[q].hi, v[q].lo);
     __syncthreads();
     if (threadIdx.x < 3) {
-        double t = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[threadIdx.x][i];
-        partials[slot * 3 + threadIdx.x] = t;
+        FF t{0.f, 0.f};
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            const float2 e = red[threadIdx.x][i];
+            t = ff_add(t, FF{e.x, e.y});
+        }
+        partials[slot * 3 + threadIdx.x] = t.value();
     }
 }
 
@@ -97,7 +101,7 @@ mom_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, 
     const int col0 = blockIdx.y * TW;
     const int tcols = min(TW, ncols - col0);
     const int r1 = part[blockIdx.x + 1];
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    KSum sums[3];
     extern __shared__ int32_t s_csr[];
     sweep_rows<STAGED, G>(rp, ci, lrp, lci, part[blockIdx.x], r1, s_csr, [&](int row, int e0, int e1,
                                                                             const int32_t* idx) {
@@ -107,13 +111,13 @@ mom_step_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, 
         gather_any<STAGED, T, G, NT, false, float>(e0, e1, idx, nullptr, zcur + col0, ld, lane, tcols, acc);
         float p0, p1, p2;
         mom_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, zprev_next, ld, first, op, p0, p1, p2);
-        // the row's degree (d_i of the X-space inner product) is its edge count
-        const double wr = e1 > e0 ? (double)(e1 - e0) : 1.0;
-        s0 += wr * (double)p0;
-        s1 += wr * (double)p1;
-        s2 += wr * (double)p2;
+        // the row's degree (d_i of the X-space inner product) is its edge count (exact in fp32)
+        const float wr = e1 > e0 ? (float)(e1 - e0) : 1.f;
+        sums[0].add(wr * p0);
+        sums[1].add(wr * p1);
+        sums[2].add(wr * p2);
     });
-    mom_block_partials(s0, s1, s2, (int64_t)blockIdx.y * gridDim.x + blockIdx.x, partials);
+    mom_block_partials(sums, (int64_t)blockIdx.y * gridDim.x + blockIdx.x, partials);
 }
 
 // Heavy rows: one CTA per row; partial slots after the regular blocks' (slot_base).
@@ -132,18 +136,18 @@ mom_step_heavy_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict_
     float acc[NT][VEC];
     gather_heavy<T, G, NT, false, float>(__ldg(rp + row), __ldg(rp + row + 1), ci, nullptr, zcur + col0, ld, lane,
                                          tcols, acc);
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    KSum sums[3];
     if (threadIdx.x < G) {
         MomOperands<T, NT> op;
         op.load(row, lane, G, col0, tcols, first, zcur, zprev_next, ld);
         float p0, p1, p2;
         mom_epilogue<T, G, NT>(row, lane, col0, tcols, acc, invdeg, zprev_next, ld, first, op, p0, p1, p2);
-        const double wr = (double)deg[row];
-        s0 = wr * (double)p0;
-        s1 = wr * (double)p1;
-        s2 = wr * (double)p2;
+        const float wr = (float)deg[row];
+        sums[0].add(wr * p0);
+        sums[1].add(wr * p1);
+        sums[2].add(wr * p2);
     }
-    mom_block_partials(s0, s1, s2, slot_base + (int64_t)blockIdx.y * gridDim.x + blockIdx.x, partials);
+    mom_block_partials(sums, slot_base + (int64_t)blockIdx.y * gridDim.x + blockIdx.x, partials);
 }
 
 template <typename T>
