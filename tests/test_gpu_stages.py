@@ -263,6 +263,45 @@ def test_interpolation_column_compaction():
     assert np.array_equal(l0.cpu().numpy(), ointerp.labels_from_indicators(f0.cpu().numpy()))
 
 
+def test_interpolation_compacted_width_shapes():
+    """Each width the compaction reaches runs lane groups of that width (the next power of
+    two of its 16-byte vectors, one column tile) with a row-range count, thread count and
+    form tuned for it and reported like any other tuned shape; a shape pinned for such a
+    width is used as it is, and the solve still meets its target."""
+    g = ci.chung_lu(20_000, exponent=2.1, mean=6.0, seed=3)
+    lap = olap.laplacian(g.row_ptr, g.col_idx)
+    k, n_s = 40, 296
+    om = osamp.sample(g.n, n_s, 4)
+    lab = (np.arange(n_s) % k).astype(np.int32)
+    omd, labd = torch.from_numpy(om).cuda(), torch.from_numpy(lab).cuda()
+    b = ointerp.rhs(g.n, om, lab, k)
+
+    def check(fz):
+        x = fz.cpu().numpy().astype(np.float64)
+        res = ointerp.apply_system(lap, ointerp.mask(g.n, om), 1e-3, 4, x) - b
+        assert np.max(np.linalg.norm(res, axis=0) / np.linalg.norm(b, axis=0)) <= 3e-6
+
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM | csc.DEGREE_ORDER) as h:
+        _, f0, i0 = csc.csc_interpolate(h, omd, labd, k, fuzzy=True, max_iter=5000)
+        narrow = [x for x in csc.csc_graph_tuned_shapes(h) if x["kernel"] == "cg" and x["columns"] < k]
+    assert i0.converged and narrow
+    check(f0)
+    for x in narrow:
+        nv = -(-x["columns"] // 4)
+        lanes = 2
+        while lanes < nv and lanes < 32:
+            lanes *= 2
+        assert (x["G"], x["NT"], x["tiles"]) == (lanes, 1, 1), x
+    w = narrow[0]
+    with csc.csc_graph_create(g.row_ptr, g.col_idx, csc.RCM | csc.DEGREE_ORDER) as h:
+        csc.csc_graph_pin_shape(h, "cg", 4, w["columns"], w["G"], 1, 256, 37, 1, 0, 1)
+        _, f1, i1 = csc.csc_interpolate(h, omd, labd, k, fuzzy=True, max_iter=5000)
+        pinned = [x for x in csc.csc_graph_tuned_shapes(h) if x["kernel"] == "cg" and x["columns"] == w["columns"]]
+    assert i1.converged
+    assert [(x["G"], x["P"], x["threads"], x["lean"]) for x in pinned] == [(w["G"], 37, 256, 1)]
+    check(f1)
+
+
 # ------------------------------------------- interpolation with g = 1 - h~
 
 def _check_highpass(g, om, lab, k, lam, m, gamma, fz, dense=True):
