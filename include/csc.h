@@ -196,7 +196,9 @@ CSC_API csc_status csc_graph_info(csc_graph g, int64_t* N, int64_t* nnz, int32_t
  * (not a step of the paper's method).  Shapes are tuned on first use per kernel
  * kind (1 = Chebyshev step, 2 = moment step, 3 = CG products, 4 = Clenshaw step),
  * storage width and column count, by timing every compiled shape on the handle's
- * graph.  Entry i
+ * graph; a CG solve that compacts its columns (csc_interpolate) also tunes each
+ * narrower width it reaches, with lane groups of that width and one column tile,
+ * and reports it as a kind-3 entry of that column count.  Entry i
  * (0-based) is written to kind, dtype_bytes (4 fp32, 2 bf16, 8 fp64), columns and
  * shape[6] = {lanes per row G, vectors per lane NT, threads per CTA, row ranges P,
  * column tiles, variant}: variant bit 0 = the index source (0: each CTA stages its
@@ -520,8 +522,12 @@ CSC_API csc_status csc_kmeans_reduced(const float* X, int64_t n, int32_t d, int3
 
 /* csc_interpolate -- Alg. 2 step 7: for every cluster j solve Eq. 5,
  * (M^T M + gamma L^g_power) x_j = M^T c_j^r, by Jacobi-preconditioned
- * conjugate gradients (fp32 vectors, fp64 inner products), then label node i
- * with argmax_j x_j(i) / ||x_j|| (Sec. 4.1; ties to the lowest j).
+ * conjugate gradients (fp32 vectors; inner products compensated in fp32 within a
+ * block and summed in fp64 across blocks; one CG per column, a column stopping at
+ * ||r_j|| <= rel_tol ||b_j||), then label node i with argmax_j x_j(i) / ||x_j||
+ * (Sec. 4.1; ties to the lowest j).  Columns that have converged leave the
+ * iteration (the others are compacted into narrower dense blocks); the first solve
+ * that reaches a width tunes a launch shape for it (csc_graph_tuned_shape).
  *   sample_idx     device int64[n]: sampled node ids (distinct).
  *   sample_labels  device int32[n]: their clusters in [0, k).
  *   g_power        >= 1.   gamma > 0.   rel_tol > 0.   max_iter >= 1.
