@@ -195,8 +195,12 @@ def recorded_traffic(workload: str, kernel_class: str, shape: dict | None):
         if not rec:
             return None, f"no ncu capture recorded for {kernel_class} on {workload}"
         want = rec.get("shape")
-        if want and shape and any(shape.get(k) != v for k, v in want.items()):
+        if want and shape and any(shape.get(k) != v for k, v in want.items() if k != "P"):
             return None, f"ncu capture was of shape {want}, this run tuned {shape}"
+        # the same kernel and lane layout over another number of row ranges: the capture's
+        # traffic stands, with the difference stated
+        p_note = (f"; captured with {want['P']} row ranges, this run tuned {shape['P']}"
+                  if want and shape and shape.get("P") != want.get("P") else "")
         h = hashlib.sha256()
         for src in rec["sources"]:
             with open(os.path.join(ROOT, src), "rb") as f:
@@ -205,7 +209,7 @@ def recorded_traffic(workload: str, kernel_class: str, shape: dict | None):
             return None, "kernel source changed since the ncu capture"
         if rec.get("bytes_per_unit") is None:
             return None, rec.get("note")
-        return float(rec["bytes_per_unit"]), rec.get("note")
+        return float(rec["bytes_per_unit"]), (rec.get("note") or "") + p_note
     except (OSError, KeyError, ValueError):
         return None, None
 
