@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <iterator>
 #include <map>
@@ -359,6 +360,49 @@ static void dichotomy(const double* mu, int m, int k, double lo, double hi, csc_
 
 void estimate_from_moments(const double* mu, int m, int k, csc_lambda_info* out) { dichotomy(mu, m, k, 0.0, 2.0, out); }
 
+// ------------------------------------------------------- host row chunks
+// body(r0, r1) over contiguous row chunks of about equal edge counts (rp: row starts,
+// clamped to a nondecreasing sequence so that an unvalidated rp still gives a partition),
+// eight chunks per thread taken in order from a shared counter by up to all host cores;
+// the caller's thread works too.  Each row must be handled independently of the split.
+template <typename F>
+static void for_row_chunks(int64_t N, const int64_t* rp, F&& body) {
+    const int64_t nnz = std::max<int64_t>(rp[N], 0);
+    const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(),
+                                                              (N + nnz) / 65536));
+    if (nt <= 1) {
+        body(0, N);
+        return;
+    }
+    const int64_t nc = nt * 8;
+    std::vector<int64_t> cut(nc + 1, N);
+    cut[0] = 0;
+    for (int64_t c = 1; c < nc; ++c) {
+        // first row whose start reaches c/nc of the edges plus rows (rows weigh one edge)
+        const int64_t target = (nnz + N) * c / nc;
+        int64_t a = cut[c - 1], z = N;
+        while (a < z) {
+            const int64_t mid = (a + z) / 2;
+            if (std::max<int64_t>(rp[mid], 0) + mid >= target) z = mid;
+            else a = mid + 1;
+        }
+        cut[c] = a;
+    }
+    std::atomic<int64_t> next(0);
+    auto worker = [&]() {
+        for (int64_t c; (c = next.fetch_add(1)) < nc;)
+            if (cut[c] < cut[c + 1]) body(cut[c], cut[c + 1]);
+    };
+    std::vector<std::thread> pool;
+    try {
+        for (int64_t t = 1; t < nt; ++t) pool.emplace_back(worker);
+    } catch (const std::system_error&) {
+        // fewer threads than asked for: the chunks are shared among those that started
+    }
+    worker();
+    for (auto& th : pool) th.join();
+}
+
 // --------------------------------------------------------- reverse Cuthill-McKee
 // Stable counting sort of ids by a small integer key (degrees): the same order as a stable
 // comparison sort by that key, in O(N + max key) without per-call allocations.
@@ -378,7 +422,7 @@ static void stable_sort_by_key(std::vector<int32_t>& ids, const std::vector<int3
 // visit order reversed gives perm[new] = old (then sorted by degree within
 // blocks of 128 rows, see below).
 static void rcm_order(int64_t N, const std::vector<int64_t>& rp, const std::vector<int32_t>& ci,
-                      std::vector<int32_t>& perm) {
+                      std::vector<int32_t>& perm, bool block_degree_sort) {
     std::vector<int32_t> deg(N);
     for (int64_t i = 0; i < N; ++i) deg[i] = (int32_t)(rp[i + 1] - rp[i]);
     std::vector<int32_t> order(N);
@@ -418,6 +462,9 @@ static void rcm_order(int64_t N, const std::vector<int64_t>& rp, const std::vect
         }
     }
     perm.assign(visit.rbegin(), visit.rend());
+    // a global stable sort by degree that follows leaves equal-degree rows in this order,
+    // which the block sort below does not change: skipped then
+    if (!block_degree_sort) return;
     // then, within blocks of kDegreeBlock consecutive rows, rows by decreasing degree: the two
     // lane groups of a warp sweep neighbouring rows, which then need about as many gather
     // batches each (power-law degrees otherwise leave one group idle while the other
@@ -448,43 +495,83 @@ static csc_status validate_and_clean(int64_t N, int64_t nnz, const int64_t* row_
     }
     out.N = N;
     out.rp.assign(N + 1, 0);
-    out.ci.clear();
-    out.ci.reserve(nnz);
-    for (int64_t i = 0; i < N; ++i) {
-        const int64_t b = row_ptr[i], e = row_ptr[i + 1];
-        if (e < b || b < 0 || e > nnz) {
-            set_error("row_ptr not nondecreasing at row %lld", (long long)(i + node_base));
-            return CSC_E_CSR;
-        }
-        int64_t prev = -1;
-        for (int64_t p = b; p < e; ++p) {
-            const int64_t c = col_idx[p];
-            if (c < 0 || c >= N) {
-                set_error("col_idx[%lld] = %lld out of range [0, %lld)", (long long)p, (long long)c, (long long)N);
-                return CSC_E_CSR;
+    // first pass, rows in parallel: each row checked as a row-by-row scan would (its extent,
+    // then its columns in order) and its kept (non-loop) entries counted into rp[i + 1]; a
+    // chunk stops at its first bad row, and the lowest bad row of all chunks is reported,
+    // so the message is the one a sequential scan gives
+    struct Bad {
+        int64_t row = -1, pos = 0, col = 0;
+        int kind = 0;  // 1 extent, 2 column out of range, 3 not strictly increasing, 4 asymmetric
+    };
+    std::mutex mu;
+    Bad first;
+    auto note = [&](const Bad& b) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (first.row < 0 || b.row < first.row || (b.row == first.row && b.pos < first.pos)) first = b;
+    };
+    for_row_chunks(N, row_ptr, [&](int64_t r0, int64_t r1) {
+        for (int64_t i = r0; i < r1; ++i) {
+            const int64_t b = row_ptr[i], e = row_ptr[i + 1];
+            if (e < b || b < 0 || e > nnz) {
+                note(Bad{i, 0, 0, 1});
+                return;
             }
-            if (c <= prev) {
-                set_error("row %lld not strictly increasing (duplicate or unsorted column %lld)",
-                          (long long)(i + node_base), (long long)c);
-                return CSC_E_CSR;
-            }
-            prev = c;
-            if (c != i) out.ci.push_back((int32_t)c);
-        }
-        out.rp[i + 1] = (int64_t)out.ci.size();
-    }
-    if (check_sym) {
-        for (int64_t i = 0; i < N; ++i) {
-            for (int64_t p = out.rp[i]; p < out.rp[i + 1]; ++p) {
-                const int32_t j = out.ci[p];
-                const int32_t* b = out.ci.data() + out.rp[j];
-                const int32_t* e = out.ci.data() + out.rp[j + 1];
-                if (!std::binary_search(b, e, (int32_t)i)) {
-                    set_error("matrix not symmetric: (%lld, %d) present, (%d, %lld) missing",
-                              (long long)(i + node_base), j, j, (long long)(i + node_base));
-                    return CSC_E_CSR;
+            int64_t prev = -1, kept = 0;
+            for (int64_t p = b; p < e; ++p) {
+                const int64_t c = col_idx[p];
+                if (c < 0 || c >= N) {
+                    note(Bad{i, p, c, 2});
+                    return;
                 }
+                if (c <= prev) {
+                    note(Bad{i, p, c, 3});
+                    return;
+                }
+                prev = c;
+                kept += c != i ? 1 : 0;
             }
+            out.rp[i + 1] = kept;
+        }
+    });
+    if (first.row >= 0) {
+        if (first.kind == 1)
+            set_error("row_ptr not nondecreasing at row %lld", (long long)(first.row + node_base));
+        else if (first.kind == 2)
+            set_error("col_idx[%lld] = %lld out of range [0, %lld)", (long long)first.pos, (long long)first.col,
+                      (long long)N);
+        else
+            set_error("row %lld not strictly increasing (duplicate or unsorted column %lld)",
+                      (long long)(first.row + node_base), (long long)first.col);
+        return CSC_E_CSR;
+    }
+    for (int64_t i = 0; i < N; ++i) out.rp[i + 1] += out.rp[i];
+    out.ci.resize((size_t)out.rp[N]);
+    // second pass: the kept entries of each row copied to its new start
+    for_row_chunks(N, row_ptr, [&](int64_t r0, int64_t r1) {
+        for (int64_t i = r0; i < r1; ++i) {
+            int64_t w = out.rp[i];
+            for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
+                if (col_idx[p] != i) out.ci[w++] = col_idx[p];
+        }
+    });
+    if (check_sym) {
+        for_row_chunks(N, out.rp.data(), [&](int64_t r0, int64_t r1) {
+            for (int64_t i = r0; i < r1; ++i)
+                for (int64_t p = out.rp[i]; p < out.rp[i + 1]; ++p) {
+                    const int32_t j = out.ci[p];
+                    const int32_t* b = out.ci.data() + out.rp[j];
+                    const int32_t* e = out.ci.data() + out.rp[j + 1];
+                    if (!std::binary_search(b, e, (int32_t)i)) {
+                        note(Bad{i, p, j, 4});
+                        return;
+                    }
+                }
+        });
+        if (first.row >= 0) {
+            set_error("matrix not symmetric: (%lld, %lld) present, (%lld, %lld) missing",
+                      (long long)(first.row + node_base), (long long)first.col, (long long)first.col,
+                      (long long)(first.row + node_base));
+            return CSC_E_CSR;
         }
     }
     return CSC_OK;
@@ -501,34 +588,17 @@ static void permute_csr(const HostCSR& in, const std::vector<int32_t>& perm, Hos
         const int32_t o = perm[p];
         out.rp[p + 1] = out.rp[p] + (in.rp[o + 1] - in.rp[o]);
     }
-    // rows relabelled and sorted independently: split over the host's cores in contiguous
-    // chunks of rows (the result does not depend on the split)
-    auto rows = [&](int64_t p0, int64_t p1) {
+    // rows relabelled and sorted independently, in chunks of about equal edge counts over
+    // the host's cores (the hub rows, which the degree orders put first, do not all fall to
+    // one thread; the result does not depend on the split)
+    for_row_chunks(N, out.rp.data(), [&](int64_t p0, int64_t p1) {
         for (int64_t p = p0; p < p1; ++p) {
             const int32_t o = perm[p];
             int64_t w = out.rp[p];
             for (int64_t e = in.rp[o]; e < in.rp[o + 1]; ++e) out.ci[w++] = iperm[in.ci[e]];
             std::sort(out.ci.begin() + out.rp[p], out.ci.begin() + out.rp[p + 1]);
         }
-    };
-    const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), N / 65536));
-    if (nt <= 1) {
-        rows(0, N);
-        return;
-    }
-    std::vector<std::thread> pool;
-    try {
-        for (int64_t t = 1; t < nt; ++t) pool.emplace_back(rows, N * t / nt, N * (t + 1) / nt);
-    } catch (const std::system_error&) {
-        // no more threads: the rest of the rows on this one
-        for (auto& th : pool) th.join();
-        const int64_t done = (int64_t)pool.size();
-        rows(0, N / nt);
-        rows(N * (done + 1) / nt, N);
-        return;
-    }
-    rows(0, N / nt);
-    for (auto& th : pool) th.join();
+    });
 }
 
 static void free_graph(Graph* g) {
@@ -759,7 +829,7 @@ csc_status csc_graph_create(int64_t N, int64_t nnz, const int64_t* row_ptr, cons
     if (flags & (CSC_RCM | CSC_DEGREE_ORDER)) {
         std::vector<int32_t> perm;
         if (flags & CSC_RCM) {
-            rcm_order(N, clean.rp, clean.ci, perm);
+            rcm_order(N, clean.rp, clean.ci, perm, (flags & CSC_DEGREE_ORDER) == 0);
         } else {
             perm.resize(N);
             std::iota(perm.begin(), perm.end(), 0);

@@ -41,6 +41,37 @@ def test_malformed_csr_rejected(L, rp, cols, flags):
     assert len(L.lib().csc_last_error()) > 0
 
 
+def _ring(n, k):
+    """Circulant graph: node i joined to i +- 1..k (mod n), rows sorted."""
+    cols = np.sort((np.arange(n)[:, None] + np.r_[-k:0, 1:k + 1][None, :]) % n, axis=1)
+    return np.arange(0, 2 * k * n + 1, 2 * k, dtype=np.int64), cols.astype(np.int32).ravel()
+
+
+@pytest.mark.parametrize("flags", [0, 2])
+def test_malformed_large_csr_reports_first_bad_row(L, flags):
+    """A CSR large enough to be checked by several host threads: with faults planted in a
+    late and an early row (and, with CSC_CHECK_SYM, asymmetric rows), the message names
+    the earliest fault, as a row-by-row scan would."""
+    n, k = 300_000, 3
+    rp, cols = _ring(n, k)
+    late, early = 250_123, 40_007
+    for row in (late, early):
+        a = rp[row]
+        cols[a], cols[a + 1] = cols[a + 1], cols[a]  # unsorted row
+    st, h = _create(L, rp, cols, flags)
+    assert st == L.CSC_E_CSR and not h.value
+    msg = L.lib().csc_last_error().decode()
+    assert f"row {early} not strictly increasing" in msg, msg
+    if flags:
+        rp, cols = _ring(n, k)
+        for row in (late, early):
+            cols[rp[row] + 2 * k - 1] = (row + k + 1) % n  # (row, row + k) -> (row, row + k + 1), still sorted
+        st, h = _create(L, rp, cols, flags)
+        assert st == L.CSC_E_CSR and not h.value
+        msg = L.lib().csc_last_error().decode()
+        assert msg.startswith(f"matrix not symmetric: ({early}, {early + k + 1}) present"), msg
+
+
 def test_invalid_arguments(L):
     out = ctypes.c_void_p()
     assert L.lib().csc_graph_create(0, 0, None, None, None, 0, None, ctypes.byref(out)) == L.CSC_E_INVALID
