@@ -2,6 +2,7 @@
 // mathematics (Jackson-Chebyshev coefficients, the eigencount dichotomy,
 // reverse Cuthill-McKee) and the Alg. 2 pipeline driver.
 #include <math.h>
+#include <stdint.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -11,6 +12,7 @@
 #include <chrono>
 #include <iterator>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <numeric>
@@ -362,12 +364,14 @@ void estimate_from_moments(const double* mu, int m, int k, csc_lambda_info* out)
 
 // ------------------------------------------------------- host row chunks
 // body(r0, r1) over contiguous row chunks of about equal edge counts (rp: row starts,
-// clamped to a nondecreasing sequence so that an unvalidated rp still gives a partition),
-// eight chunks per thread taken in order from a shared counter by up to all host cores;
-// the caller's thread works too.  Each row must be handled independently of the split.
+// clamped to a nondecreasing sequence so that an unvalidated rp still gives a partition;
+// NULL: rows of equal weight), eight chunks per thread taken in order from a shared
+// counter by up to all host cores; the caller's thread works too.  Each row must be
+// handled independently of the split.
 template <typename F>
 static void for_row_chunks(int64_t N, const int64_t* rp, F&& body) {
-    const int64_t nnz = std::max<int64_t>(rp[N], 0);
+    auto start = [&](int64_t i) { return rp ? std::max<int64_t>(rp[i], 0) : 0; };
+    const int64_t nnz = start(N);
     const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(),
                                                               (N + nnz) / 65536));
     if (nt <= 1) {
@@ -383,7 +387,7 @@ static void for_row_chunks(int64_t N, const int64_t* rp, F&& body) {
         int64_t a = cut[c - 1], z = N;
         while (a < z) {
             const int64_t mid = (a + z) / 2;
-            if (std::max<int64_t>(rp[mid], 0) + mid >= target) z = mid;
+            if (start(mid) + mid >= target) z = mid;
             else a = mid + 1;
         }
         cut[c] = a;
@@ -432,33 +436,104 @@ static void rcm_order(int64_t N, const std::vector<int64_t>& rp, const std::vect
     std::vector<int32_t> visit;
     visit.reserve(N);
     std::vector<int32_t> nb;
+    // neighbours by increasing degree, ties in index order (a stable sort); short lists by
+    // insertion, which allocates nothing
+    auto by_degree = [&](std::vector<int32_t>& l) {
+        if (l.size() <= 32) {
+            for (size_t i = 1; i < l.size(); ++i) {
+                const int32_t v = l[i];
+                size_t j = i;
+                for (; j > 0 && deg[l[j - 1]] > deg[v]; --j) l[j] = l[j - 1];
+                l[j] = v;
+            }
+        } else {
+            std::stable_sort(l.begin(), l.end(), [&](int32_t a, int32_t b) { return deg[a] < deg[b]; });
+        }
+    };
+    // A large level is expanded on all host cores with the same result: a node of the next
+    // level belongs to the first node of this level (in visit order) adjacent to it, and
+    // each node's own new neighbours follow in the order above, so the next level is its
+    // nodes' neighbour lists concatenated in visit order.  owner[v] collects that first
+    // position (an atomic minimum); owner is unset (INT32_MAX) for every other node.
+    std::unique_ptr<std::atomic<int32_t>[]> owner;
+    std::vector<int64_t> wsum, cnt;
+    auto expand_parallel = [&](int64_t l0, int64_t l1) {
+        if (!owner) {
+            owner.reset(new std::atomic<int32_t>[N]);
+            for (int64_t i = 0; i < N; ++i) owner[i].store(INT32_MAX, std::memory_order_relaxed);
+        }
+        const int64_t nl = l1 - l0;
+        wsum.assign(nl + 1, 0);
+        for (int64_t i = 0; i < nl; ++i) wsum[i + 1] = wsum[i] + deg[visit[l0 + i]];
+        for_row_chunks(nl, wsum.data(), [&](int64_t i0, int64_t i1) {
+            for (int64_t i = i0; i < i1; ++i) {
+                const int32_t u = visit[l0 + i], pos = (int32_t)(l0 + i);
+                for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+                    const int32_t v = ci[e];
+                    if (seen[v]) continue;
+                    int32_t cur = owner[v].load(std::memory_order_relaxed);
+                    while (pos < cur && !owner[v].compare_exchange_weak(cur, pos, std::memory_order_relaxed)) {
+                    }
+                }
+            }
+        });
+        cnt.assign(nl + 1, 0);
+        for_row_chunks(nl, wsum.data(), [&](int64_t i0, int64_t i1) {
+            for (int64_t i = i0; i < i1; ++i) {
+                const int32_t u = visit[l0 + i], pos = (int32_t)(l0 + i);
+                int64_t c = 0;
+                for (int64_t e = rp[u]; e < rp[u + 1]; ++e) c += owner[ci[e]].load(std::memory_order_relaxed) == pos;
+                cnt[i + 1] = c;
+            }
+        });
+        for (int64_t i = 0; i < nl; ++i) cnt[i + 1] += cnt[i];
+        visit.resize((size_t)(l1 + cnt[nl]));
+        for_row_chunks(nl, wsum.data(), [&](int64_t i0, int64_t i1) {
+            std::vector<int32_t> kids;
+            for (int64_t i = i0; i < i1; ++i) {
+                const int32_t u = visit[l0 + i], pos = (int32_t)(l0 + i);
+                kids.clear();
+                for (int64_t e = rp[u]; e < rp[u + 1]; ++e)
+                    if (owner[ci[e]].load(std::memory_order_relaxed) == pos) kids.push_back(ci[e]);
+                by_degree(kids);
+                std::copy(kids.begin(), kids.end(), visit.begin() + l1 + cnt[i]);
+            }
+        });
+        for_row_chunks(cnt[nl], nullptr, [&](int64_t j0, int64_t j1) {
+            for (int64_t j = j0; j < j1; ++j) {
+                const int32_t v = visit[l1 + j];
+                seen[v] = 1;
+                owner[v].store(INT32_MAX, std::memory_order_relaxed);
+            }
+        });
+    };
+    constexpr int64_t kParallelLevel = 1 << 17;  // edges + nodes of a level worth the threads
     for (int64_t s = 0; s < N; ++s) {
         const int32_t start = order[s];
         if (seen[start]) continue;
-        size_t head = visit.size();
+        int64_t l0 = (int64_t)visit.size();
         visit.push_back(start);
         seen[start] = 1;
-        while (head < visit.size()) {
-            const int32_t u = visit[head++];
-            nb.clear();
-            for (int64_t e = rp[u]; e < rp[u + 1]; ++e)
-                if (!seen[ci[e]]) {
-                    seen[ci[e]] = 1;
-                    nb.push_back(ci[e]);
-                }
-            // neighbours by increasing degree, ties in index order (a stable sort); short
-            // lists by insertion, which allocates nothing
-            if (nb.size() <= 32) {
-                for (size_t i = 1; i < nb.size(); ++i) {
-                    const int32_t v = nb[i];
-                    size_t j = i;
-                    for (; j > 0 && deg[nb[j - 1]] > deg[v]; --j) nb[j] = nb[j - 1];
-                    nb[j] = v;
-                }
+        while (l0 < (int64_t)visit.size()) {  // one level [l0, l1) at a time
+            const int64_t l1 = (int64_t)visit.size();
+            int64_t work = l1 - l0;
+            for (int64_t i = l0; i < l1 && work < kParallelLevel; ++i) work += deg[visit[i]];
+            if (work >= kParallelLevel && std::thread::hardware_concurrency() > 1) {
+                expand_parallel(l0, l1);
             } else {
-                std::stable_sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) { return deg[a] < deg[b]; });
+                for (int64_t i = l0; i < l1; ++i) {
+                    const int32_t u = visit[i];
+                    nb.clear();
+                    for (int64_t e = rp[u]; e < rp[u + 1]; ++e)
+                        if (!seen[ci[e]]) {
+                            seen[ci[e]] = 1;
+                            nb.push_back(ci[e]);
+                        }
+                    by_degree(nb);
+                    visit.insert(visit.end(), nb.begin(), nb.end());
+                }
             }
-            visit.insert(visit.end(), nb.begin(), nb.end());
+            l0 = l1;
         }
     }
     perm.assign(visit.rbegin(), visit.rend());
