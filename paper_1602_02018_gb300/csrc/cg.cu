@@ -16,8 +16,9 @@
 //
 // Launch shape (every kernel of one solve): CTA x sweeps the contiguous row
 // range [part[x], part[x+1]) with G lanes per row; CTA y covers the column tile
-// [y*TW, (y+1)*TW), TW = 4*G*NT.  The shape is tuned once per graph and k, and
-// narrowed with the compacted width.
+// [y*TW, (y+1)*TW), TW = 4*G*NT.  The shape is tuned once per graph and k; each
+// compacted width takes lane groups of its own width (one column tile) with a row-range
+// count, thread count and kernel form tuned for that width.
 #include <math.h>
 #include <stdio.h>
 
