@@ -1193,7 +1193,15 @@ csc_status run_interpolate(Graph* g, const int64_t* sample_idx, const int32_t* s
                 c = it->second;
                 have = true;
             } else if (tune_cache_get(g, wkey, &c)) {
+                // tuned on another handle of the same size: its staged slices must fit here
                 have = true;
+                if (c.staged) {
+                    const int32_t* pr = nullptr;
+                    CSC_TRY(get_partition(g, c.P, &pr));
+                    int room = 0;
+                    CG_SWITCH(c, room = cg_staged_room<G_, NT_>());
+                    if (staged_smem(g, c.P) > std::min(room, kStagedSmemMax)) have = false;
+                }
             }
             if (have && c.P > max_p) have = false;
             if (!have) {
