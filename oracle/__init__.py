@@ -21,6 +21,10 @@ Modules, each following the passage it cites:
 * ``ari``        adjusted Rand index (Hubert & Arabie 1985, Sec. 5.2).
 * ``pipeline``   Alg. 2 end to end.
 * ``mlp``        FP64 forward/backward of the bracket-predicting MLP.
+* ``bracket``    features and targets of the learned lambda_k bracket (the eigencount
+  of Sec. 4.3 stays the judge of the predicted interval).
+* ``sc``         dense spectral clustering, Alg. 1 (Sec. 2.2), the comparison baseline
+  of the small recovery sweeps.
 
 Parity status of every function is stated in its module header; functions
 without an independent pin say "parity unpinned".
