@@ -313,7 +313,7 @@ CSC_API csc_status csc_estimate_lambda_k_refilter(csc_graph g, int32_t k, int32_
 
 /* ------------------------------------------- learned lambda_k bracket
  * The paper is silent on learning lambda_k; these calls add a predictor of a
- * bracket for the Sec. 4.3 dichotomy, and the eigencount remains the judge:
+ * bracket for the Sec. 4.3 dichotomy, and the eigencount still decides:
  * a bracket is used only when the eigencount confirms it, otherwise the
  * plain dichotomy runs.  The predictor is a 72 -> 256 -> 256 -> 2 ReLU
  * perceptron (smooth-L1 loss, Adam) trained on the device by the calls below.
@@ -327,7 +327,7 @@ CSC_API csc_status csc_estimate_lambda_k_refilter(csc_graph g, int32_t k, int32_
 #define CSC_BRACKET_PROBES 8
 #define CSC_BRACKET_MOMENTS 64
 /* flags of csc_estimate_lambda_k_learned */
-#define CSC_EIGENCOUNT_REFILTER 1u /* judge the bracket with the paper-literal estimator */
+#define CSC_EIGENCOUNT_REFILTER 1u /* check the bracket with the paper-literal estimator */
 
 /* csc_bracket_features -- the 72 predictor inputs of one graph (host float[72]):
  * [0, 64) eigencount moments mu_j / N of CSC_BRACKET_PROBES N(0, 1) probes
@@ -493,7 +493,7 @@ CSC_API csc_status csc_coherence_scores(void* Y, csc_dtype y_type, int64_t N, in
  *   w_out    NULL or device float[n]: each draw's decoder weight Q / (N q_i)
  *            (FP64, rounded to float): 1 for a flat profile.
  *   1 <= N < 2^31, 0 <= n < 2^31.  Synchronizes `stream` (the scores are checked
- *   on the device and the verdict read back).
+ *   on the device and the outcome read back).
  * Errors: CSC_E_INVALID (arguments; a negative, NaN or infinite score; every score
  * zero), CSC_E_OOM. */
 CSC_API csc_status csc_sample_weighted(const double* score, int64_t N, int64_t n, uint64_t seed, int64_t* idx_out,

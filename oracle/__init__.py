@@ -22,7 +22,7 @@ Modules, each following the passage it cites:
 * ``pipeline``   Alg. 2 end to end.
 * ``mlp``        FP64 forward/backward of the bracket-predicting MLP.
 * ``bracket``    features and targets of the learned lambda_k bracket (the eigencount
-  of Sec. 4.3 stays the judge of the predicted interval).
+  of Sec. 4.3 still decides whether the predicted interval holds an answer).
 * ``sc``         dense spectral clustering, Alg. 1 (Sec. 2.2), the comparison baseline
   of the small recovery sweeps.
 

@@ -3,7 +3,7 @@
 The paper estimates lambda_k by a dichotomy on an eigencount (Sec. 4.3) and is
 silent on learning it.  The learned predictor maps cheap graph statistics to
 an interval that should contain an acceptable dichotomy answer; the eigencount
-stays the judge of that interval.  Readings:
+still decides whether that interval holds one.  Readings:
 
 * Features (72 values):
     0..63   mu_j / N, j = 0..63: eigencount moments (Sec. 4.3 estimator) of
