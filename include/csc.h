@@ -57,7 +57,7 @@ typedef int32_t csc_status;
 #define CSC_E_NOT_CONVERGED    5  /* iterative solver hit max_iter; outputs valid */
 #define CSC_E_DEVICE_TIMEOUT   6  /* reserved: no entry point waits on the device  */
 #define CSC_E_NUMERIC          7  /* non-finite values detected (CSC_CHECK_FINITE) */
-#define CSC_E_UNSUPPORTED      8  /* valid but outside what this build supports   */
+#define CSC_E_UNSUPPORTED      8  /* valid but outside what the library supports  */
 
 /* storage type of the signal blocks */
 typedef int32_t csc_dtype;

@@ -728,7 +728,7 @@ static csc_status upload(Graph* g, const HostCSR& h, const std::vector<int32_t>*
     const int64_t N = h.N;
     const int64_t nnz = (int64_t)h.ci.size();
     if (nnz >= (int64_t)INT32_MAX) {
-        set_error("nnz = %lld exceeds the int32 row-pointer range of this build", (long long)nnz);
+        set_error("nnz = %lld exceeds the int32 row-pointer range of the library", (long long)nnz);
         return CSC_E_UNSUPPORTED;
     }
     g->N = N;
@@ -1447,7 +1447,7 @@ csc_status csc_kmeans_reduced(const float* X, int64_t n, int32_t d, int32_t ld, 
         return CSC_E_INVALID;
     }
     if (k > 1024 || d > 256) {
-        set_error("csc_kmeans_reduced: k <= 1024 and d <= 256 in this build");
+        set_error("csc_kmeans_reduced: k <= 1024 and d <= 256 in this library");
         return CSC_E_UNSUPPORTED;
     }
     return run_kmeans(X, n, d, ld, k, replicates, max_iter, seed, labels_out, inertia_out, nullptr,
