@@ -572,8 +572,9 @@ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t t) {
 // ------------------------------------------------------------ reductions
 // fp64 instructions issue at a small fraction of the fp32 rate on this part, so sums
 // that need more than fp32 accuracy run on fp32 pairs: per thread a compensated (Kahan)
-// sum, between threads an unevaluated pair hi + lo added with Knuth's error-free
-// two-sum (about 48 significant bits), converted to fp64 once per block.
+// sum (its result carries about one fp32 rounding of its magnitude), between threads an
+// unevaluated pair hi + lo added with Knuth's error-free two-sum (the pair additions keep
+// about 48 significant bits), converted to fp64 once per block.
 struct FF {
     float hi, lo;
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
